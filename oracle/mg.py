@@ -1,0 +1,259 @@
+"""Geometric p-multigrid preconditioned Krylov solve, FP64, assembled matrices.
+
+Test infrastructure only (see ``oracle/__init__``).
+
+Paper passages followed (Sec. 5):
+  * level hierarchy: same mesh, orders P_{n-1} = ceil((P_n + 1)/2)          (Sec. 5.1)
+    (iterated down to 2, then order 1 appended: the rule's fixed point is 2)
+  * each level re-discretised on the same cells ("geometric" p-MG), either on
+    the actual geometry or on the flat, linearised geometry eta = 0 that makes
+    the preconditioner time-constant                                        (Sec. 5, Sec. 5.4)
+  * prolongation = interpolation of the coarse polynomial at the fine nodes,
+    I = Phi V^{-1} per element; restriction R = P^T                        (Sec. 5.2)
+  * additive Schwarz smoother  x <- x - S^{-1}(A x - b),
+    S^{-1} = W sum_i R_i^T (R_i A R_i^T)^{-1} R_i,  W = (sum_i R_i R_i^T)^{-1},
+    subdomain = element block plus `overlap` node lines of the neighbours   (Sec. 5.3)
+    with damping omega; post-smoothing uses the adjoint S^{-T} (W on the right)
+    so that the V-cycle is a symmetric preconditioner for CG
+  * V-cycle                                                               (Sec. 5, Fig. V-cycle)
+  * outer methods: PCG, flexible CG, and preconditioned defect correction
+    x <- x + B (b - A x)                                                  (Sec. 5.4)
+
+The coarsest level (order 1) is solved exactly by a sparse LU (library primitive).
+
+Parity status: the V-cycle's quality (iteration counts) is "parity unpinned" by the
+paper, which prints no iteration count for this operator; tests pin its symmetry and
+positivity, exact-solve limits, and the flat iteration counts in N_x and P claimed in
+Sec. 6.3.
+"""
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from . import basis
+from .sem import Mesh, lifted_system
+
+
+class Level:
+    def __init__(self, mesh, A, overlap):
+        self.mesh = mesh
+        self.dmask = mesh.dirichlet_mask()
+        self.free = np.flatnonzero(~self.dmask)
+        self.A = sp.csr_matrix(A)[self.free][:, self.free]      # A_FF of this level
+        self.pos = -np.ones(mesh.N, dtype=np.int64)             # global -> free index
+        self.pos[self.free] = np.arange(self.free.size)
+        self.overlap = overlap
+        self.blocks = None
+        self.W = None
+
+    def build_schwarz(self):
+        """Subdomains R_i (element nodes + overlap lines, free nodes only), the dense
+        Cholesky factors of R_i A R_i^T, and W = (sum R_i R_i^T)^{-1} (Sec. 5.3)."""
+        m, o = self.mesh, self.overlap
+        P = m.P
+        blocks = []
+        count = np.zeros(self.free.size)
+        for ex in range(m.Nx):
+            xs = np.arange(ex * P - o, ex * P + P + o + 1)
+            if m.periodic:
+                xs = np.unique(xs % m.NX)
+            else:
+                xs = xs[(xs >= 0) & (xs < m.NX)]
+            for ez in range(m.Nz):
+                zs = np.arange(ez * P - o, ez * P + P + o + 1)
+                zs = zs[(zs >= 0) & (zs < m.NZ - 1)]                  # drop the Dirichlet row
+                g = (xs[:, None] * m.NZ + zs[None, :]).reshape(-1)
+                idx = self.pos[g]
+                assert np.all(idx >= 0)
+                Ai = self.A[idx][:, idx].toarray()
+                blocks.append((idx, sla.cho_factor(Ai)))
+                count[idx] += 1.0
+        self.blocks = blocks
+        self.W = 1.0 / count
+
+    def schwarz(self, r):
+        """sum_i R_i^T (R_i A R_i^T)^{-1} R_i r."""
+        out = np.zeros_like(r)
+        for idx, c in self.blocks:
+            out[idx] += sla.cho_solve(c, r[idx])
+        return out
+
+
+class Hierarchy:
+    """p-multigrid hierarchy on free nodes.
+
+    geometry: 'flat' (eta = 0 for every level: the paper's time-constant
+    preconditioner) or 'actual' (each level re-discretised on eta interpolated to
+    the level's nodes).
+    """
+
+    def __init__(self, mesh, eta, orders=None, overlap=1, nu=2, omega=1.0, geometry='flat'):
+        self.orders = list(orders) if orders is not None else basis.coarsening_sequence(mesh.P)
+        assert self.orders[0] == mesh.P
+        self.nu, self.omega = nu, omega
+        self.levels = []
+        self.P = []                      # prolongations level l+1 -> l on free nodes
+        eta = np.asarray(eta, float)
+        for l, p in enumerate(self.orders):
+            ml = Mesh(mesh.Nx, mesh.Nz, p, mesh.x0, mesh.x1, mesh.h, mesh.periodic)
+            if geometry == 'flat':
+                eta_l = np.zeros(ml.NX)
+            else:
+                eta_l = self._eta_at_level(mesh, eta, ml)
+            lev = Level(ml, ml.assemble(eta_l), overlap)
+            if l < len(self.orders) - 1:
+                lev.build_schwarz()
+            self.levels.append(lev)
+        for l in range(len(self.orders) - 1):
+            self.P.append(self._prolongation(self.levels[l], self.levels[l + 1]))
+        c = self.levels[-1]
+        self.coarse_lu = spla.splu(sp.csc_matrix(c.A))
+
+    @staticmethod
+    def _eta_at_level(fine, eta, ml):
+        """Evaluate the fine-level surface polynomial of each cell at the level's nodes."""
+        I = basis.transfer_1d(fine.P, ml.P) if ml.P != fine.P else np.eye(fine.P + 1)
+        # I maps order-P nodal values to order-p nodes when p < P (evaluation of the fine
+        # polynomial at the coarse nodes): Phi^{p-nodes} V_P^{-1}.
+        out = np.zeros(ml.NX)
+        for ex in range(fine.Nx):
+            cf = (ex * fine.P + np.arange(fine.P + 1)) % fine.NX if fine.periodic else ex * fine.P + np.arange(fine.P + 1)
+            cc = (ex * ml.P + np.arange(ml.P + 1)) % ml.NX if ml.periodic else ex * ml.P + np.arange(ml.P + 1)
+            out[cc] = I @ eta[cf]
+        return out
+
+    @staticmethod
+    def _prolongation(fine, coarse):
+        """P = D_f^{-1} Q_f^T (J (x) J)_blk Q_c restricted to free nodes (Sec. 5.2).
+
+        J = transfer_1d(p_c, p_f): coarse modal expansion evaluated at fine nodes.
+        D_f = multiplicity of each fine global node (element copies agree, so this
+        averages identical values).
+        """
+        mf, mc = fine.mesh, coarse.mesh
+        J = basis.transfer_1d(mc.P, mf.P)
+        B = np.kron(J, J)                                       # (nf^2, nc^2)
+        E = mf.Nx * mf.Nz
+        rows = np.repeat(mf.e2g[:, :, None], B.shape[1], axis=2).reshape(-1)
+        cols = np.repeat(mc.e2g[:, None, :], B.shape[0], axis=1).reshape(-1)
+        vals = np.tile(B.reshape(-1), E)
+        S = sp.coo_matrix((vals, (rows, cols)), shape=(mf.N, mc.N)).tocsr()
+        mult = np.bincount(mf.e2g.reshape(-1), minlength=mf.N).astype(float)
+        Pg = sp.diags(1.0 / mult) @ S
+        return sp.csr_matrix(Pg[fine.free][:, coarse.free])
+
+    # --- smoothing and V-cycle ------------------------------------------------------
+    def smooth(self, l, b, x, post):
+        lev = self.levels[l]
+        for _ in range(self.nu):
+            r = b - lev.A @ x
+            if post:
+                x = x + self.omega * lev.schwarz(lev.W * r)
+            else:
+                x = x + self.omega * lev.W * lev.schwarz(r)
+        return x
+
+    def vcycle(self, b, l=0):
+        """One V-cycle for A_l x = b from x = 0: pre-smooth, restrict the residual,
+        recurse, prolong the correction, post-smooth.  Coarsest level: exact solve."""
+        if l == len(self.levels) - 1:
+            return self.coarse_lu.solve(b)
+        lev = self.levels[l]
+        x = self.smooth(l, b, np.zeros_like(b), post=False)
+        r = b - lev.A @ x
+        rc = self.P[l].T @ r
+        x = x + self.P[l] @ self.vcycle(rc, l + 1)
+        return self.smooth(l, b, x, post=True)
+
+
+def pcg(A, b, prec, x0=None, tol=1e-10, maxit=500):
+    """Preconditioned CG; stops when ||r||_2 / ||b||_2 <= tol (recursive residual).
+    Returns (x, iterations, relres history)."""
+    x = np.zeros_like(b) if x0 is None else np.array(x0, float, copy=True)
+    nb = np.linalg.norm(b)
+    if nb == 0.0:
+        return np.zeros_like(b), 0, [0.0]
+    r = b - A @ x
+    hist = [np.linalg.norm(r) / nb]
+    if hist[-1] <= tol:
+        return x, 0, hist
+    z = prec(r)
+    p = z.copy()
+    rz = r @ z
+    for k in range(1, maxit + 1):
+        Ap = A @ p
+        alpha = rz / (p @ Ap)
+        x = x + alpha * p
+        r = r - alpha * Ap
+        hist.append(np.linalg.norm(r) / nb)
+        if hist[-1] <= tol:
+            return x, k, hist
+        z = prec(r)
+        rz_new = r @ z
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    return x, maxit, hist
+
+
+def fcg(A, b, prec, x0=None, tol=1e-10, maxit=500):
+    """Flexible CG with the Polak-Ribiere beta = <z_k, r_k - r_{k-1}> / <z_{k-1}, r_{k-1}>."""
+    x = np.zeros_like(b) if x0 is None else np.array(x0, float, copy=True)
+    nb = np.linalg.norm(b)
+    if nb == 0.0:
+        return np.zeros_like(b), 0, [0.0]
+    r = b - A @ x
+    hist = [np.linalg.norm(r) / nb]
+    if hist[-1] <= tol:
+        return x, 0, hist
+    z = prec(r)
+    p = z.copy()
+    rz = r @ z
+    for k in range(1, maxit + 1):
+        Ap = A @ p
+        alpha = rz / (p @ Ap)
+        x = x + alpha * p
+        r_old = r
+        r = r - alpha * Ap
+        hist.append(np.linalg.norm(r) / nb)
+        if hist[-1] <= tol:
+            return x, k, hist
+        z = prec(r)
+        beta = (z @ (r - r_old)) / rz
+        rz = r @ z
+        p = z + beta * p
+    return x, maxit, hist
+
+
+def pdc(A, b, prec, x0=None, tol=1e-10, maxit=500):
+    """Preconditioned defect correction x <- x + B (b - A x) (Sec. 5.4)."""
+    x = np.zeros_like(b) if x0 is None else np.array(x0, float, copy=True)
+    nb = np.linalg.norm(b)
+    if nb == 0.0:
+        return np.zeros_like(b), 0, [0.0]
+    hist = []
+    for k in range(0, maxit + 1):
+        r = b - A @ x
+        hist.append(np.linalg.norm(r) / nb)
+        if hist[-1] <= tol:
+            return x, k, hist
+        x = x + prec(r)
+    return x, maxit, hist
+
+
+def solve(mesh, eta, b, p_dirichlet, hier=None, method='pcg', x0=None, tol=1e-10, maxit=500,
+          **hier_kw):
+    """Full solve on the actual geometry: Dirichlet lifting, then the preconditioned
+    Krylov method on A_FF with one V-cycle of `hier` as the preconditioner.
+    Returns (p full-length, iterations, history, hierarchy)."""
+    A = mesh.assemble(eta)
+    dmask = mesh.dirichlet_mask()
+    AFF, bt, free = lifted_system(A, b, p_dirichlet, dmask)
+    if hier is None:
+        hier = Hierarchy(mesh, eta, **hier_kw)
+    x0f = None if x0 is None else np.asarray(x0, float)[free]
+    f = {'pcg': pcg, 'fcg': fcg, 'pdc': pdc}[method]
+    xf, its, hist = f(AFF, bt, hier.vcycle, x0=x0f, tol=tol, maxit=maxit)
+    p = np.array(p_dirichlet, float, copy=True)
+    p[free] = xf
+    return p, its, hist, hier

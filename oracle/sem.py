@@ -1,0 +1,280 @@
+"""Sigma-mapped quadrilateral SEM discretisation of the pressure-Poisson problem, FP64.
+
+Test infrastructure only (see ``oracle/__init__``).
+
+Problem (the same-geometry symmetric reading of the paper's pressure-Poisson BVP):
+find p_h in V_P, p_h = p_D on the free surface (Sec. 3.2, p_D = 0 condition), with
+    a(N_i, p_h) = l(N_i)  for every free node i,
+    a(v, p) = int_Omega grad v . grad p dOmega                                (Sec. 4.2)
+    l(v)    = -int_Omega v f dOmega + int_{Gamma_N} v g dGamma                 (Neumann, Sec. 3.2)
+pulled back to the sigma-domain by the vertical map sigma = (z + h)/d, d = eta + h
+(Sec. 2.2), on a structured mesh of N_x x N_z quads (Sec. 4.3) with LGL nodes.
+
+Node numbering (shared by the CUDA path's ABI, defined there independently):
+    g = ix * NZ + iz,  ix in [0, NX), iz in [0, NZ),  NZ = N_z P + 1,
+    NX = N_x P + 1 (walls) or N_x P (periodic in x).  iz = NZ - 1 is the free surface.
+
+Quadrature: LGL collocation at the (P+1)^2 element nodes for stiffness, mass and
+load; the element matrices are formed densely from that definition:
+    K_e = Gx^T diag(w J) Gx + Gz^T diag(w J) Gz,  Gx = R_x Dr + S_x Ds, ...
+where (r_x, s_x, r_z, s_z) and J come from the isoparametric map of the nodal
+coordinates (x*, z = sigma d(x) - h) (Sec. 4.3, D_x = R_x D_r).
+
+Pins (tests/test_oracle_operator.py): flat element factors equal |J| D^T M D with the
+exact mass of Sec. 4.3; exactness of a(N_i, l) for physical linear l against boundary
+fluxes on a curved mesh; symmetry; SPD of A_FF; pure-Neumann A 1 = 0; spectral
+convergence to harmonic closed forms; brute-force dense solves.
+"""
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from . import basis
+
+
+class Mesh:
+    """Structured sigma-domain mesh: [x0, x1] x [0, 1] split into cells_x x cells_z quads."""
+
+    def __init__(self, cells_x, cells_z, order, x0=0.0, x1=1.0, h=1.0, periodic=False):
+        if cells_x < 1 or cells_z < 1 or order < 1:
+            raise ValueError("bad mesh")
+        self.Nx, self.Nz, self.P = int(cells_x), int(cells_z), int(order)
+        self.x0, self.x1, self.h = float(x0), float(x1), float(h)
+        self.periodic = bool(periodic)
+        P = self.P
+        self.NX = self.Nx * P + (0 if self.periodic else 1)
+        self.NZ = self.Nz * P + 1
+        self.N = self.NX * self.NZ
+        self.dx = (self.x1 - self.x0) / self.Nx
+        self.dsig = 1.0 / self.Nz
+        self.r, self.w = basis.lgl_nodes_weights(P)
+        self.D = basis.diff_matrix(P)
+        n = P + 1
+        # element -> global node map, element e = ex * Nz + ez, local node a = i * n + j
+        ex = np.arange(self.Nx)[:, None, None, None]
+        ez = np.arange(self.Nz)[None, :, None, None]
+        i = np.arange(n)[None, None, :, None]
+        j = np.arange(n)[None, None, None, :]
+        ix = (ex * P + i) % self.NX if self.periodic else ex * P + i
+        iz = ez * P + j
+        self.e2g = (ix * self.NZ + iz).reshape(self.Nx * self.Nz, n * n)
+        self.ecol = np.repeat(np.arange(self.Nx), self.Nz)
+        self.erow = np.tile(np.arange(self.Nz), self.Nx)
+
+    # --- node coordinates -------------------------------------------------------
+    def column_x(self):
+        """x* of every node column ix."""
+        P = self.P
+        ix = np.arange(self.NX)
+        ex, i = ix // P, ix % P
+        return self.x0 + (ex + (self.r[i] + 1.0) / 2.0) * self.dx
+
+    def row_sigma(self):
+        """sigma of every node row iz (0 at the bottom, 1 at the free surface)."""
+        P = self.P
+        iz = np.arange(self.NZ)
+        ez, j = np.minimum(iz // P, self.Nz - 1), iz - np.minimum(iz // P, self.Nz - 1) * P
+        return (ez + (self.r[j] + 1.0) / 2.0) * self.dsig
+
+    def node_xz(self, eta):
+        """Physical (x, z) of every global node for surface elevation eta (per column)."""
+        x = self.column_x()
+        s = self.row_sigma()
+        d = np.asarray(eta, float) + self.h
+        X = np.repeat(x, self.NZ)
+        Z = (s[None, :] * d[:, None] - self.h).reshape(-1)
+        return X, Z
+
+    def dirichlet_mask(self):
+        m = np.zeros(self.N, bool)
+        m[np.arange(self.NX) * self.NZ + self.NZ - 1] = True
+        return m
+
+    # --- element geometry (isoparametric) ---------------------------------------
+    def element_coords(self, eta):
+        """Nodal (x, z) per element, shape (E, n, n): x* from the element's own cell,
+        z = sigma d(x) - h with d = eta + h sampled at the element's surface nodes."""
+        P, n = self.P, self.P + 1
+        eta = np.asarray(eta, float)
+        xe = self.x0 + (self.ecol[:, None] + (self.r[None, :] + 1.0) / 2.0) * self.dx  # (E, n)
+        sig = (self.erow[:, None] + (self.r[None, :] + 1.0) / 2.0) * self.dsig          # (E, n)
+        cols = self.ecol[:, None] * P + np.arange(n)[None, :]
+        if self.periodic:
+            cols = cols % self.NX
+        d = eta[cols] + self.h                                                            # (E, n)
+        X = np.repeat(xe[:, :, None], n, axis=2)
+        Z = sig[:, None, :] * d[:, :, None] - self.h
+        return X, Z
+
+    def element_metrics(self, eta):
+        """Per element-local node: (r_x, r_z, s_x, s_z, J) of the isoparametric map.
+
+        x_r = D x along r, x_s = x D^T along s (same for z); J = x_r z_s - x_s z_r;
+        r_x = z_s/J, r_z = -x_s/J, s_x = -z_r/J, s_z = x_r/J.
+        """
+        X, Z = self.element_coords(eta)
+        D = self.D
+        xr = np.einsum('im,emj->eij', D, X)
+        xs = np.einsum('jm,eim->eij', D, X)
+        zr = np.einsum('im,emj->eij', D, Z)
+        zs = np.einsum('jm,eim->eij', D, Z)
+        J = xr * zs - xs * zr
+        if np.any(J <= 0):
+            raise ValueError("non-positive Jacobian: eta <= -h somewhere")
+        return zs / J, -xs / J, -zr / J, xr / J, J
+
+    def ref_gradients(self):
+        """(Gr, Gs): derivatives of the element basis at the element nodes, (n^2, n^2).
+
+        Gr[(qa,qb),(i,j)] = D[qa,i] delta(qb,j);  Gs[(qa,qb),(i,j)] = delta(qa,i) D[qb,j].
+        """
+        n = self.P + 1
+        I = np.eye(n)
+        return np.kron(self.D, I), np.kron(I, self.D)
+
+    def quad_weights(self):
+        """Tensor LGL weights w_i w_j at local node (i, j), flattened."""
+        return np.outer(self.w, self.w).reshape(-1)
+
+    def element_stiffness(self, eta, elems=None):
+        """Dense K_e = Gx^T diag(w J) Gx + Gz^T diag(w J) Gz for the selected elements."""
+        rx, rz, sx, sz, J = self.element_metrics(eta)
+        if elems is not None:
+            rx, rz, sx, sz, J = rx[elems], rz[elems], sx[elems], sz[elems], J[elems]
+        E = rx.shape[0]
+        nn = (self.P + 1) ** 2
+        Gr, Gs = self.ref_gradients()
+        wJ = self.quad_weights()[None, :] * J.reshape(E, nn)
+        Gx = rx.reshape(E, nn, 1) * Gr[None] + sx.reshape(E, nn, 1) * Gs[None]
+        Gz = rz.reshape(E, nn, 1) * Gr[None] + sz.reshape(E, nn, 1) * Gs[None]
+        return (np.einsum('eqa,eq,eqb->eab', Gx, wJ, Gx)
+                + np.einsum('eqa,eq,eqb->eab', Gz, wJ, Gz))
+
+    def assemble(self, eta, chunk=2048):
+        """Global stiffness A = sum_e Q_e^T K_e Q_e (Sec. 4.2 global = sum of local), CSR."""
+        E = self.Nx * self.Nz
+        A = sp.csr_matrix((self.N, self.N))
+        for s in range(0, E, chunk):
+            el = np.arange(s, min(E, s + chunk))
+            K = self.element_stiffness(eta, el)
+            g = self.e2g[el]
+            rows = np.repeat(g[:, :, None], g.shape[1], axis=2).reshape(-1)
+            cols = np.repeat(g[:, None, :], g.shape[1], axis=1).reshape(-1)
+            A = A + sp.coo_matrix((K.reshape(-1), (rows, cols)), shape=(self.N, self.N)).tocsr()
+        A.sum_duplicates()
+        return A
+
+    # --- load vectors -------------------------------------------------------------
+    def scatter(self, local):
+        """sum_e Q_e^T local_e for local arrays of shape (E, n^2)."""
+        out = np.zeros(self.N)
+        np.add.at(out, self.e2g.reshape(-1), local.reshape(-1))
+        return out
+
+    def gather(self, glob):
+        return np.asarray(glob)[self.e2g]
+
+    def rhs_source(self, eta, f, g_bottom=None, g_left=None, g_right=None):
+        """l(N_i) = -sum_q w_q J_q N_i f_q + Neumann edge terms (LGL collocation).
+
+        g_bottom: d p/d n on the bottom (per node column, n outward);
+        g_left / g_right: on the walls x = x0 / x = x1 (per node row).  The edge
+        quadrature uses the physical arc length |d(x,z)/d xi| of the mapped edge.
+        Entries at Dirichlet nodes are set to zero.
+        """
+        rx, rz, sx, sz, J = self.element_metrics(eta)
+        E, n, P = J.shape[0], self.P + 1, self.P
+        wJ = self.quad_weights()[None, :] * J.reshape(E, n * n)
+        b = -self.scatter(wJ * self.gather(f))
+        X, Z = self.element_coords(eta)
+        D = self.D
+        if g_bottom is not None:
+            g_bottom = np.asarray(g_bottom, float)
+            for ex in range(self.Nx):
+                e = ex * self.Nz
+                xr = D @ X[e, :, 0]
+                zr = D @ Z[e, :, 0]
+                ds = np.sqrt(xr ** 2 + zr ** 2)
+                for i in range(n):
+                    ix = (ex * P + i) % self.NX
+                    b[ix * self.NZ] += self.w[i] * ds[i] * g_bottom[ix]
+        if not self.periodic:
+            for side, gw in ((0, g_left), (1, g_right)):
+                if gw is None:
+                    continue
+                gw = np.asarray(gw, float)
+                ex = 0 if side == 0 else self.Nx - 1
+                i = 0 if side == 0 else P
+                ix = ex * P + i
+                for ez in range(self.Nz):
+                    e = ex * self.Nz + ez
+                    xs = D @ X[e, i, :]
+                    zs = D @ Z[e, i, :]
+                    ds = np.sqrt(xs ** 2 + zs ** 2)
+                    for j in range(n):
+                        iz = ez * P + j
+                        b[ix * self.NZ + iz] += self.w[j] * ds[j] * gw[iz]
+        b[self.dirichlet_mask()] = 0.0
+        return b
+
+    def rhs_divergence(self, eta, u, w, scale=1.0):
+        """l(N_i) = scale * int grad N_i . (u, w) dOmega (weak divergence, LGL collocation).
+
+        For the projection reading of the pressure step this carries the Neumann data
+        n.u on walls and bottom implicitly.  Entries at Dirichlet nodes are zero.
+        """
+        rx, rz, sx, sz, J = self.element_metrics(eta)
+        E, nn = J.shape[0], (self.P + 1) ** 2
+        Gr, Gs = self.ref_gradients()
+        wJ = self.quad_weights()[None, :] * J.reshape(E, nn)
+        Gx = rx.reshape(E, nn, 1) * Gr[None] + sx.reshape(E, nn, 1) * Gs[None]
+        Gz = rz.reshape(E, nn, 1) * Gr[None] + sz.reshape(E, nn, 1) * Gs[None]
+        ue, we = self.gather(u), self.gather(w)
+        loc = (np.einsum('eqa,eq->ea', Gx, wJ * ue) + np.einsum('eqa,eq->ea', Gz, wJ * we))
+        b = scale * self.scatter(loc)
+        b[self.dirichlet_mask()] = 0.0
+        return b
+
+
+def lifted_system(A, b, p_dirichlet, dmask):
+    """(A_FF, b_F - A_FD p_D, free index): the Dirichlet-lifted free-node system."""
+    free = np.flatnonzero(~dmask)
+    dir_ = np.flatnonzero(dmask)
+    A = sp.csr_matrix(A)
+    AFF = A[free][:, free]
+    bt = np.asarray(b, float)[free] - A[free][:, dir_] @ np.asarray(p_dirichlet, float)[dir_]
+    return AFF, bt, free
+
+
+def apply_masked(A, x, dmask):
+    """y = A_FF x_F on free rows, y_D = x_D: the operator as the CUDA ABI exposes it."""
+    x = np.asarray(x, float)
+    xf = np.where(dmask, 0.0, x)
+    y = A @ xf
+    return np.where(dmask, x, y)
+
+
+def solve_direct(A, b, p_dirichlet, dmask):
+    """Exact solution by a sparse LU of A_FF (library primitive); full-length vector."""
+    AFF, bt, free = lifted_system(A, b, p_dirichlet, dmask)
+    p = np.array(p_dirichlet, float, copy=True)
+    p[free] = spla.splu(sp.csc_matrix(AFF)).solve(bt)
+    return p
+
+
+def solve_dense(A, b, p_dirichlet, dmask):
+    """Brute force: dense Cholesky of A_FF (small meshes only)."""
+    import scipy.linalg as sla
+    AFF, bt, free = lifted_system(A, b, p_dirichlet, dmask)
+    c = sla.cho_factor(AFF.toarray())
+    p = np.array(p_dirichlet, float, copy=True)
+    p[free] = sla.cho_solve(c, bt)
+    return p
+
+
+def relative_residual(A, b, p, dmask):
+    """||b~_F - A_FF p_F||_2 / ||b~_F||_2 with b~ = b - A_FD p_D."""
+    AFF, bt, free = lifted_system(A, b, p, dmask)
+    r = bt - AFF @ np.asarray(p, float)[free]
+    nb = np.linalg.norm(bt)
+    return np.linalg.norm(r) / (nb if nb > 0 else 1.0)

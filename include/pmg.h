@@ -1,0 +1,176 @@
+/*
+ * pmg.h -- C ABI of the GB300 (sm_103a) p-multigrid-preconditioned Krylov solver for the
+ * pressure-Poisson problem of the sigma-mapped nodal spectral element wave model of
+ * Melander, Laskowski, Sherwin & Engsig-Karup (arXiv 2411.14977).
+ *
+ * Problem (the same-geometry symmetric reading of the paper's Poisson BVP, Sec. 3.1-3.2):
+ *   find p in V_P (continuous, degree <= P per quad, Sec. 4) with p = p_D on the free
+ *   surface and a(N_i, p) = b_i for every free node i, where
+ *     a(v, p) = int_Omega grad v . grad p dOmega, pulled back to the sigma-domain
+ *               sigma = (z + h)/d, d = eta + h (Sec. 2.2, Eq. for sigma_x, sigma_z),
+ *   on a structured mesh of cells_x x cells_z quadrilaterals (Sec. 4.3) with
+ *   Legendre-Gauss-Lobatto nodes and LGL collocation quadrature.
+ *
+ * Node numbering (every vector in this ABI):  g = ix * NZ + iz,  z fastest.
+ *   NZ = cells_z * order + 1, iz = 0 at the bottom, iz = NZ - 1 on the free surface;
+ *   NX = cells_x * order + 1 (walls at x0, x1) or cells_x * order (periodic in x).
+ *   The free surface row is Dirichlet; walls and bottom are Neumann.
+ *
+ * Memory: every "_dev" pointer is a CUDA device pointer owned by the caller; every
+ *   "_host" pointer is host memory owned by the caller.  The handle owns its workspace
+ *   (allocated in pmg_create, freed in pmg_destroy).  Vectors are FP64 unless the name
+ *   says f32.  Calls are asynchronous on the given stream (a cudaStream_t passed as
+ *   void*, NULL = legacy default stream) unless stated otherwise.
+ * Errors: every call returns a pmg_status; no exception crosses the ABI; the message of
+ *   the last failure on the calling thread is returned by pmg_last_error().
+ * Threads: one handle must not be used by two threads at once.  Calls on one handle
+ *   that overlap on the GPU (different streams) race on its workspace.
+ */
+#ifndef PMG_H_
+#define PMG_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PMG_OK = 0,
+  PMG_ERR_INVALID = 1,        /* bad descriptor, option, pointer or size                  */
+  PMG_ERR_OOM = 2,            /* device or pinned-host allocation failed (nothing leaked)  */
+  PMG_ERR_CUDA = 3,           /* a CUDA runtime call failed                                */
+  PMG_ERR_NOT_CONVERGED = 4,  /* iteration cap reached; last iterate and info are filled   */
+  PMG_ERR_NONFINITE = 5,      /* NaN/Inf in the input or in the residual                   */
+  PMG_ERR_TIMEOUT = 6         /* a bounded device-side wait gave up                        */
+} pmg_status;
+
+/* precision of the V-cycle (preconditioner); the outer residual and result are FP64 */
+enum { PMG_FP64 = 0, PMG_MIXED_FP32 = 1, PMG_MIXED_BF16 = 2 };
+/* outer method: PCG (FP64 only), flexible CG, or preconditioned defect correction
+ * x <- x + B(b - Ax) (Sec. 5.4).  Mixed precisions always run FP64 iterative refinement
+ * around an inner FP32 flexible-CG solve. */
+enum { PMG_PCG = 0, PMG_FCG = 1, PMG_PDC = 2 };
+/* smoother: element-block additive Schwarz (Sec. 5.3), blocks inverted by fast
+ * diagonalisation (exact for the separable flat-geometry level operators) */
+enum { PMG_ASM_FDM = 0 };
+/* geometry the multigrid levels are built on: the flat, linearised (eta = 0) geometry
+ * that makes the preconditioner time-constant (Sec. 5.4) */
+enum { PMG_FLAT_LINEARISED = 1 };
+
+typedef struct {
+  double x0, x1;     /* horizontal extent of the tank                                     */
+  double h;          /* still-water depth (flat bottom z = -h)                            */
+  int cells_x;       /* quads in x (>= 1; >= 3 and a power of two when periodic_x)         */
+  int cells_z;       /* quads in sigma (>= 1)                                              */
+  int order;         /* polynomial order P, 1..10                                          */
+  int periodic_x;    /* 0: walls at x0, x1 (Neumann); 1: periodic in x                    */
+} pmg_mesh_desc;
+
+typedef struct {
+  int precision;     /* PMG_FP64 | PMG_MIXED_FP32 | PMG_MIXED_BF16                          */
+  int outer;         /* PMG_PCG | PMG_FCG | PMG_PDC                                         */
+  int smoother;      /* PMG_ASM_FDM                                                         */
+  int precond_geom;  /* PMG_FLAT_LINEARISED                                                 */
+  int overlap;       /* Schwarz overlap in node lines (0 or 1)                              */
+  int nu;            /* pre- and post-smoothing sweeps per level (>= 1)                     */
+  double omega;      /* smoother damping                                                    */
+  double tol;        /* stop when ||b~ - A p||_2 <= tol ||b~||_2 over free nodes            */
+  int max_iter;      /* outer iteration cap                                                 */
+  int inner_max;     /* mixed precision: inner FCG iteration cap per refinement step        */
+  double inner_tol;  /* mixed precision: inner relative residual target                     */
+  int nlevels;       /* 0 = the paper's coarsening rule; else level_orders[0..nlevels-1]    */
+  int level_orders[8];
+} pmg_opts;
+
+typedef struct {
+  int iterations;        /* outer iterations (PCG/FCG/PDC) or refinement steps (mixed)      */
+  int inner_iterations;  /* mixed precision: total inner FCG iterations                    */
+  double rel_residual;   /* final ||b~ - A p||_2 / ||b~||_2, FP64                          */
+  double seconds;        /* wall time of the call                                          */
+  int status;            /* pmg_status of the solve                                         */
+} pmg_solve_info;
+
+typedef struct pmg_handle pmg_handle;
+
+/* Fill *opts with the defaults: FP64, PCG, FDM-ASM, flat preconditioner, overlap 1, nu 2,
+ * omega 0.8, tol 1e-10, max_iter 500, inner_max 40, inner_tol 1e-5, paper level rule. */
+void pmg_default_opts(pmg_opts* opts);
+
+/* Build the mesh, the level hierarchy P_{n-1} = ceil((P_n+1)/2) down to 2, then 1
+ * (Sec. 5.1), the transfer matrices I = Phi V^-1 (Sec. 5.2), the Schwarz factors
+ * (Sec. 5.3) and the coarse factor, on the current CUDA device; geometry starts flat
+ * (eta = 0).  Synchronous.  *out is NULL on failure. */
+pmg_status pmg_create(const pmg_mesh_desc* mesh, const pmg_opts* opts, pmg_handle** out);
+pmg_status pmg_destroy(pmg_handle* h);
+
+/* Sizes: total nodes n = NX*NZ, free (non-Dirichlet) nodes, NX, NZ, number of levels. */
+pmg_status pmg_num_nodes(const pmg_handle* h, int64_t* n, int64_t* n_free, int* nx, int* nz,
+                         int* nlevels);
+/* Order and node counts of level l (0 = finest). */
+pmg_status pmg_level_info(const pmg_handle* h, int level, int* order, int* nx, int* nz);
+/* x* of every node column (NX values) and sigma of every node row (NZ values), host. */
+pmg_status pmg_node_coords(const pmg_handle* h, double* x_cols_host, double* sigma_rows_host);
+
+/* Per-stage geometry (Sec. 2.2): eta at every node column (NX values, device).  The
+ * surface is the degree-P interpolant of these values per cell; d = eta + h must stay
+ * positive.  The multigrid hierarchy is not rebuilt (flat preconditioner, Sec. 5.4). */
+pmg_status pmg_set_geometry(pmg_handle* h, const double* eta_dev, void* stream);
+
+/* b_i = -int N_i f dOmega + int_{Gamma_N} N_i g dGamma (LGL collocation), b = 0 on the
+ * free surface.  f: nodal values (n); g_bottom: outward normal derivative on the bottom
+ * per node column (NX); g_left / g_right: on the walls per node row (NZ).  Any g may be
+ * NULL (zero flux); the wall arrays are ignored when periodic. */
+pmg_status pmg_assemble_rhs(pmg_handle* h, const double* f_dev, const double* g_bottom_dev,
+                            const double* g_left_dev, const double* g_right_dev, double* b_dev,
+                            void* stream);
+/* b_i = scale * int grad N_i . (u, w) dOmega: the weak divergence of a nodal velocity
+ * field (projection form of the pressure step; carries n.u on walls and bottom). */
+pmg_status pmg_assemble_rhs_div(pmg_handle* h, const double* u_dev, const double* w_dev,
+                                double scale, double* b_dev, void* stream);
+
+/* Solve for the pressure: p_out = p_D on the free surface, A_FF p_F = b_F - A_FD p_D.
+ * b_dev: load vector (free entries used); p_dirichlet_dev: values read on the surface
+ * row only; x0_dev: initial guess or NULL (zero).  Returns PMG_ERR_NOT_CONVERGED with the
+ * last iterate in p_out when max_iter is hit.  info may be NULL.  Synchronises the stream
+ * (the convergence test reads device scalars). */
+pmg_status pmg_solve(pmg_handle* h, const double* b_dev, const double* p_dirichlet_dev,
+                     const double* x0_dev, double* p_out_dev, pmg_solve_info* info,
+                     void* stream);
+
+/* Same, with all five vectors in host memory (n doubles each, x0 may be NULL): copies
+ * in, solves, copies out, through pinned staging buffers owned by the handle. */
+pmg_status pmg_solve_host(pmg_handle* h, const double* b_host, const double* p_dirichlet_host,
+                          const double* x0_host, double* p_out_host, pmg_solve_info* info,
+                          void* stream);
+
+/* ---- component entry points (parity tests and benchmarks) ------------------------- */
+/* y = A_FF x on free nodes, y = x on the surface row; actual geometry, FP64 (Sec. 4.2). */
+pmg_status pmg_apply(pmg_handle* h, const double* x_dev, double* y_dev, void* stream);
+/* The same operator in FP32 storage and arithmetic. */
+pmg_status pmg_apply_f32(pmg_handle* h, const float* x_dev, float* y_dev, void* stream);
+/* Flat level-l operator (the multigrid level matrix), masked like pmg_apply.
+ * f32 = 0: FP64 vectors, 1: FP32 vectors. */
+pmg_status pmg_level_apply(pmg_handle* h, int level, const void* x_dev, void* y_dev, int f32,
+                           void* stream);
+/* nu Schwarz sweeps on level l for A_l x = b, updating x in place (Sec. 5.3);
+ * post = 0: x += omega W sum R^T A_i^-1 R r, post = 1: the adjoint (W applied to r). */
+pmg_status pmg_level_smooth(pmg_handle* h, int level, const void* b_dev, void* x_dev, int post,
+                            int f32, void* stream);
+/* r_c = P^T r_f (level l -> l+1) and x_f += P x_c (level l+1 -> l) (Sec. 5.2). */
+pmg_status pmg_restrict(pmg_handle* h, int level, const void* rf_dev, void* rc_dev, int f32,
+                        void* stream);
+pmg_status pmg_prolong(pmg_handle* h, int level, const void* xc_dev, void* xf_dev, int f32,
+                       void* stream);
+/* Exact FP64 solve of the coarsest (order 1) level system (free nodes; surface row 0). */
+pmg_status pmg_coarse_solve(pmg_handle* h, const double* b_dev, double* x_dev, void* stream);
+/* z = B r: one V-cycle of the preconditioner on the finest level (Sec. 5). */
+pmg_status pmg_vcycle(pmg_handle* h, const void* r_dev, void* z_dev, int f32, void* stream);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* pmg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PMG_H_ */

@@ -14,7 +14,10 @@ Paper passages followed (Sec. 5):
     S^{-1} = W sum_i R_i^T (R_i A R_i^T)^{-1} R_i,  W = (sum_i R_i R_i^T)^{-1},
     subdomain = element block plus `overlap` node lines of the neighbours   (Sec. 5.3)
     with damping omega; post-smoothing uses the adjoint S^{-T} (W on the right)
-    so that the V-cycle is a symmetric preconditioner for CG
+    so that the V-cycle is a symmetric preconditioner for CG.  The overlap is the
+    user's choice (the paper leaves it open); on a level of order p it is capped at
+    floor((p-1)/2) lines so that the overlap lines of two neighbouring subdomains
+    never meet (order 2 runs without overlap)
   * V-cycle                                                               (Sec. 5, Fig. V-cycle)
   * outer methods: PCG, flexible CG, and preconditioned defect correction
     x <- x + B (b - A x)                                                  (Sec. 5.4)
@@ -101,7 +104,7 @@ class Hierarchy:
                 eta_l = np.zeros(ml.NX)
             else:
                 eta_l = self._eta_at_level(mesh, eta, ml)
-            lev = Level(ml, ml.assemble(eta_l), overlap)
+            lev = Level(ml, ml.assemble(eta_l), min(overlap, (p - 1) // 2))
             if l < len(self.orders) - 1:
                 lev.build_schwarz()
             self.levels.append(lev)

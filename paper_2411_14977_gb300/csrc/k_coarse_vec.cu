@@ -1,0 +1,300 @@
+// Coarsest-level solve and Krylov vector kernels.
+//
+// Coarse level (order 1, flat geometry): A_1 = cx K_X (x) M_Z + cz M_X (x) K_Z on the free
+// nodes.  With the generalized eigenvectors of (K_Z, M_Z) on the free rows
+// (V^T M_Z V = I, V^T K_Z V = diag(mu)) the system splits into one tridiagonal system
+// (cx K_X + cz mu_k M_X) u_k = (V^T r)_k per vertical mode k, solved by parallel cyclic
+// reduction in shared memory with multipliers precomputed on the host; u = V u_hat.
+// All coarse arithmetic is FP64 whatever the precision of the V-cycle.
+//
+// Vector kernels: dot products and the CG/FCG updates, with FP64 accumulation and the
+// deterministic grid reduction of pmg_common.cuh.  Step scalars (alpha, beta, norms) live
+// in device memory; no host round trip is needed inside an iteration.
+#include "pmg_common.cuh"
+#include "pmg_kernels.h"
+
+namespace pmg {
+
+template <typename T>
+__global__ void k_coarse_fwd(int NX1, int NZ1, const T* b, const double* V, double* rhat) {
+  int Nz = NZ1 - 1;
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= NX1 * Nz) return;
+  int ix = t / Nz, k = t % Nz;
+  const T* col = b + (size_t)ix * NZ1;
+  double acc = 0.0;
+  for (int iz = 0; iz < Nz; ++iz) acc += V[iz * Nz + k] * (double)col[iz];
+  rhat[(size_t)k * NX1 + ix] = acc;
+}
+
+// PCR: d'_i = d_i - k1_i d_{i-s} - k2_i d_{i+s} per step; x_i = d_i * inv_i.
+__global__ void k_coarse_pcr(int n, int nsteps, int periodic, const double* coef, const double* inv,
+                             double* rhat) {
+  extern __shared__ double sbuf[];
+  double* d0 = sbuf;
+  double* d1 = sbuf + n;
+  int k = blockIdx.x;
+  const double* ck = coef + (size_t)k * nsteps * n * 2;
+  double* rk = rhat + (size_t)k * n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) d0[i] = rk[i];
+  __syncthreads();
+  int st = 1;
+  for (int step = 0; step < nsteps; ++step, st <<= 1) {
+    const double* c = ck + (size_t)step * n * 2;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      int im = i - st, ip = i + st;
+      double v = d0[i];
+      if (periodic) {
+        im = ((im % n) + n) % n;
+        ip = ip % n;
+        v -= c[2 * i] * d0[im] + c[2 * i + 1] * d0[ip];
+      } else {
+        if (im >= 0) v -= c[2 * i] * d0[im];
+        if (ip < n) v -= c[2 * i + 1] * d0[ip];
+      }
+      d1[i] = v;
+    }
+    __syncthreads();
+    double* tmp = d0; d0 = d1; d1 = tmp;
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) rk[i] = d0[i] * inv[(size_t)k * n + i];
+}
+
+template <typename T>
+__global__ void k_coarse_bwd(int NX1, int NZ1, const double* V, const double* uhat, T* x) {
+  int Nz = NZ1 - 1;
+  size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= (size_t)NX1 * NZ1) return;
+  int ix = (int)(t / NZ1), iz = (int)(t % NZ1);
+  double acc = 0.0;
+  if (iz < Nz)
+    for (int k = 0; k < Nz; ++k) acc += V[iz * Nz + k] * uhat[(size_t)k * NX1 + ix];
+  x[t] = (T)acc;
+}
+
+template <typename T>
+cudaError_t coarse_solve(const CoarseArgs& a, const void* b, void* x, cudaStream_t st) {
+  int Nz = a.NZ1 - 1;
+  int tot = a.NX1 * Nz, bs = 256;
+  k_coarse_fwd<T><<<(tot + bs - 1) / bs, bs, 0, st>>>(a.NX1, a.NZ1, (const T*)b, a.V, a.work);
+  int thr = a.NX1 < 1024 ? ((a.NX1 + 31) / 32) * 32 : 1024;
+  size_t sm = 2 * (size_t)a.NX1 * sizeof(double);
+  k_coarse_pcr<<<Nz, thr, sm, st>>>(a.NX1, a.nsteps, a.periodic, a.coef, a.inv, a.work);
+  size_t N = (size_t)a.NX1 * a.NZ1;
+  k_coarse_bwd<T><<<(unsigned)((N + bs - 1) / bs), bs, 0, st>>>(a.NX1, a.NZ1, a.V, a.work, (T*)x);
+  return cudaGetLastError();
+}
+template cudaError_t coarse_solve<double>(const CoarseArgs&, const void*, void*, cudaStream_t);
+template cudaError_t coarse_solve<float>(const CoarseArgs&, const void*, void*, cudaStream_t);
+
+// ------------------------------------------------------------------------------------
+// vector kernels
+// ------------------------------------------------------------------------------------
+constexpr int VEC_BLOCKS = 304;  // 2 x 152 SMs
+constexpr int VEC_THREADS = 512;
+
+// out[0] = <x, y> (FP64 accumulation); shift: out[1] = old out[0] first.
+template <typename TA, typename TB>
+__global__ void __launch_bounds__(VEC_THREADS) k_dot(size_t n, const TA* x, const TB* y, double* out,
+                                                     int shift, Scratch sc) {
+  __shared__ double red[34];
+  __shared__ int s_flag;
+  double acc = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    acc += (double)x[i] * (double)y[i];
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) sc.partials[blockIdx.x] = acc;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_flag = (atomicAdd(sc.redcnt, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!s_flag) return;
+  __threadfence();
+  double v = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) v += ((volatile double*)sc.partials)[i];
+  v = block_sum(v, red);
+  if (threadIdx.x == 0) {
+    if (shift) out[1] = out[0];
+    out[0] = v;
+    *sc.redcnt = 0u;
+  }
+}
+
+// Scalars layout (double): see Slot in pmg_kernels.h.
+// x += alpha p, r -= alpha w, (r_old = r), RR = ||r||^2;  alpha = RZ / PAP.
+template <typename T>
+__global__ void __launch_bounds__(VEC_THREADS) k_cg_update(size_t n, T* x, T* r, const T* p, const T* w,
+                                                           T* r_old, double* s, Scratch sc) {
+  __shared__ double red[34];
+  __shared__ int s_flag;
+  double alpha = s[SLOT_RZ] / s[SLOT_PAP];
+  T a = (T)alpha;
+  double acc = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    T ri = r[i];
+    if (r_old) r_old[i] = ri;
+    x[i] += a * p[i];
+    ri -= a * w[i];
+    r[i] = ri;
+    acc += (double)ri * (double)ri;
+  }
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) sc.partials[blockIdx.x] = acc;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_flag = (atomicAdd(sc.redcnt, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!s_flag) return;
+  __threadfence();
+  double v = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) v += ((volatile double*)sc.partials)[i];
+  v = block_sum(v, red);
+  if (threadIdx.x == 0) {
+    s[SLOT_RR] = v;
+    *sc.redcnt = 0u;
+  }
+}
+
+// RZ_new = <r, z> (and for flexible CG ZRO = <z, r_old>), shifting RZ -> RZOLD.
+template <typename T>
+__global__ void __launch_bounds__(VEC_THREADS) k_rz(size_t n, const T* r, const T* z, const T* r_old,
+                                                    double* s, Scratch sc) {
+  __shared__ double red[34];
+  __shared__ int s_flag;
+  double a1 = 0.0, a2 = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    double zi = (double)z[i];
+    a1 += (double)r[i] * zi;
+    if (r_old) a2 += (double)r_old[i] * zi;
+  }
+  a1 = block_sum(a1, red);
+  a2 = block_sum(a2, red);
+  if (threadIdx.x == 0) { sc.partials[2 * blockIdx.x] = a1; sc.partials[2 * blockIdx.x + 1] = a2; }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_flag = (atomicAdd(sc.redcnt, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!s_flag) return;
+  __threadfence();
+  double v1 = 0.0, v2 = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+    v1 += ((volatile double*)sc.partials)[2 * i];
+    v2 += ((volatile double*)sc.partials)[2 * i + 1];
+  }
+  v1 = block_sum(v1, red);
+  v2 = block_sum(v2, red);
+  if (threadIdx.x == 0) {
+    s[SLOT_RZOLD] = s[SLOT_RZ];
+    s[SLOT_RZ] = v1;
+    s[SLOT_ZRO] = v2;
+    *sc.redcnt = 0u;
+  }
+}
+
+// p = z + beta p with beta = RZ/RZOLD (CG) or (RZ - ZRO)/RZOLD (flexible CG); first: p = z.
+template <typename T>
+__global__ void k_p_update(size_t n, T* p, const T* z, const double* s, int flexible, int first) {
+  double beta = 0.0;
+  if (!first) beta = (flexible ? (s[SLOT_RZ] - s[SLOT_ZRO]) : s[SLOT_RZ]) / s[SLOT_RZOLD];
+  T b = (T)beta;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    p[i] = first ? z[i] : z[i] + b * p[i];
+}
+
+// y = (float)(x * (1/sqrt(s[slot])))  (unit-norm scaling of a residual for the FP32 solve)
+__global__ void k_to_f32_scaled(size_t n, const double* x, float* y, const double* s, int slot) {
+  double nr = sqrt(s[slot]);
+  double inv = nr > 0.0 ? 1.0 / nr : 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = (float)(x[i] * inv);
+}
+// x += sqrt(s[slot]) * (double)c
+__global__ void k_add_f32_scaled(size_t n, double* x, const float* c, const double* s, int slot) {
+  double nr = sqrt(s[slot]);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    x[i] += nr * (double)c[i];
+}
+// x += y (same type)
+template <typename T>
+__global__ void k_add(size_t n, T* x, const T* y) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    x[i] += y[i];
+}
+// x = x0 (or 0) on free nodes, p_D on the surface row; out-of-range values flagged.
+__global__ void k_init_x(size_t n, int NZ, double* x, const double* x0, const double* pD, int* status) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    bool top = (int)(i % NZ) == NZ - 1;
+    double v = top ? pD[i] : (x0 ? x0[i] : 0.0);
+    if (!isfinite(v)) atomicExch(status, 1);
+    x[i] = v;
+  }
+}
+__global__ void k_check_finite(size_t n, const double* v, int* status) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    if (!isfinite(v[i])) atomicExch(status, 1);
+}
+
+static unsigned vec_grid(size_t n) {
+  size_t b = (n + VEC_THREADS - 1) / VEC_THREADS;
+  return (unsigned)(b < (size_t)VEC_BLOCKS ? (b > 0 ? b : 1) : VEC_BLOCKS);
+}
+
+template <typename TA, typename TB>
+cudaError_t dot(size_t n, const TA* x, const TB* y, double* out, int shift, const Scratch& sc, cudaStream_t st) {
+  k_dot<TA, TB><<<vec_grid(n), VEC_THREADS, 0, st>>>(n, x, y, out, shift, sc);
+  return cudaGetLastError();
+}
+template cudaError_t dot<double, double>(size_t, const double*, const double*, double*, int, const Scratch&, cudaStream_t);
+template cudaError_t dot<float, float>(size_t, const float*, const float*, double*, int, const Scratch&, cudaStream_t);
+
+template <typename T>
+cudaError_t cg_update(size_t n, T* x, T* r, const T* p, const T* w, T* r_old, double* s, const Scratch& sc,
+                      cudaStream_t st) {
+  k_cg_update<T><<<vec_grid(n), VEC_THREADS, 0, st>>>(n, x, r, p, w, r_old, s, sc);
+  return cudaGetLastError();
+}
+template cudaError_t cg_update<double>(size_t, double*, double*, const double*, const double*, double*, double*, const Scratch&, cudaStream_t);
+template cudaError_t cg_update<float>(size_t, float*, float*, const float*, const float*, float*, double*, const Scratch&, cudaStream_t);
+
+template <typename T>
+cudaError_t rz(size_t n, const T* r, const T* z, const T* r_old, double* s, const Scratch& sc, cudaStream_t st) {
+  k_rz<T><<<vec_grid(n), VEC_THREADS, 0, st>>>(n, r, z, r_old, s, sc);
+  return cudaGetLastError();
+}
+template cudaError_t rz<double>(size_t, const double*, const double*, const double*, double*, const Scratch&, cudaStream_t);
+template cudaError_t rz<float>(size_t, const float*, const float*, const float*, double*, const Scratch&, cudaStream_t);
+
+template <typename T>
+cudaError_t p_update(size_t n, T* p, const T* z, const double* s, int flexible, int first, cudaStream_t st) {
+  k_p_update<T><<<vec_grid(n), VEC_THREADS, 0, st>>>(n, p, z, s, flexible, first);
+  return cudaGetLastError();
+}
+template cudaError_t p_update<double>(size_t, double*, const double*, const double*, int, int, cudaStream_t);
+template cudaError_t p_update<float>(size_t, float*, const float*, const double*, int, int, cudaStream_t);
+
+cudaError_t to_f32_scaled(size_t n, const double* x, float* y, const double* s, int slot, cudaStream_t st) {
+  k_to_f32_scaled<<<vec_grid(n), VEC_THREADS, 0, st>>>(n, x, y, s, slot);
+  return cudaGetLastError();
+}
+cudaError_t add_f32_scaled(size_t n, double* x, const float* c, const double* s, int slot, cudaStream_t st) {
+  k_add_f32_scaled<<<vec_grid(n), VEC_THREADS, 0, st>>>(n, x, c, s, slot);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t add(size_t n, T* x, const T* y, cudaStream_t st) {
+  k_add<T><<<vec_grid(n), VEC_THREADS, 0, st>>>(n, x, y);
+  return cudaGetLastError();
+}
+template cudaError_t add<double>(size_t, double*, const double*, cudaStream_t);
+template cudaError_t add<float>(size_t, float*, const float*, cudaStream_t);
+
+cudaError_t init_x(size_t n, int NZ, double* x, const double* x0, const double* pD, int* status, cudaStream_t st) {
+  k_init_x<<<vec_grid(n), VEC_THREADS, 0, st>>>(n, NZ, x, x0, pD, status);
+  return cudaGetLastError();
+}
+cudaError_t check_finite(size_t n, const double* v, int* status, cudaStream_t st) {
+  k_check_finite<<<vec_grid(n), VEC_THREADS, 0, st>>>(n, v, status);
+  return cudaGetLastError();
+}
+
+}  // namespace pmg

@@ -1,0 +1,495 @@
+// Multigrid level kernels on the flat, linearised geometry (Sec. 5, Sec. 5.4):
+//
+//  * level operator: on eta = 0 every element has the same metric, and the assembled
+//    level matrix is the Kronecker sum  A = cx K_X (x) M_Z + cz M_X (x) K_Z  of 1D LGL
+//    stiffness K = assembled D^T diag(w) D and 1D LGL weights M (cx = h dsig/dx,
+//    cz = dx/(h dsig)).  Each output node sums 1D element stencils along its row and
+//    its column; the CTA of an element column also evaluates the left element's share of
+//    its first column, so no exchange is needed.
+//  * additive Schwarz smoother (Sec. 5.3): subdomain = element block plus `overlap` node
+//    lines, block = submatrix of the assembled level matrix, which is again a Kronecker
+//    sum; its inverse is applied exactly by fast diagonalisation with the per-class
+//    generalized eigenvectors (V^T M V = I):  A_i^-1 = (Vx (x) Vz) diag(1/(cx lx + cz lz)) (Vx (x) Vz)^T.
+//  * transfers (Sec. 5.2): prolongation = coarse polynomial evaluated at the fine nodes,
+//    J (x) J per element; restriction = its transpose, summed over distinct fine nodes.
+#include "pmg_common.cuh"
+#include "pmg_kernels.h"
+
+PMG_DEFINE_CONST_TABLES(init_consts_levels)
+
+namespace pmg {
+
+// ------------------------------------------------------------------------------------
+// level operator / residual
+// ------------------------------------------------------------------------------------
+template <typename T>
+struct FlatParams {
+  Shape s;
+  const T* x;
+  const T* b;
+  T* y;
+  T cx, cz;
+  const T* mX;  // [NX] assembled weights along x
+  const T* mZ;  // [NZ]
+  int residual; // 0: y = A x (surface row y = x); 1: y = b - A x (surface row 0)
+};
+
+template <int P, typename T>
+__global__ void __launch_bounds__(256) k_flat(FlatParams<T> p) {
+  constexpr int n = P + 1;
+  const Shape s = p.s;
+  const int NZ = s.NZ, Nz = s.Nz, NZp = slab_pitch(NZ);
+  const int ex = blockIdx.x, col0 = ex * P;
+  const bool left = s.periodic || ex > 0;
+  const bool last = !s.periodic && ex == s.Nx - 1;
+  const int own = last ? n : P;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* X = reinterpret_cast<T*>(smem_raw);  // [2P+1][NZp], local column c <-> col0 - P + c
+  T* Y = X + (2 * P + 1) * NZp;            // [n][NZp]
+  for (int t = threadIdx.x; t < (2 * P + 1) * NZ; t += blockDim.x) {
+    int c = t / NZ, iz = t - c * NZ;
+    int gc = col0 - P + c;
+    T v = T(0);
+    if ((c >= P || left) && iz != NZ - 1) v = p.x[(size_t)wrap_col(s, gc) * NZ + iz];
+    X[c * NZp + iz] = v;
+  }
+  __syncthreads();
+  // x-direction stencils, one node row per thread
+  for (int iz = threadIdx.x; iz < NZ; iz += blockDim.x) {
+    T xo[n], xl[n];
+#pragma unroll
+    for (int m = 0; m < n; ++m) { xo[m] = X[(P + m) * NZp + iz]; xl[m] = X[m * NZp + iz]; }
+    T f = p.cx * p.mZ[iz];
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+      if (i == P && !last) break;
+      T acc = T(0);
+#pragma unroll
+      for (int m = 0; m < n; ++m) acc += CT<T>::K(cT, P, i, m) * xo[m];
+      if (i == 0 && left) {  // the left element's share of the shared first column
+#pragma unroll
+        for (int m = 0; m < n; ++m) acc += CT<T>::K(cT, P, P, m) * xl[m];
+      }
+      Y[i * NZp + iz] = f * acc;
+    }
+  }
+  __syncthreads();
+  // z-direction stencils, one (column, element row) per thread, owning rows [ez P, ez P + P)
+  for (int t = threadIdx.x; t < own * Nz; t += blockDim.x) {
+    int i = t % own, ez = t / own;
+    const T* col = X + (P + i) * NZp;
+    T xv[n];
+#pragma unroll
+    for (int m = 0; m < n; ++m) xv[m] = col[ez * P + m];
+    T below = T(0);
+    if (ez > 0) {
+#pragma unroll
+      for (int m = 0; m < n; ++m) below += CT<T>::K(cT, P, P, m) * col[(ez - 1) * P + m];
+    }
+    T f = p.cz * p.mX[wrap_col(s, col0 + i)];
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+      T acc = (j == 0) ? below : T(0);
+#pragma unroll
+      for (int m = 0; m < n; ++m) acc += CT<T>::K(cT, P, j, m) * xv[m];
+      Y[i * NZp + ez * P + j] += f * acc;
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < own * NZ; t += blockDim.x) {
+    int i = t / NZ, iz = t - i * NZ;
+    size_t g = (size_t)(col0 + i) * NZ + iz;
+    bool top = iz == NZ - 1;
+    T v = Y[i * NZp + iz];
+    if (p.residual) p.y[g] = top ? T(0) : p.b[g] - v;
+    else p.y[g] = top ? p.x[g] : v;
+  }
+}
+
+template <int P, typename T>
+static cudaError_t launch_flat_p(const FlatParams<T>& prm, cudaStream_t st) {
+  int NZp = slab_pitch(prm.s.NZ);
+  size_t sm = (size_t)((2 * P + 1) + (P + 1)) * NZp * sizeof(T);
+  auto k = k_flat<P, T>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k<<<prm.s.Nx, 256, sm, st>>>(prm);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t flat_op(const FlatArgs& a, cudaStream_t st) {
+  FlatParams<T> p;
+  p.s = a.s;
+  p.x = (const T*)a.x;
+  p.b = (const T*)a.b;
+  p.y = (T*)a.y;
+  p.cx = (T)a.cx;
+  p.cz = (T)a.cz;
+  p.mX = (const T*)a.mX;
+  p.mZ = (const T*)a.mZ;
+  p.residual = a.residual;
+  switch (a.s.P) {
+#define PMG_CASE(PP) case PP: return launch_flat_p<PP, T>(p, st);
+    PMG_CASE(1) PMG_CASE(2) PMG_CASE(3) PMG_CASE(4) PMG_CASE(5)
+    PMG_CASE(6) PMG_CASE(7) PMG_CASE(8) PMG_CASE(9) PMG_CASE(10)
+#undef PMG_CASE
+  }
+  return cudaErrorInvalidValue;
+}
+template cudaError_t flat_op<double>(const FlatArgs&, cudaStream_t);
+template cudaError_t flat_op<float>(const FlatArgs&, cudaStream_t);
+
+// ------------------------------------------------------------------------------------
+// Schwarz smoother by fast diagonalisation
+// ------------------------------------------------------------------------------------
+template <typename T>
+struct FdmParams {
+  Shape s;
+  const T* r;       // residual b - A x
+  T* x;             // updated in place
+  int post;         // 0: x += omega W sum R^T A^-1 R r;  1: x += omega sum R^T A^-1 R W r
+  T omega;
+  const T* Vx;      // [4][NB][NB]  (a, alpha): class x-eigenvectors in the padded local frame
+  const T* Vz;      // [4][NB][NB]  (b, beta)
+  const T* invden;  // [4][4][NB][NB] (xcls, zcls, alpha, beta): 1/(cx lx + cz lz), 0 if padded
+  const T* wx;      // [NX] inverse 1D cover counts
+  const T* wz;      // [NZ]
+  Scratch sc;
+};
+
+__device__ __forceinline__ int xclass(const Shape& s, int ex) {
+  if (s.periodic) return 0;
+  return (ex == 0 ? 1 : 0) | (ex == s.Nx - 1 ? 2 : 0);
+}
+__device__ __forceinline__ int zclass(const Shape& s, int ez) {
+  return (ez == 0 ? 1 : 0) | (ez == s.Nz - 1 ? 2 : 0);
+}
+
+template <int P, int O, typename T>
+__global__ void __launch_bounds__(256) k_fdm(FdmParams<T> p) {
+  constexpr int NB = P + 1 + 2 * O;
+  const Shape s = p.s;
+  const int NZ = s.NZ, Nz = s.Nz, NZp = slab_pitch(NZ);
+  const int ex = blockIdx.x, col0 = ex * P;
+  const int xc = xclass(s, ex);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* R = reinterpret_cast<T*>(smem_raw);  // [NB][NZp]  input, later U
+  T* T1 = R + NB * NZp;                    // [NB][NZp]  x-transformed rows
+  T* T3 = T1 + NB * NZp;                   // [Nz][NB][NB] (ez, b, alpha)
+  T* VX = T3 + Nz * NB * NB;               // [NB][NB]
+  T* VZ = VX + NB * NB;                     // [4][NB][NB]
+  T* ID = VZ + 4 * NB * NB;                // [4][NB][NB]
+  size_t red_off = (((size_t)(2 * NB * NZp + Nz * NB * NB + 9 * NB * NB) * sizeof(T)) + 15) & ~(size_t)15;
+  int* s_flag = reinterpret_cast<int*>(smem_raw + red_off);
+
+  for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) VX[t] = p.Vx[xc * NB * NB + t];
+  for (int t = threadIdx.x; t < 4 * NB * NB; t += blockDim.x) {
+    VZ[t] = p.Vz[t];
+    ID[t] = p.invden[xc * 4 * NB * NB + t];
+  }
+  for (int t = threadIdx.x; t < NB * NZ; t += blockDim.x) {
+    int a = t / NZ, iz = t - a * NZ;
+    int gc = col0 - O + a;
+    T v = T(0);
+    if (col_valid(s, gc) && iz != NZ - 1) {
+      int c = wrap_col(s, gc);
+      v = p.r[(size_t)c * NZ + iz];
+      if (p.post) v *= p.wx[c] * p.wz[iz];
+    }
+    R[a * NZp + iz] = v;
+  }
+  __syncthreads();
+  // phase 1: T1[alpha][iz] = sum_a Vx[a][alpha] R[a][iz]
+  for (int iz = threadIdx.x; iz < NZ; iz += blockDim.x) {
+    T rv[NB];
+#pragma unroll
+    for (int a = 0; a < NB; ++a) rv[a] = R[a * NZp + iz];
+#pragma unroll
+    for (int al = 0; al < NB; ++al) {
+      T acc = T(0);
+#pragma unroll
+      for (int a = 0; a < NB; ++a) acc += VX[a * NB + al] * rv[a];
+      T1[al * NZp + iz] = acc;
+    }
+  }
+  __syncthreads();
+  // phase 2: per (alpha, ez): sigma transform, diagonal solve, inverse sigma transform
+  for (int t = threadIdx.x; t < NB * Nz; t += blockDim.x) {
+    int al = t % NB, ez = t / NB;
+    int zc = zclass(s, ez);
+    const T* vz = VZ + zc * NB * NB;
+    const T* idn = ID + (zc * NB + al) * NB;
+    T tz[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      int iz = ez * P - O + b;
+      tz[b] = (iz >= 0 && iz < NZ - 1) ? T1[al * NZp + iz] : T(0);
+    }
+    T t2[NB];
+#pragma unroll
+    for (int be = 0; be < NB; ++be) {
+      T acc = T(0);
+#pragma unroll
+      for (int b = 0; b < NB; ++b) acc += vz[b * NB + be] * tz[b];
+      t2[be] = acc * idn[be];
+    }
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      T acc = T(0);
+#pragma unroll
+      for (int be = 0; be < NB; ++be) acc += vz[b * NB + be] * t2[be];
+      T3[(ez * NB + b) * NB + al] = acc;
+    }
+  }
+  __syncthreads();
+  // phase 3: per row, sum the covering elements, inverse x transform -> U[a][iz] (in R)
+  T* U = R;
+  for (int iz = threadIdx.x; iz < NZ; iz += blockDim.x) {
+    T sv[NB];
+#pragma unroll
+    for (int al = 0; al < NB; ++al) sv[al] = T(0);
+    int e0 = (iz + O) / P;
+#pragma unroll
+    for (int d = -2; d <= 0; ++d) {
+      int ez = e0 + d;
+      if (ez < 0 || ez >= Nz) continue;
+      int b = iz - ez * P + O;
+      if (b < 0 || b >= NB) continue;
+#pragma unroll
+      for (int al = 0; al < NB; ++al) sv[al] += T3[(ez * NB + b) * NB + al];
+    }
+#pragma unroll
+    for (int a = 0; a < NB; ++a) {
+      T acc = T(0);
+#pragma unroll
+      for (int al = 0; al < NB; ++al) acc += VX[a * NB + al] * sv[al];
+      U[a * NZp + iz] = acc;
+    }
+  }
+  __syncthreads();
+  // phase 4: x update; owned interior columns directly, the two zones by exchange
+  auto upd = [&](int gc, int iz, T u) {
+    if (iz == NZ - 1) return;
+    int c = wrap_col(s, gc);
+    size_t g = (size_t)c * NZ + iz;
+    T w = p.post ? T(1) : p.wx[c] * p.wz[iz];
+    p.x[g] += p.omega * w * u;
+  };
+  for (int t = threadIdx.x; t < (P - 1 - 2 * O) * NZ; t += blockDim.x) {
+    int a = 2 * O + 1 + t / NZ, iz = t % NZ;
+    upd(col0 - O + a, iz, U[a * NZp + iz]);
+  }
+  constexpr int ZW = 2 * O + 1;
+  T* eb = reinterpret_cast<T*>(p.sc.edgebuf);
+#pragma unroll 1
+  for (int side = 0; side < 2; ++side) {
+    int a0 = side == 0 ? 0 : P;
+    int e = side == 0 ? ex : (s.periodic ? (ex + 1) % s.Nx : ex + 1);
+    bool single = !s.periodic && (e == 0 || e == s.Nx);
+    int gbase = e * P - O;
+    if (single) {
+      for (int t = threadIdx.x; t < ZW * NZ; t += blockDim.x) {
+        int c = t / NZ, iz = t % NZ;
+        if (col_valid(s, gbase + c)) upd(gbase + c, iz, U[(a0 + c) * NZp + iz]);
+      }
+    } else {
+      T* buf = eb + (size_t)e * ZW * NZ;
+      for (int t = threadIdx.x; t < ZW * NZ; t += blockDim.x) {
+        int c = t / NZ, iz = t % NZ;
+        atomic_add_t(buf + t, U[(a0 + c) * NZp + iz]);
+      }
+      if (!edge_arrive(p.sc.edgecnt + e, 2, s_flag)) continue;
+      for (int t = threadIdx.x; t < ZW * NZ; t += blockDim.x) {
+        int c = t / NZ, iz = t % NZ;
+        upd(gbase + c, iz, take_t(buf + t));
+      }
+    }
+  }
+}
+
+template <int P, int O, typename T>
+static cudaError_t launch_fdm_p(const FdmParams<T>& prm, cudaStream_t st) {
+  constexpr int NB = P + 1 + 2 * O;
+  int NZp = slab_pitch(prm.s.NZ);
+  size_t elems = (size_t)2 * NB * NZp + (size_t)prm.s.Nz * NB * NB + 9 * NB * NB;
+  size_t sm = ((elems * sizeof(T) + 15) & ~(size_t)15) + 16;
+  auto k = k_fdm<P, O, T>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k<<<prm.s.Nx, 256, sm, st>>>(prm);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t fdm_smooth(const FdmArgs& a, cudaStream_t st) {
+  FdmParams<T> p;
+  p.s = a.s;
+  p.r = (const T*)a.r;
+  p.x = (T*)a.x;
+  p.post = a.post;
+  p.omega = (T)a.omega;
+  p.Vx = (const T*)a.Vx;
+  p.Vz = (const T*)a.Vz;
+  p.invden = (const T*)a.invden;
+  p.wx = (const T*)a.wx;
+  p.wz = (const T*)a.wz;
+  p.sc = a.sc;
+  if (a.overlap == 0) {
+    switch (a.s.P) {
+#define PMG_CASE(PP) case PP: return launch_fdm_p<PP, 0, T>(p, st);
+      PMG_CASE(2) PMG_CASE(3) PMG_CASE(4) PMG_CASE(5)
+      PMG_CASE(6) PMG_CASE(7) PMG_CASE(8) PMG_CASE(9) PMG_CASE(10)
+#undef PMG_CASE
+    }
+  } else if (a.overlap == 1) {
+    switch (a.s.P) {
+#define PMG_CASE(PP) case PP: return launch_fdm_p<PP, 1, T>(p, st);
+      PMG_CASE(3) PMG_CASE(4) PMG_CASE(5)
+      PMG_CASE(6) PMG_CASE(7) PMG_CASE(8) PMG_CASE(9) PMG_CASE(10)
+#undef PMG_CASE
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+template cudaError_t fdm_smooth<double>(const FdmArgs&, cudaStream_t);
+template cudaError_t fdm_smooth<float>(const FdmArgs&, cudaStream_t);
+
+// ------------------------------------------------------------------------------------
+// transfers
+// ------------------------------------------------------------------------------------
+template <typename T>
+struct TransferParams {
+  Shape f, c;       // fine and coarse shapes (same cells)
+  const T* in;
+  T* out;
+  const double* J;  // [(Pf+1)][(Pc+1)]
+};
+
+// x_f += P x_c
+template <typename T>
+__global__ void __launch_bounds__(256) k_prolong(TransferParams<T> p) {
+  const Shape f = p.f, c = p.c;
+  const int Pf = f.P, Pc = c.P, nf = Pf + 1, nc = Pc + 1;
+  const int NZf = f.NZ, NZc = c.NZ, NZcp = slab_pitch(NZc), NZfp = slab_pitch(NZf);
+  const int ex = blockIdx.x;
+  const bool last = !f.periodic && ex == f.Nx - 1;
+  const int own = last ? nf : Pf;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Xc = reinterpret_cast<T*>(smem_raw);  // [nc][NZcp]
+  T* Tz = Xc + nc * NZcp;                   // [nc][NZfp]
+  T* Js = Tz + nc * NZfp;                   // [nf][nc]
+  for (int t = threadIdx.x; t < nf * nc; t += blockDim.x) Js[t] = (T)p.J[t];
+  for (int t = threadIdx.x; t < nc * NZc; t += blockDim.x) {
+    int k = t / NZc, iz = t - k * NZc;
+    Xc[k * NZcp + iz] = p.in[(size_t)wrap_col(c, ex * Pc + k) * NZc + iz];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nc * NZf; t += blockDim.x) {
+    int k = t / NZf, iz = t - k * NZf;
+    int ez = min(iz / Pf, f.Nz - 1), j = iz - ez * Pf;
+    T acc = T(0);
+    for (int l = 0; l < nc; ++l) acc += Js[j * nc + l] * Xc[k * NZcp + ez * Pc + l];
+    Tz[k * NZfp + iz] = acc;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < own * NZf; t += blockDim.x) {
+    int i = t / NZf, iz = t - i * NZf;
+    if (iz == NZf - 1) continue;
+    T acc = T(0);
+    for (int k = 0; k < nc; ++k) acc += Js[i * nc + k] * Tz[k * NZfp + iz];
+    p.out[(size_t)(ex * Pf + i) * NZf + iz] += acc;
+  }
+}
+
+// r_c = P^T r_f
+template <typename T>
+__global__ void __launch_bounds__(256) k_restrict(TransferParams<T> p) {
+  const Shape f = p.f, c = p.c;
+  const int Pf = f.P, Pc = c.P, nf = Pf + 1, nc = Pc + 1;
+  const int NZf = f.NZ, NZc = c.NZ, NZfp = slab_pitch(NZf), NZcp = slab_pitch(NZc);
+  const int ex = blockIdx.x;
+  const bool left = f.periodic || ex > 0;
+  const bool last = !f.periodic && ex == f.Nx - 1;
+  const int own = last ? nc : Pc;
+  const int ncol = 2 * Pf + 1;  // local fine column q <-> (ex-1) Pf + q
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Rf = reinterpret_cast<T*>(smem_raw);  // [ncol][NZfp]
+  T* Sz = Rf + ncol * NZfp;                 // [ncol][NZcp]
+  T* Js = Sz + ncol * NZcp;                 // [nf][nc]
+  for (int t = threadIdx.x; t < nf * nc; t += blockDim.x) Js[t] = (T)p.J[t];
+  for (int t = threadIdx.x; t < ncol * NZf; t += blockDim.x) {
+    int q = t / NZf, iz = t - q * NZf;
+    int gc = (ex - 1) * Pf + q;
+    T v = T(0);
+    bool ok = (q >= Pf || left) && (q < 2 * Pf || last) && iz != NZf - 1;
+    if (ok) v = p.in[(size_t)wrap_col(f, gc) * NZf + iz];
+    Rf[q * NZfp + iz] = v;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < ncol * NZc; t += blockDim.x) {
+    int q = t / NZc, lc = t - q * NZc;
+    T acc = T(0);
+    if (lc != NZc - 1) {
+      int ez = min(lc / Pc, c.Nz - 1), l = lc - ez * Pc;
+      const T* col = Rf + q * NZfp;
+      if (l == 0) {
+        acc = col[ez * Pf];
+        for (int j = 1; j < Pf; ++j) acc += Js[j * nc + 0] * col[ez * Pf + j];
+        if (ez > 0)
+          for (int j = 1; j < Pf; ++j) acc += Js[j * nc + Pc] * col[(ez - 1) * Pf + j];
+      } else {
+        for (int j = 1; j < Pf; ++j) acc += Js[j * nc + l] * col[ez * Pf + j];
+      }
+    }
+    Sz[q * NZcp + lc] = acc;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < own * NZc; t += blockDim.x) {
+    int k = t / NZc, lc = t - k * NZc;
+    T acc = T(0);
+    if (lc != NZc - 1) {
+      if (k == 0) {
+        acc = Sz[Pf * NZcp + lc];
+        for (int i = 1; i < Pf; ++i) acc += Js[i * nc + 0] * Sz[(Pf + i) * NZcp + lc];
+        if (left)
+          for (int i = 1; i < Pf; ++i) acc += Js[i * nc + Pc] * Sz[i * NZcp + lc];
+      } else if (k == Pc) {
+        acc = Sz[2 * Pf * NZcp + lc];
+        for (int i = 1; i < Pf; ++i) acc += Js[i * nc + Pc] * Sz[(Pf + i) * NZcp + lc];
+      } else {
+        for (int i = 1; i < Pf; ++i) acc += Js[i * nc + k] * Sz[(Pf + i) * NZcp + lc];
+      }
+    }
+    p.out[(size_t)(ex * Pc + k) * NZc + lc] = acc;
+  }
+}
+
+template <typename T>
+cudaError_t transfer(const TransferArgs& a, int restrict_, cudaStream_t st) {
+  TransferParams<T> p;
+  p.f = a.f;
+  p.c = a.c;
+  p.in = (const T*)a.in;
+  p.out = (T*)a.out;
+  p.J = a.J;
+  int nf = a.f.P + 1, nc = a.c.P + 1;
+  int NZfp = slab_pitch(a.f.NZ), NZcp = slab_pitch(a.c.NZ);
+  cudaError_t e;
+  if (restrict_) {
+    size_t sm = ((size_t)(2 * a.f.P + 1) * (NZfp + NZcp) + nf * nc) * sizeof(T) + 16;
+    e = cudaFuncSetAttribute(k_restrict<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_restrict<T><<<a.f.Nx, 256, sm, st>>>(p);
+  } else {
+    size_t sm = ((size_t)nc * (NZcp + NZfp) + nf * nc) * sizeof(T) + 16;
+    e = cudaFuncSetAttribute(k_prolong<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_prolong<T><<<a.f.Nx, 256, sm, st>>>(p);
+  }
+  return cudaGetLastError();
+}
+template cudaError_t transfer<double>(const TransferArgs&, int, cudaStream_t);
+template cudaError_t transfer<float>(const TransferArgs&, int, cudaStream_t);
+
+}  // namespace pmg

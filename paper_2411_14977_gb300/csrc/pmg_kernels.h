@@ -1,0 +1,111 @@
+// Launchers of the device kernels (host-callable, no device code here).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "pmg_common.cuh"
+
+namespace pmg {
+
+// Device scalar slots.  A Krylov solve uses one group of five consecutive slots
+// (offsets below) starting at its base: GROUP_OUTER or GROUP_INNER.
+enum Slot {
+  SLOT_RR = 0,      // ||r||^2 of the current (recursive) residual
+  SLOT_PAP = 1,     // <p, A p>
+  SLOT_RZ = 2,      // <r, z>
+  SLOT_RZOLD = 3,   // previous <r, z>
+  SLOT_ZRO = 4,     // <z, r_old> (flexible CG)
+  GROUP_OUTER = 0,
+  GROUP_INNER = 8,
+  SLOT_BB = 16,     // ||b~||^2 (lifted right-hand side)
+  SLOT_RR64 = 17,   // ||b~ - A x||^2 of the FP64 outer residual
+  SLOT_COUNT = 24
+};
+
+// Per-TU constant-table initialisers.
+cudaError_t init_consts_apply(const ConstTables* host);
+cudaError_t init_consts_levels(const ConstTables* host);
+
+struct CurvedArgs {
+  Shape s;
+  int mode;            // 0 apply (masked), 1 residual b - A x, 2 y = A x with <x, y>, 3 divergence load
+  const void* x;
+  const void* x2;
+  const void* b;
+  void* y;
+  const void* geo;     // column factors (type of the operator)
+  const void* sigma;   // [NZ] (type of the operator)
+  double scale;
+  int mask_input;
+  double* result;
+  Scratch sc;
+};
+template <typename T> cudaError_t curved_op(const CurvedArgs& a, cudaStream_t st);
+template <typename T>
+cudaError_t geometry(const Shape& s, const double* eta, double h, double dx, double dsig, int div,
+                     T* geo, int* status, cudaStream_t st);
+cudaError_t rhs_source(const Shape& s, const double* eta, double h, double dx, double dsig,
+                       const double* mX, const double* mZ, const double* f, const double* gb,
+                       const double* gl, const double* gr, double* b, cudaStream_t st);
+
+struct FlatArgs {
+  Shape s;
+  const void* x;
+  const void* b;
+  void* y;
+  double cx, cz;
+  const void* mX;
+  const void* mZ;
+  int residual;
+};
+template <typename T> cudaError_t flat_op(const FlatArgs& a, cudaStream_t st);
+
+struct FdmArgs {
+  Shape s;
+  int overlap;
+  const void* r;
+  void* x;
+  int post;
+  double omega;
+  const void* Vx;
+  const void* Vz;
+  const void* invden;
+  const void* wx;
+  const void* wz;
+  Scratch sc;
+};
+template <typename T> cudaError_t fdm_smooth(const FdmArgs& a, cudaStream_t st);
+
+struct TransferArgs {
+  Shape f, c;
+  const void* in;
+  void* out;
+  const double* J;
+};
+template <typename T> cudaError_t transfer(const TransferArgs& a, int restrict_, cudaStream_t st);
+
+struct CoarseArgs {
+  int NX1, NZ1, periodic, nsteps;
+  const double* V;     // [Nz][Nz]
+  const double* coef;  // [Nz][nsteps][NX1][2]
+  const double* inv;   // [Nz][NX1]
+  double* work;        // [Nz][NX1]
+};
+template <typename T> cudaError_t coarse_solve(const CoarseArgs& a, const void* b, void* x, cudaStream_t st);
+
+template <typename TA, typename TB>
+cudaError_t dot(size_t n, const TA* x, const TB* y, double* out, int shift, const Scratch& sc, cudaStream_t st);
+template <typename T>
+cudaError_t cg_update(size_t n, T* x, T* r, const T* p, const T* w, T* r_old, double* s, const Scratch& sc,
+                      cudaStream_t st);
+template <typename T>
+cudaError_t rz(size_t n, const T* r, const T* z, const T* r_old, double* s, const Scratch& sc, cudaStream_t st);
+template <typename T>
+cudaError_t p_update(size_t n, T* p, const T* z, const double* s, int flexible, int first, cudaStream_t st);
+cudaError_t to_f32_scaled(size_t n, const double* x, float* y, const double* s, int slot, cudaStream_t st);
+cudaError_t add_f32_scaled(size_t n, double* x, const float* c, const double* s, int slot, cudaStream_t st);
+template <typename T> cudaError_t add(size_t n, T* x, const T* y, cudaStream_t st);
+cudaError_t init_x(size_t n, int NZ, double* x, const double* x0, const double* pD, int* status, cudaStream_t st);
+cudaError_t check_finite(size_t n, const double* v, int* status, cudaStream_t st);
+
+}  // namespace pmg

@@ -1,0 +1,980 @@
+// Host orchestration and C ABI of the p-multigrid-preconditioned Krylov pressure solve.
+//
+// Setup (pmg_create): level orders by the coarsening rule (Sec. 5.1), the flat level
+// operators (Sec. 5.4: time-constant preconditioner on the linearised geometry), Schwarz
+// fast-diagonalisation factors per element class (Sec. 5.3), transfer matrices
+// I = Phi V^-1 (Sec. 5.2) and the coarse factor; all uploaded once.
+// Solve (pmg_solve): FP64 PCG / flexible CG / defect correction on the actual-geometry
+// operator with one V-cycle as preconditioner (Sec. 5, Sec. 5.4), or FP64 iterative
+// refinement around an FP32 flexible-CG solve whose V-cycle runs in FP32 (coarse solve FP64).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "host_basis.h"
+#include "pmg.h"
+#include "pmg_kernels.h"
+
+using namespace pmg;
+
+namespace {
+
+thread_local std::string g_err;
+
+pmg_status fail(pmg_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+#define CK(call)                                                                           \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) {                                                               \
+      return fail(e_ == cudaErrorMemoryAllocation ? PMG_ERR_OOM : PMG_ERR_CUDA,            \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                     \
+    }                                                                                      \
+  } while (0)
+
+#define CKS(call)                                                                          \
+  do {                                                                                     \
+    pmg_status s_ = (call);                                                                \
+    if (s_ != PMG_OK) return s_;                                                           \
+  } while (0)
+
+struct DeviceGuard {
+  int old = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&old);
+    if (old != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur;
+    cudaGetDevice(&cur);
+    if (old >= 0 && cur != old) cudaSetDevice(old);
+  }
+};
+
+std::mutex g_const_mu;
+std::set<int> g_const_devices;
+
+pmg_status ensure_constants(int dev) {
+  std::lock_guard<std::mutex> lk(g_const_mu);
+  if (g_const_devices.count(dev)) return PMG_OK;
+  static ConstTables t;
+  std::memset(&t, 0, sizeof(t));
+  for (int P = 1; P <= MAXP; ++P) {
+    std::vector<double> x, w;
+    lgl(P, x, w);
+    std::vector<double> D = diff_matrix(P);
+    int n = P + 1;
+    for (int i = 0; i < n; ++i) {
+      t.w[P][i] = w[i];
+      t.wf[P][i] = (float)w[i];
+      for (int m = 0; m < n; ++m) {
+        t.D[P][i][m] = D[i * n + m];
+        t.Df[P][i][m] = (float)D[i * n + m];
+        double k = 0.0;
+        for (int q = 0; q < n; ++q) k += D[q * n + i] * w[q] * D[q * n + m];
+        t.K[P][i][m] = k;
+        t.Kf[P][i][m] = (float)k;
+      }
+    }
+  }
+  CK(init_consts_apply(&t));
+  CK(init_consts_levels(&t));
+  g_const_devices.insert(dev);
+  return PMG_OK;
+}
+
+// Assembled 1D LGL stiffness entry K[a][b] of order p over ncell cells (periodic or not),
+// and assembled weights.
+struct Line1D {
+  int p, ncell, periodic, n;  // n nodes
+  std::vector<double> K1, w;  // element stiffness (p+1)^2, weights
+  Line1D(int p_, int nc, int per) : p(p_), ncell(nc), periodic(per) {
+    n = nc * p + (per ? 0 : 1);
+    std::vector<double> x;
+    lgl(p, x, w);
+    std::vector<double> D = diff_matrix(p);
+    K1.assign((p + 1) * (p + 1), 0.0);
+    for (int i = 0; i <= p; ++i)
+      for (int m = 0; m <= p; ++m) {
+        double s = 0.0;
+        for (int q = 0; q <= p; ++q) s += D[q * (p + 1) + i] * w[q] * D[q * (p + 1) + m];
+        K1[i * (p + 1) + m] = s;
+      }
+  }
+  int wrap(int a) const { return periodic ? ((a % n) + n) % n : a; }
+  // elements (cells) containing node a, with local index
+  void owners(int a, int* e, int* loc, int& cnt) const {
+    cnt = 0;
+    a = wrap(a);
+    int c = a / p, l = a - c * p;
+    if (!periodic && c == ncell) { c = ncell - 1; l = p; }
+    e[cnt] = c; loc[cnt] = l; ++cnt;
+    if (l == 0) {
+      int cl = c - 1;
+      if (periodic) cl = (cl + ncell) % ncell;
+      if (cl >= 0) { e[cnt] = cl; loc[cnt] = p; ++cnt; }
+    }
+  }
+  double K(int a, int b) const {
+    int ea[2], la[2], eb[2], lb[2], na, nb;
+    owners(a, ea, la, na);
+    owners(b, eb, lb, nb);
+    double s = 0.0;
+    for (int i = 0; i < na; ++i)
+      for (int j = 0; j < nb; ++j)
+        if (ea[i] == eb[j]) s += K1[la[i] * (p + 1) + lb[j]];
+    return s;
+  }
+  double M(int a) const {
+    int e[2], l[2], c;
+    owners(a, e, l, c);
+    double s = 0.0;
+    for (int i = 0; i < c; ++i) s += w[l[i]];
+    return s;
+  }
+};
+
+template <typename T>
+T* upload(const std::vector<double>& v, std::vector<void*>& allocs, cudaError_t& err) {
+  T* d = nullptr;
+  err = cudaMalloc(&d, std::max<size_t>(1, v.size()) * sizeof(T));
+  if (err != cudaSuccess) return nullptr;
+  allocs.push_back(d);
+  std::vector<T> h(v.begin(), v.end());
+  err = cudaMemcpy(d, h.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+  return d;
+}
+
+}  // namespace
+
+struct LevelDev {
+  int order = 0, overlap = 0;
+  Shape s{};
+  void* mX[2]{};
+  void* mZ[2]{};
+  void* Vx[2]{};
+  void* Vz[2]{};
+  void* invden[2]{};
+  void* wx[2]{};
+  void* wz[2]{};
+  double* J = nullptr;  // transfer from level l+1 (coarse) to this level
+  void* b[2]{};
+  void* x[2]{};
+  void* t[2]{};
+};
+
+struct pmg_handle {
+  pmg_mesh_desc mesh{};
+  pmg_opts opts{};
+  int device = 0;
+  double dx = 0, dsig = 0, cx = 0, cz = 0;
+  size_t N = 0, Nfree = 0;
+  std::vector<int> orders;
+  std::vector<LevelDev> lv;
+  std::vector<void*> allocs;
+  std::vector<double> xcols, sigrows;
+  // fine geometry
+  double* eta = nullptr;
+  void* geo[2]{};
+  double* geo_div = nullptr;
+  void* sigma[2]{};
+  int* status = nullptr;      // [0] inputs of the current solve, [1] geometry
+  CoarseArgs coarse{};
+  // FP64 Krylov vectors
+  double *x = nullptr, *r = nullptr, *p = nullptr, *w = nullptr, *z = nullptr, *rold = nullptr;
+  // FP32 inner vectors
+  float *r32 = nullptr, *c32 = nullptr, *p32 = nullptr, *w32 = nullptr, *z32 = nullptr, *rold32 = nullptr;
+  double* scal = nullptr;
+  double* scal_host = nullptr;
+  int* status_host = nullptr;
+  double* io = nullptr;  // pmg_solve_host: out, b, p_D, x0
+  Scratch sc{};
+
+  template <typename T> T* alloc(size_t n, cudaError_t& e) {
+    T* d = nullptr;
+    e = cudaMalloc(&d, std::max<size_t>(n, 1) * sizeof(T));
+    if (e == cudaSuccess) allocs.push_back(d);
+    return d;
+  }
+  ~pmg_handle() {
+    for (void* a : allocs) cudaFree(a);
+    if (scal_host) cudaFreeHost(scal_host);
+    if (status_host) cudaFreeHost(status_host);
+  }
+};
+
+namespace {
+
+template <typename T> constexpr int PI = std::is_same<T, double>::value ? 0 : 1;
+
+// ---- setup helpers -----------------------------------------------------------------
+pmg_status build_level(pmg_handle* h, int l) {
+  LevelDev& L = h->lv[l];
+  const pmg_mesh_desc& m = h->mesh;
+  int p = h->orders[l];
+  L.order = p;
+  L.s.P = p;
+  L.s.Nx = m.cells_x;
+  L.s.Nz = m.cells_z;
+  L.s.periodic = m.periodic_x;
+  L.s.NX = m.cells_x * p + (m.periodic_x ? 0 : 1);
+  L.s.NZ = m.cells_z * p + 1;
+  size_t NL = (size_t)L.s.NX * L.s.NZ;
+  Line1D lx(p, m.cells_x, m.periodic_x), lz(p, m.cells_z, 0);
+  std::vector<double> mX(L.s.NX), mZ(L.s.NZ);
+  for (int a = 0; a < L.s.NX; ++a) mX[a] = lx.M(a);
+  for (int a = 0; a < L.s.NZ; ++a) mZ[a] = lz.M(a);
+  cudaError_t e;
+  L.mX[0] = upload<double>(mX, h->allocs, e); CK(e);
+  L.mX[1] = upload<float>(mX, h->allocs, e); CK(e);
+  L.mZ[0] = upload<double>(mZ, h->allocs, e); CK(e);
+  L.mZ[1] = upload<float>(mZ, h->allocs, e); CK(e);
+  for (int k = 0; k < 2; ++k) {
+    size_t sz = k == 0 ? sizeof(double) : sizeof(float);
+    for (void** v : {&L.b[k], &L.x[k], &L.t[k]}) {
+      CK(cudaMalloc(v, NL * sz));
+      h->allocs.push_back(*v);
+      CK(cudaMemset(*v, 0, NL * sz));
+    }
+  }
+  bool coarsest = l == (int)h->orders.size() - 1;
+  if (coarsest) return PMG_OK;
+
+  // ---- Schwarz factors (fast diagonalisation per element class)
+  int O = (p >= 3) ? h->opts.overlap : 0;  // overlap lines of two neighbours must not meet
+  L.overlap = O;
+  int NB = p + 1 + 2 * O;
+  std::vector<double> Vx(4 * NB * NB, 0.0), Vz(4 * NB * NB, 0.0);
+  std::vector<double> lamx(4 * NB, 0.0), lamz(4 * NB, 0.0);
+  int kx[4] = {0, 0, 0, 0}, kz[4] = {0, 0, 0, 0};  // eigenpairs per class (modes >= k are padding)
+  std::vector<double> wx(L.s.NX, 0.0), wz(L.s.NZ, 0.0);
+  // x classes
+  auto xsub = [&](int ex, std::vector<int>& loc, std::vector<int>& glob) {
+    loc.clear(); glob.clear();
+    for (int a = 0; a < NB; ++a) {
+      int g = ex * p - O + a;
+      if (!m.periodic_x && (g < 0 || g >= L.s.NX)) continue;
+      loc.push_back(a);
+      glob.push_back(lx.wrap(g));
+    }
+  };
+  auto zsub = [&](int ez, std::vector<int>& loc, std::vector<int>& glob) {
+    loc.clear(); glob.clear();
+    for (int b = 0; b < NB; ++b) {
+      int g = ez * p - O + b;
+      if (g < 0 || g >= L.s.NZ - 1) continue;  // Dirichlet row excluded
+      loc.push_back(b);
+      glob.push_back(g);
+    }
+  };
+  auto fill_class = [&](const Line1D& line, const std::vector<int>& loc, const std::vector<int>& glob,
+                        double* V, double* lam, int& kcount) {
+    int k = (int)glob.size();
+    std::vector<double> K(k * k), M(k), Vk, lk;
+    for (int i = 0; i < k; ++i) {
+      M[i] = line.M(glob[i]);
+      for (int j = 0; j < k; ++j) K[i * k + j] = line.K(glob[i], glob[j]);
+    }
+    gen_eig_diag(k, K, M, Vk, lk);
+    for (int i = 0; i < k; ++i)
+      for (int a = 0; a < k; ++a) V[loc[i] * NB + a] = Vk[i * k + a];
+    for (int a = 0; a < k; ++a) lam[a] = lk[a];
+    kcount = k;
+  };
+  std::vector<int> loc, glob;
+  for (int cls = 0; cls < 4; ++cls) {
+    int ex = -1;
+    if (m.periodic_x) { if (cls == 0) ex = 0; }
+    else {
+      int Nx = m.cells_x;
+      if (cls == 0 && Nx >= 3) ex = 1;
+      if (cls == 1 && Nx >= 2) ex = 0;
+      if (cls == 2 && Nx >= 2) ex = Nx - 1;
+      if (cls == 3 && Nx == 1) ex = 0;
+    }
+    if (ex >= 0) { xsub(ex, loc, glob); fill_class(lx, loc, glob, &Vx[cls * NB * NB], &lamx[cls * NB], kx[cls]); }
+    int Nz = m.cells_z, ez = -1;
+    if (cls == 0 && Nz >= 3) ez = 1;
+    if (cls == 1 && Nz >= 2) ez = 0;
+    if (cls == 2 && Nz >= 2) ez = Nz - 1;
+    if (cls == 3 && Nz == 1) ez = 0;
+    if (ez >= 0) { zsub(ez, loc, glob); fill_class(lz, loc, glob, &Vz[cls * NB * NB], &lamz[cls * NB], kz[cls]); }
+  }
+  std::vector<double> invden(16 * NB * NB, 0.0);
+  for (int xc = 0; xc < 4; ++xc)
+    for (int zc = 0; zc < 4; ++zc)
+      for (int a = 0; a < NB; ++a)
+        for (int b = 0; b < NB; ++b) {
+          double la = lamx[xc * NB + a], lb = lamz[zc * NB + b];
+          if (a < kx[xc] && b < kz[zc]) {
+            double d = h->cx * la + h->cz * lb;
+            invden[((xc * 4 + zc) * NB + a) * NB + b] = d > 0.0 ? 1.0 / d : 0.0;
+          }
+        }
+  for (int ex = 0; ex < m.cells_x; ++ex) { xsub(ex, loc, glob); for (int g : glob) wx[g] += 1.0; }
+  for (int ez = 0; ez < m.cells_z; ++ez) { zsub(ez, loc, glob); for (int g : glob) wz[g] += 1.0; }
+  for (auto& v : wx) v = v > 0 ? 1.0 / v : 0.0;
+  for (auto& v : wz) v = v > 0 ? 1.0 / v : 0.0;
+  L.Vx[0] = upload<double>(Vx, h->allocs, e); CK(e);
+  L.Vx[1] = upload<float>(Vx, h->allocs, e); CK(e);
+  L.Vz[0] = upload<double>(Vz, h->allocs, e); CK(e);
+  L.Vz[1] = upload<float>(Vz, h->allocs, e); CK(e);
+  L.invden[0] = upload<double>(invden, h->allocs, e); CK(e);
+  L.invden[1] = upload<float>(invden, h->allocs, e); CK(e);
+  L.wx[0] = upload<double>(wx, h->allocs, e); CK(e);
+  L.wx[1] = upload<float>(wx, h->allocs, e); CK(e);
+  L.wz[0] = upload<double>(wz, h->allocs, e); CK(e);
+  L.wz[1] = upload<float>(wz, h->allocs, e); CK(e);
+  L.J = upload<double>(transfer_matrix(h->orders[l + 1], p), h->allocs, e); CK(e);
+  return PMG_OK;
+}
+
+pmg_status build_coarse(pmg_handle* h) {
+  const pmg_mesh_desc& m = h->mesh;
+  int Nz = m.cells_z, NX1 = m.cells_x + (m.periodic_x ? 0 : 1);
+  Line1D lx(1, m.cells_x, m.periodic_x), lz(1, m.cells_z, 0);
+  std::vector<double> K(Nz * Nz), M(Nz), V, mu;
+  for (int i = 0; i < Nz; ++i) {
+    M[i] = lz.M(i);
+    for (int j = 0; j < Nz; ++j) K[i * Nz + j] = lz.K(i, j);
+  }
+  gen_eig_diag(Nz, K, M, V, mu);
+  int n = NX1;
+  int nsteps = 0;
+  while ((1 << nsteps) < n) ++nsteps;
+  std::vector<double> coef((size_t)Nz * nsteps * n * 2, 0.0), inv((size_t)Nz * n, 0.0);
+  for (int k = 0; k < Nz; ++k) {
+    std::vector<double> a(n), b(n), c(n), a2(n), b2(n), c2(n);
+    for (int i = 0; i < n; ++i) {
+      b[i] = h->cx * lx.K(i, i) + h->cz * mu[k] * lx.M(i);
+      a[i] = (m.periodic_x || i > 0) ? h->cx * lx.K(i, lx.wrap(i - 1)) : 0.0;
+      c[i] = (m.periodic_x || i < n - 1) ? h->cx * lx.K(i, lx.wrap(i + 1)) : 0.0;
+    }
+    int s = 1;
+    for (int step = 0; step < nsteps; ++step, s <<= 1) {
+      for (int i = 0; i < n; ++i) {
+        int im = i - s, ip = i + s;
+        bool vm = true, vp = true;
+        if (m.periodic_x) { im = ((im % n) + n) % n; ip %= n; }
+        else { vm = im >= 0; vp = ip < n; }
+        double k1 = vm ? a[i] / b[im] : 0.0, k2 = vp ? c[i] / b[ip] : 0.0;
+        a2[i] = vm ? -k1 * a[im] : 0.0;
+        c2[i] = vp ? -k2 * c[ip] : 0.0;
+        b2[i] = b[i] - (vm ? k1 * c[im] : 0.0) - (vp ? k2 * a[ip] : 0.0);
+        coef[(((size_t)k * nsteps + step) * n + i) * 2 + 0] = k1;
+        coef[(((size_t)k * nsteps + step) * n + i) * 2 + 1] = k2;
+      }
+      a.swap(a2); b.swap(b2); c.swap(c2);
+    }
+    for (int i = 0; i < n; ++i) inv[(size_t)k * n + i] = 1.0 / (m.periodic_x ? a[i] + b[i] + c[i] : b[i]);
+  }
+  cudaError_t e;
+  h->coarse.NX1 = NX1;
+  h->coarse.NZ1 = Nz + 1;
+  h->coarse.periodic = m.periodic_x;
+  h->coarse.nsteps = nsteps;
+  h->coarse.V = upload<double>(V, h->allocs, e); CK(e);
+  h->coarse.coef = upload<double>(coef, h->allocs, e); CK(e);
+  h->coarse.inv = upload<double>(inv, h->allocs, e); CK(e);
+  h->coarse.work = h->alloc<double>((size_t)Nz * n, e); CK(e);
+  return PMG_OK;
+}
+
+// ---- level operations --------------------------------------------------------------
+template <typename T>
+pmg_status level_residual(pmg_handle* h, int l, const void* b, const void* x, void* y, int residual,
+                          cudaStream_t st) {
+  LevelDev& L = h->lv[l];
+  FlatArgs a{L.s, x, b, y, h->cx, h->cz, L.mX[PI<T>], L.mZ[PI<T>], residual};
+  CK(flat_op<T>(a, st));
+  return PMG_OK;
+}
+
+template <typename T>
+pmg_status level_fdm(pmg_handle* h, int l, const void* r, void* x, int post, cudaStream_t st) {
+  LevelDev& L = h->lv[l];
+  FdmArgs a{L.s, L.overlap, r, x, post, h->opts.omega, L.Vx[PI<T>], L.Vz[PI<T>], L.invden[PI<T>],
+            L.wx[PI<T>], L.wz[PI<T>], h->sc};
+  CK(fdm_smooth<T>(a, st));
+  return PMG_OK;
+}
+
+// nu sweeps on A_l x = b (x updated); x_zero: x is known to be zero on entry
+template <typename T>
+pmg_status level_smooth(pmg_handle* h, int l, const void* b, void* x, int post, bool x_zero,
+                        cudaStream_t st) {
+  LevelDev& L = h->lv[l];
+  for (int it = 0; it < h->opts.nu; ++it) {
+    if (it == 0 && x_zero) {
+      CKS(level_fdm<T>(h, l, b, x, post, st));
+    } else {
+      CKS(level_residual<T>(h, l, b, x, L.t[PI<T>], 1, st));
+      CKS(level_fdm<T>(h, l, L.t[PI<T>], x, post, st));
+    }
+  }
+  return PMG_OK;
+}
+
+template <typename T>
+pmg_status transfer_op(pmg_handle* h, int l, const void* in, void* out, int restrict_, cudaStream_t st) {
+  TransferArgs a{h->lv[l].s, h->lv[l + 1].s, in, out, h->lv[l].J};
+  CK(transfer<T>(a, restrict_, st));
+  return PMG_OK;
+}
+
+template <typename T>
+pmg_status vcycle(pmg_handle* h, int l, const void* b, void* x, cudaStream_t st) {
+  int nl = (int)h->lv.size();
+  LevelDev& L = h->lv[l];
+  size_t NL = (size_t)L.s.NX * L.s.NZ;
+  if (l == nl - 1) {
+    CK(coarse_solve<T>(h->coarse, b, x, st));
+    return PMG_OK;
+  }
+  CK(cudaMemsetAsync(x, 0, NL * sizeof(T), st));
+  CKS(level_smooth<T>(h, l, b, x, 0, true, st));
+  CKS(level_residual<T>(h, l, b, x, L.t[PI<T>], 1, st));
+  LevelDev& C = h->lv[l + 1];
+  CKS(transfer_op<T>(h, l, L.t[PI<T>], C.b[PI<T>], 1, st));
+  CKS(vcycle<T>(h, l + 1, C.b[PI<T>], C.x[PI<T>], st));
+  CKS(transfer_op<T>(h, l, C.x[PI<T>], x, 0, st));
+  CKS(level_smooth<T>(h, l, b, x, 1, false, st));
+  return PMG_OK;
+}
+
+template <typename T>
+pmg_status curved(pmg_handle* h, int mode, const void* x, const void* b, void* y, int mask, double* result,
+                  cudaStream_t st) {
+  CurvedArgs a{};
+  a.s = h->lv[0].s;
+  a.mode = mode;
+  a.x = x;
+  a.b = b;
+  a.y = y;
+  a.geo = h->geo[PI<T>];
+  a.sigma = h->sigma[PI<T>];
+  a.scale = 1.0;
+  a.mask_input = mask;
+  a.result = result;
+  a.sc = h->sc;
+  CK(curved_op<T>(a, st));
+  return PMG_OK;
+}
+
+pmg_status read_scalars(pmg_handle* h, cudaStream_t st) {
+  CK(cudaMemcpyAsync(h->scal_host, h->scal, SLOT_COUNT * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(h->status_host, h->status, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return PMG_OK;
+}
+
+// ---- solvers -----------------------------------------------------------------------
+// r = b - A x with the surface row of x holding p_D (lifted residual), ||r||^2 -> slot
+pmg_status outer_residual(pmg_handle* h, const double* b, int slot, cudaStream_t st) {
+  return curved<double>(h, 1, h->x, b, h->r, 0, h->scal + slot, st);
+}
+
+// ||b~||^2: residual of the zero free guess (x0 == NULL: equals the first residual)
+pmg_status lifted_norm(pmg_handle* h, const double* b, const double* pD, const double* x0, cudaStream_t st) {
+  size_t N = h->N;
+  int NZ = h->lv[0].s.NZ;
+  if (!x0) {
+    CKS(outer_residual(h, b, SLOT_BB, st));
+    CK(cudaMemcpyAsync(h->scal + SLOT_RR64, h->scal + SLOT_BB, sizeof(double), cudaMemcpyDeviceToDevice, st));
+    return PMG_OK;
+  }
+  CK(init_x(N, NZ, h->p, nullptr, pD, h->status, st));
+  CKS(curved<double>(h, 1, h->p, b, h->w, 0, h->scal + SLOT_BB, st));
+  CKS(outer_residual(h, b, SLOT_RR64, st));
+  return PMG_OK;
+}
+
+pmg_status solve_krylov64(pmg_handle* h, const double* b, pmg_solve_info* info, cudaStream_t st) {
+  // PCG (or flexible CG) on A_FF with the FP64 V-cycle; x, r = b~ - A x already set.
+  size_t N = h->N;
+  double* s = h->scal + GROUP_OUTER;
+  const double tol2 = h->opts.tol * h->opts.tol;
+  int flexible = h->opts.outer == PMG_FCG;
+  double bb = h->scal_host[SLOT_BB];
+  int it = 0;
+  bool restart = true;
+  if (h->scal_host[SLOT_RR64] <= tol2 * bb) {  // the initial guess already meets the tolerance
+    if (info) info->iterations = 0;
+    return PMG_OK;
+  }
+  while (it < h->opts.max_iter) {
+    if (restart) {
+      CKS(vcycle<double>(h, 0, h->r, h->z, st));
+      CK(rz<double>(N, h->r, h->z, nullptr, s, h->sc, st));
+      CK(p_update<double>(N, h->p, h->z, s, 0, 1, st));
+      restart = false;
+    }
+    CKS(curved<double>(h, 2, h->p, nullptr, h->w, 1, s + SLOT_PAP, st));
+    CK(cg_update<double>(N, h->x, h->r, h->p, h->w, flexible ? h->rold : nullptr, s, h->sc, st));
+    ++it;
+    CKS(read_scalars(h, st));
+    double rr = h->scal_host[GROUP_OUTER + SLOT_RR];
+    if (!std::isfinite(rr)) return fail(PMG_ERR_NONFINITE, "non-finite residual");
+    if (rr <= tol2 * bb) {
+      // confirm with the true residual; restart on drift
+      CKS(outer_residual(h, b, SLOT_RR64, st));
+      CKS(read_scalars(h, st));
+      if (h->scal_host[SLOT_RR64] <= tol2 * bb) break;
+      restart = true;
+      continue;
+    }
+    CKS(vcycle<double>(h, 0, h->r, h->z, st));
+    CK(rz<double>(N, h->r, h->z, flexible ? h->rold : nullptr, s, h->sc, st));
+    CK(p_update<double>(N, h->p, h->z, s, flexible, 0, st));
+  }
+  if (info) info->iterations = it;
+  return PMG_OK;
+}
+
+pmg_status solve_pdc(pmg_handle* h, const double* b, pmg_solve_info* info, cudaStream_t st) {
+  // x <- x + B (b~ - A x) (Sec. 5.4); B = V-cycle in the handle's precision
+  size_t N = h->N;
+  const double tol2 = h->opts.tol * h->opts.tol;
+  double bb = h->scal_host[SLOT_BB];
+  int it = 0;
+  while (it < h->opts.max_iter) {
+    CKS(read_scalars(h, st));
+    double rr = h->scal_host[SLOT_RR64];
+    if (!std::isfinite(rr)) return fail(PMG_ERR_NONFINITE, "non-finite residual");
+    if (rr <= tol2 * bb) break;
+    if (h->opts.precision == PMG_FP64) {
+      CKS(vcycle<double>(h, 0, h->r, h->z, st));
+      CK(add<double>(N, h->x, h->z, st));
+    } else {
+      CK(to_f32_scaled(N, h->r, h->r32, h->scal, SLOT_RR64, st));
+      CKS(vcycle<float>(h, 0, h->r32, h->z32, st));
+      CK(add_f32_scaled(N, h->x, h->z32, h->scal, SLOT_RR64, st));
+    }
+    ++it;
+    CKS(outer_residual(h, b, SLOT_RR64, st));
+  }
+  if (info) info->iterations = it;
+  return PMG_OK;
+}
+
+pmg_status solve_refine(pmg_handle* h, const double* b, pmg_solve_info* info, cudaStream_t st) {
+  // FP64 iterative refinement: r = b~ - A x (FP64); inner FP32 flexible CG on A c = r/||r||
+  // with the FP32 V-cycle; x += ||r|| c.
+  size_t N = h->N;
+  const double tol2 = h->opts.tol * h->opts.tol;
+  double bb = h->scal_host[SLOT_BB];
+  double* s = h->scal + GROUP_INNER;
+  double itol2 = h->opts.inner_tol * h->opts.inner_tol;
+  int outer = 0, inner_total = 0;
+  while (outer < h->opts.max_iter) {
+    CKS(read_scalars(h, st));
+    double rr = h->scal_host[SLOT_RR64];
+    if (!std::isfinite(rr)) return fail(PMG_ERR_NONFINITE, "non-finite residual");
+    if (rr <= tol2 * bb) break;
+    CK(to_f32_scaled(N, h->r, h->r32, h->scal, SLOT_RR64, st));
+    CK(cudaMemsetAsync(h->c32, 0, N * sizeof(float), st));
+    CKS(vcycle<float>(h, 0, h->r32, h->z32, st));
+    CK(rz<float>(N, h->r32, h->z32, nullptr, s, h->sc, st));
+    CK(p_update<float>(N, h->p32, h->z32, s, 0, 1, st));
+    for (int j = 0; j < h->opts.inner_max; ++j) {
+      CKS(curved<float>(h, 2, h->p32, nullptr, h->w32, 1, s + SLOT_PAP, st));
+      CK(cg_update<float>(N, h->c32, h->r32, h->p32, h->w32, h->rold32, s, h->sc, st));
+      ++inner_total;
+      CKS(read_scalars(h, st));
+      double irr = h->scal_host[GROUP_INNER + SLOT_RR];
+      if (!std::isfinite(irr)) return fail(PMG_ERR_NONFINITE, "non-finite inner residual");
+      if (irr <= itol2) break;
+      CKS(vcycle<float>(h, 0, h->r32, h->z32, st));
+      CK(rz<float>(N, h->r32, h->z32, h->rold32, s, h->sc, st));
+      CK(p_update<float>(N, h->p32, h->z32, s, 1, 0, st));
+    }
+    CK(add_f32_scaled(N, h->x, h->c32, h->scal, SLOT_RR64, st));
+    ++outer;
+    CKS(outer_residual(h, b, SLOT_RR64, st));
+  }
+  if (info) {
+    info->iterations = outer;
+    info->inner_iterations = inner_total;
+  }
+  return PMG_OK;
+}
+
+pmg_status check_handle(const pmg_handle* h) {
+  if (!h) return fail(PMG_ERR_INVALID, "null handle");
+  return PMG_OK;
+}
+
+}  // namespace
+
+// =====================================================================================
+// C ABI
+// =====================================================================================
+extern "C" {
+
+void pmg_default_opts(pmg_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = PMG_FP64;
+  o->outer = PMG_PCG;
+  o->smoother = PMG_ASM_FDM;
+  o->precond_geom = PMG_FLAT_LINEARISED;
+  o->overlap = 1;
+  o->nu = 2;
+  o->omega = 0.8;
+  o->tol = 1e-10;
+  o->max_iter = 500;
+  o->inner_max = 40;
+  o->inner_tol = 1e-5;
+  o->nlevels = 0;
+}
+
+const char* pmg_last_error(void) { return g_err.c_str(); }
+
+pmg_status pmg_create(const pmg_mesh_desc* mesh, const pmg_opts* opts, pmg_handle** out) {
+  if (!out) return fail(PMG_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!mesh) return fail(PMG_ERR_INVALID, "mesh is NULL");
+  pmg_opts o;
+  if (opts) o = *opts; else pmg_default_opts(&o);
+  const pmg_mesh_desc& m = *mesh;
+  if (m.order < 1 || m.order > MAXP) return fail(PMG_ERR_INVALID, "order must be in 1..10");
+  if (m.cells_x < 1 || m.cells_z < 1) return fail(PMG_ERR_INVALID, "cells must be >= 1");
+  if (m.cells_x > 65535 || m.cells_z > 64) return fail(PMG_ERR_INVALID, "too many cells (cells_z <= 64)");
+  if (!(m.x1 > m.x0) || !(m.h > 0.0)) return fail(PMG_ERR_INVALID, "need x1 > x0 and h > 0");
+  if (m.periodic_x && (m.cells_x < 3 || (m.cells_x & (m.cells_x - 1))))
+    return fail(PMG_ERR_INVALID, "periodic_x needs cells_x >= 3 and a power of two");
+  if (o.precision < 0 || o.precision > PMG_MIXED_FP32) return fail(PMG_ERR_INVALID, "unsupported precision");
+  if (o.outer < PMG_PCG || o.outer > PMG_PDC) return fail(PMG_ERR_INVALID, "bad outer method");
+  if (o.smoother != PMG_ASM_FDM || o.precond_geom != PMG_FLAT_LINEARISED)
+    return fail(PMG_ERR_INVALID, "unsupported smoother or preconditioner geometry");
+  if (o.overlap < 0 || o.overlap > MAXO || o.nu < 1 || !(o.omega > 0) || !(o.tol > 0) || o.max_iter < 1 ||
+      o.inner_max < 1 || !(o.inner_tol > 0))
+    return fail(PMG_ERR_INVALID, "bad solver options");
+  std::vector<int> orders;
+  if (o.nlevels > 0) {
+    if (o.nlevels > 8) return fail(PMG_ERR_INVALID, "at most 8 levels");
+    for (int i = 0; i < o.nlevels; ++i) orders.push_back(o.level_orders[i]);
+    if (orders[0] != m.order || orders.back() != 1) return fail(PMG_ERR_INVALID, "levels must run from order to 1");
+    for (size_t i = 1; i < orders.size(); ++i)
+      if (orders[i] >= orders[i - 1]) return fail(PMG_ERR_INVALID, "level orders must decrease");
+  } else {
+    orders = coarsening_sequence(m.order);
+  }
+  if (orders.size() < 2) return fail(PMG_ERR_INVALID, "order must be >= 2 (the coarsest level is order 1)");
+
+  auto* h = new (std::nothrow) pmg_handle();
+  if (!h) return fail(PMG_ERR_OOM, "host allocation failed");
+  auto bail = [&](pmg_status s) { delete h; return s; };
+  cudaGetDevice(&h->device);
+  DeviceGuard dg(h->device);
+  if (ensure_constants(h->device) != PMG_OK) return bail(PMG_ERR_CUDA);
+  h->mesh = m;
+  h->opts = o;
+  h->orders = orders;
+  h->dx = (m.x1 - m.x0) / m.cells_x;
+  h->dsig = 1.0 / m.cells_z;
+  h->cx = m.h * h->dsig / h->dx;
+  h->cz = h->dx / (m.h * h->dsig);
+  h->lv.resize(orders.size());
+  for (size_t l = 0; l < orders.size(); ++l) {
+    pmg_status s = build_level(h, (int)l);
+    if (s != PMG_OK) return bail(s);
+  }
+  {
+    pmg_status s = build_coarse(h);
+    if (s != PMG_OK) return bail(s);
+  }
+  const Shape& F = h->lv[0].s;
+  h->N = (size_t)F.NX * F.NZ;
+  h->Nfree = (size_t)F.NX * (F.NZ - 1);
+  // node coordinates
+  std::vector<double> x, w;
+  lgl(m.order, x, w);
+  h->xcols.resize(F.NX);
+  for (int ix = 0; ix < F.NX; ++ix) {
+    int ex = ix / m.order, i = ix % m.order;
+    h->xcols[ix] = m.x0 + (ex + (x[i] + 1.0) / 2.0) * h->dx;
+  }
+  h->sigrows.resize(F.NZ);
+  for (int iz = 0; iz < F.NZ; ++iz) {
+    int ez = std::min(iz / m.order, m.cells_z - 1), j = iz - ez * m.order;
+    h->sigrows[iz] = (ez + (x[j] + 1.0) / 2.0) * h->dsig;
+  }
+  cudaError_t e;
+#define ALLOC(ptr, T, n)                                   \
+  do {                                                     \
+    ptr = h->alloc<T>((n), e);                             \
+    if (e != cudaSuccess) {                                \
+      fail(PMG_ERR_OOM, "device allocation failed");       \
+      return bail(PMG_ERR_OOM);                            \
+    }                                                      \
+  } while (0)
+  ALLOC(h->eta, double, F.NX);
+  ALLOC(h->geo[0], double, (size_t)m.cells_x * (m.order + 1) * 4);
+  ALLOC(h->geo[1], float, (size_t)m.cells_x * (m.order + 1) * 4);
+  ALLOC(h->geo_div, double, (size_t)m.cells_x * (m.order + 1) * 4);
+  h->sigma[0] = upload<double>(h->sigrows, h->allocs, e);
+  if (e != cudaSuccess) return bail(fail(PMG_ERR_OOM, "upload failed"));
+  h->sigma[1] = upload<float>(h->sigrows, h->allocs, e);
+  if (e != cudaSuccess) return bail(fail(PMG_ERR_OOM, "upload failed"));
+  ALLOC(h->status, int, 2);
+  ALLOC(h->x, double, h->N);
+  ALLOC(h->r, double, h->N);
+  ALLOC(h->p, double, h->N);
+  ALLOC(h->w, double, h->N);
+  ALLOC(h->z, double, h->N);
+  ALLOC(h->rold, double, h->N);
+  ALLOC(h->r32, float, h->N);
+  ALLOC(h->c32, float, h->N);
+  ALLOC(h->p32, float, h->N);
+  ALLOC(h->w32, float, h->N);
+  ALLOC(h->z32, float, h->N);
+  ALLOC(h->rold32, float, h->N);
+  ALLOC(h->scal, double, SLOT_COUNT);
+  size_t nedges = (size_t)m.cells_x + 1;
+  size_t ebuf = nedges * (2 * MAXO + 1) * (size_t)F.NZ;
+  h->sc.edgebuf = h->alloc<double>(ebuf, e);
+  if (e != cudaSuccess) return bail(fail(PMG_ERR_OOM, "device allocation failed"));
+  ALLOC(h->sc.edgecnt, unsigned, nedges);
+  ALLOC(h->sc.partials, double, std::max<size_t>(1024, 2 * (size_t)m.cells_x + 8));
+  ALLOC(h->sc.edgepart, double, nedges);
+  ALLOC(h->sc.redcnt, unsigned, 1);
+#undef ALLOC
+  if (cudaMemset(h->sc.edgebuf, 0, ebuf * sizeof(double)) != cudaSuccess ||
+      cudaMemset(h->sc.edgecnt, 0, nedges * sizeof(unsigned)) != cudaSuccess ||
+      cudaMemset(h->sc.redcnt, 0, sizeof(unsigned)) != cudaSuccess ||
+      cudaMemset(h->status, 0, 2 * sizeof(int)) != cudaSuccess ||
+      cudaMemset(h->scal, 0, SLOT_COUNT * sizeof(double)) != cudaSuccess ||
+      cudaMemset(h->eta, 0, F.NX * sizeof(double)) != cudaSuccess)
+    return bail(fail(PMG_ERR_CUDA, "memset failed"));
+  if (cudaMallocHost(&h->scal_host, SLOT_COUNT * sizeof(double)) != cudaSuccess ||
+      cudaMallocHost(&h->status_host, 2 * sizeof(int)) != cudaSuccess)
+    return bail(fail(PMG_ERR_OOM, "pinned allocation failed"));
+  pmg_status s = pmg_set_geometry(h, h->eta, nullptr);
+  if (s != PMG_OK) return bail(s);
+  if (cudaDeviceSynchronize() != cudaSuccess) return bail(fail(PMG_ERR_CUDA, "setup failed"));
+  *out = h;
+  return PMG_OK;
+}
+
+pmg_status pmg_destroy(pmg_handle* h) {
+  if (!h) return PMG_OK;
+  DeviceGuard dg(h->device);
+  cudaDeviceSynchronize();
+  delete h;
+  return PMG_OK;
+}
+
+pmg_status pmg_num_nodes(const pmg_handle* h, int64_t* n, int64_t* n_free, int* nx, int* nz, int* nlevels) {
+  CKS(check_handle(h));
+  if (n) *n = (int64_t)h->N;
+  if (n_free) *n_free = (int64_t)h->Nfree;
+  if (nx) *nx = h->lv[0].s.NX;
+  if (nz) *nz = h->lv[0].s.NZ;
+  if (nlevels) *nlevels = (int)h->lv.size();
+  return PMG_OK;
+}
+
+pmg_status pmg_level_info(const pmg_handle* h, int level, int* order, int* nx, int* nz) {
+  CKS(check_handle(h));
+  if (level < 0 || level >= (int)h->lv.size()) return fail(PMG_ERR_INVALID, "bad level");
+  if (order) *order = h->lv[level].order;
+  if (nx) *nx = h->lv[level].s.NX;
+  if (nz) *nz = h->lv[level].s.NZ;
+  return PMG_OK;
+}
+
+pmg_status pmg_node_coords(const pmg_handle* h, double* xc, double* sr) {
+  CKS(check_handle(h));
+  if (xc) std::memcpy(xc, h->xcols.data(), h->xcols.size() * sizeof(double));
+  if (sr) std::memcpy(sr, h->sigrows.data(), h->sigrows.size() * sizeof(double));
+  return PMG_OK;
+}
+
+pmg_status pmg_set_geometry(pmg_handle* h, const double* eta_dev, void* stream) {
+  CKS(check_handle(h));
+  if (!eta_dev) return fail(PMG_ERR_INVALID, "eta is NULL");
+  DeviceGuard dg(h->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const Shape& F = h->lv[0].s;
+  if (eta_dev != h->eta) CK(cudaMemcpyAsync(h->eta, eta_dev, F.NX * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  int* gst = h->status + 1;
+  CK(cudaMemsetAsync(gst, 0, sizeof(int), st));
+  CK(geometry<double>(F, h->eta, h->mesh.h, h->dx, h->dsig, 0, (double*)h->geo[0], gst, st));
+  CK(geometry<float>(F, h->eta, h->mesh.h, h->dx, h->dsig, 0, (float*)h->geo[1], gst, st));
+  CK(geometry<double>(F, h->eta, h->mesh.h, h->dx, h->dsig, 1, h->geo_div, gst, st));
+  return PMG_OK;
+}
+
+pmg_status pmg_assemble_rhs(pmg_handle* h, const double* f, const double* gb, const double* gl,
+                            const double* gr, double* b, void* stream) {
+  CKS(check_handle(h));
+  if (!f || !b) return fail(PMG_ERR_INVALID, "f and b must be non-NULL");
+  DeviceGuard dg(h->device);
+  LevelDev& L = h->lv[0];
+  CK(rhs_source(L.s, h->eta, h->mesh.h, h->dx, h->dsig, (const double*)L.mX[0], (const double*)L.mZ[0], f, gb,
+                h->mesh.periodic_x ? nullptr : gl, h->mesh.periodic_x ? nullptr : gr, b, (cudaStream_t)stream));
+  return PMG_OK;
+}
+
+pmg_status pmg_assemble_rhs_div(pmg_handle* h, const double* u, const double* w, double scale, double* b,
+                                void* stream) {
+  CKS(check_handle(h));
+  if (!u || !w || !b) return fail(PMG_ERR_INVALID, "NULL vector");
+  DeviceGuard dg(h->device);
+  CurvedArgs a{};
+  a.s = h->lv[0].s;
+  a.mode = 3;
+  a.x = u;
+  a.x2 = w;
+  a.y = b;
+  a.geo = h->geo_div;
+  a.sigma = h->sigma[0];
+  a.scale = scale;
+  a.sc = h->sc;
+  CK(curved_op<double>(a, (cudaStream_t)stream));
+  return PMG_OK;
+}
+
+pmg_status pmg_apply(pmg_handle* h, const double* x, double* y, void* stream) {
+  CKS(check_handle(h));
+  if (!x || !y) return fail(PMG_ERR_INVALID, "NULL vector");
+  DeviceGuard dg(h->device);
+  return curved<double>(h, 0, x, nullptr, y, 1, nullptr, (cudaStream_t)stream);
+}
+
+pmg_status pmg_apply_f32(pmg_handle* h, const float* x, float* y, void* stream) {
+  CKS(check_handle(h));
+  if (!x || !y) return fail(PMG_ERR_INVALID, "NULL vector");
+  DeviceGuard dg(h->device);
+  return curved<float>(h, 0, x, nullptr, y, 1, nullptr, (cudaStream_t)stream);
+}
+
+pmg_status pmg_level_apply(pmg_handle* h, int level, const void* x, void* y, int f32, void* stream) {
+  CKS(check_handle(h));
+  if (level < 0 || level >= (int)h->lv.size() || !x || !y) return fail(PMG_ERR_INVALID, "bad level or vector");
+  DeviceGuard dg(h->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  return f32 ? level_residual<float>(h, level, nullptr, x, y, 0, st) : level_residual<double>(h, level, nullptr, x, y, 0, st);
+}
+
+pmg_status pmg_level_smooth(pmg_handle* h, int level, const void* b, void* x, int post, int f32, void* stream) {
+  CKS(check_handle(h));
+  if (level < 0 || level >= (int)h->lv.size() - 1 || !b || !x) return fail(PMG_ERR_INVALID, "bad level or vector");
+  DeviceGuard dg(h->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  return f32 ? level_smooth<float>(h, level, b, x, post, false, st) : level_smooth<double>(h, level, b, x, post, false, st);
+}
+
+pmg_status pmg_restrict(pmg_handle* h, int level, const void* rf, void* rc, int f32, void* stream) {
+  CKS(check_handle(h));
+  if (level < 0 || level >= (int)h->lv.size() - 1 || !rf || !rc) return fail(PMG_ERR_INVALID, "bad level or vector");
+  DeviceGuard dg(h->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  return f32 ? transfer_op<float>(h, level, rf, rc, 1, st) : transfer_op<double>(h, level, rf, rc, 1, st);
+}
+
+pmg_status pmg_prolong(pmg_handle* h, int level, const void* xc, void* xf, int f32, void* stream) {
+  CKS(check_handle(h));
+  if (level < 0 || level >= (int)h->lv.size() - 1 || !xc || !xf) return fail(PMG_ERR_INVALID, "bad level or vector");
+  DeviceGuard dg(h->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  return f32 ? transfer_op<float>(h, level, xc, xf, 0, st) : transfer_op<double>(h, level, xc, xf, 0, st);
+}
+
+pmg_status pmg_coarse_solve(pmg_handle* h, const double* b, double* x, void* stream) {
+  CKS(check_handle(h));
+  if (!b || !x) return fail(PMG_ERR_INVALID, "NULL vector");
+  DeviceGuard dg(h->device);
+  CK(coarse_solve<double>(h->coarse, b, x, (cudaStream_t)stream));
+  return PMG_OK;
+}
+
+pmg_status pmg_vcycle(pmg_handle* h, const void* r, void* z, int f32, void* stream) {
+  CKS(check_handle(h));
+  if (!r || !z) return fail(PMG_ERR_INVALID, "NULL vector");
+  DeviceGuard dg(h->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  return f32 ? vcycle<float>(h, 0, r, z, st) : vcycle<double>(h, 0, r, z, st);
+}
+
+pmg_status pmg_solve(pmg_handle* h, const double* b, const double* pD, const double* x0, double* p_out,
+                     pmg_solve_info* info, void* stream) {
+  CKS(check_handle(h));
+  if (!b || !pD || !p_out) return fail(PMG_ERR_INVALID, "b, p_dirichlet and p_out must be non-NULL");
+  DeviceGuard dg(h->device);
+  auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t st = (cudaStream_t)stream;
+  pmg_solve_info loc{};
+  size_t N = h->N;
+  CK(cudaMemsetAsync(h->status, 0, sizeof(int), st));
+  CK(check_finite(N, b, h->status, st));
+  CK(init_x(N, h->lv[0].s.NZ, h->x, x0, pD, h->status, st));
+  CKS(lifted_norm(h, b, pD, x0, st));
+  CKS(read_scalars(h, st));
+  pmg_status result = PMG_OK;
+  double bb = h->scal_host[SLOT_BB];
+  if (h->status_host[1]) {
+    result = fail(PMG_ERR_INVALID, "geometry has a non-positive or non-finite water depth");
+  } else if (h->status_host[0]) {
+    result = fail(PMG_ERR_NONFINITE, "non-finite input (b, p_D or x0)");
+  } else if (!std::isfinite(bb)) {
+    result = fail(PMG_ERR_NONFINITE, "non-finite right-hand side");
+  } else if (bb > 0.0) {
+    pmg_status s;
+    if (h->opts.outer == PMG_PDC) s = solve_pdc(h, b, &loc, st);
+    else if (h->opts.precision == PMG_FP64) s = solve_krylov64(h, b, &loc, st);
+    else s = solve_refine(h, b, &loc, st);
+    if (s != PMG_OK) result = s;
+    // final true residual
+    CKS(outer_residual(h, b, SLOT_RR64, st));
+    CKS(read_scalars(h, st));
+    double rel = std::sqrt(h->scal_host[SLOT_RR64] / bb);
+    loc.rel_residual = rel;
+    if (result == PMG_OK && !(rel <= h->opts.tol)) {
+      result = std::isfinite(rel) ? PMG_ERR_NOT_CONVERGED : PMG_ERR_NONFINITE;
+      fail(result, "solve did not reach the tolerance");
+    }
+  }
+  CK(cudaMemcpyAsync(p_out, h->x, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  loc.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  loc.status = result;
+  if (info) *info = loc;
+  return result;
+}
+
+pmg_status pmg_solve_host(pmg_handle* h, const double* b, const double* pD, const double* x0, double* p_out,
+                          pmg_solve_info* info, void* stream) {
+  CKS(check_handle(h));
+  if (!b || !pD || !p_out) return fail(PMG_ERR_INVALID, "b, p_dirichlet and p_out must be non-NULL");
+  DeviceGuard dg(h->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  size_t N = h->N;
+  if (!h->io) {
+    cudaError_t e;
+    h->io = h->alloc<double>(4 * N, e);
+    if (e != cudaSuccess) { h->io = nullptr; return fail(PMG_ERR_OOM, "device allocation failed"); }
+  }
+  double *dout = h->io, *db = h->io + N, *dpd = h->io + 2 * N, *dx0 = h->io + 3 * N;
+  CK(cudaMemcpyAsync(db, b, N * sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(dpd, pD, N * sizeof(double), cudaMemcpyHostToDevice, st));
+  if (x0) CK(cudaMemcpyAsync(dx0, x0, N * sizeof(double), cudaMemcpyHostToDevice, st));
+  pmg_status s = pmg_solve(h, db, dpd, x0 ? dx0 : nullptr, dout, info, stream);
+  CK(cudaMemcpyAsync(p_out, dout, N * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return s;
+}
+
+}  // extern "C"

@@ -1,0 +1,257 @@
+"""ctypes binding of the C ABI in include/pmg.h (argument marshalling only).
+
+Device vectors are torch CUDA tensors (float64 unless a call says float32); every call
+runs on torch's current CUDA stream.  Errors raise PmgError with the library's message.
+"""
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+PMG_OK, PMG_ERR_INVALID, PMG_ERR_OOM, PMG_ERR_CUDA = 0, 1, 2, 3
+PMG_ERR_NOT_CONVERGED, PMG_ERR_NONFINITE, PMG_ERR_TIMEOUT = 4, 5, 6
+PMG_FP64, PMG_MIXED_FP32, PMG_MIXED_BF16 = 0, 1, 2
+PMG_PCG, PMG_FCG, PMG_PDC = 0, 1, 2
+PMG_ASM_FDM = 0
+PMG_FLAT_LINEARISED = 1
+
+STATUS_NAMES = {0: "PMG_OK", 1: "PMG_ERR_INVALID", 2: "PMG_ERR_OOM", 3: "PMG_ERR_CUDA",
+                4: "PMG_ERR_NOT_CONVERGED", 5: "PMG_ERR_NONFINITE", 6: "PMG_ERR_TIMEOUT"}
+
+
+class PmgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class MeshDesc(ctypes.Structure):
+    _fields_ = [("x0", ctypes.c_double), ("x1", ctypes.c_double), ("h", ctypes.c_double),
+                ("cells_x", ctypes.c_int), ("cells_z", ctypes.c_int), ("order", ctypes.c_int),
+                ("periodic_x", ctypes.c_int)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("outer", ctypes.c_int), ("smoother", ctypes.c_int),
+                ("precond_geom", ctypes.c_int), ("overlap", ctypes.c_int), ("nu", ctypes.c_int),
+                ("omega", ctypes.c_double), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
+                ("inner_max", ctypes.c_int), ("inner_tol", ctypes.c_double), ("nlevels", ctypes.c_int),
+                ("level_orders", ctypes.c_int * 8)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("inner_iterations", ctypes.c_int),
+                ("rel_residual", ctypes.c_double), ("seconds", ctypes.c_double), ("status", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_P, _I, _D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+_SIGNATURES = {
+    "pmg_default_opts": (None, [ctypes.POINTER(Opts)]),
+    "pmg_create": (_I, [ctypes.POINTER(MeshDesc), ctypes.POINTER(Opts), ctypes.POINTER(_P)]),
+    "pmg_destroy": (_I, [_P]),
+    "pmg_num_nodes": (_I, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                           ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "pmg_level_info": (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "pmg_node_coords": (_I, [_P, _P, _P]),
+    "pmg_set_geometry": (_I, [_P, _P, _P]),
+    "pmg_assemble_rhs": (_I, [_P, _P, _P, _P, _P, _P, _P]),
+    "pmg_assemble_rhs_div": (_I, [_P, _P, _P, _D, _P, _P]),
+    "pmg_solve": (_I, [_P, _P, _P, _P, _P, ctypes.POINTER(SolveInfo), _P]),
+    "pmg_solve_host": (_I, [_P, _P, _P, _P, _P, ctypes.POINTER(SolveInfo), _P]),
+    "pmg_apply": (_I, [_P, _P, _P, _P]),
+    "pmg_apply_f32": (_I, [_P, _P, _P, _P]),
+    "pmg_level_apply": (_I, [_P, _I, _P, _P, _I, _P]),
+    "pmg_level_smooth": (_I, [_P, _I, _P, _P, _I, _I, _P]),
+    "pmg_restrict": (_I, [_P, _I, _P, _P, _I, _P]),
+    "pmg_prolong": (_I, [_P, _I, _P, _P, _I, _P]),
+    "pmg_coarse_solve": (_I, [_P, _P, _P, _P]),
+    "pmg_vcycle": (_I, [_P, _P, _P, _I, _P]),
+    "pmg_last_error": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(build_if_missing=False):
+    """Load libpmg.so (raises if absent: the product path has no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"native library {path} is missing: run __graft_entry__.build()")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(st):
+    if st != PMG_OK:
+        raise PmgError(st, _lib.pmg_last_error().decode())
+
+
+def _ptr(t, dtype=torch.float64):
+    if t is None:
+        return None
+    if not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"expected a contiguous CUDA {dtype} tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def default_opts(**kw):
+    lib = load()
+    o = Opts()
+    lib.pmg_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "level_orders":
+            o.nlevels = len(v)
+            for i, p in enumerate(v):
+                o.level_orders[i] = p
+        else:
+            setattr(o, k, v)
+    return o
+
+
+class Solver:
+    """One mesh + multigrid hierarchy on the current CUDA device (pmg_create)."""
+
+    def __init__(self, cells_x, cells_z, order, x0=0.0, x1=1.0, h=1.0, periodic=False, **opts):
+        lib = load()
+        self.mesh = MeshDesc(x0, x1, h, cells_x, cells_z, order, int(bool(periodic)))
+        self.opts = default_opts(**opts)
+        hh = ctypes.c_void_p()
+        _check(lib.pmg_create(ctypes.byref(self.mesh), ctypes.byref(self.opts), ctypes.byref(hh)))
+        self._h = hh
+        n, nf = ctypes.c_int64(), ctypes.c_int64()
+        nx, nz, nl = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib.pmg_num_nodes(self._h, ctypes.byref(n), ctypes.byref(nf), ctypes.byref(nx),
+                                 ctypes.byref(nz), ctypes.byref(nl)))
+        self.n, self.n_free, self.NX, self.NZ, self.nlevels = n.value, nf.value, nx.value, nz.value, nl.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().pmg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- sizes and coordinates
+    def level_info(self, level):
+        p, nx, nz = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(load().pmg_level_info(self._h, level, ctypes.byref(p), ctypes.byref(nx), ctypes.byref(nz)))
+        return p.value, nx.value, nz.value
+
+    def node_coords(self):
+        xc = torch.empty(self.NX, dtype=torch.float64)
+        sr = torch.empty(self.NZ, dtype=torch.float64)
+        _check(load().pmg_node_coords(self._h, ctypes.c_void_p(xc.data_ptr()), ctypes.c_void_p(sr.data_ptr())))
+        return xc.numpy(), sr.numpy()
+
+    # ---- per-stage inputs
+    def set_geometry(self, eta):
+        _check(load().pmg_set_geometry(self._h, _ptr(eta), _stream()))
+
+    def assemble_rhs(self, f, g_bottom=None, g_left=None, g_right=None, out=None):
+        out = torch.empty(self.n, dtype=torch.float64, device=f.device) if out is None else out
+        _check(load().pmg_assemble_rhs(self._h, _ptr(f), _ptr(g_bottom), _ptr(g_left), _ptr(g_right),
+                                       _ptr(out), _stream()))
+        return out
+
+    def assemble_rhs_div(self, u, w, scale=1.0, out=None):
+        out = torch.empty(self.n, dtype=torch.float64, device=u.device) if out is None else out
+        _check(load().pmg_assemble_rhs_div(self._h, _ptr(u), _ptr(w), float(scale), _ptr(out), _stream()))
+        return out
+
+    # ---- solve
+    def solve(self, b, p_dirichlet, x0=None, out=None, raise_on_error=True):
+        out = torch.empty(self.n, dtype=torch.float64, device=b.device) if out is None else out
+        info = SolveInfo()
+        st = load().pmg_solve(self._h, _ptr(b), _ptr(p_dirichlet), _ptr(x0), _ptr(out), ctypes.byref(info),
+                              _stream())
+        if raise_on_error and st not in (PMG_OK,):
+            _check(st)
+        return out, info.as_dict()
+
+    def solve_host(self, b, p_dirichlet, x0=None, out=None, raise_on_error=True):
+        """Host (CPU float64) buffers in and out; copies are part of the call."""
+        def hp(t):
+            if t is None:
+                return None
+            if t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+                raise ValueError("expected contiguous CPU float64 tensors")
+            return ctypes.c_void_p(t.data_ptr())
+        out = torch.empty(self.n, dtype=torch.float64, pin_memory=True) if out is None else out
+        info = SolveInfo()
+        st = load().pmg_solve_host(self._h, hp(b), hp(p_dirichlet), hp(x0), hp(out), ctypes.byref(info),
+                                   _stream())
+        if raise_on_error and st != PMG_OK:
+            _check(st)
+        return out, info.as_dict()
+
+    # ---- components
+    def apply(self, x, out=None):
+        out = torch.empty_like(x) if out is None else out
+        _check(load().pmg_apply(self._h, _ptr(x), _ptr(out), _stream()))
+        return out
+
+    def apply_f32(self, x, out=None):
+        out = torch.empty_like(x) if out is None else out
+        _check(load().pmg_apply_f32(self._h, _ptr(x, torch.float32), _ptr(out, torch.float32), _stream()))
+        return out
+
+    @staticmethod
+    def _f32(t):
+        return 1 if t.dtype == torch.float32 else 0
+
+    def level_apply(self, level, x, out=None):
+        out = torch.empty_like(x) if out is None else out
+        _check(load().pmg_level_apply(self._h, level, _ptr(x, x.dtype), _ptr(out, x.dtype), self._f32(x), _stream()))
+        return out
+
+    def level_smooth(self, level, b, x, post=False):
+        _check(load().pmg_level_smooth(self._h, level, _ptr(b, b.dtype), _ptr(x, b.dtype), int(post),
+                                       self._f32(b), _stream()))
+        return x
+
+    def restrict(self, level, rf, out):
+        _check(load().pmg_restrict(self._h, level, _ptr(rf, rf.dtype), _ptr(out, rf.dtype), self._f32(rf),
+                                   _stream()))
+        return out
+
+    def prolong(self, level, xc, xf):
+        _check(load().pmg_prolong(self._h, level, _ptr(xc, xc.dtype), _ptr(xf, xc.dtype), self._f32(xc),
+                                  _stream()))
+        return xf
+
+    def coarse_solve(self, b, out=None):
+        out = torch.empty_like(b) if out is None else out
+        _check(load().pmg_coarse_solve(self._h, _ptr(b), _ptr(out), _stream()))
+        return out
+
+    def vcycle(self, r, out=None):
+        out = torch.empty_like(r) if out is None else out
+        _check(load().pmg_vcycle(self._h, _ptr(r, r.dtype), _ptr(out, r.dtype), self._f32(r), _stream()))
+        return out

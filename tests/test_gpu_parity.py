@@ -1,0 +1,228 @@
+"""GPU parity: every kernel of the hot path, called through the C ABI, against the CPU
+oracle on the same seeded inputs (element by element), plus full solves and error paths.
+
+Tolerances: FP64 kernels agree with the oracle to rounding, bounded here by
+1e-12 * max_i (|A| |x|)_i for operator applications (the scale of the summands); FP32
+kernels by 2e-5 of the same scale (unit roundoff 6e-8 times the sum-factorised
+contraction depth).  Solves: relative L2 error against the oracle's direct solve
+<= 1e-10 with the GPU solved to a residual of 1e-12.
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_2411_14977_gb300.pmg as pmg
+import workloads as W
+from oracle import mg
+from oracle.sem import apply_masked, relative_residual, solve_direct
+from tests.gpu_helpers import Case, n, t
+
+pytestmark = pytest.mark.gpu
+
+
+def periodic_tank(cells_x=8, cells_z=3, order=5):
+    L = 0.390625 * cells_x
+    s = W.Surface(0.04, 2 * np.pi / L)
+    return W.Workload(f"periodic_{cells_x}x{cells_z}_p{order}", cells_x, cells_z, order, 0.0, L, 1.0, True,
+                      W.BASE_SEED + 77, s, "div", velocity=W.Velocity.random(W.BASE_SEED + 78))
+
+
+CASES = {
+    "tank12x3p6": lambda: W.tank(12, 3, 6),
+    "cfg1": lambda: W.config1(),
+    "periodic8x3p5": lambda: periodic_tank(),
+    "tank6x2p8": lambda: W.tank(6, 2, 8),
+    "tank5x1p4_nz1": lambda: W.tank(5, 1, 4),
+    "tank1x2p5_nx1": lambda: W.tank(1, 2, 5),
+    "tank2x2p3": lambda: W.tank(2, 2, 3),
+    "tank4x2p10": lambda: W.tank(4, 2, 10),
+    "tank7x3p2": lambda: W.tank(7, 3, 2),
+}
+_cache = {}
+
+
+def case(name):
+    if name not in _cache:
+        _cache[name] = Case(CASES[name]())
+    return _cache[name]
+
+
+def scale_of(A, x):
+    return np.max(np.abs(A) @ np.abs(x))
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_apply_fp64_and_fp32(name):
+    c = case(name)
+    A = c.m.assemble(c.eta)
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal(c.m.N)
+    ref = apply_masked(A, x, c.m.dirichlet_mask())
+    s = scale_of(A, np.where(c.m.dirichlet_mask(), 0, x))
+    y = n(c.S.apply(t(x)))
+    assert np.max(np.abs(y - ref)) <= 1e-12 * s
+    y32 = n(c.S.apply_f32(t(x, torch.float32)))
+    assert np.max(np.abs(y32 - ref)) <= 2e-5 * s
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_rhs_assembly(name):
+    c = case(name)
+    ref = c.rhs_oracle()
+    b = n(c.rhs_gpu())
+    assert np.max(np.abs(b - ref)) <= 1e-12 * max(1.0, np.max(np.abs(ref)))
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_level_operators_and_transfers(name):
+    c = case(name)
+    H = c.hierarchy()
+    rng = np.random.default_rng(2)
+    for l, lev in enumerate(H.levels):
+        N = lev.mesh.N
+        x = rng.standard_normal(N)
+        x[lev.dmask] = 0.0
+        ref = np.zeros(N)
+        ref[lev.free] = lev.A @ x[lev.free]
+        s = np.max(np.abs(lev.A) @ np.abs(x[lev.free]))
+        for dt, tol in ((torch.float64, 1e-12), (torch.float32, 2e-5)):
+            y = n(c.S.level_apply(l, t(x, dt)))
+            assert np.max(np.abs(y[lev.free] - ref[lev.free])) <= tol * s, (l, dt)
+        if l == len(H.levels) - 1:
+            continue
+        # transfers
+        C = H.levels[l + 1]
+        rf = rng.standard_normal(N)
+        rf[lev.dmask] = 0.0
+        rc_ref = np.zeros(C.mesh.N)
+        rc_ref[C.free] = H.P[l].T @ rf[lev.free]
+        xc = rng.standard_normal(C.mesh.N)
+        xc[C.dmask] = 0.0
+        xf0 = rng.standard_normal(N)
+        xf0[lev.dmask] = 0.0
+        xf_ref = xf0.copy()
+        xf_ref[lev.free] += H.P[l] @ xc[C.free]
+        for dt, tol in ((torch.float64, 1e-13), (torch.float32, 1e-5)):
+            rc = n(c.S.restrict(l, t(rf, dt), torch.zeros(C.mesh.N, dtype=dt, device="cuda")))
+            assert np.max(np.abs(rc - rc_ref)) <= tol * max(1.0, np.max(np.abs(rc_ref))), (l, dt)
+            xf = n(c.S.prolong(l, t(xc, dt), t(xf0, dt)))
+            assert np.max(np.abs(xf - xf_ref)) <= tol * max(1.0, np.max(np.abs(xf_ref))), (l, dt)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_smoother(name):
+    c = case(name)
+    H = c.hierarchy()
+    rng = np.random.default_rng(3)
+    for l, lev in enumerate(H.levels[:-1]):
+        N = lev.mesh.N
+        b = rng.standard_normal(N)
+        b[lev.dmask] = 0.0
+        x0 = rng.standard_normal(N)
+        x0[lev.dmask] = 0.0
+        for post in (False, True):
+            ref = np.zeros(N)
+            ref[lev.free] = H.smooth(l, b[lev.free], x0[lev.free], post)
+            sc = max(1.0, np.max(np.abs(ref)))
+            for dt, tol in ((torch.float64, 1e-11), (torch.float32, 1e-4)):
+                x = c.S.level_smooth(l, t(b, dt), t(x0, dt), post)
+                assert np.max(np.abs(n(x) - ref)) <= tol * sc, (l, post, dt)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_coarse_solve_and_vcycle(name):
+    c = case(name)
+    H = c.hierarchy()
+    rng = np.random.default_rng(4)
+    C = H.levels[-1]
+    b = rng.standard_normal(C.mesh.N)
+    b[C.dmask] = 0.0
+    ref = np.zeros(C.mesh.N)
+    ref[C.free] = H.coarse_lu.solve(b[C.free])
+    x = n(c.S.coarse_solve(t(b)))
+    assert np.max(np.abs(x - ref)) <= 1e-11 * np.max(np.abs(ref))
+    F = H.levels[0]
+    r = rng.standard_normal(F.mesh.N)
+    r[F.dmask] = 0.0
+    zref = np.zeros(F.mesh.N)
+    zref[F.free] = H.vcycle(r[F.free])
+    z = n(c.S.vcycle(t(r)))
+    assert np.max(np.abs(z - zref)) <= 1e-10 * np.max(np.abs(zref))
+    z32 = n(c.S.vcycle(t(r, torch.float32)))
+    assert np.max(np.abs(z32 - zref)) <= 1e-4 * np.max(np.abs(zref))
+
+
+SOLVE_CASES = ["tank12x3p6", "cfg1", "periodic8x3p5", "tank6x2p8", "tank5x1p4_nz1", "tank1x2p5_nx1",
+               "tank4x2p10", "tank7x3p2"]
+
+
+@pytest.mark.parametrize("name", SOLVE_CASES)
+@pytest.mark.parametrize("variant", [dict(), dict(outer=pmg.PMG_FCG), dict(outer=pmg.PMG_PDC),
+                                     dict(precision=pmg.PMG_MIXED_FP32),
+                                     dict(precision=pmg.PMG_MIXED_FP32, outer=pmg.PMG_PDC)])
+def test_solve_matches_direct(name, variant):
+    w = CASES[name]()
+    c = Case(w, tol=1e-12, **variant)
+    bo = c.rhs_oracle()
+    A = c.m.assemble(c.eta)
+    dm = c.m.dirichlet_mask()
+    pref = solve_direct(A, bo, c.F["pD"], dm)
+    if variant.get("outer") == pmg.PMG_PDC:
+        # defect correction converges only where the V-cycle is a contraction, ||I - BA|| < 1
+        _, its, hist, _ = mg.solve(c.m, c.eta, bo, c.F["pD"], method="pdc", tol=1e-12, maxit=500,
+                                   overlap=1, nu=2, omega=0.8)
+        if not hist[-1] <= 1e-12:
+            p, info = c.S.solve(c.rhs_gpu(), t(c.F["pD"]), raise_on_error=False)
+            assert info["status"] in (pmg.PMG_ERR_NOT_CONVERGED, pmg.PMG_ERR_NONFINITE)
+            return
+    b = c.rhs_gpu()
+    p, info = c.S.solve(b, t(c.F["pD"]))
+    p = n(p)
+    err = np.linalg.norm(p - pref) / np.linalg.norm(pref)
+    assert err <= 1e-10, (err, info)
+    assert info["rel_residual"] <= 1e-12
+    assert relative_residual(A, bo, p, dm) <= 2e-12
+    np.testing.assert_array_equal(p[dm], c.F["pD"][dm])
+    if not variant:
+        # FP64 PCG: same iteration count as the oracle's PCG with the same V-cycle (+-1)
+        _, its, _, _ = mg.solve(c.m, c.eta, bo, c.F["pD"], tol=1e-12, overlap=1, nu=2, omega=0.8)
+        assert abs(info["iterations"] - its) <= 1, (info["iterations"], its)
+
+
+def test_warm_start_exact_and_host_path():
+    c = Case(W.tank(12, 3, 6), tol=1e-10)
+    b = c.rhs_gpu()
+    pD = t(c.F["pD"])
+    p, info = c.S.solve(b, pD)
+    p2, info2 = c.S.solve(b, pD, x0=p)
+    assert info2["iterations"] == 0 and info2["rel_residual"] <= 1e-10
+    ph, infoh = c.S.solve_host(b.cpu(), pD.cpu())
+    assert torch.equal(ph, p.cpu())
+    assert infoh["iterations"] == info["iterations"]
+
+
+def test_nonfinite_and_not_converged():
+    c = Case(W.tank(6, 2, 4), tol=1e-12, max_iter=1)
+    b = c.rhs_gpu()
+    pD = t(c.F["pD"])
+    p, info = c.S.solve(b, pD, raise_on_error=False)
+    assert info["status"] == pmg.PMG_ERR_NOT_CONVERGED and info["iterations"] == 1
+    assert 0 < info["rel_residual"] < 1
+    b2 = b.clone()
+    b2[5] = float("nan")
+    with pytest.raises(pmg.PmgError) as e:
+        c.S.solve(b2, pD)
+    assert e.value.status == pmg.PMG_ERR_NONFINITE
+    # the handle stays usable after both failures
+    c2 = Case(W.tank(6, 2, 4), tol=1e-10)
+    p, info = c2.S.solve(c2.rhs_gpu(), t(c2.F["pD"]))
+    assert info["status"] == 0
+
+
+def test_bad_geometry_rejected():
+    c = Case(W.tank(6, 2, 4))
+    eta = t(np.full(c.S.NX, -2.0))
+    c.S.set_geometry(eta)
+    with pytest.raises(pmg.PmgError) as e:
+        c.S.solve(c.rhs_gpu(), t(c.F["pD"]))
+    assert e.value.status == pmg.PMG_ERR_INVALID

@@ -1,0 +1,363 @@
+#!/usr/bin/env python
+"""Throughput of the p-multigrid-preconditioned pressure-Poisson solve on GB300.
+
+One step = one Runge-Kutta-stage pressure solve of the synthetic sigma-mapped wave tank
+(512 x 32 quads on [0, 200] x [-1, eta], P = 6, curved surface, divergence right-hand
+side): set the stage geometry, assemble the weak divergence, solve to a relative residual
+of 1e-10.  Inputs are resident in HBM; L2 is flushed (256 MiB write) between steps.
+
+Prints one JSON line (rank 0):
+  value      free DOF x steps / device time, all ranks (replicas) together
+  plain_fp64 the same steps with the plain FP64 p-multigrid (the comparison the target is
+             stated against), speedup_vs_plain_fp64 the ratio
+  roofline   the dominant kernel class of a profiled step: algorithmic bytes (or FP64
+             flops) / CUDA-event device time against the measured peak
+  e2e        the same metric with the inputs copied from pinned host memory and the
+             pressure copied back inside the timed region
+  cpu_baseline  the FP64 CPU oracle on a bounded slice of the same tank
+
+--impl reference times the oracle (the CPU reference implementation of this method).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "Poisson solves/s x free DOF (DOF/s) to rel. residual 1e-10"
+UNIT = "DOF/s"
+FP64_PEAK_GFLOPS = 1250.0   # GB300 FP64 (vector and tensor), nominal
+L2_FLUSH_BYTES = 256 << 20
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg3"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ncu-step", action="store_true",
+                    help="profiling aid: one warm step, then one step inside the NVTX range 'profiled_step'")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(name):
+    import workloads as W
+    return W.config2() if name == "cfg2" else W.config3()
+
+
+def oracle_slice():
+    """A 32 x 32-cell, P = 6 slice of the config-2 tank (same cell size, depth
+    resolution and generator seed)."""
+    import workloads as W
+    return W.tank(32, 32, 6, seed=W.BASE_SEED + 2)
+
+
+def oracle_solve_timed(w, hier=None):
+    """FP64 oracle p-MG-PCG solve to 1e-10 (operator assembly + PCG; the multigrid
+    hierarchy is setup, excluded).  Returns (wall s, cpu s, free DOF, iterations, hier)."""
+    from oracle import mg
+    from oracle.sem import Mesh
+    m = Mesh(**w.mesh_kwargs())
+    F = w.fields(m.column_x(), m.row_sigma())
+    b = m.rhs_divergence(F["eta"], F["u"], F["w"])
+    if hier is None:
+        hier = mg.Hierarchy(m, F["eta"], overlap=1, nu=2, omega=0.8)
+    t0, c0 = time.perf_counter(), time.process_time()
+    _, its, hist, _ = mg.solve(m, F["eta"], b, F["pD"], hier=hier, tol=1e-10)
+    t1, c1 = time.perf_counter(), time.process_time()
+    assert hist[-1] <= 1e-10
+    return t1 - t0, c1 - c0, int((~m.dirichlet_mask()).sum()), its, hier
+
+
+def cpu_baseline_entry():
+    w = oracle_slice()
+    wall, cpu, nfree, its, _ = oracle_solve_timed(w)
+    return {"value": nfree / wall, "unit": UNIT, "cores": round(cpu / wall, 1), "kind": "oracle",
+            "sample": f"one FP64 oracle p-MG-PCG solve to 1e-10 (assembly + PCG, setup excluded) of the "
+                      f"32x32-cell P=6 slice of the tank ({nfree} free DOF, {its} iterations, {wall:.1f} s)"}
+
+
+# ------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.path = None
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# ------------------------------------------------------------------------------------
+def run_ours(args, ws, rank, local):
+    import torch
+    import paper_2411_14977_gb300.pmg as pmg
+
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pmg.load(build_if_missing=True)
+    w = workload(args.workload)
+
+    def setup(**opts):
+        S = pmg.Solver(**w.mesh_kwargs(), **opts)
+        xc, sr = S.node_coords()
+        F = w.fields(xc, sr)
+        host = {k: torch.from_numpy(np.ascontiguousarray(F[k])).pin_memory() for k in ("eta", "u", "w", "pD")}
+        devt = {k: v.to(dev) for k, v in host.items()}
+        bufs = {"b": torch.empty(S.n, dtype=torch.float64, device=dev),
+                "p": torch.empty(S.n, dtype=torch.float64, device=dev)}
+        return S, host, devt, bufs
+
+    def step(S, d, bufs):
+        S.set_geometry(d["eta"])
+        S.assemble_rhs_div(d["u"], d["w"], out=bufs["b"])
+        _, info = S.solve(bufs["b"], d["pD"], out=bufs["p"])
+        return info
+
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def timed(S, d, bufs, K, e2e=None):
+        """Per-step CUDA-event device times (L2 flushed before each step, outside the events)."""
+        evs, infos = [], []
+        st = torch.cuda.current_stream()
+        for _ in range(K):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            if e2e is None:
+                infos.append(step(S, d, bufs))
+            else:
+                host, pout = e2e
+                for k in d:
+                    d[k].copy_(host[k], non_blocking=True)
+                infos.append(step(S, d, bufs))
+                pout.copy_(bufs["p"], non_blocking=True)
+            e1.record(st)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs) / 1e3, infos
+
+    def all_max(x):
+        if ws == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---- headline: mixed precision (FP32 V-cycle inside FP64 refinement)
+    S, host, d, bufs = setup(precision=pmg.PMG_MIXED_FP32)
+    if args.ncu_step:
+        step(S, d, bufs)
+        # eager launches (the kernel-timing path): ncu does not profile kernel nodes of
+        # graphs that hold conditional nodes; the kernels and their order are the same
+        S.profile_reset(timing=True)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("profiled_step")
+        info = step(S, d, bufs)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        log("ncu step:", info)
+        return
+    for _ in range(max(args.warmup, 3)):
+        step(S, d, bufs)
+    barrier()
+    S.profile_reset(timing=False)
+    clk = ClockSampler(local)
+    barrier()
+    t_dev, infos = timed(S, d, bufs, args.steps)
+    barrier()
+    clocks = clk.stop()
+    prof = S.profile_read(full=True)
+    launches = int(sum(v[0] for v in prof.values()))
+    t_dev = all_max(t_dev)
+    K = args.steps
+    value = ws * S.n_free * K / t_dev
+    for inf in infos:
+        assert inf["status"] == 0 and inf["rel_residual"] <= 1e-10, inf
+
+    # ---- profiled step (CUDA-event pairs around every launch): per-class device time
+    S.profile_reset(timing=True)
+    flush.fill_(1.0)
+    step(S, d, bufs)
+    pclass = S.profile_read(full=True)
+    S.profile_reset(timing=False)
+    dom = max(pclass, key=lambda k: pclass[k][1])
+    n_l, ms_l, by_l, fl_l = pclass[dom]
+    peaks = measured_peaks()
+    if dom.endswith("64") and dom != "coarse":
+        achieved = fl_l / (ms_l / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
+                "frac": achieved / (FP64_PEAK_GFLOPS / 1e3), "traffic": None}
+    else:
+        peak = peaks.get("hbm_gbs", 6800.0)
+        achieved = by_l / (ms_l / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None}
+    roof.update({"kernel_class": dom, "launches": n_l, "avg_launch_us": 1e3 * ms_l / n_l,
+                 "algorithmic_bytes_per_launch": by_l / n_l, "algorithmic_flops_per_launch": fl_l / n_l,
+                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if roof["bound"] == "hbm"
+                 else "nominal GB300 FP64 1.25 TFLOP/s (1.21 measured)"})
+    shares = {k: round(v[1] / sum(x[1] for x in pclass.values()), 4) for k, v in pclass.items() if v[0]}
+
+    # ---- plain FP64 p-multigrid on the same steps
+    S64, _, d64, b64 = setup(precision=pmg.PMG_FP64)
+    for _ in range(2):
+        step(S64, d64, b64)
+    barrier()
+    K64 = max(3, K // 4)
+    t64, inf64 = timed(S64, d64, b64, K64)
+    barrier()
+    t64 = all_max(t64)
+    v64 = ws * S64.n_free * K64 / t64
+
+    # ---- end to end: pinned host inputs in, pressure out, inside the timed region
+    pout = torch.empty(S.n, dtype=torch.float64).pin_memory()
+    barrier()
+    te, _ = timed(S, d, bufs, K, e2e=(host, pout))
+    barrier()
+    te = all_max(te)
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": max(args.warmup, 3),
+        "ms_per_step": 1e3 * t_dev / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": w.name + " (512x32 quads, P=6, curved sigma-mapped tank, divergence RHS)"
+                   if args.workload == "cfg2" else w.name,
+                   "nodes": S.n, "free_dof": S.n_free, "levels": [S.level_info(l)[0] for l in range(S.nlevels)],
+                   "precision": "FP32 V-cycle + FP32 inner flexible CG inside FP64 iterative refinement; FP64 coarse",
+                   "smoother": "additive Schwarz (element + 1 overlap line, fast diagonalisation), nu=2, omega=0.8",
+                   "tol": 1e-10, "l2": "flushed between steps (256 MiB write, outside the timed events)",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                   "iterations": {"refinement": infos[-1]["iterations"], "inner": infos[-1]["inner_iterations"]}},
+        "solves_per_s": ws * K / t_dev,
+        "plain_fp64": {"value": v64, "unit": UNIT, "ms_per_step": 1e3 * t64 / K64, "steps": K64,
+                       "iterations": inf64[-1]["iterations"]},
+        "speedup_vs_plain_fp64": value / v64,
+        "roofline": roof,
+        "kernel_time_shares": shares,
+        "gpu_launches": launches,
+        "e2e": {"value": ws * S.n_free * K / te, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": S.n * 8},
+        "clocks": clocks,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_entry()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    w = oracle_slice()
+    hier = None
+    for _ in range(args.warmup):
+        _, _, _, _, hier = oracle_solve_timed(w, hier)
+    walls, cpus, nfree, its = [], [], 0, 0
+    for _ in range(args.steps):
+        wall, cpu, nfree, its, hier = oracle_solve_timed(w, hier)
+        walls.append(wall)
+        cpus.append(cpu)
+    t = sum(walls)
+    value = nfree * args.steps / t
+    sample = (f"each step: one FP64 oracle p-MG-PCG solve to 1e-10 (assembly + PCG, setup excluded) of the "
+              f"32x32-cell P=6 slice of the tank ({nfree} free DOF, {its} iterations)")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "cfg2_p6_512x32 tank family, 32x32-cell slice (oracle on host cores)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": round(sum(cpus) / t, 1), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

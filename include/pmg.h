@@ -167,6 +167,30 @@ pmg_status pmg_coarse_solve(pmg_handle* h, const double* b_dev, double* x_dev, v
 /* z = B r: one V-cycle of the preconditioner on the finest level (Sec. 5). */
 pmg_status pmg_vcycle(pmg_handle* h, const void* r_dev, void* z_dev, int f32, void* stream);
 
+/* ---- profiling ---------------------------------------------------------------------- */
+/* Kernel classes for launch counting and device timing. */
+enum {
+  PMG_K_CURVED64 = 0,  /* actual-geometry operator, FP64 (apply / residual / dot)          */
+  PMG_K_CURVED32 = 1,  /* actual-geometry operator, FP32                                    */
+  PMG_K_LEVEL64 = 2,   /* flat level operator / residual, FP64                              */
+  PMG_K_LEVEL32 = 3,   /* flat level operator / residual, FP32                              */
+  PMG_K_SMOOTH64 = 4,  /* Schwarz smoother sweep, FP64                                      */
+  PMG_K_SMOOTH32 = 5,  /* Schwarz smoother sweep, FP32                                      */
+  PMG_K_TRANSFER = 6,  /* restriction and prolongation (both precisions)                    */
+  PMG_K_COARSE = 7,    /* coarse solve (three launches per call)                            */
+  PMG_K_VECTOR = 8,    /* Krylov vector kernels and reductions                              */
+  PMG_K_SETUP = 9,     /* geometry factors and load vectors                                 */
+  PMG_K_COUNT = 10
+};
+/* Reset the per-class counters of h; timing != 0 also brackets every launch with CUDA
+ * events on its stream (adds a small per-launch cost). */
+pmg_status pmg_profile_reset(pmg_handle* h, int timing);
+/* Per class since the last reset (host arrays of PMG_K_COUNT, any may be NULL): launch
+ * counts, device milliseconds (zero unless timing was enabled), and the algorithmic bytes
+ * and floating-point operations of those launches (the minimum DRAM traffic and work the
+ * kernels' definitions imply; an FMA counts two).  Synchronises the device. */
+pmg_status pmg_profile_read(pmg_handle* h, int64_t* launches, double* ms, double* bytes, double* flops);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char* pmg_last_error(void);
 

@@ -288,7 +288,8 @@ template <int P, typename T, int MODE>
 static cudaError_t launch_curved_p(const CurvedParams<T>& prm, cudaStream_t st) {
   size_t sm = curved_smem<T>(P, prm.s.NZ, prm.s.Nz);
   auto k = k_curved<P, T, MODE>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  static std::atomic<unsigned long long> s_mask{0};
+  cudaError_t e = ensure_max_smem(k, s_mask);
   if (e != cudaSuccess) return e;
   k<<<prm.s.Nx, 256, sm, st>>>(prm);
   return cudaGetLastError();

@@ -27,13 +27,14 @@ __global__ void k_coarse_fwd(int NX1, int NZ1, const T* b, const double* V, doub
   rhat[(size_t)k * NX1 + ix] = acc;
 }
 
-// PCR: d'_i = d_i - k1_i d_{i-s} - k2_i d_{i+s} per step; x_i = d_i * inv_i.
+// PCR: d'_i = d_i - k1_i d_{i-s} - k2_i d_{i+s} per step; x_i = d_i * inv_i.  The two
+// ping-pong vectors live in shared memory, or (long tanks) in the global scratch gbuf.
 __global__ void k_coarse_pcr(int n, int nsteps, int periodic, const double* coef, const double* inv,
-                             double* rhat) {
+                             double* rhat, double* gbuf) {
   extern __shared__ double sbuf[];
-  double* d0 = sbuf;
-  double* d1 = sbuf + n;
   int k = blockIdx.x;
+  double* d0 = gbuf ? gbuf + (size_t)k * 2 * n : sbuf;
+  double* d1 = d0 + n;
   const double* ck = coef + (size_t)k * nsteps * n * 2;
   double* rk = rhat + (size_t)k * n;
   for (int i = threadIdx.x; i < n; i += blockDim.x) d0[i] = rk[i];
@@ -79,7 +80,16 @@ cudaError_t coarse_solve(const CoarseArgs& a, const void* b, void* x, cudaStream
   k_coarse_fwd<T><<<(tot + bs - 1) / bs, bs, 0, st>>>(a.NX1, a.NZ1, (const T*)b, a.V, a.work);
   int thr = a.NX1 < 1024 ? ((a.NX1 + 31) / 32) * 32 : 1024;
   size_t sm = 2 * (size_t)a.NX1 * sizeof(double);
-  k_coarse_pcr<<<Nz, thr, sm, st>>>(a.NX1, a.nsteps, a.periodic, a.coef, a.inv, a.work);
+  double* gbuf = nullptr;
+  if (sm > 200 * 1024) {  // does not fit in shared memory: ping-pong through global scratch
+    gbuf = a.pcr_buf;
+    sm = 0;
+  } else if (sm > 48 * 1024) {
+    static std::atomic<unsigned long long> s_mask{0};
+    cudaError_t e = ensure_max_smem(k_coarse_pcr, s_mask);
+    if (e != cudaSuccess) return e;
+  }
+  k_coarse_pcr<<<Nz, thr, sm, st>>>(a.NX1, a.nsteps, a.periodic, a.coef, a.inv, a.work, gbuf);
   size_t N = (size_t)a.NX1 * a.NZ1;
   k_coarse_bwd<T><<<(unsigned)((N + bs - 1) / bs), bs, 0, st>>>(a.NX1, a.NZ1, a.V, a.work, (T*)x);
   return cudaGetLastError();
@@ -232,6 +242,22 @@ __global__ void k_init_x(size_t n, int NZ, double* x, const double* x0, const do
 __global__ void k_check_finite(size_t n, const double* v, int* status) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     if (!isfinite(v[i])) atomicExch(status, 1);
+}
+
+// Device-side loop control of a graph while-node: counts the iteration and keeps the loop
+// running while ||r||^2 > thresh2 * (bb ? *bb : 1) and the cap is not reached (a NaN stops it).
+__global__ void k_loop_cond(cudaGraphConditionalHandle hnd, const double* s, const double* bb, double thresh2,
+                            int* iter, int max_iter) {
+  int it = ++(*iter);
+  double lim = thresh2 * (bb ? *bb : 1.0);
+  unsigned more = (s[SLOT_RR] > lim && it < max_iter) ? 1u : 0u;
+  cudaGraphSetConditional(hnd, more);
+}
+
+cudaError_t loop_cond(cudaGraphConditionalHandle hnd, const double* s, const double* bb, double thresh2, int* iter,
+                      int max_iter, cudaStream_t st) {
+  k_loop_cond<<<1, 1, 0, st>>>(hnd, s, bb, thresh2, iter, max_iter);
+  return cudaGetLastError();
 }
 
 static unsigned vec_grid(size_t n) {

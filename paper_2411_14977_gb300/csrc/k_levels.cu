@@ -111,7 +111,8 @@ static cudaError_t launch_flat_p(const FlatParams<T>& prm, cudaStream_t st) {
   int NZp = slab_pitch(prm.s.NZ);
   size_t sm = (size_t)((2 * P + 1) + (P + 1)) * NZp * sizeof(T);
   auto k = k_flat<P, T>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  static std::atomic<unsigned long long> s_mask{0};
+  cudaError_t e = ensure_max_smem(k, s_mask);
   if (e != cudaSuccess) return e;
   k<<<prm.s.Nx, 256, sm, st>>>(prm);
   return cudaGetLastError();
@@ -315,7 +316,8 @@ static cudaError_t launch_fdm_p(const FdmParams<T>& prm, cudaStream_t st) {
   size_t elems = (size_t)2 * NB * NZp + (size_t)prm.s.Nz * NB * NB + 9 * NB * NB;
   size_t sm = ((elems * sizeof(T) + 15) & ~(size_t)15) + 16;
   auto k = k_fdm<P, O, T>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  static std::atomic<unsigned long long> s_mask{0};
+  cudaError_t e = ensure_max_smem(k, s_mask);
   if (e != cudaSuccess) return e;
   k<<<prm.s.Nx, 256, sm, st>>>(prm);
   return cudaGetLastError();
@@ -478,12 +480,14 @@ cudaError_t transfer(const TransferArgs& a, int restrict_, cudaStream_t st) {
   cudaError_t e;
   if (restrict_) {
     size_t sm = ((size_t)(2 * a.f.P + 1) * (NZfp + NZcp) + nf * nc) * sizeof(T) + 16;
-    e = cudaFuncSetAttribute(k_restrict<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    static std::atomic<unsigned long long> s_mask{0};
+    e = ensure_max_smem(k_restrict<T>, s_mask);
     if (e != cudaSuccess) return e;
     k_restrict<T><<<a.f.Nx, 256, sm, st>>>(p);
   } else {
     size_t sm = ((size_t)nc * (NZcp + NZfp) + nf * nc) * sizeof(T) + 16;
-    e = cudaFuncSetAttribute(k_prolong<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    static std::atomic<unsigned long long> s_mask{0};
+    e = ensure_max_smem(k_prolong<T>, s_mask);
     if (e != cudaSuccess) return e;
     k_prolong<T><<<a.f.Nx, 256, sm, st>>>(p);
   }

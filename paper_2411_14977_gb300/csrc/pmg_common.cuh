@@ -13,6 +13,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 namespace pmg {
 
 constexpr int MAXP = 10;
@@ -133,6 +135,20 @@ __device__ __forceinline__ void grid_reduce(const Scratch& sc, double block_valu
     *out = v;
     *sc.redcnt = 0u;
   }
+}
+
+// Raise a kernel's dynamic shared-memory limit to the SM maximum once per device
+// (the attribute is per function and device); `mask` is the instantiation's own flag set.
+template <typename K>
+inline cudaError_t ensure_max_smem(K kernel, std::atomic<unsigned long long>& mask) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  unsigned long long bit = 1ull << (dev & 63);
+  if (mask.load(std::memory_order_relaxed) & bit) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (e == cudaSuccess) mask.fetch_or(bit);
+  return e;
 }
 
 }  // namespace pmg

@@ -90,6 +90,7 @@ struct CoarseArgs {
   const double* coef;  // [Nz][nsteps][NX1][2]
   const double* inv;   // [Nz][NX1]
   double* work;        // [Nz][NX1]
+  double* pcr_buf;     // [Nz][2][NX1] when 2 NX1 doubles exceed the shared-memory budget
 };
 template <typename T> cudaError_t coarse_solve(const CoarseArgs& a, const void* b, void* x, cudaStream_t st);
 
@@ -107,5 +108,7 @@ cudaError_t add_f32_scaled(size_t n, double* x, const float* c, const double* s,
 template <typename T> cudaError_t add(size_t n, T* x, const T* y, cudaStream_t st);
 cudaError_t init_x(size_t n, int NZ, double* x, const double* x0, const double* pD, int* status, cudaStream_t st);
 cudaError_t check_finite(size_t n, const double* v, int* status, cudaStream_t st);
+cudaError_t loop_cond(cudaGraphConditionalHandle hnd, const double* s, const double* bb, double thresh2, int* iter,
+                      int max_iter, cudaStream_t st);
 
 }  // namespace pmg

@@ -200,6 +200,24 @@ struct pmg_handle {
   int* status_host = nullptr;
   double* io = nullptr;  // pmg_solve_host: out, b, p_D, x0
   Scratch sc{};
+  // profiling: per-class launch counts; optional CUDA-event pairs around launches
+  bool timing = false;
+  int64_t launches[PMG_K_COUNT] = {};
+  double bytes[PMG_K_COUNT] = {};              // algorithmic bytes moved by the launches
+  double flops[PMG_K_COUNT] = {};              // algorithmic floating-point operations
+  std::vector<cudaEvent_t> ev_pool;            // pairs: [2k] start, [2k+1] stop
+  std::vector<std::pair<int, int>> ev_used;    // (class, pair index)
+  // device-side Krylov loops: graphs with a while-node, built on first use
+  cudaStream_t cap = nullptr;                  // capture stream
+  int* d_iter = nullptr;                       // [2] iteration counters (FP64 loop, FP32 inner loop)
+  int* iter_host = nullptr;                    // pinned copy
+  struct Loop {
+    cudaGraphExec_t exec = nullptr;
+    int64_t init_launches[PMG_K_COUNT] = {};   // kernels of the first iteration
+    int64_t body_launches[PMG_K_COUNT] = {};   // kernels of every further iteration
+    double init_bytes[PMG_K_COUNT] = {}, body_bytes[PMG_K_COUNT] = {};
+    double init_flops[PMG_K_COUNT] = {}, body_flops[PMG_K_COUNT] = {};
+  } loop64, loop32;
 
   template <typename T> T* alloc(size_t n, cudaError_t& e) {
     T* d = nullptr;
@@ -208,6 +226,11 @@ struct pmg_handle {
     return d;
   }
   ~pmg_handle() {
+    for (Loop* l : {&loop64, &loop32})
+      if (l->exec) cudaGraphExecDestroy(l->exec);
+    if (cap) cudaStreamDestroy(cap);
+    if (iter_host) cudaFreeHost(iter_host);
+    for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
     for (void* a : allocs) cudaFree(a);
     if (scal_host) cudaFreeHost(scal_host);
     if (status_host) cudaFreeHost(status_host);
@@ -217,6 +240,43 @@ struct pmg_handle {
 namespace {
 
 template <typename T> constexpr int PI = std::is_same<T, double>::value ? 0 : 1;
+
+// Every kernel launch goes through here: counts it under its class and, when timing is
+// on, brackets it with a pair of CUDA events on the launching stream.
+// Algorithmic cost of a launch, for the roofline: bytes that must cross DRAM at least
+// once and floating-point operations (an FMA counts 2).
+struct Cost {
+  double bytes = 0, flops = 0;
+};
+
+template <class F>
+pmg_status launch(pmg_handle* h, int cls, int nkernels, cudaStream_t st, Cost c, F&& f) {
+  h->launches[cls] += nkernels;
+  h->bytes[cls] += c.bytes;
+  h->flops[cls] += c.flops;
+  int pair = -1;
+  if (h->timing) {
+    pair = (int)h->ev_used.size();
+    if ((size_t)(2 * pair + 2) > h->ev_pool.size()) {
+      for (int k = 0; k < 512; ++k) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        h->ev_pool.push_back(e);
+      }
+    }
+    CK(cudaEventRecord(h->ev_pool[2 * pair], st));
+  }
+  CK(f());
+  if (pair >= 0) {
+    CK(cudaEventRecord(h->ev_pool[2 * pair + 1], st));
+    h->ev_used.push_back({cls, pair});
+  }
+  return PMG_OK;
+}
+template <class F>
+pmg_status launch(pmg_handle* h, int cls, int nkernels, cudaStream_t st, F&& f) {
+  return launch(h, cls, nkernels, st, Cost{}, f);
+}
 
 // ---- setup helpers -----------------------------------------------------------------
 pmg_status build_level(pmg_handle* h, int l) {
@@ -388,6 +448,10 @@ pmg_status build_coarse(pmg_handle* h) {
   h->coarse.coef = upload<double>(coef, h->allocs, e); CK(e);
   h->coarse.inv = upload<double>(inv, h->allocs, e); CK(e);
   h->coarse.work = h->alloc<double>((size_t)Nz * n, e); CK(e);
+  h->coarse.pcr_buf = nullptr;
+  if (2 * (size_t)n * sizeof(double) > 200 * 1024) {
+    h->coarse.pcr_buf = h->alloc<double>((size_t)Nz * 2 * n, e); CK(e);
+  }
   return PMG_OK;
 }
 
@@ -397,8 +461,9 @@ pmg_status level_residual(pmg_handle* h, int l, const void* b, const void* x, vo
                           cudaStream_t st) {
   LevelDev& L = h->lv[l];
   FlatArgs a{L.s, x, b, y, h->cx, h->cz, L.mX[PI<T>], L.mZ[PI<T>], residual};
-  CK(flat_op<T>(a, st));
-  return PMG_OK;
+  double NL = (double)L.s.NX * L.s.NZ;
+  Cost c{(residual ? 3.0 : 2.0) * NL * sizeof(T), NL * (4.0 * (L.s.P + 2) + 4.0)};
+  return launch(h, PI<T> ? PMG_K_LEVEL32 : PMG_K_LEVEL64, 1, st, c, [&] { return flat_op<T>(a, st); });
 }
 
 template <typename T>
@@ -406,8 +471,10 @@ pmg_status level_fdm(pmg_handle* h, int l, const void* r, void* x, int post, cud
   LevelDev& L = h->lv[l];
   FdmArgs a{L.s, L.overlap, r, x, post, h->opts.omega, L.Vx[PI<T>], L.Vz[PI<T>], L.invden[PI<T>],
             L.wx[PI<T>], L.wz[PI<T>], h->sc};
-  CK(fdm_smooth<T>(a, st));
-  return PMG_OK;
+  double NL = (double)L.s.NX * L.s.NZ, E = (double)L.s.Nx * L.s.Nz;
+  double NB = L.s.P + 1 + 2 * L.overlap;
+  Cost c{3.0 * NL * sizeof(T), E * 2.0 * (2.0 * L.s.P * NB * NB + 2.0 * NB * NB * NB)};
+  return launch(h, PI<T> ? PMG_K_SMOOTH32 : PMG_K_SMOOTH64, 1, st, c, [&] { return fdm_smooth<T>(a, st); });
 }
 
 // nu sweeps on A_l x = b (x updated); x_zero: x is known to be zero on entry
@@ -429,8 +496,19 @@ pmg_status level_smooth(pmg_handle* h, int l, const void* b, void* x, int post, 
 template <typename T>
 pmg_status transfer_op(pmg_handle* h, int l, const void* in, void* out, int restrict_, cudaStream_t st) {
   TransferArgs a{h->lv[l].s, h->lv[l + 1].s, in, out, h->lv[l].J};
-  CK(transfer<T>(a, restrict_, st));
-  return PMG_OK;
+  double Nf = (double)h->lv[l].s.NX * h->lv[l].s.NZ, Nc = (double)h->lv[l + 1].s.NX * h->lv[l + 1].s.NZ;
+  double pf = h->lv[l].s.P, pc = h->lv[l + 1].s.P;
+  Cost c{(restrict_ ? Nf + Nc : 2.0 * Nf + Nc) * sizeof(T), 2.0 * (Nf * (pc + 1) + Nc * (pf + 1))};
+  return launch(h, PMG_K_TRANSFER, 1, st, c, [&] { return transfer<T>(a, restrict_, st); });
+}
+
+template <typename T>
+Cost coarse_cost(pmg_handle* h) {
+  const CoarseArgs& c = h->coarse;
+  double n1 = (double)c.NX1 * c.NZ1, nz = c.NZ1 - 1;
+  double tables = nz * nz * 8.0 + nz * c.nsteps * c.NX1 * 16.0 + nz * c.NX1 * 8.0;
+  return Cost{n1 * 2.0 * sizeof(T) + tables + 2.0 * nz * c.NX1 * 8.0 * 2.0,
+              2.0 * (2.0 * c.NX1 * nz * nz + 2.0 * nz * c.NX1 * c.nsteps)};
 }
 
 template <typename T>
@@ -438,10 +516,7 @@ pmg_status vcycle(pmg_handle* h, int l, const void* b, void* x, cudaStream_t st)
   int nl = (int)h->lv.size();
   LevelDev& L = h->lv[l];
   size_t NL = (size_t)L.s.NX * L.s.NZ;
-  if (l == nl - 1) {
-    CK(coarse_solve<T>(h->coarse, b, x, st));
-    return PMG_OK;
-  }
+  if (l == nl - 1) return launch(h, PMG_K_COARSE, 3, st, coarse_cost<T>(h), [&] { return coarse_solve<T>(h->coarse, b, x, st); });
   CK(cudaMemsetAsync(x, 0, NL * sizeof(T), st));
   CKS(level_smooth<T>(h, l, b, x, 0, true, st));
   CKS(level_residual<T>(h, l, b, x, L.t[PI<T>], 1, st));
@@ -468,13 +543,16 @@ pmg_status curved(pmg_handle* h, int mode, const void* x, const void* b, void* y
   a.mask_input = mask;
   a.result = result;
   a.sc = h->sc;
-  CK(curved_op<T>(a, st));
-  return PMG_OK;
+  const Shape& F = a.s;
+  double N = (double)F.NX * F.NZ, E = (double)F.Nx * F.Nz, n = F.P + 1;
+  Cost c{(mode == 1 ? 3.0 : 2.0) * N * sizeof(T), E * (8.0 * n * n * n + 12.0 * n * n)};
+  return launch(h, PI<T> ? PMG_K_CURVED32 : PMG_K_CURVED64, 1, st, c, [&] { return curved_op<T>(a, st); });
 }
 
 pmg_status read_scalars(pmg_handle* h, cudaStream_t st) {
   CK(cudaMemcpyAsync(h->scal_host, h->scal, SLOT_COUNT * sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(h->status_host, h->status, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(h->iter_host, h->d_iter, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   return PMG_OK;
 }
@@ -494,9 +572,175 @@ pmg_status lifted_norm(pmg_handle* h, const double* b, const double* pD, const d
     CK(cudaMemcpyAsync(h->scal + SLOT_RR64, h->scal + SLOT_BB, sizeof(double), cudaMemcpyDeviceToDevice, st));
     return PMG_OK;
   }
-  CK(init_x(N, NZ, h->p, nullptr, pD, h->status, st));
+  CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{24.0 * N, 0.0}, [&] { return init_x(N, NZ, h->p, nullptr, pD, h->status, st); }));
   CKS(curved<double>(h, 1, h->p, b, h->w, 0, h->scal + SLOT_BB, st));
   CKS(outer_residual(h, b, SLOT_RR64, st));
+  return PMG_OK;
+}
+
+
+// Build a graph "init; while (cond) body" where init and body are captured launch
+// sequences that end with the loop-condition kernel.  Launch counts seen during capture
+// are moved from the live counters into the loop's per-replay tallies.
+template <class Init, class Body>
+pmg_status build_loop(pmg_handle* h, pmg_handle::Loop& L, Init&& init, Body&& body) {
+  if (!h->cap) CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+  bool timing = h->timing;
+  h->timing = false;
+  struct Restore { pmg_handle* h; bool t; ~Restore() { h->timing = t; } } restore{h, timing};
+  int64_t snap[PMG_K_COUNT];
+  double snapb[PMG_K_COUNT], snapf[PMG_K_COUNT];
+  std::memcpy(snap, h->launches, sizeof(snap));
+  std::memcpy(snapb, h->bytes, sizeof(snapb));
+  std::memcpy(snapf, h->flops, sizeof(snapf));
+  cudaGraph_t g = nullptr;
+  CK(cudaGraphCreate(&g, 0));
+  struct GraphDel { cudaGraph_t g; ~GraphDel() { if (g) cudaGraphDestroy(g); } } del{g};
+  cudaGraphConditionalHandle hc;
+  CK(cudaGraphConditionalHandleCreate(&hc, g, 1, cudaGraphCondAssignDefault));
+  cudaGraph_t out = nullptr;
+  CK(cudaStreamBeginCaptureToGraph(h->cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  pmg_status s = init(h->cap, hc);
+  cudaError_t e = cudaStreamEndCapture(h->cap, &out);
+  if (s != PMG_OK) return s;
+  CK(e);
+  for (int k = 0; k < PMG_K_COUNT; ++k) {
+    L.init_launches[k] = h->launches[k] - snap[k]; h->launches[k] = snap[k];
+    L.init_bytes[k] = h->bytes[k] - snapb[k]; h->bytes[k] = snapb[k];
+    L.init_flops[k] = h->flops[k] - snapf[k]; h->flops[k] = snapf[k];
+  }
+  size_t nn = 0;
+  CK(cudaGraphGetNodes(g, nullptr, &nn));
+  std::vector<cudaGraphNode_t> nodes(nn), leaves;
+  CK(cudaGraphGetNodes(g, nodes.data(), &nn));
+  for (cudaGraphNode_t nd : nodes) {
+    size_t k = 0;
+    CK(cudaGraphNodeGetDependentNodes(nd, nullptr, nullptr, &k));
+    if (k == 0) leaves.push_back(nd);
+  }
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = hc;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cn;
+  CK(cudaGraphAddNode(&cn, g, leaves.data(), nullptr, leaves.size(), &cp));
+  cudaGraph_t bodyg = cp.conditional.phGraph_out[0];
+  CK(cudaStreamBeginCaptureToGraph(h->cap, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  s = body(h->cap, hc);
+  e = cudaStreamEndCapture(h->cap, &out);
+  if (s != PMG_OK) return s;
+  CK(e);
+  for (int k = 0; k < PMG_K_COUNT; ++k) {
+    L.body_launches[k] = h->launches[k] - snap[k]; h->launches[k] = snap[k];
+    L.body_bytes[k] = h->bytes[k] - snapb[k]; h->bytes[k] = snapb[k];
+    L.body_flops[k] = h->flops[k] - snapf[k]; h->flops[k] = snapf[k];
+  }
+  CK(cudaGraphInstantiate(&L.exec, g, 0));
+  return PMG_OK;
+}
+
+// Run a built loop; returns the iterations it made (after a stream sync).
+pmg_status run_loop(pmg_handle* h, pmg_handle::Loop& L, int which, cudaStream_t st, int* iters) {
+  CK(cudaGraphLaunch(L.exec, st));
+  CKS(read_scalars(h, st));
+  int it = h->iter_host[which];
+  int extra = std::max(0, it - 1);
+  for (int k = 0; k < PMG_K_COUNT; ++k) {
+    h->launches[k] += L.init_launches[k] + (int64_t)extra * L.body_launches[k];
+    h->bytes[k] += L.init_bytes[k] + extra * L.body_bytes[k];
+    h->flops[k] += L.init_flops[k] + extra * L.body_flops[k];
+  }
+  *iters = it;
+  return PMG_OK;
+}
+
+// FP64 PCG / flexible CG iteration sequence (first: p = z instead of the beta update).
+pmg_status cg64_step(pmg_handle* h, bool first, cudaStream_t st, cudaGraphConditionalHandle hc) {
+  size_t N = h->N;
+  double* s = h->scal + GROUP_OUTER;
+  int flexible = h->opts.outer == PMG_FCG;
+  if (first) CK(cudaMemsetAsync(h->d_iter, 0, sizeof(int), st));
+  CKS(vcycle<double>(h, 0, h->r, h->z, st));
+  const double* ro = (flexible && !first) ? h->rold : nullptr;
+  CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{3.0 * N * 8, 4.0 * N}, [&] { return rz<double>(N, h->r, h->z, ro, s, h->sc, st); }));
+  CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{3.0 * N * 8, 2.0 * N}, [&] { return p_update<double>(N, h->p, h->z, s, flexible, first ? 1 : 0, st); }));
+  CKS(curved<double>(h, 2, h->p, nullptr, h->w, 1, s + SLOT_PAP, st));
+  CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{7.0 * N * 8, 6.0 * N}, [&] { return cg_update<double>(N, h->x, h->r, h->p, h->w, flexible ? h->rold : nullptr, s, h->sc, st); }));
+  const double tol2 = h->opts.tol * h->opts.tol;
+  return launch(h, PMG_K_VECTOR, 1, st, [&] { return loop_cond(hc, s, h->scal + SLOT_BB, tol2, h->d_iter, h->opts.max_iter, st); });
+}
+
+// FP32 inner flexible-CG iteration sequence on A c = r32 (c = 0 at the start).
+pmg_status cg32_step(pmg_handle* h, bool first, cudaStream_t st, cudaGraphConditionalHandle hc) {
+  size_t N = h->N;
+  double* s = h->scal + GROUP_INNER;
+  if (first) {
+    CK(cudaMemsetAsync(h->d_iter + 1, 0, sizeof(int), st));
+    CK(cudaMemsetAsync(h->c32, 0, N * sizeof(float), st));
+  }
+  CKS(vcycle<float>(h, 0, h->r32, h->z32, st));
+  const float* ro = first ? nullptr : h->rold32;
+  CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{3.0 * N * 4, 4.0 * N}, [&] { return rz<float>(N, h->r32, h->z32, ro, s, h->sc, st); }));
+  CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{3.0 * N * 4, 2.0 * N}, [&] { return p_update<float>(N, h->p32, h->z32, s, 1, first ? 1 : 0, st); }));
+  CKS(curved<float>(h, 2, h->p32, nullptr, h->w32, 1, s + SLOT_PAP, st));
+  CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{7.0 * N * 4, 6.0 * N}, [&] { return cg_update<float>(N, h->c32, h->r32, h->p32, h->w32, h->rold32, s, h->sc, st); }));
+  const double itol2 = h->opts.inner_tol * h->opts.inner_tol;
+  return launch(h, PMG_K_VECTOR, 1, st, [&] { return loop_cond(hc, s, nullptr, itol2, h->d_iter + 1, h->opts.inner_max, st); });
+}
+
+pmg_status solve_krylov64_graph(pmg_handle* h, const double* b, pmg_solve_info* info, cudaStream_t st) {
+  const double tol2 = h->opts.tol * h->opts.tol;
+  double bb = h->scal_host[SLOT_BB];
+  if (h->scal_host[SLOT_RR64] <= tol2 * bb) {
+    if (info) info->iterations = 0;
+    return PMG_OK;
+  }
+  if (!h->loop64.exec)
+    CKS(build_loop(h, h->loop64, [&](cudaStream_t cs, cudaGraphConditionalHandle hc) { return cg64_step(h, true, cs, hc); },
+                   [&](cudaStream_t cs, cudaGraphConditionalHandle hc) { return cg64_step(h, false, cs, hc); }));
+  int total = 0;
+  while (total < h->opts.max_iter) {
+    int it = 0;
+    CKS(run_loop(h, h->loop64, 0, st, &it));
+    total += it;
+    double rr = h->scal_host[GROUP_OUTER + SLOT_RR];
+    if (!std::isfinite(rr)) return fail(PMG_ERR_NONFINITE, "non-finite residual");
+    // confirm with the true residual; restart from it on drift
+    CKS(outer_residual(h, b, SLOT_RR64, st));
+    CKS(read_scalars(h, st));
+    if (h->scal_host[SLOT_RR64] <= tol2 * bb) break;
+  }
+  if (info) info->iterations = total;
+  return PMG_OK;
+}
+
+pmg_status solve_refine_graph(pmg_handle* h, const double* b, pmg_solve_info* info, cudaStream_t st) {
+  size_t N = h->N;
+  const double tol2 = h->opts.tol * h->opts.tol;
+  double bb = h->scal_host[SLOT_BB];
+  if (!h->loop32.exec)
+    CKS(build_loop(h, h->loop32, [&](cudaStream_t cs, cudaGraphConditionalHandle hc) { return cg32_step(h, true, cs, hc); },
+                   [&](cudaStream_t cs, cudaGraphConditionalHandle hc) { return cg32_step(h, false, cs, hc); }));
+  int outer = 0, inner_total = 0;
+  while (outer < h->opts.max_iter) {
+    double rr = h->scal_host[SLOT_RR64];
+    if (!std::isfinite(rr)) return fail(PMG_ERR_NONFINITE, "non-finite residual");
+    if (rr <= tol2 * bb) break;
+    CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{12.0 * N, 1.0 * N}, [&] { return to_f32_scaled(N, h->r, h->r32, h->scal, SLOT_RR64, st); }));
+    int it = 0;
+    CKS(run_loop(h, h->loop32, 1, st, &it));
+    inner_total += it;
+    if (!std::isfinite(h->scal_host[GROUP_INNER + SLOT_RR])) return fail(PMG_ERR_NONFINITE, "non-finite inner residual");
+    CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{20.0 * N, 2.0 * N}, [&] { return add_f32_scaled(N, h->x, h->c32, h->scal, SLOT_RR64, st); }));
+    ++outer;
+    CKS(outer_residual(h, b, SLOT_RR64, st));
+    CKS(read_scalars(h, st));
+  }
+  if (info) {
+    info->iterations = outer;
+    info->inner_iterations = inner_total;
+  }
   return PMG_OK;
 }
 
@@ -516,12 +760,12 @@ pmg_status solve_krylov64(pmg_handle* h, const double* b, pmg_solve_info* info, 
   while (it < h->opts.max_iter) {
     if (restart) {
       CKS(vcycle<double>(h, 0, h->r, h->z, st));
-      CK(rz<double>(N, h->r, h->z, nullptr, s, h->sc, st));
-      CK(p_update<double>(N, h->p, h->z, s, 0, 1, st));
+      CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{3.0 * N * 8, 4.0 * N}, [&] { return rz<double>(N, h->r, h->z, nullptr, s, h->sc, st); }));
+      CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{3.0 * N * 8, 2.0 * N}, [&] { return p_update<double>(N, h->p, h->z, s, 0, 1, st); }));
       restart = false;
     }
     CKS(curved<double>(h, 2, h->p, nullptr, h->w, 1, s + SLOT_PAP, st));
-    CK(cg_update<double>(N, h->x, h->r, h->p, h->w, flexible ? h->rold : nullptr, s, h->sc, st));
+    CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{7.0 * N * 8, 6.0 * N}, [&] { return cg_update<double>(N, h->x, h->r, h->p, h->w, flexible ? h->rold : nullptr, s, h->sc, st); }));
     ++it;
     CKS(read_scalars(h, st));
     double rr = h->scal_host[GROUP_OUTER + SLOT_RR];
@@ -535,8 +779,8 @@ pmg_status solve_krylov64(pmg_handle* h, const double* b, pmg_solve_info* info, 
       continue;
     }
     CKS(vcycle<double>(h, 0, h->r, h->z, st));
-    CK(rz<double>(N, h->r, h->z, flexible ? h->rold : nullptr, s, h->sc, st));
-    CK(p_update<double>(N, h->p, h->z, s, flexible, 0, st));
+    CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{3.0 * N * 8, 4.0 * N}, [&] { return rz<double>(N, h->r, h->z, flexible ? h->rold : nullptr, s, h->sc, st); }));
+    CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{3.0 * N * 8, 2.0 * N}, [&] { return p_update<double>(N, h->p, h->z, s, flexible, 0, st); }));
   }
   if (info) info->iterations = it;
   return PMG_OK;
@@ -555,11 +799,11 @@ pmg_status solve_pdc(pmg_handle* h, const double* b, pmg_solve_info* info, cudaS
     if (rr <= tol2 * bb) break;
     if (h->opts.precision == PMG_FP64) {
       CKS(vcycle<double>(h, 0, h->r, h->z, st));
-      CK(add<double>(N, h->x, h->z, st));
+      CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{24.0 * N, 1.0 * N}, [&] { return add<double>(N, h->x, h->z, st); }));
     } else {
-      CK(to_f32_scaled(N, h->r, h->r32, h->scal, SLOT_RR64, st));
+      CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{12.0 * N, 1.0 * N}, [&] { return to_f32_scaled(N, h->r, h->r32, h->scal, SLOT_RR64, st); }));
       CKS(vcycle<float>(h, 0, h->r32, h->z32, st));
-      CK(add_f32_scaled(N, h->x, h->z32, h->scal, SLOT_RR64, st));
+      CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{20.0 * N, 2.0 * N}, [&] { return add_f32_scaled(N, h->x, h->z32, h->scal, SLOT_RR64, st); }));
     }
     ++it;
     CKS(outer_residual(h, b, SLOT_RR64, st));
@@ -582,24 +826,24 @@ pmg_status solve_refine(pmg_handle* h, const double* b, pmg_solve_info* info, cu
     double rr = h->scal_host[SLOT_RR64];
     if (!std::isfinite(rr)) return fail(PMG_ERR_NONFINITE, "non-finite residual");
     if (rr <= tol2 * bb) break;
-    CK(to_f32_scaled(N, h->r, h->r32, h->scal, SLOT_RR64, st));
+    CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{12.0 * N, 1.0 * N}, [&] { return to_f32_scaled(N, h->r, h->r32, h->scal, SLOT_RR64, st); }));
     CK(cudaMemsetAsync(h->c32, 0, N * sizeof(float), st));
     CKS(vcycle<float>(h, 0, h->r32, h->z32, st));
-    CK(rz<float>(N, h->r32, h->z32, nullptr, s, h->sc, st));
-    CK(p_update<float>(N, h->p32, h->z32, s, 0, 1, st));
+    CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{3.0 * N * 4, 4.0 * N}, [&] { return rz<float>(N, h->r32, h->z32, nullptr, s, h->sc, st); }));
+    CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{3.0 * N * 4, 2.0 * N}, [&] { return p_update<float>(N, h->p32, h->z32, s, 0, 1, st); }));
     for (int j = 0; j < h->opts.inner_max; ++j) {
       CKS(curved<float>(h, 2, h->p32, nullptr, h->w32, 1, s + SLOT_PAP, st));
-      CK(cg_update<float>(N, h->c32, h->r32, h->p32, h->w32, h->rold32, s, h->sc, st));
+      CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{7.0 * N * 4, 6.0 * N}, [&] { return cg_update<float>(N, h->c32, h->r32, h->p32, h->w32, h->rold32, s, h->sc, st); }));
       ++inner_total;
       CKS(read_scalars(h, st));
       double irr = h->scal_host[GROUP_INNER + SLOT_RR];
       if (!std::isfinite(irr)) return fail(PMG_ERR_NONFINITE, "non-finite inner residual");
       if (irr <= itol2) break;
       CKS(vcycle<float>(h, 0, h->r32, h->z32, st));
-      CK(rz<float>(N, h->r32, h->z32, h->rold32, s, h->sc, st));
-      CK(p_update<float>(N, h->p32, h->z32, s, 1, 0, st));
+      CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{3.0 * N * 4, 4.0 * N}, [&] { return rz<float>(N, h->r32, h->z32, h->rold32, s, h->sc, st); }));
+      CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{3.0 * N * 4, 2.0 * N}, [&] { return p_update<float>(N, h->p32, h->z32, s, 1, 0, st); }));
     }
-    CK(add_f32_scaled(N, h->x, h->c32, h->scal, SLOT_RR64, st));
+    CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{20.0 * N, 2.0 * N}, [&] { return add_f32_scaled(N, h->x, h->c32, h->scal, SLOT_RR64, st); }));
     ++outer;
     CKS(outer_residual(h, b, SLOT_RR64, st));
   }
@@ -742,6 +986,7 @@ pmg_status pmg_create(const pmg_mesh_desc* mesh, const pmg_opts* opts, pmg_handl
   ALLOC(h->z32, float, h->N);
   ALLOC(h->rold32, float, h->N);
   ALLOC(h->scal, double, SLOT_COUNT);
+  ALLOC(h->d_iter, int, 2);
   size_t nedges = (size_t)m.cells_x + 1;
   size_t ebuf = nedges * (2 * MAXO + 1) * (size_t)F.NZ;
   h->sc.edgebuf = h->alloc<double>(ebuf, e);
@@ -759,7 +1004,9 @@ pmg_status pmg_create(const pmg_mesh_desc* mesh, const pmg_opts* opts, pmg_handl
       cudaMemset(h->eta, 0, F.NX * sizeof(double)) != cudaSuccess)
     return bail(fail(PMG_ERR_CUDA, "memset failed"));
   if (cudaMallocHost(&h->scal_host, SLOT_COUNT * sizeof(double)) != cudaSuccess ||
-      cudaMallocHost(&h->status_host, 2 * sizeof(int)) != cudaSuccess)
+      cudaMallocHost(&h->status_host, 2 * sizeof(int)) != cudaSuccess ||
+      cudaMallocHost(&h->iter_host, 2 * sizeof(int)) != cudaSuccess ||
+      cudaMemset(h->d_iter, 0, 2 * sizeof(int)) != cudaSuccess)
     return bail(fail(PMG_ERR_OOM, "pinned allocation failed"));
   pmg_status s = pmg_set_geometry(h, h->eta, nullptr);
   if (s != PMG_OK) return bail(s);
@@ -811,9 +1058,9 @@ pmg_status pmg_set_geometry(pmg_handle* h, const double* eta_dev, void* stream) 
   if (eta_dev != h->eta) CK(cudaMemcpyAsync(h->eta, eta_dev, F.NX * sizeof(double), cudaMemcpyDeviceToDevice, st));
   int* gst = h->status + 1;
   CK(cudaMemsetAsync(gst, 0, sizeof(int), st));
-  CK(geometry<double>(F, h->eta, h->mesh.h, h->dx, h->dsig, 0, (double*)h->geo[0], gst, st));
-  CK(geometry<float>(F, h->eta, h->mesh.h, h->dx, h->dsig, 0, (float*)h->geo[1], gst, st));
-  CK(geometry<double>(F, h->eta, h->mesh.h, h->dx, h->dsig, 1, h->geo_div, gst, st));
+  CKS(launch(h, PMG_K_SETUP, 1, st, [&] { return geometry<double>(F, h->eta, h->mesh.h, h->dx, h->dsig, 0, (double*)h->geo[0], gst, st); }));
+  CKS(launch(h, PMG_K_SETUP, 1, st, [&] { return geometry<float>(F, h->eta, h->mesh.h, h->dx, h->dsig, 0, (float*)h->geo[1], gst, st); }));
+  CKS(launch(h, PMG_K_SETUP, 1, st, [&] { return geometry<double>(F, h->eta, h->mesh.h, h->dx, h->dsig, 1, h->geo_div, gst, st); }));
   return PMG_OK;
 }
 
@@ -823,9 +1070,11 @@ pmg_status pmg_assemble_rhs(pmg_handle* h, const double* f, const double* gb, co
   if (!f || !b) return fail(PMG_ERR_INVALID, "f and b must be non-NULL");
   DeviceGuard dg(h->device);
   LevelDev& L = h->lv[0];
-  CK(rhs_source(L.s, h->eta, h->mesh.h, h->dx, h->dsig, (const double*)L.mX[0], (const double*)L.mZ[0], f, gb,
-                h->mesh.periodic_x ? nullptr : gl, h->mesh.periodic_x ? nullptr : gr, b, (cudaStream_t)stream));
-  return PMG_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  return launch(h, PMG_K_SETUP, 1, st, [&] {
+    return rhs_source(L.s, h->eta, h->mesh.h, h->dx, h->dsig, (const double*)L.mX[0], (const double*)L.mZ[0], f, gb,
+                      h->mesh.periodic_x ? nullptr : gl, h->mesh.periodic_x ? nullptr : gr, b, st);
+  });
 }
 
 pmg_status pmg_assemble_rhs_div(pmg_handle* h, const double* u, const double* w, double scale, double* b,
@@ -843,8 +1092,8 @@ pmg_status pmg_assemble_rhs_div(pmg_handle* h, const double* u, const double* w,
   a.sigma = h->sigma[0];
   a.scale = scale;
   a.sc = h->sc;
-  CK(curved_op<double>(a, (cudaStream_t)stream));
-  return PMG_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  return launch(h, PMG_K_SETUP, 1, st, [&] { return curved_op<double>(a, st); });
 }
 
 pmg_status pmg_apply(pmg_handle* h, const double* x, double* y, void* stream) {
@@ -897,8 +1146,8 @@ pmg_status pmg_coarse_solve(pmg_handle* h, const double* b, double* x, void* str
   CKS(check_handle(h));
   if (!b || !x) return fail(PMG_ERR_INVALID, "NULL vector");
   DeviceGuard dg(h->device);
-  CK(coarse_solve<double>(h->coarse, b, x, (cudaStream_t)stream));
-  return PMG_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  return launch(h, PMG_K_COARSE, 3, st, [&] { return coarse_solve<double>(h->coarse, b, x, st); });
 }
 
 pmg_status pmg_vcycle(pmg_handle* h, const void* r, void* z, int f32, void* stream) {
@@ -919,8 +1168,8 @@ pmg_status pmg_solve(pmg_handle* h, const double* b, const double* pD, const dou
   pmg_solve_info loc{};
   size_t N = h->N;
   CK(cudaMemsetAsync(h->status, 0, sizeof(int), st));
-  CK(check_finite(N, b, h->status, st));
-  CK(init_x(N, h->lv[0].s.NZ, h->x, x0, pD, h->status, st));
+  CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{8.0 * N, 0.0}, [&] { return check_finite(N, b, h->status, st); }));
+  CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{24.0 * N, 0.0}, [&] { return init_x(N, h->lv[0].s.NZ, h->x, x0, pD, h->status, st); }));
   CKS(lifted_norm(h, b, pD, x0, st));
   CKS(read_scalars(h, st));
   pmg_status result = PMG_OK;
@@ -934,8 +1183,10 @@ pmg_status pmg_solve(pmg_handle* h, const double* b, const double* pD, const dou
   } else if (bb > 0.0) {
     pmg_status s;
     if (h->opts.outer == PMG_PDC) s = solve_pdc(h, b, &loc, st);
-    else if (h->opts.precision == PMG_FP64) s = solve_krylov64(h, b, &loc, st);
-    else s = solve_refine(h, b, &loc, st);
+    else if (h->opts.precision == PMG_FP64)
+      s = h->timing ? solve_krylov64(h, b, &loc, st) : solve_krylov64_graph(h, b, &loc, st);
+    else
+      s = h->timing ? solve_refine(h, b, &loc, st) : solve_refine_graph(h, b, &loc, st);
     if (s != PMG_OK) result = s;
     // final true residual
     CKS(outer_residual(h, b, SLOT_RR64, st));
@@ -953,6 +1204,37 @@ pmg_status pmg_solve(pmg_handle* h, const double* b, const double* pD, const dou
   loc.status = result;
   if (info) *info = loc;
   return result;
+}
+
+pmg_status pmg_profile_reset(pmg_handle* h, int timing) {
+  CKS(check_handle(h));
+  DeviceGuard dg(h->device);
+  CK(cudaDeviceSynchronize());
+  for (auto& v : h->launches) v = 0;
+  for (auto& v : h->bytes) v = 0;
+  for (auto& v : h->flops) v = 0;
+  h->ev_used.clear();
+  h->timing = timing != 0;
+  return PMG_OK;
+}
+
+pmg_status pmg_profile_read(pmg_handle* h, int64_t* launches, double* ms, double* bytes, double* flops) {
+  CKS(check_handle(h));
+  DeviceGuard dg(h->device);
+  CK(cudaDeviceSynchronize());
+  double acc[PMG_K_COUNT] = {};
+  for (auto& u : h->ev_used) {
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, h->ev_pool[2 * u.second], h->ev_pool[2 * u.second + 1]));
+    acc[u.first] += t;
+  }
+  for (int k = 0; k < PMG_K_COUNT; ++k) {
+    if (launches) launches[k] = h->launches[k];
+    if (ms) ms[k] = acc[k];
+    if (bytes) bytes[k] = h->bytes[k];
+    if (flops) flops[k] = h->flops[k];
+  }
+  return PMG_OK;
 }
 
 pmg_status pmg_solve_host(pmg_handle* h, const double* b, const double* pD, const double* x0, double* p_out,

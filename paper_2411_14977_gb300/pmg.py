@@ -17,6 +17,9 @@ PMG_PCG, PMG_FCG, PMG_PDC = 0, 1, 2
 PMG_ASM_FDM = 0
 PMG_FLAT_LINEARISED = 1
 
+KERNEL_CLASSES = ["curved64", "curved32", "level64", "level32", "smooth64", "smooth32", "transfer",
+                  "coarse", "vector", "setup"]
+
 STATUS_NAMES = {0: "PMG_OK", 1: "PMG_ERR_INVALID", 2: "PMG_ERR_OOM", 3: "PMG_ERR_CUDA",
                 4: "PMG_ERR_NOT_CONVERGED", 5: "PMG_ERR_NONFINITE", 6: "PMG_ERR_TIMEOUT"}
 
@@ -71,6 +74,8 @@ _SIGNATURES = {
     "pmg_prolong": (_I, [_P, _I, _P, _P, _I, _P]),
     "pmg_coarse_solve": (_I, [_P, _P, _P, _P]),
     "pmg_vcycle": (_I, [_P, _P, _P, _I, _P]),
+    "pmg_profile_reset": (_I, [_P, _I]),
+    "pmg_profile_read": (_I, [_P, _P, _P, _P, _P]),
     "pmg_last_error": (ctypes.c_char_p, []),
 }
 
@@ -210,6 +215,22 @@ class Solver:
         if raise_on_error and st != PMG_OK:
             _check(st)
         return out, info.as_dict()
+
+    # ---- profiling
+    def profile_reset(self, timing=False):
+        _check(load().pmg_profile_reset(self._h, int(bool(timing))))
+
+    def profile_read(self, full=False):
+        """{class: (launches, device ms)} since the last reset (synchronises); with
+        full=True: {class: (launches, ms, algorithmic bytes, flops)}."""
+        k = len(KERNEL_CLASSES)
+        cnt = (ctypes.c_int64 * k)()
+        ms, by, fl = (ctypes.c_double * k)(), (ctypes.c_double * k)(), (ctypes.c_double * k)()
+        v = lambda a: ctypes.cast(a, ctypes.c_void_p)
+        _check(load().pmg_profile_read(self._h, v(cnt), v(ms), v(by), v(fl)))
+        if full:
+            return {name: (cnt[i], ms[i], by[i], fl[i]) for i, name in enumerate(KERNEL_CLASSES)}
+        return {name: (cnt[i], ms[i]) for i, name in enumerate(KERNEL_CLASSES)}
 
     # ---- components
     def apply(self, x, out=None):

@@ -226,3 +226,29 @@ def test_bad_geometry_rejected():
     with pytest.raises(pmg.PmgError) as e:
         c.S.solve(c.rhs_gpu(), t(c.F["pD"]))
     assert e.value.status == pmg.PMG_ERR_INVALID
+
+
+@pytest.mark.parametrize("precision", [pmg.PMG_FP64, pmg.PMG_MIXED_FP32])
+def test_graph_and_eager_paths_agree(precision):
+    """Solves run as CUDA-graph while-loops; with kernel timing on they run eagerly with
+    event pairs.  Both issue the same kernels in the same order: identical bits."""
+    c = Case(W.tank(10, 3, 6), tol=1e-11, precision=precision)
+    b = c.rhs_gpu()
+    pD = t(c.F["pD"])
+    p1, i1 = c.S.solve(b, pD)
+    c.S.profile_reset(timing=True)
+    p2, i2 = c.S.solve(b, pD)
+    prof = c.S.profile_read()
+    c.S.profile_reset(timing=False)
+    assert torch.equal(p1, p2)
+    assert (i1["iterations"], i1["inner_iterations"]) == (i2["iterations"], i2["inner_iterations"])
+    smooth = prof["smooth64" if precision == pmg.PMG_FP64 else "smooth32"]
+    assert smooth[0] > 0 and smooth[1] > 0.0
+    # the graph path launches the same operator/multigrid kernels (its loop control adds
+    # one condition kernel per iteration to the vector class)
+    c.S.profile_reset(timing=False)
+    c.S.solve(b, pD)
+    prof_g = c.S.profile_read()
+    for k in prof:
+        if k != "vector":
+            assert prof_g[k][0] == prof[k][0], k

@@ -167,6 +167,22 @@ pmg_status pmg_coarse_solve(pmg_handle* h, const double* b_dev, double* x_dev, v
 /* z = B r: one V-cycle of the preconditioner on the finest level (Sec. 5). */
 pmg_status pmg_vcycle(pmg_handle* h, const void* r_dev, void* z_dev, int f32, void* stream);
 
+/* ---- allocation-free apply ------------------------------------------------------------ */
+/* y = A_FF x on free nodes, y = x on the surface row -- the operator of pmg_apply on the
+ * geometry eta (NX values), without a handle and without allocating device memory.  The
+ * paper has no counterpart: this is for callers that cannot allocate (a host framework
+ * that owns every device allocation, a fixed pool, a caller inside a stream capture).
+ * The geometry factors, sigma table and slab-edge exchange buffers live in one static
+ * 4 MiB device array of the library (held by every GPU that loads it, until exit); meshes
+ * needing more, about (cells_x + 1) * (cells_z * order + 1) > 500000, return
+ * PMG_ERR_INVALID.  The first call on a device sets up (constant tables, the array's device
+ * address via cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call shares the array: calls that overlap on the GPU (other streams, other
+ * threads) race and must be serialised by the caller.  Asynchronous on the stream;
+ * x and y are caller-owned device vectors of n = NX * NZ doubles. */
+pmg_status pmg_apply_noalloc(const pmg_mesh_desc* mesh, const double* eta_dev, const double* x_dev,
+                             double* y_dev, void* stream);
+
 /* ---- profiling ---------------------------------------------------------------------- */
 /* Kernel classes for launch counting and device timing. */
 enum {

@@ -861,6 +861,12 @@ pmg_status check_handle(const pmg_handle* h) {
 
 }  // namespace
 
+namespace pmg {
+// Per-order constant tables on device `dev` (used by entry points that have no handle).
+int init_constants_for_device(int dev) { return ensure_constants(dev) == PMG_OK ? 0 : 1; }
+void set_last_error(const char* msg) { g_err = msg; }
+}  // namespace pmg
+
 // =====================================================================================
 // C ABI
 // =====================================================================================

@@ -74,6 +74,7 @@ _SIGNATURES = {
     "pmg_prolong": (_I, [_P, _I, _P, _P, _I, _P]),
     "pmg_coarse_solve": (_I, [_P, _P, _P, _P]),
     "pmg_vcycle": (_I, [_P, _P, _P, _I, _P]),
+    "pmg_apply_noalloc": (_I, [ctypes.POINTER(MeshDesc), _P, _P, _P, _P]),
     "pmg_profile_reset": (_I, [_P, _I]),
     "pmg_profile_read": (_I, [_P, _P, _P, _P, _P]),
     "pmg_last_error": (ctypes.c_char_p, []),
@@ -134,6 +135,16 @@ def default_opts(**kw):
         else:
             setattr(o, k, v)
     return o
+
+
+def apply_noalloc(mesh, eta, x, out):
+    """pmg_apply_noalloc: the actual-geometry operator without a handle and without device
+    allocation (static library scratch).  mesh: MeshDesc or dict of its fields."""
+    if isinstance(mesh, dict):
+        mesh = MeshDesc(mesh.get("x0", 0.0), mesh.get("x1", 1.0), mesh.get("h", 1.0), mesh["cells_x"],
+                        mesh["cells_z"], mesh["order"], int(bool(mesh.get("periodic", False))))
+    _check(load().pmg_apply_noalloc(ctypes.byref(mesh), _ptr(eta), _ptr(x), _ptr(out), _stream()))
+    return out
 
 
 class Solver:

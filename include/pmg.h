@@ -47,10 +47,14 @@ typedef enum {
 
 /* precision of the V-cycle (preconditioner); the outer residual and result are FP64 */
 enum { PMG_FP64 = 0, PMG_MIXED_FP32 = 1, PMG_MIXED_BF16 = 2 };
-/* outer method: PCG (FP64 only), flexible CG, or preconditioned defect correction
- * x <- x + B(b - Ax) (Sec. 5.4).  Mixed precisions always run FP64 iterative refinement
- * around an inner FP32 flexible-CG solve. */
-enum { PMG_PCG = 0, PMG_FCG = 1, PMG_PDC = 2 };
+/* outer method (always FP64 on the actual-geometry operator):
+ *   PMG_PCG  preconditioned CG (with a mixed-precision V-cycle: flexible CG)
+ *   PMG_FCG  flexible CG (Polak-Ribiere beta)
+ *   PMG_PDC  preconditioned defect correction x <- x + B(b - Ax) (Sec. 5.4)
+ *   PMG_IR   FP64 iterative refinement around an inner FP32 flexible-CG solve
+ *            (mixed precision only; inner_max / inner_tol apply)
+ * With PMG_MIXED_FP32 the V-cycle B runs in FP32 on the FP32-rounded residual. */
+enum { PMG_PCG = 0, PMG_FCG = 1, PMG_PDC = 2, PMG_IR = 3 };
 /* smoother: element-block additive Schwarz (Sec. 5.3), blocks inverted by fast
  * diagonalisation (exact for the separable flat-geometry level operators) */
 enum { PMG_ASM_FDM = 0 };
@@ -69,7 +73,7 @@ typedef struct {
 
 typedef struct {
   int precision;     /* PMG_FP64 | PMG_MIXED_FP32 | PMG_MIXED_BF16                          */
-  int outer;         /* PMG_PCG | PMG_FCG | PMG_PDC                                         */
+  int outer;         /* PMG_PCG | PMG_FCG | PMG_PDC | PMG_IR                                */
   int smoother;      /* PMG_ASM_FDM                                                         */
   int precond_geom;  /* PMG_FLAT_LINEARISED                                                 */
   int overlap;       /* Schwarz overlap in node lines (0 or 1)                              */

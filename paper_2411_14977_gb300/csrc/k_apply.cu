@@ -54,21 +54,23 @@ __global__ void __launch_bounds__(256) k_curved(CurvedParams<T> p) {
   T* Wr = Ws + L * n;                       // [Nz][n][n] (ez, j, i): W_r
   T* G = Wr + L * n;                        // [n][4]
   T* SG = G + 4 * n;                        // [NZ] sigma
-  size_t red_off = (((size_t)(2 * n * NZp + 2 * L * n + 4 * n + NZ) * sizeof(T)) + 15) & ~(size_t)15;
+  T* BB = SG + NZ;                          // [n][NZp] b (MODE_RESIDUAL) or x (MODE_DOT) of the slab
+  size_t red_off = (((size_t)(3 * n * NZp + 2 * L * n + 4 * n + NZ) * sizeof(T)) + 15) & ~(size_t)15;
   double* red = reinterpret_cast<double*>(smem_raw + red_off);  // 34 doubles
   int* s_flag = reinterpret_cast<int*>(red + 34);
   T* Y = X;
 
   const int col0 = ex * P;
   // ---- load the slab, the column factors and sigma
-  for (int t = threadIdx.x; t < n * NZ; t += blockDim.x) {
-    int i = t / NZ, iz = t - i * NZ;
-    int gc = wrap_col(s, col0 + i);
-    T v = p.x[(size_t)gc * NZ + iz];
-    if (MODE != MODE_DIV && p.mask_input && iz == NZ - 1) v = T(0);
-    X[i * NZp + iz] = v;
-    if (MODE == MODE_DIV) Ur[i * NZp + iz] = p.x2[(size_t)gc * NZ + iz];
-  }
+  for_slab(n, NZ, [&](int i, int iz) {
+    size_t g = (size_t)wrap_col(s, col0 + i) * NZ + iz;
+    bool ok = !(MODE != MODE_DIV && p.mask_input && iz == NZ - 1);
+    cp_async_elem(&X[i * NZp + iz], p.x + g, ok);
+    if (MODE == MODE_DIV) cp_async_elem(&Ur[i * NZp + iz], p.x2 + g, true);
+    if (MODE == MODE_RESIDUAL) cp_async_elem(&BB[i * NZp + iz], p.b + g, true);
+    if (MODE == MODE_DOT) cp_async_elem(&BB[i * NZp + iz], p.x + g, ok);  // X is reused for Y
+  });
+  cp_async_wait_all();
   for (int t = threadIdx.x; t < 4 * n; t += blockDim.x) G[t] = p.geo[(size_t)ex * 4 * n + t];
   for (int t = threadIdx.x; t < NZ; t += blockDim.x) SG[t] = p.sigma[t];
   __syncthreads();
@@ -176,30 +178,25 @@ __global__ void __launch_bounds__(256) k_curved(CurvedParams<T> p) {
   __syncthreads();
 
   // ---- epilogue
-  auto finish = [&](int ix, int iz, T val) -> double {
+  auto finish = [&](int ix, int i, int iz, T val, Acc<T>& ac) {  // i: local column of ix
     size_t g = (size_t)ix * NZ + iz;
     bool top = iz == NZ - 1;
     if (MODE == MODE_APPLY) {
       p.y[g] = top ? p.x[g] : val;
-      return 0.0;
     } else if (MODE == MODE_RESIDUAL) {
-      T r = top ? T(0) : p.b[g] - val;
+      T r = top ? T(0) : BB[i * NZp + iz] - val;
       p.y[g] = r;
-      return (double)r * (double)r;
+      ac.fma(r, r);
     } else if (MODE == MODE_DOT) {
       T v = top ? T(0) : val;
       p.y[g] = v;
-      return (double)p.x[g] * (double)v;
+      ac.fma(BB[i * NZp + iz], v);
     } else {
       p.y[g] = top ? T(0) : val;
-      return 0.0;
     }
   };
-  double acc = 0.0;
-  for (int t = threadIdx.x; t < (P - 1) * NZ; t += blockDim.x) {
-    int i = 1 + t / NZ, iz = t % NZ;
-    acc += finish(col0 + i, iz, Y[i * NZp + iz]);
-  }
+  Acc<T> acc;
+  for_slab(P - 1, NZ, [&](int c, int iz) { finish(col0 + 1 + c, c + 1, iz, Y[(c + 1) * NZp + iz], acc); });
   const int nedges = s.periodic ? s.Nx : s.Nx + 1;
   T* eb = reinterpret_cast<T*>(p.sc.edgebuf);
 #pragma unroll 1
@@ -208,22 +205,22 @@ __global__ void __launch_bounds__(256) k_curved(CurvedParams<T> p) {
     int e = side == 0 ? ex : (s.periodic ? (ex + 1) % s.Nx : ex + 1);
     bool single = !s.periodic && (e == 0 || e == s.Nx);
     int ix = e * P;
-    double eacc = 0.0;
+    Acc<T> eacc;
     if (single) {
-      for (int iz = threadIdx.x; iz < NZ; iz += blockDim.x) eacc += finish(ix, iz, Y[i * NZp + iz]);
+      for (int iz = threadIdx.x; iz < NZ; iz += blockDim.x) finish(ix, i, iz, Y[i * NZp + iz], eacc);
     } else {
       T* buf = eb + (size_t)e * NZ;
       for (int iz = threadIdx.x; iz < NZ; iz += blockDim.x) atomic_add_t(buf + iz, Y[i * NZp + iz]);
       if (!edge_arrive(p.sc.edgecnt + e, 2, s_flag)) continue;
-      for (int iz = threadIdx.x; iz < NZ; iz += blockDim.x) eacc += finish(ix, iz, take_t(buf + iz));
+      for (int iz = threadIdx.x; iz < NZ; iz += blockDim.x) finish(ix, i, iz, take_t(buf + iz), eacc);
     }
     if (MODE == MODE_RESIDUAL || MODE == MODE_DOT) {
-      double v = block_sum(eacc, red);
+      double v = block_sum(eacc.value(), red);
       if (threadIdx.x == 0) p.sc.edgepart[e] = v;
     }
   }
   if (MODE == MODE_RESIDUAL || MODE == MODE_DOT) {
-    double v = block_sum(acc, red);
+    double v = block_sum(acc.value(), red);
     grid_reduce(p.sc, v, nedges, p.result, red, s_flag);
   }
 }
@@ -280,7 +277,7 @@ __global__ void k_rhs_source(Shape s, const double* eta, double h, double dx, do
 template <typename T>
 static size_t curved_smem(int P, int NZ, int Nz) {
   int n = P + 1, NZp = slab_pitch(NZ), L = Nz * n;
-  size_t e = (size_t)2 * n * NZp + (size_t)2 * L * n + 4 * n + NZ;
+  size_t e = (size_t)3 * n * NZp + (size_t)2 * L * n + 4 * n + NZ;
   return ((e * sizeof(T) + 15) & ~(size_t)15) + 34 * sizeof(double) + 16;
 }
 

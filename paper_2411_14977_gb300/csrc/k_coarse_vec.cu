@@ -109,17 +109,18 @@ __global__ void __launch_bounds__(VEC_THREADS) k_dot(size_t n, const TA* x, cons
                                                      int shift, Scratch sc) {
   __shared__ double red[34];
   __shared__ int s_flag;
-  double acc = 0.0;
+  Acc<TA> a;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    acc += (double)x[i] * (double)y[i];
-  acc = block_sum(acc, red);
-  if (threadIdx.x == 0) sc.partials[blockIdx.x] = acc;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) s_flag = (atomicAdd(sc.redcnt, 1u) == gridDim.x - 1);
+    a.fma(x[i], (TA)y[i]);
+  double acc = block_sum(a.value(), red);
+  if (threadIdx.x == 0) {
+    sc.partials[blockIdx.x] = acc;
+    __threadfence();
+    s_flag = (atomicAdd(sc.redcnt, 1u) == gridDim.x - 1);
+    if (s_flag) __threadfence();
+  }
   __syncthreads();
   if (!s_flag) return;
-  __threadfence();
   double v = 0.0;
   for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) v += ((volatile double*)sc.partials)[i];
   v = block_sum(v, red);
@@ -137,25 +138,28 @@ __global__ void __launch_bounds__(VEC_THREADS) k_cg_update(size_t n, T* x, T* r,
                                                            T* r_old, double* s, Scratch sc) {
   __shared__ double red[34];
   __shared__ int s_flag;
-  double alpha = s[SLOT_RZ] / s[SLOT_PAP];
-  T a = (T)alpha;
-  double acc = 0.0;
+  __shared__ T s_alpha;
+  if (threadIdx.x == 0) s_alpha = (T)(s[SLOT_RZ] / s[SLOT_PAP]);  // one FP64 division per block
+  __syncthreads();
+  const T a = s_alpha;
+  Acc<T> ac;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     T ri = r[i];
     if (r_old) r_old[i] = ri;
     x[i] += a * p[i];
     ri -= a * w[i];
     r[i] = ri;
-    acc += (double)ri * (double)ri;
+    ac.fma(ri, ri);
   }
-  acc = block_sum(acc, red);
-  if (threadIdx.x == 0) sc.partials[blockIdx.x] = acc;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) s_flag = (atomicAdd(sc.redcnt, 1u) == gridDim.x - 1);
+  double acc = block_sum(ac.value(), red);
+  if (threadIdx.x == 0) {
+    sc.partials[blockIdx.x] = acc;
+    __threadfence();
+    s_flag = (atomicAdd(sc.redcnt, 1u) == gridDim.x - 1);
+    if (s_flag) __threadfence();
+  }
   __syncthreads();
   if (!s_flag) return;
-  __threadfence();
   double v = 0.0;
   for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) v += ((volatile double*)sc.partials)[i];
   v = block_sum(v, red);
@@ -171,21 +175,23 @@ __global__ void __launch_bounds__(VEC_THREADS) k_rz(size_t n, const T* r, const 
                                                     double* s, Scratch sc) {
   __shared__ double red[34];
   __shared__ int s_flag;
-  double a1 = 0.0, a2 = 0.0;
+  Acc<T> c1, c2;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    double zi = (double)z[i];
-    a1 += (double)r[i] * zi;
-    if (r_old) a2 += (double)r_old[i] * zi;
+    T zi = z[i];
+    c1.fma(r[i], zi);
+    if (r_old) c2.fma(r_old[i], zi);
   }
-  a1 = block_sum(a1, red);
-  a2 = block_sum(a2, red);
-  if (threadIdx.x == 0) { sc.partials[2 * blockIdx.x] = a1; sc.partials[2 * blockIdx.x + 1] = a2; }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) s_flag = (atomicAdd(sc.redcnt, 1u) == gridDim.x - 1);
+  double a1 = block_sum(c1.value(), red);
+  double a2 = block_sum(c2.value(), red);
+  if (threadIdx.x == 0) {
+    sc.partials[2 * blockIdx.x] = a1;
+    sc.partials[2 * blockIdx.x + 1] = a2;
+    __threadfence();
+    s_flag = (atomicAdd(sc.redcnt, 1u) == gridDim.x - 1);
+    if (s_flag) __threadfence();
+  }
   __syncthreads();
   if (!s_flag) return;
-  __threadfence();
   double v1 = 0.0, v2 = 0.0;
   for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
     v1 += ((volatile double*)sc.partials)[2 * i];
@@ -204,25 +210,44 @@ __global__ void __launch_bounds__(VEC_THREADS) k_rz(size_t n, const T* r, const 
 // p = z + beta p with beta = RZ/RZOLD (CG) or (RZ - ZRO)/RZOLD (flexible CG); first: p = z.
 template <typename T>
 __global__ void k_p_update(size_t n, T* p, const T* z, const double* s, int flexible, int first) {
-  double beta = 0.0;
-  if (!first) beta = (flexible ? (s[SLOT_RZ] - s[SLOT_ZRO]) : s[SLOT_RZ]) / s[SLOT_RZOLD];
-  T b = (T)beta;
+  __shared__ T s_beta;
+  if (threadIdx.x == 0)
+    s_beta = first ? T(0) : (T)((flexible ? (s[SLOT_RZ] - s[SLOT_ZRO]) : s[SLOT_RZ]) / s[SLOT_RZOLD]);
+  __syncthreads();
+  const T b = s_beta;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     p[i] = first ? z[i] : z[i] + b * p[i];
 }
 
 // y = (float)(x * (1/sqrt(s[slot])))  (unit-norm scaling of a residual for the FP32 solve)
 __global__ void k_to_f32_scaled(size_t n, const double* x, float* y, const double* s, int slot) {
-  double nr = sqrt(s[slot]);
-  double inv = nr > 0.0 ? 1.0 / nr : 0.0;
+  __shared__ double s_inv;
+  if (threadIdx.x == 0) {
+    double nr = sqrt(s[slot]);
+    s_inv = nr > 0.0 ? 1.0 / nr : 0.0;
+  }
+  __syncthreads();
+  const double inv = s_inv;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     y[i] = (float)(x[i] * inv);
 }
 // x += sqrt(s[slot]) * (double)c
 __global__ void k_add_f32_scaled(size_t n, double* x, const float* c, const double* s, int slot) {
-  double nr = sqrt(s[slot]);
+  __shared__ double s_nr;
+  if (threadIdx.x == 0) s_nr = sqrt(s[slot]);
+  __syncthreads();
+  const double nr = s_nr;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     x[i] += nr * (double)c[i];
+}
+// y = (float)x and x = (double)y casts (the FP32 preconditioner inside an FP64 Krylov loop)
+__global__ void k_cast_f32(size_t n, const double* x, float* y) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = (float)x[i];
+}
+__global__ void k_cast_f64(size_t n, const float* x, double* y) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = (double)x[i];
 }
 // x += y (same type)
 template <typename T>
@@ -258,6 +283,12 @@ cudaError_t loop_cond(cudaGraphConditionalHandle hnd, const double* s, const dou
                       int max_iter, cudaStream_t st) {
   k_loop_cond<<<1, 1, 0, st>>>(hnd, s, bb, thresh2, iter, max_iter);
   return cudaGetLastError();
+}
+
+// Fill the 8-byte exchange slots with the empty marker.
+__global__ void k_arm_exchange(unsigned long long* buf, size_t n8) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n8; i += (size_t)gridDim.x * blockDim.x)
+    buf[i] = kEmpty64;
 }
 
 static unsigned vec_grid(size_t n) {
@@ -306,6 +337,14 @@ cudaError_t add_f32_scaled(size_t n, double* x, const float* c, const double* s,
   k_add_f32_scaled<<<vec_grid(n), VEC_THREADS, 0, st>>>(n, x, c, s, slot);
   return cudaGetLastError();
 }
+cudaError_t cast_f32(size_t n, const double* x, float* y, cudaStream_t st) {
+  k_cast_f32<<<vec_grid(n), VEC_THREADS, 0, st>>>(n, x, y);
+  return cudaGetLastError();
+}
+cudaError_t cast_f64(size_t n, const float* x, double* y, cudaStream_t st) {
+  k_cast_f64<<<vec_grid(n), VEC_THREADS, 0, st>>>(n, x, y);
+  return cudaGetLastError();
+}
 template <typename T>
 cudaError_t add(size_t n, T* x, const T* y, cudaStream_t st) {
   k_add<T><<<vec_grid(n), VEC_THREADS, 0, st>>>(n, x, y);
@@ -318,6 +357,17 @@ cudaError_t init_x(size_t n, int NZ, double* x, const double* x0, const double* 
   k_init_x<<<vec_grid(n), VEC_THREADS, 0, st>>>(n, NZ, x, x0, pD, status);
   return cudaGetLastError();
 }
+cudaError_t arm_exchange(void* buf, size_t n8) {
+  k_arm_exchange<<<vec_grid(n8), VEC_THREADS>>>(static_cast<unsigned long long*>(buf), n8);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return cudaDeviceSynchronize();
+}
+cudaError_t arm_exchange_f64(void* buf, size_t n8, cudaStream_t st) {
+  k_arm_exchange<<<vec_grid(n8), VEC_THREADS, 0, st>>>(static_cast<unsigned long long*>(buf), n8);
+  return cudaGetLastError();
+}
+
 cudaError_t check_finite(size_t n, const double* v, int* status, cudaStream_t st) {
   k_check_finite<<<vec_grid(n), VEC_THREADS, 0, st>>>(n, v, status);
   return cudaGetLastError();

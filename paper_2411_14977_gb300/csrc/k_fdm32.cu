@@ -1,0 +1,259 @@
+// FP32 additive-Schwarz sweep by fast diagonalisation (Sec. 5.3), the V-cycle smoother of
+// the mixed-precision path.  Same algorithm and data flow as the generic k_fdm (see
+// k_levels.cu), but the per-class eigenvectors -- which depend only on the order, the
+// overlap and the element class, not on the mesh -- sit in constant memory and are
+// addressed at compile time, so every multiply-add of the three transforms is one FFMA
+// with a constant-bank operand instead of a shared-memory load plus an FFMA.
+//   phase 1  T1 = Vx^T R        per node row (x-transform shared by the element column)
+//   phase 2  T3 = Vz (D^-1 o (Vz^T T1_window))   per (x-mode, element)
+//   phase 3  U  = Vx (sum of the covering elements' T3)   per node row
+//   phase 4  x += omega W U (pre) / omega U with W applied to r (post); slab-edge exchange
+#include "pmg_common.cuh"
+#include "pmg_kernels.h"
+
+namespace pmg {
+
+static __constant__ float cV32[fdm32_table_size()];
+
+cudaError_t init_consts_fdm32(const float* table, size_t n) {
+  if (n != (size_t)fdm32_table_size()) return cudaErrorInvalidValue;
+  return cudaMemcpyToSymbol(cV32, table, n * sizeof(float));
+}
+
+struct Fdm32Params {
+  Shape s;
+  const float* r;
+  float* x;
+  int post;
+  float omega;
+  const float* Vz;      // [4][NB][NB] z eigenvectors (boundary classes read from shared memory)
+  const float* invden;  // [4][4][NB][NB]
+  const float* wx;
+  const float* wz;
+  Scratch sc;
+};
+
+__device__ __forceinline__ int xclass32(const Shape& s, int ex) {
+  if (s.periodic) return 0;
+  return (ex == 0 ? 1 : 0) | (ex == s.Nx - 1 ? 2 : 0);
+}
+
+template <int P, int O, int XC>
+__device__ __forceinline__ void fdm32_body(const Fdm32Params& p, unsigned char* smem_raw) {
+  constexpr int NB = P + 1 + 2 * O;
+  constexpr int OFF = fdm32_offset(P, O);
+  constexpr int VX = OFF + XC * NB * NB;  // x eigenvectors of this CTA's class
+  constexpr int VZI = OFF + 4 * NB * NB;  // z eigenvectors of interior elements
+  const Shape s = p.s;
+  const int NZ = s.NZ, Nz = s.Nz, NZp = slab_pitch(NZ);
+  const int ex = blockIdx.x, col0 = ex * P;
+  float* R = reinterpret_cast<float*>(smem_raw);  // [NB][NZp]  input, later U
+  float* T1 = R + NB * NZp;                        // [NB][NZp]
+  float* T3 = T1 + NB * NZp;                       // [Nz][NB][NB] (ez, b, alpha)
+  float* VZ = T3 + Nz * NB * NB;                   // [4][NB][NB]
+  float* ID = VZ + 4 * NB * NB;                    // [4][NB][NB] (zc, alpha, beta)
+  float* XS = ID + 4 * NB * NB;                    // [NB][NZp]
+  float* WZ = XS + NB * NZp;                       // [NZ] inverse cover counts along z
+  float* WX = WZ + NZ;                             // [NB] inverse cover counts of the subdomain columns
+  size_t red_off =
+      (((size_t)(3 * NB * NZp + Nz * NB * NB + 8 * NB * NB + NZ + NB) * sizeof(float)) + 15) & ~(size_t)15;
+  int* s_flag = reinterpret_cast<int*>(smem_raw + red_off);
+
+  for_slab(NB, NZ, [&](int a, int iz) {
+    int gc = col0 - O + a;
+    bool ok = col_valid(s, gc) && iz != NZ - 1;
+    size_t g = ok ? (size_t)wrap_col(s, gc) * NZ + iz : 0;
+    cp_async_elem(&R[a * NZp + iz], p.r + g, ok);
+    cp_async_elem(&XS[a * NZp + iz], p.x + g, ok);
+  });
+  for (int t = threadIdx.x; t < 4 * NB * NB; t += blockDim.x) {
+    VZ[t] = p.Vz[t];
+    ID[t] = p.invden[XC * 4 * NB * NB + t];
+  }
+  for (int t = threadIdx.x; t < NZ; t += blockDim.x) WZ[t] = p.wz[t];
+  if (threadIdx.x < NB) {
+    int gc = col0 - O + threadIdx.x;
+    WX[threadIdx.x] = col_valid(s, gc) ? p.wx[wrap_col(s, gc)] : 0.f;
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  if (p.post) {
+    for_slab(NB, NZ, [&](int a, int iz) { R[a * NZp + iz] *= WX[a] * WZ[iz]; });
+    __syncthreads();
+  }
+  // phase 1
+  for (int iz = threadIdx.x; iz < NZ; iz += blockDim.x) {
+    float rv[NB];
+#pragma unroll
+    for (int a = 0; a < NB; ++a) rv[a] = R[a * NZp + iz];
+#pragma unroll
+    for (int al = 0; al < NB; ++al) {
+      float acc = 0.f;
+#pragma unroll
+      for (int a = 0; a < NB; ++a) acc = fmaf(cV32[VX + a * NB + al], rv[a], acc);
+      T1[al * NZp + iz] = acc;
+    }
+  }
+  __syncthreads();
+  // phase 2
+  for (int t = threadIdx.x; t < NB * Nz; t += blockDim.x) {
+    int ez = t / NB, al = t - ez * NB;
+    int zc = (ez == 0 ? 1 : 0) | (ez == Nz - 1 ? 2 : 0);
+    const float* idn = ID + (zc * NB + al) * NB;
+    float tz[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      int iz = ez * P - O + b;
+      tz[b] = (iz >= 0 && iz < NZ - 1) ? T1[al * NZp + iz] : 0.f;
+    }
+    float t2[NB];
+    float* out = T3 + (ez * NB) * NB + al;
+    if (zc == 0) {
+#pragma unroll
+      for (int be = 0; be < NB; ++be) {
+        float acc = 0.f;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) acc = fmaf(cV32[VZI + b * NB + be], tz[b], acc);
+        t2[be] = acc * idn[be];
+      }
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        float acc = 0.f;
+#pragma unroll
+        for (int be = 0; be < NB; ++be) acc = fmaf(cV32[VZI + b * NB + be], t2[be], acc);
+        out[b * NB] = acc;
+      }
+    } else {
+      const float* vz = VZ + zc * NB * NB;
+#pragma unroll
+      for (int be = 0; be < NB; ++be) {
+        float acc = 0.f;
+#pragma unroll
+        for (int b = 0; b < NB; ++b) acc = fmaf(vz[b * NB + be], tz[b], acc);
+        t2[be] = acc * idn[be];
+      }
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        float acc = 0.f;
+#pragma unroll
+        for (int be = 0; be < NB; ++be) acc = fmaf(vz[b * NB + be], t2[be], acc);
+        out[b * NB] = acc;
+      }
+    }
+  }
+  __syncthreads();
+  // phase 3
+  float* U = R;
+  for (int iz = threadIdx.x; iz < NZ; iz += blockDim.x) {
+    float sv[NB];
+#pragma unroll
+    for (int al = 0; al < NB; ++al) sv[al] = 0.f;
+    int e0 = (iz + O) / P;
+#pragma unroll
+    for (int d = -2; d <= 0; ++d) {
+      int ez = e0 + d;
+      if (ez < 0 || ez >= Nz) continue;
+      int b = iz - ez * P + O;
+      if (b < 0 || b >= NB) continue;
+      const float* src = T3 + (ez * NB + b) * NB;
+#pragma unroll
+      for (int al = 0; al < NB; ++al) sv[al] += src[al];
+    }
+#pragma unroll
+    for (int a = 0; a < NB; ++a) {
+      float acc = 0.f;
+#pragma unroll
+      for (int al = 0; al < NB; ++al) acc = fmaf(cV32[VX + a * NB + al], sv[al], acc);
+      U[a * NZp + iz] = acc;
+    }
+  }
+  __syncthreads();
+  // phase 4
+  auto upd = [&](int a, int iz, float u) {
+    if (iz == NZ - 1) return;
+    int c = wrap_col(s, col0 - O + a);
+    float w = p.post ? 1.f : WX[a] * WZ[iz];
+    p.x[(size_t)c * NZ + iz] = XS[a * NZp + iz] + p.omega * w * u;
+  };
+  constexpr int ZW = 2 * O + 1;
+  unsigned long long* xb = reinterpret_cast<unsigned long long*>(p.sc.xbuf);
+  for_slab(P - 1 - 2 * O, NZ, [&](int c, int iz) {
+    int a = 2 * O + 1 + c;
+    upd(a, iz, U[a * NZp + iz]);
+  });
+#pragma unroll 1
+  for (int side = 0; side < 2; ++side) {
+    const int a0 = side == 0 ? 0 : P;
+    const int e = side == 0 ? ex : (s.periodic ? (ex + 1) % s.Nx : ex + 1);
+    const bool shared = s.periodic || (e != 0 && e != s.Nx);
+    const int gbase = e * P - O;
+    if (!shared) {
+      for_slab(ZW, NZ, [&](int c, int iz) {
+        if (col_valid(s, gbase + c)) upd(a0 + c, iz, U[(a0 + c) * NZp + iz]);
+      });
+    } else {
+      unsigned long long* slots = xb + (size_t)e * ZW * NZ;
+      for_slab(ZW, NZ, [&](int c, int iz) {
+        float tot;
+        if (swap_exchange(slots + c * NZ + iz, U[(a0 + c) * NZp + iz], tot)) upd(a0 + c, iz, tot);
+      });
+    }
+  }
+}
+
+template <int P, int O>
+__global__ void __launch_bounds__(256) k_fdm32(Fdm32Params p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  switch (xclass32(p.s, blockIdx.x)) {
+    case 0: fdm32_body<P, O, 0>(p, smem_raw); break;
+    case 1: fdm32_body<P, O, 1>(p, smem_raw); break;
+    case 2: fdm32_body<P, O, 2>(p, smem_raw); break;
+    default: fdm32_body<P, O, 3>(p, smem_raw); break;
+  }
+}
+
+template <int P, int O>
+static cudaError_t launch_fdm32_p(const Fdm32Params& prm, cudaStream_t st) {
+  constexpr int NB = P + 1 + 2 * O;
+  int NZp = slab_pitch(prm.s.NZ);
+  size_t elems = (size_t)3 * NB * NZp + (size_t)prm.s.Nz * NB * NB + 8 * NB * NB + prm.s.NZ + NB;
+  size_t sm = ((elems * sizeof(float) + 15) & ~(size_t)15) + 16;
+  auto k = k_fdm32<P, O>;
+  static std::atomic<unsigned long long> s_mask{0};
+  cudaError_t e = ensure_max_smem(k, s_mask);
+  if (e != cudaSuccess) return e;
+  k<<<prm.s.Nx, 256, sm, st>>>(prm);
+  return cudaGetLastError();
+}
+
+cudaError_t fdm_smooth32(const FdmArgs& a, cudaStream_t st) {
+  Fdm32Params p;
+  p.s = a.s;
+  p.r = (const float*)a.r;
+  p.x = (float*)a.x;
+  p.post = a.post;
+  p.omega = (float)a.omega;
+  p.Vz = (const float*)a.Vz;
+  p.invden = (const float*)a.invden;
+  p.wx = (const float*)a.wx;
+  p.wz = (const float*)a.wz;
+  p.sc = a.sc;
+  if (a.overlap == 0) {
+    switch (a.s.P) {
+#define PMG_CASE(PP) case PP: return launch_fdm32_p<PP, 0>(p, st);
+      PMG_CASE(2) PMG_CASE(3) PMG_CASE(4) PMG_CASE(5)
+      PMG_CASE(6) PMG_CASE(7) PMG_CASE(8) PMG_CASE(9) PMG_CASE(10)
+#undef PMG_CASE
+    }
+  } else if (a.overlap == 1) {
+    switch (a.s.P) {
+#define PMG_CASE(PP) case PP: return launch_fdm32_p<PP, 1>(p, st);
+      PMG_CASE(3) PMG_CASE(4) PMG_CASE(5)
+      PMG_CASE(6) PMG_CASE(7) PMG_CASE(8) PMG_CASE(9) PMG_CASE(10)
+#undef PMG_CASE
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace pmg

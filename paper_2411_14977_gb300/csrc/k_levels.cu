@@ -46,20 +46,26 @@ __global__ void __launch_bounds__(256) k_flat(FlatParams<T> p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* X = reinterpret_cast<T*>(smem_raw);  // [2P+1][NZp], local column c <-> col0 - P + c
   T* Y = X + (2 * P + 1) * NZp;            // [n][NZp]
-  for (int t = threadIdx.x; t < (2 * P + 1) * NZ; t += blockDim.x) {
-    int c = t / NZ, iz = t - c * NZ;
-    int gc = col0 - P + c;
-    T v = T(0);
-    if ((c >= P || left) && iz != NZ - 1) v = p.x[(size_t)wrap_col(s, gc) * NZ + iz];
-    X[c * NZp + iz] = v;
-  }
+  T* MZ = Y + n * NZp;                     // [NZ] cx * assembled weights along z
+  T* MX = MZ + NZ;                         // [n]  cz * assembled weights along x (own columns)
+  T* B = MX + n;                           // [n][NZp] right-hand side of the own columns
+  const int c_begin = left ? 0 : P;
+  for_slab(2 * P + 1, NZ, [&](int c, int iz) {
+    bool ok = c >= c_begin && iz != NZ - 1;
+    cp_async_elem(&X[c * NZp + iz], p.x + (ok ? (size_t)wrap_col(s, col0 - P + c) * NZ + iz : 0), ok);
+  });
+  if (p.residual)
+    for_slab(own, NZ, [&](int i, int iz) { cp_async_elem(&B[i * NZp + iz], p.b + (size_t)(col0 + i) * NZ + iz, true); });
+  for (int t = threadIdx.x; t < NZ; t += blockDim.x) MZ[t] = p.cx * p.mZ[t];
+  if (threadIdx.x < own) MX[threadIdx.x] = p.cz * p.mX[wrap_col(s, col0 + threadIdx.x)];
+  cp_async_wait_all();
   __syncthreads();
   // x-direction stencils, one node row per thread
   for (int iz = threadIdx.x; iz < NZ; iz += blockDim.x) {
     T xo[n], xl[n];
 #pragma unroll
     for (int m = 0; m < n; ++m) { xo[m] = X[(P + m) * NZp + iz]; xl[m] = X[m * NZp + iz]; }
-    T f = p.cx * p.mZ[iz];
+    T f = MZ[iz];
 #pragma unroll
     for (int i = 0; i < n; ++i) {
       if (i == P && !last) break;
@@ -76,7 +82,7 @@ __global__ void __launch_bounds__(256) k_flat(FlatParams<T> p) {
   __syncthreads();
   // z-direction stencils, one (column, element row) per thread, owning rows [ez P, ez P + P)
   for (int t = threadIdx.x; t < own * Nz; t += blockDim.x) {
-    int i = t % own, ez = t / own;
+    int ez = t / own, i = t - ez * own;
     const T* col = X + (P + i) * NZp;
     T xv[n];
 #pragma unroll
@@ -86,7 +92,7 @@ __global__ void __launch_bounds__(256) k_flat(FlatParams<T> p) {
 #pragma unroll
       for (int m = 0; m < n; ++m) below += CT<T>::K(cT, P, P, m) * col[(ez - 1) * P + m];
     }
-    T f = p.cz * p.mX[wrap_col(s, col0 + i)];
+    T f = MX[i];
 #pragma unroll
     for (int j = 0; j < P; ++j) {
       T acc = (j == 0) ? below : T(0);
@@ -96,20 +102,20 @@ __global__ void __launch_bounds__(256) k_flat(FlatParams<T> p) {
     }
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < own * NZ; t += blockDim.x) {
-    int i = t / NZ, iz = t - i * NZ;
-    size_t g = (size_t)(col0 + i) * NZ + iz;
+  const size_t base = (size_t)col0 * NZ;
+  for_slab(own, NZ, [&](int i, int iz) {
+    size_t g = base + (size_t)i * NZ + iz;
     bool top = iz == NZ - 1;
     T v = Y[i * NZp + iz];
-    if (p.residual) p.y[g] = top ? T(0) : p.b[g] - v;
+    if (p.residual) p.y[g] = top ? T(0) : B[i * NZp + iz] - v;
     else p.y[g] = top ? p.x[g] : v;
-  }
+  });
 }
 
 template <int P, typename T>
 static cudaError_t launch_flat_p(const FlatParams<T>& prm, cudaStream_t st) {
   int NZp = slab_pitch(prm.s.NZ);
-  size_t sm = (size_t)((2 * P + 1) + (P + 1)) * NZp * sizeof(T);
+  size_t sm = ((size_t)((2 * P + 1) + 2 * (P + 1)) * NZp + prm.s.NZ + P + 1) * sizeof(T);
   auto k = k_flat<P, T>;
   static std::atomic<unsigned long long> s_mask{0};
   cudaError_t e = ensure_max_smem(k, s_mask);
@@ -181,7 +187,8 @@ __global__ void __launch_bounds__(256) k_fdm(FdmParams<T> p) {
   T* VX = T3 + Nz * NB * NB;               // [NB][NB]
   T* VZ = VX + NB * NB;                     // [4][NB][NB]
   T* ID = VZ + 4 * NB * NB;                // [4][NB][NB]
-  size_t red_off = (((size_t)(2 * NB * NZp + Nz * NB * NB + 9 * NB * NB) * sizeof(T)) + 15) & ~(size_t)15;
+  T* XS = ID + 4 * NB * NB;                // [NB][NZp] x on the subdomain columns (prefetched)
+  size_t red_off = (((size_t)(3 * NB * NZp + Nz * NB * NB + 9 * NB * NB) * sizeof(T)) + 15) & ~(size_t)15;
   int* s_flag = reinterpret_cast<int*>(smem_raw + red_off);
 
   for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) VX[t] = p.Vx[xc * NB * NB + t];
@@ -189,17 +196,23 @@ __global__ void __launch_bounds__(256) k_fdm(FdmParams<T> p) {
     VZ[t] = p.Vz[t];
     ID[t] = p.invden[xc * 4 * NB * NB + t];
   }
-  for (int t = threadIdx.x; t < NB * NZ; t += blockDim.x) {
-    int a = t / NZ, iz = t - a * NZ;
+  for_slab(NB, NZ, [&](int a, int iz) {
     int gc = col0 - O + a;
-    T v = T(0);
-    if (col_valid(s, gc) && iz != NZ - 1) {
-      int c = wrap_col(s, gc);
-      v = p.r[(size_t)c * NZ + iz];
-      if (p.post) v *= p.wx[c] * p.wz[iz];
-    }
-    R[a * NZp + iz] = v;
-  }
+    bool ok = col_valid(s, gc) && iz != NZ - 1;
+    size_t g = ok ? (size_t)wrap_col(s, gc) * NZ + iz : 0;
+    cp_async_elem(&R[a * NZp + iz], p.r + g, ok);
+    cp_async_elem(&XS[a * NZp + iz], p.x + g, ok);
+  });
+  cp_async_wait_all();
+  __syncthreads();
+  if (p.post)
+    for_slab(NB, NZ, [&](int a, int iz) {
+      int gc = col0 - O + a;
+      if (col_valid(s, gc)) {
+        int c = wrap_col(s, gc);
+        R[a * NZp + iz] *= p.wx[c] * p.wz[iz];
+      }
+    });
   __syncthreads();
   // phase 1: T1[alpha][iz] = sum_a Vx[a][alpha] R[a][iz]
   for (int iz = threadIdx.x; iz < NZ; iz += blockDim.x) {
@@ -270,17 +283,17 @@ __global__ void __launch_bounds__(256) k_fdm(FdmParams<T> p) {
   }
   __syncthreads();
   // phase 4: x update; owned interior columns directly, the two zones by exchange
-  auto upd = [&](int gc, int iz, T u) {
+  auto upd = [&](int a, int iz, T u) {  // local column a <-> global col0 - O + a
     if (iz == NZ - 1) return;
-    int c = wrap_col(s, gc);
+    int c = wrap_col(s, col0 - O + a);
     size_t g = (size_t)c * NZ + iz;
     T w = p.post ? T(1) : p.wx[c] * p.wz[iz];
-    p.x[g] += p.omega * w * u;
+    p.x[g] = XS[a * NZp + iz] + p.omega * w * u;
   };
-  for (int t = threadIdx.x; t < (P - 1 - 2 * O) * NZ; t += blockDim.x) {
-    int a = 2 * O + 1 + t / NZ, iz = t % NZ;
-    upd(col0 - O + a, iz, U[a * NZp + iz]);
-  }
+  for_slab(P - 1 - 2 * O, NZ, [&](int c, int iz) {
+    int a = 2 * O + 1 + c;
+    upd(a, iz, U[a * NZp + iz]);
+  });
   constexpr int ZW = 2 * O + 1;
   T* eb = reinterpret_cast<T*>(p.sc.edgebuf);
 #pragma unroll 1
@@ -290,21 +303,14 @@ __global__ void __launch_bounds__(256) k_fdm(FdmParams<T> p) {
     bool single = !s.periodic && (e == 0 || e == s.Nx);
     int gbase = e * P - O;
     if (single) {
-      for (int t = threadIdx.x; t < ZW * NZ; t += blockDim.x) {
-        int c = t / NZ, iz = t % NZ;
-        if (col_valid(s, gbase + c)) upd(gbase + c, iz, U[(a0 + c) * NZp + iz]);
-      }
+      for_slab(ZW, NZ, [&](int c, int iz) {
+        if (col_valid(s, gbase + c)) upd(a0 + c, iz, U[(a0 + c) * NZp + iz]);
+      });
     } else {
       T* buf = eb + (size_t)e * ZW * NZ;
-      for (int t = threadIdx.x; t < ZW * NZ; t += blockDim.x) {
-        int c = t / NZ, iz = t % NZ;
-        atomic_add_t(buf + t, U[(a0 + c) * NZp + iz]);
-      }
+      for_slab(ZW, NZ, [&](int c, int iz) { atomic_add_t(buf + c * NZ + iz, U[(a0 + c) * NZp + iz]); });
       if (!edge_arrive(p.sc.edgecnt + e, 2, s_flag)) continue;
-      for (int t = threadIdx.x; t < ZW * NZ; t += blockDim.x) {
-        int c = t / NZ, iz = t % NZ;
-        upd(gbase + c, iz, take_t(buf + t));
-      }
+      for_slab(ZW, NZ, [&](int c, int iz) { upd(a0 + c, iz, take_t(buf + c * NZ + iz)); });
     }
   }
 }
@@ -313,7 +319,7 @@ template <int P, int O, typename T>
 static cudaError_t launch_fdm_p(const FdmParams<T>& prm, cudaStream_t st) {
   constexpr int NB = P + 1 + 2 * O;
   int NZp = slab_pitch(prm.s.NZ);
-  size_t elems = (size_t)2 * NB * NZp + (size_t)prm.s.Nz * NB * NB + 9 * NB * NB;
+  size_t elems = (size_t)3 * NB * NZp + (size_t)prm.s.Nz * NB * NB + 9 * NB * NB;
   size_t sm = ((elems * sizeof(T) + 15) & ~(size_t)15) + 16;
   auto k = k_fdm<P, O, T>;
   static std::atomic<unsigned long long> s_mask{0};
@@ -381,27 +387,25 @@ __global__ void __launch_bounds__(256) k_prolong(TransferParams<T> p) {
   T* Xc = reinterpret_cast<T*>(smem_raw);  // [nc][NZcp]
   T* Tz = Xc + nc * NZcp;                   // [nc][NZfp]
   T* Js = Tz + nc * NZfp;                   // [nf][nc]
+  T* Xf = Js + nf * nc;                     // [nf][NZfp] fine values of the own columns
+  for_slab(nc, NZc, [&](int k, int iz) { cp_async_elem(&Xc[k * NZcp + iz], p.in + (size_t)wrap_col(c, ex * Pc + k) * NZc + iz, true); });
+  for_slab(own, NZf, [&](int i, int iz) { cp_async_elem(&Xf[i * NZfp + iz], p.out + (size_t)(ex * Pf + i) * NZf + iz, true); });
   for (int t = threadIdx.x; t < nf * nc; t += blockDim.x) Js[t] = (T)p.J[t];
-  for (int t = threadIdx.x; t < nc * NZc; t += blockDim.x) {
-    int k = t / NZc, iz = t - k * NZc;
-    Xc[k * NZcp + iz] = p.in[(size_t)wrap_col(c, ex * Pc + k) * NZc + iz];
-  }
+  cp_async_wait_all();
   __syncthreads();
-  for (int t = threadIdx.x; t < nc * NZf; t += blockDim.x) {
-    int k = t / NZf, iz = t - k * NZf;
+  for_slab(nc, NZf, [&](int k, int iz) {
     int ez = min(iz / Pf, f.Nz - 1), j = iz - ez * Pf;
     T acc = T(0);
     for (int l = 0; l < nc; ++l) acc += Js[j * nc + l] * Xc[k * NZcp + ez * Pc + l];
     Tz[k * NZfp + iz] = acc;
-  }
+  });
   __syncthreads();
-  for (int t = threadIdx.x; t < own * NZf; t += blockDim.x) {
-    int i = t / NZf, iz = t - i * NZf;
-    if (iz == NZf - 1) continue;
+  for_slab(own, NZf, [&](int i, int iz) {
+    if (iz == NZf - 1) return;
     T acc = T(0);
     for (int k = 0; k < nc; ++k) acc += Js[i * nc + k] * Tz[k * NZfp + iz];
-    p.out[(size_t)(ex * Pf + i) * NZf + iz] += acc;
-  }
+    p.out[(size_t)(ex * Pf + i) * NZf + iz] = Xf[i * NZfp + iz] + acc;
+  });
 }
 
 // r_c = P^T r_f
@@ -420,17 +424,14 @@ __global__ void __launch_bounds__(256) k_restrict(TransferParams<T> p) {
   T* Sz = Rf + ncol * NZfp;                 // [ncol][NZcp]
   T* Js = Sz + ncol * NZcp;                 // [nf][nc]
   for (int t = threadIdx.x; t < nf * nc; t += blockDim.x) Js[t] = (T)p.J[t];
-  for (int t = threadIdx.x; t < ncol * NZf; t += blockDim.x) {
-    int q = t / NZf, iz = t - q * NZf;
+  for_slab(ncol, NZf, [&](int q, int iz) {
     int gc = (ex - 1) * Pf + q;
-    T v = T(0);
     bool ok = (q >= Pf || left) && (q < 2 * Pf || last) && iz != NZf - 1;
-    if (ok) v = p.in[(size_t)wrap_col(f, gc) * NZf + iz];
-    Rf[q * NZfp + iz] = v;
-  }
+    cp_async_elem(&Rf[q * NZfp + iz], p.in + (ok ? (size_t)wrap_col(f, gc) * NZf + iz : 0), ok);
+  });
+  cp_async_wait_all();
   __syncthreads();
-  for (int t = threadIdx.x; t < ncol * NZc; t += blockDim.x) {
-    int q = t / NZc, lc = t - q * NZc;
+  for_slab(ncol, NZc, [&](int q, int lc) {
     T acc = T(0);
     if (lc != NZc - 1) {
       int ez = min(lc / Pc, c.Nz - 1), l = lc - ez * Pc;
@@ -445,10 +446,9 @@ __global__ void __launch_bounds__(256) k_restrict(TransferParams<T> p) {
       }
     }
     Sz[q * NZcp + lc] = acc;
-  }
+  });
   __syncthreads();
-  for (int t = threadIdx.x; t < own * NZc; t += blockDim.x) {
-    int k = t / NZc, lc = t - k * NZc;
+  for_slab(own, NZc, [&](int k, int lc) {
     T acc = T(0);
     if (lc != NZc - 1) {
       if (k == 0) {
@@ -464,7 +464,7 @@ __global__ void __launch_bounds__(256) k_restrict(TransferParams<T> p) {
       }
     }
     p.out[(size_t)(ex * Pc + k) * NZc + lc] = acc;
-  }
+  });
 }
 
 template <typename T>
@@ -485,7 +485,7 @@ cudaError_t transfer(const TransferArgs& a, int restrict_, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     k_restrict<T><<<a.f.Nx, 256, sm, st>>>(p);
   } else {
-    size_t sm = ((size_t)nc * (NZcp + NZfp) + nf * nc) * sizeof(T) + 16;
+    size_t sm = ((size_t)nc * (NZcp + NZfp) + nf * nc + (size_t)nf * NZfp) * sizeof(T) + 16;
     static std::atomic<unsigned long long> s_mask{0};
     e = ensure_max_smem(k_prolong<T>, s_mask);
     if (e != cudaSuccess) return e;

@@ -44,6 +44,7 @@ template <> struct CT<float> {
 
 // Scratch shared by all kernels of a handle (kernels on one stream run one at a time).
 struct Scratch {
+  void* xbuf;          // [max edges][2*MAXO+1][NZ] 8-byte slots holding the empty marker
   void* edgebuf;       // [max edges][2*MAXO+1][NZ] doubles, zero between launches
   unsigned* edgecnt;   // [max edges], zero between launches
   double* partials;    // [max CTAs]
@@ -65,6 +66,63 @@ __device__ __forceinline__ bool col_valid(const Shape& s, int c) {
 }
 // Odd row pitch of a shared-memory slab (conflict-free column-parallel access).
 __host__ __device__ __forceinline__ int slab_pitch(int NZ) { return NZ | 1; }
+
+// Asynchronous global -> shared copy of one element (cp.async, Ampere and later): the
+// copies of a whole slab are in flight together instead of one load latency per element.
+// valid == false writes zero and reads nothing (src must still be a valid address).
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* smem_dst, const T* gsrc, bool valid) {
+  unsigned dst = (unsigned)__cvta_generic_to_shared(smem_dst);
+  int nbytes = valid ? (int)sizeof(T) : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(dst), "l"(gsrc), "n"(sizeof(T)),
+               "r"(nbytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Calls f(c, iz) for every (c, iz) in [0, ncols) x [0, NZ), spread over the block with
+// consecutive threads on consecutive iz (coalesced on a z-fastest slab); the flattened
+// index advances by blockDim.x per step without an integer division per element.
+template <class F>
+__device__ __forceinline__ void for_slab(int ncols, int NZ, F&& f) {
+  const int step = blockDim.x;
+  const int dc = step / NZ, dz = step - dc * NZ;
+  int c = threadIdx.x / NZ, iz = threadIdx.x - c * NZ;
+  while (c < ncols) {
+    f(c, iz);
+    c += dc;
+    iz += dz;
+    if (iz >= NZ) { iz -= NZ; ++c; }
+  }
+}
+
+// Accumulator for inner products and norms.  FP64 data: plain FP64.  FP32 data: a
+// double-float (hi, lo) sum with error-free products (fmaf) and Knuth's TwoSum, which is
+// FP64-accurate but runs on the FP32 pipe (the GB300 FP64 rate is 1/58 of its FP32
+// rate; converting every FP32 element to FP64 made these kernels FP64-bound).
+template <typename T>
+struct Acc {
+  double s = 0.0;
+  __device__ __forceinline__ void fma(T a, T b) { s += (double)a * (double)b; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct Acc<float> {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    float t = hi + x;
+    float bp = t - hi;
+    lo += (hi - (t - bp)) + (x - bp);
+    hi = t;
+  }
+  __device__ __forceinline__ void fma(float a, float b) {
+    float p = a * b;
+    float e = fmaf(a, b, -p);
+    add(p);
+    lo += e;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -95,38 +153,84 @@ __device__ __forceinline__ double take_t(double* p) {
 }
 __device__ __forceinline__ float take_t(float* p) { return atomicExch(p, 0.0f); }
 
-// Edge exchange, part 1: every thread adds its values (count n, index by callback) into
-// buf, then the block learns whether it arrived last among `contributors`.
-// Returns true in every thread of the last-arriving block.
+// Fence-free two-party exchange of one value.  A slot holds a signalling-NaN marker
+// between launches (arithmetic never produces a signalling NaN).  Each of the two
+// contributors swaps its partial in; the one that gets a non-marker value back is second:
+// it returns true with the sum in `total` (a + b == b + a, so the result does not depend
+// on which party came first) and re-arms the slot.  The partial travels inside the atomic,
+// so no memory fence or barrier is needed.
+// Slots are 8 bytes for both element types (an FP32 partial sits in the low half).
+constexpr unsigned long long kEmpty64 = 0x7FF4D00DD00DD00Dull;
+__device__ __forceinline__ bool swap_exchange(unsigned long long* slot, float v, float& total) {
+  unsigned long long old = atomicExch(slot, (unsigned long long)__float_as_uint(v));
+  if (old == kEmpty64) return false;
+  total = v + __uint_as_float((unsigned)old);
+  atomicExch(slot, kEmpty64);
+  return true;
+}
+__device__ __forceinline__ bool swap_exchange(unsigned long long* slot, double v, double& total) {
+  unsigned long long old = atomicExch(slot, (unsigned long long)__double_as_longlong(v));
+  if (old == kEmpty64) return false;
+  total = v + __longlong_as_double((long long)old);
+  atomicExch(slot, kEmpty64);
+  return true;
+}
+
+// Edge exchange: after every thread has added its values into the zeroed buffer, the
+// block learns whether it arrived last among `contributors` (true in every thread of the
+// last block).  Release/acquire by thread 0 around the ticket: the barrier orders the
+// block's adds before thread 0's fence, and fences are cumulative.
 __device__ __forceinline__ bool edge_arrive(unsigned* cnt, int contributors, int* s_flag) {
-  __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
+    __threadfence();
     unsigned t = atomicAdd(cnt, 1u);
     bool last = (int)t == contributors - 1;
-    if (last) *cnt = 0u;  // reset for the next launch
+    if (last) {
+      *cnt = 0u;  // reset for the next launch
+      __threadfence();
+    }
     *s_flag = last ? 1 : 0;
   }
   __syncthreads();
-  bool last = *s_flag != 0;
-  if (last) __threadfence();
-  return last;
+  return *s_flag != 0;
+}
+
+// Two-edge variant: after the block's adds for the edges it shares (need[k] != 0), one
+// fence and both tickets back to back; last[k] is set in every thread.  Halves the
+// serial latency of exchanging both element-edge zones of a slab.
+__device__ __forceinline__ void edge_arrive2(unsigned* cnt0, unsigned* cnt1, const bool need[2], bool last[2],
+                                             int* s_flag) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    unsigned t0 = need[0] ? atomicAdd(cnt0, 1u) : 0u;
+    unsigned t1 = need[1] ? atomicAdd(cnt1, 1u) : 0u;
+    int f = 0;
+    if (need[0] && t0 == 1u) { *cnt0 = 0u; f |= 1; }
+    if (need[1] && t1 == 1u) { *cnt1 = 0u; f |= 2; }
+    if (f) __threadfence();
+    *s_flag = f;
+  }
+  __syncthreads();
+  last[0] = (*s_flag & 1) != 0;
+  last[1] = (*s_flag & 2) != 0;
 }
 
 // Deterministic grid reduction: block b stores partials[b]; the last block sums
 // partials[0..nblocks) then edgepart[0..nedges) in index order into *out.
 __device__ __forceinline__ void grid_reduce(const Scratch& sc, double block_value, int nedges,
                                             double* out, double* red, int* s_flag) {
-  if (threadIdx.x == 0) sc.partials[blockIdx.x] = block_value;
-  __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
+    sc.partials[blockIdx.x] = block_value;
+    __threadfence();
     unsigned t = atomicAdd(sc.redcnt, 1u);
     *s_flag = (t == gridDim.x - 1) ? 1 : 0;
+    if (*s_flag) __threadfence();
   }
   __syncthreads();
   if (*s_flag == 0) return;
-  __threadfence();
   double v = 0.0;
   for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) v += ((volatile double*)sc.partials)[i];
   for (int i = threadIdx.x; i < nedges; i += blockDim.x) v += ((volatile double*)sc.edgepart)[i];

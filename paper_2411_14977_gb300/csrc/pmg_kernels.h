@@ -25,6 +25,22 @@ enum Slot {
 // Per-TU constant-table initialisers.
 cudaError_t init_consts_apply(const ConstTables* host);
 cudaError_t init_consts_levels(const ConstTables* host);
+cudaError_t init_consts_fdm32(const float* table, size_t n);
+
+// Layout of the FP32 Schwarz eigenvector table (constant memory of the FP32 smoother):
+// for every (P, O) with 2 <= P <= MAXP and O <= (P-1)/2, eight NB x NB blocks
+// (x classes 0..3, then z classes 0..3), NB = P + 1 + 2 O.
+__host__ __device__ constexpr int fdm32_offset(int P, int O) {
+  int off = 0;
+  for (int p = 2; p <= MAXP; ++p)
+    for (int o = 0; o <= MAXO; ++o) {
+      if (o > (p - 1) / 2) continue;
+      if (p == P && o == O) return off;
+      off += 8 * (p + 1 + 2 * o) * (p + 1 + 2 * o);
+    }
+  return off;
+}
+__host__ __device__ constexpr int fdm32_table_size() { return fdm32_offset(MAXP + 1, 0); }
 
 struct CurvedArgs {
   Shape s;
@@ -75,6 +91,8 @@ struct FdmArgs {
   Scratch sc;
 };
 template <typename T> cudaError_t fdm_smooth(const FdmArgs& a, cudaStream_t st);
+// FP32 sweep with the eigenvectors in constant memory (k_fdm32.cu)
+cudaError_t fdm_smooth32(const FdmArgs& a, cudaStream_t st);
 
 struct TransferArgs {
   Shape f, c;
@@ -106,8 +124,13 @@ cudaError_t p_update(size_t n, T* p, const T* z, const double* s, int flexible, 
 cudaError_t to_f32_scaled(size_t n, const double* x, float* y, const double* s, int slot, cudaStream_t st);
 cudaError_t add_f32_scaled(size_t n, double* x, const float* c, const double* s, int slot, cudaStream_t st);
 template <typename T> cudaError_t add(size_t n, T* x, const T* y, cudaStream_t st);
+cudaError_t cast_f32(size_t n, const double* x, float* y, cudaStream_t st);
+cudaError_t cast_f64(size_t n, const float* x, double* y, cudaStream_t st);
 cudaError_t init_x(size_t n, int NZ, double* x, const double* x0, const double* pD, int* status, cudaStream_t st);
 cudaError_t check_finite(size_t n, const double* v, int* status, cudaStream_t st);
+// Arm the fence-free exchange slots (pmg_common.cuh swap_exchange) with the empty marker.
+cudaError_t arm_exchange(void* buf, size_t n8);  // synchronous, at set-up
+cudaError_t arm_exchange_f64(void* buf, size_t n8, cudaStream_t st);
 cudaError_t loop_cond(cudaGraphConditionalHandle hnd, const double* s, const double* bb, double thresh2, int* iter,
                       int max_iter, cudaStream_t st);
 

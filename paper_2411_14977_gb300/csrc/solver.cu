@@ -65,6 +65,8 @@ struct DeviceGuard {
 std::mutex g_const_mu;
 std::set<int> g_const_devices;
 
+void fdm_class(int P, int O, int dir, int cls, double* V, double* lam, int& k);
+
 pmg_status ensure_constants(int dev) {
   std::lock_guard<std::mutex> lk(g_const_mu);
   if (g_const_devices.count(dev)) return PMG_OK;
@@ -90,6 +92,21 @@ pmg_status ensure_constants(int dev) {
   }
   CK(init_consts_apply(&t));
   CK(init_consts_levels(&t));
+  {
+    std::vector<float> tab(fdm32_table_size(), 0.f);
+    for (int P = 2; P <= MAXP; ++P)
+      for (int O = 0; O <= MAXO; ++O) {
+        if (O > (P - 1) / 2) continue;
+        int NB = P + 1 + 2 * O, off = fdm32_offset(P, O), k;
+        std::vector<double> V(NB * NB), lam(NB);
+        for (int dir = 0; dir < 2; ++dir)
+          for (int cls = 0; cls < 4; ++cls) {
+            fdm_class(P, O, dir, cls, V.data(), lam.data(), k);
+            for (int i = 0; i < NB * NB; ++i) tab[off + (dir * 4 + cls) * NB * NB + i] = (float)V[i];
+          }
+      }
+    CK(init_consts_fdm32(tab.data(), tab.size()));
+  }
   g_const_devices.insert(dev);
   return PMG_OK;
 }
@@ -144,6 +161,39 @@ struct Line1D {
     return s;
   }
 };
+
+// Schwarz fast-diagonalisation factors of one element class, from a canonical 1D line:
+// the subdomain of an element is its P+1 node lines plus O overlap lines of each
+// neighbour (clipped at walls; in z the surface line is Dirichlet and excluded).  The
+// factors depend only on (P, O, direction, class): class 0 interior, 1 first element
+// (wall / bottom), 2 last element (wall / surface), 3 both.  V (NB x NB, row = local
+// node, column = mode, rows of absent nodes zero) satisfies V^T M V = I, V^T K V = diag.
+void fdm_class(int P, int O, int dir, int cls, double* V, double* lam, int& k) {
+  int NB = P + 1 + 2 * O;
+  int ncell = cls == 0 ? 3 : (cls == 3 ? 1 : 2);
+  int e = (cls == 0 || cls == 2) ? 1 : 0;
+  Line1D line(P, ncell, 0);
+  int last = line.n - 1 - (dir == 1 ? 1 : 0);
+  std::vector<int> loc, glob;
+  for (int a = 0; a < NB; ++a) {
+    int g = e * P - O + a;
+    if (g < 0 || g > last) continue;
+    loc.push_back(a);
+    glob.push_back(g);
+  }
+  k = (int)glob.size();
+  std::vector<double> K(k * k), M(k), Vk, lk;
+  for (int i = 0; i < k; ++i) {
+    M[i] = line.M(glob[i]);
+    for (int j = 0; j < k; ++j) K[i * k + j] = line.K(glob[i], glob[j]);
+  }
+  gen_eig_diag(k, K, M, Vk, lk);
+  for (int i = 0; i < NB * NB; ++i) V[i] = 0.0;
+  for (int i = 0; i < NB; ++i) lam[i] = 0.0;
+  for (int i = 0; i < k; ++i)
+    for (int a = 0; a < k; ++a) V[loc[i] * NB + a] = Vk[i * k + a];
+  for (int a = 0; a < k; ++a) lam[a] = lk[a];
+}
 
 template <typename T>
 T* upload(const std::vector<double>& v, std::vector<void*>& allocs, cudaError_t& err) {
@@ -319,7 +369,6 @@ pmg_status build_level(pmg_handle* h, int l) {
   std::vector<double> lamx(4 * NB, 0.0), lamz(4 * NB, 0.0);
   int kx[4] = {0, 0, 0, 0}, kz[4] = {0, 0, 0, 0};  // eigenpairs per class (modes >= k are padding)
   std::vector<double> wx(L.s.NX, 0.0), wz(L.s.NZ, 0.0);
-  // x classes
   auto xsub = [&](int ex, std::vector<int>& loc, std::vector<int>& glob) {
     loc.clear(); glob.clear();
     for (int a = 0; a < NB; ++a) {
@@ -338,38 +387,10 @@ pmg_status build_level(pmg_handle* h, int l) {
       glob.push_back(g);
     }
   };
-  auto fill_class = [&](const Line1D& line, const std::vector<int>& loc, const std::vector<int>& glob,
-                        double* V, double* lam, int& kcount) {
-    int k = (int)glob.size();
-    std::vector<double> K(k * k), M(k), Vk, lk;
-    for (int i = 0; i < k; ++i) {
-      M[i] = line.M(glob[i]);
-      for (int j = 0; j < k; ++j) K[i * k + j] = line.K(glob[i], glob[j]);
-    }
-    gen_eig_diag(k, K, M, Vk, lk);
-    for (int i = 0; i < k; ++i)
-      for (int a = 0; a < k; ++a) V[loc[i] * NB + a] = Vk[i * k + a];
-    for (int a = 0; a < k; ++a) lam[a] = lk[a];
-    kcount = k;
-  };
   std::vector<int> loc, glob;
   for (int cls = 0; cls < 4; ++cls) {
-    int ex = -1;
-    if (m.periodic_x) { if (cls == 0) ex = 0; }
-    else {
-      int Nx = m.cells_x;
-      if (cls == 0 && Nx >= 3) ex = 1;
-      if (cls == 1 && Nx >= 2) ex = 0;
-      if (cls == 2 && Nx >= 2) ex = Nx - 1;
-      if (cls == 3 && Nx == 1) ex = 0;
-    }
-    if (ex >= 0) { xsub(ex, loc, glob); fill_class(lx, loc, glob, &Vx[cls * NB * NB], &lamx[cls * NB], kx[cls]); }
-    int Nz = m.cells_z, ez = -1;
-    if (cls == 0 && Nz >= 3) ez = 1;
-    if (cls == 1 && Nz >= 2) ez = 0;
-    if (cls == 2 && Nz >= 2) ez = Nz - 1;
-    if (cls == 3 && Nz == 1) ez = 0;
-    if (ez >= 0) { zsub(ez, loc, glob); fill_class(lz, loc, glob, &Vz[cls * NB * NB], &lamz[cls * NB], kz[cls]); }
+    fdm_class(p, O, 0, cls, &Vx[cls * NB * NB], &lamx[cls * NB], kx[cls]);
+    fdm_class(p, O, 1, cls, &Vz[cls * NB * NB], &lamz[cls * NB], kz[cls]);
   }
   std::vector<double> invden(16 * NB * NB, 0.0);
   for (int xc = 0; xc < 4; ++xc)
@@ -474,7 +495,8 @@ pmg_status level_fdm(pmg_handle* h, int l, const void* r, void* x, int post, cud
   double NL = (double)L.s.NX * L.s.NZ, E = (double)L.s.Nx * L.s.Nz;
   double NB = L.s.P + 1 + 2 * L.overlap;
   Cost c{3.0 * NL * sizeof(T), E * 2.0 * (2.0 * L.s.P * NB * NB + 2.0 * NB * NB * NB)};
-  return launch(h, PI<T> ? PMG_K_SMOOTH32 : PMG_K_SMOOTH64, 1, st, c, [&] { return fdm_smooth<T>(a, st); });
+  return launch(h, PI<T> ? PMG_K_SMOOTH32 : PMG_K_SMOOTH64, 1, st, c,
+                [&] { return PI<T> ? fdm_smooth32(a, st) : fdm_smooth<T>(a, st); });
 }
 
 // nu sweeps on A_l x = b (x updated); x_zero: x is known to be zero on entry
@@ -655,13 +677,24 @@ pmg_status run_loop(pmg_handle* h, pmg_handle::Loop& L, int which, cudaStream_t 
   return PMG_OK;
 }
 
+// z = B r for the FP64 Krylov loop: the FP64 V-cycle, or the FP32 V-cycle on the
+// FP32-rounded residual (mixed precision).
+pmg_status precondition64(pmg_handle* h, cudaStream_t st) {
+  size_t N = h->N;
+  if (h->opts.precision == PMG_FP64) return vcycle<double>(h, 0, h->r, h->z, st);
+  CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{12.0 * N, 0.0}, [&] { return cast_f32(N, h->r, h->r32, st); }));
+  CKS(vcycle<float>(h, 0, h->r32, h->z32, st));
+  return launch(h, PMG_K_VECTOR, 1, st, Cost{12.0 * N, 0.0}, [&] { return cast_f64(N, h->z32, h->z, st); });
+}
+
 // FP64 PCG / flexible CG iteration sequence (first: p = z instead of the beta update).
+// A mixed-precision V-cycle is not exactly linear, so it always runs as flexible CG.
 pmg_status cg64_step(pmg_handle* h, bool first, cudaStream_t st, cudaGraphConditionalHandle hc) {
   size_t N = h->N;
   double* s = h->scal + GROUP_OUTER;
-  int flexible = h->opts.outer == PMG_FCG;
+  int flexible = h->opts.outer == PMG_FCG || h->opts.precision != PMG_FP64;
   if (first) CK(cudaMemsetAsync(h->d_iter, 0, sizeof(int), st));
-  CKS(vcycle<double>(h, 0, h->r, h->z, st));
+  CKS(precondition64(h, st));
   const double* ro = (flexible && !first) ? h->rold : nullptr;
   CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{3.0 * N * 8, 4.0 * N}, [&] { return rz<double>(N, h->r, h->z, ro, s, h->sc, st); }));
   CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{3.0 * N * 8, 2.0 * N}, [&] { return p_update<double>(N, h->p, h->z, s, flexible, first ? 1 : 0, st); }));
@@ -749,7 +782,7 @@ pmg_status solve_krylov64(pmg_handle* h, const double* b, pmg_solve_info* info, 
   size_t N = h->N;
   double* s = h->scal + GROUP_OUTER;
   const double tol2 = h->opts.tol * h->opts.tol;
-  int flexible = h->opts.outer == PMG_FCG;
+  int flexible = h->opts.outer == PMG_FCG || h->opts.precision != PMG_FP64;
   double bb = h->scal_host[SLOT_BB];
   int it = 0;
   bool restart = true;
@@ -759,7 +792,7 @@ pmg_status solve_krylov64(pmg_handle* h, const double* b, pmg_solve_info* info, 
   }
   while (it < h->opts.max_iter) {
     if (restart) {
-      CKS(vcycle<double>(h, 0, h->r, h->z, st));
+      CKS(precondition64(h, st));
       CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{3.0 * N * 8, 4.0 * N}, [&] { return rz<double>(N, h->r, h->z, nullptr, s, h->sc, st); }));
       CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{3.0 * N * 8, 2.0 * N}, [&] { return p_update<double>(N, h->p, h->z, s, 0, 1, st); }));
       restart = false;
@@ -778,7 +811,7 @@ pmg_status solve_krylov64(pmg_handle* h, const double* b, pmg_solve_info* info, 
       restart = true;
       continue;
     }
-    CKS(vcycle<double>(h, 0, h->r, h->z, st));
+    CKS(precondition64(h, st));
     CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{3.0 * N * 8, 4.0 * N}, [&] { return rz<double>(N, h->r, h->z, flexible ? h->rold : nullptr, s, h->sc, st); }));
     CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{3.0 * N * 8, 2.0 * N}, [&] { return p_update<double>(N, h->p, h->z, s, flexible, 0, st); }));
   }
@@ -905,7 +938,9 @@ pmg_status pmg_create(const pmg_mesh_desc* mesh, const pmg_opts* opts, pmg_handl
   if (m.periodic_x && (m.cells_x < 3 || (m.cells_x & (m.cells_x - 1))))
     return fail(PMG_ERR_INVALID, "periodic_x needs cells_x >= 3 and a power of two");
   if (o.precision < 0 || o.precision > PMG_MIXED_FP32) return fail(PMG_ERR_INVALID, "unsupported precision");
-  if (o.outer < PMG_PCG || o.outer > PMG_PDC) return fail(PMG_ERR_INVALID, "bad outer method");
+  if (o.outer < PMG_PCG || o.outer > PMG_IR) return fail(PMG_ERR_INVALID, "bad outer method");
+  if (o.outer == PMG_IR && o.precision == PMG_FP64)
+    return fail(PMG_ERR_INVALID, "iterative refinement needs a mixed precision");
   if (o.smoother != PMG_ASM_FDM || o.precond_geom != PMG_FLAT_LINEARISED)
     return fail(PMG_ERR_INVALID, "unsupported smoother or preconditioner geometry");
   if (o.overlap < 0 || o.overlap > MAXO || o.nu < 1 || !(o.omega > 0) || !(o.tol > 0) || o.max_iter < 1 ||
@@ -997,6 +1032,9 @@ pmg_status pmg_create(const pmg_mesh_desc* mesh, const pmg_opts* opts, pmg_handl
   size_t ebuf = nedges * (2 * MAXO + 1) * (size_t)F.NZ;
   h->sc.edgebuf = h->alloc<double>(ebuf, e);
   if (e != cudaSuccess) return bail(fail(PMG_ERR_OOM, "device allocation failed"));
+  h->sc.xbuf = h->alloc<double>(ebuf, e);
+  if (e != cudaSuccess) return bail(fail(PMG_ERR_OOM, "device allocation failed"));
+  if (arm_exchange(h->sc.xbuf, ebuf) != cudaSuccess) return bail(fail(PMG_ERR_CUDA, "exchange init failed"));
   ALLOC(h->sc.edgecnt, unsigned, nedges);
   ALLOC(h->sc.partials, double, std::max<size_t>(1024, 2 * (size_t)m.cells_x + 8));
   ALLOC(h->sc.edgepart, double, nedges);
@@ -1189,10 +1227,10 @@ pmg_status pmg_solve(pmg_handle* h, const double* b, const double* pD, const dou
   } else if (bb > 0.0) {
     pmg_status s;
     if (h->opts.outer == PMG_PDC) s = solve_pdc(h, b, &loc, st);
-    else if (h->opts.precision == PMG_FP64)
-      s = h->timing ? solve_krylov64(h, b, &loc, st) : solve_krylov64_graph(h, b, &loc, st);
-    else
+    else if (h->opts.outer == PMG_IR)
       s = h->timing ? solve_refine(h, b, &loc, st) : solve_refine_graph(h, b, &loc, st);
+    else
+      s = h->timing ? solve_krylov64(h, b, &loc, st) : solve_krylov64_graph(h, b, &loc, st);
     if (s != PMG_OK) result = s;
     // final true residual
     CKS(outer_residual(h, b, SLOT_RR64, st));

@@ -13,7 +13,7 @@ from . import build as _build
 PMG_OK, PMG_ERR_INVALID, PMG_ERR_OOM, PMG_ERR_CUDA = 0, 1, 2, 3
 PMG_ERR_NOT_CONVERGED, PMG_ERR_NONFINITE, PMG_ERR_TIMEOUT = 4, 5, 6
 PMG_FP64, PMG_MIXED_FP32, PMG_MIXED_BF16 = 0, 1, 2
-PMG_PCG, PMG_FCG, PMG_PDC = 0, 1, 2
+PMG_PCG, PMG_FCG, PMG_PDC, PMG_IR = 0, 1, 2, 3
 PMG_ASM_FDM = 0
 PMG_FLAT_LINEARISED = 1
 

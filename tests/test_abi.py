@@ -49,6 +49,8 @@ def test_default_opts():
     (dict(), dict(nu=0), "options"),
     (dict(), dict(overlap=2), "options"),
     (dict(), dict(precision=7), "precision"),
+    (dict(), dict(outer=3), "refinement needs a mixed precision"),
+    (dict(), dict(outer=4), "outer"),
     (dict(), dict(nlevels=4, levels=[4, 2, 2, 1]), "decrease"),
     (dict(), dict(nlevels=2, levels=[4, 2]), "order to 1"),
 ])

@@ -159,6 +159,7 @@ SOLVE_CASES = ["tank12x3p6", "cfg1", "periodic8x3p5", "tank6x2p8", "tank5x1p4_nz
 @pytest.mark.parametrize("name", SOLVE_CASES)
 @pytest.mark.parametrize("variant", [dict(), dict(outer=pmg.PMG_FCG), dict(outer=pmg.PMG_PDC),
                                      dict(precision=pmg.PMG_MIXED_FP32),
+                                     dict(precision=pmg.PMG_MIXED_FP32, outer=pmg.PMG_IR),
                                      dict(precision=pmg.PMG_MIXED_FP32, outer=pmg.PMG_PDC)])
 def test_solve_matches_direct(name, variant):
     w = CASES[name]()
@@ -228,11 +229,12 @@ def test_bad_geometry_rejected():
     assert e.value.status == pmg.PMG_ERR_INVALID
 
 
-@pytest.mark.parametrize("precision", [pmg.PMG_FP64, pmg.PMG_MIXED_FP32])
-def test_graph_and_eager_paths_agree(precision):
+@pytest.mark.parametrize("precision,outer", [(pmg.PMG_FP64, pmg.PMG_PCG), (pmg.PMG_MIXED_FP32, pmg.PMG_PCG),
+                                             (pmg.PMG_MIXED_FP32, pmg.PMG_IR)])
+def test_graph_and_eager_paths_agree(precision, outer):
     """Solves run as CUDA-graph while-loops; with kernel timing on they run eagerly with
     event pairs.  Both issue the same kernels in the same order: identical bits."""
-    c = Case(W.tank(10, 3, 6), tol=1e-11, precision=precision)
+    c = Case(W.tank(10, 3, 6), tol=1e-11, precision=precision, outer=outer)
     b = c.rhs_gpu()
     pD = t(c.F["pD"])
     p1, i1 = c.S.solve(b, pD)

@@ -171,6 +171,33 @@ pmg_status pmg_coarse_solve(pmg_handle* h, const double* b_dev, double* x_dev, v
 /* z = B r: one V-cycle of the preconditioner on the finest level (Sec. 5). */
 pmg_status pmg_vcycle(pmg_handle* h, const void* r_dev, void* z_dev, int f32, void* stream);
 
+/* ---- batches of independent problems --------------------------------------------------- */
+/* n independent tanks (each its own mesh, order and workspace), solved together: every
+ * problem runs its own device-side Krylov loop (a CUDA graph with a while node) on its
+ * own stream forked from the caller's stream, so the problems' kernels share the GPU
+ * concurrently; the host synchronises three times per batch solve, not per iteration.
+ * opts apply to every problem; pmg_batch_create runs pmg_autotune on every problem. */
+typedef struct pmg_batch pmg_batch;
+pmg_status pmg_batch_create(int n, const pmg_mesh_desc* meshes, const pmg_opts* opts, pmg_batch** out);
+pmg_status pmg_batch_destroy(pmg_batch* b);
+/* The handle of problem i (owned by the batch): per-problem geometry and right-hand
+ * sides are set through it with the single-problem calls. */
+pmg_status pmg_batch_handle(pmg_batch* b, int i, pmg_handle** h);
+/* Solve every problem: b[i], p_dirichlet[i], p_out[i] are device vectors of problem i
+ * (x0 = 0).  infos (n entries) may be NULL.  Returns the first non-OK status (each
+ * problem's own status is in its info).  Synchronises the caller's stream. */
+pmg_status pmg_batch_solve(pmg_batch* b, const double* const* b_dev, const double* const* p_dirichlet_dev,
+                           double* const* p_out_dev, pmg_solve_info* infos, void* stream);
+
+/* ---- autotuner ------------------------------------------------------------------------- */
+/* Times the candidate CTA sizes (64, 128, 256 threads) of the level operator, the
+ * Schwarz sweep and the actual-geometry operator on every level of h (CUDA-event timing
+ * of graph-captured launches) and keeps the fastest per kernel and shape for h.  The
+ * choices are also remembered per (kernel, order, rows) for handles created later in the
+ * process.  Synchronous; changes no results (the kernels are correct for any of the
+ * candidate sizes). */
+pmg_status pmg_autotune(pmg_handle* h);
+
 /* ---- allocation-free apply ------------------------------------------------------------ */
 /* y = A_FF x on free nodes, y = x on the surface row -- the operator of pmg_apply on the
  * geometry eta (NX values), without a handle and without allocating device memory.  The

@@ -282,20 +282,20 @@ static size_t curved_smem(int P, int NZ, int Nz) {
 }
 
 template <int P, typename T, int MODE>
-static cudaError_t launch_curved_p(const CurvedParams<T>& prm, cudaStream_t st) {
+static cudaError_t launch_curved_p(const CurvedParams<T>& prm, int threads, cudaStream_t st) {
   size_t sm = curved_smem<T>(P, prm.s.NZ, prm.s.Nz);
   auto k = k_curved<P, T, MODE>;
   static std::atomic<unsigned long long> s_mask{0};
   cudaError_t e = ensure_max_smem(k, s_mask);
   if (e != cudaSuccess) return e;
-  k<<<prm.s.Nx, 256, sm, st>>>(prm);
+  k<<<prm.s.Nx, threads, sm, st>>>(prm);
   return cudaGetLastError();
 }
 
 template <typename T, int MODE>
-static cudaError_t launch_curved(const CurvedParams<T>& prm, cudaStream_t st) {
+static cudaError_t launch_curved(const CurvedParams<T>& prm, int threads, cudaStream_t st) {
   switch (prm.s.P) {
-#define PMG_CASE(PP) case PP: return launch_curved_p<PP, T, MODE>(prm, st);
+#define PMG_CASE(PP) case PP: return launch_curved_p<PP, T, MODE>(prm, threads, st);
     PMG_CASE(1) PMG_CASE(2) PMG_CASE(3) PMG_CASE(4) PMG_CASE(5)
     PMG_CASE(6) PMG_CASE(7) PMG_CASE(8) PMG_CASE(9) PMG_CASE(10)
 #undef PMG_CASE
@@ -317,11 +317,12 @@ cudaError_t curved_op(const CurvedArgs& a, cudaStream_t st) {
   p.mask_input = a.mask_input;
   p.result = a.result;
   p.sc = a.sc;
+  int thr = (a.threads >= 32 && a.threads <= 256) ? a.threads : 256;
   switch (a.mode) {
-    case MODE_APPLY: return launch_curved<T, MODE_APPLY>(p, st);
-    case MODE_RESIDUAL: return launch_curved<T, MODE_RESIDUAL>(p, st);
-    case MODE_DOT: return launch_curved<T, MODE_DOT>(p, st);
-    case MODE_DIV: return launch_curved<T, MODE_DIV>(p, st);
+    case MODE_APPLY: return launch_curved<T, MODE_APPLY>(p, thr, st);
+    case MODE_RESIDUAL: return launch_curved<T, MODE_RESIDUAL>(p, thr, st);
+    case MODE_DOT: return launch_curved<T, MODE_DOT>(p, thr, st);
+    case MODE_DIV: return launch_curved<T, MODE_DIV>(p, thr, st);
   }
   return cudaErrorInvalidValue;
 }

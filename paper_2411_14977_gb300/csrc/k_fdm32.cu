@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(256) k_fdm32(Fdm32Params p) {
 }
 
 template <int P, int O>
-static cudaError_t launch_fdm32_p(const Fdm32Params& prm, cudaStream_t st) {
+static cudaError_t launch_fdm32_p(const Fdm32Params& prm, int threads, cudaStream_t st) {
   constexpr int NB = P + 1 + 2 * O;
   int NZp = slab_pitch(prm.s.NZ);
   size_t elems = (size_t)3 * NB * NZp + (size_t)prm.s.Nz * NB * NB + 8 * NB * NB + prm.s.NZ + NB;
@@ -222,7 +222,7 @@ static cudaError_t launch_fdm32_p(const Fdm32Params& prm, cudaStream_t st) {
   static std::atomic<unsigned long long> s_mask{0};
   cudaError_t e = ensure_max_smem(k, s_mask);
   if (e != cudaSuccess) return e;
-  k<<<prm.s.Nx, 256, sm, st>>>(prm);
+  k<<<prm.s.Nx, threads, sm, st>>>(prm);
   return cudaGetLastError();
 }
 
@@ -238,16 +238,17 @@ cudaError_t fdm_smooth32(const FdmArgs& a, cudaStream_t st) {
   p.wx = (const float*)a.wx;
   p.wz = (const float*)a.wz;
   p.sc = a.sc;
+  int thr = (a.threads >= 32 && a.threads <= 256) ? a.threads : 256;
   if (a.overlap == 0) {
     switch (a.s.P) {
-#define PMG_CASE(PP) case PP: return launch_fdm32_p<PP, 0>(p, st);
+#define PMG_CASE(PP) case PP: return launch_fdm32_p<PP, 0>(p, thr, st);
       PMG_CASE(2) PMG_CASE(3) PMG_CASE(4) PMG_CASE(5)
       PMG_CASE(6) PMG_CASE(7) PMG_CASE(8) PMG_CASE(9) PMG_CASE(10)
 #undef PMG_CASE
     }
   } else if (a.overlap == 1) {
     switch (a.s.P) {
-#define PMG_CASE(PP) case PP: return launch_fdm32_p<PP, 1>(p, st);
+#define PMG_CASE(PP) case PP: return launch_fdm32_p<PP, 1>(p, thr, st);
       PMG_CASE(3) PMG_CASE(4) PMG_CASE(5)
       PMG_CASE(6) PMG_CASE(7) PMG_CASE(8) PMG_CASE(9) PMG_CASE(10)
 #undef PMG_CASE

@@ -113,14 +113,14 @@ __global__ void __launch_bounds__(256) k_flat(FlatParams<T> p) {
 }
 
 template <int P, typename T>
-static cudaError_t launch_flat_p(const FlatParams<T>& prm, cudaStream_t st) {
+static cudaError_t launch_flat_p(const FlatParams<T>& prm, int threads, cudaStream_t st) {
   int NZp = slab_pitch(prm.s.NZ);
   size_t sm = ((size_t)((2 * P + 1) + 2 * (P + 1)) * NZp + prm.s.NZ + P + 1) * sizeof(T);
   auto k = k_flat<P, T>;
   static std::atomic<unsigned long long> s_mask{0};
   cudaError_t e = ensure_max_smem(k, s_mask);
   if (e != cudaSuccess) return e;
-  k<<<prm.s.Nx, 256, sm, st>>>(prm);
+  k<<<prm.s.Nx, threads, sm, st>>>(prm);
   return cudaGetLastError();
 }
 
@@ -136,8 +136,9 @@ cudaError_t flat_op(const FlatArgs& a, cudaStream_t st) {
   p.mX = (const T*)a.mX;
   p.mZ = (const T*)a.mZ;
   p.residual = a.residual;
+  int thr = (a.threads >= 32 && a.threads <= 256) ? a.threads : 256;
   switch (a.s.P) {
-#define PMG_CASE(PP) case PP: return launch_flat_p<PP, T>(p, st);
+#define PMG_CASE(PP) case PP: return launch_flat_p<PP, T>(p, thr, st);
     PMG_CASE(1) PMG_CASE(2) PMG_CASE(3) PMG_CASE(4) PMG_CASE(5)
     PMG_CASE(6) PMG_CASE(7) PMG_CASE(8) PMG_CASE(9) PMG_CASE(10)
 #undef PMG_CASE
@@ -316,7 +317,7 @@ __global__ void __launch_bounds__(256) k_fdm(FdmParams<T> p) {
 }
 
 template <int P, int O, typename T>
-static cudaError_t launch_fdm_p(const FdmParams<T>& prm, cudaStream_t st) {
+static cudaError_t launch_fdm_p(const FdmParams<T>& prm, int threads, cudaStream_t st) {
   constexpr int NB = P + 1 + 2 * O;
   int NZp = slab_pitch(prm.s.NZ);
   size_t elems = (size_t)3 * NB * NZp + (size_t)prm.s.Nz * NB * NB + 9 * NB * NB;
@@ -325,7 +326,7 @@ static cudaError_t launch_fdm_p(const FdmParams<T>& prm, cudaStream_t st) {
   static std::atomic<unsigned long long> s_mask{0};
   cudaError_t e = ensure_max_smem(k, s_mask);
   if (e != cudaSuccess) return e;
-  k<<<prm.s.Nx, 256, sm, st>>>(prm);
+  k<<<prm.s.Nx, threads, sm, st>>>(prm);
   return cudaGetLastError();
 }
 
@@ -343,16 +344,17 @@ cudaError_t fdm_smooth(const FdmArgs& a, cudaStream_t st) {
   p.wx = (const T*)a.wx;
   p.wz = (const T*)a.wz;
   p.sc = a.sc;
+  int thr = (a.threads >= 32 && a.threads <= 256) ? a.threads : 256;
   if (a.overlap == 0) {
     switch (a.s.P) {
-#define PMG_CASE(PP) case PP: return launch_fdm_p<PP, 0, T>(p, st);
+#define PMG_CASE(PP) case PP: return launch_fdm_p<PP, 0, T>(p, thr, st);
       PMG_CASE(2) PMG_CASE(3) PMG_CASE(4) PMG_CASE(5)
       PMG_CASE(6) PMG_CASE(7) PMG_CASE(8) PMG_CASE(9) PMG_CASE(10)
 #undef PMG_CASE
     }
   } else if (a.overlap == 1) {
     switch (a.s.P) {
-#define PMG_CASE(PP) case PP: return launch_fdm_p<PP, 1, T>(p, st);
+#define PMG_CASE(PP) case PP: return launch_fdm_p<PP, 1, T>(p, thr, st);
       PMG_CASE(3) PMG_CASE(4) PMG_CASE(5)
       PMG_CASE(6) PMG_CASE(7) PMG_CASE(8) PMG_CASE(9) PMG_CASE(10)
 #undef PMG_CASE
@@ -483,13 +485,13 @@ cudaError_t transfer(const TransferArgs& a, int restrict_, cudaStream_t st) {
     static std::atomic<unsigned long long> s_mask{0};
     e = ensure_max_smem(k_restrict<T>, s_mask);
     if (e != cudaSuccess) return e;
-    k_restrict<T><<<a.f.Nx, 256, sm, st>>>(p);
+    k_restrict<T><<<a.f.Nx, (a.threads >= 32 && a.threads <= 256) ? a.threads : 256, sm, st>>>(p);
   } else {
     size_t sm = ((size_t)nc * (NZcp + NZfp) + nf * nc + (size_t)nf * NZfp) * sizeof(T) + 16;
     static std::atomic<unsigned long long> s_mask{0};
     e = ensure_max_smem(k_prolong<T>, s_mask);
     if (e != cudaSuccess) return e;
-    k_prolong<T><<<a.f.Nx, 256, sm, st>>>(p);
+    k_prolong<T><<<a.f.Nx, (a.threads >= 32 && a.threads <= 256) ? a.threads : 256, sm, st>>>(p);
   }
   return cudaGetLastError();
 }

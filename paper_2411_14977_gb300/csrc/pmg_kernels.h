@@ -55,6 +55,7 @@ struct CurvedArgs {
   int mask_input;
   double* result;
   Scratch sc;
+  int threads = 256;   // CTA size (autotuned; 64..256)
 };
 template <typename T> cudaError_t curved_op(const CurvedArgs& a, cudaStream_t st);
 template <typename T>
@@ -73,6 +74,7 @@ struct FlatArgs {
   const void* mX;
   const void* mZ;
   int residual;
+  int threads = 256;
 };
 template <typename T> cudaError_t flat_op(const FlatArgs& a, cudaStream_t st);
 
@@ -89,6 +91,7 @@ struct FdmArgs {
   const void* wx;
   const void* wz;
   Scratch sc;
+  int threads = 256;
 };
 template <typename T> cudaError_t fdm_smooth(const FdmArgs& a, cudaStream_t st);
 // FP32 sweep with the eigenvectors in constant memory (k_fdm32.cu)
@@ -99,6 +102,7 @@ struct TransferArgs {
   const void* in;
   void* out;
   const double* J;
+  int threads = 256;
 };
 template <typename T> cudaError_t transfer(const TransferArgs& a, int restrict_, cudaStream_t st);
 

@@ -14,7 +14,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <cstdlib>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <set>
 #include <string>
 #include <vector>
@@ -219,6 +222,7 @@ struct LevelDev {
   void* wx[2]{};
   void* wz[2]{};
   double* J = nullptr;  // transfer from level l+1 (coarse) to this level
+  int thr_flat32 = 256, thr_fdm32 = 256, thr_xfer = 256;  // CTA sizes (autotuner)
   void* b[2]{};
   void* x[2]{};
   void* t[2]{};
@@ -228,6 +232,7 @@ struct pmg_handle {
   pmg_mesh_desc mesh{};
   pmg_opts opts{};
   int device = 0;
+  int thr_curved32 = 256;  // CTA size of the FP32 actual-geometry operator (autotuner)
   double dx = 0, dsig = 0, cx = 0, cz = 0;
   size_t N = 0, Nfree = 0;
   std::vector<int> orders;
@@ -481,7 +486,7 @@ template <typename T>
 pmg_status level_residual(pmg_handle* h, int l, const void* b, const void* x, void* y, int residual,
                           cudaStream_t st) {
   LevelDev& L = h->lv[l];
-  FlatArgs a{L.s, x, b, y, h->cx, h->cz, L.mX[PI<T>], L.mZ[PI<T>], residual};
+  FlatArgs a{L.s, x, b, y, h->cx, h->cz, L.mX[PI<T>], L.mZ[PI<T>], residual, PI<T> ? L.thr_flat32 : 256};
   double NL = (double)L.s.NX * L.s.NZ;
   Cost c{(residual ? 3.0 : 2.0) * NL * sizeof(T), NL * (4.0 * (L.s.P + 2) + 4.0)};
   return launch(h, PI<T> ? PMG_K_LEVEL32 : PMG_K_LEVEL64, 1, st, c, [&] { return flat_op<T>(a, st); });
@@ -491,7 +496,7 @@ template <typename T>
 pmg_status level_fdm(pmg_handle* h, int l, const void* r, void* x, int post, cudaStream_t st) {
   LevelDev& L = h->lv[l];
   FdmArgs a{L.s, L.overlap, r, x, post, h->opts.omega, L.Vx[PI<T>], L.Vz[PI<T>], L.invden[PI<T>],
-            L.wx[PI<T>], L.wz[PI<T>], h->sc};
+            L.wx[PI<T>], L.wz[PI<T>], h->sc, PI<T> ? L.thr_fdm32 : 256};
   double NL = (double)L.s.NX * L.s.NZ, E = (double)L.s.Nx * L.s.Nz;
   double NB = L.s.P + 1 + 2 * L.overlap;
   Cost c{3.0 * NL * sizeof(T), E * 2.0 * (2.0 * L.s.P * NB * NB + 2.0 * NB * NB * NB)};
@@ -517,7 +522,7 @@ pmg_status level_smooth(pmg_handle* h, int l, const void* b, void* x, int post, 
 
 template <typename T>
 pmg_status transfer_op(pmg_handle* h, int l, const void* in, void* out, int restrict_, cudaStream_t st) {
-  TransferArgs a{h->lv[l].s, h->lv[l + 1].s, in, out, h->lv[l].J};
+  TransferArgs a{h->lv[l].s, h->lv[l + 1].s, in, out, h->lv[l].J, h->lv[l].thr_xfer};
   double Nf = (double)h->lv[l].s.NX * h->lv[l].s.NZ, Nc = (double)h->lv[l + 1].s.NX * h->lv[l + 1].s.NZ;
   double pf = h->lv[l].s.P, pc = h->lv[l + 1].s.P;
   Cost c{(restrict_ ? Nf + Nc : 2.0 * Nf + Nc) * sizeof(T), 2.0 * (Nf * (pc + 1) + Nc * (pf + 1))};
@@ -565,6 +570,7 @@ pmg_status curved(pmg_handle* h, int mode, const void* x, const void* b, void* y
   a.mask_input = mask;
   a.result = result;
   a.sc = h->sc;
+  a.threads = PI<T> ? h->thr_curved32 : 256;
   const Shape& F = a.s;
   double N = (double)F.NX * F.NZ, E = (double)F.Nx * F.Nz, n = F.P + 1;
   Cost c{(mode == 1 ? 3.0 : 2.0) * N * sizeof(T), E * (8.0 * n * n * n + 12.0 * n * n)};
@@ -899,6 +905,133 @@ namespace pmg {
 int init_constants_for_device(int dev) { return ensure_constants(dev) == PMG_OK ? 0 : 1; }
 void set_last_error(const char* msg) { g_err = msg; }
 }  // namespace pmg
+
+
+// =====================================================================================
+// Autotuner: CTA size per kernel and shape
+// =====================================================================================
+namespace {
+
+enum { TK_FLAT32 = 0, TK_FDM32 = 1, TK_XFER = 2, TK_CURVED32 = 3 };
+const char* kTuneNames[] = {"flat32", "fdm32", "transfer", "curved32"};
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int>, int> g_tune;  // (kernel, order, rows, columns) -> threads
+bool g_tune_loaded = false;
+
+// Optional persistent cache: JSON lines {"kernel": ..., "P": .., "NZ": .., "Nx": .., "threads": ..}
+// in the file named by PMG_TUNE_CACHE.
+void tune_cache_load() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* path = std::getenv("PMG_TUNE_CACHE");
+  if (!path) return;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return;
+  char line[512];
+  while (std::fgets(line, sizeof(line), f)) {
+    char name[64];
+    int P, NZ, Nx, thr;
+    if (std::sscanf(line, "{\"kernel\": \"%63[^\"]\", \"P\": %d, \"NZ\": %d, \"Nx\": %d, \"threads\": %d}", name, &P,
+                    &NZ, &Nx, &thr) == 5)
+      for (int k = 0; k < 4; ++k)
+        if (!std::strcmp(name, kTuneNames[k])) g_tune[std::make_tuple(k, P, NZ, Nx)] = thr;
+  }
+  std::fclose(f);
+}
+void tune_cache_store(int k, int P, int NZ, int Nx, int thr) {
+  const char* path = std::getenv("PMG_TUNE_CACHE");
+  if (!path) return;
+  FILE* f = std::fopen(path, "a");
+  if (!f) return;
+  std::fprintf(f, "{\"kernel\": \"%s\", \"P\": %d, \"NZ\": %d, \"Nx\": %d, \"threads\": %d}\n", kTuneNames[k], P, NZ, Nx,
+               thr);
+  std::fclose(f);
+}
+
+// Device time per launch of `reps` graph-captured launches issued by run(threads).
+template <class Run>
+pmg_status time_launches(pmg_handle* h, Run&& run, int threads, int reps, float* us) {
+  if (!h->cap) CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+  bool timing = h->timing;
+  h->timing = false;
+  int64_t snap[PMG_K_COUNT];
+  double sb[PMG_K_COUNT], sf[PMG_K_COUNT];
+  std::memcpy(snap, h->launches, sizeof(snap));
+  std::memcpy(sb, h->bytes, sizeof(sb));
+  std::memcpy(sf, h->flops, sizeof(sf));
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+  pmg_status s = PMG_OK;
+  for (int r = 0; r < reps && s == PMG_OK; ++r) s = run(threads, h->cap);
+  cudaError_t e = cudaStreamEndCapture(h->cap, &g);
+  std::memcpy(h->launches, snap, sizeof(snap));
+  std::memcpy(h->bytes, sb, sizeof(sb));
+  std::memcpy(h->flops, sf, sizeof(sf));
+  h->timing = timing;
+  if (s != PMG_OK) { if (g) cudaGraphDestroy(g); return s; }
+  CK(e);
+  cudaGraphExec_t ge = nullptr;
+  e = cudaGraphInstantiate(&ge, g, 0);
+  cudaGraphDestroy(g);
+  CK(e);
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float ms = 0.f;
+  cudaError_t err = cudaGraphLaunch(ge, h->cap);
+  if (err == cudaSuccess) err = cudaEventRecord(e0, h->cap);
+  if (err == cudaSuccess) err = cudaGraphLaunch(ge, h->cap);
+  if (err == cudaSuccess) err = cudaEventRecord(e1, h->cap);
+  if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+  if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGraphExecDestroy(ge);
+  CK(err);
+  *us = 1000.f * ms / reps;
+  return PMG_OK;
+}
+
+template <class Run>
+pmg_status tune_one(pmg_handle* h, int kernel, int P, int NZ, Run&& run, int* out) {
+  auto key = std::make_tuple(kernel, P, NZ, h->mesh.cells_x);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_cache_load();
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) { *out = it->second; return PMG_OK; }
+  }
+  int best = 256;
+  float best_us = 1e30f;
+  for (int thr : {64, 128, 256}) {
+    float us;
+    CKS(time_launches(h, run, thr, 10, &us));
+    if (us < best_us * 0.97f) { best_us = us; best = thr; }
+  }
+  *out = best;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = best;
+  tune_cache_store(kernel, P, NZ, h->mesh.cells_x, best);
+  return PMG_OK;
+}
+
+}  // namespace
+
+// =====================================================================================
+// Batches of independent problems
+// =====================================================================================
+struct pmg_batch {
+  std::vector<pmg_handle*> h;
+  std::vector<cudaStream_t> st;
+  std::vector<cudaEvent_t> done;
+  cudaEvent_t fork = nullptr;
+  ~pmg_batch() {
+    for (cudaStream_t s : st) if (s) cudaStreamDestroy(s);
+    for (cudaEvent_t e : done) if (e) cudaEventDestroy(e);
+    if (fork) cudaEventDestroy(fork);
+    for (pmg_handle* x : h) pmg_destroy(x);
+  }
+};
 
 // =====================================================================================
 // C ABI
@@ -1279,6 +1412,180 @@ pmg_status pmg_profile_read(pmg_handle* h, int64_t* launches, double* ms, double
     if (flops) flops[k] = h->flops[k];
   }
   return PMG_OK;
+}
+
+pmg_status pmg_autotune(pmg_handle* h) {
+  CKS(check_handle(h));
+  DeviceGuard dg(h->device);
+  int nl = (int)h->lv.size();
+  for (int l = 0; l < nl; ++l) {
+    LevelDev& L = h->lv[l];
+    void* x = L.x[1];
+    void* b = L.b[1];
+    void* t = L.t[1];
+    CKS(tune_one(h, TK_FLAT32, L.order, L.s.NZ, [&](int thr, cudaStream_t cs) {
+      L.thr_flat32 = thr;
+      return level_residual<float>(h, l, b, x, t, 1, cs);
+    }, &L.thr_flat32));
+    if (l == nl - 1) continue;
+    CKS(tune_one(h, TK_FDM32, L.order * 16 + L.overlap, L.s.NZ, [&](int thr, cudaStream_t cs) {
+      L.thr_fdm32 = thr;
+      return level_fdm<float>(h, l, t, x, 0, cs);
+    }, &L.thr_fdm32));
+    LevelDev& C = h->lv[l + 1];
+    CKS(tune_one(h, TK_XFER, L.order * 16 + C.order, L.s.NZ, [&](int thr, cudaStream_t cs) {
+      L.thr_xfer = thr;
+      return transfer_op<float>(h, l, t, C.b[1], 1, cs);
+    }, &L.thr_xfer));
+  }
+  CKS(tune_one(h, TK_CURVED32, h->mesh.order, h->lv[0].s.NZ, [&](int thr, cudaStream_t cs) {
+    h->thr_curved32 = thr;
+    return curved<float>(h, 0, h->r32, nullptr, h->w32, 1, nullptr, cs);
+  }, &h->thr_curved32));
+  // graphs built before tuning keep the old sizes: rebuild on next use
+  for (pmg_handle::Loop* lp : {&h->loop64, &h->loop32})
+    if (lp->exec) { cudaGraphExecDestroy(lp->exec); lp->exec = nullptr; }
+  CK(cudaDeviceSynchronize());
+  return PMG_OK;
+}
+
+pmg_status pmg_batch_create(int n, const pmg_mesh_desc* meshes, const pmg_opts* opts, pmg_batch** out) {
+  if (!out) return fail(PMG_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || !meshes) return fail(PMG_ERR_INVALID, "need n >= 1 meshes");
+  auto* b = new (std::nothrow) pmg_batch();
+  if (!b) return fail(PMG_ERR_OOM, "host allocation failed");
+  for (int i = 0; i < n; ++i) {
+    pmg_handle* h = nullptr;
+    pmg_status s = pmg_create(&meshes[i], opts, &h);
+    if (s != PMG_OK) { delete b; return s; }
+    b->h.push_back(h);
+    s = pmg_autotune(h);
+    if (s != PMG_OK) { delete b; return s; }
+    cudaStream_t st;
+    cudaEvent_t ev;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+      delete b;
+      return fail(PMG_ERR_CUDA, "stream creation failed");
+    }
+    b->st.push_back(st);
+    b->done.push_back(ev);
+  }
+  if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) {
+    delete b;
+    return fail(PMG_ERR_CUDA, "event creation failed");
+  }
+  *out = b;
+  return PMG_OK;
+}
+
+pmg_status pmg_batch_destroy(pmg_batch* b) {
+  if (b) {
+    cudaDeviceSynchronize();
+    delete b;
+  }
+  return PMG_OK;
+}
+
+pmg_status pmg_batch_handle(pmg_batch* b, int i, pmg_handle** h) {
+  if (!b || !h || i < 0 || i >= (int)b->h.size()) return fail(PMG_ERR_INVALID, "bad batch index");
+  *h = b->h[i];
+  return PMG_OK;
+}
+
+pmg_status pmg_batch_solve(pmg_batch* B, const double* const* bv, const double* const* pdv, double* const* pout,
+                           pmg_solve_info* infos, void* stream) {
+  if (!B || !bv || !pdv || !pout) return fail(PMG_ERR_INVALID, "NULL argument");
+  int n = (int)B->h.size();
+  for (int i = 0; i < n; ++i)
+    if (!bv[i] || !pdv[i] || !pout[i]) return fail(PMG_ERR_INVALID, "NULL vector in batch");
+  auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t cs = (cudaStream_t)stream;
+  CK(cudaEventRecord(B->fork, cs));
+  std::vector<pmg_solve_info> loc(n);
+  std::vector<int> active(n, 0), total(n, 0);
+  // phase 1: inputs, lifted residual and its norm on every problem's stream
+  for (int i = 0; i < n; ++i) {
+    pmg_handle* h = B->h[i];
+    cudaStream_t st = B->st[i];
+    size_t N = h->N;
+    CK(cudaStreamWaitEvent(st, B->fork, 0));
+    CK(cudaMemsetAsync(h->status, 0, sizeof(int), st));
+    CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{8.0 * N, 0.0}, [&] { return check_finite(N, bv[i], h->status, st); }));
+    CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{24.0 * N, 0.0}, [&] { return init_x(N, h->lv[0].s.NZ, h->x, nullptr, pdv[i], h->status, st); }));
+    CKS(lifted_norm(h, bv[i], pdv[i], nullptr, st));
+    CK(cudaMemcpyAsync(h->scal_host, h->scal, SLOT_COUNT * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(h->status_host, h->status, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  }
+  for (int i = 0; i < n; ++i) CK(cudaStreamSynchronize(B->st[i]));
+  // phase 2: every problem's device-side Krylov loop, concurrently; restarts on drift
+  for (int round = 0; round < 4; ++round) {
+    int launched = 0;
+    for (int i = 0; i < n; ++i) {
+      pmg_handle* h = B->h[i];
+      double bb = h->scal_host[SLOT_BB], tol2 = h->opts.tol * h->opts.tol;
+      if (round == 0) {
+        if (h->status_host[0] || h->status_host[1] || !std::isfinite(bb)) {
+          loc[i].status = h->status_host[1] ? PMG_ERR_INVALID : PMG_ERR_NONFINITE;
+          continue;
+        }
+        active[i] = bb > 0.0 && h->scal_host[SLOT_RR64] > tol2 * bb;
+      } else {
+        active[i] = active[i] && h->scal_host[SLOT_RR64] > tol2 * bb && total[i] < h->opts.max_iter &&
+                    std::isfinite(h->scal_host[SLOT_RR64]);
+      }
+      if (!active[i]) continue;
+      if (!h->loop64.exec)
+        CKS(build_loop(h, h->loop64, [&](cudaStream_t c2, cudaGraphConditionalHandle hc) { return cg64_step(h, true, c2, hc); },
+                       [&](cudaStream_t c2, cudaGraphConditionalHandle hc) { return cg64_step(h, false, c2, hc); }));
+      CK(cudaGraphLaunch(h->loop64.exec, B->st[i]));
+      CK(cudaMemcpyAsync(h->iter_host, h->d_iter, 2 * sizeof(int), cudaMemcpyDeviceToHost, B->st[i]));
+      CKS(outer_residual(h, bv[i], SLOT_RR64, B->st[i]));
+      CK(cudaMemcpyAsync(h->scal_host, h->scal, SLOT_COUNT * sizeof(double), cudaMemcpyDeviceToHost, B->st[i]));
+      ++launched;
+    }
+    if (!launched) break;
+    for (int i = 0; i < n; ++i) {
+      if (!active[i]) continue;
+      CK(cudaStreamSynchronize(B->st[i]));
+      pmg_handle* h = B->h[i];
+      int it = h->iter_host[0];
+      total[i] += it;
+      int extra = std::max(0, it - 1);
+      for (int k = 0; k < PMG_K_COUNT; ++k) {
+        h->launches[k] += h->loop64.init_launches[k] + (int64_t)extra * h->loop64.body_launches[k];
+        h->bytes[k] += h->loop64.init_bytes[k] + extra * h->loop64.body_bytes[k];
+        h->flops[k] += h->loop64.init_flops[k] + extra * h->loop64.body_flops[k];
+      }
+    }
+  }
+  // phase 3: results
+  pmg_status result = PMG_OK;
+  for (int i = 0; i < n; ++i) {
+    pmg_handle* h = B->h[i];
+    double bb = h->scal_host[SLOT_BB];
+    loc[i].iterations = total[i];
+    if (loc[i].status == PMG_OK) {
+      double rel = bb > 0.0 ? std::sqrt(h->scal_host[SLOT_RR64] / bb) : 0.0;
+      loc[i].rel_residual = rel;
+      if (!(rel <= h->opts.tol)) loc[i].status = std::isfinite(rel) ? PMG_ERR_NOT_CONVERGED : PMG_ERR_NONFINITE;
+    }
+    if (loc[i].status != PMG_OK && result == PMG_OK) {
+      result = (pmg_status)loc[i].status;
+      fail(result, "a batch problem failed (see its info)");
+    }
+    CK(cudaMemcpyAsync(pout[i], h->x, h->N * sizeof(double), cudaMemcpyDeviceToDevice, B->st[i]));
+    CK(cudaEventRecord(B->done[i], B->st[i]));
+    CK(cudaStreamWaitEvent(cs, B->done[i], 0));
+  }
+  CK(cudaStreamSynchronize(cs));
+  double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  for (int i = 0; i < n; ++i) {
+    loc[i].seconds = secs;
+    if (infos) infos[i] = loc[i];
+  }
+  return result;
 }
 
 pmg_status pmg_solve_host(pmg_handle* h, const double* b, const double* pD, const double* x0, double* p_out,

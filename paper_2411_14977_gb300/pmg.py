@@ -75,6 +75,11 @@ _SIGNATURES = {
     "pmg_coarse_solve": (_I, [_P, _P, _P, _P]),
     "pmg_vcycle": (_I, [_P, _P, _P, _I, _P]),
     "pmg_apply_noalloc": (_I, [ctypes.POINTER(MeshDesc), _P, _P, _P, _P]),
+    "pmg_batch_create": (_I, [_I, ctypes.POINTER(MeshDesc), ctypes.POINTER(Opts), ctypes.POINTER(_P)]),
+    "pmg_batch_destroy": (_I, [_P]),
+    "pmg_batch_handle": (_I, [_P, _I, ctypes.POINTER(_P)]),
+    "pmg_batch_solve": (_I, [_P, _P, _P, _P, ctypes.POINTER(SolveInfo), _P]),
+    "pmg_autotune": (_I, [_P]),
     "pmg_profile_reset": (_I, [_P, _I]),
     "pmg_profile_read": (_I, [_P, _P, _P, _P, _P]),
     "pmg_last_error": (ctypes.c_char_p, []),
@@ -227,6 +232,10 @@ class Solver:
             _check(st)
         return out, info.as_dict()
 
+    def autotune(self):
+        """pmg_autotune: pick the CTA sizes of this handle's kernels by timing."""
+        _check(load().pmg_autotune(self._h))
+
     # ---- profiling
     def profile_reset(self, timing=False):
         _check(load().pmg_profile_reset(self._h, int(bool(timing))))
@@ -287,3 +296,64 @@ class Solver:
         out = torch.empty_like(r) if out is None else out
         _check(load().pmg_vcycle(self._h, _ptr(r, r.dtype), _ptr(out, r.dtype), self._f32(r), _stream()))
         return out
+
+
+class _BatchMember(Solver):
+    """A handle owned by a Batch (not destroyed on its own)."""
+
+    def __init__(self, handle, mesh, opts):
+        lib = load()
+        self._h = handle
+        self.mesh, self.opts = mesh, opts
+        n, nf = ctypes.c_int64(), ctypes.c_int64()
+        nx, nz, nl = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib.pmg_num_nodes(self._h, ctypes.byref(n), ctypes.byref(nf), ctypes.byref(nx), ctypes.byref(nz),
+                                 ctypes.byref(nl)))
+        self.n, self.n_free, self.NX, self.NZ, self.nlevels = n.value, nf.value, nx.value, nz.value, nl.value
+
+    def close(self):
+        self._h = None
+
+
+class Batch:
+    """pmg_batch_*: independent problems solved concurrently (one handle each)."""
+
+    def __init__(self, meshes, **opts):
+        lib = load()
+        self.opts = default_opts(**opts)
+        arr = (MeshDesc * len(meshes))()
+        for i, m in enumerate(meshes):
+            arr[i] = MeshDesc(m.get("x0", 0.0), m.get("x1", 1.0), m.get("h", 1.0), m["cells_x"], m["cells_z"],
+                              m["order"], int(bool(m.get("periodic", False))))
+        hb = ctypes.c_void_p()
+        _check(lib.pmg_batch_create(len(meshes), arr, ctypes.byref(self.opts), ctypes.byref(hb)))
+        self._b = hb
+        self.members = []
+        for i in range(len(meshes)):
+            hh = ctypes.c_void_p()
+            _check(lib.pmg_batch_handle(self._b, i, ctypes.byref(hh)))
+            self.members.append(_BatchMember(hh, arr[i], self.opts))
+
+    def close(self):
+        if getattr(self, "_b", None):
+            load().pmg_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, bs, pds, outs=None, raise_on_error=True):
+        n = len(self.members)
+        outs = [torch.empty_like(b) for b in bs] if outs is None else outs
+        vp = lambda ts: (ctypes.c_void_p * n)(*[t.data_ptr() for t in ts])
+        for t in list(bs) + list(pds) + list(outs):
+            _ptr(t)
+        infos = (SolveInfo * n)()
+        st = load().pmg_batch_solve(self._b, ctypes.cast(vp(bs), ctypes.c_void_p), ctypes.cast(vp(pds), ctypes.c_void_p),
+                                    ctypes.cast(vp(outs), ctypes.c_void_p), infos, _stream())
+        if raise_on_error and st != PMG_OK:
+            _check(st)
+        return outs, [infos[i].as_dict() for i in range(n)]

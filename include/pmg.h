@@ -147,6 +147,11 @@ pmg_status pmg_solve(pmg_handle* h, const double* b_dev, const double* p_dirichl
 pmg_status pmg_solve_host(pmg_handle* h, const double* b_host, const double* p_dirichlet_host,
                           const double* x0_host, double* p_out_host, pmg_solve_info* info,
                           void* stream);
+/* ||b~ - A x~||_2 on the device: x~ is x with its surface row replaced by p_D (the lifted
+ * residual that the solve's tolerance is measured in, Sec. 4.1).  Synchronises `stream`
+ * and writes the norm to *norm (host).  PMG_ERR_NONFINITE for a non-finite input. */
+pmg_status pmg_residual_norm(pmg_handle* h, const double* b, const double* p_dirichlet, const double* x,
+                             double* norm, void* stream);
 
 /* ---- component entry points (parity tests and benchmarks) ------------------------- */
 /* y = A_FF x on free nodes, y = x on the surface row; actual geometry, FP64 (Sec. 4.2). */
@@ -170,6 +175,87 @@ pmg_status pmg_prolong(pmg_handle* h, int level, const void* xc_dev, void* xf_de
 pmg_status pmg_coarse_solve(pmg_handle* h, const double* b_dev, double* x_dev, void* stream);
 /* z = B r: one V-cycle of the preconditioner on the finest level (Sec. 5). */
 pmg_status pmg_vcycle(pmg_handle* h, const void* r_dev, void* z_dev, int f32, void* stream);
+
+/* ---- time-stepper support (the wave-tank workload around the pressure solve) --------- */
+/* Nodal physical gradient (d/dx, d/dz) of a nodal field on the current geometry by the
+ * lumped-mass L2 projection (the paper's gradient recovery, Sec. 4): element-local
+ * derivatives through the sigma-map (Sec. 2.2), averaged over the elements of a node. */
+pmg_status pmg_gradient(pmg_handle* h, const double* f_dev, double* fx_dev, double* fz_dev, void* stream);
+/* eta_x per node column (NX) of the current surface polynomial (mean at element edges). */
+pmg_status pmg_surface_slope(pmg_handle* h, double* etax_dev, void* stream);
+/* Explicit forcing of the inviscid momentum equations with the static pressure folded in
+ * (p = p_D + rho g (eta - z), Sec. 2.1): Fu = -(u u_x + w u_z) - g eta_x, Fw = -(u w_x + w w_z).
+ * The dynamic pressure then solves Delta p_D = rho div F with p_D = 0 on the surface and
+ * d p_D/dn = rho n.F elsewhere: pmg_assemble_rhs_div(Fu, Fw, rho). */
+pmg_status pmg_forcing(pmg_handle* h, const double* u_dev, const double* w_dev, const double* ux_dev,
+                       const double* uz_dev, const double* wx_dev, const double* wz_dev, const double* etax_dev,
+                       double g, double* Fu_dev, double* Fw_dev, void* stream);
+/* Stage rates at fixed sigma: eta_t = w - u eta_x on the surface (kinematic condition,
+ * Eq. freesurf1); du/dt = F - grad p_D / rho + sigma eta_t du/dz (mesh velocity sigma eta_t),
+ * the same for w.  deta has NX entries. */
+pmg_status pmg_stage_rates(pmg_handle* h, const double* u_dev, const double* w_dev, const double* uz_dev,
+                           const double* wz_dev, const double* Fu_dev, const double* Fw_dev, const double* px_dev,
+                           const double* pz_dev, const double* etax_dev, double rho, double* du_dev, double* dw_dev,
+                           double* deta_dev, void* stream);
+/* out = y + a x over n doubles (Runge-Kutta stage states and accumulation). */
+pmg_status pmg_axpy(pmg_handle* h, int64_t n, double a, const double* x_dev, const double* y_dev, double* out_dev,
+                    void* stream);
+
+/* ---- learned warm start ---------------------------------------------------------------- */
+/* A small periodic 1D convolutional network over the NX node columns of a tank predicts
+ * the change of the pressure between consecutive solves of a time-stepping run; the
+ * previous pressure plus that change is the initial guess of the next solve.  Not in the
+ * paper (an addition of this library); FP32 parameters, activations and Adam moments.
+ *
+ * Input per column x (C = NZ + 3 + period channels): eta/s_eta, (eta - eta_prev)/s_deta,
+ * eta_x, a one-hot of x mod period (period = the mesh order, so the network can tell
+ * element-boundary columns from interior ones), p_prev(x, iz)/s_p for iz = 0..NZ-1, where
+ * p_prev is the previous solve's pressure and eta_prev the surface it was solved on.
+ * Layers: conv(taps) (C -> hidden), tanh,
+ * conv(taps) (hidden -> hidden), tanh, conv(1) (hidden -> NZ); periodic in x (columns
+ * wrap).  Output y (NZ x NX): guess = p_prev + s_dp * y, surface row left at p_prev.  The
+ * last layer starts at zero, so an untrained network returns p_prev exactly.  Loss, with
+ * e = y - (p - p_prev)/s_dp on the rows below the surface (the surface row is masked):
+ * L = mean over nodes of e^2 + lam ((e(z+1) - e)^2 + (e(x+1) - e)^2), x periodic; lam
+ * (default 0, see pmg_ws_set_roughness) weights rough errors, which cost the solve most.  The solve that follows always iterates to
+ * its tolerance, so the network changes iteration counts, never the pressure returned.
+ *
+ * Parameters: one flat FP32 array [W1 (hidden, C, taps), b1 (hidden), W2 (hidden,
+ * hidden, taps), b2 (hidden), W3 (NZ, hidden), b3 (NZ)], Glorot-uniform from `seed`
+ * (SplitMix64), zero biases.  Device pointers below are float64 unless named float;
+ * every call is asynchronous on `stream` unless it returns a host value.  Errors:
+ * PMG_ERR_INVALID for NULL pointers, a batch size outside 1..max_batch or a shape that
+ * does not match; PMG_ERR_OOM / PMG_ERR_CUDA from the runtime. */
+typedef struct pmg_ws pmg_ws;
+pmg_status pmg_ws_create(int n_cols, int col_len, int period, int hidden, int taps, int max_batch, uint64_t seed,
+                         double s_eta, double s_deta, double s_p, double s_dp, pmg_ws** out);
+pmg_status pmg_ws_destroy(pmg_ws* ws);
+pmg_status pmg_ws_num_params(const pmg_ws* ws, int64_t* n);
+/* Weight lam >= 0 of the first-difference terms of the training loss. */
+pmg_status pmg_ws_set_roughness(pmg_ws* ws, double lam);
+/* Host copies of the parameters out / in (n_params floats); setting resets Adam. */
+pmg_status pmg_ws_get_params(pmg_ws* ws, float* host_out);
+pmg_status pmg_ws_set_params(pmg_ws* ws, const float* host_in);
+/* One sample's input (C x NX floats) and training target (NZ x NX floats). */
+pmg_status pmg_ws_pack(pmg_ws* ws, const double* eta, const double* eta_prev, const double* etax,
+                       const double* p_prev, float* in, void* stream);
+pmg_status pmg_ws_target(pmg_ws* ws, const double* p, const double* p_prev, float* tgt, void* stream);
+/* Forward pass of S samples (S x C x NX floats in, S x NZ x NX floats out). */
+pmg_status pmg_ws_forward(pmg_ws* ws, const float* in, int S, float* out, void* stream);
+/* x0 = p_prev + s_dp * net(input) (NX*NZ, z fastest). */
+pmg_status pmg_ws_predict(pmg_ws* ws, const double* eta, const double* eta_prev, const double* etax,
+                          const double* p_prev, double* x0, void* stream);
+/* Loss of S samples and its gradient w.r.t. every parameter (n_params floats, device);
+ * synchronises `stream` when loss_host is non-NULL. */
+pmg_status pmg_ws_gradients(pmg_ws* ws, const float* in, const float* tgt, int S, float* grad, double* loss_host,
+                            void* stream);
+/* One Adam step (Kingma & Ba; beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) on the
+ * loss of S samples. */
+pmg_status pmg_ws_train_step(pmg_ws* ws, const float* in, const float* tgt, int S, float lr, double* loss_host,
+                             void* stream);
+/* Parameters to / from a file (header: magic, version, NX, NZ, period, hidden, taps). */
+pmg_status pmg_ws_save(pmg_ws* ws, const char* path);
+pmg_status pmg_ws_load(pmg_ws* ws, const char* path);
 
 /* ---- batches of independent problems --------------------------------------------------- */
 /* n independent tanks (each its own mesh, order and workspace), solved together: every

@@ -1,0 +1,91 @@
+"""Wave-tank time stepper, FP64 numpy (test infrastructure; see oracle/__init__).
+
+Inviscid sigma-transformed INSE (Sec. 2.1-2.2) in the projection reading: per stage
+    F = -(u . grad) u - g eta_x e_x                    (p = p_D + rho g (eta - z))
+    Delta p_D = rho div F, p_D = 0 on the surface, d p_D/dn = rho n.F elsewhere
+    du/dt|sigma = F - grad p_D / rho + sigma eta_t du/dz,   eta_t = w - u eta_x  (Eq. freesurf1)
+with nodal gradients by the lumped-mass L2 projection (element-local derivatives of the
+isoparametric map, mean over the elements of a node) and classical RK4.  The pressure is
+the exact solution of the discrete system (sparse LU).
+
+Pins (tests/test_oracle_stepper.py): exact gradients of physical linear functions on a
+curved mesh; a small-amplitude wave keeps the linear dispersion relation over a period.
+"""
+import math
+
+import numpy as np
+
+from .sem import Mesh, solve_direct
+
+G = 9.81
+RHO = 999.70
+
+
+class Tank:
+    def __init__(self, mesh_kwargs):
+        self.m = Mesh(**mesh_kwargs)
+
+    def gradient(self, eta, f):
+        """Nodal (f_x, f_z): element derivatives through the metric, averaged per node."""
+        m = self.m
+        rx, rz, sx, sz, J = m.element_metrics(eta)
+        fe = m.gather(f).reshape(-1, m.P + 1, m.P + 1)
+        fr = np.einsum('im,emj->eij', m.D, fe)
+        fs = np.einsum('jm,eim->eij', m.D, fe)
+        fx = rx * fr + sx * fs
+        fz = rz * fr + sz * fs
+        cnt = m.scatter(np.ones_like(fx.reshape(fx.shape[0], -1)))
+        return m.scatter(fx.reshape(fx.shape[0], -1)) / cnt, m.scatter(fz.reshape(fz.shape[0], -1)) / cnt
+
+    def slope(self, eta):
+        """eta_x per node column: mean of the element derivatives of the surface polynomial."""
+        m = self.m
+        P = m.P
+        acc = np.zeros(m.NX)
+        cnt = np.zeros(m.NX)
+        for ex in range(m.Nx):
+            cols = ex * P + np.arange(P + 1)
+            if m.periodic:
+                cols = cols % m.NX
+            d = (m.D @ eta[cols]) * (2.0 / m.dx)
+            np.add.at(acc, cols, d)
+            np.add.at(cnt, cols, 1.0)
+        return acc / cnt
+
+    def rates(self, eta, u, w):
+        m = self.m
+        ux, uz = self.gradient(eta, u)
+        wx, wz = self.gradient(eta, w)
+        etax = self.slope(eta)
+        ex_node = np.repeat(etax, m.NZ)
+        Fu = -(u * ux + w * uz) - G * ex_node
+        Fw = -(u * wx + w * wz)
+        b = m.rhs_divergence(eta, Fu, Fw, scale=RHO)
+        p = solve_direct(m.assemble(eta), b, np.zeros(m.N), m.dirichlet_mask())
+        px, pz = self.gradient(eta, p)
+        top = np.arange(m.NX) * m.NZ + m.NZ - 1
+        eta_t = w[top] - u[top] * etax
+        sig = np.tile(m.row_sigma(), m.NX)
+        et_node = np.repeat(eta_t, m.NZ)
+        du = Fu - px / RHO + sig * et_node * uz
+        dw = Fw - pz / RHO + sig * et_node * wz
+        return eta_t, du, dw, p
+
+    def step(self, eta, u, w, dt):
+        """Classical RK4; returns the new state and the four stage pressures."""
+        k1 = self.rates(eta, u, w)
+        k2 = self.rates(eta + 0.5 * dt * k1[0], u + 0.5 * dt * k1[1], w + 0.5 * dt * k1[2])
+        k3 = self.rates(eta + 0.5 * dt * k2[0], u + 0.5 * dt * k2[1], w + 0.5 * dt * k2[2])
+        k4 = self.rates(eta + dt * k3[0], u + dt * k3[1], w + dt * k3[2])
+        comb = lambda i: (k1[i] + 2 * k2[i] + 2 * k3[i] + k4[i]) * (dt / 6.0)
+        return eta + comb(0), u + comb(1), w + comb(2), [k1[3], k2[3], k3[3], k4[3]]
+
+    def linear_wave(self, amp, k):
+        """Linear-theory progressive wave eta = a cos(kx): (eta, u, w, omega)."""
+        m = self.m
+        om = math.sqrt(G * k * math.tanh(k * m.h))
+        eta = amp * np.cos(k * m.column_x())
+        X, Z = m.node_xz(eta)
+        u = amp * om * np.cosh(k * (Z + m.h)) / np.sinh(k * m.h) * np.cos(k * X)
+        w = amp * om * np.sinh(k * (Z + m.h)) / np.sinh(k * m.h) * np.sin(k * X)
+        return eta, u, w, om

@@ -7,6 +7,13 @@
 
 namespace pmg {
 
+struct ConvDims {
+  int S, C, O, X, K;  // samples, input channels, output channels, positions, taps
+};
+struct NnScales {
+  double eta, deta, p, dp;  // surface, surface change, pressure, pressure change
+};
+
 // Device scalar slots.  A Krylov solve uses one group of five consecutive slots
 // (offsets below) starting at its base: GROUP_OUTER or GROUP_INNER.
 enum Slot {
@@ -19,6 +26,7 @@ enum Slot {
   GROUP_INNER = 8,
   SLOT_BB = 16,     // ||b~||^2 (lifted right-hand side)
   SLOT_RR64 = 17,   // ||b~ - A x||^2 of the FP64 outer residual
+  SLOT_AUX = 18,    // residual norms requested outside a solve
   SLOT_COUNT = 24
 };
 
@@ -26,6 +34,7 @@ enum Slot {
 cudaError_t init_consts_apply(const ConstTables* host);
 cudaError_t init_consts_levels(const ConstTables* host);
 cudaError_t init_consts_fdm32(const float* table, size_t n);
+cudaError_t init_consts_stepper(const ConstTables* host);
 
 // Layout of the FP32 Schwarz eigenvector table (constant memory of the FP32 smoother):
 // for every (P, O) with 2 <= P <= MAXP and O <= (P-1)/2, eight NB x NB blocks
@@ -129,6 +138,17 @@ cudaError_t to_f32_scaled(size_t n, const double* x, float* y, const double* s, 
 cudaError_t add_f32_scaled(size_t n, double* x, const float* c, const double* s, int slot, cudaStream_t st);
 template <typename T> cudaError_t add(size_t n, T* x, const T* y, cudaStream_t st);
 cudaError_t cast_f32(size_t n, const double* x, float* y, cudaStream_t st);
+// time-stepper kernels (k_stepper.cu)
+cudaError_t gradient(const Shape& s, const double* f, double* fx, double* fz, const double* eta, const double* sigma,
+                     double h, double dx, double dsig, cudaStream_t st);
+cudaError_t surface_slope(const Shape& s, const double* eta, double dx, double* etax, cudaStream_t st);
+cudaError_t forcing(size_t N, int NZ, const double* u, const double* w, const double* ux, const double* uz,
+                    const double* wx, const double* wz, const double* etax, double g, double* Fu, double* Fw,
+                    cudaStream_t st);
+cudaError_t rates(size_t N, int NZ, const double* sigma, const double* u, const double* w, const double* uz,
+                  const double* wz, const double* Fu, const double* Fw, const double* px, const double* pz,
+                  const double* etax, double rho, double* du, double* dw, double* deta, cudaStream_t st);
+cudaError_t axpy(size_t n, double a, const double* x, const double* y, double* out, cudaStream_t st);
 cudaError_t cast_f64(size_t n, const float* x, double* y, cudaStream_t st);
 cudaError_t init_x(size_t n, int NZ, double* x, const double* x0, const double* pD, int* status, cudaStream_t st);
 cudaError_t check_finite(size_t n, const double* v, int* status, cudaStream_t st);
@@ -137,5 +157,22 @@ cudaError_t arm_exchange(void* buf, size_t n8);  // synchronous, at set-up
 cudaError_t arm_exchange_f64(void* buf, size_t n8, cudaStream_t st);
 cudaError_t loop_cond(cudaGraphConditionalHandle hnd, const double* s, const double* bb, double thresh2, int* iter,
                       int max_iter, cudaStream_t st);
+
+// learned warm start (k_nn.cu)
+cudaError_t nn_conv_forward(const ConvDims& d, const float* X, const float* W, const float* b, float* Y,
+                            cudaStream_t st);
+cudaError_t nn_conv_backward_input(const ConvDims& d, const float* dY, const float* W, float* dX, cudaStream_t st);
+cudaError_t nn_conv_backward_weight(const ConvDims& d, const float* X, const float* dY, float* dW, cudaStream_t st);
+cudaError_t nn_bias_grad(const ConvDims& d, const float* dY, float* db, cudaStream_t st);
+cudaError_t nn_tanh(size_t n, float* y, cudaStream_t st);
+cudaError_t nn_tanh_back(size_t n, const float* y, float* dy, cudaStream_t st);
+cudaError_t nn_loss(int S, int NZ, int X, const float* y, const float* t, float* dy, double lam, double* loss,
+                    cudaStream_t st);
+cudaError_t nn_adam(size_t n, float* p, const float* g, float* m, float* v, float lr, float b1, float b2, float eps,
+                    int t, cudaStream_t st);
+cudaError_t nn_pack(int X, int NZ, int Q, const double* eta, const double* eta_prev, const double* etax,
+                    const double* p, NnScales sc, float* in, cudaStream_t st);
+cudaError_t nn_unpack(int X, int NZ, const double* p, const float* out, double s_dp, double* x0, cudaStream_t st);
+cudaError_t nn_target(int X, int NZ, const double* p, const double* pprev, double s_dp, float* tgt, cudaStream_t st);
 
 }  // namespace pmg

@@ -95,6 +95,7 @@ pmg_status ensure_constants(int dev) {
   }
   CK(init_consts_apply(&t));
   CK(init_consts_levels(&t));
+  CK(init_consts_stepper(&t));
   {
     std::vector<float> tab(fdm32_table_size(), 0.f);
     for (int P = 2; P <= MAXP; ++P)
@@ -1383,6 +1384,23 @@ pmg_status pmg_solve(pmg_handle* h, const double* b, const double* pD, const dou
   return result;
 }
 
+pmg_status pmg_residual_norm(pmg_handle* h, const double* b, const double* pD, const double* x, double* norm,
+                             void* stream) {
+  CKS(check_handle(h));
+  if (!b || !pD || !x || !norm) return fail(PMG_ERR_INVALID, "b, p_dirichlet, x and norm must be non-NULL");
+  DeviceGuard dg(h->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  size_t N = h->N;
+  CK(cudaMemsetAsync(h->status, 0, sizeof(int), st));
+  CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{24.0 * N, 0.0}, [&] { return init_x(N, h->lv[0].s.NZ, h->p, x, pD, h->status, st); }));
+  CKS(curved<double>(h, 1, h->p, b, h->w, 0, h->scal + SLOT_AUX, st));
+  CKS(read_scalars(h, st));
+  if (h->status_host[1]) return fail(PMG_ERR_INVALID, "geometry has a non-positive or non-finite water depth");
+  *norm = std::sqrt(h->scal_host[SLOT_AUX]);
+  if (h->status_host[0] || !std::isfinite(*norm)) return fail(PMG_ERR_NONFINITE, "non-finite input or residual");
+  return PMG_OK;
+}
+
 pmg_status pmg_profile_reset(pmg_handle* h, int timing) {
   CKS(check_handle(h));
   DeviceGuard dg(h->device);
@@ -1412,6 +1430,60 @@ pmg_status pmg_profile_read(pmg_handle* h, int64_t* launches, double* ms, double
     if (flops) flops[k] = h->flops[k];
   }
   return PMG_OK;
+}
+
+pmg_status pmg_gradient(pmg_handle* h, const double* f, double* fx, double* fz, void* stream) {
+  CKS(check_handle(h));
+  if (!f || !fx || !fz) return fail(PMG_ERR_INVALID, "NULL vector");
+  DeviceGuard dg(h->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const Shape& F = h->lv[0].s;
+  return launch(h, PMG_K_SETUP, 1, st, Cost{24.0 * h->N, 0.0}, [&] {
+    return gradient(F, f, fx, fz, h->eta, (const double*)h->sigma[0], h->mesh.h, h->dx, h->dsig, st);
+  });
+}
+
+pmg_status pmg_surface_slope(pmg_handle* h, double* etax, void* stream) {
+  CKS(check_handle(h));
+  if (!etax) return fail(PMG_ERR_INVALID, "NULL vector");
+  DeviceGuard dg(h->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  return launch(h, PMG_K_SETUP, 1, st, [&] { return surface_slope(h->lv[0].s, h->eta, h->dx, etax, st); });
+}
+
+pmg_status pmg_forcing(pmg_handle* h, const double* u, const double* w, const double* ux, const double* uz,
+                       const double* wx, const double* wz, const double* etax, double g, double* Fu, double* Fw,
+                       void* stream) {
+  CKS(check_handle(h));
+  if (!u || !w || !ux || !uz || !wx || !wz || !etax || !Fu || !Fw) return fail(PMG_ERR_INVALID, "NULL vector");
+  DeviceGuard dg(h->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  return launch(h, PMG_K_SETUP, 1, st, Cost{64.0 * h->N, 8.0 * h->N}, [&] {
+    return forcing(h->N, h->lv[0].s.NZ, u, w, ux, uz, wx, wz, etax, g, Fu, Fw, st);
+  });
+}
+
+pmg_status pmg_stage_rates(pmg_handle* h, const double* u, const double* w, const double* uz, const double* wz,
+                           const double* Fu, const double* Fw, const double* px, const double* pz, const double* etax,
+                           double rho, double* du, double* dw, double* deta, void* stream) {
+  CKS(check_handle(h));
+  if (!u || !w || !uz || !wz || !Fu || !Fw || !px || !pz || !etax || !du || !dw || !deta)
+    return fail(PMG_ERR_INVALID, "NULL vector");
+  DeviceGuard dg(h->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  return launch(h, PMG_K_SETUP, 1, st, Cost{88.0 * h->N, 12.0 * h->N}, [&] {
+    return rates(h->N, h->lv[0].s.NZ, (const double*)h->sigma[0], u, w, uz, wz, Fu, Fw, px, pz, etax, rho, du, dw,
+                 deta, st);
+  });
+}
+
+pmg_status pmg_axpy(pmg_handle* h, int64_t n, double a, const double* x, const double* y, double* out,
+                    void* stream) {
+  CKS(check_handle(h));
+  if (!x || !y || !out || n < 0) return fail(PMG_ERR_INVALID, "bad axpy arguments");
+  DeviceGuard dg(h->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  return launch(h, PMG_K_SETUP, 1, st, Cost{24.0 * n, 2.0 * n}, [&] { return axpy((size_t)n, a, x, y, out, st); });
 }
 
 pmg_status pmg_autotune(pmg_handle* h) {

@@ -66,6 +66,7 @@ _SIGNATURES = {
     "pmg_assemble_rhs_div": (_I, [_P, _P, _P, _D, _P, _P]),
     "pmg_solve": (_I, [_P, _P, _P, _P, _P, ctypes.POINTER(SolveInfo), _P]),
     "pmg_solve_host": (_I, [_P, _P, _P, _P, _P, ctypes.POINTER(SolveInfo), _P]),
+    "pmg_residual_norm": (_I, [_P, _P, _P, _P, ctypes.POINTER(_D), _P]),
     "pmg_apply": (_I, [_P, _P, _P, _P]),
     "pmg_apply_f32": (_I, [_P, _P, _P, _P]),
     "pmg_level_apply": (_I, [_P, _I, _P, _P, _I, _P]),
@@ -75,6 +76,11 @@ _SIGNATURES = {
     "pmg_coarse_solve": (_I, [_P, _P, _P, _P]),
     "pmg_vcycle": (_I, [_P, _P, _P, _I, _P]),
     "pmg_apply_noalloc": (_I, [ctypes.POINTER(MeshDesc), _P, _P, _P, _P]),
+    "pmg_gradient": (_I, [_P, _P, _P, _P, _P]),
+    "pmg_surface_slope": (_I, [_P, _P, _P]),
+    "pmg_forcing": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _D, _P, _P, _P]),
+    "pmg_stage_rates": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _D, _P, _P, _P, _P]),
+    "pmg_axpy": (_I, [_P, ctypes.c_int64, _D, _P, _P, _P, _P]),
     "pmg_batch_create": (_I, [_I, ctypes.POINTER(MeshDesc), ctypes.POINTER(Opts), ctypes.POINTER(_P)]),
     "pmg_batch_destroy": (_I, [_P]),
     "pmg_batch_handle": (_I, [_P, _I, ctypes.POINTER(_P)]),
@@ -82,6 +88,20 @@ _SIGNATURES = {
     "pmg_autotune": (_I, [_P]),
     "pmg_profile_reset": (_I, [_P, _I]),
     "pmg_profile_read": (_I, [_P, _P, _P, _P, _P]),
+    "pmg_ws_create": (_I, [_I, _I, _I, _I, _I, _I, ctypes.c_uint64, _D, _D, _D, _D, ctypes.POINTER(_P)]),
+    "pmg_ws_destroy": (_I, [_P]),
+    "pmg_ws_num_params": (_I, [_P, ctypes.POINTER(ctypes.c_int64)]),
+    "pmg_ws_set_roughness": (_I, [_P, _D]),
+    "pmg_ws_get_params": (_I, [_P, _P]),
+    "pmg_ws_set_params": (_I, [_P, _P]),
+    "pmg_ws_pack": (_I, [_P, _P, _P, _P, _P, _P, _P]),
+    "pmg_ws_target": (_I, [_P, _P, _P, _P, _P]),
+    "pmg_ws_forward": (_I, [_P, _P, _I, _P, _P]),
+    "pmg_ws_predict": (_I, [_P, _P, _P, _P, _P, _P, _P]),
+    "pmg_ws_gradients": (_I, [_P, _P, _P, _I, _P, ctypes.POINTER(_D), _P]),
+    "pmg_ws_train_step": (_I, [_P, _P, _P, _I, ctypes.c_float, ctypes.POINTER(_D), _P]),
+    "pmg_ws_save": (_I, [_P, ctypes.c_char_p]),
+    "pmg_ws_load": (_I, [_P, ctypes.c_char_p]),
     "pmg_last_error": (ctypes.c_char_p, []),
 }
 
@@ -231,6 +251,36 @@ class Solver:
         if raise_on_error and st != PMG_OK:
             _check(st)
         return out, info.as_dict()
+
+    # ---- time-stepper support
+    def residual_norm(self, b, p_dirichlet, x):
+        """||b~ - A x~|| with the surface row of x replaced by p_dirichlet (synchronises)."""
+        r = ctypes.c_double()
+        _check(load().pmg_residual_norm(self._h, _ptr(b), _ptr(p_dirichlet), _ptr(x), ctypes.byref(r), _stream()))
+        return r.value
+
+    def gradient(self, f, fx=None, fz=None):
+        fx = torch.empty_like(f) if fx is None else fx
+        fz = torch.empty_like(f) if fz is None else fz
+        _check(load().pmg_gradient(self._h, _ptr(f), _ptr(fx), _ptr(fz), _stream()))
+        return fx, fz
+
+    def surface_slope(self, out=None):
+        out = torch.empty(self.NX, dtype=torch.float64, device="cuda") if out is None else out
+        _check(load().pmg_surface_slope(self._h, _ptr(out), _stream()))
+        return out
+
+    def forcing(self, u, w, ux, uz, wx, wz, etax, g, Fu, Fw):
+        _check(load().pmg_forcing(self._h, _ptr(u), _ptr(w), _ptr(ux), _ptr(uz), _ptr(wx), _ptr(wz), _ptr(etax),
+                                  float(g), _ptr(Fu), _ptr(Fw), _stream()))
+
+    def stage_rates(self, u, w, uz, wz, Fu, Fw, px, pz, etax, rho, du, dw, deta):
+        _check(load().pmg_stage_rates(self._h, _ptr(u), _ptr(w), _ptr(uz), _ptr(wz), _ptr(Fu), _ptr(Fw), _ptr(px),
+                                      _ptr(pz), _ptr(etax), float(rho), _ptr(du), _ptr(dw), _ptr(deta), _stream()))
+
+    def axpy(self, a, x, y, out):
+        _check(load().pmg_axpy(self._h, x.numel(), float(a), _ptr(x), _ptr(y), _ptr(out), _stream()))
+        return out
 
     def autotune(self):
         """pmg_autotune: pick the CTA sizes of this handle's kernels by timing."""

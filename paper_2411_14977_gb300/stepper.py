@@ -1,0 +1,123 @@
+"""Wave-tank time stepper around the pressure solve (the workload that runs one
+Poisson solve per Runge-Kutta stage).
+
+Inviscid sigma-transformed INSE in the projection reading: per stage, with the static
+pressure folded in (p = p_D + rho g (eta - z), Sec. 2.1),
+    F      = -(u . grad) u - g eta_x e_x
+    Delta p_D = rho div F,  p_D = 0 on the surface, d p_D/dn = rho n.F elsewhere
+    du/dt  = F - grad p_D / rho + sigma eta_t du/dz        (at fixed sigma, Sec. 2.2)
+    eta_t  = w - u eta_x                                   (kinematic condition, Eq. freesurf1)
+advanced by the classical fourth-order Runge-Kutta method (four solves per step).  All
+arithmetic runs in the library's kernels; this module orders the calls.  Each solve is
+warm-started from the previous stage's pressure, optionally corrected by a learned
+predictor (paper_2411_14977_gb300.warmstart).
+"""
+import math
+
+import numpy as np
+import torch
+
+from . import pmg
+
+G = 9.81
+RHO = 999.70
+
+
+class WaveTank:
+    def __init__(self, workload, dt=None, device="cuda", predictor=None, record=False, guess_policy="residual",
+                 **solver_opts):
+        self.w = workload
+        self.S = pmg.Solver(**workload.mesh_kwargs(), **solver_opts)
+        S = self.S
+        self.dev = torch.device(device)
+        self.xc, self.sr = S.node_coords()
+        f64 = dict(dtype=torch.float64, device=self.dev)
+        self.N, self.NX, self.NZ = S.n, S.NX, S.NZ
+        z = lambda n=None: torch.zeros(self.N if n is None else n, **f64)
+        self.eta, self.u, self.wv = z(self.NX), z(), z()
+        self.p = z()                        # last stage's dynamic pressure (warm start)
+        self.eta_p = z(self.NX)             # the surface that pressure was solved on
+        self.pD = z()                       # p_D = 0 on the surface
+        self.buf = {k: z() for k in ("ux", "uz", "wx", "wz", "Fu", "Fw", "b", "px", "pz")}
+        self.etax = z(self.NX)
+        self.k = [(z(self.NX), z(), z()) for _ in range(4)]
+        self.ys = (z(self.NX), z(), z())
+        self.acc = (z(self.NX), z(), z())
+        self.dt = dt
+        self.predictor = predictor
+        # "residual": use the network's guess only where its residual is smaller than that
+        # of the previous pressure; "always": use it unconditionally
+        self.guess_policy = guess_policy
+        self.record = record
+        self.samples = []                   # (eta, eta_prev, eta_x, p_prev, p) per solve when recording
+        self.solve_infos = []
+        self.guess_log = []                 # (residual of p_prev, residual of the network's guess)
+        self.t = 0.0
+
+    def set_linear_wave(self, amp, k):
+        """Linear-theory progressive wave eta = a cos(kx) with its velocity field."""
+        h = self.w.h
+        om = math.sqrt(G * k * math.tanh(k * h))
+        X = np.repeat(self.xc, self.NZ)
+        eta0 = amp * np.cos(k * self.xc)
+        Z = (self.sr[None, :] * (eta0 + h)[:, None] - h).reshape(-1)
+        u = amp * om * np.cosh(k * (Z + h)) / np.sinh(k * h) * np.cos(k * X)
+        w = amp * om * np.sinh(k * (Z + h)) / np.sinh(k * h) * np.sin(k * X)
+        self.eta.copy_(torch.from_numpy(eta0))
+        self.eta_p.copy_(self.eta)
+        self.u.copy_(torch.from_numpy(u))
+        self.wv.copy_(torch.from_numpy(w))
+        if self.dt is None:
+            self.dt = 2 * math.pi / om / 100.0
+        return om
+
+    def rates(self, eta, u, w, out):
+        S, B = self.S, self.buf
+        deta, du, dw = out
+        S.set_geometry(eta)
+        S.gradient(u, B["ux"], B["uz"])
+        S.gradient(w, B["wx"], B["wz"])
+        S.surface_slope(self.etax)
+        S.forcing(u, w, B["ux"], B["uz"], B["wx"], B["wz"], self.etax, G, B["Fu"], B["Fw"])
+        S.assemble_rhs_div(B["Fu"], B["Fw"], RHO, out=B["b"])
+        x0 = self.p
+        if self.predictor is not None:
+            # keep the network's guess only where its residual beats the previous pressure
+            guess = self.predictor.predict(eta, self.eta_p, self.etax, self.p)
+            if self.guess_policy == "always":
+                x0 = guess
+            else:
+                r_nn = S.residual_norm(B["b"], self.pD, guess)
+                r_prev = S.residual_norm(B["b"], self.pD, self.p)
+                self.guess_log.append((r_prev, r_nn))
+                if r_nn < r_prev:
+                    x0 = guess
+        prev = (self.eta_p.clone(), self.p.clone()) if self.record else None
+        _, info = S.solve(B["b"], self.pD, x0=x0, out=self.p)
+        self.eta_p.copy_(eta)
+        self.solve_infos.append(info)
+        if self.record:
+            self.samples.append((eta.clone(), prev[0], self.etax.clone(), prev[1], self.p.clone()))
+        S.gradient(self.p, B["px"], B["pz"])
+        S.stage_rates(u, w, B["uz"], B["wz"], B["Fu"], B["Fw"], B["px"], B["pz"], self.etax, RHO, du, dw, deta)
+
+    def step(self):
+        """One classical RK4 step (four pressure solves)."""
+        S, dt = self.S, self.dt
+        y = (self.eta, self.u, self.wv)
+        cs = (0.5, 0.5, 1.0)
+        wts = (1.0, 2.0, 2.0, 1.0)
+        for a in self.acc:
+            a.zero_()
+        cur = y
+        for s in range(4):
+            self.rates(*cur, self.k[s])
+            for a, kk in zip(self.acc, self.k[s]):
+                S.axpy(wts[s] * dt / 6.0, kk, a, a)
+            if s < 3:
+                for ys, yy, kk in zip(self.ys, y, self.k[s]):
+                    S.axpy(cs[s] * dt, kk, yy, ys)
+                cur = self.ys
+        for yy, a in zip(y, self.acc):
+            S.axpy(1.0, a, yy, yy)
+        self.t += dt

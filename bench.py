@@ -49,7 +49,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg3", "cfg4"])
+    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg3", "cfg4", "cfg5"])
+    ap.add_argument("--tank-steps", type=int, default=1000, help="cfg5: RK4 steps per run")
+    ap.add_argument("--train-steps", type=int, default=200, help="cfg5: steps whose solves train the warm start")
+    ap.add_argument("--filter", default="strong", choices=["strong", "few-percent", "none"],
+                    help="cfg5 spectral filter after every step: strong = (P_c 0, alpha -36, beta 8), "
+                         "few-percent = (P_c P-2, S(P) 0.97, beta 8)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu-step", action="store_true",
                     help="profiling aid: one warm step, then one step inside the NVTX range 'profiled_step'")
@@ -404,6 +409,104 @@ def run_batch(args, ws, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_tank(args, ws, rank, local):
+    """Config 5: a nonlinear progressive wave (eta0 = 0.05 cos(pi x), kh = pi) in the
+    periodic 256 x 16, P = 6 tank, classical RK4 with dt = T/100, four pressure solves per
+    step to a relative residual of 1e-10.  Three runs from the same initial state:
+      plain_fp64     FP64 p-MG-PCG, x0 = previous stage's pressure
+      mixed          FP64 flexible CG around the FP32 V-cycle, same x0
+      mixed_learned  as mixed; the solves of the first train-steps steps train the warm
+                     start network (pmg_ws_*), which then proposes x0 for the rest (kept
+                     only where its residual beats the previous pressure)
+    Reported over the evaluation window (steps after train-steps): solves/s, iterations,
+    solve time; and the final surface against the plain FP64 run."""
+    import torch
+    import paper_2411_14977_gb300.pmg as pmg
+    import workloads as W
+    from paper_2411_14977_gb300.stepper import WaveTank, G, RHO, default_filter
+    from paper_2411_14977_gb300.warmstart import WarmStart
+
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    pmg.load(build_if_missing=True)
+    w = W.config5()
+    amp, k = 0.05, np.pi
+    n_steps, n_train = args.tank_steps, min(args.train_steps, args.tank_steps)
+    flt = {"strong": (0, -36.0, 8.0), "few-percent": default_filter(w.order), "none": None}[args.filter]
+    clk = ClockSampler(local)
+
+    def run(name, **kw):
+        learned = kw.pop("learned", False)
+        tank = WaveTank(w, record=learned, filter=flt, **kw)
+        om = tank.set_linear_wave(amp, k)
+        tank.dt = 2 * np.pi / om / 100
+        out = {"train_s": 0.0}
+        windows = []
+        t_start = None
+        for s in range(n_steps):
+            if s == n_train:
+                torch.cuda.synchronize()
+                if learned:
+                    t0 = time.perf_counter()
+                    sc = dict(s_eta=amp, s_deta=amp * om * tank.dt, s_p=RHO * G * amp,
+                              s_dp=RHO * G * amp * om * tank.dt)
+                    net = WarmStart(tank.NX, tank.NZ, period=w.order, hidden=128, taps=5, max_batch=32, seed=7,
+                                    roughness=10.0, **sc)
+                    hist = net.fit(tank.samples[4:], epochs=30, batch=32, lr=1e-3)
+                    torch.cuda.synchronize()
+                    out["train_s"] = time.perf_counter() - t0
+                    out["train_loss"] = [hist[0], hist[-1]]
+                    out["params"] = net.n_params
+                    tank.samples.clear()
+                    tank.record = False
+                    tank.predictor = net
+                tank.solve_infos, tank.guess_log = [], []
+                t_start = time.perf_counter()
+            tank.step()
+        torch.cuda.synchronize()
+        t_eval = time.perf_counter() - t_start
+        infos = tank.solve_infos
+        assert all(i["status"] == 0 for i in infos), name
+        its = [i["iterations"] for i in infos]
+        out.update({
+            "solves": len(infos), "wall_s": t_eval, "solves_per_s": len(infos) / t_eval,
+            "solve_s": sum(i["seconds"] for i in infos), "iterations_mean": float(np.mean(its)),
+            "iterations_total": int(sum(its)), "max_rel_residual": max(i["rel_residual"] for i in infos),
+        })
+        if tank.guess_log:
+            out["learned_guess_kept"] = int(sum(r_nn < r_prev for r_prev, r_nn in tank.guess_log))
+            out["median_residual_ratio_learned_vs_prev"] = float(
+                np.median([r_nn / r_prev for r_prev, r_nn in tank.guess_log]))
+        out["eta"] = tank.eta.detach().cpu().numpy()
+        log(name, {k: v for k, v in out.items() if k != "eta"})
+        return out
+
+    res = {"plain_fp64": run("plain_fp64", precision=pmg.PMG_FP64, outer=pmg.PMG_PCG),
+           "mixed": run("mixed", precision=pmg.PMG_MIXED_FP32),
+           "mixed_learned": run("mixed_learned", learned=True, precision=pmg.PMG_MIXED_FP32)}
+    clocks = clk.stop()
+    eta64 = res["plain_fp64"]["eta"]
+    for r in res.values():
+        r["final_eta_maxdiff_vs_fp64_over_amp"] = float(np.abs(r.pop("eta") - eta64).max() / amp)
+    best = res["mixed_learned"]
+    line = {
+        "metric": "Poisson solves/s in RK4 time stepping to rel. residual 1e-10 (evaluation window)",
+        "value": best["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": n_steps - n_train,
+        "warmup": n_train, "ms_per_step": 1e3 * best["wall_s"] / max(1, n_steps - n_train),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "cfg5: periodic tank [0,20]x[-1,eta], 256x16 cells, P=6, eta0=0.05cos(pi x), "
+                               "RK4 dt=T/100", "tank_steps": n_steps, "train_steps": n_train,
+                   "filter": None if flt is None else {"cutoff": flt[0], "alpha": flt[1], "beta": flt[2]},
+                   "free_dof": 1536 * 96},
+        "runs": res,
+        "speedup_vs_plain_fp64": best["solves_per_s"] / res["plain_fp64"]["solves_per_s"],
+        "learned_vs_mixed_iterations": best["iterations_total"] / res["mixed"]["iterations_total"],
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -438,6 +541,8 @@ def main():
         run_reference(args, ws, rank)
     elif args.workload == "cfg4":
         run_batch(args, ws, rank, local)
+    elif args.workload == "cfg5":
+        run_tank(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
 

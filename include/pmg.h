@@ -182,6 +182,15 @@ pmg_status pmg_vcycle(pmg_handle* h, const void* r_dev, void* z_dev, int f32, vo
  * derivatives through the sigma-map (Sec. 2.2), averaged over the elements of a node. */
 pmg_status pmg_gradient(pmg_handle* h, const double* f_dev, double* fx_dev, double* fz_dev, void* stream);
 /* eta_x per node column (NX) of the current surface polynomial (mean at element edges). */
+/* Exponential cut-off filter of the modal coefficients (Sec. "Spectral Filtering"):
+ * S(k) = 1 for k <= cutoff, exp(alpha ((k - cutoff)/(P + 1 - cutoff))^beta) above, on the
+ * orthonormal Legendre modes of each element, F = V diag(S) V^-1.  pmg_set_filter builds
+ * F on the host (0 <= cutoff <= P, alpha <= 0, beta > 0; PMG_ERR_INVALID otherwise).
+ * pmg_filter applies F (x) F per element to a nodal field (surface = 0: N values) or F to
+ * the surface elevation (surface = 1: NX values) and takes the mean at nodes shared by
+ * elements; `out` must not alias `f`. */
+pmg_status pmg_set_filter(pmg_handle* h, int cutoff, double alpha, double beta);
+pmg_status pmg_filter(pmg_handle* h, const double* f, double* out, int surface, void* stream);
 pmg_status pmg_surface_slope(pmg_handle* h, double* etax_dev, void* stream);
 /* Explicit forcing of the inviscid momentum equations with the static pressure folded in
  * (p = p_D + rho g (eta - z), Sec. 2.1): Fu = -(u u_x + w u_z) - g eta_x, Fw = -(u w_x + w w_z).

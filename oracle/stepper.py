@@ -8,17 +8,45 @@ with nodal gradients by the lumped-mass L2 projection (element-local derivatives
 isoparametric map, mean over the elements of a node) and classical RK4.  The pressure is
 the exact solution of the discrete system (sparse LU).
 
+Spectral filter (Sec. "Spectral Filtering"): per element, F = V diag(S) V^{-1} with the
+exponential cut-off S(i) = 1 for i <= P_c, exp(alpha ((i - P_c)/(P + 1 - P_c))^beta) above,
+applied as F (x) F to u, w and as F to eta, followed by the mean at shared nodes.
+
 Pins (tests/test_oracle_stepper.py): exact gradients of physical linear functions on a
-curved mesh; a small-amplitude wave keeps the linear dispersion relation over a period.
+curved mesh; a small-amplitude wave keeps the linear dispersion relation over a period;
+the filter keeps polynomials of degree <= P_c, scales mode P by S(P), and is the
+identity for alpha = 0.
 """
 import math
 
 import numpy as np
 
+from . import basis
 from .sem import Mesh, solve_direct
 
 G = 9.81
 RHO = 999.70
+
+
+def filter_response(P, cutoff, alpha, beta):
+    """S(i), i = 0..P: the exponential cut-off of the modal coefficients."""
+    i = np.arange(P + 1, dtype=np.float64)
+    S = np.ones(P + 1)
+    hi = i > cutoff
+    S[hi] = np.exp(alpha * ((i[hi] - cutoff) / (P + 1 - cutoff)) ** beta)
+    return S
+
+
+def filter_matrix(P, cutoff, alpha, beta):
+    """Nodal filter V diag(S) V^{-1} at the LGL nodes of order P."""
+    V, _ = basis.vandermonde(P)
+    return V @ np.diag(filter_response(P, cutoff, alpha, beta)) @ np.linalg.inv(V)
+
+
+def default_filter(P, strength=0.97, beta=8.0):
+    """(P_c, alpha, beta) with P_c = P - 2 and S(P) = strength."""
+    cutoff = max(P - 2, 0)
+    return cutoff, math.log(strength) / ((P - cutoff) / (P + 1 - cutoff)) ** beta, beta
 
 
 class Tank:
@@ -49,6 +77,27 @@ class Tank:
                 cols = cols % m.NX
             d = (m.D @ eta[cols]) * (2.0 / m.dx)
             np.add.at(acc, cols, d)
+            np.add.at(cnt, cols, 1.0)
+        return acc / cnt
+
+    def filter_field(self, f, F):
+        """Element-wise F (x) F on a nodal field, then the mean at shared nodes."""
+        m = self.m
+        fe = m.gather(f).reshape(-1, m.P + 1, m.P + 1)
+        fe = np.einsum('im,jq,emq->eij', F, F, fe).reshape(fe.shape[0], -1)
+        cnt = m.scatter(np.ones_like(fe))
+        return m.scatter(fe) / cnt
+
+    def filter_surface(self, eta, F):
+        """Element-wise F on the surface elevation, then the mean at shared columns."""
+        m = self.m
+        acc = np.zeros(m.NX)
+        cnt = np.zeros(m.NX)
+        for ex in range(m.Nx):
+            cols = ex * m.P + np.arange(m.P + 1)
+            if m.periodic:
+                cols = cols % m.NX
+            np.add.at(acc, cols, F @ np.asarray(eta)[cols])
             np.add.at(cnt, cols, 1.0)
         return acc / cnt
 

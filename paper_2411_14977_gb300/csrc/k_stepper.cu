@@ -1,8 +1,9 @@
 // Kernels of the free-surface time stepper around the pressure solve (scaffold of the
 // wave-tank workload): nodal physical gradients by lumped L2 projection on the sigma-mesh
 // (the paper's gradient recovery, Sec. 4), the surface slope, the explicit forcing of the
-// inviscid sigma-transformed momentum equations (Sec. 2.2) and the stage rates including
-// the kinematic free-surface condition (Eq. freesurf1).  FP64.
+// inviscid sigma-transformed momentum equations (Sec. 2.2), the stage rates including
+// the kinematic free-surface condition (Eq. freesurf1), and the modal exponential
+// cut-off filter (Sec. "Spectral Filtering").  FP64.
 //
 // Gradient of a nodal field f on element (ex, ez), local node (i, j):
 //   f_r = sum_m D[i][m] f[m][j],  f_s = sum_m D[j][m] f[i][m]
@@ -94,6 +95,87 @@ __global__ void __launch_bounds__(256) k_grad(GradParams p) {
   });
 }
 
+// Spectral filter of a nodal field: per element F (x) F with the (P+1)^2 nodal filter
+// matrix F = V diag(S) V^-1 (row-major, device), then the mean over the elements of each
+// node (the same averaging as the gradient recovery).  Same slab layout as k_grad.
+struct FilterParams {
+  Shape s;
+  const double* f;
+  double* out;
+  const double* F;  // [n][n]
+};
+
+template <int P>
+__global__ void __launch_bounds__(256) k_filter(FilterParams p) {
+  constexpr int n = P + 1;
+  const Shape s = p.s;
+  const int NZ = s.NZ, Nz = s.Nz, NZp = slab_pitch(NZ);
+  const int ex = blockIdx.x, col0 = ex * P;
+  const bool left = s.periodic || ex > 0;
+  const bool last = !s.periodic && ex == s.Nx - 1;
+  const int own = last ? n : P;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* Fs = reinterpret_cast<double*>(smem_raw);  // [2P+1][NZp]
+  double* Fm = Fs + (2 * P + 1) * NZp;               // [n][n]
+  for_slab(2 * P + 1, NZ, [&](int c, int iz) {
+    bool ok = c >= P || left;
+    cp_async_elem(&Fs[c * NZp + iz], p.f + (ok ? (size_t)wrap_col(s, col0 - P + c) * NZ + iz : 0), ok);
+  });
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) Fm[t] = p.F[t];
+  cp_async_wait_all();
+  __syncthreads();
+  for_slab(own, NZ, [&](int i, int iz) {
+    int ec0 = (i == 0 && left) ? 0 : 1;
+    int ez_hi = min(iz / P, Nz - 1);
+    int ez0 = (iz == ez_hi * P && ez_hi > 0) ? ez_hi - 1 : ez_hi;
+    double sum = 0.0;
+    int cnt = 0;
+    for (int el = ec0; el <= 1; ++el) {
+      int li = el == 0 ? P : i;
+      const double* Fc = Fs + (el * P) * NZp;
+      for (int ez = ez0; ez <= ez_hi; ++ez) {
+        int lj = iz - ez * P;
+        double acc = 0.0;
+#pragma unroll
+        for (int m = 0; m < n; ++m) {
+          double g = 0.0;
+#pragma unroll
+          for (int q = 0; q < n; ++q) g += Fm[lj * n + q] * Fc[m * NZp + ez * P + q];
+          acc += Fm[li * n + m] * g;
+        }
+        sum += acc;
+        ++cnt;
+      }
+    }
+    p.out[(size_t)(col0 + i) * NZ + iz] = sum / cnt;
+  });
+}
+
+// The same filter on the surface elevation (one value per node column).
+template <int P>
+__global__ void k_filter_surface(Shape s, const double* eta, const double* F, double* out) {
+  int ix = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ix >= s.NX) return;
+  int ex = ix / P, i = ix - ex * P;
+  if (!s.periodic && ex == s.Nx) { ex = s.Nx - 1; i = P; }
+  double acc = 0.0;
+  int cnt = 0;
+  for (int el = 0; el < 2; ++el) {
+    int e = ex - el, li = el == 0 ? i : P;
+    if (el == 1 && i != 0) break;
+    if (e < 0) {
+      if (!s.periodic) break;
+      e += s.Nx;
+    }
+    double v = 0.0;
+#pragma unroll
+    for (int m = 0; m < P + 1; ++m) v += F[li * (P + 1) + m] * eta[wrap_col(s, e * P + m)];
+    acc += v;
+    ++cnt;
+  }
+  out[ix] = acc / cnt;
+}
+
 // eta_x per node column: mean of the element-local derivatives of the surface polynomial.
 template <int P>
 __global__ void k_slope(Shape s, const double* eta, double dx, double* etax) {
@@ -183,6 +265,39 @@ cudaError_t surface_slope(const Shape& s, const double* eta, double dx, double* 
   int nb = (s.NX + 127) / 128;
   switch (s.P) {
 #define PMG_CASE(PP) case PP: k_slope<PP><<<nb, 128, 0, st>>>(s, eta, dx, etax); break;
+    PMG_CASE(1) PMG_CASE(2) PMG_CASE(3) PMG_CASE(4) PMG_CASE(5)
+    PMG_CASE(6) PMG_CASE(7) PMG_CASE(8) PMG_CASE(9) PMG_CASE(10)
+#undef PMG_CASE
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t spectral_filter(const Shape& s, const double* f, double* out, const double* F, int surface,
+                            cudaStream_t st) {
+  if (surface) {
+    int nb = (s.NX + 127) / 128;
+    switch (s.P) {
+#define PMG_CASE(PP) case PP: k_filter_surface<PP><<<nb, 128, 0, st>>>(s, f, F, out); break;
+      PMG_CASE(1) PMG_CASE(2) PMG_CASE(3) PMG_CASE(4) PMG_CASE(5)
+      PMG_CASE(6) PMG_CASE(7) PMG_CASE(8) PMG_CASE(9) PMG_CASE(10)
+#undef PMG_CASE
+      default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+  }
+  FilterParams p{s, f, out, F};
+  int NZp = slab_pitch(s.NZ);
+  size_t sm = ((size_t)(2 * s.P + 1) * NZp + (size_t)(s.P + 1) * (s.P + 1)) * sizeof(double) + 16;
+  switch (s.P) {
+#define PMG_CASE(PP)                                                        \
+  case PP: {                                                                \
+    static std::atomic<unsigned long long> mask{0};                        \
+    cudaError_t e = ensure_max_smem(k_filter<PP>, mask);                    \
+    if (e != cudaSuccess) return e;                                         \
+    k_filter<PP><<<s.Nx, 256, sm, st>>>(p);                                \
+    break;                                                                  \
+  }
     PMG_CASE(1) PMG_CASE(2) PMG_CASE(3) PMG_CASE(4) PMG_CASE(5)
     PMG_CASE(6) PMG_CASE(7) PMG_CASE(8) PMG_CASE(9) PMG_CASE(10)
 #undef PMG_CASE

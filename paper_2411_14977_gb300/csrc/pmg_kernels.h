@@ -142,6 +142,8 @@ cudaError_t cast_f32(size_t n, const double* x, float* y, cudaStream_t st);
 cudaError_t gradient(const Shape& s, const double* f, double* fx, double* fz, const double* eta, const double* sigma,
                      double h, double dx, double dsig, cudaStream_t st);
 cudaError_t surface_slope(const Shape& s, const double* eta, double dx, double* etax, cudaStream_t st);
+cudaError_t spectral_filter(const Shape& s, const double* f, double* out, const double* F, int surface,
+                            cudaStream_t st);
 cudaError_t forcing(size_t N, int NZ, const double* u, const double* w, const double* ux, const double* uz,
                     const double* wx, const double* wz, const double* etax, double g, double* Fu, double* Fw,
                     cudaStream_t st);

@@ -255,6 +255,7 @@ struct pmg_handle {
   double* scal_host = nullptr;
   int* status_host = nullptr;
   double* io = nullptr;  // pmg_solve_host: out, b, p_D, x0
+  double* filt = nullptr;  // (P+1)^2 nodal spectral filter, set by pmg_set_filter
   Scratch sc{};
   // profiling: per-class launch counts; optional CUDA-event pairs around launches
   bool timing = false;
@@ -1441,6 +1442,48 @@ pmg_status pmg_gradient(pmg_handle* h, const double* f, double* fx, double* fz, 
   return launch(h, PMG_K_SETUP, 1, st, Cost{24.0 * h->N, 0.0}, [&] {
     return gradient(F, f, fx, fz, h->eta, (const double*)h->sigma[0], h->mesh.h, h->dx, h->dsig, st);
   });
+}
+
+pmg_status pmg_set_filter(pmg_handle* h, int cutoff, double alpha, double beta) {
+  CKS(check_handle(h));
+  const int P = h->mesh.order, n = P + 1;
+  if (cutoff < 0 || cutoff > P || !std::isfinite(alpha) || alpha > 0.0 || !(beta > 0.0) || !std::isfinite(beta))
+    return fail(PMG_ERR_INVALID, "filter needs 0 <= cutoff <= P, finite alpha <= 0, beta > 0");
+  DeviceGuard dg(h->device);
+  // F = V diag(S) V^-1, V[i][k] = P~_k(r_i) (orthonormal Legendre at the LGL nodes)
+  std::vector<double> r, wq;
+  lgl(P, r, wq);
+  std::vector<double> V(n * n), Vi, d(n), tmp(n);
+  for (int i = 0; i < n; ++i) {
+    legendre_orthonormal(P, r[i], tmp.data(), d.data());
+    for (int k = 0; k < n; ++k) V[i * n + k] = tmp[k];
+  }
+  Vi = V;
+  if (!invert(n, Vi)) return fail(PMG_ERR_INVALID, "singular Vandermonde matrix");
+  std::vector<double> F(n * n, 0.0);
+  for (int k = 0; k < n; ++k) {
+    double S = k <= cutoff ? 1.0 : std::exp(alpha * std::pow((double)(k - cutoff) / (P + 1 - cutoff), beta));
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) F[i * n + j] += V[i * n + k] * S * Vi[k * n + j];
+  }
+  cudaError_t e = cudaSuccess;
+  if (!h->filt) {
+    h->filt = h->alloc<double>(n * n, e);
+    CK(e);
+  }
+  CK(cudaMemcpy(h->filt, F.data(), n * n * sizeof(double), cudaMemcpyHostToDevice));
+  return PMG_OK;
+}
+
+pmg_status pmg_filter(pmg_handle* h, const double* f, double* out, int surface, void* stream) {
+  CKS(check_handle(h));
+  if (!f || !out || f == out) return fail(PMG_ERR_INVALID, "filter needs distinct non-NULL input and output");
+  if (!h->filt) return fail(PMG_ERR_INVALID, "no filter set (pmg_set_filter)");
+  DeviceGuard dg(h->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  double nv = surface ? (double)h->lv[0].s.NX : (double)h->N;
+  return launch(h, PMG_K_SETUP, 1, st, Cost{16.0 * nv, 0.0},
+                [&] { return spectral_filter(h->lv[0].s, f, out, h->filt, surface, st); });
 }
 
 pmg_status pmg_surface_slope(pmg_handle* h, double* etax, void* stream) {

@@ -78,6 +78,8 @@ _SIGNATURES = {
     "pmg_apply_noalloc": (_I, [ctypes.POINTER(MeshDesc), _P, _P, _P, _P]),
     "pmg_gradient": (_I, [_P, _P, _P, _P, _P]),
     "pmg_surface_slope": (_I, [_P, _P, _P]),
+    "pmg_set_filter": (_I, [_P, _I, _D, _D]),
+    "pmg_filter": (_I, [_P, _P, _P, _I, _P]),
     "pmg_forcing": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _D, _P, _P, _P]),
     "pmg_stage_rates": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _D, _P, _P, _P, _P]),
     "pmg_axpy": (_I, [_P, ctypes.c_int64, _D, _P, _P, _P, _P]),
@@ -264,6 +266,15 @@ class Solver:
         fz = torch.empty_like(f) if fz is None else fz
         _check(load().pmg_gradient(self._h, _ptr(f), _ptr(fx), _ptr(fz), _stream()))
         return fx, fz
+
+    def set_filter(self, cutoff, alpha, beta):
+        """Exponential cut-off filter of the element modes above `cutoff`."""
+        _check(load().pmg_set_filter(self._h, int(cutoff), float(alpha), float(beta)))
+
+    def filter(self, f, out=None, surface=False):
+        out = torch.empty_like(f) if out is None else out
+        _check(load().pmg_filter(self._h, _ptr(f), _ptr(out), int(bool(surface)), _stream()))
+        return out
 
     def surface_slope(self, out=None):
         out = torch.empty(self.NX, dtype=torch.float64, device="cuda") if out is None else out

@@ -7,7 +7,9 @@ pressure folded in (p = p_D + rho g (eta - z), Sec. 2.1),
     Delta p_D = rho div F,  p_D = 0 on the surface, d p_D/dn = rho n.F elsewhere
     du/dt  = F - grad p_D / rho + sigma eta_t du/dz        (at fixed sigma, Sec. 2.2)
     eta_t  = w - u eta_x                                   (kinematic condition, Eq. freesurf1)
-advanced by the classical fourth-order Runge-Kutta method (four solves per step).  All
+advanced by the classical fourth-order Runge-Kutta method (four solves per step),
+optionally followed by the modal exponential cut-off filter of eta, u and w (Sec.
+"Spectral Filtering").  All
 arithmetic runs in the library's kernels; this module orders the calls.  Each solve is
 warm-started from the previous stage's pressure, optionally corrected by a learned
 predictor (paper_2411_14977_gb300.warmstart).
@@ -23,9 +25,15 @@ G = 9.81
 RHO = 999.70
 
 
+def default_filter(P, strength=0.97, beta=8.0):
+    """(cutoff, alpha, beta): modes above P - 2 damped, the highest by the factor `strength`."""
+    cutoff = max(P - 2, 0)
+    return cutoff, math.log(strength) / ((P - cutoff) / (P + 1 - cutoff)) ** beta, beta
+
+
 class WaveTank:
     def __init__(self, workload, dt=None, device="cuda", predictor=None, record=False, guess_policy="residual",
-                 **solver_opts):
+                 filter=None, filter_stages=False, **solver_opts):
         self.w = workload
         self.S = pmg.Solver(**workload.mesh_kwargs(), **solver_opts)
         S = self.S
@@ -53,6 +61,12 @@ class WaveTank:
         self.solve_infos = []
         self.guess_log = []                 # (residual of p_prev, residual of the network's guess)
         self.t = 0.0
+        # spectral filter after every step: None, or (cutoff, alpha, beta)
+        self.filter = filter
+        self.filter_stages = filter_stages     # also filter every intermediate stage state
+        if filter is not None:
+            S.set_filter(*filter)
+            self.ftmp = (z(self.NX), z(), z())
 
     def set_linear_wave(self, amp, k):
         """Linear-theory progressive wave eta = a cos(kx) with its velocity field."""
@@ -117,7 +131,16 @@ class WaveTank:
             if s < 3:
                 for ys, yy, kk in zip(self.ys, y, self.k[s]):
                     S.axpy(cs[s] * dt, kk, yy, ys)
+                if self.filter is not None and self.filter_stages:
+                    self._filter(self.ys)
                 cur = self.ys
         for yy, a in zip(y, self.acc):
             S.axpy(1.0, a, yy, yy)
+        if self.filter is not None:
+            self._filter(y)
         self.t += dt
+
+    def _filter(self, state):
+        for i, (yy, tmp) in enumerate(zip(state, self.ftmp)):
+            self.S.filter(yy, tmp, surface=(i == 0))
+            yy.copy_(tmp)

@@ -12,8 +12,8 @@ import pytest
 import torch
 
 import paper_2411_14977_gb300.pmg as pmg
-from oracle.stepper import Tank
-from paper_2411_14977_gb300.stepper import WaveTank
+from oracle.stepper import Tank, default_filter as oracle_default_filter, filter_matrix
+from paper_2411_14977_gb300.stepper import WaveTank, default_filter
 import workloads as W
 from tests.gpu_helpers import n, t
 
@@ -45,11 +45,35 @@ def test_gradient_and_slope_match_oracle(periodic, order):
     np.testing.assert_allclose(n(ex), T.slope(eta), rtol=0, atol=1e-12 * np.abs(T.slope(eta)).max())
 
 
-@pytest.mark.parametrize("periodic,cells", [(True, (8, 2, 6)), (False, (5, 2, 5))])
-def test_rk4_steps_match_oracle(periodic, cells):
+@pytest.mark.parametrize("periodic", [True, False])
+@pytest.mark.parametrize("order", [3, 6, 10])
+def test_filter_matches_oracle(periodic, order):
+    w = wave_workload(8 if periodic else 5, 3, order, periodic)
+    S = pmg.Solver(**w.mesh_kwargs())
+    T = Tank(w.mesh_kwargs())
+    flt = default_filter(order, strength=0.5, beta=4.0)
+    assert np.allclose(flt, oracle_default_filter(order, strength=0.5, beta=4.0), rtol=1e-15)
+    S.set_filter(*flt)
+    F = filter_matrix(order, *flt)
+    f = W.normal(W.BASE_SEED + 94, S.n)
+    eta = W.normal(W.BASE_SEED + 95, S.NX)
+    np.testing.assert_allclose(n(S.filter(t(f))), T.filter_field(f, F), rtol=0, atol=1e-13 * np.abs(f).max())
+    np.testing.assert_allclose(n(S.filter(t(eta), surface=True)), T.filter_surface(eta, F), rtol=0,
+                               atol=1e-13 * np.abs(eta).max())
+    with pytest.raises(pmg.PmgError):
+        x = t(f)
+        S.filter(x, out=x)
+    with pytest.raises(pmg.PmgError):
+        S.set_filter(order + 1, -1.0, 8.0)
+
+
+@pytest.mark.parametrize("periodic,cells,filtered", [(True, (8, 2, 6), False), (False, (5, 2, 5), False),
+                                                      (True, (8, 2, 6), True)])
+def test_rk4_steps_match_oracle(periodic, cells, filtered):
     w = wave_workload(*cells, periodic)
     amp, k = 0.03, 2 * np.pi / 2.0
-    tank = WaveTank(w, tol=1e-12)
+    flt = default_filter(cells[2]) if filtered else None
+    tank = WaveTank(w, tol=1e-12, filter=flt)
     om = tank.set_linear_wave(amp, k)
     dt = 2 * math.pi / om / 40
     tank.dt = dt
@@ -59,9 +83,12 @@ def test_rk4_steps_match_oracle(periodic, cells):
     np.testing.assert_allclose(n(tank.eta), eta, rtol=0, atol=1e-15)
     np.testing.assert_allclose(n(tank.u), u, rtol=0, atol=1e-13)
     np.testing.assert_allclose(n(tank.wv), wv, rtol=0, atol=1e-13)
+    F = filter_matrix(cells[2], *flt) if filtered else None
     for _ in range(3):
         tank.step()
         eta, u, wv, ps = T.step(eta, u, wv, dt)
+        if filtered:
+            eta, u, wv = T.filter_surface(eta, F), T.filter_field(u, F), T.filter_field(wv, F)
     torch.cuda.synchronize()
     for a, b in ((tank.eta, eta), (tank.u, u), (tank.wv, wv)):
         err = np.abs(n(a) - b).max() / np.abs(b).max()

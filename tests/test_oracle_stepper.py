@@ -3,7 +3,8 @@ import math
 
 import numpy as np
 
-from oracle.stepper import Tank
+from oracle import basis
+from oracle.stepper import Tank, default_filter, filter_matrix, filter_response
 
 
 def test_gradient_exact_for_physical_linear_fields_on_curved_mesh():
@@ -38,3 +39,48 @@ def test_small_wave_keeps_linear_dispersion_over_one_period():
     for _ in range(steps // 2):
         eta, u, w, _ = T.step(eta, u, w, dt)
     assert np.max(np.abs(eta + eta0)) <= 3e-3 * amp
+
+
+def test_filter_response_and_default_strength():
+    P = 6
+    Pc, alpha, beta = default_filter(P)
+    S = filter_response(P, Pc, alpha, beta)
+    assert Pc == 4 and beta == 8.0
+    np.testing.assert_array_equal(S[:5], 1.0)
+    assert abs(S[P] - 0.97) < 1e-15
+    assert 0.97 < S[5] < 1.0
+    # alpha = 0 is the identity
+    np.testing.assert_allclose(filter_matrix(P, Pc, 0.0, beta), np.eye(P + 1), atol=1e-13)
+
+
+def test_filter_scales_highest_mode_and_keeps_low_degree_polynomials():
+    P = 5
+    Pc, alpha, beta = default_filter(P)
+    F = filter_matrix(P, Pc, alpha, beta)
+    r, _ = basis.lgl_nodes_weights(P)
+    V, _ = basis.vandermonde(P)
+    np.testing.assert_allclose(F @ V[:, P], filter_response(P, Pc, alpha, beta)[P] * V[:, P], atol=1e-13)
+    for deg in range(Pc + 1):
+        np.testing.assert_allclose(F @ r ** deg, r ** deg, atol=1e-13)
+    # on a mesh: fields polynomial of degree <= P_c in (x*, sigma) are unchanged, including
+    # the averaging at shared nodes; the filtered surface likewise
+    T = Tank(dict(cells_x=3, cells_z=2, order=P, x0=0.0, x1=3.0, h=1.0))
+    x, sg = T.m.column_x(), T.m.row_sigma()
+    X = np.repeat(x, T.m.NZ)
+    S = np.tile(sg, T.m.NX)
+    f = 0.3 + X ** 2 * S - 0.5 * X ** 3 + S ** 3
+    np.testing.assert_allclose(T.filter_field(f, F), f, atol=1e-12)
+    np.testing.assert_allclose(T.filter_surface(0.1 * x ** 3 - x, F), 0.1 * x ** 3 - x, atol=1e-12)
+
+
+def test_filter_single_element_mode_product():
+    """One element, no shared nodes: a product of Legendre modes i (x) j is scaled by S(i) S(j)."""
+    P = 6
+    Pc, alpha, beta = default_filter(P)
+    S = filter_response(P, Pc, alpha, beta)
+    T = Tank(dict(cells_x=1, cells_z=1, order=P, x0=0.0, x1=1.0, h=1.0))
+    V, _ = basis.vandermonde(P)
+    F = filter_matrix(P, Pc, alpha, beta)
+    for i, j in [(6, 6), (5, 2), (0, 6), (3, 4)]:
+        f = np.outer(V[:, i], V[:, j]).reshape(-1)   # node (ix, iz), z fastest
+        np.testing.assert_allclose(T.filter_field(f, F), S[i] * S[j] * f, atol=1e-13)

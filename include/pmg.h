@@ -85,6 +85,8 @@ typedef struct {
   double inner_tol;  /* mixed precision: inner relative residual target                     */
   int nlevels;       /* 0 = the paper's coarsening rule; else level_orders[0..nlevels-1]    */
   int level_orders[8];
+  int fuse_residual; /* FP32 sweeps that form their own level residual: 1 on every level,   */
+                     /* 0 never, -1 (default) where pmg_autotune measured it to be faster    */
 } pmg_opts;
 
 typedef struct {

@@ -41,7 +41,7 @@ struct CurvedParams {
 };
 
 template <int P, typename T, int MODE>
-__global__ void __launch_bounds__(256) k_curved(CurvedParams<T> p) {
+__global__ void __launch_bounds__(512) k_curved(CurvedParams<T> p) {
   constexpr int n = P + 1;
   const Shape s = p.s;
   const int NZ = s.NZ, Nz = s.Nz, NZp = slab_pitch(NZ);
@@ -317,7 +317,7 @@ cudaError_t curved_op(const CurvedArgs& a, cudaStream_t st) {
   p.mask_input = a.mask_input;
   p.result = a.result;
   p.sc = a.sc;
-  int thr = (a.threads >= 32 && a.threads <= 256) ? a.threads : 256;
+  int thr = (a.threads >= 32 && a.threads <= 512) ? a.threads : 256;
   switch (a.mode) {
     case MODE_APPLY: return launch_curved<T, MODE_APPLY>(p, thr, st);
     case MODE_RESIDUAL: return launch_curved<T, MODE_RESIDUAL>(p, thr, st);

@@ -8,22 +8,34 @@
 //   phase 2  T3 = Vz (D^-1 o (Vz^T T1_window))   per (x-mode, element)
 //   phase 3  U  = Vx (sum of the covering elements' T3)   per node row
 //   phase 4  x += omega W U (pre) / omega U with W applied to r (post); slab-edge exchange
+// With a right-hand side b the sweep also forms its own residual (phase 0): the CTA loads
+// x on the 3P+1 columns that the stencils of its subdomain columns touch and evaluates
+// r = b - (cx K_X (x) M_Z + cz M_X (x) K_Z) x there, so the level residual needs neither
+// a launch of its own nor a round trip through global memory.  Those columns include the
+// neighbouring CTAs' interiors, which they update in the same launch, so the fused sweep
+// reads the iterate from one buffer and writes it to another (x -> xout).
 #include "pmg_common.cuh"
 #include "pmg_kernels.h"
 
 namespace pmg {
 
 static __constant__ float cV32[fdm32_table_size()];
+static __constant__ float cK32[MAXP + 1][MAXP + 1][MAXP + 1];  // 1D LGL stiffness per order
 
-cudaError_t init_consts_fdm32(const float* table, size_t n) {
-  if (n != (size_t)fdm32_table_size()) return cudaErrorInvalidValue;
-  return cudaMemcpyToSymbol(cV32, table, n * sizeof(float));
+cudaError_t init_consts_fdm32(const float* table, size_t n, const float* K, size_t nk) {
+  if (n != (size_t)fdm32_table_size() || nk != (size_t)(MAXP + 1) * (MAXP + 1) * (MAXP + 1))
+    return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemcpyToSymbol(cV32, table, n * sizeof(float));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyToSymbol(cK32, K, nk * sizeof(float));
 }
 
 struct Fdm32Params {
   Shape s;
   const float* r;
-  float* x;
+  float* x;     // iterate in
+  float* xout;  // iterate out (== x: in place; required distinct when b is set)
+  int xzero;    // the iterate in is zero: not read
   int post;
   float omega;
   const float* Vz;      // [4][NB][NB] z eigenvectors (boundary classes read from shared memory)
@@ -31,6 +43,11 @@ struct Fdm32Params {
   const float* wx;
   const float* wz;
   Scratch sc;
+  // fused residual (b != nullptr): r = b - A x with the flat level operator
+  const float* b;
+  float cx, cz;
+  const float* mX;  // [NX] assembled LGL weights along x
+  const float* mZ;  // [NZ]
 };
 
 __device__ __forceinline__ int xclass32(const Shape& s, int ex) {
@@ -38,7 +55,7 @@ __device__ __forceinline__ int xclass32(const Shape& s, int ex) {
   return (ex == 0 ? 1 : 0) | (ex == s.Nx - 1 ? 2 : 0);
 }
 
-template <int P, int O, int XC>
+template <int P, int O, int XC, bool RES>
 __device__ __forceinline__ void fdm32_body(const Fdm32Params& p, unsigned char* smem_raw) {
   constexpr int NB = P + 1 + 2 * O;
   constexpr int OFF = fdm32_offset(P, O);
@@ -52,20 +69,45 @@ __device__ __forceinline__ void fdm32_body(const Fdm32Params& p, unsigned char* 
   float* T3 = T1 + NB * NZp;                       // [Nz][NB][NB] (ez, b, alpha)
   float* VZ = T3 + Nz * NB * NB;                   // [4][NB][NB]
   float* ID = VZ + 4 * NB * NB;                    // [4][NB][NB] (zc, alpha, beta)
-  float* XS = ID + 4 * NB * NB;                    // [NB][NZp]
-  float* WZ = XS + NB * NZp;                       // [NZ] inverse cover counts along z
+  // x slab: the subdomain columns [NB][NZp], or with RES the stencil columns [3P+1][NZp]
+  // (local column c <-> global col0 - P + c; subdomain column a sits at c = a - O + P)
+  constexpr int XCOLS = RES ? 3 * P + 1 : NB;
+  constexpr int XOFF = RES ? P - O : 0;
+  float* XS = ID + 4 * NB * NB;                    // [XCOLS][NZp]
+  float* WZ = XS + XCOLS * NZp;                    // [NZ] inverse cover counts along z
   float* WX = WZ + NZ;                             // [NB] inverse cover counts of the subdomain columns
-  size_t red_off =
-      (((size_t)(3 * NB * NZp + Nz * NB * NB + 8 * NB * NB + NZ + NB) * sizeof(float)) + 15) & ~(size_t)15;
+  float* MZC = WX + NB;                            // [NZ] cx * assembled z weights (RES)
+  float* MXC = MZC + (RES ? NZ : 0);               // [NB] cz * assembled x weights (RES)
+  size_t red_off = (((size_t)((2 + 0) * NB * NZp + XCOLS * NZp + Nz * NB * NB + 8 * NB * NB + NZ + NB +
+                              (RES ? NZ + NB : 0)) * sizeof(float)) + 15) & ~(size_t)15;
   int* s_flag = reinterpret_cast<int*>(smem_raw + red_off);
 
-  for_slab(NB, NZ, [&](int a, int iz) {
-    int gc = col0 - O + a;
-    bool ok = col_valid(s, gc) && iz != NZ - 1;
-    size_t g = ok ? (size_t)wrap_col(s, gc) * NZ + iz : 0;
-    cp_async_elem(&R[a * NZp + iz], p.r + g, ok);
-    cp_async_elem(&XS[a * NZp + iz], p.x + g, ok);
-  });
+  if (RES) {
+    for_slab(XCOLS, NZ, [&](int c, int iz) {
+      int gc = col0 - P + c;
+      bool ok = col_valid(s, gc) && iz != NZ - 1;
+      ok = ok && !p.xzero;
+      cp_async_elem(&XS[c * NZp + iz], p.x + (ok ? (size_t)wrap_col(s, gc) * NZ + iz : 0), ok);
+    });
+    for_slab(NB, NZ, [&](int a, int iz) {
+      int gc = col0 - O + a;
+      bool ok = col_valid(s, gc) && iz != NZ - 1;
+      cp_async_elem(&R[a * NZp + iz], p.b + (ok ? (size_t)wrap_col(s, gc) * NZ + iz : 0), ok);
+    });
+    for (int t = threadIdx.x; t < NZ; t += blockDim.x) MZC[t] = p.cx * p.mZ[t];
+    if (threadIdx.x < NB) {
+      int gc = col0 - O + threadIdx.x;
+      MXC[threadIdx.x] = col_valid(s, gc) ? p.cz * p.mX[wrap_col(s, gc)] : 0.f;
+    }
+  } else {
+    for_slab(NB, NZ, [&](int a, int iz) {
+      int gc = col0 - O + a;
+      bool ok = col_valid(s, gc) && iz != NZ - 1;
+      size_t g = ok ? (size_t)wrap_col(s, gc) * NZ + iz : 0;
+      cp_async_elem(&R[a * NZp + iz], p.r + g, ok);
+      cp_async_elem(&XS[a * NZp + iz], p.x + g, ok && !p.xzero);
+    });
+  }
   for (int t = threadIdx.x; t < 4 * NB * NB; t += blockDim.x) {
     VZ[t] = p.Vz[t];
     ID[t] = p.invden[XC * 4 * NB * NB + t];
@@ -77,6 +119,38 @@ __device__ __forceinline__ void fdm32_body(const Fdm32Params& p, unsigned char* 
   }
   cp_async_wait_all();
   __syncthreads();
+  if (RES) {
+    // phase 0: R = b - A x on the subdomain columns (R holds b, zero off the mesh and on
+    // the surface row, which stay zero)
+    for_slab(NB, NZ, [&](int a, int iz) {
+      if (iz == NZ - 1 || MXC[a] == 0.f) return;
+      const int c = a + XOFF;
+      const int e = c / P, li = c - e * P;  // element of the slab (0 left, 1 own, 2 right)
+      // a wall column is also the last (first) column of the missing element beyond it,
+      // whose stencil must not be added: zero data alone does not exclude it
+      auto exists = [&](int el) { int g = ex - 1 + el; return s.periodic || (g >= 0 && g < s.Nx); };
+      float kx = 0.f;
+      if (exists(e)) {
+#pragma unroll
+        for (int m = 0; m <= P; ++m) kx = fmaf(cK32[P][li][m], XS[(e * P + m) * NZp + iz], kx);
+      }
+      if (li == 0 && e > 0 && exists(e - 1)) {
+#pragma unroll
+        for (int m = 0; m <= P; ++m) kx = fmaf(cK32[P][P][m], XS[((e - 1) * P + m) * NZp + iz], kx);
+      }
+      const int ez = min(iz / P, Nz - 1), lj = iz - ez * P;
+      const float* col = XS + c * NZp;
+      float kz = 0.f;
+#pragma unroll
+      for (int m = 0; m <= P; ++m) kz = fmaf(cK32[P][lj][m], col[ez * P + m], kz);
+      if (lj == 0 && ez > 0) {
+#pragma unroll
+        for (int m = 0; m <= P; ++m) kz = fmaf(cK32[P][P][m], col[(ez - 1) * P + m], kz);
+      }
+      R[a * NZp + iz] -= MZC[iz] * kx + MXC[a] * kz;
+    });
+    __syncthreads();
+  }
   if (p.post) {
     for_slab(NB, NZ, [&](int a, int iz) { R[a * NZp + iz] *= WX[a] * WZ[iz]; });
     __syncthreads();
@@ -173,7 +247,7 @@ __device__ __forceinline__ void fdm32_body(const Fdm32Params& p, unsigned char* 
     if (iz == NZ - 1) return;
     int c = wrap_col(s, col0 - O + a);
     float w = p.post ? 1.f : WX[a] * WZ[iz];
-    p.x[(size_t)c * NZ + iz] = XS[a * NZp + iz] + p.omega * w * u;
+    p.xout[(size_t)c * NZ + iz] = XS[(a + XOFF) * NZp + iz] + p.omega * w * u;
   };
   constexpr int ZW = 2 * O + 1;
   unsigned long long* xb = reinterpret_cast<unsigned long long*>(p.sc.xbuf);
@@ -201,24 +275,26 @@ __device__ __forceinline__ void fdm32_body(const Fdm32Params& p, unsigned char* 
   }
 }
 
-template <int P, int O>
-__global__ void __launch_bounds__(256) k_fdm32(Fdm32Params p) {
+template <int P, int O, bool RES>
+__global__ void __launch_bounds__(512) k_fdm32(Fdm32Params p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   switch (xclass32(p.s, blockIdx.x)) {
-    case 0: fdm32_body<P, O, 0>(p, smem_raw); break;
-    case 1: fdm32_body<P, O, 1>(p, smem_raw); break;
-    case 2: fdm32_body<P, O, 2>(p, smem_raw); break;
-    default: fdm32_body<P, O, 3>(p, smem_raw); break;
+    case 0: fdm32_body<P, O, 0, RES>(p, smem_raw); break;
+    case 1: fdm32_body<P, O, 1, RES>(p, smem_raw); break;
+    case 2: fdm32_body<P, O, 2, RES>(p, smem_raw); break;
+    default: fdm32_body<P, O, 3, RES>(p, smem_raw); break;
   }
 }
 
-template <int P, int O>
-static cudaError_t launch_fdm32_p(const Fdm32Params& prm, int threads, cudaStream_t st) {
+template <int P, int O, bool RES>
+static cudaError_t launch_fdm32_pr(const Fdm32Params& prm, int threads, cudaStream_t st) {
   constexpr int NB = P + 1 + 2 * O;
+  constexpr int XCOLS = RES ? 3 * P + 1 : NB;
   int NZp = slab_pitch(prm.s.NZ);
-  size_t elems = (size_t)3 * NB * NZp + (size_t)prm.s.Nz * NB * NB + 8 * NB * NB + prm.s.NZ + NB;
+  size_t elems = (size_t)(2 * NB + XCOLS) * NZp + (size_t)prm.s.Nz * NB * NB + 8 * NB * NB + prm.s.NZ + NB +
+                 (RES ? prm.s.NZ + NB : 0);
   size_t sm = ((elems * sizeof(float) + 15) & ~(size_t)15) + 16;
-  auto k = k_fdm32<P, O>;
+  auto k = k_fdm32<P, O, RES>;
   static std::atomic<unsigned long long> s_mask{0};
   cudaError_t e = ensure_max_smem(k, s_mask);
   if (e != cudaSuccess) return e;
@@ -226,11 +302,19 @@ static cudaError_t launch_fdm32_p(const Fdm32Params& prm, int threads, cudaStrea
   return cudaGetLastError();
 }
 
+template <int P, int O>
+static cudaError_t launch_fdm32_p(const Fdm32Params& prm, int threads, cudaStream_t st) {
+  return prm.b ? launch_fdm32_pr<P, O, true>(prm, threads, st) : launch_fdm32_pr<P, O, false>(prm, threads, st);
+}
+
 cudaError_t fdm_smooth32(const FdmArgs& a, cudaStream_t st) {
   Fdm32Params p;
   p.s = a.s;
   p.r = (const float*)a.r;
   p.x = (float*)a.x;
+  p.xout = a.xout ? (float*)a.xout : (float*)a.x;
+  p.xzero = a.xzero;
+  if (a.b && p.xout == p.x) return cudaErrorInvalidValue;  // neighbours read x while it is written
   p.post = a.post;
   p.omega = (float)a.omega;
   p.Vz = (const float*)a.Vz;
@@ -238,7 +322,12 @@ cudaError_t fdm_smooth32(const FdmArgs& a, cudaStream_t st) {
   p.wx = (const float*)a.wx;
   p.wz = (const float*)a.wz;
   p.sc = a.sc;
-  int thr = (a.threads >= 32 && a.threads <= 256) ? a.threads : 256;
+  p.b = (const float*)a.b;
+  p.cx = (float)a.cx;
+  p.cz = (float)a.cz;
+  p.mX = (const float*)a.mX;
+  p.mZ = (const float*)a.mZ;
+  int thr = (a.threads >= 32 && a.threads <= 512) ? a.threads : 256;
   if (a.overlap == 0) {
     switch (a.s.P) {
 #define PMG_CASE(PP) case PP: return launch_fdm32_p<PP, 0>(p, thr, st);

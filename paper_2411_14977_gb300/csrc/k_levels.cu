@@ -35,7 +35,7 @@ struct FlatParams {
 };
 
 template <int P, typename T>
-__global__ void __launch_bounds__(256) k_flat(FlatParams<T> p) {
+__global__ void __launch_bounds__(512) k_flat(FlatParams<T> p) {
   constexpr int n = P + 1;
   const Shape s = p.s;
   const int NZ = s.NZ, Nz = s.Nz, NZp = slab_pitch(NZ);
@@ -136,7 +136,7 @@ cudaError_t flat_op(const FlatArgs& a, cudaStream_t st) {
   p.mX = (const T*)a.mX;
   p.mZ = (const T*)a.mZ;
   p.residual = a.residual;
-  int thr = (a.threads >= 32 && a.threads <= 256) ? a.threads : 256;
+  int thr = (a.threads >= 32 && a.threads <= 512) ? a.threads : 256;
   switch (a.s.P) {
 #define PMG_CASE(PP) case PP: return launch_flat_p<PP, T>(p, thr, st);
     PMG_CASE(1) PMG_CASE(2) PMG_CASE(3) PMG_CASE(4) PMG_CASE(5)
@@ -344,7 +344,7 @@ cudaError_t fdm_smooth(const FdmArgs& a, cudaStream_t st) {
   p.wx = (const T*)a.wx;
   p.wz = (const T*)a.wz;
   p.sc = a.sc;
-  int thr = (a.threads >= 32 && a.threads <= 256) ? a.threads : 256;
+  int thr = (a.threads >= 32 && a.threads <= 512) ? a.threads : 256;
   if (a.overlap == 0) {
     switch (a.s.P) {
 #define PMG_CASE(PP) case PP: return launch_fdm_p<PP, 0, T>(p, thr, st);
@@ -378,7 +378,7 @@ struct TransferParams {
 
 // x_f += P x_c
 template <typename T>
-__global__ void __launch_bounds__(256) k_prolong(TransferParams<T> p) {
+__global__ void __launch_bounds__(512) k_prolong(TransferParams<T> p) {
   const Shape f = p.f, c = p.c;
   const int Pf = f.P, Pc = c.P, nf = Pf + 1, nc = Pc + 1;
   const int NZf = f.NZ, NZc = c.NZ, NZcp = slab_pitch(NZc), NZfp = slab_pitch(NZf);
@@ -412,7 +412,7 @@ __global__ void __launch_bounds__(256) k_prolong(TransferParams<T> p) {
 
 // r_c = P^T r_f
 template <typename T>
-__global__ void __launch_bounds__(256) k_restrict(TransferParams<T> p) {
+__global__ void __launch_bounds__(512) k_restrict(TransferParams<T> p) {
   const Shape f = p.f, c = p.c;
   const int Pf = f.P, Pc = c.P, nf = Pf + 1, nc = Pc + 1;
   const int NZf = f.NZ, NZc = c.NZ, NZfp = slab_pitch(NZf), NZcp = slab_pitch(NZc);
@@ -485,13 +485,13 @@ cudaError_t transfer(const TransferArgs& a, int restrict_, cudaStream_t st) {
     static std::atomic<unsigned long long> s_mask{0};
     e = ensure_max_smem(k_restrict<T>, s_mask);
     if (e != cudaSuccess) return e;
-    k_restrict<T><<<a.f.Nx, (a.threads >= 32 && a.threads <= 256) ? a.threads : 256, sm, st>>>(p);
+    k_restrict<T><<<a.f.Nx, (a.threads >= 32 && a.threads <= 512) ? a.threads : 256, sm, st>>>(p);
   } else {
     size_t sm = ((size_t)nc * (NZcp + NZfp) + nf * nc + (size_t)nf * NZfp) * sizeof(T) + 16;
     static std::atomic<unsigned long long> s_mask{0};
     e = ensure_max_smem(k_prolong<T>, s_mask);
     if (e != cudaSuccess) return e;
-    k_prolong<T><<<a.f.Nx, (a.threads >= 32 && a.threads <= 256) ? a.threads : 256, sm, st>>>(p);
+    k_prolong<T><<<a.f.Nx, (a.threads >= 32 && a.threads <= 512) ? a.threads : 256, sm, st>>>(p);
   }
   return cudaGetLastError();
 }

@@ -33,7 +33,7 @@ enum Slot {
 // Per-TU constant-table initialisers.
 cudaError_t init_consts_apply(const ConstTables* host);
 cudaError_t init_consts_levels(const ConstTables* host);
-cudaError_t init_consts_fdm32(const float* table, size_t n);
+cudaError_t init_consts_fdm32(const float* table, size_t n, const float* K, size_t nk);
 cudaError_t init_consts_stepper(const ConstTables* host);
 
 // Layout of the FP32 Schwarz eigenvector table (constant memory of the FP32 smoother):
@@ -101,6 +101,14 @@ struct FdmArgs {
   const void* wz;
   Scratch sc;
   int threads = 256;
+  // FP32 sweep only: with b set, the sweep forms r = b - A x itself (r is ignored) and
+  // xout must differ from x; xzero: the iterate in is zero and is not read
+  void* xout = nullptr;
+  int xzero = 0;
+  const void* b = nullptr;
+  double cx = 0.0, cz = 0.0;
+  const void* mX = nullptr;
+  const void* mZ = nullptr;
 };
 template <typename T> cudaError_t fdm_smooth(const FdmArgs& a, cudaStream_t st);
 // FP32 sweep with the eigenvectors in constant memory (k_fdm32.cu)

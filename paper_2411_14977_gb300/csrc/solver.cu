@@ -109,7 +109,7 @@ pmg_status ensure_constants(int dev) {
             for (int i = 0; i < NB * NB; ++i) tab[off + (dir * 4 + cls) * NB * NB + i] = (float)V[i];
           }
       }
-    CK(init_consts_fdm32(tab.data(), tab.size()));
+    CK(init_consts_fdm32(tab.data(), tab.size(), &t.Kf[0][0][0], sizeof(t.Kf) / sizeof(float)));
   }
   g_const_devices.insert(dev);
   return PMG_OK;
@@ -224,6 +224,7 @@ struct LevelDev {
   void* wz[2]{};
   double* J = nullptr;  // transfer from level l+1 (coarse) to this level
   int thr_flat32 = 256, thr_fdm32 = 256, thr_xfer = 256;  // CTA sizes (autotuner)
+  bool fuse_res = false;  // FP32 sweeps form their own residual (autotuner, when faster)
   void* b[2]{};
   void* x[2]{};
   void* t[2]{};
@@ -233,7 +234,7 @@ struct pmg_handle {
   pmg_mesh_desc mesh{};
   pmg_opts opts{};
   int device = 0;
-  int thr_curved32 = 256;  // CTA size of the FP32 actual-geometry operator (autotuner)
+  int thr_curved32 = 256, thr_curved64 = 256;  // CTA sizes of the actual-geometry operators (autotuner)
   double dx = 0, dsig = 0, cx = 0, cz = 0;
   size_t N = 0, Nfree = 0;
   std::vector<int> orders;
@@ -341,6 +342,7 @@ pmg_status build_level(pmg_handle* h, int l) {
   const pmg_mesh_desc& m = h->mesh;
   int p = h->orders[l];
   L.order = p;
+  L.fuse_res = h->opts.fuse_residual == 1;
   L.s.P = p;
   L.s.Nx = m.cells_x;
   L.s.Nz = m.cells_z;
@@ -494,24 +496,58 @@ pmg_status level_residual(pmg_handle* h, int l, const void* b, const void* x, vo
   return launch(h, PI<T> ? PMG_K_LEVEL32 : PMG_K_LEVEL64, 1, st, c, [&] { return flat_op<T>(a, st); });
 }
 
+// One Schwarz sweep xout = x + B_l r.  r given, or (FP32 with fused_b) r = fused_b - A_l x
+// formed inside the sweep; xout (default: x, in place) must differ from x when fused.
 template <typename T>
-pmg_status level_fdm(pmg_handle* h, int l, const void* r, void* x, int post, cudaStream_t st) {
+pmg_status level_fdm(pmg_handle* h, int l, const void* r, void* x, int post, cudaStream_t st,
+                     const void* fused_b = nullptr, void* xout = nullptr, bool xzero = false) {
   LevelDev& L = h->lv[l];
   FdmArgs a{L.s, L.overlap, r, x, post, h->opts.omega, L.Vx[PI<T>], L.Vz[PI<T>], L.invden[PI<T>],
             L.wx[PI<T>], L.wz[PI<T>], h->sc, PI<T> ? L.thr_fdm32 : 256};
   double NL = (double)L.s.NX * L.s.NZ, E = (double)L.s.Nx * L.s.Nz;
   double NB = L.s.P + 1 + 2 * L.overlap;
   Cost c{3.0 * NL * sizeof(T), E * 2.0 * (2.0 * L.s.P * NB * NB + 2.0 * NB * NB * NB)};
+  if (PI<T>) {
+    a.xout = xout;
+    a.xzero = xzero ? 1 : 0;
+  }
+  if (fused_b) {
+    a.b = fused_b;
+    a.cx = h->cx;
+    a.cz = h->cz;
+    a.mX = L.mX[1];
+    a.mZ = L.mZ[1];
+    c.flops += NL * (4.0 * (L.s.P + 2) + 4.0);
+  }
   return launch(h, PI<T> ? PMG_K_SMOOTH32 : PMG_K_SMOOTH64, 1, st, c,
                 [&] { return PI<T> ? fdm_smooth32(a, st) : fdm_smooth<T>(a, st); });
 }
 
-// nu sweeps on A_l x = b (x updated); x_zero: x is known to be zero on entry
+// nu sweeps on A_l x = b (x updated); x_zero: x is known to be zero on entry.
+// FP32: every sweep after a zero start forms its residual inside the sweep kernel and the
+// iterate alternates between x and the level scratch t (t's surface row stays zero),
+// arranged so that the last sweep writes x.
 template <typename T>
 pmg_status level_smooth(pmg_handle* h, int l, const void* b, void* x, int post, bool x_zero,
                         cudaStream_t st) {
   LevelDev& L = h->lv[l];
-  for (int it = 0; it < h->opts.nu; ++it) {
+  const int nu = h->opts.nu;
+  if (PI<T> && L.s.P >= 2 && L.fuse_res) {
+    void* tb = L.t[1];
+    void* src = (nu % 2 == 0) ? x : tb;  // buffer read by the first sweep
+    if (src != x && !x_zero) {
+      size_t NL = (size_t)L.s.NX * L.s.NZ;
+      CK(cudaMemcpyAsync(tb, x, NL * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    }
+    for (int it = 0; it < nu; ++it) {
+      void* dst = (src == x) ? tb : x;
+      if (it == 0 && x_zero) CKS(level_fdm<T>(h, l, b, src, post, st, nullptr, dst, true));
+      else CKS(level_fdm<T>(h, l, nullptr, src, post, st, b, dst, false));
+      src = dst;
+    }
+    return PMG_OK;
+  }
+  for (int it = 0; it < nu; ++it) {
     if (it == 0 && x_zero) {
       CKS(level_fdm<T>(h, l, b, x, post, st));
     } else {
@@ -572,7 +608,7 @@ pmg_status curved(pmg_handle* h, int mode, const void* x, const void* b, void* y
   a.mask_input = mask;
   a.result = result;
   a.sc = h->sc;
-  a.threads = PI<T> ? h->thr_curved32 : 256;
+  a.threads = PI<T> ? h->thr_curved32 : h->thr_curved64;
   const Shape& F = a.s;
   double N = (double)F.NX * F.NZ, E = (double)F.Nx * F.Nz, n = F.P + 1;
   Cost c{(mode == 1 ? 3.0 : 2.0) * N * sizeof(T), E * (8.0 * n * n * n + 12.0 * n * n)};
@@ -914,8 +950,8 @@ void set_last_error(const char* msg) { g_err = msg; }
 // =====================================================================================
 namespace {
 
-enum { TK_FLAT32 = 0, TK_FDM32 = 1, TK_XFER = 2, TK_CURVED32 = 3 };
-const char* kTuneNames[] = {"flat32", "fdm32", "transfer", "curved32"};
+enum { TK_FLAT32 = 0, TK_FDM32 = 1, TK_XFER = 2, TK_CURVED32 = 3, TK_CURVED64 = 4 };
+const char* kTuneNames[] = {"flat32", "fdm32", "transfer", "curved32", "curved64"};
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int>, int> g_tune;  // (kernel, order, rows, columns) -> threads
 bool g_tune_loaded = false;
@@ -935,7 +971,7 @@ void tune_cache_load() {
     int P, NZ, Nx, thr;
     if (std::sscanf(line, "{\"kernel\": \"%63[^\"]\", \"P\": %d, \"NZ\": %d, \"Nx\": %d, \"threads\": %d}", name, &P,
                     &NZ, &Nx, &thr) == 5)
-      for (int k = 0; k < 4; ++k)
+      for (int k = 0; k < 5; ++k)
         if (!std::strcmp(name, kTuneNames[k])) g_tune[std::make_tuple(k, P, NZ, Nx)] = thr;
   }
   std::fclose(f);
@@ -1005,7 +1041,7 @@ pmg_status tune_one(pmg_handle* h, int kernel, int P, int NZ, Run&& run, int* ou
   }
   int best = 256;
   float best_us = 1e30f;
-  for (int thr : {64, 128, 256}) {
+  for (int thr : {64, 128, 192, 256, 320, 384, 512}) {
     float us;
     CKS(time_launches(h, run, thr, 10, &us));
     if (us < best_us * 0.97f) { best_us = us; best = thr; }
@@ -1055,6 +1091,7 @@ void pmg_default_opts(pmg_opts* o) {
   o->inner_max = 40;
   o->inner_tol = 1e-5;
   o->nlevels = 0;
+  o->fuse_residual = -1;
 }
 
 const char* pmg_last_error(void) { return g_err.c_str(); }
@@ -1079,7 +1116,7 @@ pmg_status pmg_create(const pmg_mesh_desc* mesh, const pmg_opts* opts, pmg_handl
   if (o.smoother != PMG_ASM_FDM || o.precond_geom != PMG_FLAT_LINEARISED)
     return fail(PMG_ERR_INVALID, "unsupported smoother or preconditioner geometry");
   if (o.overlap < 0 || o.overlap > MAXO || o.nu < 1 || !(o.omega > 0) || !(o.tol > 0) || o.max_iter < 1 ||
-      o.inner_max < 1 || !(o.inner_tol > 0))
+      o.inner_max < 1 || !(o.inner_tol > 0) || o.fuse_residual < -1 || o.fuse_residual > 1)
     return fail(PMG_ERR_INVALID, "bad solver options");
   std::vector<int> orders;
   if (o.nlevels > 0) {
@@ -1547,6 +1584,18 @@ pmg_status pmg_autotune(pmg_handle* h) {
       L.thr_fdm32 = thr;
       return level_fdm<float>(h, l, t, x, 0, cs);
     }, &L.thr_fdm32));
+    {
+      // residual launch + sweep, or one sweep that forms its residual (x -> t ping-pong)
+      float us_split = 0.f, us_fused = 0.f;
+      CKS(time_launches(h, [&](int thr, cudaStream_t cs) {
+        CKS(level_residual<float>(h, l, b, x, t, 1, cs));
+        return level_fdm<float>(h, l, t, x, 0, cs);
+      }, L.thr_fdm32, 10, &us_split));
+      CKS(time_launches(h, [&](int thr, cudaStream_t cs) {
+        return level_fdm<float>(h, l, nullptr, x, 0, cs, b, t, false);
+      }, L.thr_fdm32, 10, &us_fused));
+      if (h->opts.fuse_residual < 0) L.fuse_res = L.order >= 2 && us_fused < 0.97f * us_split;
+    }
     LevelDev& C = h->lv[l + 1];
     CKS(tune_one(h, TK_XFER, L.order * 16 + C.order, L.s.NZ, [&](int thr, cudaStream_t cs) {
       L.thr_xfer = thr;
@@ -1557,6 +1606,10 @@ pmg_status pmg_autotune(pmg_handle* h) {
     h->thr_curved32 = thr;
     return curved<float>(h, 0, h->r32, nullptr, h->w32, 1, nullptr, cs);
   }, &h->thr_curved32));
+  CKS(tune_one(h, TK_CURVED64, h->mesh.order, h->lv[0].s.NZ, [&](int thr, cudaStream_t cs) {
+    h->thr_curved64 = thr;
+    return curved<double>(h, 0, h->p, nullptr, h->w, 1, nullptr, cs);
+  }, &h->thr_curved64));
   // graphs built before tuning keep the old sizes: rebuild on next use
   for (pmg_handle::Loop* lp : {&h->loop64, &h->loop32})
     if (lp->exec) { cudaGraphExecDestroy(lp->exec); lp->exec = nullptr; }

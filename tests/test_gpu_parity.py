@@ -41,10 +41,11 @@ CASES = {
 _cache = {}
 
 
-def case(name):
-    if name not in _cache:
-        _cache[name] = Case(CASES[name]())
-    return _cache[name]
+def case(name, **opts):
+    key = (name, tuple(sorted(opts.items())))
+    if key not in _cache:
+        _cache[key] = Case(CASES[name](), **opts)
+    return _cache[key]
 
 
 def scale_of(A, x):
@@ -109,9 +110,12 @@ def test_level_operators_and_transfers(name):
             assert np.max(np.abs(xf - xf_ref)) <= tol * max(1.0, np.max(np.abs(xf_ref))), (l, dt)
 
 
+@pytest.mark.parametrize("fuse", [0, 1])
 @pytest.mark.parametrize("name", list(CASES))
-def test_smoother(name):
-    c = case(name)
+def test_smoother(name, fuse):
+    """nu = 2 sweeps; FP32 with the residual launched apart (fuse 0) or formed inside the
+    sweep kernel with the iterate ping-ponged (fuse 1)."""
+    c = case(name, fuse_residual=fuse)
     H = c.hierarchy()
     rng = np.random.default_rng(3)
     for l, lev in enumerate(H.levels[:-1]):
@@ -160,7 +164,8 @@ SOLVE_CASES = ["tank12x3p6", "cfg1", "periodic8x3p5", "tank6x2p8", "tank5x1p4_nz
 @pytest.mark.parametrize("variant", [dict(), dict(outer=pmg.PMG_FCG), dict(outer=pmg.PMG_PDC),
                                      dict(precision=pmg.PMG_MIXED_FP32),
                                      dict(precision=pmg.PMG_MIXED_FP32, outer=pmg.PMG_IR),
-                                     dict(precision=pmg.PMG_MIXED_FP32, outer=pmg.PMG_PDC)])
+                                     dict(precision=pmg.PMG_MIXED_FP32, outer=pmg.PMG_PDC),
+                                     dict(precision=pmg.PMG_MIXED_FP32, fuse_residual=1)])
 def test_solve_matches_direct(name, variant):
     w = CASES[name]()
     c = Case(w, tol=1e-12, **variant)

@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg3", "cfg4", "cfg5"])
+    ap.add_argument("--variants", action="store_true",
+                    help="cfg2/cfg3: every precision variant (iterations, time, error vs FP64) and the "
+                         "operator kernels (FP64, FP32, BF16 tensor cores) side by side")
     ap.add_argument("--tank-steps", type=int, default=1000, help="cfg5: RK4 steps per run")
     ap.add_argument("--train-steps", type=int, default=200, help="cfg5: steps whose solves train the warm start")
     ap.add_argument("--filter", default="strong", choices=["strong", "few-percent", "none"],
@@ -413,6 +416,101 @@ def run_batch(args, ws, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_variants(args, ws, rank, local):
+    """Precision variants of the solve on one tank (config 3: 512 x 32, P = 8): plain FP64
+    PCG, FP64 flexible CG around the FP32 V-cycle, FP64 refinement around an inner FP32
+    flexible CG, and the same with the inner operator on the BF16 tensor cores.  Each:
+    iterations, device time per solve (CUDA events, L2 flushed), relative L2 error against
+    an FP64 solve to 1e-12.  Then the operator builds timed alone."""
+    import torch
+    import paper_2411_14977_gb300.pmg as pmg
+
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pmg.load(build_if_missing=True)
+    w = workload(args.workload)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    variants = [("fp64_pcg", dict(precision=pmg.PMG_FP64)),
+                ("mixed_fp32_fcg", dict(precision=pmg.PMG_MIXED_FP32)),
+                ("mixed_fp32_ir", dict(precision=pmg.PMG_MIXED_FP32, outer=pmg.PMG_IR)),
+                ("mixed_bf16_ir", dict(precision=pmg.PMG_MIXED_BF16, outer=pmg.PMG_IR))]
+    ref = None
+    out = {}
+    clk = ClockSampler(local)
+    ref_info = None
+    for name, opts in [("reference_fp64_tol1e-12", dict(precision=pmg.PMG_FP64, tol=1e-12))] + variants:
+        S = pmg.Solver(**w.mesh_kwargs(), **opts)
+        xc, sr = S.node_coords()
+        F = w.fields(xc, sr)
+        d = {k: torch.as_tensor(np.ascontiguousarray(F[k]), dtype=torch.float64, device=dev)
+             for k in ("eta", "u", "w", "pD")}
+        S.set_geometry(d["eta"])
+        S.autotune()
+        b = S.assemble_rhs_div(d["u"], d["w"])
+        p = torch.empty_like(b)
+        if ref is None:
+            _, ref_info = S.solve(b, d["pD"], out=p)
+            ref = p.clone()
+            S.close()
+            continue
+        for _ in range(max(args.warmup, 3)):
+            S.solve(b, d["pD"], out=p)
+        ts = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            _, info = S.solve(b, d["pD"], out=p)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        err = (torch.linalg.norm(p - ref) / torch.linalg.norm(ref)).item()
+        ms = float(np.median(ts))
+        out[name] = {"ms_per_solve": ms, "dof_per_s": S.n_free / (ms / 1e3), "iterations": info["iterations"],
+                     "inner_iterations": info["inner_iterations"], "rel_residual": info["rel_residual"],
+                     "rel_l2_err_vs_fp64": err}
+        log(name, out[name])
+        if name == "mixed_bf16_ir":
+            # the operator builds alone: CUDA-event time per launch (graph-free, warm)
+            x32 = torch.randn(S.n, dtype=torch.float32, device=dev)
+            x64 = x32.double()
+            kern = {}
+            for kname, fn in [("fp64_cuda_cores", lambda: S.apply(x64)),
+                              ("fp32_cuda_cores", lambda: S.apply_f32(x32)),
+                              ("bf16_tensor_split", lambda: S.apply_bf16(x32, split=True)),
+                              ("bf16_tensor_plain", lambda: S.apply_bf16(x32, split=False))]:
+                for _ in range(5):
+                    fn()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(50):
+                    fn()
+                e1.record()
+                torch.cuda.synchronize()
+                kern[kname] = {"us_per_apply": 1e3 * e0.elapsed_time(e1) / 50}
+            y64 = S.apply(x64)
+            for kname, fn in [("fp32_cuda_cores", lambda: S.apply_f32(x32)),
+                              ("bf16_tensor_split", lambda: S.apply_bf16(x32, split=True)),
+                              ("bf16_tensor_plain", lambda: S.apply_bf16(x32, split=False))]:
+                kern[kname]["rel_err_vs_fp64_apply"] = (torch.linalg.norm(fn().double() - y64) /
+                                                        torch.linalg.norm(y64)).item()
+            out["operator_kernels"] = kern
+            log("kernels", kern)
+        S.close()
+    clocks = clk.stop()
+    base = out["fp64_pcg"]["ms_per_solve"]
+    for k, v in out.items():
+        if "ms_per_solve" in v:
+            v["speedup_vs_fp64"] = base / v["ms_per_solve"]
+    print(json.dumps({"metric": METRIC, "workload": w.name, "nodes": int(S.n), "free_dof": int(S.n_free),
+                      "tol": 1e-10, "l2": "flushed before every timed solve", "variants": out,
+                      "reference": {"tol": 1e-12, "iterations": ref_info["iterations"],
+                                    "rel_residual": ref_info["rel_residual"]},
+                      "clocks": clocks}), flush=True)
+
+
 def run_tank(args, ws, rank, local):
     """Config 5: a nonlinear progressive wave (eta0 = 0.05 cos(pi x), kh = pi) in the
     periodic 256 x 16, P = 6 tank, classical RK4 with dt = T/100, four pressure solves per
@@ -547,6 +645,8 @@ def main():
         run_batch(args, ws, rank, local)
     elif args.workload == "cfg5":
         run_tank(args, ws, rank, local)
+    elif args.variants:
+        run_variants(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
 

@@ -53,7 +53,10 @@ enum { PMG_FP64 = 0, PMG_MIXED_FP32 = 1, PMG_MIXED_BF16 = 2 };
  *   PMG_PDC  preconditioned defect correction x <- x + B(b - Ax) (Sec. 5.4)
  *   PMG_IR   FP64 iterative refinement around an inner FP32 flexible-CG solve
  *            (mixed precision only; inner_max / inner_tol apply)
- * With PMG_MIXED_FP32 the V-cycle B runs in FP32 on the FP32-rounded residual. */
+ * With PMG_MIXED_FP32 the V-cycle B runs in FP32 on the FP32-rounded residual.
+ * PMG_MIXED_BF16 (requires PMG_IR): as PMG_MIXED_FP32, and the inner solve's
+ * actual-geometry operator runs its contractions on the BF16 tensor cores with hi/lo
+ * split operands and FP32 accumulation (pmg_apply_bf16, split = 1). */
 enum { PMG_PCG = 0, PMG_FCG = 1, PMG_PDC = 2, PMG_IR = 3 };
 /* smoother: element-block additive Schwarz (Sec. 5.3), blocks inverted by fast
  * diagonalisation (exact for the separable flat-geometry level operators) */
@@ -160,6 +163,11 @@ pmg_status pmg_residual_norm(pmg_handle* h, const double* b, const double* p_dir
 pmg_status pmg_apply(pmg_handle* h, const double* x_dev, double* y_dev, void* stream);
 /* The same operator in FP32 storage and arithmetic. */
 pmg_status pmg_apply_f32(pmg_handle* h, const float* x_dev, float* y_dev, void* stream);
+/* The same FP32 operator with its four sum-factorised contractions on the BF16 tensor
+ * cores (mma.sync m16n8k16, FP32 accumulation): split = 0 rounds D and the operand to
+ * BF16 once; split = 1 adds hi*hi + hi*lo + lo*hi of their BF16 hi/lo parts (about 16
+ * significant bits per product).  Not in the paper.  x, y: NX*NZ floats on the device. */
+pmg_status pmg_apply_bf16(pmg_handle* h, const float* x_dev, float* y_dev, int split, void* stream);
 /* Flat level-l operator (the multigrid level matrix), masked like pmg_apply.
  * f32 = 0: FP64 vectors, 1: FP32 vectors. */
 pmg_status pmg_level_apply(pmg_handle* h, int level, const void* x_dev, void* y_dev, int f32,

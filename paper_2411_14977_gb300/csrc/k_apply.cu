@@ -21,209 +21,9 @@
 
 PMG_DEFINE_CONST_TABLES(init_consts_apply)
 
+#include "k_curved.cuh"
+
 namespace pmg {
-
-enum { MODE_APPLY = 0, MODE_RESIDUAL = 1, MODE_DOT = 2, MODE_DIV = 3 };
-
-template <typename T>
-struct CurvedParams {
-  Shape s;
-  const T* x;       // input (MODE_DIV: u)
-  const T* x2;      // MODE_DIV: w
-  const T* b;       // MODE_RESIDUAL: load vector
-  T* y;             // output
-  const T* geo;     // [Nx][P+1][4]: A, B, C, E
-  const T* sigma;   // [NZ]
-  T scale;          // MODE_DIV: scale
-  int mask_input;   // 1: surface-row input read as zero
-  double* result;   // MODE_RESIDUAL: ||r||^2, MODE_DOT: <x, y>
-  Scratch sc;
-};
-
-template <int P, typename T, int MODE>
-__global__ void __launch_bounds__(512) k_curved(CurvedParams<T> p) {
-  constexpr int n = P + 1;
-  const Shape s = p.s;
-  const int NZ = s.NZ, Nz = s.Nz, NZp = slab_pitch(NZ);
-  const int L = Nz * n;
-  const int ex = blockIdx.x;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* X = reinterpret_cast<T*>(smem_raw);   // [n][NZp]   input slab, later Y
-  T* Ur = X + n * NZp;                      // [n][NZp]   U_r per node row
-  T* Ws = Ur + n * NZp;                     // [Nz][n][n] (ez, j, i): U_s then W_s
-  T* Wr = Ws + L * n;                       // [Nz][n][n] (ez, j, i): W_r
-  T* G = Wr + L * n;                        // [n][4]
-  T* SG = G + 4 * n;                        // [NZ] sigma
-  T* BB = SG + NZ;                          // [n][NZp] b (MODE_RESIDUAL) or x (MODE_DOT) of the slab
-  size_t red_off = (((size_t)(3 * n * NZp + 2 * L * n + 4 * n + NZ) * sizeof(T)) + 15) & ~(size_t)15;
-  double* red = reinterpret_cast<double*>(smem_raw + red_off);  // 34 doubles
-  int* s_flag = reinterpret_cast<int*>(red + 34);
-  T* Y = X;
-
-  const int col0 = ex * P;
-  // ---- load the slab, the column factors and sigma
-  for_slab(n, NZ, [&](int i, int iz) {
-    size_t g = (size_t)wrap_col(s, col0 + i) * NZ + iz;
-    bool ok = !(MODE != MODE_DIV && p.mask_input && iz == NZ - 1);
-    cp_async_elem(&X[i * NZp + iz], p.x + g, ok);
-    if (MODE == MODE_DIV) cp_async_elem(&Ur[i * NZp + iz], p.x2 + g, true);
-    if (MODE == MODE_RESIDUAL) cp_async_elem(&BB[i * NZp + iz], p.b + g, true);
-    if (MODE == MODE_DOT) cp_async_elem(&BB[i * NZp + iz], p.x + g, ok);  // X is reused for Y
-  });
-  cp_async_wait_all();
-  for (int t = threadIdx.x; t < 4 * n; t += blockDim.x) G[t] = p.geo[(size_t)ex * 4 * n + t];
-  for (int t = threadIdx.x; t < NZ; t += blockDim.x) SG[t] = p.sigma[t];
-  __syncthreads();
-
-  if (MODE != MODE_DIV) {
-    // ---- phase 1: U_r along x, one node row per thread
-    for (int iz = threadIdx.x; iz < NZ; iz += blockDim.x) {
-      T xv[n];
-#pragma unroll
-      for (int m = 0; m < n; ++m) xv[m] = X[m * NZp + iz];
-#pragma unroll
-      for (int i = 0; i < n; ++i) {
-        T acc = T(0);
-#pragma unroll
-        for (int m = 0; m < n; ++m) acc += CT<T>::D(cT, P, i, m) * xv[m];
-        Ur[i * NZp + iz] = acc;
-      }
-    }
-    // ---- phase 2: U_s along sigma, one (column i, element ez) per thread
-    for (int t = threadIdx.x; t < L; t += blockDim.x) {
-      int i = t % n, ez = t / n;
-      T xv[n];
-#pragma unroll
-      for (int m = 0; m < n; ++m) xv[m] = X[i * NZp + ez * P + m];
-#pragma unroll
-      for (int j = 0; j < n; ++j) {
-        T acc = T(0);
-#pragma unroll
-        for (int m = 0; m < n; ++m) acc += CT<T>::D(cT, P, j, m) * xv[m];
-        Ws[(ez * n + j) * n + i] = acc;
-      }
-    }
-    __syncthreads();
-    // ---- phase 3: pointwise metric
-    for (int t = threadIdx.x; t < L * n; t += blockDim.x) {
-      int i = t % n, r = t / n, j = r % n, ez = r / n;
-      int iz = ez * P + j;
-      T wj = CT<T>::w(cT, P, j);
-      T sg = SG[iz];
-      T ur = Ur[i * NZp + iz];
-      T us = Ws[t];
-      T grr = wj * G[i * 4 + 0];
-      T grs = -wj * sg * G[i * 4 + 1];
-      T gss = wj * G[i * 4 + 2] * (T(1) + sg * sg * G[i * 4 + 3]);
-      Wr[t] = grr * ur + grs * us;
-      Ws[t] = grs * ur + gss * us;
-    }
-  } else {
-    // ---- divergence load vector: W_r = w_i w_j (d dsig/2) u, W_s = w_i w_j (dx/2)(w - sigma d_x u)
-    // Column factors in this mode: A = w_i d dsig/2, B = w_i d_x, C = w_i dx/2.
-    for (int t = threadIdx.x; t < L * n; t += blockDim.x) {
-      int i = t % n, r = t / n, j = r % n, ez = r / n;
-      int iz = ez * P + j;
-      T wj = CT<T>::w(cT, P, j);
-      T u = X[i * NZp + iz], w = Ur[i * NZp + iz];
-      Wr[t] = p.scale * wj * G[i * 4 + 0] * u;
-      Ws[t] = p.scale * wj * (G[i * 4 + 2] * w - SG[iz] * G[i * 4 + 1] * (G[i * 4 + 2] / CT<T>::w(cT, P, i)) * u);
-    }
-  }
-  __syncthreads();
-  // ---- phase 4a: x-contraction Y[i][iz] = sum_k D[k][i] sum_{ez owning iz} W_r
-  for (int iz = threadIdx.x; iz < NZ; iz += blockDim.x) {
-    int ez = min(iz / P, Nz - 1), j = iz - ez * P;
-    T wv[n];
-#pragma unroll
-    for (int k = 0; k < n; ++k) wv[k] = Wr[(ez * n + j) * n + k];
-    if (j == 0 && ez > 0) {
-#pragma unroll
-      for (int k = 0; k < n; ++k) wv[k] += Wr[((ez - 1) * n + P) * n + k];
-    }
-#pragma unroll
-    for (int i = 0; i < n; ++i) {
-      T acc = T(0);
-#pragma unroll
-      for (int k = 0; k < n; ++k) acc += CT<T>::D(cT, P, k, i) * wv[k];
-      Y[i * NZp + iz] = acc;
-    }
-  }
-  __syncthreads();
-  // ---- phase 4b: sigma-contraction of the rows [ez P, ez P + P) owned by (i, ez)
-  for (int t = threadIdx.x; t < L; t += blockDim.x) {
-    int i = t % n, ez = t / n;
-    T wv[n];
-#pragma unroll
-    for (int k = 0; k < n; ++k) wv[k] = Ws[(ez * n + k) * n + i];
-    T below = T(0);
-    if (ez > 0) {
-#pragma unroll
-      for (int k = 0; k < n; ++k) below += CT<T>::D(cT, P, k, P) * Ws[((ez - 1) * n + k) * n + i];
-    }
-#pragma unroll
-    for (int j = 0; j < P; ++j) {
-      T acc = (j == 0) ? below : T(0);
-#pragma unroll
-      for (int k = 0; k < n; ++k) acc += CT<T>::D(cT, P, k, j) * wv[k];
-      Y[i * NZp + ez * P + j] += acc;
-    }
-    if (ez == Nz - 1) {  // surface row: used by MODE_DIV only (masked otherwise)
-      T acc = T(0);
-#pragma unroll
-      for (int k = 0; k < n; ++k) acc += CT<T>::D(cT, P, k, P) * wv[k];
-      Y[i * NZp + NZ - 1] += acc;
-    }
-  }
-  __syncthreads();
-
-  // ---- epilogue
-  auto finish = [&](int ix, int i, int iz, T val, Acc<T>& ac) {  // i: local column of ix
-    size_t g = (size_t)ix * NZ + iz;
-    bool top = iz == NZ - 1;
-    if (MODE == MODE_APPLY) {
-      p.y[g] = top ? p.x[g] : val;
-    } else if (MODE == MODE_RESIDUAL) {
-      T r = top ? T(0) : BB[i * NZp + iz] - val;
-      p.y[g] = r;
-      ac.fma(r, r);
-    } else if (MODE == MODE_DOT) {
-      T v = top ? T(0) : val;
-      p.y[g] = v;
-      ac.fma(BB[i * NZp + iz], v);
-    } else {
-      p.y[g] = top ? T(0) : val;
-    }
-  };
-  Acc<T> acc;
-  for_slab(P - 1, NZ, [&](int c, int iz) { finish(col0 + 1 + c, c + 1, iz, Y[(c + 1) * NZp + iz], acc); });
-  const int nedges = s.periodic ? s.Nx : s.Nx + 1;
-  T* eb = reinterpret_cast<T*>(p.sc.edgebuf);
-#pragma unroll 1
-  for (int side = 0; side < 2; ++side) {
-    int i = side == 0 ? 0 : P;
-    int e = side == 0 ? ex : (s.periodic ? (ex + 1) % s.Nx : ex + 1);
-    bool single = !s.periodic && (e == 0 || e == s.Nx);
-    int ix = e * P;
-    Acc<T> eacc;
-    if (single) {
-      for (int iz = threadIdx.x; iz < NZ; iz += blockDim.x) finish(ix, i, iz, Y[i * NZp + iz], eacc);
-    } else {
-      T* buf = eb + (size_t)e * NZ;
-      for (int iz = threadIdx.x; iz < NZ; iz += blockDim.x) atomic_add_t(buf + iz, Y[i * NZp + iz]);
-      if (!edge_arrive(p.sc.edgecnt + e, 2, s_flag)) continue;
-      for (int iz = threadIdx.x; iz < NZ; iz += blockDim.x) finish(ix, i, iz, take_t(buf + iz), eacc);
-    }
-    if (MODE == MODE_RESIDUAL || MODE == MODE_DOT) {
-      double v = block_sum(eacc.value(), red);
-      if (threadIdx.x == 0) p.sc.edgepart[e] = v;
-    }
-  }
-  if (MODE == MODE_RESIDUAL || MODE == MODE_DOT) {
-    double v = block_sum(acc.value(), red);
-    grid_reduce(p.sc, v, nedges, p.result, red, s_flag);
-  }
-}
 
 template <int P, typename T>
 __global__ void k_geometry(Shape s, const double* eta, double h, double dx, double dsig, int div,
@@ -275,35 +75,6 @@ __global__ void k_rhs_source(Shape s, const double* eta, double h, double dx, do
 }
 
 template <typename T>
-static size_t curved_smem(int P, int NZ, int Nz) {
-  int n = P + 1, NZp = slab_pitch(NZ), L = Nz * n;
-  size_t e = (size_t)3 * n * NZp + (size_t)2 * L * n + 4 * n + NZ;
-  return ((e * sizeof(T) + 15) & ~(size_t)15) + 34 * sizeof(double) + 16;
-}
-
-template <int P, typename T, int MODE>
-static cudaError_t launch_curved_p(const CurvedParams<T>& prm, int threads, cudaStream_t st) {
-  size_t sm = curved_smem<T>(P, prm.s.NZ, prm.s.Nz);
-  auto k = k_curved<P, T, MODE>;
-  static std::atomic<unsigned long long> s_mask{0};
-  cudaError_t e = ensure_max_smem(k, s_mask);
-  if (e != cudaSuccess) return e;
-  k<<<prm.s.Nx, threads, sm, st>>>(prm);
-  return cudaGetLastError();
-}
-
-template <typename T, int MODE>
-static cudaError_t launch_curved(const CurvedParams<T>& prm, int threads, cudaStream_t st) {
-  switch (prm.s.P) {
-#define PMG_CASE(PP) case PP: return launch_curved_p<PP, T, MODE>(prm, threads, st);
-    PMG_CASE(1) PMG_CASE(2) PMG_CASE(3) PMG_CASE(4) PMG_CASE(5)
-    PMG_CASE(6) PMG_CASE(7) PMG_CASE(8) PMG_CASE(9) PMG_CASE(10)
-#undef PMG_CASE
-    default: return cudaErrorInvalidValue;
-  }
-}
-
-template <typename T>
 cudaError_t curved_op(const CurvedArgs& a, cudaStream_t st) {
   CurvedParams<T> p;
   p.s = a.s;
@@ -318,11 +89,15 @@ cudaError_t curved_op(const CurvedArgs& a, cudaStream_t st) {
   p.result = a.result;
   p.sc = a.sc;
   int thr = (a.threads >= 32 && a.threads <= 512) ? a.threads : 256;
+  if (a.tc) {
+    if (!std::is_same<T, float>::value || (a.mode != MODE_APPLY && a.mode != MODE_DOT)) return cudaErrorInvalidValue;
+    return curved_op_tc(a, st);
+  }
   switch (a.mode) {
-    case MODE_APPLY: return launch_curved<T, MODE_APPLY>(p, thr, st);
-    case MODE_RESIDUAL: return launch_curved<T, MODE_RESIDUAL>(p, thr, st);
-    case MODE_DOT: return launch_curved<T, MODE_DOT>(p, thr, st);
-    case MODE_DIV: return launch_curved<T, MODE_DIV>(p, thr, st);
+    case MODE_APPLY: return launch_curved<T, MODE_APPLY, 0>(p, thr, st);
+    case MODE_RESIDUAL: return launch_curved<T, MODE_RESIDUAL, 0>(p, thr, st);
+    case MODE_DOT: return launch_curved<T, MODE_DOT, 0>(p, thr, st);
+    case MODE_DIV: return launch_curved<T, MODE_DIV, 0>(p, thr, st);
   }
   return cudaErrorInvalidValue;
 }

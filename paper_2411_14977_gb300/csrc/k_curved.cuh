@@ -1,0 +1,369 @@
+// Actual-geometry operator kernel template, shared by the CUDA-core build (k_apply.cu,
+// TC = 0) and the BF16 tensor-core build (k_apply_tc.cu, TC = 1 or 3).  The including
+// translation unit defines the constant tables cT first (PMG_DEFINE_CONST_TABLES).
+//
+// TC != 0 (FP32 vectors): the four sum-factorised contractions U_r = D U, U_s = U D^T,
+// D^T W_r, W_s D run on the tensor cores as mma.sync m16n8k16 tiles with BF16 operands
+// and FP32 accumulation: the (P+1) x (P+1) matrix D (or D^T) padded to 16 x 16 is the A
+// operand, eight node rows (or element columns) of the slab form the 16 x 8 B operand.
+// TC = 1 rounds both operands to BF16 once; TC = 3 splits each into hi + lo BF16 parts
+// and adds the three products hi*hi + hi*lo + lo*hi, which keeps about 16 significant
+// bits of every product instead of 8.
+#pragma once
+#include <cuda_bf16.h>
+
+#include <type_traits>
+
+namespace pmg {
+
+enum { MODE_APPLY = 0, MODE_RESIDUAL = 1, MODE_DOT = 2, MODE_DIV = 3 };
+
+template <typename T>
+struct CurvedParams {
+  Shape s;
+  const T* x;       // input (MODE_DIV: u)
+  const T* x2;      // MODE_DIV: w
+  const T* b;       // MODE_RESIDUAL: load vector
+  T* y;             // output
+  const T* geo;     // [Nx][P+1][4]: A, B, C, E
+  const T* sigma;   // [NZ]
+  T scale;          // MODE_DIV: scale
+  int mask_input;   // 1: surface-row input read as zero
+  double* result;   // MODE_RESIDUAL: ||r||^2, MODE_DOT: <x, y>
+  Scratch sc;
+};
+
+// ---- BF16 tensor-core helpers (mma.sync.m16n8k16, fragment layouts of the PTX ISA)
+__device__ __forceinline__ unsigned bf16_pack(float first, float second) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(first, second);  // first -> low 16 bits
+  return *reinterpret_cast<unsigned*>(&v);
+}
+__device__ __forceinline__ float bf16_round(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+
+__device__ __forceinline__ void mma_bf16_16816(float c[4], const unsigned a[4], unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+enum class TcKind { D, DT };  // A operand: D[r][k] or its transpose D[k][r]
+
+// out(r, c) = sum_k A(r, k) B(k, c) for r, k < P+1 and the tile columns c of `ntiles` tiles
+// of 8; the warps of the CTA take the tiles round robin.  getb(k, c) returns B (zero
+// beyond the valid columns), put(r, c, v) is called for r < P+1 (c may exceed the valid
+// range: put checks).
+template <int P, int TC, class GetB, class Put>
+__device__ __forceinline__ void tc_contract(TcKind kind, int ntiles, GetB getb, Put put) {
+  constexpr int n = P + 1;
+  static_assert(n <= 16, "one 16 x 16 A tile");
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  // A fragment registers: (g, 2t..2t+1), (g+8, 2t..), (g, 2t+8..), (g+8, 2t+8..)
+  unsigned ah[4], al[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    int r = g + ((q & 1) ? 8 : 0), k = 2 * t + ((q & 2) ? 8 : 0);
+    float v0 = 0.f, v1 = 0.f;
+    if (r < n && k < n) v0 = kind == TcKind::D ? cT.Df[P][r][k] : cT.Df[P][k][r];
+    if (r < n && k + 1 < n) v1 = kind == TcKind::D ? cT.Df[P][r][k + 1] : cT.Df[P][k + 1][r];
+    float h0 = bf16_round(v0), h1 = bf16_round(v1);
+    ah[q] = bf16_pack(h0, h1);
+    al[q] = bf16_pack(v0 - h0, v1 - h1);
+  }
+  for (int tt = warp; tt < ntiles; tt += nwarps) {
+    const int c0 = tt * 8;
+    // B fragment registers: (k = 2t..2t+1, col g), (k = 2t+8.., col g)
+    float bv[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int k = 2 * t + (q & 1) + ((q & 2) ? 8 : 0);
+      bv[q] = k < n ? getb(k, c0 + g) : 0.f;
+    }
+    float bh[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) bh[q] = bf16_round(bv[q]);
+    float c[4] = {0.f, 0.f, 0.f, 0.f};
+    mma_bf16_16816(c, ah, bf16_pack(bh[0], bh[1]), bf16_pack(bh[2], bh[3]));
+    if (TC == 3) {
+      mma_bf16_16816(c, ah, bf16_pack(bv[0] - bh[0], bv[1] - bh[1]), bf16_pack(bv[2] - bh[2], bv[3] - bh[3]));
+      mma_bf16_16816(c, al, bf16_pack(bh[0], bh[1]), bf16_pack(bh[2], bh[3]));
+    }
+    // C fragment: (g, c0 + 2t..2t+1), (g + 8, c0 + 2t..)
+    if (g < n) {
+      put(g, c0 + 2 * t, c[0]);
+      put(g, c0 + 2 * t + 1, c[1]);
+    }
+    if (g + 8 < n) {
+      put(g + 8, c0 + 2 * t, c[2]);
+      put(g + 8, c0 + 2 * t + 1, c[3]);
+    }
+  }
+}
+
+template <int P, typename T, int MODE, int TC>
+__global__ void __launch_bounds__(512) k_curved(CurvedParams<T> p) {
+  static_assert(TC == 0 || (std::is_same<T, float>::value && MODE != MODE_DIV), "tensor-core path: FP32 operator");
+  constexpr int n = P + 1;
+  const Shape s = p.s;
+  const int NZ = s.NZ, Nz = s.Nz, NZp = slab_pitch(NZ);
+  const int L = Nz * n;
+  const int ex = blockIdx.x;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* X = reinterpret_cast<T*>(smem_raw);   // [n][NZp]   input slab, later Y
+  T* Ur = X + n * NZp;                      // [n][NZp]   U_r per node row
+  T* Ws = Ur + n * NZp;                     // [Nz][n][n] (ez, j, i): U_s then W_s
+  T* Wr = Ws + L * n;                       // [Nz][n][n] (ez, j, i): W_r
+  T* G = Wr + L * n;                        // [n][4]
+  T* SG = G + 4 * n;                        // [NZ] sigma
+  T* BB = SG + NZ;                          // [n][NZp] b (MODE_RESIDUAL) or x (MODE_DOT) of the slab
+  size_t red_off = (((size_t)(3 * n * NZp + 2 * L * n + 4 * n + NZ) * sizeof(T)) + 15) & ~(size_t)15;
+  double* red = reinterpret_cast<double*>(smem_raw + red_off);  // 34 doubles
+  int* s_flag = reinterpret_cast<int*>(red + 34);
+  T* Y = X;
+
+  const int col0 = ex * P;
+  // ---- load the slab, the column factors and sigma
+  for_slab(n, NZ, [&](int i, int iz) {
+    size_t g = (size_t)wrap_col(s, col0 + i) * NZ + iz;
+    bool ok = !(MODE != MODE_DIV && p.mask_input && iz == NZ - 1);
+    cp_async_elem(&X[i * NZp + iz], p.x + g, ok);
+    if (MODE == MODE_DIV) cp_async_elem(&Ur[i * NZp + iz], p.x2 + g, true);
+    if (MODE == MODE_RESIDUAL) cp_async_elem(&BB[i * NZp + iz], p.b + g, true);
+    if (MODE == MODE_DOT) cp_async_elem(&BB[i * NZp + iz], p.x + g, ok);  // X is reused for Y
+  });
+  cp_async_wait_all();
+  for (int t = threadIdx.x; t < 4 * n; t += blockDim.x) G[t] = p.geo[(size_t)ex * 4 * n + t];
+  for (int t = threadIdx.x; t < NZ; t += blockDim.x) SG[t] = p.sigma[t];
+  __syncthreads();
+
+  if (MODE != MODE_DIV) {
+    if constexpr (TC != 0) {
+      tc_contract<P, TC>(TcKind::D, (NZ + 7) / 8,
+          [&](int k, int c) { return c < NZ ? (float)X[k * NZp + c] : 0.f; },
+          [&](int i, int c, float v) { if (c < NZ) Ur[i * NZp + c] = v; });
+      tc_contract<P, TC>(TcKind::D, (L + 7) / 8,
+          [&](int k, int q) {
+            if (q >= L) return 0.f;
+            int ez = q / n, i = q - ez * n;
+            return (float)X[i * NZp + ez * P + k];
+          },
+          [&](int j, int q, float v) {
+            if (q < L) { int ez = q / n, i = q - ez * n; Ws[(ez * n + j) * n + i] = v; }
+          });
+    } else {
+    // ---- phase 1: U_r along x, one node row per thread
+    for (int iz = threadIdx.x; iz < NZ; iz += blockDim.x) {
+      T xv[n];
+#pragma unroll
+      for (int m = 0; m < n; ++m) xv[m] = X[m * NZp + iz];
+#pragma unroll
+      for (int i = 0; i < n; ++i) {
+        T acc = T(0);
+#pragma unroll
+        for (int m = 0; m < n; ++m) acc += CT<T>::D(cT, P, i, m) * xv[m];
+        Ur[i * NZp + iz] = acc;
+      }
+    }
+    // ---- phase 2: U_s along sigma, one (column i, element ez) per thread
+    for (int t = threadIdx.x; t < L; t += blockDim.x) {
+      int i = t % n, ez = t / n;
+      T xv[n];
+#pragma unroll
+      for (int m = 0; m < n; ++m) xv[m] = X[i * NZp + ez * P + m];
+#pragma unroll
+      for (int j = 0; j < n; ++j) {
+        T acc = T(0);
+#pragma unroll
+        for (int m = 0; m < n; ++m) acc += CT<T>::D(cT, P, j, m) * xv[m];
+        Ws[(ez * n + j) * n + i] = acc;
+      }
+    }
+    }  // CUDA-core contractions
+    __syncthreads();
+    // ---- phase 3: pointwise metric
+    for (int t = threadIdx.x; t < L * n; t += blockDim.x) {
+      int i = t % n, r = t / n, j = r % n, ez = r / n;
+      int iz = ez * P + j;
+      T wj = CT<T>::w(cT, P, j);
+      T sg = SG[iz];
+      T ur = Ur[i * NZp + iz];
+      T us = Ws[t];
+      T grr = wj * G[i * 4 + 0];
+      T grs = -wj * sg * G[i * 4 + 1];
+      T gss = wj * G[i * 4 + 2] * (T(1) + sg * sg * G[i * 4 + 3]);
+      Wr[t] = grr * ur + grs * us;
+      Ws[t] = grs * ur + gss * us;
+    }
+  } else {
+    // ---- divergence load vector: W_r = w_i w_j (d dsig/2) u, W_s = w_i w_j (dx/2)(w - sigma d_x u)
+    // Column factors in this mode: A = w_i d dsig/2, B = w_i d_x, C = w_i dx/2.
+    for (int t = threadIdx.x; t < L * n; t += blockDim.x) {
+      int i = t % n, r = t / n, j = r % n, ez = r / n;
+      int iz = ez * P + j;
+      T wj = CT<T>::w(cT, P, j);
+      T u = X[i * NZp + iz], w = Ur[i * NZp + iz];
+      Wr[t] = p.scale * wj * G[i * 4 + 0] * u;
+      Ws[t] = p.scale * wj * (G[i * 4 + 2] * w - SG[iz] * G[i * 4 + 1] * (G[i * 4 + 2] / CT<T>::w(cT, P, i)) * u);
+    }
+  }
+  __syncthreads();
+  if constexpr (TC != 0) {
+    // ---- phase 4a: Y[i][iz] = sum_k D[k][i] (W_r of the element(s) owning row iz)[k]
+    tc_contract<P, TC>(TcKind::DT, (NZ + 7) / 8,
+        [&](int k, int c) {
+          if (c >= NZ) return 0.f;
+          int ez = min(c / P, Nz - 1), j = c - ez * P;
+          float v = Wr[(ez * n + j) * n + k];
+          if (j == 0 && ez > 0) v += Wr[((ez - 1) * n + P) * n + k];
+          return v;
+        },
+        [&](int i, int c, float v) { if (c < NZ) Y[i * NZp + c] = v; });
+    __syncthreads();
+    // ---- phase 4b: T[ez][j][i] = sum_k D[k][j] W_s[ez][k][i] into the W_r buffer
+    tc_contract<P, TC>(TcKind::DT, (L + 7) / 8,
+        [&](int k, int q) {
+          if (q >= L) return 0.f;
+          int ez = q / n, i = q - ez * n;
+          return (float)Ws[(ez * n + k) * n + i];
+        },
+        [&](int j, int q, float v) {
+          if (q < L) { int ez = q / n, i = q - ez * n; Wr[(ez * n + j) * n + i] = v; }
+        });
+    __syncthreads();
+    // ---- phase 4c: rows shared by two elements take both elements' sums
+    for_slab(n, NZ, [&](int i, int iz) {
+      int ez = min(iz / P, Nz - 1), j = iz - ez * P;
+      float v = Wr[(ez * n + j) * n + i];
+      if (j == 0 && ez > 0) v += Wr[((ez - 1) * n + P) * n + i];
+      Y[i * NZp + iz] += v;
+    });
+    __syncthreads();
+  } else {
+  // ---- phase 4a: x-contraction Y[i][iz] = sum_k D[k][i] sum_{ez owning iz} W_r
+  for (int iz = threadIdx.x; iz < NZ; iz += blockDim.x) {
+    int ez = min(iz / P, Nz - 1), j = iz - ez * P;
+    T wv[n];
+#pragma unroll
+    for (int k = 0; k < n; ++k) wv[k] = Wr[(ez * n + j) * n + k];
+    if (j == 0 && ez > 0) {
+#pragma unroll
+      for (int k = 0; k < n; ++k) wv[k] += Wr[((ez - 1) * n + P) * n + k];
+    }
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+      T acc = T(0);
+#pragma unroll
+      for (int k = 0; k < n; ++k) acc += CT<T>::D(cT, P, k, i) * wv[k];
+      Y[i * NZp + iz] = acc;
+    }
+  }
+  __syncthreads();
+  // ---- phase 4b: sigma-contraction of the rows [ez P, ez P + P) owned by (i, ez)
+  for (int t = threadIdx.x; t < L; t += blockDim.x) {
+    int i = t % n, ez = t / n;
+    T wv[n];
+#pragma unroll
+    for (int k = 0; k < n; ++k) wv[k] = Ws[(ez * n + k) * n + i];
+    T below = T(0);
+    if (ez > 0) {
+#pragma unroll
+      for (int k = 0; k < n; ++k) below += CT<T>::D(cT, P, k, P) * Ws[((ez - 1) * n + k) * n + i];
+    }
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+      T acc = (j == 0) ? below : T(0);
+#pragma unroll
+      for (int k = 0; k < n; ++k) acc += CT<T>::D(cT, P, k, j) * wv[k];
+      Y[i * NZp + ez * P + j] += acc;
+    }
+    if (ez == Nz - 1) {  // surface row: used by MODE_DIV only (masked otherwise)
+      T acc = T(0);
+#pragma unroll
+      for (int k = 0; k < n; ++k) acc += CT<T>::D(cT, P, k, P) * wv[k];
+      Y[i * NZp + NZ - 1] += acc;
+    }
+  }
+  __syncthreads();
+
+  }  // CUDA-core contractions
+  // ---- epilogue
+  auto finish = [&](int ix, int i, int iz, T val, Acc<T>& ac) {  // i: local column of ix
+    size_t g = (size_t)ix * NZ + iz;
+    bool top = iz == NZ - 1;
+    if (MODE == MODE_APPLY) {
+      p.y[g] = top ? p.x[g] : val;
+    } else if (MODE == MODE_RESIDUAL) {
+      T r = top ? T(0) : BB[i * NZp + iz] - val;
+      p.y[g] = r;
+      ac.fma(r, r);
+    } else if (MODE == MODE_DOT) {
+      T v = top ? T(0) : val;
+      p.y[g] = v;
+      ac.fma(BB[i * NZp + iz], v);
+    } else {
+      p.y[g] = top ? T(0) : val;
+    }
+  };
+  Acc<T> acc;
+  for_slab(P - 1, NZ, [&](int c, int iz) { finish(col0 + 1 + c, c + 1, iz, Y[(c + 1) * NZp + iz], acc); });
+  const int nedges = s.periodic ? s.Nx : s.Nx + 1;
+  T* eb = reinterpret_cast<T*>(p.sc.edgebuf);
+#pragma unroll 1
+  for (int side = 0; side < 2; ++side) {
+    int i = side == 0 ? 0 : P;
+    int e = side == 0 ? ex : (s.periodic ? (ex + 1) % s.Nx : ex + 1);
+    bool single = !s.periodic && (e == 0 || e == s.Nx);
+    int ix = e * P;
+    Acc<T> eacc;
+    if (single) {
+      for (int iz = threadIdx.x; iz < NZ; iz += blockDim.x) finish(ix, i, iz, Y[i * NZp + iz], eacc);
+    } else {
+      T* buf = eb + (size_t)e * NZ;
+      for (int iz = threadIdx.x; iz < NZ; iz += blockDim.x) atomic_add_t(buf + iz, Y[i * NZp + iz]);
+      if (!edge_arrive(p.sc.edgecnt + e, 2, s_flag)) continue;
+      for (int iz = threadIdx.x; iz < NZ; iz += blockDim.x) finish(ix, i, iz, take_t(buf + iz), eacc);
+    }
+    if (MODE == MODE_RESIDUAL || MODE == MODE_DOT) {
+      double v = block_sum(eacc.value(), red);
+      if (threadIdx.x == 0) p.sc.edgepart[e] = v;
+    }
+  }
+  if (MODE == MODE_RESIDUAL || MODE == MODE_DOT) {
+    double v = block_sum(acc.value(), red);
+    grid_reduce(p.sc, v, nedges, p.result, red, s_flag);
+  }
+}
+
+template <typename T>
+static size_t curved_smem(int P, int NZ, int Nz) {
+  int n = P + 1, NZp = slab_pitch(NZ), L = Nz * n;
+  size_t e = (size_t)3 * n * NZp + (size_t)2 * L * n + 4 * n + NZ;
+  return ((e * sizeof(T) + 15) & ~(size_t)15) + 34 * sizeof(double) + 16;
+}
+
+template <int P, typename T, int MODE, int TC>
+static cudaError_t launch_curved_p(const CurvedParams<T>& prm, int threads, cudaStream_t st) {
+  size_t sm = curved_smem<T>(P, prm.s.NZ, prm.s.Nz);
+  auto k = k_curved<P, T, MODE, TC>;
+  static std::atomic<unsigned long long> s_mask{0};
+  cudaError_t e = ensure_max_smem(k, s_mask);
+  if (e != cudaSuccess) return e;
+  k<<<prm.s.Nx, threads, sm, st>>>(prm);
+  return cudaGetLastError();
+}
+
+template <typename T, int MODE, int TC>
+static cudaError_t launch_curved(const CurvedParams<T>& prm, int threads, cudaStream_t st) {
+  switch (prm.s.P) {
+#define PMG_CASE(PP) case PP: return launch_curved_p<PP, T, MODE, TC>(prm, threads, st);
+    PMG_CASE(1) PMG_CASE(2) PMG_CASE(3) PMG_CASE(4) PMG_CASE(5)
+    PMG_CASE(6) PMG_CASE(7) PMG_CASE(8) PMG_CASE(9) PMG_CASE(10)
+#undef PMG_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+
+}  // namespace pmg

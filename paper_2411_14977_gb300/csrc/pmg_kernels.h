@@ -32,6 +32,7 @@ enum Slot {
 
 // Per-TU constant-table initialisers.
 cudaError_t init_consts_apply(const ConstTables* host);
+cudaError_t init_consts_apply_tc(const ConstTables* host);
 cudaError_t init_consts_levels(const ConstTables* host);
 cudaError_t init_consts_fdm32(const float* table, size_t n, const float* K, size_t nk);
 cudaError_t init_consts_stepper(const ConstTables* host);
@@ -64,9 +65,11 @@ struct CurvedArgs {
   int mask_input;
   double* result;
   Scratch sc;
-  int threads = 256;   // CTA size (autotuned; 64..256)
+  int threads = 256;   // CTA size (autotuned; 64..512)
+  int tc = 0;          // FP32 only: 0 CUDA cores, 1 BF16 tensor cores, 3 BF16 hi/lo split
 };
 template <typename T> cudaError_t curved_op(const CurvedArgs& a, cudaStream_t st);
+cudaError_t curved_op_tc(const CurvedArgs& a, cudaStream_t st);
 template <typename T>
 cudaError_t geometry(const Shape& s, const double* eta, double h, double dx, double dsig, int div,
                      T* geo, int* status, cudaStream_t st);

@@ -94,6 +94,7 @@ pmg_status ensure_constants(int dev) {
     }
   }
   CK(init_consts_apply(&t));
+  CK(init_consts_apply_tc(&t));
   CK(init_consts_levels(&t));
   CK(init_consts_stepper(&t));
   {
@@ -235,6 +236,7 @@ struct pmg_handle {
   pmg_opts opts{};
   int device = 0;
   int thr_curved32 = 256, thr_curved64 = 256;  // CTA sizes of the actual-geometry operators (autotuner)
+  int tc = 0;  // FP32 operator in the inner solve: 0 CUDA cores, 3 BF16 tensor cores (hi/lo split)
   double dx = 0, dsig = 0, cx = 0, cz = 0;
   size_t N = 0, Nfree = 0;
   std::vector<int> orders;
@@ -593,9 +595,10 @@ pmg_status vcycle(pmg_handle* h, int l, const void* b, void* x, cudaStream_t st)
   return PMG_OK;
 }
 
+// tc: tensor-core variant of the FP32 operator (-1: the handle's, 0 CUDA cores, 1/3 BF16)
 template <typename T>
 pmg_status curved(pmg_handle* h, int mode, const void* x, const void* b, void* y, int mask, double* result,
-                  cudaStream_t st) {
+                  cudaStream_t st, int tc = -1) {
   CurvedArgs a{};
   a.s = h->lv[0].s;
   a.mode = mode;
@@ -609,6 +612,7 @@ pmg_status curved(pmg_handle* h, int mode, const void* x, const void* b, void* y
   a.result = result;
   a.sc = h->sc;
   a.threads = PI<T> ? h->thr_curved32 : h->thr_curved64;
+  if (PI<T> && (mode == 0 || mode == 2)) a.tc = tc >= 0 ? tc : h->tc;
   const Shape& F = a.s;
   double N = (double)F.NX * F.NZ, E = (double)F.Nx * F.Nz, n = F.P + 1;
   Cost c{(mode == 1 ? 3.0 : 2.0) * N * sizeof(T), E * (8.0 * n * n * n + 12.0 * n * n)};
@@ -1109,7 +1113,9 @@ pmg_status pmg_create(const pmg_mesh_desc* mesh, const pmg_opts* opts, pmg_handl
   if (!(m.x1 > m.x0) || !(m.h > 0.0)) return fail(PMG_ERR_INVALID, "need x1 > x0 and h > 0");
   if (m.periodic_x && (m.cells_x < 3 || (m.cells_x & (m.cells_x - 1))))
     return fail(PMG_ERR_INVALID, "periodic_x needs cells_x >= 3 and a power of two");
-  if (o.precision < 0 || o.precision > PMG_MIXED_FP32) return fail(PMG_ERR_INVALID, "unsupported precision");
+  if (o.precision < 0 || o.precision > PMG_MIXED_BF16) return fail(PMG_ERR_INVALID, "unsupported precision");
+  if (o.precision == PMG_MIXED_BF16 && o.outer != PMG_IR)
+    return fail(PMG_ERR_INVALID, "the BF16 operator runs in the inner solve of iterative refinement (outer = PMG_IR)");
   if (o.outer < PMG_PCG || o.outer > PMG_IR) return fail(PMG_ERR_INVALID, "bad outer method");
   if (o.outer == PMG_IR && o.precision == PMG_FP64)
     return fail(PMG_ERR_INVALID, "iterative refinement needs a mixed precision");
@@ -1138,6 +1144,7 @@ pmg_status pmg_create(const pmg_mesh_desc* mesh, const pmg_opts* opts, pmg_handl
   if (ensure_constants(h->device) != PMG_OK) return bail(PMG_ERR_CUDA);
   h->mesh = m;
   h->opts = o;
+  h->tc = o.precision == PMG_MIXED_BF16 ? 3 : 0;
   h->orders = orders;
   h->dx = (m.x1 - m.x0) / m.cells_x;
   h->dsig = 1.0 / m.cells_z;
@@ -1323,7 +1330,14 @@ pmg_status pmg_apply_f32(pmg_handle* h, const float* x, float* y, void* stream) 
   CKS(check_handle(h));
   if (!x || !y) return fail(PMG_ERR_INVALID, "NULL vector");
   DeviceGuard dg(h->device);
-  return curved<float>(h, 0, x, nullptr, y, 1, nullptr, (cudaStream_t)stream);
+  return curved<float>(h, 0, x, nullptr, y, 1, nullptr, (cudaStream_t)stream, 0);
+}
+
+pmg_status pmg_apply_bf16(pmg_handle* h, const float* x, float* y, int split, void* stream) {
+  CKS(check_handle(h));
+  if (!x || !y || split < 0 || split > 1) return fail(PMG_ERR_INVALID, "NULL vector or bad split flag");
+  DeviceGuard dg(h->device);
+  return curved<float>(h, 0, x, nullptr, y, 1, nullptr, (cudaStream_t)stream, split ? 3 : 1);
 }
 
 pmg_status pmg_level_apply(pmg_handle* h, int level, const void* x, void* y, int f32, void* stream) {

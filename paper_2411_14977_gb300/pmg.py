@@ -69,6 +69,7 @@ _SIGNATURES = {
     "pmg_residual_norm": (_I, [_P, _P, _P, _P, ctypes.POINTER(_D), _P]),
     "pmg_apply": (_I, [_P, _P, _P, _P]),
     "pmg_apply_f32": (_I, [_P, _P, _P, _P]),
+    "pmg_apply_bf16": (_I, [_P, _P, _P, _I, _P]),
     "pmg_level_apply": (_I, [_P, _I, _P, _P, _I, _P]),
     "pmg_level_smooth": (_I, [_P, _I, _P, _P, _I, _I, _P]),
     "pmg_restrict": (_I, [_P, _I, _P, _P, _I, _P]),
@@ -322,6 +323,13 @@ class Solver:
     def apply_f32(self, x, out=None):
         out = torch.empty_like(x) if out is None else out
         _check(load().pmg_apply_f32(self._h, _ptr(x, torch.float32), _ptr(out, torch.float32), _stream()))
+        return out
+
+    def apply_bf16(self, x, out=None, split=True):
+        """A x on the BF16 tensor cores (FP32 vectors); split: hi/lo BF16 parts."""
+        out = torch.empty_like(x) if out is None else out
+        _check(load().pmg_apply_bf16(self._h, _ptr(x, torch.float32), _ptr(out, torch.float32), int(bool(split)),
+                                     _stream()))
         return out
 
     @staticmethod

@@ -50,6 +50,9 @@ def test_default_opts():
     (dict(), dict(overlap=2), "options"),
     (dict(), dict(precision=7), "precision"),
     (dict(), dict(outer=3), "refinement needs a mixed precision"),
+    (dict(), dict(precision=2), "outer = PMG_IR"),
+    (dict(), dict(precision=2, outer=1), "outer = PMG_IR"),
+    (dict(), dict(fuse_residual=2), "options"),
     (dict(), dict(outer=4), "outer"),
     (dict(), dict(nlevels=4, levels=[4, 2, 2, 1]), "decrease"),
     (dict(), dict(nlevels=2, levels=[4, 2]), "order to 1"),

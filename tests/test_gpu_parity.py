@@ -67,6 +67,26 @@ def test_apply_fp64_and_fp32(name):
 
 
 @pytest.mark.parametrize("name", list(CASES))
+def test_apply_bf16_tensor_cores(name):
+    """The FP32 operator with its contractions on the BF16 tensor cores.  Plain BF16
+    operands (unit roundoff 2^-8 = 3.9e-3 each) stay within 3e-2 of the summand scale; the
+    hi/lo split keeps about 16 bits per product and stays within 2e-4, and is at least
+    ten times closer than the plain rounding."""
+    c = case(name)
+    A = c.m.assemble(c.eta)
+    rng = np.random.default_rng(11)
+    x = rng.standard_normal(c.m.N)
+    ref = apply_masked(A, x, c.m.dirichlet_mask())
+    s = scale_of(A, np.where(c.m.dirichlet_mask(), 0, x))
+    x32 = t(x, torch.float32)
+    e_split = np.max(np.abs(n(c.S.apply_bf16(x32, split=True)) - ref))
+    e_plain = np.max(np.abs(n(c.S.apply_bf16(x32, split=False)) - ref))
+    assert e_split <= 2e-4 * s, e_split / s
+    assert e_plain <= 3e-2 * s, e_plain / s
+    assert e_split <= 0.1 * e_plain
+
+
+@pytest.mark.parametrize("name", list(CASES))
 def test_rhs_assembly(name):
     c = case(name)
     ref = c.rhs_oracle()
@@ -165,7 +185,8 @@ SOLVE_CASES = ["tank12x3p6", "cfg1", "periodic8x3p5", "tank6x2p8", "tank5x1p4_nz
                                      dict(precision=pmg.PMG_MIXED_FP32),
                                      dict(precision=pmg.PMG_MIXED_FP32, outer=pmg.PMG_IR),
                                      dict(precision=pmg.PMG_MIXED_FP32, outer=pmg.PMG_PDC),
-                                     dict(precision=pmg.PMG_MIXED_FP32, fuse_residual=1)])
+                                     dict(precision=pmg.PMG_MIXED_FP32, fuse_residual=1),
+                                     dict(precision=pmg.PMG_MIXED_BF16, outer=pmg.PMG_IR)])
 def test_solve_matches_direct(name, variant):
     w = CASES[name]()
     c = Case(w, tol=1e-12, **variant)

@@ -76,15 +76,16 @@ __global__ void k_rhs_source(Shape s, const double* eta, double h, double dx, do
 
 template <typename T>
 cudaError_t curved_op(const CurvedArgs& a, cudaStream_t st) {
+  using IO = typename IOT<T>::type;
   CurvedParams<T> p;
   p.s = a.s;
-  p.x = (const T*)a.x;
-  p.x2 = (const T*)a.x2;
-  p.b = (const T*)a.b;
-  p.y = (T*)a.y;
-  p.geo = (const T*)a.geo;
-  p.sigma = (const T*)a.sigma;
-  p.scale = (T)a.scale;
+  p.x = (const IO*)a.x;
+  p.x2 = (const IO*)a.x2;
+  p.b = (const IO*)a.b;
+  p.y = (IO*)a.y;
+  p.geo = (const IO*)a.geo;
+  p.sigma = (const IO*)a.sigma;
+  p.scale = from_io<T>((IO)a.scale);
   p.mask_input = a.mask_input;
   p.result = a.result;
   p.sc = a.sc;
@@ -97,12 +98,15 @@ cudaError_t curved_op(const CurvedArgs& a, cudaStream_t st) {
     case MODE_APPLY: return launch_curved<T, MODE_APPLY, 0>(p, thr, st);
     case MODE_RESIDUAL: return launch_curved<T, MODE_RESIDUAL, 0>(p, thr, st);
     case MODE_DOT: return launch_curved<T, MODE_DOT, 0>(p, thr, st);
-    case MODE_DIV: return launch_curved<T, MODE_DIV, 0>(p, thr, st);
+    case MODE_DIV:
+      if constexpr (!std::is_same<T, df64>::value) return launch_curved<T, MODE_DIV, 0>(p, thr, st);
+      break;
   }
   return cudaErrorInvalidValue;
 }
 template cudaError_t curved_op<double>(const CurvedArgs&, cudaStream_t);
 template cudaError_t curved_op<float>(const CurvedArgs&, cudaStream_t);
+template cudaError_t curved_op<df64>(const CurvedArgs&, cudaStream_t);
 
 template <typename T>
 cudaError_t geometry(const Shape& s, const double* eta, double h, double dx, double dsig, int div,

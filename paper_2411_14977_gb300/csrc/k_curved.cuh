@@ -20,16 +20,17 @@ enum { MODE_APPLY = 0, MODE_RESIDUAL = 1, MODE_DOT = 2, MODE_DIV = 3 };
 
 template <typename T>
 struct CurvedParams {
+  using IO = typename IOT<T>::type;  // global-memory type (FP64 for double-float compute)
   Shape s;
-  const T* x;       // input (MODE_DIV: u)
-  const T* x2;      // MODE_DIV: w
-  const T* b;       // MODE_RESIDUAL: load vector
-  T* y;             // output
-  const T* geo;     // [Nx][P+1][4]: A, B, C, E
-  const T* sigma;   // [NZ]
-  T scale;          // MODE_DIV: scale
-  int mask_input;   // 1: surface-row input read as zero
-  double* result;   // MODE_RESIDUAL: ||r||^2, MODE_DOT: <x, y>
+  const IO* x;       // input (MODE_DIV: u)
+  const IO* x2;      // MODE_DIV: w
+  const IO* b;       // MODE_RESIDUAL: load vector
+  IO* y;             // output
+  const IO* geo;     // [Nx][P+1][4]: A, B, C, E
+  const IO* sigma;   // [NZ]
+  T scale;           // MODE_DIV: scale
+  int mask_input;    // 1: surface-row input read as zero
+  double* result;    // MODE_RESIDUAL: ||r||^2, MODE_DOT: <x, y>
   Scratch sc;
 };
 
@@ -134,11 +135,11 @@ __global__ void __launch_bounds__(512) k_curved(CurvedParams<T> p) {
     if (MODE == MODE_DOT) cp_async_elem(&BB[i * NZp + iz], p.x + g, ok);  // X is reused for Y
   });
   cp_async_wait_all();
-  for (int t = threadIdx.x; t < 4 * n; t += blockDim.x) G[t] = p.geo[(size_t)ex * 4 * n + t];
-  for (int t = threadIdx.x; t < NZ; t += blockDim.x) SG[t] = p.sigma[t];
+  for (int t = threadIdx.x; t < 4 * n; t += blockDim.x) G[t] = from_io<T>(p.geo[(size_t)ex * 4 * n + t]);
+  for (int t = threadIdx.x; t < NZ; t += blockDim.x) SG[t] = from_io<T>(p.sigma[t]);
   __syncthreads();
 
-  if (MODE != MODE_DIV) {
+  if constexpr (MODE != MODE_DIV) {
     if constexpr (TC != 0) {
       tc_contract<P, TC>(TcKind::D, (NZ + 7) / 8,
           [&](int k, int c) { return c < NZ ? (float)X[k * NZp + c] : 0.f; },
@@ -293,17 +294,17 @@ __global__ void __launch_bounds__(512) k_curved(CurvedParams<T> p) {
     size_t g = (size_t)ix * NZ + iz;
     bool top = iz == NZ - 1;
     if (MODE == MODE_APPLY) {
-      p.y[g] = top ? p.x[g] : val;
+      p.y[g] = top ? p.x[g] : to_io(val);
     } else if (MODE == MODE_RESIDUAL) {
       T r = top ? T(0) : BB[i * NZp + iz] - val;
-      p.y[g] = r;
+      p.y[g] = to_io(r);
       ac.fma(r, r);
     } else if (MODE == MODE_DOT) {
       T v = top ? T(0) : val;
-      p.y[g] = v;
+      p.y[g] = to_io(v);
       ac.fma(BB[i * NZp + iz], v);
     } else {
-      p.y[g] = top ? T(0) : val;
+      p.y[g] = to_io(top ? T(0) : val);
     }
   };
   Acc<T> acc;

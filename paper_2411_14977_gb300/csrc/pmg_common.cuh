@@ -21,6 +21,55 @@ constexpr int MAXP = 10;
 constexpr int MAXO = 1;
 constexpr int MAXNB = MAXP + 1 + 2 * MAXO;
 
+// Double-float number: value = hi + lo with |lo| <= ulp(hi)/2, two FP32 words (a 48-bit
+// significand, FP32 exponent range).  Arithmetic from the error-free transformations of
+// Knuth (TwoSum), Dekker (FastTwoSum) and the FMA product error (TwoProd): the products
+// and sums of the operator run on the FP32 pipe, which the GB300 issues 58x faster than
+// its FP64 pipe.  Addition is the one-correction ("sloppy") variant: its error is within
+// a few units of 2^-48 of the larger addend, i.e. relative to the summands, which is
+// the accuracy the operator needs (its output is compared with |A||x|).
+struct df64 {
+  float hi, lo;
+  df64() = default;
+  __host__ __device__ __forceinline__ explicit df64(float h) : hi(h), lo(0.f) {}
+  __host__ __device__ __forceinline__ df64(float h, float l) : hi(h), lo(l) {}
+};
+__host__ __device__ __forceinline__ df64 df64_from_double(double v) {
+  float h = (float)v;
+  return df64(h, (float)(v - (double)h));
+}
+__host__ __device__ __forceinline__ double df64_to_double(df64 a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ df64 df64_fast_two_sum(float a, float b) {  // |a| >= |b| or a == 0
+  float s = a + b;
+  return df64(s, b - (s - a));
+}
+__device__ __forceinline__ df64 operator+(df64 a, df64 b) {
+  float s = a.hi + b.hi;
+  float bb = s - a.hi;
+  float e = (a.hi - (s - bb)) + (b.hi - bb);  // TwoSum error of the high parts
+  e += a.lo + b.lo;
+  return df64_fast_two_sum(s, e);
+}
+__device__ __forceinline__ df64 operator-(df64 a) { return df64(-a.hi, -a.lo); }
+__device__ __forceinline__ df64 operator-(df64 a, df64 b) { return a + (-b); }
+__device__ __forceinline__ df64 operator*(df64 a, df64 b) {
+  float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);  // TwoProd error of the high parts
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  return df64_fast_two_sum(p, e);
+}
+__device__ __forceinline__ df64& operator+=(df64& a, df64 b) { return a = a + b; }
+
+// Global-memory type of a compute type: double-float kernels read and write FP64.
+template <typename T> struct IOT { using type = T; };
+template <> struct IOT<df64> { using type = double; };
+template <typename T> __host__ __device__ __forceinline__ T from_io(typename IOT<T>::type v) { return v; }
+template <> __host__ __device__ __forceinline__ df64 from_io<df64>(double v) { return df64_from_double(v); }
+__host__ __device__ __forceinline__ float to_io(float v) { return v; }
+__host__ __device__ __forceinline__ double to_io(double v) { return v; }
+__host__ __device__ __forceinline__ double to_io(df64 v) { return df64_to_double(v); }
+
 struct ConstTables {
   double D[MAXP + 1][MAXP + 1][MAXP + 1];  // D[P][i][m] = d h_m/dr at r_i
   double K[MAXP + 1][MAXP + 1][MAXP + 1];  // 1D stiffness D^T diag(w) D
@@ -28,6 +77,8 @@ struct ConstTables {
   float Df[MAXP + 1][MAXP + 1][MAXP + 1];
   float Kf[MAXP + 1][MAXP + 1][MAXP + 1];
   float wf[MAXP + 1][MAXP + 1];
+  df64 Dd[MAXP + 1][MAXP + 1][MAXP + 1];  // D and w as double-float pairs
+  df64 wd[MAXP + 1][MAXP + 1];
 };
 
 template <typename T> struct CT;
@@ -40,6 +91,10 @@ template <> struct CT<float> {
   static __device__ __forceinline__ float D(const ConstTables& c, int P, int i, int m) { return c.Df[P][i][m]; }
   static __device__ __forceinline__ float K(const ConstTables& c, int P, int i, int m) { return c.Kf[P][i][m]; }
   static __device__ __forceinline__ float w(const ConstTables& c, int P, int i) { return c.wf[P][i]; }
+};
+template <> struct CT<df64> {
+  static __device__ __forceinline__ df64 D(const ConstTables& c, int P, int i, int m) { return c.Dd[P][i][m]; }
+  static __device__ __forceinline__ df64 w(const ConstTables& c, int P, int i) { return c.wd[P][i]; }
 };
 
 // Scratch shared by all kernels of a handle (kernels on one stream run one at a time).
@@ -77,6 +132,10 @@ __device__ __forceinline__ void cp_async_elem(T* smem_dst, const T* gsrc, bool v
   asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(dst), "l"(gsrc), "n"(sizeof(T)),
                "r"(nbytes)
                : "memory");
+}
+// Double-float slab element from an FP64 vector: converted in registers (no async copy).
+__device__ __forceinline__ void cp_async_elem(df64* smem_dst, const double* gsrc, bool valid) {
+  *smem_dst = valid ? df64_from_double(*gsrc) : df64(0.f);
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
@@ -123,6 +182,12 @@ struct Acc<float> {
   }
   __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
+template <>
+struct Acc<df64> {  // inner products of double-float data, accumulated in FP64 (N terms)
+  double s = 0.0;
+  __device__ __forceinline__ void fma(df64 a, df64 b) { s = ::fma(df64_to_double(a), df64_to_double(b), s); }
+  __device__ __forceinline__ double value() const { return s; }
+};
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -152,6 +217,9 @@ __device__ __forceinline__ double take_t(double* p) {
   return __longlong_as_double((long long)atomicExch((unsigned long long*)p, 0ull));
 }
 __device__ __forceinline__ float take_t(float* p) { return atomicExch(p, 0.0f); }
+// double-float partials travel through the FP64 edge buffer (two addends into zero)
+__device__ __forceinline__ void atomic_add_t(df64* p, df64 v) { atomicAdd(reinterpret_cast<double*>(p), df64_to_double(v)); }
+__device__ __forceinline__ df64 take_t(df64* p) { return df64_from_double(take_t(reinterpret_cast<double*>(p))); }
 
 // Fence-free two-party exchange of one value.  A slot holds a signalling-NaN marker
 // between launches (arithmetic never produces a signalling NaN).  Each of the two

@@ -83,9 +83,11 @@ pmg_status ensure_constants(int dev) {
     for (int i = 0; i < n; ++i) {
       t.w[P][i] = w[i];
       t.wf[P][i] = (float)w[i];
+      t.wd[P][i] = df64_from_double(w[i]);
       for (int m = 0; m < n; ++m) {
         t.D[P][i][m] = D[i * n + m];
         t.Df[P][i][m] = (float)D[i * n + m];
+        t.Dd[P][i][m] = df64_from_double(D[i * n + m]);
         double k = 0.0;
         for (int q = 0; q < n; ++q) k += D[q * n + i] * w[q] * D[q * n + m];
         t.K[P][i][m] = k;
@@ -237,6 +239,7 @@ struct pmg_handle {
   int device = 0;
   int thr_curved32 = 256, thr_curved64 = 256;  // CTA sizes of the actual-geometry operators (autotuner)
   int tc = 0;  // FP32 operator in the inner solve: 0 CUDA cores, 3 BF16 tensor cores (hi/lo split)
+  bool df64_outer = false;  // outer operator in double-float arithmetic (FP64 in and out)
   double dx = 0, dsig = 0, cx = 0, cz = 0;
   size_t N = 0, Nfree = 0;
   std::vector<int> orders;
@@ -616,6 +619,8 @@ pmg_status curved(pmg_handle* h, int mode, const void* x, const void* b, void* y
   const Shape& F = a.s;
   double N = (double)F.NX * F.NZ, E = (double)F.Nx * F.Nz, n = F.P + 1;
   Cost c{(mode == 1 ? 3.0 : 2.0) * N * sizeof(T), E * (8.0 * n * n * n + 12.0 * n * n)};
+  if (!PI<T> && h->df64_outer && mode != 3)
+    return launch(h, PMG_K_CURVED64, 1, st, c, [&] { return curved_op<df64>(a, st); });
   return launch(h, PI<T> ? PMG_K_CURVED32 : PMG_K_CURVED64, 1, st, c, [&] { return curved_op<T>(a, st); });
 }
 
@@ -1096,6 +1101,7 @@ void pmg_default_opts(pmg_opts* o) {
   o->inner_tol = 1e-5;
   o->nlevels = 0;
   o->fuse_residual = -1;
+  o->df64_outer = -1;
 }
 
 const char* pmg_last_error(void) { return g_err.c_str(); }
@@ -1122,7 +1128,8 @@ pmg_status pmg_create(const pmg_mesh_desc* mesh, const pmg_opts* opts, pmg_handl
   if (o.smoother != PMG_ASM_FDM || o.precond_geom != PMG_FLAT_LINEARISED)
     return fail(PMG_ERR_INVALID, "unsupported smoother or preconditioner geometry");
   if (o.overlap < 0 || o.overlap > MAXO || o.nu < 1 || !(o.omega > 0) || !(o.tol > 0) || o.max_iter < 1 ||
-      o.inner_max < 1 || !(o.inner_tol > 0) || o.fuse_residual < -1 || o.fuse_residual > 1)
+      o.inner_max < 1 || !(o.inner_tol > 0) || o.fuse_residual < -1 || o.fuse_residual > 1 || o.df64_outer < -1 ||
+      o.df64_outer > 1)
     return fail(PMG_ERR_INVALID, "bad solver options");
   std::vector<int> orders;
   if (o.nlevels > 0) {
@@ -1145,6 +1152,7 @@ pmg_status pmg_create(const pmg_mesh_desc* mesh, const pmg_opts* opts, pmg_handl
   h->mesh = m;
   h->opts = o;
   h->tc = o.precision == PMG_MIXED_BF16 ? 3 : 0;
+  h->df64_outer = o.df64_outer == 1 || (o.df64_outer < 0 && o.precision != PMG_FP64);
   h->orders = orders;
   h->dx = (m.x1 - m.x0) / m.cells_x;
   h->dsig = 1.0 / m.cells_z;

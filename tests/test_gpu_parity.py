@@ -53,8 +53,11 @@ def scale_of(A, x):
 
 
 @pytest.mark.parametrize("name", list(CASES))
-def test_apply_fp64_and_fp32(name):
-    c = case(name)
+@pytest.mark.parametrize("df64", [0, 1])
+def test_apply_fp64_and_fp32(name, df64):
+    """FP64 operator on the FP64 pipe (df64 0) or in double-float arithmetic with FP64
+    vectors (df64 1: 48-bit significands, the same 1e-12 bound of the summand scale)."""
+    c = case(name, df64_outer=df64)
     A = c.m.assemble(c.eta)
     rng = np.random.default_rng(1)
     x = rng.standard_normal(c.m.N)

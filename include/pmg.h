@@ -88,8 +88,9 @@ typedef struct {
   double inner_tol;  /* mixed precision: inner relative residual target                     */
   int nlevels;       /* 0 = the paper's coarsening rule; else level_orders[0..nlevels-1]    */
   int level_orders[8];
-  int fuse_residual; /* FP32 sweeps that form their own level residual: 1 on every level,   */
-                     /* 0 never, -1 (default) where pmg_autotune measured it to be faster    */
+  int fuse_residual; /* sweeps (FP32) and restrictions that form their own level residual:  */
+                     /* 1 on every level, 0 never, -1 (default) where pmg_autotune measured   */
+                     /* it to be faster                                                       */
   int df64_outer;    /* outer actual-geometry operator (FP64 vectors in and out) computed in */
                      /* double-float arithmetic on the FP32 pipe (48-bit significand): 1 on, */
                      /* 0 off (FP64 pipe), -1 (default) on for the mixed precisions only     */

@@ -371,9 +371,14 @@ template cudaError_t fdm_smooth<float>(const FdmArgs&, cudaStream_t);
 template <typename T>
 struct TransferParams {
   Shape f, c;       // fine and coarse shapes (same cells)
-  const T* in;
+  const T* in;      // prolong: x_c; restrict: r_f, or b_f when xf is set
   T* out;
   const double* J;  // [(Pf+1)][(Pc+1)]
+  // restriction of the residual formed in the kernel: r_f = in - A_f xf (flat level operator)
+  const T* xf;
+  T cx, cz;
+  const T* mX;      // [NXf] assembled LGL weights of the fine level
+  const T* mZ;      // [NZf]
 };
 
 // x_f += P x_c
@@ -425,14 +430,51 @@ __global__ void __launch_bounds__(512) k_restrict(TransferParams<T> p) {
   T* Rf = reinterpret_cast<T*>(smem_raw);  // [ncol][NZfp]
   T* Sz = Rf + ncol * NZfp;                 // [ncol][NZcp]
   T* Js = Sz + ncol * NZcp;                 // [nf][nc]
+  T* Xs = Js + nf * nc;                     // fused: [ncol][NZfp] fine iterate
+  T* MZ = Xs + ncol * NZfp;                 // fused: [NZf] cx * assembled z weights
+  T* MX = MZ + NZf;                         // fused: [ncol] cz * assembled x weights
+  const bool fused = p.xf != nullptr;
   for (int t = threadIdx.x; t < nf * nc; t += blockDim.x) Js[t] = (T)p.J[t];
   for_slab(ncol, NZf, [&](int q, int iz) {
     int gc = (ex - 1) * Pf + q;
     bool ok = (q >= Pf || left) && (q < 2 * Pf || last) && iz != NZf - 1;
     cp_async_elem(&Rf[q * NZfp + iz], p.in + (ok ? (size_t)wrap_col(f, gc) * NZf + iz : 0), ok);
+    if (fused) {
+      bool okx = (q >= Pf || left) && iz != NZf - 1;  // x of the left and own elements
+      cp_async_elem(&Xs[q * NZfp + iz], p.xf + (okx ? (size_t)wrap_col(f, gc) * NZf + iz : 0), okx);
+    }
   });
+  if (fused) {
+    for (int t = threadIdx.x; t < NZf; t += blockDim.x) MZ[t] = p.cx * p.mZ[t];
+    for (int q = threadIdx.x; q < ncol; q += blockDim.x) {
+      int gc = (ex - 1) * Pf + q;
+      MX[q] = (q >= Pf || left) ? p.cz * p.mX[wrap_col(f, gc)] : T(0);
+    }
+  }
   cp_async_wait_all();
   __syncthreads();
+  if (fused) {
+    // Rf = b - A_f x on the fine columns the restriction reads: (ex-1)Pf + 1 .. (ex+1)Pf - 1,
+    // and (ex+1)Pf on the wall CTA.  Element 0 of the slab is the left one (absent at a
+    // wall: its stencil is skipped, not only its data zeroed), element 1 the own one.
+    for_slab(ncol, NZf, [&](int q, int iz) {
+      if (iz == NZf - 1 || q == 0 || (q == 2 * Pf && !last) || (q < Pf && !left)) return;
+      int e = q / Pf, li = q - e * Pf;
+      if (e == 2) { e = 1; li = Pf; }
+      T kx = T(0);
+      for (int m = 0; m < nf; ++m) kx += CT<T>::K(cT, Pf, li, m) * Xs[(e * Pf + m) * NZfp + iz];
+      if (li == 0 && e == 1 && left)
+        for (int m = 0; m < nf; ++m) kx += CT<T>::K(cT, Pf, Pf, m) * Xs[m * NZfp + iz];
+      const int ez = min(iz / Pf, f.Nz - 1), lj = iz - ez * Pf;
+      const T* col = Xs + q * NZfp;
+      T kz = T(0);
+      for (int m = 0; m < nf; ++m) kz += CT<T>::K(cT, Pf, lj, m) * col[ez * Pf + m];
+      if (lj == 0 && ez > 0)
+        for (int m = 0; m < nf; ++m) kz += CT<T>::K(cT, Pf, Pf, m) * col[(ez - 1) * Pf + m];
+      Rf[q * NZfp + iz] -= MZ[iz] * kx + MX[q] * kz;
+    });
+    __syncthreads();
+  }
   for_slab(ncol, NZc, [&](int q, int lc) {
     T acc = T(0);
     if (lc != NZc - 1) {
@@ -477,11 +519,17 @@ cudaError_t transfer(const TransferArgs& a, int restrict_, cudaStream_t st) {
   p.in = (const T*)a.in;
   p.out = (T*)a.out;
   p.J = a.J;
+  p.xf = (const T*)a.xf;
+  p.cx = (T)a.cx;
+  p.cz = (T)a.cz;
+  p.mX = (const T*)a.mX;
+  p.mZ = (const T*)a.mZ;
   int nf = a.f.P + 1, nc = a.c.P + 1;
   int NZfp = slab_pitch(a.f.NZ), NZcp = slab_pitch(a.c.NZ);
   cudaError_t e;
   if (restrict_) {
     size_t sm = ((size_t)(2 * a.f.P + 1) * (NZfp + NZcp) + nf * nc) * sizeof(T) + 16;
+    if (a.xf) sm += ((size_t)(2 * a.f.P + 1) * (NZfp + 1) + a.f.NZ) * sizeof(T);
     static std::atomic<unsigned long long> s_mask{0};
     e = ensure_max_smem(k_restrict<T>, s_mask);
     if (e != cudaSuccess) return e;

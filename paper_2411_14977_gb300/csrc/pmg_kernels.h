@@ -123,6 +123,12 @@ struct TransferArgs {
   void* out;
   const double* J;
   int threads = 256;
+  // restriction only: with xf set, `in` is the fine right-hand side and the kernel
+  // restricts r = in - A_f xf (flat level operator cx, cz, assembled weights mX, mZ)
+  const void* xf = nullptr;
+  double cx = 0.0, cz = 0.0;
+  const void* mX = nullptr;
+  const void* mZ = nullptr;
 };
 template <typename T> cudaError_t transfer(const TransferArgs& a, int restrict_, cudaStream_t st);
 

@@ -228,6 +228,7 @@ struct LevelDev {
   double* J = nullptr;  // transfer from level l+1 (coarse) to this level
   int thr_flat32 = 256, thr_fdm32 = 256, thr_xfer = 256;  // CTA sizes (autotuner)
   bool fuse_res = false;  // FP32 sweeps form their own residual (autotuner, when faster)
+  bool fuse_restrict = false;  // the restriction forms the level residual (autotuner, when faster)
   void* b[2]{};
   void* x[2]{};
   void* t[2]{};
@@ -348,6 +349,7 @@ pmg_status build_level(pmg_handle* h, int l) {
   int p = h->orders[l];
   L.order = p;
   L.fuse_res = h->opts.fuse_residual == 1;
+  L.fuse_restrict = h->opts.fuse_residual == 1;
   L.s.P = p;
   L.s.Nx = m.cells_x;
   L.s.Nz = m.cells_z;
@@ -563,12 +565,25 @@ pmg_status level_smooth(pmg_handle* h, int l, const void* b, void* x, int post, 
   return PMG_OK;
 }
 
+// Transfer between levels l and l+1.  Restriction with xf: restricts b - A_l xf (the
+// level residual formed inside the restriction kernel; `in` = b).
 template <typename T>
-pmg_status transfer_op(pmg_handle* h, int l, const void* in, void* out, int restrict_, cudaStream_t st) {
-  TransferArgs a{h->lv[l].s, h->lv[l + 1].s, in, out, h->lv[l].J, h->lv[l].thr_xfer};
-  double Nf = (double)h->lv[l].s.NX * h->lv[l].s.NZ, Nc = (double)h->lv[l + 1].s.NX * h->lv[l + 1].s.NZ;
-  double pf = h->lv[l].s.P, pc = h->lv[l + 1].s.P;
+pmg_status transfer_op(pmg_handle* h, int l, const void* in, void* out, int restrict_, cudaStream_t st,
+                       const void* xf = nullptr) {
+  LevelDev& L = h->lv[l];
+  TransferArgs a{L.s, h->lv[l + 1].s, in, out, L.J, L.thr_xfer};
+  double Nf = (double)L.s.NX * L.s.NZ, Nc = (double)h->lv[l + 1].s.NX * h->lv[l + 1].s.NZ;
+  double pf = L.s.P, pc = h->lv[l + 1].s.P;
   Cost c{(restrict_ ? Nf + Nc : 2.0 * Nf + Nc) * sizeof(T), 2.0 * (Nf * (pc + 1) + Nc * (pf + 1))};
+  if (restrict_ && xf) {
+    a.xf = xf;
+    a.cx = h->cx;
+    a.cz = h->cz;
+    a.mX = L.mX[PI<T>];
+    a.mZ = L.mZ[PI<T>];
+    c.bytes += Nf * sizeof(T);
+    c.flops += Nf * (4.0 * (pf + 2) + 4.0);
+  }
   return launch(h, PMG_K_TRANSFER, 1, st, c, [&] { return transfer<T>(a, restrict_, st); });
 }
 
@@ -589,9 +604,13 @@ pmg_status vcycle(pmg_handle* h, int l, const void* b, void* x, cudaStream_t st)
   if (l == nl - 1) return launch(h, PMG_K_COARSE, 3, st, coarse_cost<T>(h), [&] { return coarse_solve<T>(h->coarse, b, x, st); });
   CK(cudaMemsetAsync(x, 0, NL * sizeof(T), st));
   CKS(level_smooth<T>(h, l, b, x, 0, true, st));
-  CKS(level_residual<T>(h, l, b, x, L.t[PI<T>], 1, st));
   LevelDev& C = h->lv[l + 1];
-  CKS(transfer_op<T>(h, l, L.t[PI<T>], C.b[PI<T>], 1, st));
+  if (L.fuse_restrict) {
+    CKS(transfer_op<T>(h, l, b, C.b[PI<T>], 1, st, x));  // restricts b - A_l x
+  } else {
+    CKS(level_residual<T>(h, l, b, x, L.t[PI<T>], 1, st));
+    CKS(transfer_op<T>(h, l, L.t[PI<T>], C.b[PI<T>], 1, st));
+  }
   CKS(vcycle<T>(h, l + 1, C.b[PI<T>], C.x[PI<T>], st));
   CKS(transfer_op<T>(h, l, C.x[PI<T>], x, 0, st));
   CKS(level_smooth<T>(h, l, b, x, 1, false, st));
@@ -1623,6 +1642,18 @@ pmg_status pmg_autotune(pmg_handle* h) {
       L.thr_xfer = thr;
       return transfer_op<float>(h, l, t, C.b[1], 1, cs);
     }, &L.thr_xfer));
+    {
+      // residual launch + restriction, or a restriction that forms the residual itself
+      float us_split = 0.f, us_fused = 0.f;
+      CKS(time_launches(h, [&](int thr, cudaStream_t cs) {
+        CKS(level_residual<float>(h, l, b, x, t, 1, cs));
+        return transfer_op<float>(h, l, t, C.b[1], 1, cs);
+      }, L.thr_xfer, 10, &us_split));
+      CKS(time_launches(h, [&](int thr, cudaStream_t cs) {
+        return transfer_op<float>(h, l, b, C.b[1], 1, cs, x);
+      }, L.thr_xfer, 10, &us_fused));
+      if (h->opts.fuse_residual < 0) L.fuse_restrict = us_fused < 0.97f * us_split;
+    }
   }
   CKS(tune_one(h, TK_CURVED32, h->mesh.order, h->lv[0].s.NZ, [&](int thr, cudaStream_t cs) {
     h->thr_curved32 = thr;

@@ -156,9 +156,12 @@ def test_smoother(name, fuse):
                 assert np.max(np.abs(n(x) - ref)) <= tol * sc, (l, post, dt)
 
 
+@pytest.mark.parametrize("fuse", [0, 1])
 @pytest.mark.parametrize("name", list(CASES))
-def test_coarse_solve_and_vcycle(name):
-    c = case(name)
+def test_coarse_solve_and_vcycle(name, fuse):
+    """Coarse solve, and the V-cycle in FP64 and FP32 with the level residuals launched
+    apart (fuse 0) or formed inside the sweeps and restrictions (fuse 1)."""
+    c = case(name, fuse_residual=fuse)
     H = c.hierarchy()
     rng = np.random.default_rng(4)
     C = H.levels[-1]

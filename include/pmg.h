@@ -178,6 +178,10 @@ pmg_status pmg_level_apply(pmg_handle* h, int level, const void* x_dev, void* y_
                            void* stream);
 /* nu Schwarz sweeps on level l for A_l x = b, updating x in place (Sec. 5.3);
  * post = 0: x += omega W sum R^T A_i^-1 R r, post = 1: the adjoint (W applied to r). */
+/* One additive-Schwarz sweep x += omega W sum_e R_e^T A_e^-1 R_e r (post = 0) or its adjoint
+ * (post = 1) on level `level` for a given residual r (Sec. 5.3): a single kernel launch,
+ * for timing and tests.  Vectors as in pmg_level_smooth. */
+pmg_status pmg_level_sweep(pmg_handle* h, int level, const void* r, void* x, int post, int f32, void* stream);
 pmg_status pmg_level_smooth(pmg_handle* h, int level, const void* b_dev, void* x_dev, int post,
                             int f32, void* stream);
 /* r_c = P^T r_f (level l -> l+1) and x_f += P x_c (level l+1 -> l) (Sec. 5.2). */

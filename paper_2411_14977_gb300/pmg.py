@@ -72,6 +72,7 @@ _SIGNATURES = {
     "pmg_apply_bf16": (_I, [_P, _P, _P, _I, _P]),
     "pmg_level_apply": (_I, [_P, _I, _P, _P, _I, _P]),
     "pmg_level_smooth": (_I, [_P, _I, _P, _P, _I, _I, _P]),
+    "pmg_level_sweep": (_I, [_P, _I, _P, _P, _I, _I, _P]),
     "pmg_restrict": (_I, [_P, _I, _P, _P, _I, _P]),
     "pmg_prolong": (_I, [_P, _I, _P, _P, _I, _P]),
     "pmg_coarse_solve": (_I, [_P, _P, _P, _P]),
@@ -340,6 +341,12 @@ class Solver:
         out = torch.empty_like(x) if out is None else out
         _check(load().pmg_level_apply(self._h, level, _ptr(x, x.dtype), _ptr(out, x.dtype), self._f32(x), _stream()))
         return out
+
+    def level_sweep(self, level, r, x, post=False):
+        """One Schwarz sweep x += B_l r (a single kernel launch)."""
+        dt = r.dtype
+        _check(load().pmg_level_sweep(self._h, level, _ptr(r, dt), _ptr(x, dt), int(post), self._f32(r), _stream()))
+        return x
 
     def level_smooth(self, level, b, x, post=False):
         _check(load().pmg_level_smooth(self._h, level, _ptr(b, b.dtype), _ptr(x, b.dtype), int(post),

@@ -54,8 +54,13 @@ class WaveTank:
         self.dt = dt
         self.predictor = predictor
         # "residual": use the network's guess only where its residual is smaller than that
-        # of the previous pressure; "always": use it unconditionally
+        # of the previous pressure; after `probe_after` rejections in a row the network is
+        # consulted only on every `probe_every`-th solve until it wins again (its checks
+        # cost two operator applications); "always": use it unconditionally
         self.guess_policy = guess_policy
+        self.probe_after, self.probe_every = 8, 16
+        self._rejected = 0
+        self._skipped = 0
         self.record = record
         self.samples = []                   # (eta, eta_prev, eta_x, p_prev, p) per solve when recording
         self.solve_infos = []
@@ -97,15 +102,21 @@ class WaveTank:
         x0 = self.p
         if self.predictor is not None:
             # keep the network's guess only where its residual beats the previous pressure
-            guess = self.predictor.predict(eta, self.eta_p, self.etax, self.p)
             if self.guess_policy == "always":
-                x0 = guess
-            else:
+                x0 = self.predictor.predict(eta, self.eta_p, self.etax, self.p)
+            elif self._rejected < self.probe_after or self._skipped + 1 >= self.probe_every:
+                self._skipped = 0
+                guess = self.predictor.predict(eta, self.eta_p, self.etax, self.p)
                 r_nn = S.residual_norm(B["b"], self.pD, guess)
                 r_prev = S.residual_norm(B["b"], self.pD, self.p)
                 self.guess_log.append((r_prev, r_nn))
                 if r_nn < r_prev:
                     x0 = guess
+                    self._rejected = 0
+                else:
+                    self._rejected += 1
+            else:
+                self._skipped += 1
         prev = (self.eta_p.clone(), self.p.clone()) if self.record else None
         _, info = S.solve(B["b"], self.pD, x0=x0, out=self.p)
         self.eta_p.copy_(eta)

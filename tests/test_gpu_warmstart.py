@@ -158,6 +158,6 @@ def test_warm_start_against_previous_pressure():
     print("loss", hist[0], hist[-1], "iterations", it_a, it_b,
           "median residual ratio", float(np.median([r_nn / r_prev for r_prev, r_nn in log])))
     assert hist[-1] < 0.01 * hist[0]
-    assert len(log) == 32
+    assert 0 < len(log) <= 32
     assert np.abs(eta_a - eta_b).max() <= 1e-6 * amp
     assert it_b <= it_a, (it_b, it_a)

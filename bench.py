@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg3", "cfg4", "cfg5"])
+    ap.add_argument("--kernel-scaling", action="store_true",
+                    help="time the hot kernels alone on config-2 tanks of growing length and report "
+                         "their HBM roofline fractions")
     ap.add_argument("--variants", action="store_true",
                     help="cfg2/cfg3: every precision variant (iterations, time, error vs FP64) and the "
                          "operator kernels (FP64, FP32, BF16 tensor cores) side by side")
@@ -165,6 +168,31 @@ def measured_peaks():
 
 
 # ------------------------------------------------------------------------------------
+def graph_launch_us(torch, fn, reps=50):
+    """Device time per launch of fn: `reps` launches captured in one CUDA graph and
+    replayed (CUDA events around the replays), so host-side call overhead is excluded."""
+    for _ in range(5):
+        fn()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(st):
+        with torch.cuda.graph(g, stream=st):
+            for _ in range(reps):
+                fn()
+    torch.cuda.synchronize()
+    g.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(4):
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    return 1e3 * e0.elapsed_time(e1) / (4 * reps)
+
+
 def run_ours(args, ws, rank, local):
     import torch
     import paper_2411_14977_gb300.pmg as pmg
@@ -271,19 +299,11 @@ def run_ours(args, ws, rank, local):
     hbm = peaks.get("hbm_gbs", 6800.0)
 
     def per_launch_us(fn, reps=50):
-        for _ in range(5):
-            fn()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(reps):
-            fn()
-        e1.record()
-        torch.cuda.synchronize()
-        return 1e3 * e0.elapsed_time(e1) / reps
+        return graph_launch_us(torch, fn, reps)
 
     # ---- dominant kernel: the finest-level FP32 Schwarz sweep (one launch per call),
-    # timed alone on the launching (current) stream; its vectors (7 MB) stay in L2
+    # timed alone: 50 launches captured in a CUDA graph (no host overhead); its vectors
+    # (7 MB) stay in L2
     N0 = S.n
     r32 = torch.randn(N0, dtype=torch.float32, device=dev)
     x32 = torch.zeros(N0, dtype=torch.float32, device=dev)
@@ -443,6 +463,65 @@ def run_batch(args, ws, rank, local):
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
+
+
+def run_kernel_scaling(args, ws, rank, local):
+    """The hot kernels alone (CUDA events around a CUDA graph of 50 launches) on the
+    config-2 tank family (32 cells deep, P = 6) with 512 ... 16384 element columns: from an
+    L2-resident working set (config 2: 2.4 MB per FP32 vector) to vectors 15x the 129 MB
+    L2.  Achieved = algorithmic bytes / time against the measured HBM copy rate."""
+    import torch
+    import paper_2411_14977_gb300.pmg as pmg
+    import workloads as W
+
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pmg.load(build_if_missing=True)
+    hbm = measured_peaks().get("hbm_gbs", 6800.0)
+
+    def per_launch_us(fn, reps=50):
+        return graph_launch_us(torch, fn, reps)
+
+    rows = []
+    clk = ClockSampler(local)
+    for cx in (512, 2048, 8192, 16384):
+        w = W.tank(cx, 32, 6)
+        S = pmg.Solver(**w.mesh_kwargs(), precision=pmg.PMG_MIXED_FP32)
+        xc, sr = S.node_coords()
+        F = w.fields(xc, sr)
+        S.set_geometry(torch.as_tensor(np.ascontiguousarray(F["eta"]), dtype=torch.float64, device=dev))
+        S.autotune()
+        N = S.n
+        f32 = lambda: torch.randn(N, dtype=torch.float32, device=dev)
+        f64 = lambda: torch.randn(N, dtype=torch.float64, device=dev)
+        r32, x32, y32, b32 = f32(), f32(), f32(), f32()
+        x64, y64 = f64(), f64()
+        P1 = 7
+        E = cx * 32
+        kern = {
+            "k_fdm32 sweep (FP32)": (lambda: S.level_sweep(0, r32, x32), 3 * N * 4),
+            "k_flat level residual (FP32)": (lambda: S.level_apply(0, x32, y32), 2 * N * 4),
+            "k_curved operator (FP32)": (lambda: S.apply_f32(x32, y32), 2 * N * 4),
+            "k_curved operator (double-float, FP64 vectors)": (lambda: S.apply(x64, y64), 2 * N * 8),
+        }
+        row = {"cells_x": cx, "nodes": N, "fp32_vector_MB": N * 4 / 1e6}
+        for name, (fn, by) in kern.items():
+            us = per_launch_us(fn)
+            row[name] = {"us": us, "GB/s": by / (us * 1e-6) / 1e9, "frac_hbm": by / (us * 1e-6) / 1e9 / hbm}
+        us = per_launch_us(lambda: S.apply(x64, y64))
+        row["k_curved operator (double-float, FP64 vectors)"]["fp64_equiv_TFLOPs"] = \
+            E * (8.0 * P1 ** 3 + 12.0 * P1 ** 2) / (us * 1e-6) / 1e12
+        rows.append(row)
+        log(cx, {k: (round(v["frac_hbm"], 3) if isinstance(v, dict) else v) for k, v in row.items()})
+        S.close()
+        del r32, x32, y32, b32, x64, y64
+        torch.cuda.empty_cache()
+    clocks = clk.stop()
+    print(json.dumps({"kernel_scaling": rows, "peak_hbm_gbs": hbm,
+                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured), burst", "clocks": clocks}),
+          flush=True)
 
 
 def run_variants(args, ws, rank, local):
@@ -678,6 +757,8 @@ def main():
         run_tank(args, ws, rank, local)
     elif args.variants:
         run_variants(args, ws, rank, local)
+    elif args.kernel_scaling:
+        run_kernel_scaling(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
 

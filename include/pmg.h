@@ -91,6 +91,8 @@ typedef struct {
   int fuse_residual; /* sweeps (FP32) and restrictions that form their own level residual:  */
                      /* 1 on every level, 0 never, -1 (default) where pmg_autotune measured   */
                      /* it to be faster                                                       */
+  int flat_kernel;   /* FP32 level operator: 0 slab CTAs (one element column each), 1 one   */
+                     /* thread per node, -1 (default) slab until pmg_autotune picks by time   */
   int df64_outer;    /* outer actual-geometry operator (FP64 vectors in and out) computed in */
                      /* double-float arithmetic on the FP32 pipe (48-bit significand): 1 on, */
                      /* 0 off (FP64 pipe), -1 (default) on for the mixed precisions only     */

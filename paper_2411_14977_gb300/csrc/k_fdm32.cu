@@ -255,22 +255,47 @@ __device__ __forceinline__ void fdm32_body(const Fdm32Params& p, unsigned char* 
     int a = 2 * O + 1 + c;
     upd(a, iz, U[a * NZp + iz]);
   });
-#pragma unroll 1
-  for (int side = 0; side < 2; ++side) {
-    const int a0 = side == 0 ? 0 : P;
-    const int e = side == 0 ? ex : (s.periodic ? (ex + 1) % s.Nx : ex + 1);
-    const bool shared = s.periodic || (e != 0 && e != s.Nx);
-    const int gbase = e * P - O;
-    if (!shared) {
-      for_slab(ZW, NZ, [&](int c, int iz) {
-        if (col_valid(s, gbase + c)) upd(a0 + c, iz, U[(a0 + c) * NZp + iz]);
-      });
-    } else {
-      unsigned long long* slots = xb + (size_t)e * ZW * NZ;
-      for_slab(ZW, NZ, [&](int c, int iz) {
-        float tot;
-        if (swap_exchange(slots + c * NZ + iz, U[(a0 + c) * NZp + iz], tot)) upd(a0 + c, iz, tot);
-      });
+  // Edge zones of both sides, 2 ZW NZ nodes.  A thread swaps up to K partials into their
+  // slots back to back -- independent atomics in flight together instead of one L2 round
+  // trip per node -- and then finalises those whose partner had already arrived.
+  {
+    const int e_left = ex, e_right = s.periodic ? (ex + 1) % s.Nx : ex + 1;
+    const bool sh_left = s.periodic || ex != 0, sh_right = s.periodic || ex + 1 != s.Nx;
+    const int zone = ZW * NZ, total = 2 * zone;
+    constexpr int K = 4;
+    for (int base = threadIdx.x; base < total; base += K * blockDim.x) {
+      unsigned long long old[K];
+      unsigned long long* slot[K];
+      float u[K];
+      int aa[K], zz[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        old[k] = kEmpty64;
+        slot[k] = nullptr;
+        const int idx = base + k * blockDim.x;
+        if (idx >= total) continue;
+        const int side = idx >= zone ? 1 : 0;
+        const int rem = idx - side * zone;
+        const int c = rem / NZ, iz = rem - c * NZ;
+        aa[k] = (side ? P : 0) + c;
+        zz[k] = iz;
+        u[k] = U[aa[k] * NZp + iz];
+        const int e = side ? e_right : e_left;
+        if (side ? sh_right : sh_left) {
+          slot[k] = xb + ((size_t)e * ZW + c) * NZ + iz;
+          old[k] = atomicExch(slot[k], (unsigned long long)__float_as_uint(u[k]));
+        } else if (col_valid(s, e * P - O + c)) {
+          upd(aa[k], iz, u[k]);  // wall: this CTA is the only contributor
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        if (slot[k] && old[k] != kEmpty64) {  // second to arrive: the sum is complete
+          float tot = u[k] + __uint_as_float((unsigned)old[k]);
+          atomicExch(slot[k], kEmpty64);
+          upd(aa[k], zz[k], tot);
+        }
+      }
     }
   }
 }

@@ -112,8 +112,55 @@ __global__ void __launch_bounds__(512) k_flat(FlatParams<T> p) {
   });
 }
 
+// The same level operator node-parallel: one thread per node reads its x- and z-stencil
+// neighbours straight from global memory (L1/L2 serve the reuse), no shared memory and no
+// barriers, so a CTA's critical path is one load wave and ~2(P+1) FMAs.
+template <int P, typename T>
+__global__ void __launch_bounds__(256) k_flat_np(FlatParams<T> p) {
+  constexpr int n = P + 1;
+  const Shape s = p.s;
+  const int NZ = s.NZ, Nz = s.Nz;
+  const size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (g >= (size_t)s.NX * NZ) return;
+  const int ix = (int)(g / NZ), iz = (int)(g - (size_t)ix * NZ);
+  if (iz == NZ - 1) {
+    p.y[g] = p.residual ? T(0) : p.x[g];
+    return;
+  }
+  // x stencil: the element(s) of column ix (the wall side has one)
+  const int ex = min(ix / P, s.Nx - 1), i = ix - ex * P;
+  T ax = T(0);
+#pragma unroll
+  for (int m = 0; m < n; ++m) ax += CT<T>::K(cT, P, i, m) * p.x[(size_t)wrap_col(s, ex * P + m) * NZ + iz];
+  if (i == 0 && (s.periodic || ex > 0)) {
+#pragma unroll
+    for (int m = 0; m < n; ++m) ax += CT<T>::K(cT, P, P, m) * p.x[(size_t)wrap_col(s, (ex - 1) * P + m) * NZ + iz];
+  }
+  // z stencil along the column (the surface row of x is read as zero)
+  const T* col = p.x + (size_t)ix * NZ;
+  const int ez = min(iz / P, Nz - 1), j = iz - ez * P;
+  T az = T(0);
+#pragma unroll
+  for (int m = 0; m < n; ++m) {
+    int r = ez * P + m;
+    az += CT<T>::K(cT, P, j, m) * (r == NZ - 1 ? T(0) : col[r]);
+  }
+  if (j == 0 && ez > 0) {
+#pragma unroll
+    for (int m = 0; m < n; ++m) az += CT<T>::K(cT, P, P, m) * col[(ez - 1) * P + m];
+  }
+  T v = p.cx * p.mZ[iz] * ax + p.cz * p.mX[ix] * az;
+  p.y[g] = p.residual ? p.b[g] - v : v;
+}
+
 template <int P, typename T>
 static cudaError_t launch_flat_p(const FlatParams<T>& prm, int threads, cudaStream_t st) {
+  if (threads < 0) {  // node-parallel variant, -threads per CTA
+    size_t N = (size_t)prm.s.NX * prm.s.NZ;
+    int bs = -threads;
+    k_flat_np<P, T><<<(unsigned)((N + bs - 1) / bs), bs, 0, st>>>(prm);
+    return cudaGetLastError();
+  }
   int NZp = slab_pitch(prm.s.NZ);
   size_t sm = ((size_t)((2 * P + 1) + 2 * (P + 1)) * NZp + prm.s.NZ + P + 1) * sizeof(T);
   auto k = k_flat<P, T>;
@@ -136,7 +183,7 @@ cudaError_t flat_op(const FlatArgs& a, cudaStream_t st) {
   p.mX = (const T*)a.mX;
   p.mZ = (const T*)a.mZ;
   p.residual = a.residual;
-  int thr = (a.threads >= 32 && a.threads <= 512) ? a.threads : 256;
+  int thr = (a.threads >= 32 && a.threads <= 512) ? a.threads : (a.threads <= -32 && a.threads >= -256) ? a.threads : 256;
   switch (a.s.P) {
 #define PMG_CASE(PP) case PP: return launch_flat_p<PP, T>(p, thr, st);
     PMG_CASE(1) PMG_CASE(2) PMG_CASE(3) PMG_CASE(4) PMG_CASE(5)

@@ -86,7 +86,7 @@ struct FlatArgs {
   const void* mX;
   const void* mZ;
   int residual;
-  int threads = 256;
+  int threads = 256;   // > 0: slab CTA size; < 0: node-parallel kernel with -threads per CTA
 };
 template <typename T> cudaError_t flat_op(const FlatArgs& a, cudaStream_t st);
 

@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <initializer_list>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -349,6 +350,7 @@ pmg_status build_level(pmg_handle* h, int l) {
   int p = h->orders[l];
   L.order = p;
   L.fuse_res = h->opts.fuse_residual == 1;
+  if (h->opts.flat_kernel == 1) L.thr_flat32 = -128;
   L.fuse_restrict = h->opts.fuse_residual == 1;
   L.s.P = p;
   L.s.Nx = m.cells_x;
@@ -1059,7 +1061,8 @@ pmg_status time_launches(pmg_handle* h, Run&& run, int threads, int reps, float*
 }
 
 template <class Run>
-pmg_status tune_one(pmg_handle* h, int kernel, int P, int NZ, Run&& run, int* out) {
+pmg_status tune_one(pmg_handle* h, int kernel, int P, int NZ, Run&& run, int* out,
+                    std::initializer_list<int> cands = {64, 128, 192, 256, 320, 384, 512}) {
   auto key = std::make_tuple(kernel, P, NZ, h->mesh.cells_x);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -1069,7 +1072,7 @@ pmg_status tune_one(pmg_handle* h, int kernel, int P, int NZ, Run&& run, int* ou
   }
   int best = 256;
   float best_us = 1e30f;
-  for (int thr : {64, 128, 192, 256, 320, 384, 512}) {
+  for (int thr : cands) {
     float us;
     CKS(time_launches(h, run, thr, 10, &us));
     if (us < best_us * 0.97f) { best_us = us; best = thr; }
@@ -1120,6 +1123,7 @@ void pmg_default_opts(pmg_opts* o) {
   o->inner_tol = 1e-5;
   o->nlevels = 0;
   o->fuse_residual = -1;
+  o->flat_kernel = -1;
   o->df64_outer = -1;
 }
 
@@ -1148,7 +1152,7 @@ pmg_status pmg_create(const pmg_mesh_desc* mesh, const pmg_opts* opts, pmg_handl
     return fail(PMG_ERR_INVALID, "unsupported smoother or preconditioner geometry");
   if (o.overlap < 0 || o.overlap > MAXO || o.nu < 1 || !(o.omega > 0) || !(o.tol > 0) || o.max_iter < 1 ||
       o.inner_max < 1 || !(o.inner_tol > 0) || o.fuse_residual < -1 || o.fuse_residual > 1 || o.df64_outer < -1 ||
-      o.df64_outer > 1)
+      o.df64_outer > 1 || o.flat_kernel < -1 || o.flat_kernel > 1)
     return fail(PMG_ERR_INVALID, "bad solver options");
   std::vector<int> orders;
   if (o.nlevels > 0) {
@@ -1624,10 +1628,13 @@ pmg_status pmg_autotune(pmg_handle* h) {
     void* x = L.x[1];
     void* b = L.b[1];
     void* t = L.t[1];
+    // slab CTAs (positive sizes) or node-parallel CTAs (negative sizes)
     CKS(tune_one(h, TK_FLAT32, L.order, L.s.NZ, [&](int thr, cudaStream_t cs) {
       L.thr_flat32 = thr;
       return level_residual<float>(h, l, b, x, t, 1, cs);
-    }, &L.thr_flat32));
+    }, &L.thr_flat32, h->opts.flat_kernel == 1 ? std::initializer_list<int>{-64, -128, -256}
+                       : h->opts.flat_kernel == 0 ? std::initializer_list<int>{64, 128, 192, 256, 320, 384, 512}
+                       : std::initializer_list<int>{64, 128, 192, 256, 320, 384, 512, -64, -128, -256}));
     if (l == nl - 1) continue;
     CKS(tune_one(h, TK_FDM32, L.order * 16 + L.overlap, L.s.NZ, [&](int thr, cudaStream_t cs) {
       L.thr_fdm32 = thr;

@@ -41,7 +41,8 @@ class Opts(ctypes.Structure):
                 ("precond_geom", ctypes.c_int), ("overlap", ctypes.c_int), ("nu", ctypes.c_int),
                 ("omega", ctypes.c_double), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("inner_max", ctypes.c_int), ("inner_tol", ctypes.c_double), ("nlevels", ctypes.c_int),
-                ("level_orders", ctypes.c_int * 8), ("fuse_residual", ctypes.c_int), ("df64_outer", ctypes.c_int)]
+                ("level_orders", ctypes.c_int * 8), ("fuse_residual", ctypes.c_int), ("flat_kernel", ctypes.c_int),
+                ("df64_outer", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):

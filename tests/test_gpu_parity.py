@@ -97,9 +97,12 @@ def test_rhs_assembly(name):
     assert np.max(np.abs(b - ref)) <= 1e-12 * max(1.0, np.max(np.abs(ref)))
 
 
+@pytest.mark.parametrize("flat", [0, 1])
 @pytest.mark.parametrize("name", list(CASES))
-def test_level_operators_and_transfers(name):
-    c = case(name)
+def test_level_operators_and_transfers(name, flat):
+    """Level operators (FP32: slab CTAs, flat 0, or one thread per node, flat 1) and the
+    transfers between consecutive levels."""
+    c = case(name, flat_kernel=flat)
     H = c.hierarchy()
     rng = np.random.default_rng(2)
     for l, lev in enumerate(H.levels):
@@ -192,7 +195,8 @@ SOLVE_CASES = ["tank12x3p6", "cfg1", "periodic8x3p5", "tank6x2p8", "tank5x1p4_nz
                                      dict(precision=pmg.PMG_MIXED_FP32, outer=pmg.PMG_IR),
                                      dict(precision=pmg.PMG_MIXED_FP32, outer=pmg.PMG_PDC),
                                      dict(precision=pmg.PMG_MIXED_FP32, fuse_residual=1),
-                                     dict(precision=pmg.PMG_MIXED_BF16, outer=pmg.PMG_IR)])
+                                     dict(precision=pmg.PMG_MIXED_BF16, outer=pmg.PMG_IR),
+                                     dict(precision=pmg.PMG_MIXED_FP32, flat_kernel=1)])
 def test_solve_matches_direct(name, variant):
     w = CASES[name]()
     c = Case(w, tol=1e-12, **variant)

@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg3", "cfg4", "cfg5"])
+    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg3", "cfg4", "cfg5", "paper"])
     ap.add_argument("--kernel-scaling", action="store_true",
                     help="time the hot kernels alone on config-2 tanks of growing length and report "
                          "their HBM roofline fractions")
@@ -465,6 +465,104 @@ def run_batch(args, ws, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_paper(args, ws, rank, local):
+    """The paper's own solver experiments in shape (Sec. 6.3): the Table 1 case (P = 8,
+    N_x = 102, N_z = 2, 17 waves of kh = 1, H/L = 0.0301) at tolerances 1e-4 ... 1e-10
+    with FP64 PCG, FP64 PDC and the mixed-precision solve, the oracle on the host cores
+    beside it; then the scaling sweeps at tol 1e-6 (N_x = 25 ... 800 at P = 8; P = 2 ... 10
+    at N_x = 200; ~48 points per wavelength).  Device time per solve: CUDA events, median
+    of `steps` solves from a zero initial guess."""
+    import torch
+    import paper_2411_14977_gb300.pmg as pmg
+    import workloads as W
+
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pmg.load(build_if_missing=True)
+    methods = [("fp64_pcg", dict(precision=pmg.PMG_FP64, outer=pmg.PMG_PCG)),
+               ("fp64_pdc", dict(precision=pmg.PMG_FP64, outer=pmg.PMG_PDC)),
+               ("mixed", dict(precision=pmg.PMG_MIXED_FP32))]
+
+    def prepare(w, **opts):
+        S = pmg.Solver(**w.mesh_kwargs(), **opts)
+        xc, sr = S.node_coords()
+        F = w.fields(xc, sr)
+        d = {k: torch.as_tensor(np.ascontiguousarray(F[k]), dtype=torch.float64, device=dev)
+             for k in ("eta", "u", "w", "pD")}
+        S.set_geometry(d["eta"])
+        b = S.assemble_rhs_div(d["u"], d["w"])
+        return S, b, d["pD"]
+
+    def time_solve(S, b, pD):
+        p = torch.empty_like(b)
+        info = None
+        for _ in range(2):
+            _, info = S.solve(b, pD, out=p, raise_on_error=False)
+        ts = []
+        for _ in range(max(args.steps, 3)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            _, info = S.solve(b, pD, out=p, raise_on_error=False)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts)), info
+
+    clk = ClockSampler(local)
+    w = W.paper_shape()
+    table = {}
+    for name, opts in methods:
+        for tol in (1e-4, 1e-6, 1e-8, 1e-10):
+            S, b, pD = prepare(w, tol=tol, **opts)
+            ms, info = time_solve(S, b, pD)
+            table[f"{name}@{tol:g}"] = {"iterations": info["iterations"], "ms": ms, "status": info["status"],
+                                        "rel_residual": info["rel_residual"],
+                                        "nodes_per_s": S.n / (ms / 1e3)}
+            log(name, tol, table[f"{name}@{tol:g}"])
+            S.close()
+    # the oracle (FP64 p-MG-PCG, same levels and smoother) on the host cores, 1e-6 and 1e-10
+    from oracle import mg as omg
+    from oracle.sem import Mesh
+    m = Mesh(**w.mesh_kwargs())
+    F = w.fields(m.column_x(), m.row_sigma())
+    bo = m.rhs_divergence(F["eta"], F["u"], F["w"])
+    oracle = {}
+    for tol in (1e-6, 1e-10):
+        t0, c0 = time.perf_counter(), time.process_time()
+        _, its, _, _ = omg.solve(m, F["eta"], bo, F["pD"], tol=tol, overlap=1, nu=2, omega=0.8)
+        wall, cpu = time.perf_counter() - t0, time.process_time() - c0
+        oracle[f"{tol:g}"] = {"iterations": its, "s_incl_setup": wall, "cores": round(cpu / wall, 1)}
+    # scaling sweeps at tol 1e-6
+    sweep = {"cells_x": [], "order": []}
+    for cx in (25, 50, 102, 200, 400, 800):
+        row = {"cells_x": cx, "order": 8}
+        for name, opts in (methods[0], methods[2]):
+            S, b, pD = prepare(W.paper_scaling(cx, 8), tol=1e-6, **opts)
+            ms, info = time_solve(S, b, pD)
+            row[name] = {"iterations": info["iterations"], "ms": ms, "nodes": S.n}
+            S.close()
+        sweep["cells_x"].append(row)
+        log("cells_x", row)
+    for order in (2, 3, 4, 5, 6, 7, 8, 9, 10):
+        row = {"cells_x": 200, "order": order}
+        for name, opts in (methods[0], methods[2]):
+            S, b, pD = prepare(W.paper_scaling(200, order), tol=1e-6, **opts)
+            ms, info = time_solve(S, b, pD)
+            row[name] = {"iterations": info["iterations"], "ms": ms, "nodes": S.n}
+            S.close()
+        sweep["order"].append(row)
+        log("order", row)
+    clocks = clk.stop()
+    print(json.dumps({"workload": w.name, "nodes": int(m.N), "table1_shape": table, "oracle_host": oracle,
+                      "scaling_tol1e-6": sweep, "clocks": clocks,
+                      "paper_table1_context": {"pdc_mg_iterations": [3, 5, 8], "gmres_mg_iterations": [1, 3, 4],
+                                               "tolerances": [1e-4, 1e-6, 1e-8],
+                                               "note": "mixed-stage nonsymmetric operator, MATLAB, unstated CPU"}}),
+          flush=True)
+
+
 def run_kernel_scaling(args, ws, rank, local):
     """The hot kernels alone (CUDA events around a CUDA graph of 50 launches) on the
     config-2 tank family (32 cells deep, P = 6) with 512 ... 16384 element columns: from an
@@ -755,6 +853,8 @@ def main():
         run_batch(args, ws, rank, local)
     elif args.workload == "cfg5":
         run_tank(args, ws, rank, local)
+    elif args.workload == "paper":
+        run_paper(args, ws, rank, local)
     elif args.variants:
         run_variants(args, ws, rank, local)
     elif args.kernel_scaling:

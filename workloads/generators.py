@@ -246,6 +246,16 @@ def paper_shape():
                     velocity=Velocity.random(BASE_SEED + 9))
 
 
+def paper_scaling(cells_x, order, ppw=48.0):
+    """Sec. 6.3 scaling family: N_z = 2, P_z = order, waves of kh = 1 and H/L = 0.0301 at
+    about `ppw` points per wavelength (the domain grows with the node count)."""
+    k = 1.0
+    L = cells_x * order * 2 * np.pi / ppw
+    s = Surface(0.5 * 0.0301 * 2 * np.pi, k)
+    return Workload(f'paper_scaling_p{order}_{cells_x}x2', cells_x, 2, order, 0.0, L, 1.0, False,
+                    BASE_SEED + 6, s, 'div', velocity=Velocity.random(BASE_SEED + 9))
+
+
 def by_name(name):
     return {'cfg1': config1, 'cfg2': config2, 'cfg3': config3, 'cfg5': config5,
             'paper': paper_shape}[name]()

@@ -60,6 +60,8 @@ def parse():
                          "operator kernels (FP64, FP32, BF16 tensor cores) side by side")
     ap.add_argument("--tank-steps", type=int, default=1000, help="cfg5: RK4 steps per run")
     ap.add_argument("--train-steps", type=int, default=200, help="cfg5: steps whose solves train the warm start")
+    ap.add_argument("--scheme", default="rk4", choices=["rk4", "lserk54"],
+                    help="cfg5 time integrator: classical RK4 (4 solves/step) or LSERK(5,4) (5 solves/step)")
     ap.add_argument("--filter", default="strong", choices=["strong", "few-percent", "none"],
                     help="cfg5 spectral filter after every step: strong = (P_c 0, alpha -36, beta 8), "
                          "few-percent = (P_c P-2, S(P) 0.97, beta 8)")
@@ -747,7 +749,7 @@ def run_tank(args, ws, rank, local):
 
     def run(name, **kw):
         learned = kw.pop("learned", False)
-        tank = WaveTank(w, record=learned, filter=flt, **kw)
+        tank = WaveTank(w, record=learned, filter=flt, scheme=args.scheme, **kw)
         om = tank.set_linear_wave(amp, k)
         tank.dt = 2 * np.pi / om / 100
         out = {"train_s": 0.0}
@@ -806,7 +808,8 @@ def run_tank(args, ws, rank, local):
         "warmup": n_train, "ms_per_step": 1e3 * best["wall_s"] / max(1, n_steps - n_train),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": "cfg5: periodic tank [0,20]x[-1,eta], 256x16 cells, P=6, eta0=0.05cos(pi x), "
-                               "RK4 dt=T/100", "tank_steps": n_steps, "train_steps": n_train,
+                               f"{'RK4' if args.scheme == 'rk4' else 'LSERK(5,4)'} dt=T/100",
+                   "tank_steps": n_steps, "train_steps": n_train,
                    "filter": None if flt is None else {"cutoff": flt[0], "alpha": flt[1], "beta": flt[2]},
                    "free_dof": 1536 * 96},
         "runs": res,

@@ -12,10 +12,14 @@ Spectral filter (Sec. "Spectral Filtering"): per element, F = V diag(S) V^{-1} w
 exponential cut-off S(i) = 1 for i <= P_c, exp(alpha ((i - P_c)/(P + 1 - P_c))^beta) above,
 applied as F (x) F to u, w and as F to eta, followed by the mean at shared nodes.
 
+Time stepping: classical RK4, or the paper's five-stage fourth-order low-storage scheme
+(LSERK(5,4), Carpenter & Kennedy 1994).
+
 Pins (tests/test_oracle_stepper.py): exact gradients of physical linear functions on a
 curved mesh; a small-amplitude wave keeps the linear dispersion relation over a period;
 the filter keeps polynomials of degree <= P_c, scales mode P by S(P), and is the
-identity for alpha = 0.
+identity for alpha = 0; LSERK(5,4) has order four on y' = lambda y (stability polynomial
+matches exp to z^4) and keeps the dispersion relation like RK4.
 """
 import math
 
@@ -26,6 +30,30 @@ from .sem import Mesh, solve_direct
 
 G = 9.81
 RHO = 999.70
+
+
+# Five-stage fourth-order 2N-storage Runge-Kutta (Carpenter & Kennedy 1994), the scheme of
+# the paper's time stepping (Sec. 3): K <- a_k K + dt f(y), y <- y + b_k K.
+LSERK54_A = (0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+             -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0)
+LSERK54_B = (1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+             1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+             2277821191437.0 / 14882151754819.0)
+
+
+def lserk54(f, y, dt):
+    """One LSERK(5,4) step of y' = f(y) for a list of arrays y; returns (y_new, stage extras):
+    f returns (rates..., extra) with one rate per component of y."""
+    K = [np.zeros_like(v) for v in y]
+    y = [np.array(v, dtype=np.float64, copy=True) for v in y]
+    extras = []
+    for a, b in zip(LSERK54_A, LSERK54_B):
+        out = f(y)
+        rates, extra = out[:len(y)], out[len(y):]
+        K = [a * Kv + dt * r for Kv, r in zip(K, rates)]
+        y = [v + b * Kv for v, Kv in zip(y, K)]
+        extras.append(extra)
+    return y, extras
 
 
 def filter_response(P, cutoff, alpha, beta):
@@ -128,6 +156,11 @@ class Tank:
         k4 = self.rates(eta + dt * k3[0], u + dt * k3[1], w + dt * k3[2])
         comb = lambda i: (k1[i] + 2 * k2[i] + 2 * k3[i] + k4[i]) * (dt / 6.0)
         return eta + comb(0), u + comb(1), w + comb(2), [k1[3], k2[3], k3[3], k4[3]]
+
+    def step_lserk(self, eta, u, w, dt):
+        """LSERK(5,4) step (five pressure solves); returns the new state and the stage pressures."""
+        (eta, u, w), extras = lserk54(lambda y: self.rates(*y), [eta, u, w], dt)
+        return eta, u, w, [e[0] for e in extras]
 
     def linear_wave(self, amp, k):
         """Linear-theory progressive wave eta = a cos(kx): (eta, u, w, omega)."""

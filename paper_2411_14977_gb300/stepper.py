@@ -25,6 +25,15 @@ G = 9.81
 RHO = 999.70
 
 
+# Five-stage fourth-order 2N-storage Runge-Kutta of Carpenter & Kennedy (1994), the
+# paper's time integrator (Sec. 3): K <- a_k K + dt f(y), y <- y + b_k K.
+LSERK_A = (0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+           -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0)
+LSERK_B = (1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+           1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+           2277821191437.0 / 14882151754819.0)
+
+
 def default_filter(P, strength=0.97, beta=8.0):
     """(cutoff, alpha, beta): modes above P - 2 damped, the highest by the factor `strength`."""
     cutoff = max(P - 2, 0)
@@ -33,7 +42,10 @@ def default_filter(P, strength=0.97, beta=8.0):
 
 class WaveTank:
     def __init__(self, workload, dt=None, device="cuda", predictor=None, record=False, guess_policy="residual",
-                 filter=None, filter_stages=False, **solver_opts):
+                 filter=None, filter_stages=False, scheme="rk4", **solver_opts):
+        if scheme not in ("rk4", "lserk54"):
+            raise ValueError("scheme: rk4 or lserk54")
+        self.scheme = scheme
         self.w = workload
         self.S = pmg.Solver(**workload.mesh_kwargs(), **solver_opts)
         S = self.S
@@ -127,7 +139,9 @@ class WaveTank:
         S.stage_rates(u, w, B["uz"], B["wz"], B["Fu"], B["Fw"], B["px"], B["pz"], self.etax, RHO, du, dw, deta)
 
     def step(self):
-        """One classical RK4 step (four pressure solves)."""
+        """One time step: classical RK4 (four pressure solves) or LSERK(5,4) (five)."""
+        if self.scheme == "lserk54":
+            return self._step_lserk()
         S, dt = self.S, self.dt
         y = (self.eta, self.u, self.wv)
         cs = (0.5, 0.5, 1.0)
@@ -147,6 +161,24 @@ class WaveTank:
                 cur = self.ys
         for yy, a in zip(y, self.acc):
             S.axpy(1.0, a, yy, yy)
+        if self.filter is not None:
+            self._filter(y)
+        self.t += dt
+
+    def _step_lserk(self):
+        S, dt = self.S, self.dt
+        y = (self.eta, self.u, self.wv)
+        K, kk = self.acc, self.k[0]
+        for a, b in zip(LSERK_A, LSERK_B):
+            self.rates(*y, kk)
+            for Kv, r in zip(K, kk):
+                if a == 0.0:
+                    Kv.zero_()
+                else:
+                    S.axpy(a - 1.0, Kv, Kv, Kv)  # K <- a K
+                S.axpy(dt, r, Kv, Kv)            # K <- K + dt f
+            for yy, Kv in zip(y, K):
+                S.axpy(b, Kv, yy, yy)            # y <- y + b K
         if self.filter is not None:
             self._filter(y)
         self.t += dt

@@ -67,13 +67,16 @@ def test_filter_matches_oracle(periodic, order):
         S.set_filter(order + 1, -1.0, 8.0)
 
 
-@pytest.mark.parametrize("periodic,cells,filtered", [(True, (8, 2, 6), False), (False, (5, 2, 5), False),
-                                                      (True, (8, 2, 6), True)])
-def test_rk4_steps_match_oracle(periodic, cells, filtered):
+@pytest.mark.parametrize("periodic,cells,filtered,scheme", [(True, (8, 2, 6), False, "rk4"),
+                                                             (False, (5, 2, 5), False, "rk4"),
+                                                             (True, (8, 2, 6), True, "rk4"),
+                                                             (True, (8, 2, 6), False, "lserk54"),
+                                                             (False, (5, 2, 5), True, "lserk54")])
+def test_steps_match_oracle(periodic, cells, filtered, scheme):
     w = wave_workload(*cells, periodic)
     amp, k = 0.03, 2 * np.pi / 2.0
     flt = default_filter(cells[2]) if filtered else None
-    tank = WaveTank(w, tol=1e-12, filter=flt)
+    tank = WaveTank(w, tol=1e-12, filter=flt, scheme=scheme)
     om = tank.set_linear_wave(amp, k)
     dt = 2 * math.pi / om / 40
     tank.dt = dt
@@ -86,7 +89,7 @@ def test_rk4_steps_match_oracle(periodic, cells, filtered):
     F = filter_matrix(cells[2], *flt) if filtered else None
     for _ in range(3):
         tank.step()
-        eta, u, wv, ps = T.step(eta, u, wv, dt)
+        eta, u, wv, ps = (T.step if scheme == "rk4" else T.step_lserk)(eta, u, wv, dt)
         if filtered:
             eta, u, wv = T.filter_surface(eta, F), T.filter_field(u, F), T.filter_field(wv, F)
     torch.cuda.synchronize()

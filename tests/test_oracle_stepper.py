@@ -4,7 +4,7 @@ import math
 import numpy as np
 
 from oracle import basis
-from oracle.stepper import Tank, default_filter, filter_matrix, filter_response
+from oracle.stepper import LSERK54_A, LSERK54_B, Tank, default_filter, filter_matrix, filter_response, lserk54
 
 
 def test_gradient_exact_for_physical_linear_fields_on_curved_mesh():
@@ -84,3 +84,33 @@ def test_filter_single_element_mode_product():
     for i, j in [(6, 6), (5, 2), (0, 6), (3, 4)]:
         f = np.outer(V[:, i], V[:, j]).reshape(-1)   # node (ix, iz), z fastest
         np.testing.assert_allclose(T.filter_field(f, F), S[i] * S[j] * f, atol=1e-13)
+
+
+def test_lserk54_is_fourth_order():
+    """On y' = lam y one step multiplies by the stability polynomial R(z), z = lam dt: its
+    Taylor coefficients up to z^4 are those of exp(z) (order four), the z^5 one is not 1/120
+    (five stages, fourth order)."""
+    zs = np.array([1e-2, 2e-2, -3e-2, 4e-2])
+    R = np.array([lserk54(lambda y: (z * y[0],), [np.array([1.0])], 1.0)[0][0][0] for z in zs])
+    taylor4 = 1 + zs + zs ** 2 / 2 + zs ** 3 / 6 + zs ** 4 / 24
+    c5 = (R - taylor4) / zs ** 5
+    np.testing.assert_allclose(c5, c5[0], rtol=2e-2)  # R is a degree-5 polynomial
+    assert abs(c5[0] - 1 / 120) > 1e-4
+    # exact polynomial coefficients from 5 points: degree 5 with the Taylor part up to z^4
+    pts = np.array([0.1, 0.2, 0.3, 0.4, 0.5, 0.6])
+    vals = [lserk54(lambda y: (z * y[0],), [np.array([1.0])], 1.0)[0][0][0] for z in pts]
+    coef = np.polyfit(pts, vals, 5)[::-1]
+    np.testing.assert_allclose(coef[:5], [1, 1, 1 / 2, 1 / 6, 1 / 24], atol=1e-9)
+    assert len(LSERK54_A) == len(LSERK54_B) == 5 and LSERK54_A[0] == 0.0
+
+
+def test_small_wave_keeps_linear_dispersion_with_lserk54():
+    T = Tank(dict(cells_x=8, cells_z=2, order=6, x0=0.0, x1=2.0, h=1.0, periodic=True))
+    amp, k = 1e-4, math.pi
+    eta, u, w, om = T.linear_wave(amp, k)
+    eta0 = eta.copy()
+    steps = 60
+    dt = 2 * math.pi / om / steps
+    for _ in range(steps):
+        eta, u, w, _ = T.step_lserk(eta, u, w, dt)
+    assert np.max(np.abs(eta - eta0)) <= 3e-3 * amp

@@ -470,7 +470,7 @@ def run_batch(args, ws, rank, local):
 def run_paper(args, ws, rank, local):
     """The paper's own solver experiments in shape (Sec. 6.3): the Table 1 case (P = 8,
     N_x = 102, N_z = 2, 17 waves of kh = 1, H/L = 0.0301) at tolerances 1e-4 ... 1e-10
-    with FP64 PCG, FP64 PDC and the mixed-precision solve, the oracle on the host cores
+    with FP64 PCG, FP64 PDC, FP64 flexible GMRES and the mixed-precision solve, the oracle on the host cores
     beside it; then the scaling sweeps at tol 1e-6 (N_x = 25 ... 800 at P = 8; P = 2 ... 10
     at N_x = 200; ~48 points per wavelength).  Device time per solve: CUDA events, median
     of `steps` solves from a zero initial guess."""
@@ -485,6 +485,7 @@ def run_paper(args, ws, rank, local):
     pmg.load(build_if_missing=True)
     methods = [("fp64_pcg", dict(precision=pmg.PMG_FP64, outer=pmg.PMG_PCG)),
                ("fp64_pdc", dict(precision=pmg.PMG_FP64, outer=pmg.PMG_PDC)),
+               ("fp64_gmres", dict(precision=pmg.PMG_FP64, outer=pmg.PMG_GMRES)),
                ("mixed", dict(precision=pmg.PMG_MIXED_FP32))]
 
     def prepare(w, **opts):
@@ -540,7 +541,7 @@ def run_paper(args, ws, rank, local):
     sweep = {"cells_x": [], "order": []}
     for cx in (25, 50, 102, 200, 400, 800):
         row = {"cells_x": cx, "order": 8}
-        for name, opts in (methods[0], methods[2]):
+        for name, opts in (methods[0], methods[3]):
             S, b, pD = prepare(W.paper_scaling(cx, 8), tol=1e-6, **opts)
             ms, info = time_solve(S, b, pD)
             row[name] = {"iterations": info["iterations"], "ms": ms, "nodes": S.n}
@@ -549,7 +550,7 @@ def run_paper(args, ws, rank, local):
         log("cells_x", row)
     for order in (2, 3, 4, 5, 6, 7, 8, 9, 10):
         row = {"cells_x": 200, "order": order}
-        for name, opts in (methods[0], methods[2]):
+        for name, opts in (methods[0], methods[3]):
             S, b, pD = prepare(W.paper_scaling(200, order), tol=1e-6, **opts)
             ms, info = time_solve(S, b, pD)
             row[name] = {"iterations": info["iterations"], "ms": ms, "nodes": S.n}

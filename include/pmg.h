@@ -53,11 +53,14 @@ enum { PMG_FP64 = 0, PMG_MIXED_FP32 = 1, PMG_MIXED_BF16 = 2 };
  *   PMG_PDC  preconditioned defect correction x <- x + B(b - Ax) (Sec. 5.4)
  *   PMG_IR   FP64 iterative refinement around an inner FP32 flexible-CG solve
  *            (mixed precision only; inner_max / inner_tol apply)
+ *   PMG_GMRES  flexible GMRES(gmres_restart) with the V-cycle as right preconditioner
+ *            (Sec. 5.4's GMRES-MG on the same-stage operator); Arnoldi by classical
+ *            Gram-Schmidt applied twice, one host synchronisation per iteration
  * With PMG_MIXED_FP32 the V-cycle B runs in FP32 on the FP32-rounded residual.
  * PMG_MIXED_BF16 (requires PMG_IR): as PMG_MIXED_FP32, and the inner solve's
  * actual-geometry operator runs its contractions on the BF16 tensor cores with hi/lo
  * split operands and FP32 accumulation (pmg_apply_bf16, split = 1). */
-enum { PMG_PCG = 0, PMG_FCG = 1, PMG_PDC = 2, PMG_IR = 3 };
+enum { PMG_PCG = 0, PMG_FCG = 1, PMG_PDC = 2, PMG_IR = 3, PMG_GMRES = 4 };
 /* smoother: element-block additive Schwarz (Sec. 5.3), blocks inverted by fast
  * diagonalisation (exact for the separable flat-geometry level operators) */
 enum { PMG_ASM_FDM = 0 };
@@ -96,6 +99,8 @@ typedef struct {
   int df64_outer;    /* outer actual-geometry operator (FP64 vectors in and out) computed in */
                      /* double-float arithmetic on the FP32 pipe (48-bit significand): 1 on, */
                      /* 0 off (FP64 pipe), -1 (default) on for the mixed precisions only     */
+  int gmres_restart; /* PMG_GMRES cycle length m, 1..60 (default 30); the handle then holds */
+                     /* 2m+1 extra FP64 vectors                                              */
 } pmg_opts;
 
 typedef struct {

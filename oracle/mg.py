@@ -244,6 +244,61 @@ def pdc(A, b, prec, x0=None, tol=1e-10, maxit=500):
     return x, maxit, hist
 
 
+def fgmres(A, b, prec, x0=None, tol=1e-10, maxit=500, restart=30):
+    """Flexible GMRES(restart) with right preconditioning (Saad 1993): Arnoldi by modified
+    Gram-Schmidt on z_j = prec(v_j), the least-squares problem by Givens rotations, and
+    x = x0 + Z y at the end of a cycle.  Stops when the residual estimate |g_{j+1}| <=
+    tol ||b|| (checked against the true residual at each restart).  Returns (x,
+    iterations, relres history)."""
+    x = np.zeros_like(b) if x0 is None else np.array(x0, float, copy=True)
+    nb = np.linalg.norm(b)
+    if nb == 0.0:
+        return np.zeros_like(b), 0, [0.0]
+    r = b - A @ x
+    hist = [np.linalg.norm(r) / nb]
+    its = 0
+    while hist[-1] > tol and its < maxit:
+        beta = np.linalg.norm(r)
+        m = min(restart, maxit - its)
+        V = np.zeros((m + 1, b.size))
+        Z = np.zeros((m, b.size))
+        H = np.zeros((m + 1, m))
+        cs, sn = np.zeros(m), np.zeros(m)
+        g = np.zeros(m + 1)
+        g[0] = beta
+        V[0] = r / beta
+        k = 0
+        for j in range(m):
+            Z[j] = prec(V[j])
+            w = A @ Z[j]
+            for i in range(j + 1):
+                H[i, j] = w @ V[i]
+                w = w - H[i, j] * V[i]
+            H[j + 1, j] = np.linalg.norm(w)
+            if H[j + 1, j] > 0:
+                V[j + 1] = w / H[j + 1, j]
+            for i in range(j):  # earlier rotations on the new column
+                t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+                H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
+                H[i, j] = t
+            den = np.hypot(H[j, j], H[j + 1, j])
+            cs[j], sn[j] = H[j, j] / den, H[j + 1, j] / den
+            H[j, j] = den
+            H[j + 1, j] = 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            its += 1
+            k = j + 1
+            hist.append(abs(g[j + 1]) / nb)
+            if hist[-1] <= tol:
+                break
+        y = np.linalg.solve(np.triu(H[:k, :k]), g[:k])
+        x = x + Z[:k].T @ y
+        r = b - A @ x
+        hist[-1] = np.linalg.norm(r) / nb
+    return x, its, hist
+
+
 def solve(mesh, eta, b, p_dirichlet, hier=None, method='pcg', x0=None, tol=1e-10, maxit=500,
           **hier_kw):
     """Full solve on the actual geometry: Dirichlet lifting, then the preconditioned
@@ -255,7 +310,7 @@ def solve(mesh, eta, b, p_dirichlet, hier=None, method='pcg', x0=None, tol=1e-10
     if hier is None:
         hier = Hierarchy(mesh, eta, **hier_kw)
     x0f = None if x0 is None else np.asarray(x0, float)[free]
-    f = {'pcg': pcg, 'fcg': fcg, 'pdc': pdc}[method]
+    f = {'pcg': pcg, 'fcg': fcg, 'pdc': pdc, 'gmres': fgmres}[method]
     xf, its, hist = f(AFF, bt, hier.vcycle, x0=x0f, tol=tol, maxit=maxit)
     p = np.array(p_dirichlet, float, copy=True)
     p[free] = xf

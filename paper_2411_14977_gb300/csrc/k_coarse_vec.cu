@@ -373,4 +373,69 @@ cudaError_t check_finite(size_t n, const double* v, int* status, cudaStream_t st
   return cudaGetLastError();
 }
 
+// ---- GMRES (Arnoldi) vector kernels -------------------------------------------------
+// h[k] = <w, V_k> for k < nv (V_k = V + k n): per-block partials of every k, then the last
+// block to finish (ticket) adds them in block order, so the sums are deterministic.
+__global__ void __launch_bounds__(VEC_THREADS) k_mdot(size_t n, const double* w, const double* V, int nv,
+                                                      double* h, double* part, unsigned* cnt) {
+  __shared__ double red[34];
+  __shared__ int s_flag;
+  for (int k = 0; k < nv; ++k) {
+    const double* v = V + (size_t)k * n;
+    double a = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+      a = fma(w[i], v[i], a);
+    a = block_sum(a, red);
+    if (threadIdx.x == 0) part[(size_t)k * gridDim.x + blockIdx.x] = a;
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_flag = (atomicAdd(cnt, 1u) == gridDim.x - 1);
+    if (s_flag) __threadfence();
+  }
+  __syncthreads();
+  if (!s_flag) return;
+  for (int k = 0; k < nv; ++k) {
+    double v = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) v += ((volatile double*)part)[(size_t)k * gridDim.x + b];
+    v = block_sum(v, red);
+    if (threadIdx.x == 0) h[k] = v;
+  }
+  if (threadIdx.x == 0) *cnt = 0u;
+}
+
+// w += sign sum_k c[k] V_k  (c on the device)
+__global__ void k_maxpy(size_t n, double* w, const double* V, int nv, const double* c, double sign) {
+  __shared__ double cs[64];
+  for (int k = threadIdx.x; k < nv; k += blockDim.x) cs[k] = sign * c[k];
+  __syncthreads();
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    double a = w[i];
+    for (int k = 0; k < nv; ++k) a = fma(cs[k], V[(size_t)k * n + i], a);
+    w[i] = a;
+  }
+}
+
+// v = w / sqrt(*nrm2)   (a zero norm leaves v unused: the caller stops the cycle)
+__global__ void k_scale_inv_norm(size_t n, const double* w, const double* nrm2, double* v) {
+  double s = 1.0 / sqrt(*nrm2);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    v[i] = w[i] * s;
+}
+
+cudaError_t gmres_mdot(size_t n, const double* w, const double* V, int nv, double* h, double* part, unsigned* cnt,
+                       cudaStream_t st) {
+  k_mdot<<<VEC_BLOCKS, VEC_THREADS, 0, st>>>(n, w, V, nv, h, part, cnt);
+  return cudaGetLastError();
+}
+cudaError_t gmres_maxpy(size_t n, double* w, const double* V, int nv, const double* c, double sign, cudaStream_t st) {
+  if (nv > 64) return cudaErrorInvalidValue;
+  k_maxpy<<<vec_grid(n), VEC_THREADS, 0, st>>>(n, w, V, nv, c, sign);
+  return cudaGetLastError();
+}
+cudaError_t gmres_scale(size_t n, const double* w, const double* nrm2, double* v, cudaStream_t st) {
+  k_scale_inv_norm<<<vec_grid(n), VEC_THREADS, 0, st>>>(n, w, nrm2, v);
+  return cudaGetLastError();
+}
+
 }  // namespace pmg

@@ -155,6 +155,12 @@ cudaError_t to_f32_scaled(size_t n, const double* x, float* y, const double* s, 
 cudaError_t add_f32_scaled(size_t n, double* x, const float* c, const double* s, int slot, cudaStream_t st);
 template <typename T> cudaError_t add(size_t n, T* x, const T* y, cudaStream_t st);
 cudaError_t cast_f32(size_t n, const double* x, float* y, cudaStream_t st);
+// GMRES: h[k] = <w, V_k> (k < nv, deterministic; part: >= nv * 304 doubles, cnt zeroed),
+// w += sign sum_k c[k] V_k (nv <= 64), v = w / sqrt(*nrm2)
+cudaError_t gmres_mdot(size_t n, const double* w, const double* V, int nv, double* h, double* part, unsigned* cnt,
+                       cudaStream_t st);
+cudaError_t gmres_maxpy(size_t n, double* w, const double* V, int nv, const double* c, double sign, cudaStream_t st);
+cudaError_t gmres_scale(size_t n, const double* w, const double* nrm2, double* v, cudaStream_t st);
 // time-stepper kernels (k_stepper.cu)
 cudaError_t gradient(const Shape& s, const double* f, double* fx, double* fz, const double* eta, const double* sigma,
                      double h, double dx, double dsig, cudaStream_t st);

@@ -264,6 +264,10 @@ struct pmg_handle {
   int* status_host = nullptr;
   double* io = nullptr;  // pmg_solve_host: out, b, p_D, x0
   double* filt = nullptr;  // (P+1)^2 nodal spectral filter, set by pmg_set_filter
+  // flexible GMRES(m): Arnoldi basis V [(m+1) N], preconditioned directions Z [m N], device
+  // coefficients (two Gram-Schmidt passes and the new norm), block partials, ticket, y
+  double *gm_V = nullptr, *gm_Z = nullptr, *gm_h = nullptr, *gm_part = nullptr, *gm_y = nullptr;
+  unsigned* gm_cnt = nullptr;
   Scratch sc{};
   // profiling: per-class launch counts; optional CUDA-event pairs around launches
   bool timing = false;
@@ -893,6 +897,92 @@ pmg_status solve_krylov64(pmg_handle* h, const double* b, pmg_solve_info* info, 
   return PMG_OK;
 }
 
+// z = B v with the handle's V-cycle (FP32 V-cycle on the rounded vector when mixed)
+pmg_status precondition_vec(pmg_handle* h, const double* v, double* z, cudaStream_t st) {
+  size_t N = h->N;
+  if (h->opts.precision == PMG_FP64) return vcycle<double>(h, 0, v, z, st);
+  CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{12.0 * N, 0.0}, [&] { return cast_f32(N, v, h->r32, st); }));
+  CKS(vcycle<float>(h, 0, h->r32, h->z32, st));
+  return launch(h, PMG_K_VECTOR, 1, st, Cost{12.0 * N, 0.0}, [&] { return cast_f64(N, h->z32, z, st); });
+}
+
+// Flexible GMRES(m) with right preconditioning by the V-cycle (Sec. 5.4's GMRES-MG on the
+// same-stage operator): Arnoldi by classical Gram-Schmidt applied twice (device multi-dot
+// and multi-axpy kernels), the Hessenberg least-squares problem by Givens rotations on the
+// host (one synchronisation per iteration), x += Z y at the end of a cycle, the true FP64
+// residual at every restart.
+pmg_status solve_gmres(pmg_handle* h, const double* b, pmg_solve_info* info, cudaStream_t st) {
+  const size_t N = h->N;
+  const int m = h->opts.gmres_restart;
+  const double tol2 = h->opts.tol * h->opts.tol * h->scal_host[SLOT_BB];
+  double* V = h->gm_V;
+  double* Z = h->gm_Z;
+  double* hd = h->gm_h;  // [0, m]: first pass, [m+1, 2m+1]: second pass, [2m+2]: ||w||^2
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m), col(2 * (m + 1) + 1);
+  auto Hij = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
+  CKS(outer_residual(h, b, SLOT_RR64, st));
+  CKS(read_scalars(h, st));
+  int its = 0;
+  while (true) {
+    const double rr = h->scal_host[SLOT_RR64];
+    if (!std::isfinite(rr)) return fail(PMG_ERR_NONFINITE, "non-finite residual");
+    if (rr <= tol2 || its >= h->opts.max_iter) break;
+    CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{16.0 * N, 1.0 * N}, [&] { return gmres_scale(N, h->r, h->scal + SLOT_RR64, V, st); }));
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = std::sqrt(rr);
+    int k = 0;
+    for (int j = 0; j < m && its < h->opts.max_iter; ++j) {
+      double* vj = V + (size_t)j * N;
+      CKS(precondition_vec(h, vj, Z + (size_t)j * N, st));
+      CKS(curved<double>(h, 0, Z + (size_t)j * N, nullptr, h->w, 1, nullptr, st));
+      const int nv = j + 1;
+      for (int pass = 0; pass < 2; ++pass) {
+        double* c = hd + pass * (m + 1);
+        CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{8.0 * N * (nv + 1), 2.0 * N * nv},
+                   [&] { return gmres_mdot(N, h->w, V, nv, c, h->gm_part, h->gm_cnt, st); }));
+        CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{8.0 * N * (nv + 2), 2.0 * N * nv},
+                   [&] { return gmres_maxpy(N, h->w, V, nv, c, -1.0, st); }));
+      }
+      CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{8.0 * N, 2.0 * N},
+                 [&] { return dot<double, double>(N, h->w, h->w, hd + 2 * (m + 1), 0, h->sc, st); }));
+      CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{16.0 * N, 1.0 * N},
+                 [&] { return gmres_scale(N, h->w, hd + 2 * (m + 1), V + (size_t)(j + 1) * N, st); }));
+      CK(cudaMemcpyAsync(col.data(), hd, col.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      for (int i = 0; i <= j; ++i) Hij(i, j) = col[i] + col[(m + 1) + i];
+      const double hn = std::sqrt(std::max(col[2 * (m + 1)], 0.0));
+      if (!std::isfinite(hn)) return fail(PMG_ERR_NONFINITE, "non-finite Arnoldi vector");
+      for (int i = 0; i < j; ++i) {  // earlier rotations on the new column
+        double t = cs[i] * Hij(i, j) + sn[i] * Hij(i + 1, j);
+        Hij(i + 1, j) = -sn[i] * Hij(i, j) + cs[i] * Hij(i + 1, j);
+        Hij(i, j) = t;
+      }
+      const double den = std::hypot(Hij(j, j), hn);
+      if (!(den > 0.0)) return fail(PMG_ERR_NONFINITE, "GMRES breakdown");
+      cs[j] = Hij(j, j) / den;
+      sn[j] = hn / den;
+      Hij(j, j) = den;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++its;
+      k = j + 1;
+      if (g[j + 1] * g[j + 1] <= tol2 || !(hn > 0.0)) break;  // converged or lucky breakdown
+    }
+    for (int i = k - 1; i >= 0; --i) {  // back substitution H y = g
+      double v = g[i];
+      for (int l = i + 1; l < k; ++l) v -= Hij(i, l) * y[l];
+      y[i] = v / Hij(i, i);
+    }
+    CK(cudaMemcpyAsync(h->gm_y, y.data(), k * sizeof(double), cudaMemcpyHostToDevice, st));
+    CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{8.0 * N * (k + 2), 2.0 * N * k},
+               [&] { return gmres_maxpy(N, h->x, Z, k, h->gm_y, 1.0, st); }));
+    CKS(outer_residual(h, b, SLOT_RR64, st));
+    CKS(read_scalars(h, st));
+  }
+  if (info) info->iterations = its;
+  return PMG_OK;
+}
+
 pmg_status solve_pdc(pmg_handle* h, const double* b, pmg_solve_info* info, cudaStream_t st) {
   // x <- x + B (b~ - A x) (Sec. 5.4); B = V-cycle in the handle's precision
   size_t N = h->N;
@@ -1125,6 +1215,7 @@ void pmg_default_opts(pmg_opts* o) {
   o->fuse_residual = -1;
   o->flat_kernel = -1;
   o->df64_outer = -1;
+  o->gmres_restart = 30;
 }
 
 const char* pmg_last_error(void) { return g_err.c_str(); }
@@ -1145,7 +1236,9 @@ pmg_status pmg_create(const pmg_mesh_desc* mesh, const pmg_opts* opts, pmg_handl
   if (o.precision < 0 || o.precision > PMG_MIXED_BF16) return fail(PMG_ERR_INVALID, "unsupported precision");
   if (o.precision == PMG_MIXED_BF16 && o.outer != PMG_IR)
     return fail(PMG_ERR_INVALID, "the BF16 operator runs in the inner solve of iterative refinement (outer = PMG_IR)");
-  if (o.outer < PMG_PCG || o.outer > PMG_IR) return fail(PMG_ERR_INVALID, "bad outer method");
+  if (o.outer < PMG_PCG || o.outer > PMG_GMRES) return fail(PMG_ERR_INVALID, "bad outer method");
+  if (o.outer == PMG_GMRES && (o.gmres_restart < 1 || o.gmres_restart > 60))
+    return fail(PMG_ERR_INVALID, "gmres_restart must be in 1..60");
   if (o.outer == PMG_IR && o.precision == PMG_FP64)
     return fail(PMG_ERR_INVALID, "iterative refinement needs a mixed precision");
   if (o.smoother != PMG_ASM_FDM || o.precond_geom != PMG_FLAT_LINEARISED)
@@ -1249,6 +1342,19 @@ pmg_status pmg_create(const pmg_mesh_desc* mesh, const pmg_opts* opts, pmg_handl
   ALLOC(h->sc.partials, double, std::max<size_t>(1024, 2 * (size_t)m.cells_x + 8));
   ALLOC(h->sc.edgepart, double, nedges);
   ALLOC(h->sc.redcnt, unsigned, 1);
+  if (o.outer == PMG_GMRES) {
+    const size_t mm = (size_t)o.gmres_restart;
+    ALLOC(h->gm_V, double, (mm + 1) * h->N);
+    ALLOC(h->gm_Z, double, mm * h->N);
+    ALLOC(h->gm_h, double, 2 * (mm + 1) + 1);
+    ALLOC(h->gm_part, double, (mm + 1) * 304);
+    ALLOC(h->gm_y, double, mm);
+    ALLOC(h->gm_cnt, unsigned, 1);
+    if (cudaMemset(h->gm_cnt, 0, sizeof(unsigned)) != cudaSuccess ||
+        cudaMemset(h->gm_V, 0, (mm + 1) * h->N * sizeof(double)) != cudaSuccess ||
+        cudaMemset(h->gm_Z, 0, mm * h->N * sizeof(double)) != cudaSuccess)
+      return bail(fail(PMG_ERR_CUDA, "memset failed"));
+  }
 #undef ALLOC
   if (cudaMemset(h->sc.edgebuf, 0, ebuf * sizeof(double)) != cudaSuccess ||
       cudaMemset(h->sc.edgecnt, 0, nedges * sizeof(unsigned)) != cudaSuccess ||
@@ -1452,6 +1558,7 @@ pmg_status pmg_solve(pmg_handle* h, const double* b, const double* pD, const dou
   } else if (bb > 0.0) {
     pmg_status s;
     if (h->opts.outer == PMG_PDC) s = solve_pdc(h, b, &loc, st);
+    else if (h->opts.outer == PMG_GMRES) s = solve_gmres(h, b, &loc, st);
     else if (h->opts.outer == PMG_IR)
       s = h->timing ? solve_refine(h, b, &loc, st) : solve_refine_graph(h, b, &loc, st);
     else

@@ -13,7 +13,7 @@ from . import build as _build
 PMG_OK, PMG_ERR_INVALID, PMG_ERR_OOM, PMG_ERR_CUDA = 0, 1, 2, 3
 PMG_ERR_NOT_CONVERGED, PMG_ERR_NONFINITE, PMG_ERR_TIMEOUT = 4, 5, 6
 PMG_FP64, PMG_MIXED_FP32, PMG_MIXED_BF16 = 0, 1, 2
-PMG_PCG, PMG_FCG, PMG_PDC, PMG_IR = 0, 1, 2, 3
+PMG_PCG, PMG_FCG, PMG_PDC, PMG_IR, PMG_GMRES = 0, 1, 2, 3, 4
 PMG_ASM_FDM = 0
 PMG_FLAT_LINEARISED = 1
 
@@ -42,7 +42,7 @@ class Opts(ctypes.Structure):
                 ("omega", ctypes.c_double), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("inner_max", ctypes.c_int), ("inner_tol", ctypes.c_double), ("nlevels", ctypes.c_int),
                 ("level_orders", ctypes.c_int * 8), ("fuse_residual", ctypes.c_int), ("flat_kernel", ctypes.c_int),
-                ("df64_outer", ctypes.c_int)]
+                ("df64_outer", ctypes.c_int), ("gmres_restart", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):

@@ -55,7 +55,9 @@ def test_default_opts():
     (dict(), dict(fuse_residual=2), "options"),
     (dict(), dict(df64_outer=3), "options"),
     (dict(), dict(flat_kernel=2), "options"),
-    (dict(), dict(outer=4), "outer"),
+    (dict(), dict(outer=5), "outer"),
+    (dict(), dict(outer=4, gmres_restart=0), "gmres_restart"),
+    (dict(), dict(outer=4, gmres_restart=61), "gmres_restart"),
     (dict(), dict(nlevels=4, levels=[4, 2, 2, 1]), "decrease"),
     (dict(), dict(nlevels=2, levels=[4, 2]), "order to 1"),
 ])

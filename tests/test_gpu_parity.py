@@ -196,7 +196,9 @@ SOLVE_CASES = ["tank12x3p6", "cfg1", "periodic8x3p5", "tank6x2p8", "tank5x1p4_nz
                                      dict(precision=pmg.PMG_MIXED_FP32, outer=pmg.PMG_PDC),
                                      dict(precision=pmg.PMG_MIXED_FP32, fuse_residual=1),
                                      dict(precision=pmg.PMG_MIXED_BF16, outer=pmg.PMG_IR),
-                                     dict(precision=pmg.PMG_MIXED_FP32, flat_kernel=1)])
+                                     dict(precision=pmg.PMG_MIXED_FP32, flat_kernel=1),
+                                     dict(outer=pmg.PMG_GMRES), dict(outer=pmg.PMG_GMRES, gmres_restart=3),
+                                     dict(precision=pmg.PMG_MIXED_FP32, outer=pmg.PMG_GMRES)])
 def test_solve_matches_direct(name, variant):
     w = CASES[name]()
     c = Case(w, tol=1e-12, **variant)
@@ -223,6 +225,11 @@ def test_solve_matches_direct(name, variant):
     if not variant:
         # FP64 PCG: same iteration count as the oracle's PCG with the same V-cycle (+-1)
         _, its, _, _ = mg.solve(c.m, c.eta, bo, c.F["pD"], tol=1e-12, overlap=1, nu=2, omega=0.8)
+        assert abs(info["iterations"] - its) <= 1, (info["iterations"], its)
+    if variant == dict(outer=pmg.PMG_GMRES):
+        # FP64 GMRES: the oracle's flexible GMRES with the same V-cycle (+-1)
+        _, its, _, _ = mg.solve(c.m, c.eta, bo, c.F["pD"], method="gmres", tol=1e-12, overlap=1, nu=2,
+                                omega=0.8)
         assert abs(info["iterations"] - its) <= 1, (info["iterations"], its)
 
 

@@ -114,3 +114,41 @@ def test_iterations_flat_in_nx_and_p():
         m, eta, b, pD = _problem(w)
         its_p.append(mg.solve(m, eta, b, pD, tol=1e-6, **DEFAULTS)[1])
     assert max(its_p) - min(its_p) <= 3 and its_p[-1] <= its_p[0] + 2, its_p
+
+
+def test_fgmres_finite_termination_and_scipy():
+    """GMRES on an n x n system reaches the solution within n iterations (identity
+    preconditioner, no restart); with the exact inverse as preconditioner in one; the
+    result agrees with scipy.sparse.linalg.gmres; the residual history never increases
+    within a cycle."""
+    import scipy.sparse.linalg as spla
+    rng = np.random.default_rng(7)
+    n = 12
+    A = rng.standard_normal((n, n)) + n * np.eye(n)  # nonsymmetric, well conditioned
+    b = rng.standard_normal(n)
+    x, its, hist = mg.fgmres(A, b, lambda v: v, tol=1e-13, restart=n)
+    assert its <= n
+    np.testing.assert_allclose(A @ x, b, atol=1e-11 * np.linalg.norm(b))
+    assert all(h2 <= h1 * (1 + 1e-12) for h1, h2 in zip(hist[:-1], hist[1:-1]))
+    Ainv = np.linalg.inv(A)
+    x1, its1, _ = mg.fgmres(A, b, lambda v: Ainv @ v, tol=1e-12)
+    assert its1 == 1
+    xs, info = spla.gmres(A, b, rtol=1e-13, restart=n, atol=0.0)
+    assert info == 0
+    np.testing.assert_allclose(x, xs, rtol=0, atol=1e-10 * np.linalg.norm(xs))
+    # restarted: still converges, more iterations than the unrestarted run
+    x3, its3, _ = mg.fgmres(A, b, lambda v: v, tol=1e-10, restart=3)
+    np.testing.assert_allclose(A @ x3, b, atol=1e-9 * np.linalg.norm(b))
+    assert its3 >= its - 1
+
+
+def test_fgmres_with_vcycle_matches_pcg_solution():
+    w = W.tank(6, 2, 4)
+    m = Mesh(**w.mesh_kwargs())
+    F = w.fields(m.column_x(), m.row_sigma())
+    b = m.rhs_divergence(F["eta"], F["u"], F["w"])
+    p1, its_g, hist_g, _ = mg.solve(m, F["eta"], b, F["pD"], method="gmres", tol=1e-12, overlap=1, nu=2, omega=0.8)
+    p2, its_c, _, _ = mg.solve(m, F["eta"], b, F["pD"], method="pcg", tol=1e-12, overlap=1, nu=2, omega=0.8)
+    np.testing.assert_allclose(p1, p2, rtol=0, atol=1e-9 * np.abs(p2).max())
+    assert hist_g[-1] <= 1e-12
+    assert its_g <= its_c + 1

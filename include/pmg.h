@@ -136,6 +136,14 @@ pmg_status pmg_node_coords(const pmg_handle* h, double* x_cols_host, double* sig
  * surface is the degree-P interpolant of these values per cell; d = eta + h must stay
  * positive.  The multigrid hierarchy is not rebuilt (flat preconditioner, Sec. 5.4). */
 pmg_status pmg_set_geometry(pmg_handle* h, const double* eta_dev, void* stream);
+/* Mixed-stage operator (Sec. 3, the mixed-stage Laplace operator nabla^k . nabla^(k-1)):
+ * sets the stage-k geometry as pmg_set_geometry does (eta: stage k, also used by the
+ * right-hand sides) and makes the outer operator a(v, p) = int over the stage-k domain of
+ * grad^k v . grad^(k-1) p, the trial gradient taken on the stage-(k-1) surface eta_prev
+ * (both NX doubles, device).  Nonsymmetric: pmg_solve then needs outer PMG_PDC or
+ * PMG_GMRES (else PMG_ERR_INVALID); the V-cycle keeps the flat geometry.
+ * pmg_set_geometry returns to the same-stage operator. */
+pmg_status pmg_set_geometry_mixed(pmg_handle* h, const double* eta_dev, const double* eta_prev_dev, void* stream);
 
 /* b_i = -int N_i f dOmega + int_{Gamma_N} N_i g dGamma (LGL collocation), b = 0 on the
  * free surface.  f: nodal values (n); g_bottom: outward normal derivative on the bottom

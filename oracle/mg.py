@@ -300,11 +300,12 @@ def fgmres(A, b, prec, x0=None, tol=1e-10, maxit=500, restart=30):
 
 
 def solve(mesh, eta, b, p_dirichlet, hier=None, method='pcg', x0=None, tol=1e-10, maxit=500,
-          **hier_kw):
+          eta_prev=None, **hier_kw):
     """Full solve on the actual geometry: Dirichlet lifting, then the preconditioned
-    Krylov method on A_FF with one V-cycle of `hier` as the preconditioner.
+    Krylov method on A_FF with one V-cycle of `hier` as the preconditioner.  With
+    eta_prev the operator is the mixed-stage one (stage k = eta, stage k-1 = eta_prev).
     Returns (p full-length, iterations, history, hierarchy)."""
-    A = mesh.assemble(eta)
+    A = mesh.assemble(eta) if eta_prev is None else mesh.assemble_mixed(eta, eta_prev)
     dmask = mesh.dirichlet_mask()
     AFF, bt, free = lifted_system(A, b, p_dirichlet, dmask)
     if hier is None:

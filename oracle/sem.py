@@ -150,6 +150,41 @@ class Mesh:
         return (np.einsum('eqa,eq,eqb->eab', Gx, wJ, Gx)
                 + np.einsum('eqa,eq,eqb->eab', Gz, wJ, Gz))
 
+    def element_stiffness_mixed(self, eta_k, eta_km1, elems=None):
+        """Mixed-stage element matrices (Sec. 3, the mixed-stage Laplace operator) in the
+        conservative weak form a(v, p) = int_{Omega^k} grad^k v . grad^(k-1) p: the test
+        gradient with the stage-k map, the trial gradient with the stage-(k-1) map, the
+        measure of stage k.  Nonsymmetric unless the two surfaces coincide."""
+        rx, rz, sx, sz, J = self.element_metrics(eta_k)
+        qx, qz, tx, tz, _ = self.element_metrics(eta_km1)
+        if elems is not None:
+            rx, rz, sx, sz, J = rx[elems], rz[elems], sx[elems], sz[elems], J[elems]
+            qx, qz, tx, tz = qx[elems], qz[elems], tx[elems], tz[elems]
+        E = rx.shape[0]
+        nn = (self.P + 1) ** 2
+        Gr, Gs = self.ref_gradients()
+        wJ = self.quad_weights()[None, :] * J.reshape(E, nn)
+        Vx = rx.reshape(E, nn, 1) * Gr[None] + sx.reshape(E, nn, 1) * Gs[None]
+        Vz = rz.reshape(E, nn, 1) * Gr[None] + sz.reshape(E, nn, 1) * Gs[None]
+        Px = qx.reshape(E, nn, 1) * Gr[None] + tx.reshape(E, nn, 1) * Gs[None]
+        Pz = qz.reshape(E, nn, 1) * Gr[None] + tz.reshape(E, nn, 1) * Gs[None]
+        return (np.einsum('eqa,eq,eqb->eab', Vx, wJ, Px)
+                + np.einsum('eqa,eq,eqb->eab', Vz, wJ, Pz))
+
+    def assemble_mixed(self, eta_k, eta_km1, chunk=2048):
+        """Global mixed-stage matrix sum_e Q_e^T K_e Q_e (rows: stage-k test functions)."""
+        E = self.Nx * self.Nz
+        A = sp.csr_matrix((self.N, self.N))
+        for s in range(0, E, chunk):
+            el = np.arange(s, min(E, s + chunk))
+            K = self.element_stiffness_mixed(eta_k, eta_km1, el)
+            g = self.e2g[el]
+            rows = np.repeat(g[:, :, None], g.shape[1], axis=2).reshape(-1)
+            cols = np.repeat(g[:, None, :], g.shape[1], axis=1).reshape(-1)
+            A = A + sp.coo_matrix((K.reshape(-1), (rows, cols)), shape=(self.N, self.N)).tocsr()
+        A.sum_duplicates()
+        return A
+
     def assemble(self, eta, chunk=2048):
         """Global stiffness A = sum_e Q_e^T K_e Q_e (Sec. 4.2 global = sum of local), CSR."""
         E = self.Nx * self.Nz

@@ -54,6 +54,49 @@ __global__ void k_geometry(Shape s, const double* eta, double h, double dx, doub
   }
 }
 
+// Column factors of the mixed-stage operator (stage k surface eta, stage k-1 surface etap):
+// A = w d dsig/dx, B1 = w d_x' d/d', B2 = w d_x, C = w (dx/dsig)/d', E = d_x d_x'.
+template <int P>
+__global__ void k_geometry_mixed(Shape s, const double* eta, const double* etap, double h, double dx, double dsig,
+                                 double* geo, int* status) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  constexpr int n = P + 1;
+  if (t >= s.Nx * n) return;
+  int ex = t / n, i = t % n;
+  double dd = 0.0, ddp = 0.0;
+#pragma unroll
+  for (int m = 0; m < n; ++m) {
+    int c = wrap_col(s, ex * P + m);
+    dd += cT.D[P][i][m] * eta[c];
+    ddp += cT.D[P][i][m] * etap[c];
+  }
+  dd *= 2.0 / dx;
+  ddp *= 2.0 / dx;
+  int c = wrap_col(s, ex * P + i);
+  double d = eta[c] + h, dp = etap[c] + h;
+  if (!(d > 0.0) || !(dp > 0.0) || !isfinite(dd) || !isfinite(ddp)) atomicExch(status, 1);
+  double w = cT.w[P][i];
+  double* g = geo + (size_t)t * 5;
+  g[0] = w * d * dsig / dx;
+  g[1] = w * ddp * d / dp;
+  g[2] = w * dd;
+  g[3] = w * (dx / dsig) / dp;
+  g[4] = dd * ddp;
+}
+
+cudaError_t geometry_mixed(const Shape& s, const double* eta, const double* etap, double h, double dx, double dsig,
+                           double* geo, int* status, cudaStream_t st) {
+  int n = s.P + 1, tot = s.Nx * n, bs = 128, nb = (tot + bs - 1) / bs;
+  switch (s.P) {
+#define PMG_CASE(PP) case PP: k_geometry_mixed<PP><<<nb, bs, 0, st>>>(s, eta, etap, h, dx, dsig, geo, status); break;
+    PMG_CASE(1) PMG_CASE(2) PMG_CASE(3) PMG_CASE(4) PMG_CASE(5)
+    PMG_CASE(6) PMG_CASE(7) PMG_CASE(8) PMG_CASE(9) PMG_CASE(10)
+#undef PMG_CASE
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 // b = -w_i w_j J f + edge terms; J = (dx/2)(dsig/2) d summed over the elements of a node
 // equals d (dx dsig / 4) mX mZ with mX, mZ the assembled LGL weights.
 __global__ void k_rhs_source(Shape s, const double* eta, double h, double dx, double dsig,
@@ -93,6 +136,16 @@ cudaError_t curved_op(const CurvedArgs& a, cudaStream_t st) {
   if (a.tc) {
     if (!std::is_same<T, float>::value || (a.mode != MODE_APPLY && a.mode != MODE_DOT)) return cudaErrorInvalidValue;
     return curved_op_tc(a, st);
+  }
+  if (a.mix) {
+    if constexpr (std::is_same<T, float>::value) {
+      return cudaErrorInvalidValue;
+    } else {
+      p.geo = (const IO*)a.geo5;
+      if (a.mode == MODE_APPLY) return launch_curved<T, MODE_APPLY, 0, true>(p, thr, st);
+      if (a.mode == MODE_RESIDUAL) return launch_curved<T, MODE_RESIDUAL, 0, true>(p, thr, st);
+      return cudaErrorInvalidValue;
+    }
   }
   switch (a.mode) {
     case MODE_APPLY: return launch_curved<T, MODE_APPLY, 0>(p, thr, st);

@@ -103,9 +103,15 @@ __device__ __forceinline__ void tc_contract(TcKind kind, int ntiles, GetB getb, 
   }
 }
 
-template <int P, typename T, int MODE, int TC>
+// MIX: the mixed-stage operator a(v, p) = int_{Omega^k} grad^k v . grad^(k-1) p (Sec. 3) with
+// five column factors per node column (k_geometry_mixed): A = w d_k dsig/dx,
+// B1 = w d_x(k-1) d_k / d_(k-1), B2 = w d_x(k), C = w (dx/dsig) / d_(k-1), E = d_x(k) d_x(k-1):
+//   W_r = w_j (A U_r - sigma B1 U_s),  W_s = w_j (-sigma B2 U_r + C (1 + sigma^2 E) U_s).
+template <int P, typename T, int MODE, int TC, bool MIX = false>
 __global__ void __launch_bounds__(512) k_curved(CurvedParams<T> p) {
   static_assert(TC == 0 || (std::is_same<T, float>::value && MODE != MODE_DIV), "tensor-core path: FP32 operator");
+  static_assert(!MIX || (TC == 0 && (MODE == MODE_APPLY || MODE == MODE_RESIDUAL)), "mixed-stage: apply/residual");
+  constexpr int NG = MIX ? 5 : 4;  // column factors per node column
   constexpr int n = P + 1;
   const Shape s = p.s;
   const int NZ = s.NZ, Nz = s.Nz, NZp = slab_pitch(NZ);
@@ -116,10 +122,10 @@ __global__ void __launch_bounds__(512) k_curved(CurvedParams<T> p) {
   T* Ur = X + n * NZp;                      // [n][NZp]   U_r per node row
   T* Ws = Ur + n * NZp;                     // [Nz][n][n] (ez, j, i): U_s then W_s
   T* Wr = Ws + L * n;                       // [Nz][n][n] (ez, j, i): W_r
-  T* G = Wr + L * n;                        // [n][4]
-  T* SG = G + 4 * n;                        // [NZ] sigma
+  T* G = Wr + L * n;                        // [n][NG]
+  T* SG = G + NG * n;                       // [NZ] sigma
   T* BB = SG + NZ;                          // [n][NZp] b (MODE_RESIDUAL) or x (MODE_DOT) of the slab
-  size_t red_off = (((size_t)(3 * n * NZp + 2 * L * n + 4 * n + NZ) * sizeof(T)) + 15) & ~(size_t)15;
+  size_t red_off = (((size_t)(3 * n * NZp + 2 * L * n + NG * n + NZ) * sizeof(T)) + 15) & ~(size_t)15;
   double* red = reinterpret_cast<double*>(smem_raw + red_off);  // 34 doubles
   int* s_flag = reinterpret_cast<int*>(red + 34);
   T* Y = X;
@@ -135,7 +141,7 @@ __global__ void __launch_bounds__(512) k_curved(CurvedParams<T> p) {
     if (MODE == MODE_DOT) cp_async_elem(&BB[i * NZp + iz], p.x + g, ok);  // X is reused for Y
   });
   cp_async_wait_all();
-  for (int t = threadIdx.x; t < 4 * n; t += blockDim.x) G[t] = from_io<T>(p.geo[(size_t)ex * 4 * n + t]);
+  for (int t = threadIdx.x; t < NG * n; t += blockDim.x) G[t] = from_io<T>(p.geo[(size_t)ex * NG * n + t]);
   for (int t = threadIdx.x; t < NZ; t += blockDim.x) SG[t] = from_io<T>(p.sigma[t]);
   __syncthreads();
 
@@ -191,11 +197,20 @@ __global__ void __launch_bounds__(512) k_curved(CurvedParams<T> p) {
       T sg = SG[iz];
       T ur = Ur[i * NZp + iz];
       T us = Ws[t];
-      T grr = wj * G[i * 4 + 0];
-      T grs = -wj * sg * G[i * 4 + 1];
-      T gss = wj * G[i * 4 + 2] * (T(1) + sg * sg * G[i * 4 + 3]);
-      Wr[t] = grr * ur + grs * us;
-      Ws[t] = grs * ur + gss * us;
+      if constexpr (MIX) {
+        T grr = wj * G[i * 5 + 0];
+        T grs = -wj * sg * G[i * 5 + 1];
+        T gsr = -wj * sg * G[i * 5 + 2];
+        T gss = wj * G[i * 5 + 3] * (T(1) + sg * sg * G[i * 5 + 4]);
+        Wr[t] = grr * ur + grs * us;
+        Ws[t] = gsr * ur + gss * us;
+      } else {
+        T grr = wj * G[i * 4 + 0];
+        T grs = -wj * sg * G[i * 4 + 1];
+        T gss = wj * G[i * 4 + 2] * (T(1) + sg * sg * G[i * 4 + 3]);
+        Wr[t] = grr * ur + grs * us;
+        Ws[t] = grs * ur + gss * us;
+      }
     }
   } else {
     // ---- divergence load vector: W_r = w_i w_j (d dsig/2) u, W_s = w_i w_j (dx/2)(w - sigma d_x u)
@@ -338,16 +353,16 @@ __global__ void __launch_bounds__(512) k_curved(CurvedParams<T> p) {
 }
 
 template <typename T>
-static size_t curved_smem(int P, int NZ, int Nz) {
+static size_t curved_smem(int P, int NZ, int Nz, int ng = 4) {
   int n = P + 1, NZp = slab_pitch(NZ), L = Nz * n;
-  size_t e = (size_t)3 * n * NZp + (size_t)2 * L * n + 4 * n + NZ;
+  size_t e = (size_t)3 * n * NZp + (size_t)2 * L * n + (size_t)ng * n + NZ;
   return ((e * sizeof(T) + 15) & ~(size_t)15) + 34 * sizeof(double) + 16;
 }
 
-template <int P, typename T, int MODE, int TC>
+template <int P, typename T, int MODE, int TC, bool MIX = false>
 static cudaError_t launch_curved_p(const CurvedParams<T>& prm, int threads, cudaStream_t st) {
-  size_t sm = curved_smem<T>(P, prm.s.NZ, prm.s.Nz);
-  auto k = k_curved<P, T, MODE, TC>;
+  size_t sm = curved_smem<T>(P, prm.s.NZ, prm.s.Nz, MIX ? 5 : 4);
+  auto k = k_curved<P, T, MODE, TC, MIX>;
   static std::atomic<unsigned long long> s_mask{0};
   cudaError_t e = ensure_max_smem(k, s_mask);
   if (e != cudaSuccess) return e;
@@ -355,10 +370,10 @@ static cudaError_t launch_curved_p(const CurvedParams<T>& prm, int threads, cuda
   return cudaGetLastError();
 }
 
-template <typename T, int MODE, int TC>
+template <typename T, int MODE, int TC, bool MIX = false>
 static cudaError_t launch_curved(const CurvedParams<T>& prm, int threads, cudaStream_t st) {
   switch (prm.s.P) {
-#define PMG_CASE(PP) case PP: return launch_curved_p<PP, T, MODE, TC>(prm, threads, st);
+#define PMG_CASE(PP) case PP: return launch_curved_p<PP, T, MODE, TC, MIX>(prm, threads, st);
     PMG_CASE(1) PMG_CASE(2) PMG_CASE(3) PMG_CASE(4) PMG_CASE(5)
     PMG_CASE(6) PMG_CASE(7) PMG_CASE(8) PMG_CASE(9) PMG_CASE(10)
 #undef PMG_CASE

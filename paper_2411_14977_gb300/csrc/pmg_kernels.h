@@ -67,12 +67,16 @@ struct CurvedArgs {
   Scratch sc;
   int threads = 256;   // CTA size (autotuned; 64..512)
   int tc = 0;          // FP32 only: 0 CUDA cores, 1 BF16 tensor cores, 3 BF16 hi/lo split
+  int mix = 0;         // FP64 / double-float apply and residual: the mixed-stage operator
+  const void* geo5 = nullptr;  // its column factors [Nx][P+1][5] (FP64)
 };
 template <typename T> cudaError_t curved_op(const CurvedArgs& a, cudaStream_t st);
 cudaError_t curved_op_tc(const CurvedArgs& a, cudaStream_t st);
 template <typename T>
 cudaError_t geometry(const Shape& s, const double* eta, double h, double dx, double dsig, int div,
                      T* geo, int* status, cudaStream_t st);
+cudaError_t geometry_mixed(const Shape& s, const double* eta, const double* etap, double h, double dx, double dsig,
+                           double* geo, int* status, cudaStream_t st);
 cudaError_t rhs_source(const Shape& s, const double* eta, double h, double dx, double dsig,
                        const double* mX, const double* mZ, const double* f, const double* gb,
                        const double* gl, const double* gr, double* b, cudaStream_t st);

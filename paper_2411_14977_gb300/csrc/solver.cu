@@ -264,6 +264,9 @@ struct pmg_handle {
   int* status_host = nullptr;
   double* io = nullptr;  // pmg_solve_host: out, b, p_D, x0
   double* filt = nullptr;  // (P+1)^2 nodal spectral filter, set by pmg_set_filter
+  double* geo5 = nullptr;  // mixed-stage column factors [Nx][P+1][5] (pmg_set_geometry_mixed)
+  double* eta_prev = nullptr;
+  bool mixed_stage = false;  // the outer operator is the mixed-stage one
   // flexible GMRES(m): Arnoldi basis V [(m+1) N], preconditioned directions Z [m N], device
   // coefficients (two Gram-Schmidt passes and the new norm), block partials, ticket, y
   double *gm_V = nullptr, *gm_Z = nullptr, *gm_h = nullptr, *gm_part = nullptr, *gm_y = nullptr;
@@ -641,6 +644,10 @@ pmg_status curved(pmg_handle* h, int mode, const void* x, const void* b, void* y
   a.sc = h->sc;
   a.threads = PI<T> ? h->thr_curved32 : h->thr_curved64;
   if (PI<T> && (mode == 0 || mode == 2)) a.tc = tc >= 0 ? tc : h->tc;
+  if (!PI<T> && h->mixed_stage && (mode == 0 || mode == 1)) {
+    a.mix = 1;
+    a.geo5 = h->geo5;
+  }
   const Shape& F = a.s;
   double N = (double)F.NX * F.NZ, E = (double)F.Nx * F.Nz, n = F.P + 1;
   Cost c{(mode == 1 ? 3.0 : 2.0) * N * sizeof(T), E * (8.0 * n * n * n + 12.0 * n * n)};
@@ -1421,6 +1428,29 @@ pmg_status pmg_set_geometry(pmg_handle* h, const double* eta_dev, void* stream) 
   CKS(launch(h, PMG_K_SETUP, 1, st, [&] { return geometry<double>(F, h->eta, h->mesh.h, h->dx, h->dsig, 0, (double*)h->geo[0], gst, st); }));
   CKS(launch(h, PMG_K_SETUP, 1, st, [&] { return geometry<float>(F, h->eta, h->mesh.h, h->dx, h->dsig, 0, (float*)h->geo[1], gst, st); }));
   CKS(launch(h, PMG_K_SETUP, 1, st, [&] { return geometry<double>(F, h->eta, h->mesh.h, h->dx, h->dsig, 1, h->geo_div, gst, st); }));
+  h->mixed_stage = false;
+  return PMG_OK;
+}
+
+pmg_status pmg_set_geometry_mixed(pmg_handle* h, const double* eta_dev, const double* eta_prev_dev, void* stream) {
+  CKS(pmg_set_geometry(h, eta_dev, stream));
+  if (!eta_prev_dev) return fail(PMG_ERR_INVALID, "eta_prev is NULL");
+  DeviceGuard dg(h->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const Shape& F = h->lv[0].s;
+  cudaError_t e = cudaSuccess;
+  if (!h->geo5) {
+    h->geo5 = h->alloc<double>((size_t)h->mesh.cells_x * (h->mesh.order + 1) * 5, e);
+    CK(e);
+    h->eta_prev = h->alloc<double>(F.NX, e);
+    CK(e);
+  }
+  CK(cudaMemcpyAsync(h->eta_prev, eta_prev_dev, F.NX * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  int* gst = h->status + 1;
+  CKS(launch(h, PMG_K_SETUP, 1, st, [&] {
+    return geometry_mixed(F, h->eta, h->eta_prev, h->mesh.h, h->dx, h->dsig, h->geo5, gst, st);
+  }));
+  h->mixed_stage = true;
   return PMG_OK;
 }
 
@@ -1542,6 +1572,8 @@ pmg_status pmg_solve(pmg_handle* h, const double* b, const double* pD, const dou
   cudaStream_t st = (cudaStream_t)stream;
   pmg_solve_info loc{};
   size_t N = h->N;
+  if (h->mixed_stage && h->opts.outer != PMG_PDC && h->opts.outer != PMG_GMRES)
+    return fail(PMG_ERR_INVALID, "the mixed-stage operator is nonsymmetric: use outer PMG_PDC or PMG_GMRES");
   CK(cudaMemsetAsync(h->status, 0, sizeof(int), st));
   CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{8.0 * N, 0.0}, [&] { return check_finite(N, b, h->status, st); }));
   CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{24.0 * N, 0.0}, [&] { return init_x(N, h->lv[0].s.NZ, h->x, x0, pD, h->status, st); }));

@@ -63,6 +63,7 @@ _SIGNATURES = {
     "pmg_level_info": (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "pmg_node_coords": (_I, [_P, _P, _P]),
     "pmg_set_geometry": (_I, [_P, _P, _P]),
+    "pmg_set_geometry_mixed": (_I, [_P, _P, _P, _P]),
     "pmg_assemble_rhs": (_I, [_P, _P, _P, _P, _P, _P, _P]),
     "pmg_assemble_rhs_div": (_I, [_P, _P, _P, _D, _P, _P]),
     "pmg_solve": (_I, [_P, _P, _P, _P, _P, ctypes.POINTER(SolveInfo), _P]),
@@ -217,6 +218,11 @@ class Solver:
         return xc.numpy(), sr.numpy()
 
     # ---- per-stage inputs
+    def set_geometry_mixed(self, eta, eta_prev):
+        """Mixed-stage operator: test gradients on `eta` (stage k), trial gradients on
+        `eta_prev` (stage k-1); solve with outer PMG_PDC or PMG_GMRES."""
+        _check(load().pmg_set_geometry_mixed(self._h, _ptr(eta), _ptr(eta_prev), _stream()))
+
     def set_geometry(self, eta):
         _check(load().pmg_set_geometry(self._h, _ptr(eta), _stream()))
 

@@ -175,3 +175,41 @@ def test_dense_bruteforce_equals_sparse_direct(wl):
     assert relative_residual(A, b, p1, dm) < 1e-13
     y = apply_masked(A, p1, dm)
     np.testing.assert_array_equal(y[dm], p1[dm])
+
+
+def _two_surfaces(m):
+    x = m.column_x()
+    L = m.x1 - m.x0
+    eta_k = 0.08 * np.cos(2 * np.pi * x / L) + 0.02 * np.sin(6 * np.pi * x / L)
+    eta_km1 = 0.08 * np.cos(2 * np.pi * (x - 0.05) / L) + 0.03 * np.sin(6 * np.pi * x / L + 0.3)
+    return eta_k, eta_km1
+
+
+def test_mixed_stage_operator_reduces_to_same_stage():
+    m = Mesh(cells_x=4, cells_z=2, order=4, x0=0.0, x1=2.0, h=1.0)
+    eta_k, _ = _two_surfaces(m)
+    Am = m.assemble_mixed(eta_k, eta_k).toarray()
+    A = m.assemble(eta_k).toarray()
+    np.testing.assert_allclose(Am, A, rtol=0, atol=1e-12 * np.abs(A).max())
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_mixed_stage_operator_on_physical_linear_functions(periodic):
+    """A linear function of the physical coordinates has the same constant gradient on
+    both stages' meshes, so A_mix(eta_k, eta_km1) l(stage k-1 nodes) = A(eta_k) l(stage k
+    nodes) -- tying the mixed operator to the pinned same-stage one; and A_mix is not
+    symmetric when the surfaces differ."""
+    m = Mesh(cells_x=4, cells_z=3, order=5, x0=0.0, x1=2.0, h=1.0, periodic=periodic)
+    eta_k, eta_km1 = _two_surfaces(m)
+    Am = m.assemble_mixed(eta_k, eta_km1)
+    A = m.assemble(eta_k)
+    for al, be, ga in [(0.0, 0.0, 1.0), (0.0, 1.0, -0.3), (1.3, -0.7, 0.2)]:
+        if periodic and al != 0.0:
+            continue  # x is not periodic
+        Xm, Zm = m.node_xz(eta_km1)
+        Xk, Zk = m.node_xz(eta_k)
+        lm = al * Xm + be * Zm + ga
+        lk = al * Xk + be * Zk + ga
+        np.testing.assert_allclose(Am @ lm, A @ lk, rtol=0, atol=1e-11 * max(1.0, np.abs(A @ lk).max()))
+    D = (Am - Am.T).toarray()
+    assert np.abs(D).max() > 1e-6 * np.abs(Am).max()

@@ -316,7 +316,7 @@ def run_ours(args, ws, rank, local):
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
             # dram__bytes_read.sum + dram__bytes_write.sum of this kernel, one ncu capture of the
             # same build and workload (profiles/k_fdm32_p6_cfg2.md)
-            "traffic": 4.851968e6 if p0 == 6 and args.workload == "cfg2" else None,
+            "traffic": 4.863744e6 if p0 == 6 and args.workload == "cfg2" else None,
             "kernel": f"k_fdm32<{p0},1> finest-level FP32 Schwarz sweep", "avg_launch_us": us_sweep,
             "algorithmic_bytes_per_launch": bytes_sweep,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured); burst peak, kernel timed alone",

@@ -92,8 +92,8 @@ typedef struct {
   int nlevels;       /* 0 = the paper's coarsening rule; else level_orders[0..nlevels-1]    */
   int level_orders[8];
   int fuse_residual; /* sweeps (FP32) and restrictions that form their own level residual:  */
-                     /* 1 on every level, 0 never, -1 (default) where pmg_autotune measured   */
-                     /* it to be faster                                                       */
+                     /* 1 on every level, 0 (default) never, -1 where pmg_autotune measured   */
+                     /* it to be 10% faster (solve times are equal within noise at config 2) */
   int flat_kernel;   /* FP32 level operator: 0 slab CTAs (one element column each), 1 one   */
                      /* thread per node, -1 (default) slab until pmg_autotune picks by time   */
   int df64_outer;    /* outer actual-geometry operator (FP64 vectors in and out) computed in */

@@ -1219,7 +1219,7 @@ void pmg_default_opts(pmg_opts* o) {
   o->inner_max = 40;
   o->inner_tol = 1e-5;
   o->nlevels = 0;
-  o->fuse_residual = -1;
+  o->fuse_residual = 0;
   o->flat_kernel = -1;
   o->df64_outer = -1;
   o->gmres_restart = 30;

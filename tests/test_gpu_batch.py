@@ -51,9 +51,12 @@ def test_batch_matches_oracle_and_single_solves(precision):
         assert torch.allclose(o, sgl, rtol=0, atol=1e-10 * torch.max(torch.abs(sgl)).item())
 
 
-def test_autotune_keeps_results():
+@pytest.mark.parametrize("fuse", [0, -1])
+def test_autotune_keeps_results(fuse):
+    """CTA sizes, the level-operator kernel and (fuse -1) the fused level residuals picked
+    by timing leave the answer unchanged."""
     w = W.tank(16, 4, 6)
-    S = pmg.Solver(**w.mesh_kwargs(), tol=1e-11, precision=pmg.PMG_MIXED_FP32)
+    S = pmg.Solver(**w.mesh_kwargs(), tol=1e-11, precision=pmg.PMG_MIXED_FP32, fuse_residual=fuse)
     xc, sr = S.node_coords()
     F = w.fields(xc, sr)
     S.set_geometry(t(F["eta"]))

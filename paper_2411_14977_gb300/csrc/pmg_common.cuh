@@ -35,10 +35,53 @@ struct df64 {
   __host__ __device__ __forceinline__ df64(float h, float l) : hi(h), lo(l) {}
 };
 __host__ __device__ __forceinline__ df64 df64_from_double(double v) {
+#ifdef __CUDA_ARCH__
+  // Integer split of the FP64 bits (no FP64-pipe work): hi = the value truncated to 24
+  // significant bits, lo = the remaining 29 mantissa bits, exact as an integer and rounded
+  // once to 24 bits by the integer-to-float conversion.  Zero, denormals and magnitudes
+  // below 2^-126 map to 0; magnitudes above the FP32 range to +-inf.
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7FF);
+  const int fe = e - 1023 + 127;
+  if (fe <= 0) return df64(0.f, 0.f);
+  if (fe >= 255) return df64(__int_as_float((int)(sign | 0x7F800000u)), 0.f);
+  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  const float hi = __int_as_float((int)(sign | ((unsigned)fe << 23) | (unsigned)(m >> 29)));
+  const unsigned low = (unsigned)(m & 0x1FFFFFFFull);  // 29 bits, weight 2^(e - 1075)
+  const int le = e - 1075 + 127;                       // biased exponent of 2^(e - 1075)
+  float lo = 0.f;
+  if (low != 0u) {
+    const float l = __uint2float_rn(low);
+    // 2^(e-1075): one normal factor, or 2^(le+64-127) * 2^-64 when le <= 0 (fe > 0 keeps
+    // le + 64 > 0)
+    lo = le > 0 ? l * __int_as_float(le << 23) : l * __int_as_float((le + 64) << 23) * __int_as_float(63 << 23);
+  }
+  return df64(hi, sign ? -lo : lo);
+#else
   float h = (float)v;
   return df64(h, (float)(v - (double)h));
+#endif
 }
-__host__ __device__ __forceinline__ double df64_to_double(df64 a) { return (double)a.hi + (double)a.lo; }
+#ifdef __CUDA_ARCH__
+// exact FP32 -> FP64 by bit manipulation (normal and zero values)
+__device__ __forceinline__ double df64_f2d(float f) {
+  const unsigned u = (unsigned)__float_as_int(f);
+  const unsigned e = (u >> 23) & 0xFFu;
+  if (e == 0u || e == 255u) return (double)f;  // zero, denormal, inf, nan: the rare path
+  const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
+                               ((unsigned long long)(e - 127u + 1023u) << 52) |
+                               ((unsigned long long)(u & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)b);
+}
+#endif
+__host__ __device__ __forceinline__ double df64_to_double(df64 a) {
+#ifdef __CUDA_ARCH__
+  return df64_f2d(a.hi) + df64_f2d(a.lo);
+#else
+  return (double)a.hi + (double)a.lo;
+#endif
+}
 __device__ __forceinline__ df64 df64_fast_two_sum(float a, float b) {  // |a| >= |b| or a == 0
   float s = a + b;
   return df64(s, b - (s - a));
@@ -183,10 +226,10 @@ struct Acc<float> {
   __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 template <>
-struct Acc<df64> {  // inner products of double-float data, accumulated in FP64 (N terms)
-  double s = 0.0;
-  __device__ __forceinline__ void fma(df64 a, df64 b) { s = ::fma(df64_to_double(a), df64_to_double(b), s); }
-  __device__ __forceinline__ double value() const { return s; }
+struct Acc<df64> {  // inner products of double-float data, accumulated in double-float
+  df64 s{0.f, 0.f};
+  __device__ __forceinline__ void fma(df64 a, df64 b) { s = s + a * b; }
+  __device__ __forceinline__ double value() const { return df64_to_double(s); }
 };
 
 __device__ __forceinline__ double warp_sum(double v) {

@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(VEC_THREADS) k_dot(size_t n, const TA* x, cons
 // x += alpha p, r -= alpha w, (r_old = r), RR = ||r||^2;  alpha = RZ / PAP.
 template <typename T>
 __global__ void __launch_bounds__(VEC_THREADS) k_cg_update(size_t n, T* x, T* r, const T* p, const T* w,
-                                                           T* r_old, double* s, Scratch sc) {
+                                                           T* r_old, double* s, Scratch sc, float* r32) {
   __shared__ double red[34];
   __shared__ int s_flag;
   __shared__ T s_alpha;
@@ -149,6 +149,7 @@ __global__ void __launch_bounds__(VEC_THREADS) k_cg_update(size_t n, T* x, T* r,
     x[i] += a * p[i];
     ri -= a * w[i];
     r[i] = ri;
+    if (r32) r32[i] = (float)ri;  // the FP32 copy the next V-cycle reads
     ac.fma(ri, ri);
   }
   double acc = block_sum(ac.value(), red);
@@ -170,14 +171,14 @@ __global__ void __launch_bounds__(VEC_THREADS) k_cg_update(size_t n, T* x, T* r,
 }
 
 // RZ_new = <r, z> (and for flexible CG ZRO = <z, r_old>), shifting RZ -> RZOLD.
-template <typename T>
-__global__ void __launch_bounds__(VEC_THREADS) k_rz(size_t n, const T* r, const T* z, const T* r_old,
+template <typename T, typename TZ>
+__global__ void __launch_bounds__(VEC_THREADS) k_rz(size_t n, const T* r, const TZ* z, const T* r_old,
                                                     double* s, Scratch sc) {
   __shared__ double red[34];
   __shared__ int s_flag;
   Acc<T> c1, c2;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    T zi = z[i];
+    T zi = (T)z[i];  // an FP32 preconditioned residual widens exactly
     c1.fma(r[i], zi);
     if (r_old) c2.fma(r_old[i], zi);
   }
@@ -208,15 +209,15 @@ __global__ void __launch_bounds__(VEC_THREADS) k_rz(size_t n, const T* r, const 
 }
 
 // p = z + beta p with beta = RZ/RZOLD (CG) or (RZ - ZRO)/RZOLD (flexible CG); first: p = z.
-template <typename T>
-__global__ void k_p_update(size_t n, T* p, const T* z, const double* s, int flexible, int first) {
+template <typename T, typename TZ>
+__global__ void k_p_update(size_t n, T* p, const TZ* z, const double* s, int flexible, int first) {
   __shared__ T s_beta;
   if (threadIdx.x == 0)
     s_beta = first ? T(0) : (T)((flexible ? (s[SLOT_RZ] - s[SLOT_ZRO]) : s[SLOT_RZ]) / s[SLOT_RZOLD]);
   __syncthreads();
   const T b = s_beta;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    p[i] = first ? z[i] : z[i] + b * p[i];
+    p[i] = first ? (T)z[i] : (T)z[i] + b * p[i];
 }
 
 // y = (float)(x * (1/sqrt(s[slot])))  (unit-norm scaling of a residual for the FP32 solve)
@@ -306,28 +307,32 @@ template cudaError_t dot<float, float>(size_t, const float*, const float*, doubl
 
 template <typename T>
 cudaError_t cg_update(size_t n, T* x, T* r, const T* p, const T* w, T* r_old, double* s, const Scratch& sc,
-                      cudaStream_t st) {
-  k_cg_update<T><<<vec_grid(n), VEC_THREADS, 0, st>>>(n, x, r, p, w, r_old, s, sc);
+                      cudaStream_t st, float* r32) {
+  k_cg_update<T><<<vec_grid(n), VEC_THREADS, 0, st>>>(n, x, r, p, w, r_old, s, sc, r32);
   return cudaGetLastError();
 }
-template cudaError_t cg_update<double>(size_t, double*, double*, const double*, const double*, double*, double*, const Scratch&, cudaStream_t);
-template cudaError_t cg_update<float>(size_t, float*, float*, const float*, const float*, float*, double*, const Scratch&, cudaStream_t);
+template cudaError_t cg_update<double>(size_t, double*, double*, const double*, const double*, double*, double*,
+                                       const Scratch&, cudaStream_t, float*);
+template cudaError_t cg_update<float>(size_t, float*, float*, const float*, const float*, float*, double*,
+                                      const Scratch&, cudaStream_t, float*);
 
-template <typename T>
-cudaError_t rz(size_t n, const T* r, const T* z, const T* r_old, double* s, const Scratch& sc, cudaStream_t st) {
-  k_rz<T><<<vec_grid(n), VEC_THREADS, 0, st>>>(n, r, z, r_old, s, sc);
+template <typename T, typename TZ>
+cudaError_t rz(size_t n, const T* r, const TZ* z, const T* r_old, double* s, const Scratch& sc, cudaStream_t st) {
+  k_rz<T, TZ><<<vec_grid(n), VEC_THREADS, 0, st>>>(n, r, z, r_old, s, sc);
   return cudaGetLastError();
 }
-template cudaError_t rz<double>(size_t, const double*, const double*, const double*, double*, const Scratch&, cudaStream_t);
-template cudaError_t rz<float>(size_t, const float*, const float*, const float*, double*, const Scratch&, cudaStream_t);
+template cudaError_t rz<double, double>(size_t, const double*, const double*, const double*, double*, const Scratch&, cudaStream_t);
+template cudaError_t rz<double, float>(size_t, const double*, const float*, const double*, double*, const Scratch&, cudaStream_t);
+template cudaError_t rz<float, float>(size_t, const float*, const float*, const float*, double*, const Scratch&, cudaStream_t);
 
-template <typename T>
-cudaError_t p_update(size_t n, T* p, const T* z, const double* s, int flexible, int first, cudaStream_t st) {
-  k_p_update<T><<<vec_grid(n), VEC_THREADS, 0, st>>>(n, p, z, s, flexible, first);
+template <typename T, typename TZ>
+cudaError_t p_update(size_t n, T* p, const TZ* z, const double* s, int flexible, int first, cudaStream_t st) {
+  k_p_update<T, TZ><<<vec_grid(n), VEC_THREADS, 0, st>>>(n, p, z, s, flexible, first);
   return cudaGetLastError();
 }
-template cudaError_t p_update<double>(size_t, double*, const double*, const double*, int, int, cudaStream_t);
-template cudaError_t p_update<float>(size_t, float*, const float*, const double*, int, int, cudaStream_t);
+template cudaError_t p_update<double, double>(size_t, double*, const double*, const double*, int, int, cudaStream_t);
+template cudaError_t p_update<double, float>(size_t, double*, const float*, const double*, int, int, cudaStream_t);
+template cudaError_t p_update<float, float>(size_t, float*, const float*, const double*, int, int, cudaStream_t);
 
 cudaError_t to_f32_scaled(size_t n, const double* x, float* y, const double* s, int slot, cudaStream_t st) {
   k_to_f32_scaled<<<vec_grid(n), VEC_THREADS, 0, st>>>(n, x, y, s, slot);

@@ -150,11 +150,11 @@ template <typename TA, typename TB>
 cudaError_t dot(size_t n, const TA* x, const TB* y, double* out, int shift, const Scratch& sc, cudaStream_t st);
 template <typename T>
 cudaError_t cg_update(size_t n, T* x, T* r, const T* p, const T* w, T* r_old, double* s, const Scratch& sc,
-                      cudaStream_t st);
-template <typename T>
-cudaError_t rz(size_t n, const T* r, const T* z, const T* r_old, double* s, const Scratch& sc, cudaStream_t st);
-template <typename T>
-cudaError_t p_update(size_t n, T* p, const T* z, const double* s, int flexible, int first, cudaStream_t st);
+                      cudaStream_t st, float* r32 = nullptr);  // r32: also write (float)r
+template <typename T, typename TZ = T>
+cudaError_t rz(size_t n, const T* r, const TZ* z, const T* r_old, double* s, const Scratch& sc, cudaStream_t st);
+template <typename T, typename TZ = T>
+cudaError_t p_update(size_t n, T* p, const TZ* z, const double* s, int flexible, int first, cudaStream_t st);
 cudaError_t to_f32_scaled(size_t n, const double* x, float* y, const double* s, int slot, cudaStream_t st);
 cudaError_t add_f32_scaled(size_t n, double* x, const float* c, const double* s, int slot, cudaStream_t st);
 template <typename T> cudaError_t add(size_t n, T* x, const T* y, cudaStream_t st);

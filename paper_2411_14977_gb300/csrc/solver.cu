@@ -762,29 +762,40 @@ pmg_status run_loop(pmg_handle* h, pmg_handle::Loop& L, int which, cudaStream_t 
   return PMG_OK;
 }
 
-// z = B r for the FP64 Krylov loop: the FP64 V-cycle, or the FP32 V-cycle on the
-// FP32-rounded residual (mixed precision).
-pmg_status precondition64(pmg_handle* h, cudaStream_t st) {
-  size_t N = h->N;
-  if (h->opts.precision == PMG_FP64) return vcycle<double>(h, 0, h->r, h->z, st);
-  CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{12.0 * N, 0.0}, [&] { return cast_f32(N, h->r, h->r32, st); }));
-  CKS(vcycle<float>(h, 0, h->r32, h->z32, st));
-  return launch(h, PMG_K_VECTOR, 1, st, Cost{12.0 * N, 0.0}, [&] { return cast_f64(N, h->z32, h->z, st); });
-}
 
 // FP64 PCG / flexible CG iteration sequence (first: p = z instead of the beta update).
 // A mixed-precision V-cycle is not exactly linear, so it always runs as flexible CG.
+// z = B r, then <r, z> (and <r_old, z> when flexible) and p = z + beta p (p = z when
+// `first`).  Mixed precision: the FP32 V-cycle reads the FP32 copy of r that the previous
+// update wrote (made here when `first`), and its FP32 output feeds the inner products and
+// the direction update directly (exact widening), so no cast kernels run in the loop.
+pmg_status precondition_dir(pmg_handle* h, bool first, int flexible, cudaStream_t st) {
+  const size_t N = h->N;
+  double* s = h->scal + GROUP_OUTER;
+  const double* ro = (flexible && !first) ? h->rold : nullptr;
+  if (h->opts.precision == PMG_FP64) {
+    CKS(vcycle<double>(h, 0, h->r, h->z, st));
+    CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{3.0 * N * 8, 4.0 * N}, [&] { return rz<double>(N, h->r, h->z, ro, s, h->sc, st); }));
+    return launch(h, PMG_K_VECTOR, 1, st, Cost{3.0 * N * 8, 2.0 * N}, [&] { return p_update<double>(N, h->p, h->z, s, flexible, first ? 1 : 0, st); });
+  }
+  if (first) CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{12.0 * N, 0.0}, [&] { return cast_f32(N, h->r, h->r32, st); }));
+  CKS(vcycle<float>(h, 0, h->r32, h->z32, st));
+  CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{3.0 * N * 8 - 4.0 * N, 4.0 * N}, [&] { return rz<double, float>(N, h->r, h->z32, ro, s, h->sc, st); }));
+  return launch(h, PMG_K_VECTOR, 1, st, Cost{3.0 * N * 8 - 4.0 * N, 2.0 * N}, [&] { return p_update<double, float>(N, h->p, h->z32, s, flexible, first ? 1 : 0, st); });
+}
+
 pmg_status cg64_step(pmg_handle* h, bool first, cudaStream_t st, cudaGraphConditionalHandle hc) {
   size_t N = h->N;
   double* s = h->scal + GROUP_OUTER;
   int flexible = h->opts.outer == PMG_FCG || h->opts.precision != PMG_FP64;
   if (first) CK(cudaMemsetAsync(h->d_iter, 0, sizeof(int), st));
-  CKS(precondition64(h, st));
-  const double* ro = (flexible && !first) ? h->rold : nullptr;
-  CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{3.0 * N * 8, 4.0 * N}, [&] { return rz<double>(N, h->r, h->z, ro, s, h->sc, st); }));
-  CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{3.0 * N * 8, 2.0 * N}, [&] { return p_update<double>(N, h->p, h->z, s, flexible, first ? 1 : 0, st); }));
+  const bool mixed = h->opts.precision != PMG_FP64;
+  CKS(precondition_dir(h, first, flexible, st));
   CKS(curved<double>(h, 2, h->p, nullptr, h->w, 1, s + SLOT_PAP, st));
-  CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{7.0 * N * 8, 6.0 * N}, [&] { return cg_update<double>(N, h->x, h->r, h->p, h->w, flexible ? h->rold : nullptr, s, h->sc, st); }));
+  CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{7.0 * N * 8 + (mixed ? 4.0 * N : 0.0), 6.0 * N}, [&] {
+    return cg_update<double>(N, h->x, h->r, h->p, h->w, flexible ? h->rold : nullptr, s, h->sc, st,
+                             mixed ? h->r32 : nullptr);
+  }));
   const double tol2 = h->opts.tol * h->opts.tol;
   return launch(h, PMG_K_VECTOR, 1, st, [&] { return loop_cond(hc, s, h->scal + SLOT_BB, tol2, h->d_iter, h->opts.max_iter, st); });
 }
@@ -876,14 +887,16 @@ pmg_status solve_krylov64(pmg_handle* h, const double* b, pmg_solve_info* info, 
     return PMG_OK;
   }
   while (it < h->opts.max_iter) {
+    const bool mixed = h->opts.precision != PMG_FP64;
     if (restart) {
-      CKS(precondition64(h, st));
-      CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{3.0 * N * 8, 4.0 * N}, [&] { return rz<double>(N, h->r, h->z, nullptr, s, h->sc, st); }));
-      CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{3.0 * N * 8, 2.0 * N}, [&] { return p_update<double>(N, h->p, h->z, s, 0, 1, st); }));
+      CKS(precondition_dir(h, true, flexible, st));
       restart = false;
     }
     CKS(curved<double>(h, 2, h->p, nullptr, h->w, 1, s + SLOT_PAP, st));
-    CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{7.0 * N * 8, 6.0 * N}, [&] { return cg_update<double>(N, h->x, h->r, h->p, h->w, flexible ? h->rold : nullptr, s, h->sc, st); }));
+    CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{7.0 * N * 8 + (mixed ? 4.0 * N : 0.0), 6.0 * N}, [&] {
+      return cg_update<double>(N, h->x, h->r, h->p, h->w, flexible ? h->rold : nullptr, s, h->sc, st,
+                               mixed ? h->r32 : nullptr);
+    }));
     ++it;
     CKS(read_scalars(h, st));
     double rr = h->scal_host[GROUP_OUTER + SLOT_RR];
@@ -896,9 +909,7 @@ pmg_status solve_krylov64(pmg_handle* h, const double* b, pmg_solve_info* info, 
       restart = true;
       continue;
     }
-    CKS(precondition64(h, st));
-    CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{3.0 * N * 8, 4.0 * N}, [&] { return rz<double>(N, h->r, h->z, flexible ? h->rold : nullptr, s, h->sc, st); }));
-    CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{3.0 * N * 8, 2.0 * N}, [&] { return p_update<double>(N, h->p, h->z, s, flexible, 0, st); }));
+    CKS(precondition_dir(h, false, flexible, st));
   }
   if (info) info->iterations = it;
   return PMG_OK;

@@ -706,7 +706,7 @@ def run_variants(args, ws, rank, local):
             x32 = torch.randn(S.n, dtype=torch.float32, device=dev)
             x64 = x32.double()
             kern = {}
-            for kname, fn in [("fp64_cuda_cores", lambda: S.apply(x64)),
+            for kname, fn in [("outer_fp64_vectors_double_float", lambda: S.apply(x64)),
                               ("fp32_cuda_cores", lambda: S.apply_f32(x32)),
                               ("bf16_tensor_split", lambda: S.apply_bf16(x32, split=True)),
                               ("bf16_tensor_plain", lambda: S.apply_bf16(x32, split=False))]:

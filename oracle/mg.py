@@ -8,6 +8,9 @@ Paper passages followed (Sec. 5):
   * each level re-discretised on the same cells ("geometric" p-MG), either on
     the actual geometry or on the flat, linearised geometry eta = 0 that makes
     the preconditioner time-constant                                        (Sec. 5, Sec. 5.4)
+    (with a varying still-water depth h(x) the flat level operator keeps each node
+    column's depth, evaluated at the level's nodes, and drops the bottom-slope terms:
+    `Mesh.element_stiffness_separable`)
   * prolongation = interpolation of the coarse polynomial at the fine nodes,
     I = Phi V^{-1} per element; restriction R = P^T                        (Sec. 5.2)
   * additive Schwarz smoother  x <- x - S^{-1}(A x - b),
@@ -100,11 +103,18 @@ class Hierarchy:
         eta = np.asarray(eta, float)
         for l, p in enumerate(self.orders):
             ml = Mesh(mesh.Nx, mesh.Nz, p, mesh.x0, mesh.x1, mesh.h, mesh.periodic)
+            if mesh.variable_depth:
+                probe = ml
+                h_l = self._eta_at_level(mesh, mesh.hcol, probe)
+                ml = Mesh(mesh.Nx, mesh.Nz, p, mesh.x0, mesh.x1, mesh.h, mesh.periodic, depth=h_l)
             if geometry == 'flat':
-                eta_l = np.zeros(ml.NX)
+                if mesh.variable_depth:
+                    A_l = ml.assemble_separable(ml.hcol)
+                else:
+                    A_l = ml.assemble(np.zeros(ml.NX))
             else:
-                eta_l = self._eta_at_level(mesh, eta, ml)
-            lev = Level(ml, ml.assemble(eta_l), min(overlap, (p - 1) // 2))
+                A_l = ml.assemble(self._eta_at_level(mesh, eta, ml))
+            lev = Level(ml, A_l, min(overlap, (p - 1) // 2))
             if l < len(self.orders) - 1:
                 lev.build_schwarz()
             self.levels.append(lev)

@@ -7,8 +7,9 @@ find p_h in V_P, p_h = p_D on the free surface (Sec. 3.2, p_D = 0 condition), wi
     a(N_i, p_h) = l(N_i)  for every free node i,
     a(v, p) = int_Omega grad v . grad p dOmega                                (Sec. 4.2)
     l(v)    = -int_Omega v f dOmega + int_{Gamma_N} v g dGamma                 (Neumann, Sec. 3.2)
-pulled back to the sigma-domain by the vertical map sigma = (z + h)/d, d = eta + h
-(Sec. 2.2), on a structured mesh of N_x x N_z quads (Sec. 4.3) with LGL nodes.
+pulled back to the sigma-domain by the vertical map sigma = (z + h(x))/d, d = eta + h(x)
+(Sec. 2.2, Eq. sigtrans: h(x) is the still-water depth, constant unless a per-column
+depth is given), on a structured mesh of N_x x N_z quads (Sec. 4.3) with LGL nodes.
 
 Node numbering (shared by the CUDA path's ABI, defined there independently):
     g = ix * NZ + iz,  ix in [0, NX), iz in [0, NZ),  NZ = N_z P + 1,
@@ -23,7 +24,10 @@ coordinates (x*, z = sigma d(x) - h) (Sec. 4.3, D_x = R_x D_r).
 Pins (tests/test_oracle_operator.py): flat element factors equal |J| D^T M D with the
 exact mass of Sec. 4.3; exactness of a(N_i, l) for physical linear l against boundary
 fluxes on a curved mesh; symmetry; SPD of A_FF; pure-Neumann A 1 = 0; spectral
-convergence to harmonic closed forms; brute-force dense solves.
+convergence to harmonic closed forms; brute-force dense solves; with a varying depth
+(tests/test_oracle_bathymetry.py) the same identities with the bottom-slope fluxes, the
+reduction to the constant-depth mesh, and the separable level operator of
+`assemble_separable` against its Kronecker-sum form.
 """
 import numpy as np
 import scipy.sparse as sp
@@ -35,7 +39,10 @@ from . import basis
 class Mesh:
     """Structured sigma-domain mesh: [x0, x1] x [0, 1] split into cells_x x cells_z quads."""
 
-    def __init__(self, cells_x, cells_z, order, x0=0.0, x1=1.0, h=1.0, periodic=False):
+    def __init__(self, cells_x, cells_z, order, x0=0.0, x1=1.0, h=1.0, periodic=False, depth=None):
+        """h: constant still-water depth; depth: optional still-water depth h(x) per node
+        column (array of NX values, or a function of x evaluated at the node columns),
+        which then replaces h everywhere."""
         if cells_x < 1 or cells_z < 1 or order < 1:
             raise ValueError("bad mesh")
         self.Nx, self.Nz, self.P = int(cells_x), int(cells_z), int(order)
@@ -60,6 +67,16 @@ class Mesh:
         self.e2g = (ix * self.NZ + iz).reshape(self.Nx * self.Nz, n * n)
         self.ecol = np.repeat(np.arange(self.Nx), self.Nz)
         self.erow = np.tile(np.arange(self.Nz), self.Nx)
+        self.variable_depth = depth is not None
+        if depth is None:
+            self.hcol = np.full(self.NX, self.h)
+        else:
+            hc = depth(self.column_x()) if callable(depth) else depth
+            self.hcol = np.array(hc, dtype=float).reshape(-1)
+            if self.hcol.size != self.NX:
+                raise ValueError("depth needs one value per node column")
+        if not np.all(self.hcol > 0.0):
+            raise ValueError("still-water depth must be positive")
 
     # --- node coordinates -------------------------------------------------------
     def column_x(self):
@@ -80,9 +97,9 @@ class Mesh:
         """Physical (x, z) of every global node for surface elevation eta (per column)."""
         x = self.column_x()
         s = self.row_sigma()
-        d = np.asarray(eta, float) + self.h
+        d = np.asarray(eta, float) + self.hcol
         X = np.repeat(x, self.NZ)
-        Z = (s[None, :] * d[:, None] - self.h).reshape(-1)
+        Z = (s[None, :] * d[:, None] - self.hcol[:, None]).reshape(-1)
         return X, Z
 
     def dirichlet_mask(self):
@@ -93,7 +110,7 @@ class Mesh:
     # --- element geometry (isoparametric) ---------------------------------------
     def element_coords(self, eta):
         """Nodal (x, z) per element, shape (E, n, n): x* from the element's own cell,
-        z = sigma d(x) - h with d = eta + h sampled at the element's surface nodes."""
+        z = sigma d(x) - h(x) with d = eta + h sampled at the element's node columns."""
         P, n = self.P, self.P + 1
         eta = np.asarray(eta, float)
         xe = self.x0 + (self.ecol[:, None] + (self.r[None, :] + 1.0) / 2.0) * self.dx  # (E, n)
@@ -101,9 +118,10 @@ class Mesh:
         cols = self.ecol[:, None] * P + np.arange(n)[None, :]
         if self.periodic:
             cols = cols % self.NX
-        d = eta[cols] + self.h                                                            # (E, n)
+        hc = self.hcol[cols]                                                              # (E, n)
+        d = eta[cols] + hc
         X = np.repeat(xe[:, :, None], n, axis=2)
-        Z = sig[:, None, :] * d[:, :, None] - self.h
+        Z = sig[:, None, :] * d[:, :, None] - hc[:, :, None]
         return X, Z
 
     def element_metrics(self, eta):
@@ -196,6 +214,39 @@ class Mesh:
             rows = np.repeat(g[:, :, None], g.shape[1], axis=2).reshape(-1)
             cols = np.repeat(g[:, None, :], g.shape[1], axis=1).reshape(-1)
             A = A + sp.coo_matrix((K.reshape(-1), (rows, cols)), shape=(self.N, self.N)).tocsr()
+        A.sum_duplicates()
+        return A
+
+    def element_stiffness_separable(self, depth, elems=None):
+        """Element matrices of the still-water (eta = 0) operator with the bottom-slope
+        terms dropped: each node column keeps its own depth d_i = depth[column], the
+        metric loses its cross term, so
+            G_rr = w_i w_j d_i dsig/dx,  G_rs = 0,  G_ss = w_i w_j (dx/dsig) / d_i,
+            K_e = Dr^T diag(G_rr) Dr + Ds^T diag(G_ss) Ds.
+        With a constant depth this is the flat operator exactly (the sigma-map of a flat
+        bottom has no cross term); with a varying depth it is the time-constant level
+        operator of the p-multigrid preconditioner (a reading: the slope terms are what
+        would make it non-separable)."""
+        depth = np.asarray(depth, float)
+        P, n = self.P, self.P + 1
+        el = np.arange(self.Nx * self.Nz) if elems is None else np.asarray(elems)
+        cols = self.ecol[el][:, None] * P + np.arange(n)[None, :]
+        if self.periodic:
+            cols = cols % self.NX
+        dcol = depth[cols]                                                     # (E, n): d_i
+        W = self.quad_weights().reshape(n, n)                                  # w_i w_j
+        grr = (W[None] * dcol[:, :, None] * (self.dsig / self.dx)).reshape(len(el), n * n)
+        gss = (W[None] / dcol[:, :, None] * (self.dx / self.dsig)).reshape(len(el), n * n)
+        Gr, Gs = self.ref_gradients()
+        return (np.einsum('qa,eq,qb->eab', Gr, grr, Gr) + np.einsum('qa,eq,qb->eab', Gs, gss, Gs))
+
+    def assemble_separable(self, depth):
+        """Global sum of `element_stiffness_separable` (CSR)."""
+        K = self.element_stiffness_separable(depth)
+        g = self.e2g
+        rows = np.repeat(g[:, :, None], g.shape[1], axis=2).reshape(-1)
+        cols = np.repeat(g[:, None, :], g.shape[1], axis=1).reshape(-1)
+        A = sp.coo_matrix((K.reshape(-1), (rows, cols)), shape=(self.N, self.N)).tocsr()
         A.sum_duplicates()
         return A
 

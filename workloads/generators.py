@@ -120,6 +120,32 @@ class Harmonic:
         return px, pz
 
 
+@dataclass
+class Bar:
+    """Still-water depth of a submerged bar: depth h0 off the bar, hc over its crest, the
+    crest between x_a and x_b, smooth tanh ramps of widths w_a (up-slope) and w_b
+    (down-slope):  h(x) = h0 - (h0 - hc) (tanh((x - x_a)/w_a) - tanh((x - x_b)/w_b)) / 2.
+    A synthetic stand-in with the features of a bar experiment (shoaling up-slope, shallow
+    crest, steeper down-slope); with its derivative for Neumann data."""
+    h0: float
+    hc: float
+    x_a: float
+    x_b: float
+    w_a: float
+    w_b: float
+
+    def __call__(self, x):
+        x = np.asarray(x, float)
+        s = 0.5 * (np.tanh((x - self.x_a) / self.w_a) - np.tanh((x - self.x_b) / self.w_b))
+        return self.h0 - (self.h0 - self.hc) * s
+
+    def slope(self, x):
+        x = np.asarray(x, float)
+        ds = 0.5 * (1.0 / (self.w_a * np.cosh((x - self.x_a) / self.w_a) ** 2)
+                    - 1.0 / (self.w_b * np.cosh((x - self.x_b) / self.w_b) ** 2))
+        return -(self.h0 - self.hc) * ds
+
+
 # ---------------------------------------------------------------------------------
 # Workloads
 # ---------------------------------------------------------------------------------
@@ -139,10 +165,16 @@ class Workload:
     velocity: Velocity = None
     pressure: Harmonic = None
     noise_sd: float = 0.0
+    bathymetry: Bar = None            # still-water depth h(x); None: the constant h
 
     def mesh_kwargs(self):
         return dict(cells_x=self.cells_x, cells_z=self.cells_z, order=self.order,
                     x0=self.x0, x1=self.x1, h=self.h, periodic=self.periodic)
+
+    def depth(self, x_cols):
+        """Still-water depth at the node columns."""
+        x_cols = np.asarray(x_cols, float)
+        return self.bathymetry(x_cols) if self.bathymetry is not None else np.full(x_cols.size, self.h)
 
     def fields(self, x_cols, sig_rows):
         """Input arrays at the nodes given by their column x* and row sigma.
@@ -153,10 +185,11 @@ class Workload:
         x_cols, sig_rows = np.asarray(x_cols, float), np.asarray(sig_rows, float)
         NX, NZ = x_cols.size, sig_rows.size
         eta = self.surface(x_cols)
-        d = eta + self.h
+        hc = self.depth(x_cols)
+        d = eta + hc
         X = np.repeat(x_cols, NZ)
-        Z = (sig_rows[None, :] * d[:, None] - self.h).reshape(-1)
-        out = dict(eta=eta, X=X, Z=Z)
+        Z = (sig_rows[None, :] * d[:, None] - hc[:, None]).reshape(-1)
+        out = dict(eta=eta, X=X, Z=Z, h=hc)
         top = np.arange(NX) * NZ + NZ - 1
         pD = np.zeros(NX * NZ)
         if self.rhs == 'div':
@@ -170,11 +203,15 @@ class Workload:
         gb, gl, gr = np.zeros(NX), np.zeros(NZ), np.zeros(NZ)
         if self.pressure is not None:
             pD[top] = self.pressure(x_cols, eta)
-            px, pz = self.pressure.grad(x_cols, -self.h * np.ones(NX))
-            gb = -pz                                                  # n = (0, -1)
-            zl = sig_rows * (eta[0] + self.h) - self.h
+            px, pz = self.pressure.grad(x_cols, -hc)
+            if self.bathymetry is None:
+                gb = -pz                                              # n = (0, -1)
+            else:                                                     # n = -(h_x, 1)/|.|
+                hx = self.bathymetry.slope(x_cols)
+                gb = -(hx * px + pz) / np.sqrt(1.0 + hx * hx)
+            zl = sig_rows * (eta[0] + hc[0]) - hc[0]
             gl = -self.pressure.grad(np.full(NZ, self.x0), zl)[0]      # n = (-1, 0)
-            zr = sig_rows * (eta[-1] + self.h) - self.h
+            zr = sig_rows * (eta[-1] + hc[-1]) - hc[-1]
             gr = self.pressure.grad(np.full(NZ, self.x1), zr)[0]       # n = (+1, 0)
         out.update(pD=pD, g_bottom=gb, g_left=gl, g_right=gr)
         return out
@@ -254,6 +291,26 @@ def paper_scaling(cells_x, order, ppw=48.0):
     s = Surface(0.5 * 0.0301 * 2 * np.pi, k)
     return Workload(f'paper_scaling_p{order}_{cells_x}x2', cells_x, 2, order, 0.0, L, 1.0, False,
                     BASE_SEED + 6, s, 'div', velocity=Velocity.random(BASE_SEED + 9))
+
+
+def bar(cells_x=100, cells_z=2, order=8, rhs='div'):
+    """Wave tank over a submerged bar (the shape of the paper's bar experiment, Sec. 6:
+    P = 8, N_x = 100, N_z = 2 there): depth 0.4 (kh = 0.67 at the paper's wavelength
+    3.74), a synthetic smooth bar (crest depth 0.1, up-slope ramp width 2, down-slope
+    ramp width 1, crest from x = 12 to 20) on [0, 36], waves of height 0.02 and length
+    3.74.  rhs='div': weak divergence of a random velocity field; 'source': manufactured
+    harmonic pressure with its exact Neumann data on the sloped bottom and the walls."""
+    L = 36.0
+    h0 = 0.4
+    bathy = Bar(h0, 0.1, 12.0, 20.0, 2.0, 1.0)
+    s = Surface(0.01, 2 * np.pi / 3.74)
+    seed = BASE_SEED + 10
+    name = f'bar_p{order}_{cells_x}x{cells_z}'
+    if rhs == 'div':
+        return Workload(name, cells_x, cells_z, order, 0.0, L, h0, False, seed, s, 'div',
+                        velocity=Velocity.random(seed + 3), bathymetry=bathy)
+    return Workload(name, cells_x, cells_z, order, 0.0, L, h0, False, seed, s, 'source',
+                    pressure=Harmonic(2 * np.pi / 3.74, 0.0, h0), bathymetry=bathy)
 
 
 def by_name(name):

@@ -145,6 +145,22 @@ pmg_status pmg_set_geometry(pmg_handle* h, const double* eta_dev, void* stream);
  * pmg_set_geometry returns to the same-stage operator. */
 pmg_status pmg_set_geometry_mixed(pmg_handle* h, const double* eta_dev, const double* eta_prev_dev, void* stream);
 
+/* Varying still-water depth h(x) (Sec. 2.2, the sigma map sigma = (z + h(x)) / d with
+ * d = eta + h(x); Sec. 6 runs over a submerged bar): h_dev holds the depth at every node
+ * column (NX doubles, device, each > 0 and finite; the bottom is the degree-P interpolant
+ * per cell).  It replaces the mesh's constant h for every later operator, load vector and
+ * solve: the outer operator gains the bottom-slope metric terms, the bottom Neumann term
+ * uses the arc length of the mapped bottom, and every multigrid level becomes the
+ * still-water operator with the slope terms dropped -- each node column keeps its depth,
+ * evaluated at the level's nodes -- which is still a Kronecker sum, so the Schwarz blocks
+ * (now one x-factorisation per element column) and the coarse solve stay exact.  The
+ * geometry set last is recomputed.  Synchronous on `stream` (tables are built on the host).
+ * PMG_ERR_INVALID: NULL, a depth <= 0 or non-finite (also after interpolation to a coarse
+ * level), the BF16 tensor-core operator (PMG_MIXED_BF16), a periodic mesh of one cell.
+ * Afterwards pmg_set_geometry_mixed and pmg_gradient return PMG_ERR_INVALID (they take a
+ * constant depth only); there is no way back to a constant depth but a new handle. */
+pmg_status pmg_set_bathymetry(pmg_handle* h, const double* h_dev, void* stream);
+
 /* b_i = -int N_i f dOmega + int_{Gamma_N} N_i g dGamma (LGL collocation), b = 0 on the
  * free surface.  f: nodal values (n); g_bottom: outward normal derivative on the bottom
  * per node column (NX); g_left / g_right: on the walls per node row (NZ).  Any g may be

@@ -25,20 +25,38 @@ PMG_DEFINE_CONST_TABLES(init_consts_apply)
 
 namespace pmg {
 
+// Per (element column, local column i): total depth d = eta + h and the slopes d_x, h_x of
+// the element's interpolants (x-derivative (2/dx) D of the nodal values); hcol == NULL:
+// constant depth h, h_x = 0.
+template <int P>
+__device__ __forceinline__ bool column_depth(const Shape& s, const double* eta, double h, const double* hcol,
+                                             double dx, int ex, int i, double& d, double& dd, double& hx) {
+  constexpr int n = P + 1;
+  dd = 0.0;
+  hx = 0.0;
+#pragma unroll
+  for (int m = 0; m < n; ++m) {
+    int c = wrap_col(s, ex * P + m);
+    dd += cT.D[P][i][m] * eta[c];
+    if (hcol) hx += cT.D[P][i][m] * hcol[c];
+  }
+  hx *= 2.0 / dx;
+  dd = dd * (2.0 / dx) + hx;  // d_x = eta_x + h_x
+  int c = wrap_col(s, ex * P + i);
+  d = eta[c] + (hcol ? hcol[c] : h);
+  return d > 0.0 && isfinite(dd) && isfinite(hx);
+}
+
 template <int P, typename T>
-__global__ void k_geometry(Shape s, const double* eta, double h, double dx, double dsig, int div,
+__global__ void k_geometry(Shape s, const double* eta, double h, const double* hcol, double dx, double dsig, int div,
                            T* geo, int* status) {
   // one thread per (element column, local column i)
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   constexpr int n = P + 1;
   if (t >= s.Nx * n) return;
   int ex = t / n, i = t % n;
-  double dd = 0.0;
-#pragma unroll
-  for (int m = 0; m < n; ++m) dd += cT.D[P][i][m] * eta[wrap_col(s, ex * P + m)];
-  dd *= 2.0 / dx;
-  double d = eta[wrap_col(s, ex * P + i)] + h;
-  if (!(d > 0.0) || !isfinite(dd)) atomicExch(status, 1);
+  double d, dd, hx;
+  if (!column_depth<P>(s, eta, h, hcol, dx, ex, i, d, dd, hx)) atomicExch(status, 1);
   double w = cT.w[P][i];
   T* g = geo + (size_t)t * 4;
   if (!div) {
@@ -50,8 +68,31 @@ __global__ void k_geometry(Shape s, const double* eta, double h, double dx, doub
     g[0] = (T)(w * d * dsig / 2.0);
     g[1] = (T)(w * dd);
     g[2] = (T)(w * dx / 2.0);
-    g[3] = (T)0;
+    g[3] = (T)(w * hx);
   }
+}
+
+// Over a varying still-water depth the sigma map z = sigma d(x) - h(x) gives the metric
+//   G_rr = w_i w_j d dsig/dx,  G_rs = w_i w_j (h_x - sigma d_x),
+//   G_ss = w_i w_j (dx/dsig) (1 + (h_x - sigma d_x)^2) / d        (Sec. 2.2)
+// stored as six column factors [w d dsig/dx, w d_x, w (dx/dsig)/d, d_x, w h_x, h_x].
+template <int P, typename T>
+__global__ void k_geometry_bathy(Shape s, const double* eta, const double* hcol, double dx, double dsig, T* geo,
+                                 int* status) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  constexpr int n = P + 1;
+  if (t >= s.Nx * n) return;
+  int ex = t / n, i = t % n;
+  double d, dd, hx;
+  if (!column_depth<P>(s, eta, 0.0, hcol, dx, ex, i, d, dd, hx)) atomicExch(status, 1);
+  double w = cT.w[P][i];
+  T* g = geo + (size_t)t * 6;
+  g[0] = (T)(w * d * dsig / dx);
+  g[1] = (T)(w * dd);
+  g[2] = (T)(w * (dx / dsig) / d);
+  g[3] = (T)dd;
+  g[4] = (T)(w * hx);
+  g[5] = (T)hx;
 }
 
 // Column factors of the mixed-stage operator (stage k surface eta, stage k-1 surface etap):
@@ -98,18 +139,19 @@ cudaError_t geometry_mixed(const Shape& s, const double* eta, const double* etap
 }
 
 // b = -w_i w_j J f + edge terms; J = (dx/2)(dsig/2) d summed over the elements of a node
-// equals d (dx dsig / 4) mX mZ with mX, mZ the assembled LGL weights.
-__global__ void k_rhs_source(Shape s, const double* eta, double h, double dx, double dsig,
-                             const double* mX, const double* mZ, const double* f, const double* gb,
-                             const double* gl, const double* gr, double* b) {
+// equals d (dx dsig / 4) mX mZ with mX, mZ the assembled LGL weights.  The bottom edge
+// term uses the arc length of the mapped bottom (mb), the walls d dsig / 2.
+__global__ void k_rhs_source(Shape s, const double* eta, double h, const double* hcol, double dx, double dsig,
+                             const double* mX, const double* mZ, const double* mb, const double* f,
+                             const double* gb, const double* gl, const double* gr, double* b) {
   size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   size_t N = (size_t)s.NX * s.NZ;
   if (g >= N) return;
   int ix = (int)(g / s.NZ), iz = (int)(g % s.NZ);
   if (iz == s.NZ - 1) { b[g] = 0.0; return; }
-  double d = eta[ix] + h;
+  double d = eta[ix] + (hcol ? hcol[ix] : h);
   double v = -f[g] * d * (dx * dsig * 0.25) * mX[ix] * mZ[iz];
-  if (iz == 0 && gb) v += mX[ix] * (dx * 0.5) * gb[ix];
+  if (iz == 0 && gb) v += (mb ? mb[ix] : mX[ix] * (dx * 0.5)) * gb[ix];
   if (!s.periodic) {
     if (ix == 0 && gl) v += mZ[iz] * (dsig * 0.5) * d * gl[iz];
     if (ix == s.NX - 1 && gr) v += mZ[iz] * (dsig * 0.5) * d * gr[iz];
@@ -134,8 +176,13 @@ cudaError_t curved_op(const CurvedArgs& a, cudaStream_t st) {
   p.sc = a.sc;
   int thr = (a.threads >= 32 && a.threads <= 512) ? a.threads : 256;
   if (a.tc) {
-    if (!std::is_same<T, float>::value || (a.mode != MODE_APPLY && a.mode != MODE_DOT)) return cudaErrorInvalidValue;
+    if (!std::is_same<T, float>::value || (a.mode != MODE_APPLY && a.mode != MODE_DOT) || a.bathy)
+      return cudaErrorInvalidValue;
     return curved_op_tc(a, st);
+  }
+  if (a.bathy) {
+    if (a.mix || a.mode == MODE_DIV) return cudaErrorInvalidValue;
+    return curved_op_bathy<T>(a, st);
   }
   if (a.mix) {
     if constexpr (std::is_same<T, float>::value) {
@@ -162,11 +209,12 @@ template cudaError_t curved_op<float>(const CurvedArgs&, cudaStream_t);
 template cudaError_t curved_op<df64>(const CurvedArgs&, cudaStream_t);
 
 template <typename T>
-cudaError_t geometry(const Shape& s, const double* eta, double h, double dx, double dsig, int div,
-                     T* geo, int* status, cudaStream_t st) {
+cudaError_t geometry(const Shape& s, const double* eta, double h, const double* hcol, double dx, double dsig,
+                     int div, T* geo, int* status, cudaStream_t st) {
+  if (hcol && !div) return cudaErrorInvalidValue;  // the operator over a varying depth takes six factors
   int n = s.P + 1, tot = s.Nx * n, bs = 128, nb = (tot + bs - 1) / bs;
   switch (s.P) {
-#define PMG_CASE(PP) case PP: k_geometry<PP, T><<<nb, bs, 0, st>>>(s, eta, h, dx, dsig, div, geo, status); break;
+#define PMG_CASE(PP) case PP: k_geometry<PP, T><<<nb, bs, 0, st>>>(s, eta, h, hcol, dx, dsig, div, geo, status); break;
     PMG_CASE(1) PMG_CASE(2) PMG_CASE(3) PMG_CASE(4) PMG_CASE(5)
     PMG_CASE(6) PMG_CASE(7) PMG_CASE(8) PMG_CASE(9) PMG_CASE(10)
 #undef PMG_CASE
@@ -174,15 +222,36 @@ cudaError_t geometry(const Shape& s, const double* eta, double h, double dx, dou
   }
   return cudaGetLastError();
 }
-template cudaError_t geometry<double>(const Shape&, const double*, double, double, double, int, double*, int*, cudaStream_t);
-template cudaError_t geometry<float>(const Shape&, const double*, double, double, double, int, float*, int*, cudaStream_t);
+template cudaError_t geometry<double>(const Shape&, const double*, double, const double*, double, double, int, double*,
+                                      int*, cudaStream_t);
+template cudaError_t geometry<float>(const Shape&, const double*, double, const double*, double, double, int, float*,
+                                     int*, cudaStream_t);
 
-cudaError_t rhs_source(const Shape& s, const double* eta, double h, double dx, double dsig,
-                       const double* mX, const double* mZ, const double* f, const double* gb,
+template <typename T>
+cudaError_t geometry_bathy(const Shape& s, const double* eta, const double* hcol, double dx, double dsig,
+                           T* geo, int* status, cudaStream_t st) {
+  if (!hcol) return cudaErrorInvalidValue;
+  int n = s.P + 1, tot = s.Nx * n, bs = 128, nb = (tot + bs - 1) / bs;
+  switch (s.P) {
+#define PMG_CASE(PP) case PP: k_geometry_bathy<PP, T><<<nb, bs, 0, st>>>(s, eta, hcol, dx, dsig, geo, status); break;
+    PMG_CASE(1) PMG_CASE(2) PMG_CASE(3) PMG_CASE(4) PMG_CASE(5)
+    PMG_CASE(6) PMG_CASE(7) PMG_CASE(8) PMG_CASE(9) PMG_CASE(10)
+#undef PMG_CASE
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+template cudaError_t geometry_bathy<double>(const Shape&, const double*, const double*, double, double, double*, int*,
+                                            cudaStream_t);
+template cudaError_t geometry_bathy<float>(const Shape&, const double*, const double*, double, double, float*, int*,
+                                           cudaStream_t);
+
+cudaError_t rhs_source(const Shape& s, const double* eta, double h, const double* hcol, double dx, double dsig,
+                       const double* mX, const double* mZ, const double* mb, const double* f, const double* gb,
                        const double* gl, const double* gr, double* b, cudaStream_t st) {
   size_t N = (size_t)s.NX * s.NZ;
   int bs = 256;
-  k_rhs_source<<<(unsigned)((N + bs - 1) / bs), bs, 0, st>>>(s, eta, h, dx, dsig, mX, mZ, f, gb, gl, gr, b);
+  k_rhs_source<<<(unsigned)((N + bs - 1) / bs), bs, 0, st>>>(s, eta, h, hcol, dx, dsig, mX, mZ, mb, f, gb, gl, gr, b);
   return cudaGetLastError();
 }
 

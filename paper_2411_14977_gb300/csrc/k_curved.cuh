@@ -26,7 +26,7 @@ struct CurvedParams {
   const IO* x2;      // MODE_DIV: w
   const IO* b;       // MODE_RESIDUAL: load vector
   IO* y;             // output
-  const IO* geo;     // [Nx][P+1][4]: A, B, C, E
+  const IO* geo;     // [Nx][P+1][NG]: the column factors (4 constant depth, 5 mixed-stage, 6 varying depth)
   const IO* sigma;   // [NZ]
   T scale;           // MODE_DIV: scale
   int mask_input;    // 1: surface-row input read as zero
@@ -107,11 +107,15 @@ __device__ __forceinline__ void tc_contract(TcKind kind, int ntiles, GetB getb, 
 // five column factors per node column (k_geometry_mixed): A = w d_k dsig/dx,
 // B1 = w d_x(k-1) d_k / d_(k-1), B2 = w d_x(k), C = w (dx/dsig) / d_(k-1), E = d_x(k) d_x(k-1):
 //   W_r = w_j (A U_r - sigma B1 U_s),  W_s = w_j (-sigma B2 U_r + C (1 + sigma^2 E) U_s).
-template <int P, typename T, int MODE, int TC, bool MIX = false>
+// BATHY: the same-stage operator over a varying still-water depth h(x) (Sec. 2.2) with six
+// column factors (k_geometry_bathy) [A, B, C, d_x, H = w h_x, h_x]; with s = h_x - sigma d_x:
+//   W_r = w_j (A U_r + (H - sigma B) U_s),  W_s = w_j ((H - sigma B) U_r + C (1 + s^2) U_s).
+template <int P, typename T, int MODE, int TC, bool MIX = false, bool BATHY = false>
 __global__ void __launch_bounds__(512) k_curved(CurvedParams<T> p) {
   static_assert(TC == 0 || (std::is_same<T, float>::value && MODE != MODE_DIV), "tensor-core path: FP32 operator");
   static_assert(!MIX || (TC == 0 && (MODE == MODE_APPLY || MODE == MODE_RESIDUAL)), "mixed-stage: apply/residual");
-  constexpr int NG = MIX ? 5 : 4;  // column factors per node column
+  static_assert(!BATHY || (TC == 0 && !MIX && MODE != MODE_DIV), "varying depth: CUDA-core same-stage operator");
+  constexpr int NG = MIX ? 5 : (BATHY ? 6 : 4);  // column factors per node column
   constexpr int n = P + 1;
   const Shape s = p.s;
   const int NZ = s.NZ, Nz = s.Nz, NZp = slab_pitch(NZ);
@@ -197,7 +201,15 @@ __global__ void __launch_bounds__(512) k_curved(CurvedParams<T> p) {
       T sg = SG[iz];
       T ur = Ur[i * NZp + iz];
       T us = Ws[t];
-      if constexpr (MIX) {
+      if constexpr (BATHY) {
+        const T* g = G + i * 6;
+        T grr = wj * g[0];
+        T grs = wj * (g[4] - sg * g[1]);
+        T sl = g[5] - sg * g[3];
+        T gss = wj * g[2] * (T(1) + sl * sl);
+        Wr[t] = grr * ur + grs * us;
+        Ws[t] = grs * ur + gss * us;
+      } else if constexpr (MIX) {
         T grr = wj * G[i * 5 + 0];
         T grs = -wj * sg * G[i * 5 + 1];
         T gsr = -wj * sg * G[i * 5 + 2];
@@ -213,15 +225,16 @@ __global__ void __launch_bounds__(512) k_curved(CurvedParams<T> p) {
       }
     }
   } else {
-    // ---- divergence load vector: W_r = w_i w_j (d dsig/2) u, W_s = w_i w_j (dx/2)(w - sigma d_x u)
-    // Column factors in this mode: A = w_i d dsig/2, B = w_i d_x, C = w_i dx/2.
+    // ---- divergence load vector: W_r = w_i w_j (d dsig/2) u,
+    // W_s = w_i w_j (dx/2)(w + (h_x - sigma d_x) u).  Column factors in this mode:
+    // A = w_i d dsig/2, B = w_i d_x, C = w_i dx/2, H = w_i h_x (zero over a constant depth).
     for (int t = threadIdx.x; t < L * n; t += blockDim.x) {
       int i = t % n, r = t / n, j = r % n, ez = r / n;
       int iz = ez * P + j;
       T wj = CT<T>::w(cT, P, j);
       T u = X[i * NZp + iz], w = Ur[i * NZp + iz];
       Wr[t] = p.scale * wj * G[i * 4 + 0] * u;
-      Ws[t] = p.scale * wj * (G[i * 4 + 2] * w - SG[iz] * G[i * 4 + 1] * (G[i * 4 + 2] / CT<T>::w(cT, P, i)) * u);
+      Ws[t] = p.scale * wj * (G[i * 4 + 2] * w + (G[i * 4 + 3] - SG[iz] * G[i * 4 + 1]) * (G[i * 4 + 2] / CT<T>::w(cT, P, i)) * u);
     }
   }
   __syncthreads();
@@ -359,10 +372,10 @@ static size_t curved_smem(int P, int NZ, int Nz, int ng = 4) {
   return ((e * sizeof(T) + 15) & ~(size_t)15) + 34 * sizeof(double) + 16;
 }
 
-template <int P, typename T, int MODE, int TC, bool MIX = false>
+template <int P, typename T, int MODE, int TC, bool MIX = false, bool BATHY = false>
 static cudaError_t launch_curved_p(const CurvedParams<T>& prm, int threads, cudaStream_t st) {
-  size_t sm = curved_smem<T>(P, prm.s.NZ, prm.s.Nz, MIX ? 5 : 4);
-  auto k = k_curved<P, T, MODE, TC, MIX>;
+  size_t sm = curved_smem<T>(P, prm.s.NZ, prm.s.Nz, MIX ? 5 : (BATHY ? 6 : 4));
+  auto k = k_curved<P, T, MODE, TC, MIX, BATHY>;
   static std::atomic<unsigned long long> s_mask{0};
   cudaError_t e = ensure_max_smem(k, s_mask);
   if (e != cudaSuccess) return e;
@@ -370,10 +383,10 @@ static cudaError_t launch_curved_p(const CurvedParams<T>& prm, int threads, cuda
   return cudaGetLastError();
 }
 
-template <typename T, int MODE, int TC, bool MIX = false>
+template <typename T, int MODE, int TC, bool MIX = false, bool BATHY = false>
 static cudaError_t launch_curved(const CurvedParams<T>& prm, int threads, cudaStream_t st) {
   switch (prm.s.P) {
-#define PMG_CASE(PP) case PP: return launch_curved_p<PP, T, MODE, TC, MIX>(prm, threads, st);
+#define PMG_CASE(PP) case PP: return launch_curved_p<PP, T, MODE, TC, MIX, BATHY>(prm, threads, st);
     PMG_CASE(1) PMG_CASE(2) PMG_CASE(3) PMG_CASE(4) PMG_CASE(5)
     PMG_CASE(6) PMG_CASE(7) PMG_CASE(8) PMG_CASE(9) PMG_CASE(10)
 #undef PMG_CASE

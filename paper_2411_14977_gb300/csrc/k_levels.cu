@@ -32,9 +32,21 @@ struct FlatParams {
   const T* mX;  // [NX] assembled weights along x
   const T* mZ;  // [NZ]
   int residual; // 0: y = A x (surface row y = x); 1: y = b - A x (surface row 0)
+  const T* Kx;  // VAR: [Nx][n][n] x-stiffness of each element column (cx folded in)
 };
 
-template <int P, typename T>
+// Level operator A = cx K_X (x) M_Z + cz M_X (x) K_Z (the flat level of Sec. 5, a Kronecker
+// sum).  VAR: over a varying depth the level keeps each node column's depth d and drops
+// the bottom-slope terms, A = K_X[d] (x) M_Z + M_X[1/d] (x) K_Z, with the element x-stiffness
+// (dsig/dx) D^T diag(w d) D of each element column in Kx and (dx/dsig) M_X[1/d] in mX
+// (cx = cz = 1): still a Kronecker sum, so the same kernels apply.
+template <int P, typename T, bool VAR>
+__device__ __forceinline__ T kx_coef(const T* KE, int i, int m) {
+  if constexpr (VAR) return KE[i * (P + 1) + m];
+  else return CT<T>::K(cT, P, i, m);
+}
+
+template <int P, typename T, bool VAR>
 __global__ void __launch_bounds__(512) k_flat(FlatParams<T> p) {
   constexpr int n = P + 1;
   const Shape s = p.s;
@@ -49,7 +61,15 @@ __global__ void __launch_bounds__(512) k_flat(FlatParams<T> p) {
   T* MZ = Y + n * NZp;                     // [NZ] cx * assembled weights along z
   T* MX = MZ + NZ;                         // [n]  cz * assembled weights along x (own columns)
   T* B = MX + n;                           // [n][NZp] right-hand side of the own columns
+  T* KO = B + n * NZp;                     // VAR: [n][n] own element's x-stiffness
+  T* KL = KO + n * n;                      // VAR: [n] last row of the left element's
   const int c_begin = left ? 0 : P;
+  if constexpr (VAR) {
+    const T* ko = p.Kx + (size_t)ex * n * n;
+    const T* kl = p.Kx + (size_t)(left ? (ex == 0 ? s.Nx - 1 : ex - 1) : ex) * n * n + P * n;
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) KO[t] = ko[t];
+    if (threadIdx.x < n) KL[threadIdx.x] = kl[threadIdx.x];
+  }
   for_slab(2 * P + 1, NZ, [&](int c, int iz) {
     bool ok = c >= c_begin && iz != NZ - 1;
     cp_async_elem(&X[c * NZp + iz], p.x + (ok ? (size_t)wrap_col(s, col0 - P + c) * NZ + iz : 0), ok);
@@ -71,10 +91,10 @@ __global__ void __launch_bounds__(512) k_flat(FlatParams<T> p) {
       if (i == P && !last) break;
       T acc = T(0);
 #pragma unroll
-      for (int m = 0; m < n; ++m) acc += CT<T>::K(cT, P, i, m) * xo[m];
+      for (int m = 0; m < n; ++m) acc += kx_coef<P, T, VAR>(KO, i, m) * xo[m];
       if (i == 0 && left) {  // the left element's share of the shared first column
 #pragma unroll
-        for (int m = 0; m < n; ++m) acc += CT<T>::K(cT, P, P, m) * xl[m];
+        for (int m = 0; m < n; ++m) acc += (VAR ? KL[m] : CT<T>::K(cT, P, P, m)) * xl[m];
       }
       Y[i * NZp + iz] = f * acc;
     }
@@ -115,7 +135,7 @@ __global__ void __launch_bounds__(512) k_flat(FlatParams<T> p) {
 // The same level operator node-parallel: one thread per node reads its x- and z-stencil
 // neighbours straight from global memory (L1/L2 serve the reuse), no shared memory and no
 // barriers, so a CTA's critical path is one load wave and ~2(P+1) FMAs.
-template <int P, typename T>
+template <int P, typename T, bool VAR>
 __global__ void __launch_bounds__(256) k_flat_np(FlatParams<T> p) {
   constexpr int n = P + 1;
   const Shape s = p.s;
@@ -129,12 +149,14 @@ __global__ void __launch_bounds__(256) k_flat_np(FlatParams<T> p) {
   }
   // x stencil: the element(s) of column ix (the wall side has one)
   const int ex = min(ix / P, s.Nx - 1), i = ix - ex * P;
+  const T* ko = VAR ? p.Kx + (size_t)ex * n * n : nullptr;
   T ax = T(0);
 #pragma unroll
-  for (int m = 0; m < n; ++m) ax += CT<T>::K(cT, P, i, m) * p.x[(size_t)wrap_col(s, ex * P + m) * NZ + iz];
+  for (int m = 0; m < n; ++m) ax += kx_coef<P, T, VAR>(ko, i, m) * p.x[(size_t)wrap_col(s, ex * P + m) * NZ + iz];
   if (i == 0 && (s.periodic || ex > 0)) {
+    const T* kl = VAR ? p.Kx + (size_t)(ex == 0 ? s.Nx - 1 : ex - 1) * n * n : nullptr;
 #pragma unroll
-    for (int m = 0; m < n; ++m) ax += CT<T>::K(cT, P, P, m) * p.x[(size_t)wrap_col(s, (ex - 1) * P + m) * NZ + iz];
+    for (int m = 0; m < n; ++m) ax += kx_coef<P, T, VAR>(kl, P, m) * p.x[(size_t)wrap_col(s, (ex - 1) * P + m) * NZ + iz];
   }
   // z stencil along the column (the surface row of x is read as zero)
   const T* col = p.x + (size_t)ix * NZ;
@@ -153,17 +175,17 @@ __global__ void __launch_bounds__(256) k_flat_np(FlatParams<T> p) {
   p.y[g] = p.residual ? p.b[g] - v : v;
 }
 
-template <int P, typename T>
+template <int P, typename T, bool VAR>
 static cudaError_t launch_flat_p(const FlatParams<T>& prm, int threads, cudaStream_t st) {
   if (threads < 0) {  // node-parallel variant, -threads per CTA
     size_t N = (size_t)prm.s.NX * prm.s.NZ;
     int bs = -threads;
-    k_flat_np<P, T><<<(unsigned)((N + bs - 1) / bs), bs, 0, st>>>(prm);
+    k_flat_np<P, T, VAR><<<(unsigned)((N + bs - 1) / bs), bs, 0, st>>>(prm);
     return cudaGetLastError();
   }
   int NZp = slab_pitch(prm.s.NZ);
-  size_t sm = ((size_t)((2 * P + 1) + 2 * (P + 1)) * NZp + prm.s.NZ + P + 1) * sizeof(T);
-  auto k = k_flat<P, T>;
+  size_t sm = ((size_t)((2 * P + 1) + 2 * (P + 1)) * NZp + prm.s.NZ + P + 1 + (VAR ? (P + 1) * (P + 2) : 0)) * sizeof(T);
+  auto k = k_flat<P, T, VAR>;
   static std::atomic<unsigned long long> s_mask{0};
   cudaError_t e = ensure_max_smem(k, s_mask);
   if (e != cudaSuccess) return e;
@@ -183,9 +205,10 @@ cudaError_t flat_op(const FlatArgs& a, cudaStream_t st) {
   p.mX = (const T*)a.mX;
   p.mZ = (const T*)a.mZ;
   p.residual = a.residual;
+  p.Kx = (const T*)a.Kx;
   int thr = (a.threads >= 32 && a.threads <= 512) ? a.threads : (a.threads <= -32 && a.threads >= -256) ? a.threads : 256;
   switch (a.s.P) {
-#define PMG_CASE(PP) case PP: return launch_flat_p<PP, T>(p, thr, st);
+#define PMG_CASE(PP) case PP: return p.Kx ? launch_flat_p<PP, T, true>(p, thr, st) : launch_flat_p<PP, T, false>(p, thr, st);
     PMG_CASE(1) PMG_CASE(2) PMG_CASE(3) PMG_CASE(4) PMG_CASE(5)
     PMG_CASE(6) PMG_CASE(7) PMG_CASE(8) PMG_CASE(9) PMG_CASE(10)
 #undef PMG_CASE
@@ -211,6 +234,7 @@ struct FdmParams {
   const T* wx;      // [NX] inverse 1D cover counts
   const T* wz;      // [NZ]
   Scratch sc;
+  int xpercol;      // Vx [Nx][NB][NB] and invden [Nx][4][NB][NB]: one x-class per element column
 };
 
 __device__ __forceinline__ int xclass(const Shape& s, int ex) {
@@ -227,7 +251,7 @@ __global__ void __launch_bounds__(256) k_fdm(FdmParams<T> p) {
   const Shape s = p.s;
   const int NZ = s.NZ, Nz = s.Nz, NZp = slab_pitch(NZ);
   const int ex = blockIdx.x, col0 = ex * P;
-  const int xc = xclass(s, ex);
+  const int xc = p.xpercol ? ex : xclass(s, ex);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* R = reinterpret_cast<T*>(smem_raw);  // [NB][NZp]  input, later U
   T* T1 = R + NB * NZp;                    // [NB][NZp]  x-transformed rows
@@ -391,6 +415,7 @@ cudaError_t fdm_smooth(const FdmArgs& a, cudaStream_t st) {
   p.wx = (const T*)a.wx;
   p.wz = (const T*)a.wz;
   p.sc = a.sc;
+  p.xpercol = a.xpercol;
   int thr = (a.threads >= 32 && a.threads <= 512) ? a.threads : 256;
   if (a.overlap == 0) {
     switch (a.s.P) {

@@ -130,7 +130,7 @@ extern "C" pmg_status pmg_apply_noalloc(const pmg_mesh_desc* mesh, const double*
   double dx = (m.x1 - m.x0) / m.cells_x, dsig = 1.0 / m.cells_z;
   double* geo = reinterpret_cast<double*>(base + off_geo);
   double* sig = reinterpret_cast<double*>(base + off_sig);
-  if (!ck(geometry<double>(F, eta_dev, m.h, dx, dsig, 0, geo, reinterpret_cast<int*>(base), st))) return PMG_ERR_CUDA;
+  if (!ck(geometry<double>(F, eta_dev, m.h, nullptr, dx, dsig, 0, geo, reinterpret_cast<int*>(base), st))) return PMG_ERR_CUDA;
   Nodes nodes{};
   for (int i = 0; i <= m.order; ++i) nodes.r[i] = g_nodes[m.order][i];
   k_sigma_rows<<<(F.NZ + 127) / 128, 128, 0, st>>>(F.NZ, m.order, m.cells_z, nodes, sig);

@@ -36,6 +36,7 @@ cudaError_t init_consts_apply_tc(const ConstTables* host);
 cudaError_t init_consts_levels(const ConstTables* host);
 cudaError_t init_consts_fdm32(const float* table, size_t n, const float* K, size_t nk);
 cudaError_t init_consts_stepper(const ConstTables* host);
+cudaError_t init_consts_apply_bathy(const ConstTables* host);
 
 // Layout of the FP32 Schwarz eigenvector table (constant memory of the FP32 smoother):
 // for every (P, O) with 2 <= P <= MAXP and O <= (P-1)/2, eight NB x NB blocks
@@ -69,16 +70,28 @@ struct CurvedArgs {
   int tc = 0;          // FP32 only: 0 CUDA cores, 1 BF16 tensor cores, 3 BF16 hi/lo split
   int mix = 0;         // FP64 / double-float apply and residual: the mixed-stage operator
   const void* geo5 = nullptr;  // its column factors [Nx][P+1][5] (FP64)
+  int bathy = 0;       // varying still-water depth: the six-factor operator (CUDA cores)
+  const void* geo6 = nullptr;  // its column factors [Nx][P+1][6] (type of the operator)
 };
 template <typename T> cudaError_t curved_op(const CurvedArgs& a, cudaStream_t st);
 cudaError_t curved_op_tc(const CurvedArgs& a, cudaStream_t st);
+template <typename T> cudaError_t curved_op_bathy(const CurvedArgs& a, cudaStream_t st);
+// Column factors of the actual-geometry operator.  hcol: still-water depth per node column
+// (NULL: the constant h).  div = 0 writes [A, B, C, E] (constant depth only), div = 1 the
+// divergence-load factors [w d dsig/2, w d_x, w dx/2, w h_x]; geometry_bathy writes the six
+// factors [A, B, C, d_x, w h_x, h_x] of the operator over a varying depth.
 template <typename T>
-cudaError_t geometry(const Shape& s, const double* eta, double h, double dx, double dsig, int div,
-                     T* geo, int* status, cudaStream_t st);
+cudaError_t geometry(const Shape& s, const double* eta, double h, const double* hcol, double dx, double dsig,
+                     int div, T* geo, int* status, cudaStream_t st);
+template <typename T>
+cudaError_t geometry_bathy(const Shape& s, const double* eta, const double* hcol, double dx, double dsig,
+                           T* geo, int* status, cudaStream_t st);
 cudaError_t geometry_mixed(const Shape& s, const double* eta, const double* etap, double h, double dx, double dsig,
                            double* geo, int* status, cudaStream_t st);
-cudaError_t rhs_source(const Shape& s, const double* eta, double h, double dx, double dsig,
-                       const double* mX, const double* mZ, const double* f, const double* gb,
+// hcol: depth per node column (NULL: h); mb: bottom edge weights per node column, the sum
+// over the column's elements of w_i (dx/2) sqrt(1 + h_x^2) (NULL: mX dx/2, a flat bottom)
+cudaError_t rhs_source(const Shape& s, const double* eta, double h, const double* hcol, double dx, double dsig,
+                       const double* mX, const double* mZ, const double* mb, const double* f, const double* gb,
                        const double* gl, const double* gr, double* b, cudaStream_t st);
 
 struct FlatArgs {
@@ -91,6 +104,9 @@ struct FlatArgs {
   const void* mZ;
   int residual;
   int threads = 256;   // > 0: slab CTA size; < 0: node-parallel kernel with -threads per CTA
+  // varying depth: per element column x-stiffness [Nx][P+1][P+1] with cx folded in (then
+  // cx = cz = 1 and mX holds the depth-weighted x weights)
+  const void* Kx = nullptr;
 };
 template <typename T> cudaError_t flat_op(const FlatArgs& a, cudaStream_t st);
 
@@ -116,6 +132,7 @@ struct FdmArgs {
   double cx = 0.0, cz = 0.0;
   const void* mX = nullptr;
   const void* mZ = nullptr;
+  int xpercol = 0;  // generic sweep: Vx / invden hold one x-class per element column
 };
 template <typename T> cudaError_t fdm_smooth(const FdmArgs& a, cudaStream_t st);
 // FP32 sweep with the eigenvectors in constant memory (k_fdm32.cu)
@@ -133,6 +150,7 @@ struct TransferArgs {
   double cx = 0.0, cz = 0.0;
   const void* mX = nullptr;
   const void* mZ = nullptr;
+  int xpercol = 0;  // generic sweep: Vx / invden hold one x-class per element column
 };
 template <typename T> cudaError_t transfer(const TransferArgs& a, int restrict_, cudaStream_t st);
 

@@ -100,6 +100,7 @@ pmg_status ensure_constants(int dev) {
   CK(init_consts_apply_tc(&t));
   CK(init_consts_levels(&t));
   CK(init_consts_stepper(&t));
+  CK(init_consts_apply_bathy(&t));
   {
     std::vector<float> tab(fdm32_table_size(), 0.f);
     for (int P = 2; P <= MAXP; ++P)
@@ -233,6 +234,13 @@ struct LevelDev {
   void* b[2]{};
   void* x[2]{};
   void* t[2]{};
+  // varying still-water depth (pmg_set_bathymetry): the level keeps each node column's
+  // depth and drops the bottom-slope terms; tables per element column
+  bool var = false;
+  void* Kx[2]{};       // [Nx][p+1][p+1] element x-stiffness (dsig/dx) D^T diag(w d) D
+  void* mXd[2]{};      // [NX] (dx/dsig) sum over the column's elements of w / d
+  void* Vxc[2]{};      // [Nx][NB][NB] Schwarz x-eigenvectors of each element column
+  void* invdenc[2]{};  // [Nx][4][NB][NB] 1 / (lambda_x + lambda_z)
 };
 
 struct pmg_handle {
@@ -267,6 +275,11 @@ struct pmg_handle {
   double* geo5 = nullptr;  // mixed-stage column factors [Nx][P+1][5] (pmg_set_geometry_mixed)
   double* eta_prev = nullptr;
   bool mixed_stage = false;  // the outer operator is the mixed-stage one
+  // varying still-water depth h(x) (pmg_set_bathymetry)
+  bool bathy = false;
+  double* hcol = nullptr;    // [NX] depth per node column
+  void* geo6[2]{};           // [Nx][P+1][6] column factors of the operator over it
+  double* mb = nullptr;      // [NX] bottom edge weights sum_e w_i (dx/2) sqrt(1 + h_x^2)
   // flexible GMRES(m): Arnoldi basis V [(m+1) N], preconditioned directions Z [m N], device
   // coefficients (two Gram-Schmidt passes and the new norm), block partials, ticket, y
   double *gm_V = nullptr, *gm_Z = nullptr, *gm_h = nullptr, *gm_part = nullptr, *gm_y = nullptr;
@@ -446,26 +459,138 @@ pmg_status build_level(pmg_handle* h, int l) {
   return PMG_OK;
 }
 
-pmg_status build_coarse(pmg_handle* h) {
+// ---- varying still-water depth: level tables ----------------------------------------
+// Element x-stiffness (dsig/dx) D^T diag(w d) D of every element column for the nodal depth
+// dl of an order-p level, row-major [Nx][p+1][p+1].
+std::vector<double> element_kx(int p, const Line1D& lx, const std::vector<double>& dl, double ax) {
+  int n = p + 1, Nx = lx.ncell;
+  std::vector<double> xg, w;
+  lgl(p, xg, w);
+  std::vector<double> D = diff_matrix(p);
+  std::vector<double> Kx((size_t)Nx * n * n);
+  for (int ex = 0; ex < Nx; ++ex)
+    for (int i = 0; i < n; ++i)
+      for (int k = 0; k < n; ++k) {
+        double s = 0.0;
+        for (int q = 0; q < n; ++q) s += D[q * n + i] * w[q] * dl[lx.wrap(ex * p + q)] * D[q * n + k];
+        Kx[((size_t)ex * n + i) * n + k] = ax * s;
+      }
+  return Kx;
+}
+
+// Assembled entry (a, b) of the 1D x-stiffness from per-element matrices.
+double kx_assembled(const Line1D& lx, const std::vector<double>& Kx, int a, int b) {
+  int n = lx.p + 1;
+  int ea[2], la[2], eb[2], lb[2], na, nb;
+  lx.owners(a, ea, la, na);
+  lx.owners(b, eb, lb, nb);
+  double s = 0.0;
+  for (int i = 0; i < na; ++i)
+    for (int j = 0; j < nb; ++j)
+      if (ea[i] == eb[j]) s += Kx[((size_t)ea[i] * n + la[i]) * n + lb[j]];
+  return s;
+}
+
+template <typename T>
+pmg_status upload_into(void*& dst, const std::vector<double>& v, pmg_handle* h) {
+  cudaError_t e = cudaSuccess;
+  if (!dst) {
+    dst = upload<T>(v, h->allocs, e);
+    CK(e);
+    return PMG_OK;
+  }
+  std::vector<T> t(v.begin(), v.end());
+  CK(cudaMemcpy(dst, t.data(), t.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return PMG_OK;
+}
+
+// Level l over the nodal depth dl (NX_l values): the slope-free level operator
+// A = K_X[d] (x) M_Z + M_X[1/d] (x) K_Z and its Schwarz factors per element column.  The
+// x-direction generalized eigenproblem of each subdomain is solved here; the z factors are
+// the depth-free class factors of the constant-depth level.
+pmg_status build_level_var(pmg_handle* h, int l, const std::vector<double>& dl) {
+  LevelDev& L = h->lv[l];
+  const pmg_mesh_desc& m = h->mesh;
+  const int p = L.order, n = p + 1, Nx = m.cells_x, NX = L.s.NX;
+  const double ax = h->dsig / h->dx, az = h->dx / h->dsig;
+  Line1D lx(p, Nx, m.periodic_x);
+  std::vector<double> Kx = element_kx(p, lx, dl, ax), mXd(NX, 0.0);
+  for (int a = 0; a < NX; ++a) mXd[a] = az * lx.M(a) / dl[a];
+  for (int k = 0; k < 2; ++k) {
+    CKS(k == 0 ? upload_into<double>(L.Kx[0], Kx, h) : upload_into<float>(L.Kx[1], Kx, h));
+    CKS(k == 0 ? upload_into<double>(L.mXd[0], mXd, h) : upload_into<float>(L.mXd[1], mXd, h));
+  }
+  L.var = true;
+  L.fuse_res = false;
+  L.fuse_restrict = false;
+  if (l == (int)h->orders.size() - 1) return PMG_OK;
+  const int O = L.overlap, NB = n + 2 * O;
+  std::vector<double> Vz(NB * NB), lamz(4 * NB, 0.0);
+  int kz[4];
+  for (int cls = 0; cls < 4; ++cls) fdm_class(p, O, 1, cls, Vz.data(), &lamz[cls * NB], kz[cls]);
+  std::vector<double> Vx((size_t)Nx * NB * NB, 0.0), invden((size_t)Nx * 4 * NB * NB, 0.0);
+  std::vector<int> loc, glob;
+  for (int ex = 0; ex < Nx; ++ex) {
+    loc.clear();
+    glob.clear();
+    for (int a = 0; a < NB; ++a) {
+      int g = ex * p - O + a;
+      if (!m.periodic_x && (g < 0 || g >= NX)) continue;
+      loc.push_back(a);
+      glob.push_back(lx.wrap(g));
+    }
+    const int k = (int)glob.size();
+    std::vector<double> K(k * k), M(k), Vk, lk;
+    for (int i = 0; i < k; ++i) {
+      M[i] = mXd[glob[i]];
+      for (int j = 0; j < k; ++j) K[i * k + j] = kx_assembled(lx, Kx, glob[i], glob[j]);
+    }
+    gen_eig_diag(k, K, M, Vk, lk);
+    for (int i = 0; i < k; ++i)
+      for (int a = 0; a < k; ++a) Vx[((size_t)ex * NB + loc[i]) * NB + a] = Vk[i * k + a];
+    for (int zc = 0; zc < 4; ++zc)
+      for (int a = 0; a < k; ++a)
+        for (int b = 0; b < kz[zc]; ++b) {
+          double d = lk[a] + lamz[zc * NB + b];
+          invden[(((size_t)ex * 4 + zc) * NB + a) * NB + b] = d > 0.0 ? 1.0 / d : 0.0;
+        }
+  }
+  CKS(upload_into<double>(L.Vxc[0], Vx, h));
+  CKS(upload_into<float>(L.Vxc[1], Vx, h));
+  CKS(upload_into<double>(L.invdenc[0], invden, h));
+  CKS(upload_into<float>(L.invdenc[1], invden, h));
+  return PMG_OK;
+}
+
+// Coarse (order 1) tables: sigma eigenmodes V (Nz x Nz) and, per mode, the PCR
+// elimination factors of the x-tridiagonal system (K_X + mu_k M_X).  d1 == NULL: constant
+// depth (cx K_X, cz M_X); otherwise the slope-free operator over the nodal depth d1.
+void coarse_tables(pmg_handle* h, const std::vector<double>* d1, std::vector<double>& V, std::vector<double>& coef,
+                   std::vector<double>& inv, int& nsteps) {
   const pmg_mesh_desc& m = h->mesh;
   int Nz = m.cells_z, NX1 = m.cells_x + (m.periodic_x ? 0 : 1);
   Line1D lx(1, m.cells_x, m.periodic_x), lz(1, m.cells_z, 0);
-  std::vector<double> K(Nz * Nz), M(Nz), V, mu;
+  std::vector<double> K(Nz * Nz), M(Nz), mu;
   for (int i = 0; i < Nz; ++i) {
     M[i] = lz.M(i);
     for (int j = 0; j < Nz; ++j) K[i * Nz + j] = lz.K(i, j);
   }
   gen_eig_diag(Nz, K, M, V, mu);
   int n = NX1;
-  int nsteps = 0;
+  nsteps = 0;
   while ((1 << nsteps) < n) ++nsteps;
-  std::vector<double> coef((size_t)Nz * nsteps * n * 2, 0.0), inv((size_t)Nz * n, 0.0);
+  std::vector<double> Kx1;
+  if (d1) Kx1 = element_kx(1, lx, *d1, h->dsig / h->dx);
+  auto kx = [&](int i, int j) { return d1 ? kx_assembled(lx, Kx1, i, j) : h->cx * lx.K(i, j); };
+  auto mx = [&](int i) { return d1 ? (h->dx / h->dsig) * lx.M(i) / (*d1)[i] : h->cz * lx.M(i); };
+  coef.assign((size_t)Nz * nsteps * n * 2, 0.0);
+  inv.assign((size_t)Nz * n, 0.0);
   for (int k = 0; k < Nz; ++k) {
     std::vector<double> a(n), b(n), c(n), a2(n), b2(n), c2(n);
     for (int i = 0; i < n; ++i) {
-      b[i] = h->cx * lx.K(i, i) + h->cz * mu[k] * lx.M(i);
-      a[i] = (m.periodic_x || i > 0) ? h->cx * lx.K(i, lx.wrap(i - 1)) : 0.0;
-      c[i] = (m.periodic_x || i < n - 1) ? h->cx * lx.K(i, lx.wrap(i + 1)) : 0.0;
+      b[i] = kx(i, i) + mu[k] * mx(i);
+      a[i] = (m.periodic_x || i > 0) ? kx(i, lx.wrap(i - 1)) : 0.0;
+      c[i] = (m.periodic_x || i < n - 1) ? kx(i, lx.wrap(i + 1)) : 0.0;
     }
     int s = 1;
     for (int step = 0; step < nsteps; ++step, s <<= 1) {
@@ -485,6 +610,14 @@ pmg_status build_coarse(pmg_handle* h) {
     }
     for (int i = 0; i < n; ++i) inv[(size_t)k * n + i] = 1.0 / (m.periodic_x ? a[i] + b[i] + c[i] : b[i]);
   }
+}
+
+pmg_status build_coarse(pmg_handle* h) {
+  const pmg_mesh_desc& m = h->mesh;
+  int Nz = m.cells_z, NX1 = m.cells_x + (m.periodic_x ? 0 : 1);
+  int n = NX1, nsteps = 0;
+  std::vector<double> V, coef, inv;
+  coarse_tables(h, nullptr, V, coef, inv, nsteps);
   cudaError_t e;
   h->coarse.NX1 = NX1;
   h->coarse.NZ1 = Nz + 1;
@@ -506,7 +639,9 @@ template <typename T>
 pmg_status level_residual(pmg_handle* h, int l, const void* b, const void* x, void* y, int residual,
                           cudaStream_t st) {
   LevelDev& L = h->lv[l];
-  FlatArgs a{L.s, x, b, y, h->cx, h->cz, L.mX[PI<T>], L.mZ[PI<T>], residual, PI<T> ? L.thr_flat32 : 256};
+  FlatArgs a{L.s, x, b, y, L.var ? 1.0 : h->cx, L.var ? 1.0 : h->cz, L.var ? L.mXd[PI<T>] : L.mX[PI<T>],
+             L.mZ[PI<T>], residual, PI<T> ? L.thr_flat32 : 256};
+  if (L.var) a.Kx = L.Kx[PI<T>];
   double NL = (double)L.s.NX * L.s.NZ;
   Cost c{(residual ? 3.0 : 2.0) * NL * sizeof(T), NL * (4.0 * (L.s.P + 2) + 4.0)};
   return launch(h, PI<T> ? PMG_K_LEVEL32 : PMG_K_LEVEL64, 1, st, c, [&] { return flat_op<T>(a, st); });
@@ -526,6 +661,15 @@ pmg_status level_fdm(pmg_handle* h, int l, const void* r, void* x, int post, cud
   if (PI<T>) {
     a.xout = xout;
     a.xzero = xzero ? 1 : 0;
+  }
+  if (L.var) {
+    // per element column x-classes: the generic sweep (tables from global memory), in place
+    if (fused_b || (xout && xout != x)) return fail(PMG_ERR_INVALID, "fused sweep over a varying depth");
+    a.Vx = L.Vxc[PI<T>];
+    a.invden = L.invdenc[PI<T>];
+    a.xpercol = 1;
+    a.threads = 256;
+    return launch(h, PI<T> ? PMG_K_SMOOTH32 : PMG_K_SMOOTH64, 1, st, c, [&] { return fdm_smooth<T>(a, st); });
   }
   if (fused_b) {
     a.b = fused_b;
@@ -647,6 +791,11 @@ pmg_status curved(pmg_handle* h, int mode, const void* x, const void* b, void* y
   if (!PI<T> && h->mixed_stage && (mode == 0 || mode == 1)) {
     a.mix = 1;
     a.geo5 = h->geo5;
+  }
+  if (h->bathy) {
+    a.bathy = 1;
+    a.geo6 = h->geo6[PI<T>];
+    a.tc = 0;
   }
   const Shape& F = a.s;
   double N = (double)F.NX * F.NZ, E = (double)F.Nx * F.Nz, n = F.P + 1;
@@ -1088,8 +1237,10 @@ void set_last_error(const char* msg) { g_err = msg; }
 // =====================================================================================
 namespace {
 
-enum { TK_FLAT32 = 0, TK_FDM32 = 1, TK_XFER = 2, TK_CURVED32 = 3, TK_CURVED64 = 4 };
-const char* kTuneNames[] = {"flat32", "fdm32", "transfer", "curved32", "curved64"};
+enum { TK_FLAT32 = 0, TK_FDM32 = 1, TK_XFER = 2, TK_CURVED32 = 3, TK_CURVED64 = 4, TK_FLAT32V = 5,
+       TK_CURVED32B = 6, TK_CURVED64B = 7, TK_COUNT = 8 };
+const char* kTuneNames[] = {"flat32", "fdm32", "transfer", "curved32", "curved64", "flat32_depth", "curved32_depth",
+                            "curved64_depth"};
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int>, int> g_tune;  // (kernel, order, rows, columns) -> threads
 bool g_tune_loaded = false;
@@ -1109,7 +1260,7 @@ void tune_cache_load() {
     int P, NZ, Nx, thr;
     if (std::sscanf(line, "{\"kernel\": \"%63[^\"]\", \"P\": %d, \"NZ\": %d, \"Nx\": %d, \"threads\": %d}", name, &P,
                     &NZ, &Nx, &thr) == 5)
-      for (int k = 0; k < 5; ++k)
+      for (int k = 0; k < TK_COUNT; ++k)
         if (!std::strcmp(name, kTuneNames[k])) g_tune[std::make_tuple(k, P, NZ, Nx)] = thr;
   }
   std::fclose(f);
@@ -1436,14 +1587,90 @@ pmg_status pmg_set_geometry(pmg_handle* h, const double* eta_dev, void* stream) 
   if (eta_dev != h->eta) CK(cudaMemcpyAsync(h->eta, eta_dev, F.NX * sizeof(double), cudaMemcpyDeviceToDevice, st));
   int* gst = h->status + 1;
   CK(cudaMemsetAsync(gst, 0, sizeof(int), st));
-  CKS(launch(h, PMG_K_SETUP, 1, st, [&] { return geometry<double>(F, h->eta, h->mesh.h, h->dx, h->dsig, 0, (double*)h->geo[0], gst, st); }));
-  CKS(launch(h, PMG_K_SETUP, 1, st, [&] { return geometry<float>(F, h->eta, h->mesh.h, h->dx, h->dsig, 0, (float*)h->geo[1], gst, st); }));
-  CKS(launch(h, PMG_K_SETUP, 1, st, [&] { return geometry<double>(F, h->eta, h->mesh.h, h->dx, h->dsig, 1, h->geo_div, gst, st); }));
+  const double* hc = h->bathy ? h->hcol : nullptr;
+  if (h->bathy) {
+    CKS(launch(h, PMG_K_SETUP, 1, st, [&] { return geometry_bathy<double>(F, h->eta, hc, h->dx, h->dsig, (double*)h->geo6[0], gst, st); }));
+    CKS(launch(h, PMG_K_SETUP, 1, st, [&] { return geometry_bathy<float>(F, h->eta, hc, h->dx, h->dsig, (float*)h->geo6[1], gst, st); }));
+  } else {
+    CKS(launch(h, PMG_K_SETUP, 1, st, [&] { return geometry<double>(F, h->eta, h->mesh.h, nullptr, h->dx, h->dsig, 0, (double*)h->geo[0], gst, st); }));
+    CKS(launch(h, PMG_K_SETUP, 1, st, [&] { return geometry<float>(F, h->eta, h->mesh.h, nullptr, h->dx, h->dsig, 0, (float*)h->geo[1], gst, st); }));
+  }
+  CKS(launch(h, PMG_K_SETUP, 1, st, [&] { return geometry<double>(F, h->eta, h->mesh.h, hc, h->dx, h->dsig, 1, h->geo_div, gst, st); }));
   h->mixed_stage = false;
   return PMG_OK;
 }
 
+pmg_status pmg_set_bathymetry(pmg_handle* h, const double* h_dev, void* stream) {
+  CKS(check_handle(h));
+  if (!h_dev) return fail(PMG_ERR_INVALID, "depth is NULL");
+  if (h->tc) return fail(PMG_ERR_INVALID, "the BF16 tensor-core operator takes a constant depth only");
+  if (h->mesh.periodic_x && h->mesh.cells_x < 2) return fail(PMG_ERR_INVALID, "periodic mesh needs 2 or more cells");
+  DeviceGuard dg(h->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const pmg_mesh_desc& m = h->mesh;
+  const Shape& F = h->lv[0].s;
+  const int P = m.order, n = P + 1;
+  std::vector<double> hc(F.NX);
+  CK(cudaMemcpyAsync(hc.data(), h_dev, F.NX * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (double v : hc)
+    if (!(v > 0.0) || !std::isfinite(v)) return fail(PMG_ERR_INVALID, "still-water depth must be positive and finite");
+  Line1D lf(P, m.cells_x, m.periodic_x);
+  // level depths: the fine interpolant of each cell evaluated at the level's nodes
+  std::vector<std::vector<double>> dl(h->lv.size());
+  for (size_t l = 0; l < h->lv.size(); ++l) {
+    const int p = h->lv[l].order;
+    if (p == P) { dl[l] = hc; continue; }
+    std::vector<double> E = transfer_matrix(P, p);  // (p+1) x (P+1): order-P data at order-p nodes
+    Line1D ll(p, m.cells_x, m.periodic_x);
+    dl[l].assign(h->lv[l].s.NX, 0.0);
+    for (int ex = 0; ex < m.cells_x; ++ex)
+      for (int i = 0; i <= p; ++i) {
+        double v = 0.0;
+        for (int k = 0; k < n; ++k) v += E[i * n + k] * hc[lf.wrap(ex * P + k)];
+        dl[l][ll.wrap(ex * p + i)] = v;
+      }
+    for (double v : dl[l])
+      if (!(v > 0.0)) return fail(PMG_ERR_INVALID, "the depth interpolated to a coarse level is not positive");
+  }
+  for (size_t l = 0; l < h->lv.size(); ++l) CKS(build_level_var(h, (int)l, dl[l]));
+  {
+    std::vector<double> V, coef, inv;
+    int nsteps = 0;
+    coarse_tables(h, &dl.back(), V, coef, inv, nsteps);
+    CK(cudaMemcpy((void*)h->coarse.V, V.data(), V.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy((void*)h->coarse.coef, coef.data(), coef.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy((void*)h->coarse.inv, inv.data(), inv.size() * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  // bottom edge weights: arc length of the mapped bottom z = -h(x) per node column
+  std::vector<double> xg, w, D = diff_matrix(P), mb(F.NX, 0.0);
+  lgl(P, xg, w);
+  for (int ex = 0; ex < m.cells_x; ++ex)
+    for (int i = 0; i < n; ++i) {
+      double hx = 0.0;
+      for (int k = 0; k < n; ++k) hx += D[i * n + k] * hc[lf.wrap(ex * P + k)];
+      hx *= 2.0 / h->dx;
+      mb[lf.wrap(ex * P + i)] += w[i] * (h->dx * 0.5) * std::sqrt(1.0 + hx * hx);
+    }
+  cudaError_t e = cudaSuccess;
+  if (!h->hcol) {
+    h->hcol = h->alloc<double>(F.NX, e); CK(e);
+    h->mb = h->alloc<double>(F.NX, e); CK(e);
+    h->geo6[0] = h->alloc<double>((size_t)m.cells_x * n * 6, e); CK(e);
+    h->geo6[1] = h->alloc<float>((size_t)m.cells_x * n * 6, e); CK(e);
+  }
+  CK(cudaMemcpy(h->hcol, hc.data(), F.NX * sizeof(double), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->mb, mb.data(), F.NX * sizeof(double), cudaMemcpyHostToDevice));
+  h->bathy = true;
+  // graphs captured before hold the constant-depth kernels: rebuild on next use
+  for (pmg_handle::Loop* lp : {&h->loop64, &h->loop32})
+    if (lp->exec) { cudaGraphExecDestroy(lp->exec); lp->exec = nullptr; }
+  return pmg_set_geometry(h, h->eta, stream);
+}
+
 pmg_status pmg_set_geometry_mixed(pmg_handle* h, const double* eta_dev, const double* eta_prev_dev, void* stream) {
+  CKS(check_handle(h));
+  if (h->bathy) return fail(PMG_ERR_INVALID, "the mixed-stage operator takes a constant depth only");
   CKS(pmg_set_geometry(h, eta_dev, stream));
   if (!eta_prev_dev) return fail(PMG_ERR_INVALID, "eta_prev is NULL");
   DeviceGuard dg(h->device);
@@ -1473,7 +1700,8 @@ pmg_status pmg_assemble_rhs(pmg_handle* h, const double* f, const double* gb, co
   LevelDev& L = h->lv[0];
   cudaStream_t st = (cudaStream_t)stream;
   return launch(h, PMG_K_SETUP, 1, st, [&] {
-    return rhs_source(L.s, h->eta, h->mesh.h, h->dx, h->dsig, (const double*)L.mX[0], (const double*)L.mZ[0], f, gb,
+    return rhs_source(L.s, h->eta, h->mesh.h, h->bathy ? h->hcol : nullptr, h->dx, h->dsig, (const double*)L.mX[0],
+                      (const double*)L.mZ[0], h->bathy ? h->mb : nullptr, f, gb,
                       h->mesh.periodic_x ? nullptr : gl, h->mesh.periodic_x ? nullptr : gr, b, st);
   });
 }
@@ -1676,6 +1904,7 @@ pmg_status pmg_profile_read(pmg_handle* h, int64_t* launches, double* ms, double
 pmg_status pmg_gradient(pmg_handle* h, const double* f, double* fx, double* fz, void* stream) {
   CKS(check_handle(h));
   if (!f || !fx || !fz) return fail(PMG_ERR_INVALID, "NULL vector");
+  if (h->bathy) return fail(PMG_ERR_INVALID, "gradient recovery takes a constant depth only");
   DeviceGuard dg(h->device);
   cudaStream_t st = (cudaStream_t)stream;
   const Shape& F = h->lv[0].s;
@@ -1779,13 +2008,22 @@ pmg_status pmg_autotune(pmg_handle* h) {
     void* b = L.b[1];
     void* t = L.t[1];
     // slab CTAs (positive sizes) or node-parallel CTAs (negative sizes)
-    CKS(tune_one(h, TK_FLAT32, L.order, L.s.NZ, [&](int thr, cudaStream_t cs) {
+    CKS(tune_one(h, L.var ? TK_FLAT32V : TK_FLAT32, L.order, L.s.NZ, [&](int thr, cudaStream_t cs) {
       L.thr_flat32 = thr;
       return level_residual<float>(h, l, b, x, t, 1, cs);
     }, &L.thr_flat32, h->opts.flat_kernel == 1 ? std::initializer_list<int>{-64, -128, -256}
                        : h->opts.flat_kernel == 0 ? std::initializer_list<int>{64, 128, 192, 256, 320, 384, 512}
                        : std::initializer_list<int>{64, 128, 192, 256, 320, 384, 512, -64, -128, -256}));
     if (l == nl - 1) continue;
+    if (L.var) {
+      // varying depth: generic sweep (fixed CTA size), split residuals; only the transfers tune
+      LevelDev& C = h->lv[l + 1];
+      CKS(tune_one(h, TK_XFER, L.order * 16 + C.order, L.s.NZ, [&](int thr, cudaStream_t cs) {
+        L.thr_xfer = thr;
+        return transfer_op<float>(h, l, t, C.b[1], 1, cs);
+      }, &L.thr_xfer));
+      continue;
+    }
     CKS(tune_one(h, TK_FDM32, L.order * 16 + L.overlap, L.s.NZ, [&](int thr, cudaStream_t cs) {
       L.thr_fdm32 = thr;
       return level_fdm<float>(h, l, t, x, 0, cs);
@@ -1821,11 +2059,11 @@ pmg_status pmg_autotune(pmg_handle* h) {
       if (h->opts.fuse_residual < 0) L.fuse_restrict = us_fused < 0.9f * us_split;
     }
   }
-  CKS(tune_one(h, TK_CURVED32, h->mesh.order, h->lv[0].s.NZ, [&](int thr, cudaStream_t cs) {
+  CKS(tune_one(h, h->bathy ? TK_CURVED32B : TK_CURVED32, h->mesh.order, h->lv[0].s.NZ, [&](int thr, cudaStream_t cs) {
     h->thr_curved32 = thr;
     return curved<float>(h, 0, h->r32, nullptr, h->w32, 1, nullptr, cs);
   }, &h->thr_curved32));
-  CKS(tune_one(h, TK_CURVED64, h->mesh.order, h->lv[0].s.NZ, [&](int thr, cudaStream_t cs) {
+  CKS(tune_one(h, h->bathy ? TK_CURVED64B : TK_CURVED64, h->mesh.order, h->lv[0].s.NZ, [&](int thr, cudaStream_t cs) {
     h->thr_curved64 = thr;
     return curved<double>(h, 0, h->p, nullptr, h->w, 1, nullptr, cs);
   }, &h->thr_curved64));

@@ -64,6 +64,7 @@ _SIGNATURES = {
     "pmg_node_coords": (_I, [_P, _P, _P]),
     "pmg_set_geometry": (_I, [_P, _P, _P]),
     "pmg_set_geometry_mixed": (_I, [_P, _P, _P, _P]),
+    "pmg_set_bathymetry": (_I, [_P, _P, _P]),
     "pmg_assemble_rhs": (_I, [_P, _P, _P, _P, _P, _P, _P]),
     "pmg_assemble_rhs_div": (_I, [_P, _P, _P, _D, _P, _P]),
     "pmg_solve": (_I, [_P, _P, _P, _P, _P, ctypes.POINTER(SolveInfo), _P]),
@@ -225,6 +226,10 @@ class Solver:
 
     def set_geometry(self, eta):
         _check(load().pmg_set_geometry(self._h, _ptr(eta), _stream()))
+
+    def set_bathymetry(self, depth):
+        """Varying still-water depth h(x) at the node columns (NX doubles on the device)."""
+        _check(load().pmg_set_bathymetry(self._h, _ptr(depth), _stream()))
 
     def assemble_rhs(self, f, g_bottom=None, g_left=None, g_right=None, out=None):
         out = torch.empty(self.n, dtype=torch.float64, device=f.device) if out is None else out

@@ -30,6 +30,10 @@ class Case:
         np.testing.assert_allclose(sr, self.m.row_sigma(), rtol=0, atol=1e-15)
         self.F = w.fields(xc, sr)
         self.eta = self.F["eta"]
+        if w.bathymetry is not None:
+            # both sides get the same nodal depths
+            self.m = Mesh(**w.mesh_kwargs(), depth=self.F["h"])
+            self.S.set_bathymetry(t(self.F["h"]))
         self.S.set_geometry(t(self.eta))
         self.opts = self.S.opts
 

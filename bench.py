@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg3", "cfg4", "cfg5", "paper"])
+    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg3", "cfg4", "cfg5", "paper", "bar"])
     ap.add_argument("--kernel-scaling", action="store_true",
                     help="time the hot kernels alone on config-2 tanks of growing length and report "
                          "their HBM roofline fractions")
@@ -586,6 +586,105 @@ def run_paper(args, ws, rank, local):
           flush=True)
 
 
+def run_bar(args, ws, rank, local):
+    """Solves over a varying still-water depth (the bar geometry of Sec. 6, synthetic bar):
+    the paper's bar discretisation (P = 8, N_x = 100, N_z = 2) and a 1.2M-node bar tank
+    (P = 6, N_x = 2048, N_z = 16), FP64 PCG and the mixed-precision solve to 1e-10, each
+    beside the same mesh over a flat bottom of the off-bar depth (what the slope-free level
+    operator costs in iterations), the oracle's iteration count on the paper-size case,
+    and the finest Schwarz sweep alone (per-column factors vs the constant-depth kernel).
+    Device time per solve: CUDA events, median of `steps` solves from a zero guess."""
+    import torch
+    import paper_2411_14977_gb300.pmg as pmg
+    import workloads as W
+
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pmg.load(build_if_missing=True)
+
+    def prepare(w, flat_bottom=False, **opts):
+        S = pmg.Solver(**w.mesh_kwargs(), **opts)
+        xc, sr = S.node_coords()
+        F = w.fields(xc, sr)
+        d = {k: torch.as_tensor(np.ascontiguousarray(F[k]), dtype=torch.float64, device=dev)
+             for k in ("eta", "u", "w", "pD", "h")}
+        if not flat_bottom:
+            S.set_bathymetry(d["h"])
+        S.set_geometry(d["eta"])
+        S.autotune()
+        b = S.assemble_rhs_div(d["u"], d["w"])
+        return S, b, d["pD"]
+
+    def time_solve(S, b, pD):
+        p = torch.empty_like(b)
+        info = None
+        for _ in range(2):
+            _, info = S.solve(b, pD, out=p, raise_on_error=False)
+        ts = []
+        for _ in range(max(args.steps, 3)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            _, info = S.solve(b, pD, out=p, raise_on_error=False)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts)), info, p
+
+    clk = ClockSampler(local)
+    out = {}
+    for w in (W.bar(100, 2, 8), W.bar(2048, 16, 6)):
+        row = {}
+        ref = None
+        for name, opts in (("fp64_pcg", dict(precision=pmg.PMG_FP64)), ("mixed", dict(precision=pmg.PMG_MIXED_FP32))):
+            for bottom in ("bar", "flat"):
+                S, b, pD = prepare(w, flat_bottom=bottom == "flat", tol=1e-10, **opts)
+                ms, info, p = time_solve(S, b, pD)
+                e = {"iterations": info["iterations"], "ms": ms, "status": info["status"],
+                     "rel_residual": info["rel_residual"], "dof_per_s": (S.n - S.level_info(0)[1]) / (ms / 1e3)}
+                if bottom == "bar":
+                    if ref is None:
+                        ref = p.clone()
+                    else:
+                        e["rel_l2_vs_fp64"] = float(torch.linalg.norm(p - ref) / torch.linalg.norm(ref))
+                row[f"{name}_{bottom}"] = e
+                log(w.name, name, bottom, e)
+                if bottom == "bar" and name == "mixed":
+                    N0 = S.n
+                    r32 = torch.randn(N0, dtype=torch.float32, device=dev)
+                    x32 = torch.zeros(N0, dtype=torch.float32, device=dev)
+                    row["sweep_us_per_column_factors"] = graph_launch_us(torch, lambda: S.level_sweep(0, r32, x32))
+                    row["flat_op_us_per_column_depth"] = graph_launch_us(torch, lambda: S.level_apply(0, r32, x32))
+                    x64 = torch.randn(N0, dtype=torch.float64, device=dev)
+                    y64 = torch.empty_like(x64)
+                    row["outer_apply_us_bathymetry"] = graph_launch_us(torch, lambda: S.apply(x64, y64))
+                if bottom == "flat" and name == "mixed":
+                    N0 = S.n
+                    r32 = torch.randn(N0, dtype=torch.float32, device=dev)
+                    x32 = torch.zeros(N0, dtype=torch.float32, device=dev)
+                    row["sweep_us_constant_depth"] = graph_launch_us(torch, lambda: S.level_sweep(0, r32, x32))
+                    row["flat_op_us_constant_depth"] = graph_launch_us(torch, lambda: S.level_apply(0, r32, x32))
+                    x64 = torch.randn(N0, dtype=torch.float64, device=dev)
+                    y64 = torch.empty_like(x64)
+                    row["outer_apply_us_flat_bottom"] = graph_launch_us(torch, lambda: S.apply(x64, y64))
+                nodes = S.n
+                S.close()
+        row["nodes"] = int(nodes)
+        out[w.name] = row
+    # the oracle (FP64 p-MG-PCG with the same slope-free levels) on the paper-size bar
+    from oracle import mg as omg
+    from oracle.sem import Mesh
+    w = W.bar(100, 2, 8)
+    m = Mesh(**w.mesh_kwargs(), depth=w.bathymetry)
+    F = w.fields(m.column_x(), m.row_sigma())
+    bo = m.rhs_divergence(F["eta"], F["u"], F["w"])
+    t0 = time.perf_counter()
+    _, its, _, _ = omg.solve(m, F["eta"], bo, F["pD"], tol=1e-10, overlap=1, nu=2, omega=0.8)
+    out["oracle_bar_p8_100x2"] = {"iterations": its, "s_incl_setup": time.perf_counter() - t0}
+    print(json.dumps({"workload": "bar", "results": out, "clocks": clk.stop()}), flush=True)
+
+
 def run_kernel_scaling(args, ws, rank, local):
     """The hot kernels alone (CUDA events around a CUDA graph of 50 launches) on the
     config-2 tank family (32 cells deep, P = 6) with 512 ... 16384 element columns: from an
@@ -879,6 +978,8 @@ def main():
         run_tank(args, ws, rank, local)
     elif args.workload == "paper":
         run_paper(args, ws, rank, local)
+    elif args.workload == "bar":
+        run_bar(args, ws, rank, local)
     elif args.variants:
         run_variants(args, ws, rank, local)
     elif args.kernel_scaling:

@@ -13,13 +13,22 @@ exponential cut-off S(i) = 1 for i <= P_c, exp(alpha ((i - P_c)/(P + 1 - P_c))^b
 applied as F (x) F to u, w and as F to eta, followed by the mean at shared nodes.
 
 Time stepping: classical RK4, or the paper's five-stage fourth-order low-storage scheme
-(LSERK(5,4), Carpenter & Kennedy 1994).
+(LSERK(5,4), Carpenter & Kennedy 1994), with the projection above per stage or with the
+paper's mixed-stage pressure-velocity coupling (Sec. 3, Eq. rkforc1 to Eq. bcpdneu): stage k
+advances eta by the kinematic condition, forms the velocity u* of Eq. rkforc1 with every
+force except the dynamic pressure, solves the mixed-stage Poisson problem
+    int_{Omega^k} grad^k v . grad^(k-1) p = rho / (beta_k dt) int_{Omega^k} grad^k v . u*
+(the weak form of Eq. poissonp; its boundary terms are the Neumann data of Eq. bcpdneu),
+and sets u^(k) = u* - (beta_k dt / rho) grad^(k-1) p, the dynamic-pressure force of
+f(q^(k-1)) taken on the stage-(k-1) surface.
 
 Pins (tests/test_oracle_stepper.py): exact gradients of physical linear functions on a
 curved mesh; a small-amplitude wave keeps the linear dispersion relation over a period;
 the filter keeps polynomials of degree <= P_c, scales mode P by S(P), and is the
 identity for alpha = 0; LSERK(5,4) has order four on y' = lambda y (stability polynomial
-matches exp to z^4) and keeps the dispersion relation like RK4.
+matches exp to z^4) and keeps the dispersion relation like RK4; the mixed-stage coupling
+keeps still water still, keeps the dispersion relation, removes the stage-k divergence of
+u* down to the gradient-recovery error, and tracks the projection-form LSERK.
 """
 import math
 
@@ -128,6 +137,44 @@ class Tank:
             np.add.at(acc, cols, F @ np.asarray(eta)[cols])
             np.add.at(cnt, cols, 1.0)
         return acc / cnt
+
+    def rates_without_dynamic_pressure(self, eta, u, w):
+        """(eta_t, du, dw) of the sigma-frame equations with every force except grad p_D."""
+        m = self.m
+        ux, uz = self.gradient(eta, u)
+        wx, wz = self.gradient(eta, w)
+        etax = self.slope(eta)
+        ex_node = np.repeat(etax, m.NZ)
+        Fu = -(u * ux + w * uz) - G * ex_node
+        Fw = -(u * wx + w * wz)
+        top = np.arange(m.NX) * m.NZ + m.NZ - 1
+        eta_t = w[top] - u[top] * etax
+        sig = np.tile(m.row_sigma(), m.NX)
+        et_node = np.repeat(eta_t, m.NZ)
+        return eta_t, Fu + sig * et_node * uz, Fw + sig * et_node * wz
+
+    def step_lserk_mixed(self, eta, u, w, dt):
+        """LSERK(5,4) with the mixed-stage coupling of Sec. 3 (five nonsymmetric solves);
+        returns the new state and the stage pressures."""
+        m = self.m
+        dmask = m.dirichlet_mask()
+        y = [np.array(v, dtype=np.float64, copy=True) for v in (eta, u, w)]
+        K = [np.zeros_like(v) for v in y]
+        ps = []
+        for a, b in zip(LSERK54_A, LSERK54_B):
+            eta0, u0, w0 = y
+            rates = self.rates_without_dynamic_pressure(eta0, u0, w0)
+            K = [a * Kv + dt * r for Kv, r in zip(K, rates)]
+            eta1 = eta0 + b * K[0]
+            us, ws = u0 + b * K[1], w0 + b * K[2]
+            rhs = m.rhs_divergence(eta1, us, ws, scale=RHO / (b * dt))
+            p = solve_direct(m.assemble_mixed(eta1, eta0), rhs, np.zeros(m.N), dmask)
+            px, pz = self.gradient(eta0, p)
+            K[1] = K[1] - dt * px / RHO
+            K[2] = K[2] - dt * pz / RHO
+            y = [eta1, u0 + b * K[1], w0 + b * K[2]]
+            ps.append(p)
+        return y[0], y[1], y[2], ps
 
     def rates(self, eta, u, w):
         m = self.m

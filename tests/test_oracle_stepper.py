@@ -114,3 +114,56 @@ def test_small_wave_keeps_linear_dispersion_with_lserk54():
     for _ in range(steps):
         eta, u, w, _ = T.step_lserk(eta, u, w, dt)
     assert np.max(np.abs(eta - eta0)) <= 3e-3 * amp
+
+
+def test_mixed_stage_lserk_keeps_still_water_still():
+    T = Tank(dict(cells_x=4, cells_z=2, order=4, x0=0.0, x1=2.0, h=1.0, periodic=True))
+    z = np.zeros(T.m.NX), np.zeros(T.m.N), np.zeros(T.m.N)
+    eta, u, w, ps = T.step_lserk_mixed(*z, 0.01)
+    assert np.all(eta == 0.0) and np.all(u == 0.0) and np.all(w == 0.0)
+    assert all(np.all(p == 0.0) for p in ps)
+
+
+def test_small_wave_keeps_linear_dispersion_with_mixed_stage_lserk():
+    """The paper's mixed-stage coupling (Sec. 3): a small wave returns after one linear
+    period and is inverted half a period later."""
+    T = Tank(dict(cells_x=8, cells_z=2, order=6, x0=0.0, x1=2.0, h=1.0, periodic=True))
+    amp, k = 1e-4, math.pi
+    eta, u, w, om = T.linear_wave(amp, k)
+    eta0 = eta.copy()
+    steps = 60
+    dt = 2 * math.pi / om / steps
+    for _ in range(steps):
+        eta, u, w, _ = T.step_lserk_mixed(eta, u, w, dt)
+    assert np.max(np.abs(eta - eta0)) <= 3e-3 * amp
+    for _ in range(steps // 2):
+        eta, u, w, _ = T.step_lserk_mixed(eta, u, w, dt)
+    assert np.max(np.abs(eta + eta0)) <= 4e-3 * amp
+
+
+def test_mixed_stage_stage_divergence_and_projection_agreement():
+    """One mixed-stage LSERK step of a steep wave: after each stage the weak divergence on
+    that stage's surface is the gradient-recovery error of the correction, far below that
+    of u*; and the step agrees with the projection-form LSERK step (both consistent with
+    the same equations) far below the wave's own change over the step."""
+    T = Tank(dict(cells_x=8, cells_z=2, order=6, x0=0.0, x1=2.0, h=1.0, periodic=True))
+    m = T.m
+    amp, k = 0.03, math.pi
+    eta, u, w, om = T.linear_wave(amp, k)
+    dt = 2 * math.pi / om / 50
+    free = ~m.dirichlet_mask()
+    # first stage by hand: the divergence of u* and of u^(1) on the stage-1 surface
+    rates = T.rates_without_dynamic_pressure(eta, u, w)
+    b1 = LSERK54_B[0]
+    eta1 = eta + b1 * dt * rates[0]
+    us, ws = u + b1 * dt * rates[1], w + b1 * dt * rates[2]
+    div_star = np.abs(m.rhs_divergence(eta1, us, ws)[free]).max()
+    e1, u1, w1, ps = T.step_lserk_mixed(eta, u, w, dt)
+    # replay the first stage of the step to get u^(1)
+    px, pz = T.gradient(eta, ps[0])
+    u_1, w_1 = us - b1 * dt * px / 999.70, ws - b1 * dt * pz / 999.70
+    div_1 = np.abs(m.rhs_divergence(eta1, u_1, w_1)[free]).max()
+    assert div_1 < 1e-2 * div_star, (div_1, div_star)
+    e2, u2, w2, _ = T.step_lserk(eta, u, w, dt)
+    change = np.abs(e2 - eta).max()
+    assert np.abs(e1 - e2).max() < 1e-2 * change, (np.abs(e1 - e2).max(), change)

@@ -7,9 +7,15 @@ pressure folded in (p = p_D + rho g (eta - z), Sec. 2.1),
     Delta p_D = rho div F,  p_D = 0 on the surface, d p_D/dn = rho n.F elsewhere
     du/dt  = F - grad p_D / rho + sigma eta_t du/dz        (at fixed sigma, Sec. 2.2)
     eta_t  = w - u eta_x                                   (kinematic condition, Eq. freesurf1)
-advanced by the classical fourth-order Runge-Kutta method (four solves per step),
-optionally followed by the modal exponential cut-off filter of eta, u and w (Sec.
-"Spectral Filtering").  All
+advanced by the classical fourth-order Runge-Kutta method (four solves per step) or the
+paper's LSERK(5,4) (five), optionally followed by the modal exponential cut-off filter of
+eta, u and w (Sec. "Spectral Filtering").
+
+scheme="lserk54_mixed" is the paper's own mixed-stage pressure-velocity coupling (Sec. 3,
+Eq. rkforc1 to Eq. bcpdneu): stage k advances eta by the kinematic condition, forms u* of
+Eq. rkforc1 with every force except the dynamic pressure, solves the mixed-stage Poisson
+problem  int grad^k v . grad^(k-1) p = rho/(beta_k dt) int grad^k v . u*  (nonsymmetric:
+outer PDC or GMRES) and sets u^(k) = u* - (beta_k dt/rho) grad^(k-1) p.  All
 arithmetic runs in the library's kernels; this module orders the calls.  Each solve is
 warm-started from the previous stage's pressure, optionally corrected by a learned
 predictor (paper_2411_14977_gb300.warmstart).
@@ -43,10 +49,12 @@ def default_filter(P, strength=0.97, beta=8.0):
 class WaveTank:
     def __init__(self, workload, dt=None, device="cuda", predictor=None, record=False, guess_policy="residual",
                  filter=None, filter_stages=False, scheme="rk4", **solver_opts):
-        if scheme not in ("rk4", "lserk54"):
-            raise ValueError("scheme: rk4 or lserk54")
+        if scheme not in ("rk4", "lserk54", "lserk54_mixed"):
+            raise ValueError("scheme: rk4, lserk54 or lserk54_mixed")
         self.scheme = scheme
         self.w = workload
+        if scheme == "lserk54_mixed":
+            solver_opts.setdefault("outer", pmg.PMG_GMRES)  # the mixed-stage operator is nonsymmetric
         self.S = pmg.Solver(**workload.mesh_kwargs(), **solver_opts)
         S = self.S
         self.dev = torch.device(device)
@@ -58,7 +66,8 @@ class WaveTank:
         self.p = z()                        # last stage's dynamic pressure (warm start)
         self.eta_p = z(self.NX)             # the surface that pressure was solved on
         self.pD = z()                       # p_D = 0 on the surface
-        self.buf = {k: z() for k in ("ux", "uz", "wx", "wz", "Fu", "Fw", "b", "px", "pz")}
+        self.buf = {k: z() for k in ("ux", "uz", "wx", "wz", "Fu", "Fw", "b", "px", "pz", "zero", "us", "ws")}
+        self.eta_km1 = z(self.NX)           # stage-(k-1) surface of the mixed-stage coupling
         self.etax = z(self.NX)
         self.k = [(z(self.NX), z(), z()) for _ in range(4)]
         self.ys = (z(self.NX), z(), z())
@@ -102,15 +111,19 @@ class WaveTank:
             self.dt = 2 * math.pi / om / 100.0
         return om
 
-    def rates(self, eta, u, w, out):
+    def _forces(self, eta, u, w):
+        """Velocity gradients, surface slope and the forcing F on the surface eta."""
         S, B = self.S, self.buf
-        deta, du, dw = out
         S.set_geometry(eta)
         S.gradient(u, B["ux"], B["uz"])
         S.gradient(w, B["wx"], B["wz"])
         S.surface_slope(self.etax)
         S.forcing(u, w, B["ux"], B["uz"], B["wx"], B["wz"], self.etax, G, B["Fu"], B["Fw"])
-        S.assemble_rhs_div(B["Fu"], B["Fw"], RHO, out=B["b"])
+
+    def _solve(self, eta):
+        """Pressure solve of the right-hand side in buf["b"] on the operator set last, from the
+        previous pressure or the predictor's guess; the result replaces self.p."""
+        S, B = self.S, self.buf
         x0 = self.p
         if self.predictor is not None:
             # keep the network's guess only where its residual beats the previous pressure
@@ -135,13 +148,23 @@ class WaveTank:
         self.solve_infos.append(info)
         if self.record:
             self.samples.append((eta.clone(), prev[0], self.etax.clone(), prev[1], self.p.clone()))
+
+    def rates(self, eta, u, w, out):
+        S, B = self.S, self.buf
+        deta, du, dw = out
+        self._forces(eta, u, w)
+        S.assemble_rhs_div(B["Fu"], B["Fw"], RHO, out=B["b"])
+        self._solve(eta)
         S.gradient(self.p, B["px"], B["pz"])
         S.stage_rates(u, w, B["uz"], B["wz"], B["Fu"], B["Fw"], B["px"], B["pz"], self.etax, RHO, du, dw, deta)
 
     def step(self):
-        """One time step: classical RK4 (four pressure solves) or LSERK(5,4) (five)."""
+        """One time step: classical RK4 (four pressure solves) or LSERK(5,4) (five, projection
+        or mixed-stage coupling)."""
         if self.scheme == "lserk54":
             return self._step_lserk()
+        if self.scheme == "lserk54_mixed":
+            return self._step_lserk_mixed()
         S, dt = self.S, self.dt
         y = (self.eta, self.u, self.wv)
         cs = (0.5, 0.5, 1.0)
@@ -181,6 +204,39 @@ class WaveTank:
                 S.axpy(b, Kv, yy, yy)            # y <- y + b K
         if self.filter is not None:
             self._filter(y)
+        self.t += dt
+
+    def _step_lserk_mixed(self):
+        S, B, dt = self.S, self.buf, self.dt
+        K, r = self.acc, self.k[0]
+        for a, b in zip(LSERK_A, LSERK_B):
+            self.eta_km1.copy_(self.eta)
+            # f(q^(k-1)) without the dynamic pressure, on the stage-(k-1) surface
+            self._forces(self.eta, self.u, self.wv)
+            S.stage_rates(self.u, self.wv, B["uz"], B["wz"], B["Fu"], B["Fw"], B["zero"], B["zero"], self.etax, RHO,
+                          r[1], r[2], r[0])
+            for Kv, rv in zip(K, r):
+                if a == 0.0:
+                    Kv.zero_()
+                else:
+                    S.axpy(a - 1.0, Kv, Kv, Kv)      # K <- a K
+                S.axpy(dt, rv, Kv, Kv)               # K <- K + dt f
+            S.axpy(b, K[0], self.eta, self.eta)      # eta^(k)
+            S.axpy(b, K[1], self.u, B["us"])         # u* = u^(k-1) + b K
+            S.axpy(b, K[2], self.wv, B["ws"])
+            # int grad^k v . grad^(k-1) p = rho/(b dt) int grad^k v . u*
+            S.set_geometry_mixed(self.eta, self.eta_km1)
+            S.assemble_rhs_div(B["us"], B["ws"], RHO / (b * dt), out=B["b"])
+            self._solve(self.eta)
+            # K <- K - dt grad^(k-1) p / rho;  u^(k) = u^(k-1) + b K
+            S.set_geometry(self.eta_km1)
+            S.gradient(self.p, B["px"], B["pz"])
+            S.axpy(-dt / RHO, B["px"], K[1], K[1])
+            S.axpy(-dt / RHO, B["pz"], K[2], K[2])
+            S.axpy(b, K[1], self.u, self.u)
+            S.axpy(b, K[2], self.wv, self.wv)
+        if self.filter is not None:
+            self._filter((self.eta, self.u, self.wv))
         self.t += dt
 
     def _filter(self, state):

@@ -71,7 +71,10 @@ def test_filter_matches_oracle(periodic, order):
                                                              (False, (5, 2, 5), False, "rk4"),
                                                              (True, (8, 2, 6), True, "rk4"),
                                                              (True, (8, 2, 6), False, "lserk54"),
-                                                             (False, (5, 2, 5), True, "lserk54")])
+                                                             (False, (5, 2, 5), True, "lserk54"),
+                                                             (True, (8, 2, 6), False, "lserk54_mixed"),
+                                                             (False, (5, 2, 5), False, "lserk54_mixed"),
+                                                             (True, (8, 3, 4), True, "lserk54_mixed")])
 def test_steps_match_oracle(periodic, cells, filtered, scheme):
     w = wave_workload(*cells, periodic)
     amp, k = 0.03, 2 * np.pi / 2.0
@@ -89,7 +92,8 @@ def test_steps_match_oracle(periodic, cells, filtered, scheme):
     F = filter_matrix(cells[2], *flt) if filtered else None
     for _ in range(3):
         tank.step()
-        eta, u, wv, ps = (T.step if scheme == "rk4" else T.step_lserk)(eta, u, wv, dt)
+        eta, u, wv, ps = {"rk4": T.step, "lserk54": T.step_lserk, "lserk54_mixed": T.step_lserk_mixed}[scheme](
+            eta, u, wv, dt)
         if filtered:
             eta, u, wv = T.filter_surface(eta, F), T.filter_field(u, F), T.filter_field(wv, F)
     torch.cuda.synchronize()
@@ -133,3 +137,27 @@ def test_untrained_predictor_keeps_previous_pressure_and_answer():
         runs.append((n(tank.eta), [i["iterations"] for i in tank.solve_infos]))
     np.testing.assert_array_equal(runs[0][0], runs[1][0])
     assert runs[0][1] == runs[1][1]
+
+
+@pytest.mark.parametrize("precision", [pmg.PMG_FP64, pmg.PMG_MIXED_FP32])
+@pytest.mark.parametrize("outer", [pmg.PMG_GMRES, pmg.PMG_PDC])
+def test_mixed_stage_stepper_outer_methods(precision, outer):
+    """The mixed-stage coupling with either nonsymmetric outer method and precision gives
+    the oracle's state after a few steps; CG is refused by the mixed-stage operator."""
+    w = wave_workload(8, 2, 6, True)
+    amp, k = 0.03, 2 * np.pi / 2.0
+    tank = WaveTank(w, tol=1e-12, scheme="lserk54_mixed", precision=precision, outer=outer)
+    om = tank.set_linear_wave(amp, k)
+    dt = 2 * math.pi / om / 40
+    tank.dt = dt
+    T = Tank(w.mesh_kwargs())
+    eta, u, wv, _ = T.linear_wave(amp, k)
+    for _ in range(2):
+        tank.step()
+        eta, u, wv, ps = T.step_lserk_mixed(eta, u, wv, dt)
+    torch.cuda.synchronize()
+    for a, b in ((tank.eta, eta), (tank.u, u), (tank.wv, wv)):
+        assert np.abs(n(a) - b).max() / np.abs(b).max() <= 1e-9
+    assert all(i["status"] == 0 for i in tank.solve_infos)
+    with pytest.raises(pmg.PmgError):
+        WaveTank(w, dt=0.01, scheme="lserk54_mixed", outer=pmg.PMG_PCG).step()

@@ -133,3 +133,21 @@ def coarsening_sequence(P):
     if seq[-1] != 1:
         seq.append(1)
     return seq
+
+
+def semi_coarsening_sequence(P, Pz):
+    """Level order pairs (p_x, p_z) for different horizontal and vertical orders (Sec. 5.1:
+    semi-coarsening reduces the higher order until the two match).  Reading: while they
+    differ, only the higher order takes a step of the rule P_{n-1} = ceil((P_n + 1) / 2),
+    clamped so as not to fall below the other; once equal, both follow
+    `coarsening_sequence`."""
+    px, pz = int(P), int(Pz)
+    seq = [(px, pz)]
+    while px != pz:
+        if px > pz:
+            px = max(pz, int(np.ceil((px + 1) / 2.0)))
+        else:
+            pz = max(px, int(np.ceil((pz + 1) / 2.0)))
+        seq.append((px, pz))
+    seq += [(p, p) for p in coarsening_sequence(px)[1:]]
+    return seq

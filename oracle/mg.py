@@ -4,7 +4,9 @@ Test infrastructure only (see ``oracle/__init__``).
 
 Paper passages followed (Sec. 5):
   * level hierarchy: same mesh, orders P_{n-1} = ceil((P_n + 1)/2)          (Sec. 5.1)
-    (iterated down to 2, then order 1 appended: the rule's fixed point is 2)
+    (iterated down to 2, then order 1 appended: the rule's fixed point is 2); with
+    different horizontal and vertical orders, semi-coarsening of the higher one until
+    they match (`basis.semi_coarsening_sequence`)
   * each level re-discretised on the same cells ("geometric" p-MG), either on
     the actual geometry or on the flat, linearised geometry eta = 0 that makes
     the preconditioner time-constant                                        (Sec. 5, Sec. 5.4)
@@ -42,7 +44,7 @@ from .sem import Mesh, lifted_system
 
 
 class Level:
-    def __init__(self, mesh, A, overlap):
+    def __init__(self, mesh, A, overlap, overlap_z=None):
         self.mesh = mesh
         self.dmask = mesh.dirichlet_mask()
         self.free = np.flatnonzero(~self.dmask)
@@ -50,14 +52,15 @@ class Level:
         self.pos = -np.ones(mesh.N, dtype=np.int64)             # global -> free index
         self.pos[self.free] = np.arange(self.free.size)
         self.overlap = overlap
+        self.overlap_z = overlap if overlap_z is None else overlap_z
         self.blocks = None
         self.W = None
 
     def build_schwarz(self):
         """Subdomains R_i (element nodes + overlap lines, free nodes only), the dense
         Cholesky factors of R_i A R_i^T, and W = (sum R_i R_i^T)^{-1} (Sec. 5.3)."""
-        m, o = self.mesh, self.overlap
-        P = m.P
+        m, o, oz = self.mesh, self.overlap, self.overlap_z
+        P, Pz = m.P, m.Pz
         blocks = []
         count = np.zeros(self.free.size)
         for ex in range(m.Nx):
@@ -67,7 +70,7 @@ class Level:
             else:
                 xs = xs[(xs >= 0) & (xs < m.NX)]
             for ez in range(m.Nz):
-                zs = np.arange(ez * P - o, ez * P + P + o + 1)
+                zs = np.arange(ez * Pz - oz, ez * Pz + Pz + oz + 1)
                 zs = zs[(zs >= 0) & (zs < m.NZ - 1)]                  # drop the Dirichlet row
                 g = (xs[:, None] * m.NZ + zs[None, :]).reshape(-1)
                 idx = self.pos[g]
@@ -95,18 +98,27 @@ class Hierarchy:
     """
 
     def __init__(self, mesh, eta, orders=None, overlap=1, nu=2, omega=1.0, geometry='flat'):
-        self.orders = list(orders) if orders is not None else basis.coarsening_sequence(mesh.P)
-        assert self.orders[0] == mesh.P
+        """orders: x-orders of the levels (equal orders in both directions), or (p_x, p_z)
+        pairs; default: the coarsening rule, with semi-coarsening when P_z != P."""
+        if orders is None:
+            pairs = (basis.semi_coarsening_sequence(mesh.P, mesh.Pz) if mesh.Pz != mesh.P
+                     else [(p, p) for p in basis.coarsening_sequence(mesh.P)])
+        else:
+            pairs = [tuple(o) if np.ndim(o) else (int(o), int(o)) for o in orders]
+        assert pairs[0] == (mesh.P, mesh.Pz)
+        self.pairs = pairs
+        self.orders = [px for px, _ in pairs]
+        self.orders_z = [pz for _, pz in pairs]
         self.nu, self.omega = nu, omega
         self.levels = []
         self.P = []                      # prolongations level l+1 -> l on free nodes
         eta = np.asarray(eta, float)
-        for l, p in enumerate(self.orders):
-            ml = Mesh(mesh.Nx, mesh.Nz, p, mesh.x0, mesh.x1, mesh.h, mesh.periodic)
+        for l, (p, pz) in enumerate(self.pairs):
+            ml = Mesh(mesh.Nx, mesh.Nz, p, mesh.x0, mesh.x1, mesh.h, mesh.periodic, order_z=pz)
             if mesh.variable_depth:
                 probe = ml
                 h_l = self._eta_at_level(mesh, mesh.hcol, probe)
-                ml = Mesh(mesh.Nx, mesh.Nz, p, mesh.x0, mesh.x1, mesh.h, mesh.periodic, depth=h_l)
+                ml = Mesh(mesh.Nx, mesh.Nz, p, mesh.x0, mesh.x1, mesh.h, mesh.periodic, depth=h_l, order_z=pz)
             if geometry == 'flat':
                 if mesh.variable_depth:
                     A_l = ml.assemble_separable(ml.hcol)
@@ -114,7 +126,7 @@ class Hierarchy:
                     A_l = ml.assemble(np.zeros(ml.NX))
             else:
                 A_l = ml.assemble(self._eta_at_level(mesh, eta, ml))
-            lev = Level(ml, A_l, min(overlap, (p - 1) // 2))
+            lev = Level(ml, A_l, min(overlap, (p - 1) // 2), min(overlap, (pz - 1) // 2))
             if l < len(self.orders) - 1:
                 lev.build_schwarz()
             self.levels.append(lev)
@@ -145,8 +157,9 @@ class Hierarchy:
         averages identical values).
         """
         mf, mc = fine.mesh, coarse.mesh
-        J = basis.transfer_1d(mc.P, mf.P)
-        B = np.kron(J, J)                                       # (nf^2, nc^2)
+        Jx = basis.transfer_1d(mc.P, mf.P) if mc.P != mf.P else np.eye(mf.P + 1)
+        Jz = basis.transfer_1d(mc.Pz, mf.Pz) if mc.Pz != mf.Pz else np.eye(mf.Pz + 1)
+        B = np.kron(Jx, Jz)                                     # (nf_x nf_z, nc_x nc_z)
         E = mf.Nx * mf.Nz
         rows = np.repeat(mf.e2g[:, :, None], B.shape[1], axis=2).reshape(-1)
         cols = np.repeat(mc.e2g[:, None, :], B.shape[0], axis=1).reshape(-1)

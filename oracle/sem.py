@@ -12,8 +12,9 @@ pulled back to the sigma-domain by the vertical map sigma = (z + h(x))/d, d = et
 depth is given), on a structured mesh of N_x x N_z quads (Sec. 4.3) with LGL nodes.
 
 Node numbering (shared by the CUDA path's ABI, defined there independently):
-    g = ix * NZ + iz,  ix in [0, NX), iz in [0, NZ),  NZ = N_z P + 1,
+    g = ix * NZ + iz,  ix in [0, NX), iz in [0, NZ),  NZ = N_z P_z + 1,
     NX = N_x P + 1 (walls) or N_x P (periodic in x).  iz = NZ - 1 is the free surface.
+The vertical order P_z defaults to the horizontal order P (Sec. 5.1 allows them to differ).
 
 Quadrature: LGL collocation at the (P+1)^2 element nodes for stiffness, mass and
 load; the element matrices are formed densely from that definition:
@@ -39,32 +40,36 @@ from . import basis
 class Mesh:
     """Structured sigma-domain mesh: [x0, x1] x [0, 1] split into cells_x x cells_z quads."""
 
-    def __init__(self, cells_x, cells_z, order, x0=0.0, x1=1.0, h=1.0, periodic=False, depth=None):
-        """h: constant still-water depth; depth: optional still-water depth h(x) per node
+    def __init__(self, cells_x, cells_z, order, x0=0.0, x1=1.0, h=1.0, periodic=False, depth=None, order_z=None):
+        """order: polynomial order along x (P); order_z: along sigma (P_z, default P).
+        h: constant still-water depth; depth: optional still-water depth h(x) per node
         column (array of NX values, or a function of x evaluated at the node columns),
         which then replaces h everywhere."""
-        if cells_x < 1 or cells_z < 1 or order < 1:
+        order_z = order if order_z is None else order_z
+        if cells_x < 1 or cells_z < 1 or order < 1 or order_z < 1:
             raise ValueError("bad mesh")
-        self.Nx, self.Nz, self.P = int(cells_x), int(cells_z), int(order)
+        self.Nx, self.Nz, self.P, self.Pz = int(cells_x), int(cells_z), int(order), int(order_z)
         self.x0, self.x1, self.h = float(x0), float(x1), float(h)
         self.periodic = bool(periodic)
-        P = self.P
+        P, Pz = self.P, self.Pz
         self.NX = self.Nx * P + (0 if self.periodic else 1)
-        self.NZ = self.Nz * P + 1
+        self.NZ = self.Nz * Pz + 1
         self.N = self.NX * self.NZ
         self.dx = (self.x1 - self.x0) / self.Nx
         self.dsig = 1.0 / self.Nz
         self.r, self.w = basis.lgl_nodes_weights(P)
         self.D = basis.diff_matrix(P)
-        n = P + 1
-        # element -> global node map, element e = ex * Nz + ez, local node a = i * n + j
+        self.rz, self.wz = basis.lgl_nodes_weights(Pz)
+        self.Dz = basis.diff_matrix(Pz)
+        nx, nz = P + 1, Pz + 1
+        # element -> global node map, element e = ex * Nz + ez, local node a = i * (Pz + 1) + j
         ex = np.arange(self.Nx)[:, None, None, None]
         ez = np.arange(self.Nz)[None, :, None, None]
-        i = np.arange(n)[None, None, :, None]
-        j = np.arange(n)[None, None, None, :]
+        i = np.arange(nx)[None, None, :, None]
+        j = np.arange(nz)[None, None, None, :]
         ix = (ex * P + i) % self.NX if self.periodic else ex * P + i
-        iz = ez * P + j
-        self.e2g = (ix * self.NZ + iz).reshape(self.Nx * self.Nz, n * n)
+        iz = ez * Pz + j
+        self.e2g = (ix * self.NZ + iz).reshape(self.Nx * self.Nz, nx * nz)
         self.ecol = np.repeat(np.arange(self.Nx), self.Nz)
         self.erow = np.tile(np.arange(self.Nz), self.Nx)
         self.variable_depth = depth is not None
@@ -88,10 +93,10 @@ class Mesh:
 
     def row_sigma(self):
         """sigma of every node row iz (0 at the bottom, 1 at the free surface)."""
-        P = self.P
+        Pz = self.Pz
         iz = np.arange(self.NZ)
-        ez, j = np.minimum(iz // P, self.Nz - 1), iz - np.minimum(iz // P, self.Nz - 1) * P
-        return (ez + (self.r[j] + 1.0) / 2.0) * self.dsig
+        ez, j = np.minimum(iz // Pz, self.Nz - 1), iz - np.minimum(iz // Pz, self.Nz - 1) * Pz
+        return (ez + (self.rz[j] + 1.0) / 2.0) * self.dsig
 
     def node_xz(self, eta):
         """Physical (x, z) of every global node for surface elevation eta (per column)."""
@@ -111,16 +116,16 @@ class Mesh:
     def element_coords(self, eta):
         """Nodal (x, z) per element, shape (E, n, n): x* from the element's own cell,
         z = sigma d(x) - h(x) with d = eta + h sampled at the element's node columns."""
-        P, n = self.P, self.P + 1
+        P, n, nz = self.P, self.P + 1, self.Pz + 1
         eta = np.asarray(eta, float)
         xe = self.x0 + (self.ecol[:, None] + (self.r[None, :] + 1.0) / 2.0) * self.dx  # (E, n)
-        sig = (self.erow[:, None] + (self.r[None, :] + 1.0) / 2.0) * self.dsig          # (E, n)
+        sig = (self.erow[:, None] + (self.rz[None, :] + 1.0) / 2.0) * self.dsig         # (E, nz)
         cols = self.ecol[:, None] * P + np.arange(n)[None, :]
         if self.periodic:
             cols = cols % self.NX
         hc = self.hcol[cols]                                                              # (E, n)
         d = eta[cols] + hc
-        X = np.repeat(xe[:, :, None], n, axis=2)
+        X = np.repeat(xe[:, :, None], nz, axis=2)
         Z = sig[:, None, :] * d[:, :, None] - hc[:, :, None]
         return X, Z
 
@@ -131,11 +136,11 @@ class Mesh:
         r_x = z_s/J, r_z = -x_s/J, s_x = -z_r/J, s_z = x_r/J.
         """
         X, Z = self.element_coords(eta)
-        D = self.D
+        D, Dz = self.D, self.Dz
         xr = np.einsum('im,emj->eij', D, X)
-        xs = np.einsum('jm,eim->eij', D, X)
+        xs = np.einsum('jm,eim->eij', Dz, X)
         zr = np.einsum('im,emj->eij', D, Z)
-        zs = np.einsum('jm,eim->eij', D, Z)
+        zs = np.einsum('jm,eim->eij', Dz, Z)
         J = xr * zs - xs * zr
         if np.any(J <= 0):
             raise ValueError("non-positive Jacobian: eta <= -h somewhere")
@@ -144,15 +149,13 @@ class Mesh:
     def ref_gradients(self):
         """(Gr, Gs): derivatives of the element basis at the element nodes, (n^2, n^2).
 
-        Gr[(qa,qb),(i,j)] = D[qa,i] delta(qb,j);  Gs[(qa,qb),(i,j)] = delta(qa,i) D[qb,j].
+        Gr[(qa,qb),(i,j)] = D[qa,i] delta(qb,j);  Gs[(qa,qb),(i,j)] = delta(qa,i) D_z[qb,j].
         """
-        n = self.P + 1
-        I = np.eye(n)
-        return np.kron(self.D, I), np.kron(I, self.D)
+        return np.kron(self.D, np.eye(self.Pz + 1)), np.kron(np.eye(self.P + 1), self.Dz)
 
     def quad_weights(self):
         """Tensor LGL weights w_i w_j at local node (i, j), flattened."""
-        return np.outer(self.w, self.w).reshape(-1)
+        return np.outer(self.w, self.wz).reshape(-1)
 
     def element_stiffness(self, eta, elems=None):
         """Dense K_e = Gx^T diag(w J) Gx + Gz^T diag(w J) Gz for the selected elements."""
@@ -160,7 +163,7 @@ class Mesh:
         if elems is not None:
             rx, rz, sx, sz, J = rx[elems], rz[elems], sx[elems], sz[elems], J[elems]
         E = rx.shape[0]
-        nn = (self.P + 1) ** 2
+        nn = (self.P + 1) * (self.Pz + 1)
         Gr, Gs = self.ref_gradients()
         wJ = self.quad_weights()[None, :] * J.reshape(E, nn)
         Gx = rx.reshape(E, nn, 1) * Gr[None] + sx.reshape(E, nn, 1) * Gs[None]
@@ -179,7 +182,7 @@ class Mesh:
             rx, rz, sx, sz, J = rx[elems], rz[elems], sx[elems], sz[elems], J[elems]
             qx, qz, tx, tz = qx[elems], qz[elems], tx[elems], tz[elems]
         E = rx.shape[0]
-        nn = (self.P + 1) ** 2
+        nn = (self.P + 1) * (self.Pz + 1)
         Gr, Gs = self.ref_gradients()
         wJ = self.quad_weights()[None, :] * J.reshape(E, nn)
         Vx = rx.reshape(E, nn, 1) * Gr[None] + sx.reshape(E, nn, 1) * Gs[None]
@@ -234,9 +237,10 @@ class Mesh:
         if self.periodic:
             cols = cols % self.NX
         dcol = depth[cols]                                                     # (E, n): d_i
-        W = self.quad_weights().reshape(n, n)                                  # w_i w_j
-        grr = (W[None] * dcol[:, :, None] * (self.dsig / self.dx)).reshape(len(el), n * n)
-        gss = (W[None] / dcol[:, :, None] * (self.dx / self.dsig)).reshape(len(el), n * n)
+        nz = self.Pz + 1
+        W = self.quad_weights().reshape(n, nz)                                 # w_i w_j
+        grr = (W[None] * dcol[:, :, None] * (self.dsig / self.dx)).reshape(len(el), n * nz)
+        gss = (W[None] / dcol[:, :, None] * (self.dx / self.dsig)).reshape(len(el), n * nz)
         Gr, Gs = self.ref_gradients()
         return (np.einsum('qa,eq,qb->eab', Gr, grr, Gr) + np.einsum('qa,eq,qb->eab', Gs, gss, Gs))
 
@@ -269,8 +273,8 @@ class Mesh:
         Entries at Dirichlet nodes are set to zero.
         """
         rx, rz, sx, sz, J = self.element_metrics(eta)
-        E, n, P = J.shape[0], self.P + 1, self.P
-        wJ = self.quad_weights()[None, :] * J.reshape(E, n * n)
+        E, n, P, nz, Pz = J.shape[0], self.P + 1, self.P, self.Pz + 1, self.Pz
+        wJ = self.quad_weights()[None, :] * J.reshape(E, n * nz)
         b = -self.scatter(wJ * self.gather(f))
         X, Z = self.element_coords(eta)
         D = self.D
@@ -294,12 +298,12 @@ class Mesh:
                 ix = ex * P + i
                 for ez in range(self.Nz):
                     e = ex * self.Nz + ez
-                    xs = D @ X[e, i, :]
-                    zs = D @ Z[e, i, :]
+                    xs = self.Dz @ X[e, i, :]
+                    zs = self.Dz @ Z[e, i, :]
                     ds = np.sqrt(xs ** 2 + zs ** 2)
-                    for j in range(n):
-                        iz = ez * P + j
-                        b[ix * self.NZ + iz] += self.w[j] * ds[j] * gw[iz]
+                    for j in range(nz):
+                        iz = ez * Pz + j
+                        b[ix * self.NZ + iz] += self.wz[j] * ds[j] * gw[iz]
         b[self.dirichlet_mask()] = 0.0
         return b
 
@@ -310,7 +314,7 @@ class Mesh:
         n.u on walls and bottom implicitly.  Entries at Dirichlet nodes are zero.
         """
         rx, rz, sx, sz, J = self.element_metrics(eta)
-        E, nn = J.shape[0], (self.P + 1) ** 2
+        E, nn = J.shape[0], (self.P + 1) * (self.Pz + 1)
         Gr, Gs = self.ref_gradients()
         wJ = self.quad_weights()[None, :] * J.reshape(E, nn)
         Gx = rx.reshape(E, nn, 1) * Gr[None] + sx.reshape(E, nn, 1) * Gs[None]

@@ -73,8 +73,12 @@ typedef struct {
   double h;          /* still-water depth (flat bottom z = -h)                            */
   int cells_x;       /* quads in x (>= 1; >= 3 and a power of two when periodic_x)         */
   int cells_z;       /* quads in sigma (>= 1)                                              */
-  int order;         /* polynomial order P, 1..10                                          */
+  int order;         /* polynomial order P along x, 1..10                                  */
   int periodic_x;    /* 0: walls at x0, x1 (Neumann); 1: periodic in x                    */
+  int order_z;       /* polynomial order along sigma (Sec. 5.1); 0 = order.  Different orders
+                        are semi-coarsened (the higher one reduced by the level rule, not below
+                        the other, until they match) and are built for the pairs of the
+                        paper's scaling study: order_z = 8 with order 2..10                   */
 } pmg_mesh_desc;
 
 typedef struct {

@@ -142,6 +142,19 @@ std::vector<int> coarsening_sequence(int P) {
   return s;
 }
 
+std::vector<std::pair<int, int>> semi_coarsening_sequence(int P, int Pz) {
+  std::vector<std::pair<int, int>> s{{P, Pz}};
+  int px = P, pz = Pz;
+  while (px != pz) {
+    if (px > pz) px = std::max(pz, (px + 2) / 2);
+    else pz = std::max(px, (pz + 2) / 2);
+    s.push_back({px, pz});
+  }
+  std::vector<int> iso = coarsening_sequence(px);
+  for (size_t i = 1; i < iso.size(); ++i) s.push_back({iso[i], iso[i]});
+  return s;
+}
+
 void sym_eig(int n, std::vector<double> a, std::vector<double>& Q, std::vector<double>& lam) {
   Q.assign(n * n, 0.0);
   for (int i = 0; i < n; ++i) Q[i * n + i] = 1.0;

@@ -7,6 +7,7 @@
 // The generalized symmetric eigenproblems of the fast-diagonalisation Schwarz blocks are
 // solved with the cyclic Jacobi method.
 #pragma once
+#include <utility>
 #include <vector>
 
 namespace pmg {
@@ -21,6 +22,10 @@ std::vector<double> diff_matrix(int p);
 std::vector<double> transfer_matrix(int pc, int pf);
 // Level orders from the coarsening rule.
 std::vector<int> coarsening_sequence(int P);
+// Level order pairs (p_x, p_z) for different orders (Sec. 5.1 semi-coarsening): while they
+// differ, the higher one takes a step of the rule, not below the other; then both follow
+// coarsening_sequence.
+std::vector<std::pair<int, int>> semi_coarsening_sequence(int P, int Pz);
 
 // In-place Gauss-Jordan inverse of a row-major n x n matrix; false if singular.
 bool invert(int n, std::vector<double>& a);

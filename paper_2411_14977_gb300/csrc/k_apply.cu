@@ -161,6 +161,7 @@ __global__ void k_rhs_source(Shape s, const double* eta, double h, const double*
 
 template <typename T>
 cudaError_t curved_op(const CurvedArgs& a, cudaStream_t st) {
+  if (a.s.pz() != a.s.P) return curved_op_aniso<T>(a, st);
   using IO = typename IOT<T>::type;
   CurvedParams<T> p;
   p.s = a.s;

@@ -110,13 +110,17 @@ __device__ __forceinline__ void tc_contract(TcKind kind, int ntiles, GetB getb, 
 // BATHY: the same-stage operator over a varying still-water depth h(x) (Sec. 2.2) with six
 // column factors (k_geometry_bathy) [A, B, C, d_x, H = w h_x, h_x]; with s = h_x - sigma d_x:
 //   W_r = w_j (A U_r + (H - sigma B) U_s),  W_s = w_j ((H - sigma B) U_r + C (1 + s^2) U_s).
-template <int P, typename T, int MODE, int TC, bool MIX = false, bool BATHY = false>
+// PZ: polynomial order along sigma when it differs from the order P along x (Sec. 5.1);
+// the x-contractions use P + 1 nodes, the sigma-contractions PZ + 1.
+template <int P, typename T, int MODE, int TC, bool MIX = false, bool BATHY = false, int PZ = P>
 __global__ void __launch_bounds__(512) k_curved(CurvedParams<T> p) {
+  static_assert(TC == 0 || PZ == P, "tensor-core path: equal orders");
   static_assert(TC == 0 || (std::is_same<T, float>::value && MODE != MODE_DIV), "tensor-core path: FP32 operator");
   static_assert(!MIX || (TC == 0 && (MODE == MODE_APPLY || MODE == MODE_RESIDUAL)), "mixed-stage: apply/residual");
   static_assert(!BATHY || (TC == 0 && !MIX && MODE != MODE_DIV), "varying depth: CUDA-core same-stage operator");
   constexpr int NG = MIX ? 5 : (BATHY ? 6 : 4);  // column factors per node column
-  constexpr int n = P + 1;
+  constexpr int n = P + 1;    // element nodes along x
+  constexpr int nz = PZ + 1;  // along sigma
   const Shape s = p.s;
   const int NZ = s.NZ, Nz = s.Nz, NZp = slab_pitch(NZ);
   const int L = Nz * n;
@@ -124,12 +128,12 @@ __global__ void __launch_bounds__(512) k_curved(CurvedParams<T> p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* X = reinterpret_cast<T*>(smem_raw);   // [n][NZp]   input slab, later Y
   T* Ur = X + n * NZp;                      // [n][NZp]   U_r per node row
-  T* Ws = Ur + n * NZp;                     // [Nz][n][n] (ez, j, i): U_s then W_s
-  T* Wr = Ws + L * n;                       // [Nz][n][n] (ez, j, i): W_r
-  T* G = Wr + L * n;                        // [n][NG]
+  T* Ws = Ur + n * NZp;                     // [Nz][nz][n] (ez, j, i): U_s then W_s
+  T* Wr = Ws + L * nz;                      // [Nz][nz][n] (ez, j, i): W_r
+  T* G = Wr + L * nz;                       // [n][NG]
   T* SG = G + NG * n;                       // [NZ] sigma
   T* BB = SG + NZ;                          // [n][NZp] b (MODE_RESIDUAL) or x (MODE_DOT) of the slab
-  size_t red_off = (((size_t)(3 * n * NZp + 2 * L * n + NG * n + NZ) * sizeof(T)) + 15) & ~(size_t)15;
+  size_t red_off = (((size_t)(3 * n * NZp + 2 * L * nz + NG * n + NZ) * sizeof(T)) + 15) & ~(size_t)15;
   double* red = reinterpret_cast<double*>(smem_raw + red_off);  // 34 doubles
   int* s_flag = reinterpret_cast<int*>(red + 34);
   T* Y = X;
@@ -180,24 +184,24 @@ __global__ void __launch_bounds__(512) k_curved(CurvedParams<T> p) {
     // ---- phase 2: U_s along sigma, one (column i, element ez) per thread
     for (int t = threadIdx.x; t < L; t += blockDim.x) {
       int i = t % n, ez = t / n;
-      T xv[n];
+      T xv[nz];
 #pragma unroll
-      for (int m = 0; m < n; ++m) xv[m] = X[i * NZp + ez * P + m];
+      for (int m = 0; m < nz; ++m) xv[m] = X[i * NZp + ez * PZ + m];
 #pragma unroll
-      for (int j = 0; j < n; ++j) {
+      for (int j = 0; j < nz; ++j) {
         T acc = T(0);
 #pragma unroll
-        for (int m = 0; m < n; ++m) acc += CT<T>::D(cT, P, j, m) * xv[m];
-        Ws[(ez * n + j) * n + i] = acc;
+        for (int m = 0; m < nz; ++m) acc += CT<T>::D(cT, PZ, j, m) * xv[m];
+        Ws[(ez * nz + j) * n + i] = acc;
       }
     }
     }  // CUDA-core contractions
     __syncthreads();
     // ---- phase 3: pointwise metric
-    for (int t = threadIdx.x; t < L * n; t += blockDim.x) {
-      int i = t % n, r = t / n, j = r % n, ez = r / n;
-      int iz = ez * P + j;
-      T wj = CT<T>::w(cT, P, j);
+    for (int t = threadIdx.x; t < L * nz; t += blockDim.x) {
+      int i = t % n, r = t / n, j = r % nz, ez = r / nz;
+      int iz = ez * PZ + j;
+      T wj = CT<T>::w(cT, PZ, j);
       T sg = SG[iz];
       T ur = Ur[i * NZp + iz];
       T us = Ws[t];
@@ -228,10 +232,10 @@ __global__ void __launch_bounds__(512) k_curved(CurvedParams<T> p) {
     // ---- divergence load vector: W_r = w_i w_j (d dsig/2) u,
     // W_s = w_i w_j (dx/2)(w + (h_x - sigma d_x) u).  Column factors in this mode:
     // A = w_i d dsig/2, B = w_i d_x, C = w_i dx/2, H = w_i h_x (zero over a constant depth).
-    for (int t = threadIdx.x; t < L * n; t += blockDim.x) {
-      int i = t % n, r = t / n, j = r % n, ez = r / n;
-      int iz = ez * P + j;
-      T wj = CT<T>::w(cT, P, j);
+    for (int t = threadIdx.x; t < L * nz; t += blockDim.x) {
+      int i = t % n, r = t / n, j = r % nz, ez = r / nz;
+      int iz = ez * PZ + j;
+      T wj = CT<T>::w(cT, PZ, j);
       T u = X[i * NZp + iz], w = Ur[i * NZp + iz];
       Wr[t] = p.scale * wj * G[i * 4 + 0] * u;
       Ws[t] = p.scale * wj * (G[i * 4 + 2] * w + (G[i * 4 + 3] - SG[iz] * G[i * 4 + 1]) * (G[i * 4 + 2] / CT<T>::w(cT, P, i)) * u);
@@ -272,13 +276,13 @@ __global__ void __launch_bounds__(512) k_curved(CurvedParams<T> p) {
   } else {
   // ---- phase 4a: x-contraction Y[i][iz] = sum_k D[k][i] sum_{ez owning iz} W_r
   for (int iz = threadIdx.x; iz < NZ; iz += blockDim.x) {
-    int ez = min(iz / P, Nz - 1), j = iz - ez * P;
+    int ez = min(iz / PZ, Nz - 1), j = iz - ez * PZ;
     T wv[n];
 #pragma unroll
-    for (int k = 0; k < n; ++k) wv[k] = Wr[(ez * n + j) * n + k];
+    for (int k = 0; k < n; ++k) wv[k] = Wr[(ez * nz + j) * n + k];
     if (j == 0 && ez > 0) {
 #pragma unroll
-      for (int k = 0; k < n; ++k) wv[k] += Wr[((ez - 1) * n + P) * n + k];
+      for (int k = 0; k < n; ++k) wv[k] += Wr[((ez - 1) * nz + PZ) * n + k];
     }
 #pragma unroll
     for (int i = 0; i < n; ++i) {
@@ -289,28 +293,28 @@ __global__ void __launch_bounds__(512) k_curved(CurvedParams<T> p) {
     }
   }
   __syncthreads();
-  // ---- phase 4b: sigma-contraction of the rows [ez P, ez P + P) owned by (i, ez)
+  // ---- phase 4b: sigma-contraction of the rows [ez PZ, ez PZ + PZ) owned by (i, ez)
   for (int t = threadIdx.x; t < L; t += blockDim.x) {
     int i = t % n, ez = t / n;
-    T wv[n];
+    T wv[nz];
 #pragma unroll
-    for (int k = 0; k < n; ++k) wv[k] = Ws[(ez * n + k) * n + i];
+    for (int k = 0; k < nz; ++k) wv[k] = Ws[(ez * nz + k) * n + i];
     T below = T(0);
     if (ez > 0) {
 #pragma unroll
-      for (int k = 0; k < n; ++k) below += CT<T>::D(cT, P, k, P) * Ws[((ez - 1) * n + k) * n + i];
+      for (int k = 0; k < nz; ++k) below += CT<T>::D(cT, PZ, k, PZ) * Ws[((ez - 1) * nz + k) * n + i];
     }
 #pragma unroll
-    for (int j = 0; j < P; ++j) {
+    for (int j = 0; j < PZ; ++j) {
       T acc = (j == 0) ? below : T(0);
 #pragma unroll
-      for (int k = 0; k < n; ++k) acc += CT<T>::D(cT, P, k, j) * wv[k];
-      Y[i * NZp + ez * P + j] += acc;
+      for (int k = 0; k < nz; ++k) acc += CT<T>::D(cT, PZ, k, j) * wv[k];
+      Y[i * NZp + ez * PZ + j] += acc;
     }
     if (ez == Nz - 1) {  // surface row: used by MODE_DIV only (masked otherwise)
       T acc = T(0);
 #pragma unroll
-      for (int k = 0; k < n; ++k) acc += CT<T>::D(cT, P, k, P) * wv[k];
+      for (int k = 0; k < nz; ++k) acc += CT<T>::D(cT, PZ, k, PZ) * wv[k];
       Y[i * NZp + NZ - 1] += acc;
     }
   }
@@ -366,16 +370,16 @@ __global__ void __launch_bounds__(512) k_curved(CurvedParams<T> p) {
 }
 
 template <typename T>
-static size_t curved_smem(int P, int NZ, int Nz, int ng = 4) {
-  int n = P + 1, NZp = slab_pitch(NZ), L = Nz * n;
-  size_t e = (size_t)3 * n * NZp + (size_t)2 * L * n + (size_t)ng * n + NZ;
+static size_t curved_smem(int P, int NZ, int Nz, int ng = 4, int PZ = -1) {
+  int n = P + 1, nz = (PZ < 0 ? P : PZ) + 1, NZp = slab_pitch(NZ), L = Nz * n;
+  size_t e = (size_t)3 * n * NZp + (size_t)2 * L * nz + (size_t)ng * n + NZ;
   return ((e * sizeof(T) + 15) & ~(size_t)15) + 34 * sizeof(double) + 16;
 }
 
-template <int P, typename T, int MODE, int TC, bool MIX = false, bool BATHY = false>
+template <int P, typename T, int MODE, int TC, bool MIX = false, bool BATHY = false, int PZ = P>
 static cudaError_t launch_curved_p(const CurvedParams<T>& prm, int threads, cudaStream_t st) {
-  size_t sm = curved_smem<T>(P, prm.s.NZ, prm.s.Nz, MIX ? 5 : (BATHY ? 6 : 4));
-  auto k = k_curved<P, T, MODE, TC, MIX, BATHY>;
+  size_t sm = curved_smem<T>(P, prm.s.NZ, prm.s.Nz, MIX ? 5 : (BATHY ? 6 : 4), PZ);
+  auto k = k_curved<P, T, MODE, TC, MIX, BATHY, PZ>;
   static std::atomic<unsigned long long> s_mask{0};
   cudaError_t e = ensure_max_smem(k, s_mask);
   if (e != cudaSuccess) return e;

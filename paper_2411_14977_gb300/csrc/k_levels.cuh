@@ -1,0 +1,369 @@
+// Level-operator and Schwarz-sweep kernel templates (Sec. 5.3), shared by k_levels.cu
+// (equal orders) and k_levels_aniso.cu (different orders along x and sigma).  The
+// including translation unit defines the constant tables cT first.
+#pragma once
+
+namespace pmg {
+
+// ------------------------------------------------------------------------------------
+// level operator / residual
+// ------------------------------------------------------------------------------------
+template <typename T>
+struct FlatParams {
+  Shape s;
+  const T* x;
+  const T* b;
+  T* y;
+  T cx, cz;
+  const T* mX;  // [NX] assembled weights along x
+  const T* mZ;  // [NZ]
+  int residual; // 0: y = A x (surface row y = x); 1: y = b - A x (surface row 0)
+  const T* Kx;  // VAR: [Nx][n][n] x-stiffness of each element column (cx folded in)
+};
+
+// Level operator A = cx K_X (x) M_Z + cz M_X (x) K_Z (the flat level of Sec. 5, a Kronecker
+// sum).  VAR: over a varying depth the level keeps each node column's depth d and drops
+// the bottom-slope terms, A = K_X[d] (x) M_Z + M_X[1/d] (x) K_Z, with the element x-stiffness
+// (dsig/dx) D^T diag(w d) D of each element column in Kx and (dx/dsig) M_X[1/d] in mX
+// (cx = cz = 1): still a Kronecker sum, so the same kernels apply.
+template <int P, typename T, bool VAR>
+__device__ __forceinline__ T kx_coef(const T* KE, int i, int m) {
+  if constexpr (VAR) return KE[i * (P + 1) + m];
+  else return CT<T>::K(cT, P, i, m);
+}
+
+// PZ: order along sigma when it differs from P (the z stencils use PZ + 1 nodes).
+template <int P, typename T, bool VAR, int PZ = P>
+__global__ void __launch_bounds__(512) k_flat(FlatParams<T> p) {
+  constexpr int n = P + 1;
+  const Shape s = p.s;
+  const int NZ = s.NZ, Nz = s.Nz, NZp = slab_pitch(NZ);
+  const int ex = blockIdx.x, col0 = ex * P;
+  const bool left = s.periodic || ex > 0;
+  const bool last = !s.periodic && ex == s.Nx - 1;
+  const int own = last ? n : P;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* X = reinterpret_cast<T*>(smem_raw);  // [2P+1][NZp], local column c <-> col0 - P + c
+  T* Y = X + (2 * P + 1) * NZp;            // [n][NZp]
+  T* MZ = Y + n * NZp;                     // [NZ] cx * assembled weights along z
+  T* MX = MZ + NZ;                         // [n]  cz * assembled weights along x (own columns)
+  T* B = MX + n;                           // [n][NZp] right-hand side of the own columns
+  T* KO = B + n * NZp;                     // VAR: [n][n] own element's x-stiffness
+  T* KL = KO + n * n;                      // VAR: [n] last row of the left element's
+  const int c_begin = left ? 0 : P;
+  if constexpr (VAR) {
+    const T* ko = p.Kx + (size_t)ex * n * n;
+    const T* kl = p.Kx + (size_t)(left ? (ex == 0 ? s.Nx - 1 : ex - 1) : ex) * n * n + P * n;
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) KO[t] = ko[t];
+    if (threadIdx.x < n) KL[threadIdx.x] = kl[threadIdx.x];
+  }
+  for_slab(2 * P + 1, NZ, [&](int c, int iz) {
+    bool ok = c >= c_begin && iz != NZ - 1;
+    cp_async_elem(&X[c * NZp + iz], p.x + (ok ? (size_t)wrap_col(s, col0 - P + c) * NZ + iz : 0), ok);
+  });
+  if (p.residual)
+    for_slab(own, NZ, [&](int i, int iz) { cp_async_elem(&B[i * NZp + iz], p.b + (size_t)(col0 + i) * NZ + iz, true); });
+  for (int t = threadIdx.x; t < NZ; t += blockDim.x) MZ[t] = p.cx * p.mZ[t];
+  if (threadIdx.x < own) MX[threadIdx.x] = p.cz * p.mX[wrap_col(s, col0 + threadIdx.x)];
+  cp_async_wait_all();
+  __syncthreads();
+  // x-direction stencils, one node row per thread
+  for (int iz = threadIdx.x; iz < NZ; iz += blockDim.x) {
+    T xo[n], xl[n];
+#pragma unroll
+    for (int m = 0; m < n; ++m) { xo[m] = X[(P + m) * NZp + iz]; xl[m] = X[m * NZp + iz]; }
+    T f = MZ[iz];
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+      if (i == P && !last) break;
+      T acc = T(0);
+#pragma unroll
+      for (int m = 0; m < n; ++m) acc += kx_coef<P, T, VAR>(KO, i, m) * xo[m];
+      if (i == 0 && left) {  // the left element's share of the shared first column
+#pragma unroll
+        for (int m = 0; m < n; ++m) acc += (VAR ? KL[m] : CT<T>::K(cT, P, P, m)) * xl[m];
+      }
+      Y[i * NZp + iz] = f * acc;
+    }
+  }
+  __syncthreads();
+  // z-direction stencils, one (column, element row) per thread, owning rows [ez PZ, ez PZ + PZ)
+  constexpr int nz = PZ + 1;
+  for (int t = threadIdx.x; t < own * Nz; t += blockDim.x) {
+    int ez = t / own, i = t - ez * own;
+    const T* col = X + (P + i) * NZp;
+    T xv[nz];
+#pragma unroll
+    for (int m = 0; m < nz; ++m) xv[m] = col[ez * PZ + m];
+    T below = T(0);
+    if (ez > 0) {
+#pragma unroll
+      for (int m = 0; m < nz; ++m) below += CT<T>::K(cT, PZ, PZ, m) * col[(ez - 1) * PZ + m];
+    }
+    T f = MX[i];
+#pragma unroll
+    for (int j = 0; j < PZ; ++j) {
+      T acc = (j == 0) ? below : T(0);
+#pragma unroll
+      for (int m = 0; m < nz; ++m) acc += CT<T>::K(cT, PZ, j, m) * xv[m];
+      Y[i * NZp + ez * PZ + j] += f * acc;
+    }
+  }
+  __syncthreads();
+  const size_t base = (size_t)col0 * NZ;
+  for_slab(own, NZ, [&](int i, int iz) {
+    size_t g = base + (size_t)i * NZ + iz;
+    bool top = iz == NZ - 1;
+    T v = Y[i * NZp + iz];
+    if (p.residual) p.y[g] = top ? T(0) : B[i * NZp + iz] - v;
+    else p.y[g] = top ? p.x[g] : v;
+  });
+}
+
+// The same level operator node-parallel: one thread per node reads its x- and z-stencil
+// neighbours straight from global memory (L1/L2 serve the reuse), no shared memory and no
+// barriers, so a CTA's critical path is one load wave and ~2(P+1) FMAs.
+template <int P, typename T, bool VAR, int PZ = P>
+__global__ void __launch_bounds__(256) k_flat_np(FlatParams<T> p) {
+  constexpr int n = P + 1;
+  const Shape s = p.s;
+  const int NZ = s.NZ, Nz = s.Nz;
+  const size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (g >= (size_t)s.NX * NZ) return;
+  const int ix = (int)(g / NZ), iz = (int)(g - (size_t)ix * NZ);
+  if (iz == NZ - 1) {
+    p.y[g] = p.residual ? T(0) : p.x[g];
+    return;
+  }
+  // x stencil: the element(s) of column ix (the wall side has one)
+  const int ex = min(ix / P, s.Nx - 1), i = ix - ex * P;
+  const T* ko = VAR ? p.Kx + (size_t)ex * n * n : nullptr;
+  T ax = T(0);
+#pragma unroll
+  for (int m = 0; m < n; ++m) ax += kx_coef<P, T, VAR>(ko, i, m) * p.x[(size_t)wrap_col(s, ex * P + m) * NZ + iz];
+  if (i == 0 && (s.periodic || ex > 0)) {
+    const T* kl = VAR ? p.Kx + (size_t)(ex == 0 ? s.Nx - 1 : ex - 1) * n * n : nullptr;
+#pragma unroll
+    for (int m = 0; m < n; ++m) ax += kx_coef<P, T, VAR>(kl, P, m) * p.x[(size_t)wrap_col(s, (ex - 1) * P + m) * NZ + iz];
+  }
+  // z stencil along the column (the surface row of x is read as zero)
+  const T* col = p.x + (size_t)ix * NZ;
+  const int ez = min(iz / PZ, Nz - 1), j = iz - ez * PZ;
+  T az = T(0);
+#pragma unroll
+  for (int m = 0; m <= PZ; ++m) {
+    int r = ez * PZ + m;
+    az += CT<T>::K(cT, PZ, j, m) * (r == NZ - 1 ? T(0) : col[r]);
+  }
+  if (j == 0 && ez > 0) {
+#pragma unroll
+    for (int m = 0; m <= PZ; ++m) az += CT<T>::K(cT, PZ, PZ, m) * col[(ez - 1) * PZ + m];
+  }
+  T v = p.cx * p.mZ[iz] * ax + p.cz * p.mX[ix] * az;
+  p.y[g] = p.residual ? p.b[g] - v : v;
+}
+
+template <int P, typename T, bool VAR, int PZ = P>
+static cudaError_t launch_flat_p(const FlatParams<T>& prm, int threads, cudaStream_t st) {
+  if (threads < 0) {  // node-parallel variant, -threads per CTA
+    size_t N = (size_t)prm.s.NX * prm.s.NZ;
+    int bs = -threads;
+    k_flat_np<P, T, VAR, PZ><<<(unsigned)((N + bs - 1) / bs), bs, 0, st>>>(prm);
+    return cudaGetLastError();
+  }
+  int NZp = slab_pitch(prm.s.NZ);
+  size_t sm = ((size_t)((2 * P + 1) + 2 * (P + 1)) * NZp + prm.s.NZ + P + 1 + (VAR ? (P + 1) * (P + 2) : 0)) * sizeof(T);
+  auto k = k_flat<P, T, VAR, PZ>;
+  static std::atomic<unsigned long long> s_mask{0};
+  cudaError_t e = ensure_max_smem(k, s_mask);
+  if (e != cudaSuccess) return e;
+  k<<<prm.s.Nx, threads, sm, st>>>(prm);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------
+// Schwarz smoother by fast diagonalisation
+// ------------------------------------------------------------------------------------
+template <typename T>
+struct FdmParams {
+  Shape s;
+  const T* r;       // residual b - A x
+  T* x;             // updated in place
+  int post;         // 0: x += omega W sum R^T A^-1 R r;  1: x += omega sum R^T A^-1 R W r
+  T omega;
+  const T* Vx;      // [4][NB][NB]  (a, alpha): class x-eigenvectors in the padded local frame
+  const T* Vz;      // [4][NBZ][NBZ]  (b, beta)
+  const T* invden;  // [4][4][NB][NBZ] (xcls, zcls, alpha, beta): 1/(cx lx + cz lz), 0 if padded
+  const T* wx;      // [NX] inverse 1D cover counts
+  const T* wz;      // [NZ]
+  Scratch sc;
+  int xpercol;      // Vx [Nx][NB][NB] and invden [Nx][4][NB][NB]: one x-class per element column
+};
+
+__device__ __forceinline__ int xclass(const Shape& s, int ex) {
+  if (s.periodic) return 0;
+  return (ex == 0 ? 1 : 0) | (ex == s.Nx - 1 ? 2 : 0);
+}
+__device__ __forceinline__ int zclass(const Shape& s, int ez) {
+  return (ez == 0 ? 1 : 0) | (ez == s.Nz - 1 ? 2 : 0);
+}
+
+// PZ, OZ: order and overlap along sigma when they differ from P, O.  Subdomain blocks are
+// NBX = P + 1 + 2 O node lines along x by NBZ = PZ + 1 + 2 OZ along sigma.
+template <int P, int O, typename T, int PZ = P, int OZ = O>
+__global__ void __launch_bounds__(256) k_fdm(FdmParams<T> p) {
+  constexpr int NB = P + 1 + 2 * O;     // along x
+  constexpr int NBZ = PZ + 1 + 2 * OZ;  // along sigma
+  const Shape s = p.s;
+  const int NZ = s.NZ, Nz = s.Nz, NZp = slab_pitch(NZ);
+  const int ex = blockIdx.x, col0 = ex * P;
+  const int xc = p.xpercol ? ex : xclass(s, ex);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* R = reinterpret_cast<T*>(smem_raw);  // [NB][NZp]  input, later U
+  T* T1 = R + NB * NZp;                    // [NB][NZp]  x-transformed rows
+  T* T3 = T1 + NB * NZp;                   // [Nz][NBZ][NB] (ez, b, alpha)
+  T* VX = T3 + Nz * NBZ * NB;              // [NB][NB]
+  T* VZ = VX + NB * NB;                     // [4][NBZ][NBZ]
+  T* ID = VZ + 4 * NBZ * NBZ;              // [4][NB][NBZ]
+  T* XS = ID + 4 * NB * NBZ;               // [NB][NZp] x on the subdomain columns (prefetched)
+  size_t red_off = (((size_t)(3 * NB * NZp + Nz * NBZ * NB + NB * NB + 4 * NBZ * NBZ + 4 * NB * NBZ) * sizeof(T)) +
+                    15) & ~(size_t)15;
+  int* s_flag = reinterpret_cast<int*>(smem_raw + red_off);
+
+  for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) VX[t] = p.Vx[xc * NB * NB + t];
+  for (int t = threadIdx.x; t < 4 * NBZ * NBZ; t += blockDim.x) VZ[t] = p.Vz[t];
+  for (int t = threadIdx.x; t < 4 * NB * NBZ; t += blockDim.x) ID[t] = p.invden[xc * 4 * NB * NBZ + t];
+  for_slab(NB, NZ, [&](int a, int iz) {
+    int gc = col0 - O + a;
+    bool ok = col_valid(s, gc) && iz != NZ - 1;
+    size_t g = ok ? (size_t)wrap_col(s, gc) * NZ + iz : 0;
+    cp_async_elem(&R[a * NZp + iz], p.r + g, ok);
+    cp_async_elem(&XS[a * NZp + iz], p.x + g, ok);
+  });
+  cp_async_wait_all();
+  __syncthreads();
+  if (p.post)
+    for_slab(NB, NZ, [&](int a, int iz) {
+      int gc = col0 - O + a;
+      if (col_valid(s, gc)) {
+        int c = wrap_col(s, gc);
+        R[a * NZp + iz] *= p.wx[c] * p.wz[iz];
+      }
+    });
+  __syncthreads();
+  // phase 1: T1[alpha][iz] = sum_a Vx[a][alpha] R[a][iz]
+  for (int iz = threadIdx.x; iz < NZ; iz += blockDim.x) {
+    T rv[NB];
+#pragma unroll
+    for (int a = 0; a < NB; ++a) rv[a] = R[a * NZp + iz];
+#pragma unroll
+    for (int al = 0; al < NB; ++al) {
+      T acc = T(0);
+#pragma unroll
+      for (int a = 0; a < NB; ++a) acc += VX[a * NB + al] * rv[a];
+      T1[al * NZp + iz] = acc;
+    }
+  }
+  __syncthreads();
+  // phase 2: per (alpha, ez): sigma transform, diagonal solve, inverse sigma transform
+  for (int t = threadIdx.x; t < NB * Nz; t += blockDim.x) {
+    int al = t % NB, ez = t / NB;
+    int zc = zclass(s, ez);
+    const T* vz = VZ + zc * NBZ * NBZ;
+    const T* idn = ID + (zc * NB + al) * NBZ;
+    T tz[NBZ];
+#pragma unroll
+    for (int b = 0; b < NBZ; ++b) {
+      int iz = ez * PZ - OZ + b;
+      tz[b] = (iz >= 0 && iz < NZ - 1) ? T1[al * NZp + iz] : T(0);
+    }
+    T t2[NBZ];
+#pragma unroll
+    for (int be = 0; be < NBZ; ++be) {
+      T acc = T(0);
+#pragma unroll
+      for (int b = 0; b < NBZ; ++b) acc += vz[b * NBZ + be] * tz[b];
+      t2[be] = acc * idn[be];
+    }
+#pragma unroll
+    for (int b = 0; b < NBZ; ++b) {
+      T acc = T(0);
+#pragma unroll
+      for (int be = 0; be < NBZ; ++be) acc += vz[b * NBZ + be] * t2[be];
+      T3[(ez * NBZ + b) * NB + al] = acc;
+    }
+  }
+  __syncthreads();
+  // phase 3: per row, sum the covering elements, inverse x transform -> U[a][iz] (in R)
+  T* U = R;
+  for (int iz = threadIdx.x; iz < NZ; iz += blockDim.x) {
+    T sv[NB];
+#pragma unroll
+    for (int al = 0; al < NB; ++al) sv[al] = T(0);
+    int e0 = (iz + OZ) / PZ;
+#pragma unroll
+    for (int d = -2; d <= 0; ++d) {
+      int ez = e0 + d;
+      if (ez < 0 || ez >= Nz) continue;
+      int b = iz - ez * PZ + OZ;
+      if (b < 0 || b >= NBZ) continue;
+#pragma unroll
+      for (int al = 0; al < NB; ++al) sv[al] += T3[(ez * NBZ + b) * NB + al];
+    }
+#pragma unroll
+    for (int a = 0; a < NB; ++a) {
+      T acc = T(0);
+#pragma unroll
+      for (int al = 0; al < NB; ++al) acc += VX[a * NB + al] * sv[al];
+      U[a * NZp + iz] = acc;
+    }
+  }
+  __syncthreads();
+  // phase 4: x update; owned interior columns directly, the two zones by exchange
+  auto upd = [&](int a, int iz, T u) {  // local column a <-> global col0 - O + a
+    if (iz == NZ - 1) return;
+    int c = wrap_col(s, col0 - O + a);
+    size_t g = (size_t)c * NZ + iz;
+    T w = p.post ? T(1) : p.wx[c] * p.wz[iz];
+    p.x[g] = XS[a * NZp + iz] + p.omega * w * u;
+  };
+  for_slab(P - 1 - 2 * O, NZ, [&](int c, int iz) {
+    int a = 2 * O + 1 + c;
+    upd(a, iz, U[a * NZp + iz]);
+  });
+  constexpr int ZW = 2 * O + 1;
+  T* eb = reinterpret_cast<T*>(p.sc.edgebuf);
+#pragma unroll 1
+  for (int side = 0; side < 2; ++side) {
+    int a0 = side == 0 ? 0 : P;
+    int e = side == 0 ? ex : (s.periodic ? (ex + 1) % s.Nx : ex + 1);
+    bool single = !s.periodic && (e == 0 || e == s.Nx);
+    int gbase = e * P - O;
+    if (single) {
+      for_slab(ZW, NZ, [&](int c, int iz) {
+        if (col_valid(s, gbase + c)) upd(a0 + c, iz, U[(a0 + c) * NZp + iz]);
+      });
+    } else {
+      T* buf = eb + (size_t)e * ZW * NZ;
+      for_slab(ZW, NZ, [&](int c, int iz) { atomic_add_t(buf + c * NZ + iz, U[(a0 + c) * NZp + iz]); });
+      if (!edge_arrive(p.sc.edgecnt + e, 2, s_flag)) continue;
+      for_slab(ZW, NZ, [&](int c, int iz) { upd(a0 + c, iz, take_t(buf + c * NZ + iz)); });
+    }
+  }
+}
+
+template <int P, int O, typename T, int PZ = P, int OZ = O>
+static cudaError_t launch_fdm_p(const FdmParams<T>& prm, int threads, cudaStream_t st) {
+  constexpr int NB = P + 1 + 2 * O, NBZ = PZ + 1 + 2 * OZ;
+  int NZp = slab_pitch(prm.s.NZ);
+  size_t elems = (size_t)3 * NB * NZp + (size_t)prm.s.Nz * NBZ * NB + NB * NB + 4 * NBZ * NBZ + 4 * NB * NBZ;
+  size_t sm = ((elems * sizeof(T) + 15) & ~(size_t)15) + 16;
+  auto k = k_fdm<P, O, T, PZ, OZ>;
+  static std::atomic<unsigned long long> s_mask{0};
+  cudaError_t e = ensure_max_smem(k, s_mask);
+  if (e != cudaSuccess) return e;
+  k<<<prm.s.Nx, threads, sm, st>>>(prm);
+  return cudaGetLastError();
+}
+
+}  // namespace pmg

@@ -87,12 +87,14 @@ extern "C" pmg_status pmg_apply_noalloc(const pmg_mesh_desc* mesh, const double*
   }
   const pmg_mesh_desc& m = *mesh;
   if (m.order < 1 || m.order > MAXP || m.cells_x < 1 || m.cells_z < 1 || !(m.x1 > m.x0) || !(m.h > 0.0) ||
-      (m.periodic_x && m.cells_x < 3)) {
-    set_last_error("bad mesh descriptor (order 1..10, cells >= 1, x1 > x0, h > 0, periodic needs cells_x >= 3)");
+      (m.periodic_x && m.cells_x < 3) || (m.order_z != 0 && m.order_z != m.order)) {
+    set_last_error("bad mesh descriptor (order 1..10, cells >= 1, x1 > x0, h > 0, periodic needs cells_x >= 3, "
+                   "order_z 0 or order)");
     return PMG_ERR_INVALID;
   }
-  Shape F;
+  Shape F{};
   F.P = m.order;
+  F.PZ = m.order;
   F.Nx = m.cells_x;
   F.Nz = m.cells_z;
   F.periodic = m.periodic_x;

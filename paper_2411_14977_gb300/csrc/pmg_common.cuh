@@ -153,6 +153,8 @@ struct Scratch {
 // Mesh shape of one level.
 struct Shape {
   int NX, NZ, Nx, Nz, P, periodic;
+  int PZ;  // order along sigma when it differs from P (0: equal orders)
+  __host__ __device__ int pz() const { return PZ > 0 ? PZ : P; }
 };
 
 __device__ __forceinline__ int wrap_col(const Shape& s, int c) {

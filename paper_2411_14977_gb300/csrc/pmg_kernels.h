@@ -37,6 +37,8 @@ cudaError_t init_consts_levels(const ConstTables* host);
 cudaError_t init_consts_fdm32(const float* table, size_t n, const float* K, size_t nk);
 cudaError_t init_consts_stepper(const ConstTables* host);
 cudaError_t init_consts_apply_bathy(const ConstTables* host);
+cudaError_t init_consts_apply_aniso(const ConstTables* host);
+cudaError_t init_consts_levels_aniso(const ConstTables* host);
 
 // Layout of the FP32 Schwarz eigenvector table (constant memory of the FP32 smoother):
 // for every (P, O) with 2 <= P <= MAXP and O <= (P-1)/2, eight NB x NB blocks
@@ -133,8 +135,20 @@ struct FdmArgs {
   const void* mX = nullptr;
   const void* mZ = nullptr;
   int xpercol = 0;  // generic sweep: Vx / invden hold one x-class per element column
+  int overlap_z = -1;  // overlap along sigma (-1: overlap)
 };
 template <typename T> cudaError_t fdm_smooth(const FdmArgs& a, cudaStream_t st);
+// Level operator, generic sweep and actual-geometry operator for different orders along x
+// and sigma (s.pz() != s.P): the pairs of the paper's scaling study (k_levels_aniso.cu,
+// k_apply_aniso.cu); other pairs return cudaErrorInvalidValue.
+template <typename T> cudaError_t flat_op_aniso(const FlatArgs& a, cudaStream_t st);
+template <typename T> cudaError_t fdm_smooth_aniso(const FdmArgs& a, cudaStream_t st);
+template <typename T> cudaError_t curved_op_aniso(const CurvedArgs& a, cudaStream_t st);
+bool aniso_pair_supported(int P, int PZ, bool fine);
+// (P, PZ) pairs with kernels: the finest levels of the scaling study (order_z = 8) and the
+// levels that its semi-coarsening visits
+#define PMG_ANISO_FINE(X) X(2, 8) X(3, 8) X(4, 8) X(5, 8) X(6, 8) X(7, 8) X(9, 8) X(10, 8)
+#define PMG_ANISO_COARSE(X) X(2, 5) X(3, 5) X(4, 5) X(2, 3)
 // FP32 sweep with the eigenvectors in constant memory (k_fdm32.cu)
 cudaError_t fdm_smooth32(const FdmArgs& a, cudaStream_t st);
 
@@ -142,7 +156,7 @@ struct TransferArgs {
   Shape f, c;
   const void* in;
   void* out;
-  const double* J;
+  const double* J;     // transfer along x, [(Pf+1)][(Pc+1)]
   int threads = 256;
   // restriction only: with xf set, `in` is the fine right-hand side and the kernel
   // restricts r = in - A_f xf (flat level operator cx, cz, assembled weights mX, mZ)
@@ -150,7 +164,7 @@ struct TransferArgs {
   double cx = 0.0, cz = 0.0;
   const void* mX = nullptr;
   const void* mZ = nullptr;
-  int xpercol = 0;  // generic sweep: Vx / invden hold one x-class per element column
+  const double* Jz = nullptr;  // transfer along sigma when the orders differ (NULL: J)
 };
 template <typename T> cudaError_t transfer(const TransferArgs& a, int restrict_, cudaStream_t st);
 

@@ -101,6 +101,8 @@ pmg_status ensure_constants(int dev) {
   CK(init_consts_levels(&t));
   CK(init_consts_stepper(&t));
   CK(init_consts_apply_bathy(&t));
+  CK(init_consts_apply_aniso(&t));
+  CK(init_consts_levels_aniso(&t));
   {
     std::vector<float> tab(fdm32_table_size(), 0.f);
     for (int P = 2; P <= MAXP; ++P)
@@ -219,6 +221,9 @@ T* upload(const std::vector<double>& v, std::vector<void*>& allocs, cudaError_t&
 
 struct LevelDev {
   int order = 0, overlap = 0;
+  int order_z = 0, overlap_z = 0;  // along sigma (equal to order / overlap unless semi-coarsened)
+  bool aniso = false;              // different orders along x and sigma
+  double* Jz = nullptr;            // transfer from level l+1 along sigma (J when the orders agree)
   Shape s{};
   void* mX[2]{};
   void* mZ[2]{};
@@ -252,7 +257,8 @@ struct pmg_handle {
   bool df64_outer = false;  // outer operator in double-float arithmetic (FP64 in and out)
   double dx = 0, dsig = 0, cx = 0, cz = 0;
   size_t N = 0, Nfree = 0;
-  std::vector<int> orders;
+  std::vector<int> orders, orders_z;  // level orders along x and along sigma
+  bool aniso = false;                 // the finest orders differ (Sec. 5.1 semi-coarsening)
   std::vector<LevelDev> lv;
   std::vector<void*> allocs;
   std::vector<double> xcols, sigrows;
@@ -367,19 +373,22 @@ pmg_status launch(pmg_handle* h, int cls, int nkernels, cudaStream_t st, F&& f) 
 pmg_status build_level(pmg_handle* h, int l) {
   LevelDev& L = h->lv[l];
   const pmg_mesh_desc& m = h->mesh;
-  int p = h->orders[l];
+  int p = h->orders[l], pz = h->orders_z[l];
   L.order = p;
-  L.fuse_res = h->opts.fuse_residual == 1;
+  L.order_z = pz;
+  L.aniso = pz != p;
+  L.fuse_res = h->opts.fuse_residual == 1 && !L.aniso;
   if (h->opts.flat_kernel == 1) L.thr_flat32 = -128;
-  L.fuse_restrict = h->opts.fuse_residual == 1;
+  L.fuse_restrict = h->opts.fuse_residual == 1 && !L.aniso;
   L.s.P = p;
+  L.s.PZ = pz;
   L.s.Nx = m.cells_x;
   L.s.Nz = m.cells_z;
   L.s.periodic = m.periodic_x;
   L.s.NX = m.cells_x * p + (m.periodic_x ? 0 : 1);
-  L.s.NZ = m.cells_z * p + 1;
+  L.s.NZ = m.cells_z * pz + 1;
   size_t NL = (size_t)L.s.NX * L.s.NZ;
-  Line1D lx(p, m.cells_x, m.periodic_x), lz(p, m.cells_z, 0);
+  Line1D lx(p, m.cells_x, m.periodic_x), lz(pz, m.cells_z, 0);
   std::vector<double> mX(L.s.NX), mZ(L.s.NZ);
   for (int a = 0; a < L.s.NX; ++a) mX[a] = lx.M(a);
   for (int a = 0; a < L.s.NZ; ++a) mZ[a] = lz.M(a);
@@ -399,12 +408,15 @@ pmg_status build_level(pmg_handle* h, int l) {
   bool coarsest = l == (int)h->orders.size() - 1;
   if (coarsest) return PMG_OK;
 
-  // ---- Schwarz factors (fast diagonalisation per element class)
+  // ---- Schwarz factors (fast diagonalisation per element class), per direction with its
+  // own order and overlap
   int O = (p >= 3) ? h->opts.overlap : 0;  // overlap lines of two neighbours must not meet
+  int OZ = (pz >= 3) ? h->opts.overlap : 0;
   L.overlap = O;
-  int NB = p + 1 + 2 * O;
-  std::vector<double> Vx(4 * NB * NB, 0.0), Vz(4 * NB * NB, 0.0);
-  std::vector<double> lamx(4 * NB, 0.0), lamz(4 * NB, 0.0);
+  L.overlap_z = OZ;
+  int NB = p + 1 + 2 * O, NBZ = pz + 1 + 2 * OZ;
+  std::vector<double> Vx(4 * NB * NB, 0.0), Vz(4 * NBZ * NBZ, 0.0);
+  std::vector<double> lamx(4 * NB, 0.0), lamz(4 * NBZ, 0.0);
   int kx[4] = {0, 0, 0, 0}, kz[4] = {0, 0, 0, 0};  // eigenpairs per class (modes >= k are padding)
   std::vector<double> wx(L.s.NX, 0.0), wz(L.s.NZ, 0.0);
   auto xsub = [&](int ex, std::vector<int>& loc, std::vector<int>& glob) {
@@ -418,8 +430,8 @@ pmg_status build_level(pmg_handle* h, int l) {
   };
   auto zsub = [&](int ez, std::vector<int>& loc, std::vector<int>& glob) {
     loc.clear(); glob.clear();
-    for (int b = 0; b < NB; ++b) {
-      int g = ez * p - O + b;
+    for (int b = 0; b < NBZ; ++b) {
+      int g = ez * pz - OZ + b;
       if (g < 0 || g >= L.s.NZ - 1) continue;  // Dirichlet row excluded
       loc.push_back(b);
       glob.push_back(g);
@@ -428,17 +440,17 @@ pmg_status build_level(pmg_handle* h, int l) {
   std::vector<int> loc, glob;
   for (int cls = 0; cls < 4; ++cls) {
     fdm_class(p, O, 0, cls, &Vx[cls * NB * NB], &lamx[cls * NB], kx[cls]);
-    fdm_class(p, O, 1, cls, &Vz[cls * NB * NB], &lamz[cls * NB], kz[cls]);
+    fdm_class(pz, OZ, 1, cls, &Vz[cls * NBZ * NBZ], &lamz[cls * NBZ], kz[cls]);
   }
-  std::vector<double> invden(16 * NB * NB, 0.0);
+  std::vector<double> invden(16 * NB * NBZ, 0.0);
   for (int xc = 0; xc < 4; ++xc)
     for (int zc = 0; zc < 4; ++zc)
       for (int a = 0; a < NB; ++a)
-        for (int b = 0; b < NB; ++b) {
-          double la = lamx[xc * NB + a], lb = lamz[zc * NB + b];
+        for (int b = 0; b < NBZ; ++b) {
+          double la = lamx[xc * NB + a], lb = lamz[zc * NBZ + b];
           if (a < kx[xc] && b < kz[zc]) {
             double d = h->cx * la + h->cz * lb;
-            invden[((xc * 4 + zc) * NB + a) * NB + b] = d > 0.0 ? 1.0 / d : 0.0;
+            invden[((xc * 4 + zc) * NB + a) * NBZ + b] = d > 0.0 ? 1.0 / d : 0.0;
           }
         }
   for (int ex = 0; ex < m.cells_x; ++ex) { xsub(ex, loc, glob); for (int g : glob) wx[g] += 1.0; }
@@ -455,7 +467,21 @@ pmg_status build_level(pmg_handle* h, int l) {
   L.wx[1] = upload<float>(wx, h->allocs, e); CK(e);
   L.wz[0] = upload<double>(wz, h->allocs, e); CK(e);
   L.wz[1] = upload<float>(wz, h->allocs, e); CK(e);
-  L.J = upload<double>(transfer_matrix(h->orders[l + 1], p), h->allocs, e); CK(e);
+  // transfers per direction: the coarse interpolant at the fine nodes, the identity along a
+  // direction that this level step does not coarsen
+  auto transfer_or_identity = [](int pc, int pf) {
+    if (pc != pf) return transfer_matrix(pc, pf);
+    std::vector<double> I((size_t)(pf + 1) * (pf + 1), 0.0);
+    for (int i = 0; i <= pf; ++i) I[(size_t)i * (pf + 1) + i] = 1.0;
+    return I;
+  };
+  const int pcx = h->orders[l + 1], pcz = h->orders_z[l + 1];
+  L.J = upload<double>(transfer_or_identity(pcx, p), h->allocs, e); CK(e);
+  if (pcz == pcx && pz == p) {
+    L.Jz = L.J;
+  } else {
+    L.Jz = upload<double>(transfer_or_identity(pcz, pz), h->allocs, e); CK(e);
+  }
   return PMG_OK;
 }
 
@@ -655,6 +681,7 @@ pmg_status level_fdm(pmg_handle* h, int l, const void* r, void* x, int post, cud
   LevelDev& L = h->lv[l];
   FdmArgs a{L.s, L.overlap, r, x, post, h->opts.omega, L.Vx[PI<T>], L.Vz[PI<T>], L.invden[PI<T>],
             L.wx[PI<T>], L.wz[PI<T>], h->sc, PI<T> ? L.thr_fdm32 : 256};
+  a.overlap_z = L.overlap_z;
   double NL = (double)L.s.NX * L.s.NZ, E = (double)L.s.Nx * L.s.Nz;
   double NB = L.s.P + 1 + 2 * L.overlap;
   Cost c{3.0 * NL * sizeof(T), E * 2.0 * (2.0 * L.s.P * NB * NB + 2.0 * NB * NB * NB)};
@@ -662,12 +689,15 @@ pmg_status level_fdm(pmg_handle* h, int l, const void* r, void* x, int post, cud
     a.xout = xout;
     a.xzero = xzero ? 1 : 0;
   }
-  if (L.var) {
-    // per element column x-classes: the generic sweep (tables from global memory), in place
-    if (fused_b || (xout && xout != x)) return fail(PMG_ERR_INVALID, "fused sweep over a varying depth");
-    a.Vx = L.Vxc[PI<T>];
-    a.invden = L.invdenc[PI<T>];
-    a.xpercol = 1;
+  if (L.var || L.aniso) {
+    // per element column x-classes (varying depth) or different orders: the generic sweep
+    // (tables from global memory), in place
+    if (fused_b || (xout && xout != x)) return fail(PMG_ERR_INVALID, "fused sweep on this level");
+    if (L.var) {
+      a.Vx = L.Vxc[PI<T>];
+      a.invden = L.invdenc[PI<T>];
+      a.xpercol = 1;
+    }
     a.threads = 256;
     return launch(h, PI<T> ? PMG_K_SMOOTH32 : PMG_K_SMOOTH64, 1, st, c, [&] { return fdm_smooth<T>(a, st); });
   }
@@ -725,6 +755,7 @@ pmg_status transfer_op(pmg_handle* h, int l, const void* in, void* out, int rest
                        const void* xf = nullptr) {
   LevelDev& L = h->lv[l];
   TransferArgs a{L.s, h->lv[l + 1].s, in, out, L.J, L.thr_xfer};
+  a.Jz = L.Jz;
   double Nf = (double)L.s.NX * L.s.NZ, Nc = (double)h->lv[l + 1].s.NX * h->lv[l + 1].s.NZ;
   double pf = L.s.P, pc = h->lv[l + 1].s.P;
   Cost c{(restrict_ ? Nf + Nc : 2.0 * Nf + Nc) * sizeof(T), 2.0 * (Nf * (pc + 1) + Nc * (pf + 1))};
@@ -1416,8 +1447,22 @@ pmg_status pmg_create(const pmg_mesh_desc* mesh, const pmg_opts* opts, pmg_handl
       o.inner_max < 1 || !(o.inner_tol > 0) || o.fuse_residual < -1 || o.fuse_residual > 1 || o.df64_outer < -1 ||
       o.df64_outer > 1 || o.flat_kernel < -1 || o.flat_kernel > 1)
     return fail(PMG_ERR_INVALID, "bad solver options");
-  std::vector<int> orders;
-  if (o.nlevels > 0) {
+  const int order_z = m.order_z == 0 ? m.order : m.order_z;
+  if (order_z < 1 || order_z > MAXP) return fail(PMG_ERR_INVALID, "order_z must be 0 or in 1..10");
+  std::vector<int> orders, orders_z;
+  if (order_z != m.order) {
+    // semi-coarsening (Sec. 5.1): the higher order is reduced until both match
+    if (o.nlevels > 0) return fail(PMG_ERR_INVALID, "custom level orders need equal orders along x and sigma");
+    if (o.precision == PMG_MIXED_BF16) return fail(PMG_ERR_INVALID, "the BF16 operator needs equal orders");
+    if (!aniso_pair_supported(m.order, order_z, true))
+      return fail(PMG_ERR_INVALID, "order pair not built (order_z = 8 with order 2..10 are)");
+    for (auto pr : semi_coarsening_sequence(m.order, order_z)) {
+      orders.push_back(pr.first);
+      orders_z.push_back(pr.second);
+      if (pr.first != pr.second && !aniso_pair_supported(pr.first, pr.second, false))
+        return fail(PMG_ERR_INVALID, "level order pair not built");
+    }
+  } else if (o.nlevels > 0) {
     if (o.nlevels > 8) return fail(PMG_ERR_INVALID, "at most 8 levels");
     for (int i = 0; i < o.nlevels; ++i) orders.push_back(o.level_orders[i]);
     if (orders[0] != m.order || orders.back() != 1) return fail(PMG_ERR_INVALID, "levels must run from order to 1");
@@ -1426,6 +1471,7 @@ pmg_status pmg_create(const pmg_mesh_desc* mesh, const pmg_opts* opts, pmg_handl
   } else {
     orders = coarsening_sequence(m.order);
   }
+  if (orders_z.empty()) orders_z = orders;
   if (orders.size() < 2) return fail(PMG_ERR_INVALID, "order must be >= 2 (the coarsest level is order 1)");
 
   auto* h = new (std::nothrow) pmg_handle();
@@ -1435,10 +1481,13 @@ pmg_status pmg_create(const pmg_mesh_desc* mesh, const pmg_opts* opts, pmg_handl
   DeviceGuard dg(h->device);
   if (ensure_constants(h->device) != PMG_OK) return bail(PMG_ERR_CUDA);
   h->mesh = m;
+  h->mesh.order_z = order_z;
   h->opts = o;
   h->tc = o.precision == PMG_MIXED_BF16 ? 3 : 0;
   h->df64_outer = o.df64_outer == 1 || (o.df64_outer < 0 && o.precision != PMG_FP64);
   h->orders = orders;
+  h->orders_z = orders_z;
+  h->aniso = order_z != m.order;
   h->dx = (m.x1 - m.x0) / m.cells_x;
   h->dsig = 1.0 / m.cells_z;
   h->cx = m.h * h->dsig / h->dx;
@@ -1463,10 +1512,12 @@ pmg_status pmg_create(const pmg_mesh_desc* mesh, const pmg_opts* opts, pmg_handl
     int ex = ix / m.order, i = ix % m.order;
     h->xcols[ix] = m.x0 + (ex + (x[i] + 1.0) / 2.0) * h->dx;
   }
+  std::vector<double> xz, wz;
+  lgl(order_z, xz, wz);
   h->sigrows.resize(F.NZ);
   for (int iz = 0; iz < F.NZ; ++iz) {
-    int ez = std::min(iz / m.order, m.cells_z - 1), j = iz - ez * m.order;
-    h->sigrows[iz] = (ez + (x[j] + 1.0) / 2.0) * h->dsig;
+    int ez = std::min(iz / order_z, m.cells_z - 1), j = iz - ez * order_z;
+    h->sigrows[iz] = (ez + (xz[j] + 1.0) / 2.0) * h->dsig;
   }
   cudaError_t e;
 #define ALLOC(ptr, T, n)                                   \
@@ -1603,6 +1654,7 @@ pmg_status pmg_set_geometry(pmg_handle* h, const double* eta_dev, void* stream) 
 pmg_status pmg_set_bathymetry(pmg_handle* h, const double* h_dev, void* stream) {
   CKS(check_handle(h));
   if (!h_dev) return fail(PMG_ERR_INVALID, "depth is NULL");
+  if (h->aniso) return fail(PMG_ERR_INVALID, "a varying depth needs equal orders along x and sigma");
   if (h->tc) return fail(PMG_ERR_INVALID, "the BF16 tensor-core operator takes a constant depth only");
   if (h->mesh.periodic_x && h->mesh.cells_x < 2) return fail(PMG_ERR_INVALID, "periodic mesh needs 2 or more cells");
   DeviceGuard dg(h->device);
@@ -1671,6 +1723,7 @@ pmg_status pmg_set_bathymetry(pmg_handle* h, const double* h_dev, void* stream) 
 pmg_status pmg_set_geometry_mixed(pmg_handle* h, const double* eta_dev, const double* eta_prev_dev, void* stream) {
   CKS(check_handle(h));
   if (h->bathy) return fail(PMG_ERR_INVALID, "the mixed-stage operator takes a constant depth only");
+  if (h->aniso) return fail(PMG_ERR_INVALID, "the mixed-stage operator needs equal orders along x and sigma");
   CKS(pmg_set_geometry(h, eta_dev, stream));
   if (!eta_prev_dev) return fail(PMG_ERR_INVALID, "eta_prev is NULL");
   DeviceGuard dg(h->device);
@@ -1905,6 +1958,7 @@ pmg_status pmg_gradient(pmg_handle* h, const double* f, double* fx, double* fz, 
   CKS(check_handle(h));
   if (!f || !fx || !fz) return fail(PMG_ERR_INVALID, "NULL vector");
   if (h->bathy) return fail(PMG_ERR_INVALID, "gradient recovery takes a constant depth only");
+  if (h->aniso) return fail(PMG_ERR_INVALID, "gradient recovery needs equal orders along x and sigma");
   DeviceGuard dg(h->device);
   cudaStream_t st = (cudaStream_t)stream;
   const Shape& F = h->lv[0].s;
@@ -1915,6 +1969,7 @@ pmg_status pmg_gradient(pmg_handle* h, const double* f, double* fx, double* fz, 
 
 pmg_status pmg_set_filter(pmg_handle* h, int cutoff, double alpha, double beta) {
   CKS(check_handle(h));
+  if (h->aniso) return fail(PMG_ERR_INVALID, "the stepper kernels need equal orders along x and sigma");
   const int P = h->mesh.order, n = P + 1;
   if (cutoff < 0 || cutoff > P || !std::isfinite(alpha) || alpha > 0.0 || !(beta > 0.0) || !std::isfinite(beta))
     return fail(PMG_ERR_INVALID, "filter needs 0 <= cutoff <= P, finite alpha <= 0, beta > 0");
@@ -1946,6 +2001,7 @@ pmg_status pmg_set_filter(pmg_handle* h, int cutoff, double alpha, double beta) 
 
 pmg_status pmg_filter(pmg_handle* h, const double* f, double* out, int surface, void* stream) {
   CKS(check_handle(h));
+  if (h->aniso) return fail(PMG_ERR_INVALID, "the stepper kernels need equal orders along x and sigma");
   if (!f || !out || f == out) return fail(PMG_ERR_INVALID, "filter needs distinct non-NULL input and output");
   if (!h->filt) return fail(PMG_ERR_INVALID, "no filter set (pmg_set_filter)");
   DeviceGuard dg(h->device);
@@ -1967,6 +2023,7 @@ pmg_status pmg_forcing(pmg_handle* h, const double* u, const double* w, const do
                        const double* wx, const double* wz, const double* etax, double g, double* Fu, double* Fw,
                        void* stream) {
   CKS(check_handle(h));
+  if (h->aniso) return fail(PMG_ERR_INVALID, "the stepper kernels need equal orders along x and sigma");
   if (!u || !w || !ux || !uz || !wx || !wz || !etax || !Fu || !Fw) return fail(PMG_ERR_INVALID, "NULL vector");
   DeviceGuard dg(h->device);
   cudaStream_t st = (cudaStream_t)stream;
@@ -1979,6 +2036,7 @@ pmg_status pmg_stage_rates(pmg_handle* h, const double* u, const double* w, cons
                            const double* Fu, const double* Fw, const double* px, const double* pz, const double* etax,
                            double rho, double* du, double* dw, double* deta, void* stream) {
   CKS(check_handle(h));
+  if (h->aniso) return fail(PMG_ERR_INVALID, "the stepper kernels need equal orders along x and sigma");
   if (!u || !w || !uz || !wz || !Fu || !Fw || !px || !pz || !etax || !du || !dw || !deta)
     return fail(PMG_ERR_INVALID, "NULL vector");
   DeviceGuard dg(h->device);
@@ -2008,17 +2066,20 @@ pmg_status pmg_autotune(pmg_handle* h) {
     void* b = L.b[1];
     void* t = L.t[1];
     // slab CTAs (positive sizes) or node-parallel CTAs (negative sizes)
-    CKS(tune_one(h, L.var ? TK_FLAT32V : TK_FLAT32, L.order, L.s.NZ, [&](int thr, cudaStream_t cs) {
+    CKS(tune_one(h, L.var ? TK_FLAT32V : TK_FLAT32, L.order + 100 * (L.aniso ? L.order_z : 0), L.s.NZ,
+                 [&](int thr, cudaStream_t cs) {
       L.thr_flat32 = thr;
       return level_residual<float>(h, l, b, x, t, 1, cs);
     }, &L.thr_flat32, h->opts.flat_kernel == 1 ? std::initializer_list<int>{-64, -128, -256}
                        : h->opts.flat_kernel == 0 ? std::initializer_list<int>{64, 128, 192, 256, 320, 384, 512}
                        : std::initializer_list<int>{64, 128, 192, 256, 320, 384, 512, -64, -128, -256}));
     if (l == nl - 1) continue;
-    if (L.var) {
-      // varying depth: generic sweep (fixed CTA size), split residuals; only the transfers tune
+    if (L.var || L.aniso) {
+      // varying depth or different orders: generic sweep (fixed CTA size), split residuals;
+      // only the transfers tune
       LevelDev& C = h->lv[l + 1];
-      CKS(tune_one(h, TK_XFER, L.order * 16 + C.order, L.s.NZ, [&](int thr, cudaStream_t cs) {
+      CKS(tune_one(h, TK_XFER, L.order * 16 + C.order + 1000 * (L.aniso ? L.order_z : 0), L.s.NZ,
+                   [&](int thr, cudaStream_t cs) {
         L.thr_xfer = thr;
         return transfer_op<float>(h, l, t, C.b[1], 1, cs);
       }, &L.thr_xfer));
@@ -2059,11 +2120,12 @@ pmg_status pmg_autotune(pmg_handle* h) {
       if (h->opts.fuse_residual < 0) L.fuse_restrict = us_fused < 0.9f * us_split;
     }
   }
-  CKS(tune_one(h, h->bathy ? TK_CURVED32B : TK_CURVED32, h->mesh.order, h->lv[0].s.NZ, [&](int thr, cudaStream_t cs) {
+  const int curved_key = h->mesh.order + 100 * (h->aniso ? h->mesh.order_z : 0);
+  CKS(tune_one(h, h->bathy ? TK_CURVED32B : TK_CURVED32, curved_key, h->lv[0].s.NZ, [&](int thr, cudaStream_t cs) {
     h->thr_curved32 = thr;
     return curved<float>(h, 0, h->r32, nullptr, h->w32, 1, nullptr, cs);
   }, &h->thr_curved32));
-  CKS(tune_one(h, h->bathy ? TK_CURVED64B : TK_CURVED64, h->mesh.order, h->lv[0].s.NZ, [&](int thr, cudaStream_t cs) {
+  CKS(tune_one(h, h->bathy ? TK_CURVED64B : TK_CURVED64, curved_key, h->lv[0].s.NZ, [&](int thr, cudaStream_t cs) {
     h->thr_curved64 = thr;
     return curved<double>(h, 0, h->p, nullptr, h->w, 1, nullptr, cs);
   }, &h->thr_curved64));

@@ -33,7 +33,7 @@ class PmgError(RuntimeError):
 class MeshDesc(ctypes.Structure):
     _fields_ = [("x0", ctypes.c_double), ("x1", ctypes.c_double), ("h", ctypes.c_double),
                 ("cells_x", ctypes.c_int), ("cells_z", ctypes.c_int), ("order", ctypes.c_int),
-                ("periodic_x", ctypes.c_int)]
+                ("periodic_x", ctypes.c_int), ("order_z", ctypes.c_int)]
 
 
 class Opts(ctypes.Structure):
@@ -182,9 +182,9 @@ def apply_noalloc(mesh, eta, x, out):
 class Solver:
     """One mesh + multigrid hierarchy on the current CUDA device (pmg_create)."""
 
-    def __init__(self, cells_x, cells_z, order, x0=0.0, x1=1.0, h=1.0, periodic=False, **opts):
+    def __init__(self, cells_x, cells_z, order, x0=0.0, x1=1.0, h=1.0, periodic=False, order_z=None, **opts):
         lib = load()
-        self.mesh = MeshDesc(x0, x1, h, cells_x, cells_z, order, int(bool(periodic)))
+        self.mesh = MeshDesc(x0, x1, h, cells_x, cells_z, order, int(bool(periodic)), int(order_z or 0))
         self.opts = default_opts(**opts)
         hh = ctypes.c_void_p()
         _check(lib.pmg_create(ctypes.byref(self.mesh), ctypes.byref(self.opts), ctypes.byref(hh)))
@@ -412,7 +412,7 @@ class Batch:
         arr = (MeshDesc * len(meshes))()
         for i, m in enumerate(meshes):
             arr[i] = MeshDesc(m.get("x0", 0.0), m.get("x1", 1.0), m.get("h", 1.0), m["cells_x"], m["cells_z"],
-                              m["order"], int(bool(m.get("periodic", False))))
+                              m["order"], int(bool(m.get("periodic", False))), int(m.get("order_z") or 0))
         hb = ctypes.c_void_p()
         _check(lib.pmg_batch_create(len(meshes), arr, ctypes.byref(self.opts), ctypes.byref(hb)))
         self._b = hb

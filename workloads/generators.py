@@ -166,10 +166,14 @@ class Workload:
     pressure: Harmonic = None
     noise_sd: float = 0.0
     bathymetry: Bar = None            # still-water depth h(x); None: the constant h
+    order_z: int = None               # order along sigma; None: order
 
     def mesh_kwargs(self):
-        return dict(cells_x=self.cells_x, cells_z=self.cells_z, order=self.order,
-                    x0=self.x0, x1=self.x1, h=self.h, periodic=self.periodic)
+        d = dict(cells_x=self.cells_x, cells_z=self.cells_z, order=self.order,
+                 x0=self.x0, x1=self.x1, h=self.h, periodic=self.periodic)
+        if self.order_z is not None and self.order_z != self.order:
+            d["order_z"] = self.order_z
+        return d
 
     def depth(self, x_cols):
         """Still-water depth at the node columns."""
@@ -283,14 +287,16 @@ def paper_shape():
                     velocity=Velocity.random(BASE_SEED + 9))
 
 
-def paper_scaling(cells_x, order, ppw=48.0):
-    """Sec. 6.3 scaling family: N_z = 2, P_z = order, waves of kh = 1 and H/L = 0.0301 at
-    about `ppw` points per wavelength (the domain grows with the node count)."""
+def paper_scaling(cells_x, order, ppw=48.0, order_z=None):
+    """Sec. 6.3 scaling family: N_z = 2, waves of kh = 1 and H/L = 0.0301 at about `ppw`
+    points per wavelength along x (the domain grows with the node count); the vertical
+    order is `order_z` (the paper's P_z = 8) or, when None, the horizontal one."""
     k = 1.0
     L = cells_x * order * 2 * np.pi / ppw
     s = Surface(0.5 * 0.0301 * 2 * np.pi, k)
-    return Workload(f'paper_scaling_p{order}_{cells_x}x2', cells_x, 2, order, 0.0, L, 1.0, False,
-                    BASE_SEED + 6, s, 'div', velocity=Velocity.random(BASE_SEED + 9))
+    tag = f'p{order}' if order_z in (None, order) else f'p{order}z{order_z}'
+    return Workload(f'paper_scaling_{tag}_{cells_x}x2', cells_x, 2, order, 0.0, L, 1.0, False,
+                    BASE_SEED + 6, s, 'div', velocity=Velocity.random(BASE_SEED + 9), order_z=order_z)
 
 
 def bar(cells_x=100, cells_z=2, order=8, rhs='div'):

@@ -472,7 +472,8 @@ def run_paper(args, ws, rank, local):
     N_x = 102, N_z = 2, 17 waves of kh = 1, H/L = 0.0301) at tolerances 1e-4 ... 1e-10
     with FP64 PCG, FP64 PDC, FP64 flexible GMRES and the mixed-precision solve, the oracle on the host cores
     beside it; then the scaling sweeps at tol 1e-6 (N_x = 25 ... 800 at P = 8; P = 2 ... 10
-    at N_x = 200; ~48 points per wavelength).  Device time per solve: CUDA events, median
+    at N_x = 200 with equal orders, and P_x = 2 ... 10 at P_z = 8 as in the paper; ~48 points
+    per wavelength).  Device time per solve: CUDA events, median
     of `steps` solves from a zero initial guess."""
     import torch
     import paper_2411_14977_gb300.pmg as pmg
@@ -576,6 +577,18 @@ def run_paper(args, ws, rank, local):
             S.close()
         sweep["order"].append(row)
         log("order", row)
+    # the paper's own order sweep: P_x varied at N_x = 200 with the vertical order fixed at
+    # P_z = 8 (semi-coarsened hierarchy)
+    sweep["order_x_at_order_z_8"] = []
+    for order in (2, 3, 4, 5, 6, 7, 8, 9, 10):
+        row = {"cells_x": 200, "order_x": order, "order_z": 8}
+        for name, opts in (methods[0], methods[3]):
+            S, b, pD = prepare(W.paper_scaling(200, order, order_z=8), tol=1e-6, **opts)
+            ms, info = time_solve(S, b, pD)
+            row[name] = {"iterations": info["iterations"], "ms": ms, "nodes": S.n}
+            S.close()
+        sweep["order_x_at_order_z_8"].append(row)
+        log("order_x (P_z = 8)", row)
     clocks = clk.stop()
     print(json.dumps({"workload": w.name, "nodes": int(m.N), "table1_shape": table,
                       "table1_shape_mixed_stage": mixed_stage, "oracle_host": oracle,

@@ -382,9 +382,10 @@ cudaError_t check_finite(size_t n, const double* v, int* status, cudaStream_t st
 // h[k] = <w, V_k> for k < nv (V_k = V + k n): per-block partials of every k, then the last
 // block to finish (ticket) adds them in block order, so the sums are deterministic.
 __global__ void __launch_bounds__(VEC_THREADS) k_mdot(size_t n, const double* w, const double* V, int nv,
-                                                      double* h, double* part, unsigned* cnt) {
+                                                      double* h, double* part, unsigned* cnt, const int* nvdev) {
   __shared__ double red[34];
   __shared__ int s_flag;
+  if (nvdev) nv = *nvdev + 1;  // device-side Arnoldi index j: the vectors V_0 .. V_j
   for (int k = 0; k < nv; ++k) {
     const double* v = V + (size_t)k * n;
     double a = 0.0;
@@ -409,9 +410,11 @@ __global__ void __launch_bounds__(VEC_THREADS) k_mdot(size_t n, const double* w,
   if (threadIdx.x == 0) *cnt = 0u;
 }
 
-// w += sign sum_k c[k] V_k  (c on the device)
-__global__ void k_maxpy(size_t n, double* w, const double* V, int nv, const double* c, double sign) {
+// w += sign sum_k c[k] V_k  (c on the device; nvdev: nv = *nvdev + nvadd)
+__global__ void k_maxpy(size_t n, double* w, const double* V, int nv, const double* c, double sign, const int* nvdev,
+                        int nvadd) {
   __shared__ double cs[64];
+  if (nvdev) nv = *nvdev + nvadd;
   for (int k = threadIdx.x; k < nv; k += blockDim.x) cs[k] = sign * c[k];
   __syncthreads();
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
@@ -421,25 +424,131 @@ __global__ void k_maxpy(size_t n, double* w, const double* V, int nv, const doub
   }
 }
 
-// v = w / sqrt(*nrm2)   (a zero norm leaves v unused: the caller stops the cycle)
-__global__ void k_scale_inv_norm(size_t n, const double* w, const double* nrm2, double* v) {
+// v = w / sqrt(*nrm2)   (a zero norm leaves v unused: the caller stops the cycle);
+// jdev: v is the basis vector V_(j+1) of v = V
+__global__ void k_scale_inv_norm(size_t n, const double* w, const double* nrm2, double* v, const int* jdev) {
   double s = 1.0 / sqrt(*nrm2);
+  if (jdev) v += (size_t)(*jdev + 1) * n;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     v[i] = w[i] * s;
 }
 
 cudaError_t gmres_mdot(size_t n, const double* w, const double* V, int nv, double* h, double* part, unsigned* cnt,
-                       cudaStream_t st) {
-  k_mdot<<<VEC_BLOCKS, VEC_THREADS, 0, st>>>(n, w, V, nv, h, part, cnt);
+                       cudaStream_t st, const int* jdev) {
+  k_mdot<<<VEC_BLOCKS, VEC_THREADS, 0, st>>>(n, w, V, nv, h, part, cnt, jdev);
   return cudaGetLastError();
 }
-cudaError_t gmres_maxpy(size_t n, double* w, const double* V, int nv, const double* c, double sign, cudaStream_t st) {
+cudaError_t gmres_maxpy(size_t n, double* w, const double* V, int nv, const double* c, double sign, cudaStream_t st,
+                        const int* nvdev, int nvadd) {
   if (nv > 64) return cudaErrorInvalidValue;
-  k_maxpy<<<vec_grid(n), VEC_THREADS, 0, st>>>(n, w, V, nv, c, sign);
+  k_maxpy<<<vec_grid(n), VEC_THREADS, 0, st>>>(n, w, V, nv, c, sign, nvdev, nvadd);
   return cudaGetLastError();
 }
-cudaError_t gmres_scale(size_t n, const double* w, const double* nrm2, double* v, cudaStream_t st) {
-  k_scale_inv_norm<<<vec_grid(n), VEC_THREADS, 0, st>>>(n, w, nrm2, v);
+cudaError_t gmres_scale(size_t n, const double* w, const double* nrm2, double* v, cudaStream_t st, const int* jdev) {
+  k_scale_inv_norm<<<vec_grid(n), VEC_THREADS, 0, st>>>(n, w, nrm2, v, jdev);
+  return cudaGetLastError();
+}
+
+// ---- device-side GMRES cycle (graph with a while-node) -----------------------------
+// State: j (the Arnoldi index, = the cycle's iteration count), the cap of iterations for
+// this cycle, the Hessenberg matrix H [(m+1) x m] after the rotations, their cosines and
+// sines, g (the rotated right-hand side, ||r|| e_1 at the start) and y.
+
+// V_j (device j) into the V-cycle input: FP64 (v64) or FP32 (v32)
+__global__ void k_gm_gather(size_t n, const double* V, const int* jdev, double* v64, float* v32) {
+  const double* vj = V + (size_t)(*jdev) * n;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    if (v64) v64[i] = vj[i];
+    else v32[i] = (float)vj[i];
+  }
+}
+
+// Z_j = z (the V-cycle output: FP64 z64, or FP32 z32 widened, also into zw)
+__global__ void k_gm_scatter(size_t n, const double* z64, const float* z32, double* Z, const int* jdev, double* zw) {
+  double* zj = Z + (size_t)(*jdev) * n;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    double v = z64 ? z64[i] : (double)z32[i];
+    zj[i] = v;
+    if (zw) zw[i] = v;
+  }
+}
+
+// Start of a cycle: j = 0, g = ||r|| e_1, cap = this cycle's iteration limit, counter 0.
+__global__ void k_gm_init(const double* rr, double* g, int m, int* jdev, int* capdev, int cap, int* iter) {
+  for (int i = threadIdx.x; i <= m; i += blockDim.x) g[i] = i == 0 ? sqrt(*rr) : 0.0;
+  if (threadIdx.x == 0) {
+    *jdev = 0;
+    *capdev = cap;
+    *iter = 0;
+  }
+}
+
+// Column j of H from the two Gram-Schmidt passes (c1, c2) and ||w||^2 (hn2), the earlier
+// rotations on it, a new rotation zeroing H[j+1][j], g rotated.  Continue while the
+// residual estimate |g[j+1]|^2 is above tol2 ||b~||^2 (*bb), the cycle has room, and no breakdown
+// (a zero or non-finite ||w|| or pivot).  out[0] = |g[j+1]|^2, out[1] = 1 on breakdown.
+__global__ void k_gm_givens(cudaGraphConditionalHandle hnd, const double* c1, const double* c2, const double* hn2,
+                            double* H, double* cs, double* sn, double* g, int m, int* jdev, const int* capdev,
+                            int* iter, double tol2, const double* bb, double* out) {
+  const int j = *jdev;
+  double* col = H + j;  // H[i][j] = H[i * m + j]
+  for (int i = 0; i <= j; ++i) col[(size_t)i * m] = c1[i] + c2[i];
+  const double hn = sqrt(fmax(*hn2, 0.0));
+  for (int i = 0; i < j; ++i) {
+    double a = col[(size_t)i * m], b = col[(size_t)(i + 1) * m];
+    col[(size_t)i * m] = cs[i] * a + sn[i] * b;
+    col[(size_t)(i + 1) * m] = -sn[i] * a + cs[i] * b;
+  }
+  const double hjj = col[(size_t)j * m];
+  const double den = hypot(hjj, hn);
+  const bool ok = den > 0.0 && isfinite(den);
+  double c = ok ? hjj / den : 1.0, sv = ok ? hn / den : 0.0;
+  cs[j] = c;
+  sn[j] = sv;
+  col[(size_t)j * m] = ok ? den : hjj;
+  g[j + 1] = -sv * g[j];
+  g[j] = c * g[j];
+  const int it = ++(*iter);
+  *jdev = j + 1;
+  const double r2 = g[j + 1] * g[j + 1];
+  out[0] = r2;
+  out[1] = ok ? 0.0 : 1.0;
+  const bool more = ok && hn > 0.0 && isfinite(r2) && r2 > tol2 * (*bb) && j + 1 < m && it < *capdev;
+  cudaGraphSetConditional(hnd, more ? 1u : 0u);
+}
+
+// y = H^-1 g over the k = j leading rows (back substitution)
+__global__ void k_gm_backsub(const double* H, const double* g, double* y, int m, const int* jdev) {
+  const int k = *jdev;
+  for (int i = k - 1; i >= 0; --i) {
+    double v = g[i];
+    for (int l = i + 1; l < k; ++l) v -= H[(size_t)i * m + l] * y[l];
+    y[i] = v / H[(size_t)i * m + i];
+  }
+}
+
+cudaError_t gmres_gather(size_t n, const double* V, const int* jdev, double* v64, float* v32, cudaStream_t st) {
+  k_gm_gather<<<vec_grid(n), VEC_THREADS, 0, st>>>(n, V, jdev, v64, v32);
+  return cudaGetLastError();
+}
+cudaError_t gmres_scatter(size_t n, const double* z64, const float* z32, double* Z, const int* jdev, double* zw,
+                          cudaStream_t st) {
+  k_gm_scatter<<<vec_grid(n), VEC_THREADS, 0, st>>>(n, z64, z32, Z, jdev, zw);
+  return cudaGetLastError();
+}
+cudaError_t gmres_init(const double* rr, double* g, int m, int* jdev, int* capdev, int cap, int* iter,
+                       cudaStream_t st) {
+  k_gm_init<<<1, 64, 0, st>>>(rr, g, m, jdev, capdev, cap, iter);
+  return cudaGetLastError();
+}
+cudaError_t gmres_givens(cudaGraphConditionalHandle hnd, const double* c1, const double* c2, const double* hn2,
+                         double* H, double* cs, double* sn, double* g, int m, int* jdev, const int* capdev,
+                         int* iter, double tol2, const double* bb, double* out, cudaStream_t st) {
+  k_gm_givens<<<1, 1, 0, st>>>(hnd, c1, c2, hn2, H, cs, sn, g, m, jdev, capdev, iter, tol2, bb, out);
+  return cudaGetLastError();
+}
+cudaError_t gmres_backsub(const double* H, const double* g, double* y, int m, const int* jdev, cudaStream_t st) {
+  k_gm_backsub<<<1, 1, 0, st>>>(H, g, y, m, jdev);
   return cudaGetLastError();
 }
 

@@ -27,6 +27,8 @@ enum Slot {
   SLOT_BB = 16,     // ||b~||^2 (lifted right-hand side)
   SLOT_RR64 = 17,   // ||b~ - A x||^2 of the FP64 outer residual
   SLOT_AUX = 18,    // residual norms requested outside a solve
+  SLOT_GM_RES = 21,   // device-side GMRES: |g_(j+1)|^2, the residual estimate of the cycle
+  SLOT_GM_BREAK = 22, // device-side GMRES: 1 after a breakdown (zero or non-finite pivot)
   SLOT_COUNT = 24
 };
 
@@ -193,10 +195,23 @@ template <typename T> cudaError_t add(size_t n, T* x, const T* y, cudaStream_t s
 cudaError_t cast_f32(size_t n, const double* x, float* y, cudaStream_t st);
 // GMRES: h[k] = <w, V_k> (k < nv, deterministic; part: >= nv * 304 doubles, cnt zeroed),
 // w += sign sum_k c[k] V_k (nv <= 64), v = w / sqrt(*nrm2)
+// Arnoldi kernels; jdev / nvdev (device ints): the count comes from the device-side
+// Arnoldi index (nv = j + 1 for the dot and scale, nv = *nvdev + nvadd for the axpy)
 cudaError_t gmres_mdot(size_t n, const double* w, const double* V, int nv, double* h, double* part, unsigned* cnt,
+                       cudaStream_t st, const int* jdev = nullptr);
+cudaError_t gmres_maxpy(size_t n, double* w, const double* V, int nv, const double* c, double sign, cudaStream_t st,
+                        const int* nvdev = nullptr, int nvadd = 0);
+cudaError_t gmres_scale(size_t n, const double* w, const double* nrm2, double* v, cudaStream_t st,
+                        const int* jdev = nullptr);
+cudaError_t gmres_gather(size_t n, const double* V, const int* jdev, double* v64, float* v32, cudaStream_t st);
+cudaError_t gmres_scatter(size_t n, const double* z64, const float* z32, double* Z, const int* jdev, double* zw,
+                          cudaStream_t st);
+cudaError_t gmres_init(const double* rr, double* g, int m, int* jdev, int* capdev, int cap, int* iter,
                        cudaStream_t st);
-cudaError_t gmres_maxpy(size_t n, double* w, const double* V, int nv, const double* c, double sign, cudaStream_t st);
-cudaError_t gmres_scale(size_t n, const double* w, const double* nrm2, double* v, cudaStream_t st);
+cudaError_t gmres_givens(cudaGraphConditionalHandle hnd, const double* c1, const double* c2, const double* hn2,
+                         double* H, double* cs, double* sn, double* g, int m, int* jdev, const int* capdev,
+                         int* iter, double tol2, const double* bb, double* out, cudaStream_t st);
+cudaError_t gmres_backsub(const double* H, const double* g, double* y, int m, const int* jdev, cudaStream_t st);
 // time-stepper kernels (k_stepper.cu)
 cudaError_t gradient(const Shape& s, const double* f, double* fx, double* fz, const double* eta, const double* sigma,
                      double h, double dx, double dsig, cudaStream_t st);

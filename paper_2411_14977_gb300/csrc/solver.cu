@@ -308,7 +308,11 @@ struct pmg_handle {
     int64_t body_launches[PMG_K_COUNT] = {};   // kernels of every further iteration
     double init_bytes[PMG_K_COUNT] = {}, body_bytes[PMG_K_COUNT] = {};
     double init_flops[PMG_K_COUNT] = {}, body_flops[PMG_K_COUNT] = {};
-  } loop64, loop32;
+  } loop64, loop32, loop_gm, loop_pdc;
+  bool loop_gm_mix = false, loop_pdc_mix = false;  // operator kind the loop captured (mixed-stage or not)
+  double* gm_state = nullptr;  // device GMRES cycle: H [(m+1) m], cs [m], sn [m], g [m+1]
+  int* gm_ctr = nullptr;       // device GMRES cycle: j, iteration cap
+  double* b_copy = nullptr;    // right-hand side captured by the PDC loop
 
   template <typename T> T* alloc(size_t n, cudaError_t& e) {
     T* d = nullptr;
@@ -317,7 +321,7 @@ struct pmg_handle {
     return d;
   }
   ~pmg_handle() {
-    for (Loop* l : {&loop64, &loop32})
+    for (Loop* l : {&loop64, &loop32, &loop_gm, &loop_pdc})
       if (l->exec) cudaGraphExecDestroy(l->exec);
     if (cap) cudaStreamDestroy(cap);
     if (iter_host) cudaFreeHost(iter_host);
@@ -1181,6 +1185,141 @@ pmg_status solve_gmres(pmg_handle* h, const double* b, pmg_solve_info* info, cud
   return PMG_OK;
 }
 
+// One device-side Arnoldi step of flexible GMRES (the body of the cycle's while-node): the
+// V-cycle on V_j (read through the device index j into fixed buffers), Z_j, w = A Z_j, two
+// classical Gram-Schmidt passes and the new basis vector, then the Givens update of the
+// Hessenberg column and the loop condition (k_gm_givens).
+pmg_status gmres_step(pmg_handle* h, cudaStream_t st, cudaGraphConditionalHandle hc) {
+  const size_t N = h->N;
+  const int m = h->opts.gmres_restart;
+  const bool fp64 = h->opts.precision == PMG_FP64;
+  double* V = h->gm_V;
+  double* Z = h->gm_Z;
+  double* hd = h->gm_h;
+  int* jd = h->gm_ctr;
+  double* H = h->gm_state;
+  double *cs = H + (size_t)(m + 1) * m, *sn = cs + m, *g = sn + m;
+  CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{16.0 * N, 0.0},
+             [&] { return gmres_gather(N, V, jd, fp64 ? h->p : nullptr, fp64 ? nullptr : h->r32, st); }));
+  if (fp64) CKS(vcycle<double>(h, 0, h->p, h->z, st));
+  else CKS(vcycle<float>(h, 0, h->r32, h->z32, st));
+  CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{(fp64 ? 16.0 : 20.0) * N, 0.0},
+             [&] { return gmres_scatter(N, fp64 ? h->z : nullptr, fp64 ? nullptr : h->z32, Z, jd, fp64 ? nullptr : h->z, st); }));
+  CKS(curved<double>(h, 0, h->z, nullptr, h->w, 1, nullptr, st));
+  for (int pass = 0; pass < 2; ++pass) {
+    double* c = hd + pass * (m + 1);
+    CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{8.0 * N * (m / 2 + 1), 2.0 * N * (m / 2)},
+               [&] { return gmres_mdot(N, h->w, V, 0, c, h->gm_part, h->gm_cnt, st, jd); }));
+    CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{8.0 * N * (m / 2 + 2), 2.0 * N * (m / 2)},
+               [&] { return gmres_maxpy(N, h->w, V, 0, c, -1.0, st, jd, 1); }));
+  }
+  CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{8.0 * N, 2.0 * N},
+             [&] { return dot<double, double>(N, h->w, h->w, hd + 2 * (m + 1), 0, h->sc, st); }));
+  CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{16.0 * N, 1.0 * N},
+             [&] { return gmres_scale(N, h->w, hd + 2 * (m + 1), V, st, jd); }));
+  const double tol2 = h->opts.tol * h->opts.tol;
+  return launch(h, PMG_K_VECTOR, 1, st, [&] {
+    return gmres_givens(hc, hd, hd + (m + 1), hd + 2 * (m + 1), H, cs, sn, g, m, jd, jd + 1, h->d_iter, tol2,
+                        h->scal + SLOT_BB, h->scal + SLOT_GM_RES, st);
+  });
+}
+
+// Flexible GMRES(m) with the cycle on the device: one graph launch (a while-node over
+// gmres_step) per restart cycle, then y = H^-1 g and x += Z y on the device and the true
+// FP64 residual; the host reads the scalars once per cycle.  The loop is rebuilt only when
+// the operator kind (mixed-stage or not) changes.
+pmg_status solve_gmres_graph(pmg_handle* h, const double* b, pmg_solve_info* info, cudaStream_t st) {
+  const size_t N = h->N;
+  const int m = h->opts.gmres_restart;
+  const double tol2 = h->opts.tol * h->opts.tol * h->scal_host[SLOT_BB];
+  double* H = h->gm_state;
+  double* g = H + (size_t)(m + 1) * m + 2 * m;
+  CKS(outer_residual(h, b, SLOT_RR64, st));
+  CKS(read_scalars(h, st));
+  if (h->loop_gm.exec && h->loop_gm_mix != h->mixed_stage) {
+    cudaGraphExecDestroy(h->loop_gm.exec);
+    h->loop_gm.exec = nullptr;
+  }
+  if (!h->loop_gm.exec) {
+    CKS(build_loop(h, h->loop_gm, [&](cudaStream_t cs, cudaGraphConditionalHandle hc) { return gmres_step(h, cs, hc); },
+                   [&](cudaStream_t cs, cudaGraphConditionalHandle hc) { return gmres_step(h, cs, hc); }));
+    h->loop_gm_mix = h->mixed_stage;
+  }
+  int total = 0;
+  while (true) {
+    const double rr = h->scal_host[SLOT_RR64];
+    if (!std::isfinite(rr)) return fail(PMG_ERR_NONFINITE, "non-finite residual");
+    if (rr <= tol2 || total >= h->opts.max_iter) break;
+    const int cap = std::min(m, h->opts.max_iter - total);
+    CKS(launch(h, PMG_K_VECTOR, 1, st, [&] { return gmres_init(h->scal + SLOT_RR64, g, m, h->gm_ctr, h->gm_ctr + 1, cap, h->d_iter, st); }));
+    CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{16.0 * N, 1.0 * N}, [&] { return gmres_scale(N, h->r, h->scal + SLOT_RR64, h->gm_V, st); }));
+    int it = 0;
+    CKS(run_loop(h, h->loop_gm, 0, st, &it));
+    total += it;
+    if (h->scal_host[SLOT_GM_BREAK] != 0.0) return fail(PMG_ERR_NONFINITE, "GMRES breakdown");
+    CKS(launch(h, PMG_K_VECTOR, 1, st, [&] { return gmres_backsub(H, g, h->gm_y, m, h->gm_ctr, st); }));
+    CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{8.0 * N * (it + 2), 2.0 * N * it},
+               [&] { return gmres_maxpy(N, h->x, h->gm_Z, 0, h->gm_y, 1.0, st, h->gm_ctr, 0); }));
+    CKS(outer_residual(h, b, SLOT_RR64, st));
+    CKS(read_scalars(h, st));
+  }
+  if (info) info->iterations = total;
+  return PMG_OK;
+}
+
+// PDC with the loop on the device: x <- x + B r and the true residual r = b~ - A x per
+// iteration inside one while-node (the right-hand side is copied into the handle so the
+// captured residual kernel does not depend on the caller's buffer).
+pmg_status pdc_step(pmg_handle* h, bool first, cudaStream_t st, cudaGraphConditionalHandle hc) {
+  const size_t N = h->N;
+  if (first) CK(cudaMemsetAsync(h->d_iter, 0, sizeof(int), st));
+  if (h->opts.precision == PMG_FP64) {
+    CKS(vcycle<double>(h, 0, h->r, h->z, st));
+    CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{24.0 * N, 1.0 * N}, [&] { return add<double>(N, h->x, h->z, st); }));
+  } else {
+    CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{12.0 * N, 1.0 * N}, [&] { return to_f32_scaled(N, h->r, h->r32, h->scal, SLOT_RR64, st); }));
+    CKS(vcycle<float>(h, 0, h->r32, h->z32, st));
+    CKS(launch(h, PMG_K_VECTOR, 1, st, Cost{20.0 * N, 2.0 * N}, [&] { return add_f32_scaled(N, h->x, h->z32, h->scal, SLOT_RR64, st); }));
+  }
+  CKS(outer_residual(h, h->b_copy, SLOT_RR64, st));
+  const double tol2 = h->opts.tol * h->opts.tol;
+  return launch(h, PMG_K_VECTOR, 1, st, [&] {
+    return loop_cond(hc, h->scal + SLOT_RR64, h->scal + SLOT_BB, tol2, h->d_iter, h->opts.max_iter, st);
+  });
+}
+
+pmg_status solve_pdc_graph(pmg_handle* h, const double* b, pmg_solve_info* info, cudaStream_t st) {
+  const size_t N = h->N;
+  const double tol2 = h->opts.tol * h->opts.tol;
+  if (!h->b_copy) {
+    cudaError_t e = cudaSuccess;
+    h->b_copy = h->alloc<double>(N, e);
+    CK(e);
+  }
+  CK(cudaMemcpyAsync(h->b_copy, b, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CKS(read_scalars(h, st));
+  const double rr = h->scal_host[SLOT_RR64];
+  if (!std::isfinite(rr)) return fail(PMG_ERR_NONFINITE, "non-finite residual");
+  if (rr <= tol2 * h->scal_host[SLOT_BB]) {
+    if (info) info->iterations = 0;
+    return PMG_OK;
+  }
+  if (h->loop_pdc.exec && h->loop_pdc_mix != h->mixed_stage) {
+    cudaGraphExecDestroy(h->loop_pdc.exec);
+    h->loop_pdc.exec = nullptr;
+  }
+  if (!h->loop_pdc.exec) {
+    CKS(build_loop(h, h->loop_pdc, [&](cudaStream_t cs, cudaGraphConditionalHandle hc) { return pdc_step(h, true, cs, hc); },
+                   [&](cudaStream_t cs, cudaGraphConditionalHandle hc) { return pdc_step(h, false, cs, hc); }));
+    h->loop_pdc_mix = h->mixed_stage;
+  }
+  int it = 0;
+  CKS(run_loop(h, h->loop_pdc, 0, st, &it));
+  if (!std::isfinite(h->scal_host[SLOT_RR64])) return fail(PMG_ERR_NONFINITE, "non-finite residual");
+  if (info) info->iterations = it;
+  return PMG_OK;
+}
+
 pmg_status solve_pdc(pmg_handle* h, const double* b, pmg_solve_info* info, cudaStream_t st) {
   // x <- x + B (b~ - A x) (Sec. 5.4); B = V-cycle in the handle's precision
   size_t N = h->N;
@@ -1570,6 +1709,8 @@ pmg_status pmg_create(const pmg_mesh_desc* mesh, const pmg_opts* opts, pmg_handl
     ALLOC(h->gm_part, double, (mm + 1) * 304);
     ALLOC(h->gm_y, double, mm);
     ALLOC(h->gm_cnt, unsigned, 1);
+    ALLOC(h->gm_state, double, (mm + 1) * mm + 3 * mm + 1);
+    ALLOC(h->gm_ctr, int, 2);
     if (cudaMemset(h->gm_cnt, 0, sizeof(unsigned)) != cudaSuccess ||
         cudaMemset(h->gm_V, 0, (mm + 1) * h->N * sizeof(double)) != cudaSuccess ||
         cudaMemset(h->gm_Z, 0, mm * h->N * sizeof(double)) != cudaSuccess)
@@ -1715,7 +1856,7 @@ pmg_status pmg_set_bathymetry(pmg_handle* h, const double* h_dev, void* stream) 
   CK(cudaMemcpy(h->mb, mb.data(), F.NX * sizeof(double), cudaMemcpyHostToDevice));
   h->bathy = true;
   // graphs captured before hold the constant-depth kernels: rebuild on next use
-  for (pmg_handle::Loop* lp : {&h->loop64, &h->loop32})
+  for (pmg_handle::Loop* lp : {&h->loop64, &h->loop32, &h->loop_gm, &h->loop_pdc})
     if (lp->exec) { cudaGraphExecDestroy(lp->exec); lp->exec = nullptr; }
   return pmg_set_geometry(h, h->eta, stream);
 }
@@ -1881,8 +2022,8 @@ pmg_status pmg_solve(pmg_handle* h, const double* b, const double* pD, const dou
     result = fail(PMG_ERR_NONFINITE, "non-finite right-hand side");
   } else if (bb > 0.0) {
     pmg_status s;
-    if (h->opts.outer == PMG_PDC) s = solve_pdc(h, b, &loc, st);
-    else if (h->opts.outer == PMG_GMRES) s = solve_gmres(h, b, &loc, st);
+    if (h->opts.outer == PMG_PDC) s = h->timing ? solve_pdc(h, b, &loc, st) : solve_pdc_graph(h, b, &loc, st);
+    else if (h->opts.outer == PMG_GMRES) s = h->timing ? solve_gmres(h, b, &loc, st) : solve_gmres_graph(h, b, &loc, st);
     else if (h->opts.outer == PMG_IR)
       s = h->timing ? solve_refine(h, b, &loc, st) : solve_refine_graph(h, b, &loc, st);
     else
@@ -2130,7 +2271,7 @@ pmg_status pmg_autotune(pmg_handle* h) {
     return curved<double>(h, 0, h->p, nullptr, h->w, 1, nullptr, cs);
   }, &h->thr_curved64));
   // graphs built before tuning keep the old sizes: rebuild on next use
-  for (pmg_handle::Loop* lp : {&h->loop64, &h->loop32})
+  for (pmg_handle::Loop* lp : {&h->loop64, &h->loop32, &h->loop_gm, &h->loop_pdc})
     if (lp->exec) { cudaGraphExecDestroy(lp->exec); lp->exec = nullptr; }
   CK(cudaDeviceSynchronize());
   return PMG_OK;

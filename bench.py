@@ -695,6 +695,35 @@ def run_bar(args, ws, rank, local):
     t0 = time.perf_counter()
     _, its, _, _ = omg.solve(m, F["eta"], bo, F["pD"], tol=1e-10, overlap=1, nu=2, omega=0.8)
     out["oracle_bar_p8_100x2"] = {"iterations": its, "s_incl_setup": time.perf_counter() - t0}
+    # time stepping over the bar: a surface hump (0.01 high, released at rest at x = 6) runs
+    # 500 RK4 steps of 0.02 (10 s: across the bar) with one pressure solve per stage
+    from paper_2411_14977_gb300.stepper import WaveTank
+    wl = W.bar(100, 2, 8)
+    stepping = {}
+    etas = {}
+    for name, opts in (("fp64_pcg", dict(precision=pmg.PMG_FP64)), ("mixed", dict(precision=pmg.PMG_MIXED_FP32))):
+        tank = WaveTank(wl, filter=(0, -36.0, 8.0), scheme="rk4", dt=0.02, **opts)
+        zero = np.zeros(tank.N)
+        tank.set_state(0.01 * np.exp(-((tank.xc - 6.0) / 1.5) ** 2), zero, zero)
+        for _ in range(10):
+            tank.step()
+        tank.solve_infos = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(490):
+            tank.step()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        infos = tank.solve_infos
+        assert all(i["status"] == 0 for i in infos), name
+        etas[name] = tank.eta.detach().cpu().numpy()
+        stepping[name] = {"solves": len(infos), "solves_per_s": len(infos) / wall, "wall_s": wall,
+                          "iterations_mean": float(np.mean([i["iterations"] for i in infos])),
+                          "max_rel_residual": max(i["rel_residual"] for i in infos),
+                          "final_max_eta": float(np.abs(etas[name]).max())}
+        log("bar stepping", name, stepping[name])
+    stepping["final_eta_maxdiff_mixed_vs_fp64_over_amp"] = float(np.abs(etas["mixed"] - etas["fp64_pcg"]).max() / 0.01)
+    out["stepping_bar_p8_100x2"] = stepping
     print(json.dumps({"workload": "bar", "results": out, "clocks": clk.stop()}), flush=True)
 
 

@@ -161,8 +161,9 @@ pmg_status pmg_set_geometry_mixed(pmg_handle* h, const double* eta_dev, const do
  * geometry set last is recomputed.  Synchronous on `stream` (tables are built on the host).
  * PMG_ERR_INVALID: NULL, a depth <= 0 or non-finite (also after interpolation to a coarse
  * level), the BF16 tensor-core operator (PMG_MIXED_BF16), a periodic mesh of one cell.
- * Afterwards pmg_set_geometry_mixed and pmg_gradient return PMG_ERR_INVALID (they take a
- * constant depth only); there is no way back to a constant depth but a new handle. */
+ * Gradient recovery (pmg_gradient) then uses the depth and its slope too.  Afterwards
+ * pmg_set_geometry_mixed returns PMG_ERR_INVALID (the mixed-stage operator takes a constant
+ * depth only); there is no way back to a constant depth but a new handle. */
 pmg_status pmg_set_bathymetry(pmg_handle* h, const double* h_dev, void* stream);
 
 /* b_i = -int N_i f dOmega + int_{Gamma_N} N_i g dGamma (LGL collocation), b = 0 on the

@@ -27,6 +27,7 @@ struct GradParams {
   const double* eta;    // [NX]
   const double* sigma;  // [NZ]
   double h, dx, dsig;
+  const double* hcol;   // [NX] still-water depth per node column (NULL: the constant h)
 };
 
 template <int P>
@@ -41,25 +42,33 @@ __global__ void __launch_bounds__(256) k_grad(GradParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* F = reinterpret_cast<double*>(smem_raw);  // [2P+1][NZp]: columns col0 - P ..
   double* E = F + (2 * P + 1) * NZp;                 // [2P+1] eta
-  double* DX = E + 2 * P + 1;                        // [2][n] d_x of the left and own elements
+  double* DX = E + 2 * P + 1;                        // [2][n] eta_x of the left and own elements
   double* SG = DX + 2 * n;                           // [NZ]
+  double* HC = SG + NZ;                              // [2P+1] still-water depth
+  double* HX = HC + 2 * P + 1;                       // [2][n] h_x (zero over a constant depth)
   for_slab(2 * P + 1, NZ, [&](int c, int iz) {
     bool ok = c >= P || left;
     cp_async_elem(&F[c * NZp + iz], p.f + (ok ? (size_t)wrap_col(s, col0 - P + c) * NZ + iz : 0), ok);
   });
   if (threadIdx.x < 2 * P + 1) {
     int c = threadIdx.x;
-    E[c] = (c >= P || left) ? p.eta[wrap_col(s, col0 - P + c)] : 0.0;
+    bool ok = c >= P || left;
+    E[c] = ok ? p.eta[wrap_col(s, col0 - P + c)] : 0.0;
+    HC[c] = (ok && p.hcol) ? p.hcol[wrap_col(s, col0 - P + c)] : p.h;
   }
   for (int t = threadIdx.x; t < NZ; t += blockDim.x) SG[t] = p.sigma[t];
   cp_async_wait_all();
   __syncthreads();
   if (threadIdx.x < 2 * n) {
     int el = threadIdx.x / n, i = threadIdx.x % n;  // el 0: left element, 1: own element
-    double acc = 0.0;
+    double acc = 0.0, hacc = 0.0;
 #pragma unroll
-    for (int m = 0; m < n; ++m) acc += cT.D[P][i][m] * E[el * P + m];
+    for (int m = 0; m < n; ++m) {
+      acc += cT.D[P][i][m] * E[el * P + m];
+      if (p.hcol) hacc += cT.D[P][i][m] * HC[el * P + m];
+    }
     DX[el * n + i] = acc * (2.0 / p.dx);
+    HX[el * n + i] = hacc * (2.0 / p.dx);
   }
   __syncthreads();
   // one thread per owned node: mean of the element values over the elements of the node
@@ -72,8 +81,9 @@ __global__ void __launch_bounds__(256) k_grad(GradParams p) {
     for (int el = ec0; el <= 1; ++el) {
       int li = el == 0 ? P : i;            // local column in that element
       const double* Fc = F + (el * P) * NZp;  // element's first column in the slab
-      double d = E[el * P + li] + p.h;
-      double ddx = DX[el * n + li];
+      double d = E[el * P + li] + HC[el * P + li];
+      double hx = HX[el * n + li];
+      double ddx = DX[el * n + li] + hx;  // d_x = eta_x + h_x
       for (int ez = ez0; ez <= ez_hi; ++ez) {
         int lj = iz - ez * P;
         double fr = 0.0, fs = 0.0;
@@ -83,7 +93,8 @@ __global__ void __launch_bounds__(256) k_grad(GradParams p) {
           fs += cT.D[P][lj][m] * Fc[li * NZp + ez * P + m];
         }
         double sg = SG[iz];
-        double beta = -sg * ddx * (2.0 / p.dsig) / d, gamma = 2.0 / (d * p.dsig);
+        // sigma_x = (h_x - sigma d_x) / d (Sec. 2.2)
+        double beta = (hx - sg * ddx) * (2.0 / p.dsig) / d, gamma = 2.0 / (d * p.dsig);
         sx += (2.0 / p.dx) * fr + beta * fs;
         sz += gamma * fs;
         ++cnt;
@@ -240,10 +251,10 @@ static unsigned grid_for(size_t n) {
 }
 
 cudaError_t gradient(const Shape& s, const double* f, double* fx, double* fz, const double* eta, const double* sigma,
-                     double h, double dx, double dsig, cudaStream_t st) {
-  GradParams p{s, f, fx, fz, eta, sigma, h, dx, dsig};
+                     double h, double dx, double dsig, cudaStream_t st, const double* hcol) {
+  GradParams p{s, f, fx, fz, eta, sigma, h, dx, dsig, hcol};
   int NZp = slab_pitch(s.NZ);
-  size_t sm = ((size_t)(2 * s.P + 1) * NZp + 2 * s.P + 1 + 2 * (s.P + 1) + s.NZ) * sizeof(double) + 16;
+  size_t sm = ((size_t)(2 * s.P + 1) * NZp + 2 * (2 * s.P + 1) + 4 * (s.P + 1) + s.NZ) * sizeof(double) + 16;
   switch (s.P) {
 #define PMG_CASE(PP)                                                        \
   case PP: {                                                                \

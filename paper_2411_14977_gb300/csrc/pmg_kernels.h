@@ -214,7 +214,8 @@ cudaError_t gmres_givens(cudaGraphConditionalHandle hnd, const double* c1, const
 cudaError_t gmres_backsub(const double* H, const double* g, double* y, int m, const int* jdev, cudaStream_t st);
 // time-stepper kernels (k_stepper.cu)
 cudaError_t gradient(const Shape& s, const double* f, double* fx, double* fz, const double* eta, const double* sigma,
-                     double h, double dx, double dsig, cudaStream_t st);
+                     double h, double dx, double dsig, cudaStream_t st,
+                     const double* hcol = nullptr);
 cudaError_t surface_slope(const Shape& s, const double* eta, double dx, double* etax, cudaStream_t st);
 cudaError_t spectral_filter(const Shape& s, const double* f, double* out, const double* F, int surface,
                             cudaStream_t st);

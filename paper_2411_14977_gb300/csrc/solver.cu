@@ -2098,13 +2098,13 @@ pmg_status pmg_profile_read(pmg_handle* h, int64_t* launches, double* ms, double
 pmg_status pmg_gradient(pmg_handle* h, const double* f, double* fx, double* fz, void* stream) {
   CKS(check_handle(h));
   if (!f || !fx || !fz) return fail(PMG_ERR_INVALID, "NULL vector");
-  if (h->bathy) return fail(PMG_ERR_INVALID, "gradient recovery takes a constant depth only");
   if (h->aniso) return fail(PMG_ERR_INVALID, "gradient recovery needs equal orders along x and sigma");
   DeviceGuard dg(h->device);
   cudaStream_t st = (cudaStream_t)stream;
   const Shape& F = h->lv[0].s;
   return launch(h, PMG_K_SETUP, 1, st, Cost{24.0 * h->N, 0.0}, [&] {
-    return gradient(F, f, fx, fz, h->eta, (const double*)h->sigma[0], h->mesh.h, h->dx, h->dsig, st);
+    return gradient(F, f, fx, fz, h->eta, (const double*)h->sigma[0], h->mesh.h, h->dx, h->dsig, st,
+                    h->bathy ? h->hcol : nullptr);
   });
 }
 

@@ -59,6 +59,9 @@ class WaveTank:
         S = self.S
         self.dev = torch.device(device)
         self.xc, self.sr = S.node_coords()
+        if workload.bathymetry is not None:  # varying still-water depth (projection schemes)
+            self.depth = torch.as_tensor(workload.depth(self.xc), dtype=torch.float64, device=self.dev)
+            S.set_bathymetry(self.depth)
         f64 = dict(dtype=torch.float64, device=self.dev)
         self.N, self.NX, self.NZ = S.n, S.NX, S.NZ
         z = lambda n=None: torch.zeros(self.N if n is None else n, **f64)
@@ -93,6 +96,12 @@ class WaveTank:
         if filter is not None:
             S.set_filter(*filter)
             self.ftmp = (z(self.NX), z(), z())
+
+    def set_state(self, eta, u, w):
+        """Initial surface (NX) and velocities (N), any array-likes."""
+        for dst, src in ((self.eta, eta), (self.u, u), (self.wv, w)):
+            dst.copy_(torch.as_tensor(np.asarray(src, dtype=np.float64)))
+        self.eta_p.copy_(self.eta)
 
     def set_linear_wave(self, amp, k):
         """Linear-theory progressive wave eta = a cos(kx) with its velocity field."""

@@ -217,9 +217,6 @@ def test_varying_depth_rejections():
     c = Case(w)
     with pytest.raises(pmg.PmgError):
         c.S.set_geometry_mixed(t(c.eta), t(c.eta))
-    f = torch.zeros(c.m.N, dtype=torch.float64, device="cuda")
-    with pytest.raises(pmg.PmgError):
-        c.S.gradient(f)
     S = pmg.Solver(**w.mesh_kwargs())
     xc, _ = S.node_coords()
     bad = w.depth(xc)

@@ -167,3 +167,25 @@ def test_mixed_stage_stage_divergence_and_projection_agreement():
     e2, u2, w2, _ = T.step_lserk(eta, u, w, dt)
     change = np.abs(e2 - eta).max()
     assert np.abs(e1 - e2).max() < 1e-2 * change, (np.abs(e1 - e2).max(), change)
+
+
+def test_gradient_exact_for_physical_linear_fields_over_sloped_bottom():
+    """sigma_x = (h_x - sigma d_x) / d over a varying still-water depth (Sec. 2.2)."""
+    import workloads as W
+    bar = W.Bar(1.0, 0.6, 1.0, 2.0, 0.3, 0.2)
+    T = Tank(dict(cells_x=6, cells_z=3, order=5, x0=0.0, x1=3.0, h=1.0, depth=bar))
+    m = T.m
+    eta = 0.05 * np.cos(2 * np.pi * m.column_x() / 3.0)
+    X, Z = m.node_xz(eta)
+    fx, fz = T.gradient(eta, 0.7 * X - 1.3 * Z + 0.2)
+    np.testing.assert_allclose(fx, 0.7, atol=1e-10)
+    np.testing.assert_allclose(fz, -1.3, atol=1e-10)
+
+
+def test_still_water_over_bar_stays_still():
+    import workloads as W
+    wl = W.bar(8, 2, 4)
+    T = Tank(dict(**wl.mesh_kwargs(), depth=wl.bathymetry))
+    z = np.zeros(T.m.NX), np.zeros(T.m.N), np.zeros(T.m.N)
+    eta, u, w, ps = T.step(*z, 0.01)
+    assert np.all(eta == 0.0) and np.all(u == 0.0) and np.all(w == 0.0)

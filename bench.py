@@ -71,6 +71,21 @@ def parse():
     return ap.parse_args()
 
 
+def aggregate_over_ranks(t_local, units_per_step, steps, ws, device="cpu"):
+    """Whole-job rate of `ws` independent replicas (the path has no exchange step across
+    tanks): the job lasts as long as its slowest rank, so the per-rank times are reduced by
+    MAX over the process group (any backend: NCCL with CUDA tensors, gloo on the CPU), and
+    value = ws * units_per_step * steps / t_max.  Returns (t_max, value)."""
+    t = float(t_local)
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        tt = torch.tensor([t], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    return t, ws * units_per_step * steps / t
+
+
 def dist_setup(args):
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -254,11 +269,7 @@ def run_ours(args, ws, rank, local):
         return sum(a.elapsed_time(b) for a, b in evs) / 1e3, infos
 
     def all_max(x):
-        if ws == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+        return aggregate_over_ranks(x, 1, 1, ws, device=dev)[0]
 
     # ---- headline: mixed precision (FP32 V-cycle inside FP64 refinement)
     S, host, d, bufs = setup(precision=pmg.PMG_MIXED_FP32)
@@ -285,9 +296,8 @@ def run_ours(args, ws, rank, local):
     clocks = clk.stop()
     prof = S.profile_read(full=True)
     launches = int(sum(v[0] for v in prof.values()))
-    t_dev = all_max(t_dev)
     K = args.steps
-    value = ws * S.n_free * K / t_dev
+    t_dev, value = aggregate_over_ranks(t_dev, S.n_free, K, ws, device=dev)
     for inf in infos:
         assert inf["status"] == 0 and inf["rel_residual"] <= 1e-10, inf
 

@@ -1,0 +1,53 @@
+"""The N > 1 path of bench.py on CPU: replicas of the solve (no data-path collective), the
+whole-job rate from the slowest rank by a MAX all-reduce, run here as two gloo ranks; and
+the reference arm under a multi-rank launch (rank 0 alone works)."""
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, ws, port, out):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=ws)
+    t, value = bench.aggregate_over_ranks(1.0 + rank, 1000.0, 5, ws)
+    out[rank] = (t, value)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_replica_rate_takes_the_slowest_rank_gloo():
+    ws = 2
+    with mp.get_context("spawn").Manager() as mgr:
+        out = mgr.dict()
+        mp.start_processes(_rank, args=(ws, _free_port(), out), nprocs=ws, join=True, start_method="spawn")
+        res = dict(out)
+    # rank times 1 s and 2 s: the job takes 2 s for 2 x 1000 x 5 units
+    assert res[0] == res[1] == (2.0, 2 * 1000.0 * 5 / 2.0)
+
+
+def test_single_rank_rate_has_no_collective():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.aggregate_over_ranks(0.5, 10.0, 4, 1) == (0.5, 80.0)
+
+
+def test_reference_arm_other_ranks_exit_without_work():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1", MASTER_ADDR="127.0.0.1", MASTER_PORT="29531")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
+                        "--steps", "1", "--warmup", "0"], env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == ""

@@ -743,7 +743,7 @@ pmg_status level_smooth(pmg_handle* h, int l, const void* b, void* x, int post, 
   }
   for (int it = 0; it < nu; ++it) {
     if (it == 0 && x_zero) {
-      CKS(level_fdm<T>(h, l, b, x, post, st));
+      CKS(level_fdm<T>(h, l, b, x, post, st, nullptr, nullptr, PI<T> && !L.var && !L.aniso));
     } else {
       CKS(level_residual<T>(h, l, b, x, L.t[PI<T>], 1, st));
       CKS(level_fdm<T>(h, l, L.t[PI<T>], x, post, st));
@@ -790,7 +790,12 @@ pmg_status vcycle(pmg_handle* h, int l, const void* b, void* x, cudaStream_t st)
   LevelDev& L = h->lv[l];
   size_t NL = (size_t)L.s.NX * L.s.NZ;
   if (l == nl - 1) return launch(h, PMG_K_COARSE, 3, st, coarse_cost<T>(h), [&] { return coarse_solve<T>(h->coarse, b, x, st); });
-  CK(cudaMemsetAsync(x, 0, NL * sizeof(T), st));
+  // x = 0 before the first sweep.  The FP32 sweep of constant-memory tables reads a zero
+  // iterate as zero without loading it and writes every node below the surface row, so on
+  // the handle's own level buffers (surface row zeroed at setup, never written) the clear
+  // is implicit; elsewhere (the caller's level-0 output, the generic sweep) it is a memset.
+  const bool implicit_zero = PI<T> && l > 0 && !L.var && !L.aniso;
+  if (!implicit_zero) CK(cudaMemsetAsync(x, 0, NL * sizeof(T), st));
   CKS(level_smooth<T>(h, l, b, x, 0, true, st));
   LevelDev& C = h->lv[l + 1];
   if (L.fuse_restrict) {

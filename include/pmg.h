@@ -63,10 +63,10 @@ enum { PMG_FP64 = 0, PMG_MIXED_FP32 = 1, PMG_MIXED_BF16 = 2 };
 enum { PMG_PCG = 0, PMG_FCG = 1, PMG_PDC = 2, PMG_IR = 3, PMG_GMRES = 4 };
 /* smoother: element-block additive Schwarz (Sec. 5.3), blocks inverted by fast
  * diagonalisation (exact for the separable flat-geometry level operators) */
-enum { PMG_ASM_FDM = 0 };
+enum { PMG_ASM_FDM = 0, PMG_ASM_DENSE = 1 };
 /* geometry the multigrid levels are built on: the flat, linearised (eta = 0) geometry
  * that makes the preconditioner time-constant (Sec. 5.4) */
-enum { PMG_FLAT_LINEARISED = 1 };
+enum { PMG_ACTUAL = 0, PMG_FLAT_LINEARISED = 1 };
 
 typedef struct {
   double x0, x1;     /* horizontal extent of the tank                                     */
@@ -84,8 +84,12 @@ typedef struct {
 typedef struct {
   int precision;     /* PMG_FP64 | PMG_MIXED_FP32 | PMG_MIXED_BF16                          */
   int outer;         /* PMG_PCG | PMG_FCG | PMG_PDC | PMG_IR                                */
-  int smoother;      /* PMG_ASM_FDM                                                         */
-  int precond_geom;  /* PMG_FLAT_LINEARISED                                                 */
+  int smoother;      /* PMG_ASM_FDM (fast diagonalisation) | PMG_ASM_DENSE (dense inverses of
+                        the (P+1+2o)^2-node subdomain blocks, built on the device, Sec. 5.3) */
+  int precond_geom;  /* PMG_FLAT_LINEARISED (time-constant levels on eta = 0, Sec. 5.4) |
+                        PMG_ACTUAL (every level but the order-1 one re-discretised on the
+                        current surface at each pmg_set_geometry; needs PMG_ASM_DENSE, equal
+                        orders and a constant depth)                                        */
   int overlap;       /* Schwarz overlap in node lines (0 or 1)                              */
   int nu;            /* pre- and post-smoothing sweeps per level (>= 1)                     */
   double omega;      /* smoother damping                                                    */

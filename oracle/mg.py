@@ -97,9 +97,12 @@ class Hierarchy:
     the level's nodes).
     """
 
-    def __init__(self, mesh, eta, orders=None, overlap=1, nu=2, omega=1.0, geometry='flat'):
+    def __init__(self, mesh, eta, orders=None, overlap=1, nu=2, omega=1.0, geometry='flat', coarse_geometry=None):
         """orders: x-orders of the levels (equal orders in both directions), or (p_x, p_z)
-        pairs; default: the coarsening rule, with semi-coarsening when P_z != P."""
+        pairs; default: the coarsening rule, with semi-coarsening when P_z != P.
+        coarse_geometry: geometry of the coarsest level ('flat' or 'actual'; default: as
+        `geometry`).  With geometry='actual' and coarse_geometry='flat' the order-1 level
+        keeps the still-water operator, whose exact solve is separable."""
         if orders is None:
             pairs = (basis.semi_coarsening_sequence(mesh.P, mesh.Pz) if mesh.Pz != mesh.P
                      else [(p, p) for p in basis.coarsening_sequence(mesh.P)])
@@ -113,13 +116,15 @@ class Hierarchy:
         self.levels = []
         self.P = []                      # prolongations level l+1 -> l on free nodes
         eta = np.asarray(eta, float)
+        coarse_geometry = geometry if coarse_geometry is None else coarse_geometry
         for l, (p, pz) in enumerate(self.pairs):
+            geo_l = coarse_geometry if l == len(self.pairs) - 1 else geometry
             ml = Mesh(mesh.Nx, mesh.Nz, p, mesh.x0, mesh.x1, mesh.h, mesh.periodic, order_z=pz)
             if mesh.variable_depth:
                 probe = ml
                 h_l = self._eta_at_level(mesh, mesh.hcol, probe)
                 ml = Mesh(mesh.Nx, mesh.Nz, p, mesh.x0, mesh.x1, mesh.h, mesh.periodic, depth=h_l, order_z=pz)
-            if geometry == 'flat':
+            if geo_l == 'flat':
                 if mesh.variable_depth:
                     A_l = ml.assemble_separable(ml.hcol)
                 else:

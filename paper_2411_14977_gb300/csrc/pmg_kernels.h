@@ -41,6 +41,7 @@ cudaError_t init_consts_stepper(const ConstTables* host);
 cudaError_t init_consts_apply_bathy(const ConstTables* host);
 cudaError_t init_consts_apply_aniso(const ConstTables* host);
 cudaError_t init_consts_levels_aniso(const ConstTables* host);
+cudaError_t init_consts_dense(const ConstTables* host);
 
 // Layout of the FP32 Schwarz eigenvector table (constant memory of the FP32 smoother):
 // for every (P, O) with 2 <= P <= MAXP and O <= (P-1)/2, eight NB x NB blocks
@@ -140,6 +141,19 @@ struct FdmArgs {
   int overlap_z = -1;  // overlap along sigma (-1: overlap)
 };
 template <typename T> cudaError_t fdm_smooth(const FdmArgs& a, cudaStream_t st);
+// Dense additive Schwarz (k_dense.cu): block inverses of the level operator described by
+// the per-column factors geo [Nx][P+1][4] (A, B, C, E as the operator kernels) and sigma
+// rows, FP64 and FP32 [Nx*Nz][NB*NB]; a sweep x += omega (W) sum R^T A_e^-1 R (W) r with
+// the per-subdomain scratch U [Nx*Nz][NB].
+size_t dense_block_elems(const Shape& s, int ox, int oz);
+// the fine surface polynomial of each cell at a level's nodes: out = E eta per cell
+cudaError_t eta_level(const Shape& fine, const Shape& lev, const double* E, const double* eta, double* out,
+                      cudaStream_t st);
+cudaError_t dense_setup(const Shape& s, int ox, int oz, const double* geo, const double* sigma, double* inv64,
+                        float* inv32, cudaStream_t st);
+template <typename T>
+cudaError_t dense_sweep(const Shape& s, int ox, int oz, const T* inv, const T* r, T* x, const T* wx, const T* wz,
+                        int post, double omega, T* U, cudaStream_t st);
 // Level operator, generic sweep and actual-geometry operator for different orders along x
 // and sigma (s.pz() != s.P): the pairs of the paper's scaling study (k_levels_aniso.cu,
 // k_apply_aniso.cu); other pairs return cudaErrorInvalidValue.

@@ -103,6 +103,7 @@ pmg_status ensure_constants(int dev) {
   CK(init_consts_apply_bathy(&t));
   CK(init_consts_apply_aniso(&t));
   CK(init_consts_levels_aniso(&t));
+  CK(init_consts_dense(&t));
   {
     std::vector<float> tab(fdm32_table_size(), 0.f);
     for (int P = 2; P <= MAXP; ++P)
@@ -246,6 +247,18 @@ struct LevelDev {
   void* mXd[2]{};      // [NX] (dx/dsig) sum over the column's elements of w / d
   void* Vxc[2]{};      // [Nx][NB][NB] Schwarz x-eigenvectors of each element column
   void* invdenc[2]{};  // [Nx][4][NB][NB] 1 / (lambda_x + lambda_z)
+  // dense Schwarz (PMG_ASM_DENSE): subdomain inverses of the level operator and scratch
+  bool dense = false;
+  void* dinv[2]{};           // [Nx*Nz][NB*NB] FP64 / FP32
+  void* dU[2]{};             // [Nx*Nz][NB]
+  double* dgeo = nullptr;    // [Nx][P+1][4] column factors of the level operator
+  double* dsig = nullptr;    // [NZ] sigma rows of the level
+  // PMG_ACTUAL: the level re-discretised on the current surface
+  bool actual = false;
+  double* Eeta = nullptr;    // [(p+1) x (P+1)] the fine surface polynomial at this level's nodes
+  double* aeta = nullptr;    // [NX] surface at this level's node columns
+  void* ageo[2]{};           // [Nx][p+1][4] column factors of the level operator
+  float* asig32 = nullptr;   // [NZ] sigma rows (FP32)
 };
 
 struct pmg_handle {
@@ -374,6 +387,50 @@ pmg_status launch(pmg_handle* h, int cls, int nkernels, cudaStream_t st, F&& f) 
 }
 
 // ---- setup helpers -----------------------------------------------------------------
+// Dense Schwarz tables of level l (PMG_ASM_DENSE): the level operator's column factors
+// (flat: depth dl per node column of the level, or the constant depth; no slope terms),
+// its sigma rows, and the subdomain inverses built on the device.
+pmg_status build_level_dense(pmg_handle* h, int l, const std::vector<double>* dl) {
+  LevelDev& L = h->lv[l];
+  const pmg_mesh_desc& m = h->mesh;
+  const int p = L.order, pz = L.order_z, n = p + 1;
+  std::vector<double> xg, w, zg, wzv;
+  lgl(p, xg, w);
+  lgl(pz, zg, wzv);
+  std::vector<double> geo((size_t)m.cells_x * n * 4, 0.0), sig(L.s.NZ);
+  Line1D lx(p, m.cells_x, m.periodic_x);
+  for (int ex = 0; ex < m.cells_x; ++ex)
+    for (int i = 0; i < n; ++i) {
+      const double d = dl ? (*dl)[lx.wrap(ex * p + i)] : m.h;
+      double* g = &geo[((size_t)ex * n + i) * 4];
+      g[0] = w[i] * d * h->dsig / h->dx;
+      g[2] = w[i] * (h->dx / h->dsig) / d;
+    }
+  for (int iz = 0; iz < L.s.NZ; ++iz) {
+    int ez = std::min(iz / pz, m.cells_z - 1), j = iz - ez * pz;
+    sig[iz] = (ez + (zg[j] + 1.0) / 2.0) * h->dsig;
+  }
+  cudaError_t e = cudaSuccess;
+  const size_t E = (size_t)m.cells_x * m.cells_z, nb2 = dense_block_elems(L.s, L.overlap, L.overlap_z);
+  const size_t nb = (size_t)(p + 1 + 2 * L.overlap) * (pz + 1 + 2 * L.overlap_z);
+  if (!L.dinv[0]) {
+    L.dinv[0] = h->alloc<double>(E * nb2, e); CK(e);
+    L.dinv[1] = h->alloc<float>(E * nb2, e); CK(e);
+    L.dU[0] = h->alloc<double>(E * nb, e); CK(e);
+    L.dU[1] = h->alloc<float>(E * nb, e); CK(e);
+    L.dgeo = h->alloc<double>(geo.size(), e); CK(e);
+    L.dsig = h->alloc<double>(sig.size(), e); CK(e);
+  }
+  CK(cudaMemcpy(L.dgeo, geo.data(), geo.size() * sizeof(double), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(L.dsig, sig.data(), sig.size() * sizeof(double), cudaMemcpyHostToDevice));
+  CK(dense_setup(L.s, L.overlap, L.overlap_z, L.dgeo, L.dsig, (double*)L.dinv[0], (float*)L.dinv[1], nullptr));
+  CK(cudaDeviceSynchronize());
+  L.dense = true;
+  L.fuse_res = false;
+  L.fuse_restrict = false;
+  return PMG_OK;
+}
+
 pmg_status build_level(pmg_handle* h, int l) {
   LevelDev& L = h->lv[l];
   const pmg_mesh_desc& m = h->mesh;
@@ -485,6 +542,30 @@ pmg_status build_level(pmg_handle* h, int l) {
     L.Jz = L.J;
   } else {
     L.Jz = upload<double>(transfer_or_identity(pcz, pz), h->allocs, e); CK(e);
+  }
+  if (h->opts.smoother == PMG_ASM_DENSE) CKS(build_level_dense(h, l, nullptr));
+  if (h->opts.precond_geom == PMG_ACTUAL) {
+    // the surface and column factors are filled by pmg_set_geometry
+    const int P = h->orders[0];
+    std::vector<double> E;
+    if (p == P) {
+      E.assign((size_t)(P + 1) * (P + 1), 0.0);
+      for (int i = 0; i <= P; ++i) E[(size_t)i * (P + 1) + i] = 1.0;
+    } else {
+      E = transfer_matrix(P, p);
+    }
+    L.Eeta = upload<double>(E, h->allocs, e); CK(e);
+    L.aeta = h->alloc<double>(L.s.NX, e); CK(e);
+    L.ageo[0] = h->alloc<double>((size_t)m.cells_x * (p + 1) * 4, e); CK(e);
+    L.ageo[1] = h->alloc<float>((size_t)m.cells_x * (p + 1) * 4, e); CK(e);
+    std::vector<double> sg(L.s.NZ), zg, wzv;
+    lgl(pz, zg, wzv);
+    for (int iz = 0; iz < L.s.NZ; ++iz) {
+      int ez = std::min(iz / pz, m.cells_z - 1), j = iz - ez * pz;
+      sg[iz] = (ez + (zg[j] + 1.0) / 2.0) * h->dsig;
+    }
+    L.asig32 = upload<float>(sg, h->allocs, e); CK(e);
+    L.actual = true;
   }
   return PMG_OK;
 }
@@ -669,6 +750,24 @@ template <typename T>
 pmg_status level_residual(pmg_handle* h, int l, const void* b, const void* x, void* y, int residual,
                           cudaStream_t st) {
   LevelDev& L = h->lv[l];
+  if (L.actual) {  // the actual-geometry operator at the level's order and surface
+    CurvedArgs c{};
+    c.s = L.s;
+    c.mode = residual ? 1 : 0;
+    c.x = x;
+    c.b = b;
+    c.y = y;
+    c.geo = L.ageo[PI<T>];
+    c.sigma = PI<T> ? (const void*)L.asig32 : (const void*)L.dsig;
+    c.scale = 1.0;
+    c.mask_input = residual ? 0 : 1;
+    c.result = h->scal + SLOT_AUX + 5;
+    c.sc = h->sc;
+    c.threads = 256;
+    double NL = (double)L.s.NX * L.s.NZ, E = (double)L.s.Nx * L.s.Nz, n = L.s.P + 1;
+    Cost cc{(residual ? 3.0 : 2.0) * NL * sizeof(T), E * (8.0 * n * n * n + 12.0 * n * n)};
+    return launch(h, PI<T> ? PMG_K_LEVEL32 : PMG_K_LEVEL64, 1, st, cc, [&] { return curved_op<T>(c, st); });
+  }
   FlatArgs a{L.s, x, b, y, L.var ? 1.0 : h->cx, L.var ? 1.0 : h->cz, L.var ? L.mXd[PI<T>] : L.mX[PI<T>],
              L.mZ[PI<T>], residual, PI<T> ? L.thr_flat32 : 256};
   if (L.var) a.Kx = L.Kx[PI<T>];
@@ -692,6 +791,13 @@ pmg_status level_fdm(pmg_handle* h, int l, const void* r, void* x, int post, cud
   if (PI<T>) {
     a.xout = xout;
     a.xzero = xzero ? 1 : 0;
+  }
+  if (L.dense) {
+    if (fused_b || (xout && xout != x)) return fail(PMG_ERR_INVALID, "fused sweep with the dense smoother");
+    return launch(h, PI<T> ? PMG_K_SMOOTH32 : PMG_K_SMOOTH64, 2, st, c, [&] {
+      return dense_sweep<T>(L.s, L.overlap, L.overlap_z, (const T*)L.dinv[PI<T>], (const T*)r, (T*)x,
+                            (const T*)L.wx[PI<T>], (const T*)L.wz[PI<T>], post, h->opts.omega, (T*)L.dU[PI<T>], st);
+    });
   }
   if (L.var || L.aniso) {
     // per element column x-classes (varying depth) or different orders: the generic sweep
@@ -743,7 +849,7 @@ pmg_status level_smooth(pmg_handle* h, int l, const void* b, void* x, int post, 
   }
   for (int it = 0; it < nu; ++it) {
     if (it == 0 && x_zero) {
-      CKS(level_fdm<T>(h, l, b, x, post, st, nullptr, nullptr, PI<T> && !L.var && !L.aniso));
+      CKS(level_fdm<T>(h, l, b, x, post, st, nullptr, nullptr, PI<T> && !L.var && !L.aniso && !L.dense));
     } else {
       CKS(level_residual<T>(h, l, b, x, L.t[PI<T>], 1, st));
       CKS(level_fdm<T>(h, l, L.t[PI<T>], x, post, st));
@@ -794,7 +900,7 @@ pmg_status vcycle(pmg_handle* h, int l, const void* b, void* x, cudaStream_t st)
   // iterate as zero without loading it and writes every node below the surface row, so on
   // the handle's own level buffers (surface row zeroed at setup, never written) the clear
   // is implicit; elsewhere (the caller's level-0 output, the generic sweep) it is a memset.
-  const bool implicit_zero = PI<T> && l > 0 && !L.var && !L.aniso;
+  const bool implicit_zero = PI<T> && l > 0 && !L.var && !L.aniso && !L.dense;
   if (!implicit_zero) CK(cudaMemsetAsync(x, 0, NL * sizeof(T), st));
   CKS(level_smooth<T>(h, l, b, x, 0, true, st));
   LevelDev& C = h->lv[l + 1];
@@ -1585,8 +1691,13 @@ pmg_status pmg_create(const pmg_mesh_desc* mesh, const pmg_opts* opts, pmg_handl
     return fail(PMG_ERR_INVALID, "gmres_restart must be in 1..60");
   if (o.outer == PMG_IR && o.precision == PMG_FP64)
     return fail(PMG_ERR_INVALID, "iterative refinement needs a mixed precision");
-  if (o.smoother != PMG_ASM_FDM || o.precond_geom != PMG_FLAT_LINEARISED)
+  if ((o.smoother != PMG_ASM_FDM && o.smoother != PMG_ASM_DENSE) ||
+      (o.precond_geom != PMG_FLAT_LINEARISED && o.precond_geom != PMG_ACTUAL))
     return fail(PMG_ERR_INVALID, "unsupported smoother or preconditioner geometry");
+  if (o.precond_geom == PMG_ACTUAL && o.smoother != PMG_ASM_DENSE)
+    return fail(PMG_ERR_INVALID, "levels on the actual geometry are not separable: they need PMG_ASM_DENSE");
+  if (o.precond_geom == PMG_ACTUAL && m.order_z != 0 && m.order_z != m.order)
+    return fail(PMG_ERR_INVALID, "levels on the actual geometry need equal orders along x and sigma");
   if (o.overlap < 0 || o.overlap > MAXO || o.nu < 1 || !(o.omega > 0) || !(o.tol > 0) || o.max_iter < 1 ||
       o.inner_max < 1 || !(o.inner_tol > 0) || o.fuse_residual < -1 || o.fuse_residual > 1 || o.df64_outer < -1 ||
       o.df64_outer > 1 || o.flat_kernel < -1 || o.flat_kernel > 1)
@@ -1616,6 +1727,13 @@ pmg_status pmg_create(const pmg_mesh_desc* mesh, const pmg_opts* opts, pmg_handl
     orders = coarsening_sequence(m.order);
   }
   if (orders_z.empty()) orders_z = orders;
+  if (o.smoother == PMG_ASM_DENSE)
+    for (size_t l = 0; l + 1 < orders.size(); ++l) {
+      const int ox = orders[l] >= 3 ? o.overlap : 0, oz = orders_z[l] >= 3 ? o.overlap : 0;
+      const size_t nb = (size_t)(orders[l] + 1 + 2 * ox) * (orders_z[l] + 1 + 2 * oz);
+      if (nb * nb * sizeof(double) > 227 * 1024)
+        return fail(PMG_ERR_INVALID, "dense Schwarz blocks too large for one CTA (order 10 with overlap 1)");
+    }
   if (orders.size() < 2) return fail(PMG_ERR_INVALID, "order must be >= 2 (the coarsest level is order 1)");
 
   auto* h = new (std::nothrow) pmg_handle();
@@ -1793,6 +1911,17 @@ pmg_status pmg_set_geometry(pmg_handle* h, const double* eta_dev, void* stream) 
     CKS(launch(h, PMG_K_SETUP, 1, st, [&] { return geometry<float>(F, h->eta, h->mesh.h, nullptr, h->dx, h->dsig, 0, (float*)h->geo[1], gst, st); }));
   }
   CKS(launch(h, PMG_K_SETUP, 1, st, [&] { return geometry<double>(F, h->eta, h->mesh.h, hc, h->dx, h->dsig, 1, h->geo_div, gst, st); }));
+  for (LevelDev& L : h->lv) {
+    if (!L.actual) continue;
+    // the level on the current surface: eta at its nodes, column factors, dense inverses
+    CKS(launch(h, PMG_K_SETUP, 1, st, [&] { return eta_level(F, L.s, L.Eeta, h->eta, L.aeta, st); }));
+    CKS(launch(h, PMG_K_SETUP, 1, st, [&] { return geometry<double>(L.s, L.aeta, h->mesh.h, nullptr, h->dx, h->dsig, 0, (double*)L.ageo[0], gst, st); }));
+    CKS(launch(h, PMG_K_SETUP, 1, st, [&] { return geometry<float>(L.s, L.aeta, h->mesh.h, nullptr, h->dx, h->dsig, 0, (float*)L.ageo[1], gst, st); }));
+    CKS(launch(h, PMG_K_SETUP, 1, st, [&] {
+      return dense_setup(L.s, L.overlap, L.overlap_z, (const double*)L.ageo[0], L.dsig, (double*)L.dinv[0],
+                         (float*)L.dinv[1], st);
+    }));
+  }
   h->mixed_stage = false;
   return PMG_OK;
 }
@@ -1801,6 +1930,8 @@ pmg_status pmg_set_bathymetry(pmg_handle* h, const double* h_dev, void* stream) 
   CKS(check_handle(h));
   if (!h_dev) return fail(PMG_ERR_INVALID, "depth is NULL");
   if (h->aniso) return fail(PMG_ERR_INVALID, "a varying depth needs equal orders along x and sigma");
+  if (h->opts.precond_geom == PMG_ACTUAL)
+    return fail(PMG_ERR_INVALID, "levels on the actual geometry take a constant depth only");
   if (h->tc) return fail(PMG_ERR_INVALID, "the BF16 tensor-core operator takes a constant depth only");
   if (h->mesh.periodic_x && h->mesh.cells_x < 2) return fail(PMG_ERR_INVALID, "periodic mesh needs 2 or more cells");
   DeviceGuard dg(h->device);
@@ -1831,7 +1962,10 @@ pmg_status pmg_set_bathymetry(pmg_handle* h, const double* h_dev, void* stream) 
     for (double v : dl[l])
       if (!(v > 0.0)) return fail(PMG_ERR_INVALID, "the depth interpolated to a coarse level is not positive");
   }
-  for (size_t l = 0; l < h->lv.size(); ++l) CKS(build_level_var(h, (int)l, dl[l]));
+  for (size_t l = 0; l < h->lv.size(); ++l) {
+    CKS(build_level_var(h, (int)l, dl[l]));
+    if (h->opts.smoother == PMG_ASM_DENSE && l + 1 < h->lv.size()) CKS(build_level_dense(h, (int)l, &dl[l]));
+  }
   {
     std::vector<double> V, coef, inv;
     int nsteps = 0;
@@ -2212,6 +2346,7 @@ pmg_status pmg_autotune(pmg_handle* h) {
     void* b = L.b[1];
     void* t = L.t[1];
     // slab CTAs (positive sizes) or node-parallel CTAs (negative sizes)
+    if (!L.actual)
     CKS(tune_one(h, L.var ? TK_FLAT32V : TK_FLAT32, L.order + 100 * (L.aniso ? L.order_z : 0), L.s.NZ,
                  [&](int thr, cudaStream_t cs) {
       L.thr_flat32 = thr;
@@ -2220,8 +2355,8 @@ pmg_status pmg_autotune(pmg_handle* h) {
                        : h->opts.flat_kernel == 0 ? std::initializer_list<int>{64, 128, 192, 256, 320, 384, 512}
                        : std::initializer_list<int>{64, 128, 192, 256, 320, 384, 512, -64, -128, -256}));
     if (l == nl - 1) continue;
-    if (L.var || L.aniso) {
-      // varying depth or different orders: generic sweep (fixed CTA size), split residuals;
+    if (L.var || L.aniso || L.dense) {
+      // varying depth, different orders or dense blocks: no k_fdm32 sweep, split residuals;
       // only the transfers tune
       LevelDev& C = h->lv[l + 1];
       CKS(tune_one(h, TK_XFER, L.order * 16 + C.order + 1000 * (L.aniso ? L.order_z : 0), L.s.NZ,

@@ -15,6 +15,8 @@ PMG_ERR_NOT_CONVERGED, PMG_ERR_NONFINITE, PMG_ERR_TIMEOUT = 4, 5, 6
 PMG_FP64, PMG_MIXED_FP32, PMG_MIXED_BF16 = 0, 1, 2
 PMG_PCG, PMG_FCG, PMG_PDC, PMG_IR, PMG_GMRES = 0, 1, 2, 3, 4
 PMG_ASM_FDM = 0
+PMG_ASM_DENSE = 1
+PMG_ACTUAL = 0
 PMG_FLAT_LINEARISED = 1
 
 KERNEL_CLASSES = ["curved64", "curved32", "level64", "level32", "smooth64", "smooth32", "transfer",

@@ -152,3 +152,27 @@ def test_fgmres_with_vcycle_matches_pcg_solution():
     np.testing.assert_allclose(p1, p2, rtol=0, atol=1e-9 * np.abs(p2).max())
     assert hist_g[-1] <= 1e-12
     assert its_g <= its_c + 1
+
+
+def test_actual_geometry_hierarchy_reduces_to_flat_at_rest_and_is_symmetric():
+    """Re-discretised levels (geometry='actual', the coarsest kept flat): at eta = 0 the
+    V-cycle is the flat one; on a wave it stays a symmetric preconditioner and PCG reaches
+    the direct solution."""
+    import workloads as W
+    from oracle.sem import Mesh, solve_direct
+    wl = W.tank(8, 2, 5)
+    m = Mesh(**wl.mesh_kwargs())
+    F = wl.fields(m.column_x(), m.row_sigma())
+    flat = mg.Hierarchy(m, F["eta"], overlap=1, nu=2, omega=0.8)
+    act0 = mg.Hierarchy(m, np.zeros(m.NX), overlap=1, nu=2, omega=0.8, geometry='actual', coarse_geometry='flat')
+    n = flat.levels[0].free.size
+    r = np.sin(np.arange(n) * 0.7)
+    np.testing.assert_allclose(act0.vcycle(r), flat.vcycle(r), rtol=0, atol=1e-12 * np.abs(flat.vcycle(r)).max())
+    eta = 4.0 * F["eta"]
+    act = mg.Hierarchy(m, eta, overlap=1, nu=2, omega=0.8, geometry='actual', coarse_geometry='flat')
+    r2 = np.cos(np.arange(n) * 0.3)
+    assert abs(r2 @ act.vcycle(r) - r @ act.vcycle(r2)) <= 1e-12 * abs(r2 @ act.vcycle(r))
+    b = m.rhs_divergence(eta, F["u"], F["w"])
+    p, its, _, _ = mg.solve(m, eta, b, F["pD"], hier=act, tol=1e-10)
+    pref = solve_direct(m.assemble(eta), b, F["pD"], m.dirichlet_mask())
+    assert np.max(np.abs(p - pref)) <= 1e-8 * np.max(np.abs(pref)) and its <= 15

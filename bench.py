@@ -815,7 +815,10 @@ def run_variants(args, ws, rank, local):
     variants = [("fp64_pcg", dict(precision=pmg.PMG_FP64)),
                 ("mixed_fp32_fcg", dict(precision=pmg.PMG_MIXED_FP32)),
                 ("mixed_fp32_ir", dict(precision=pmg.PMG_MIXED_FP32, outer=pmg.PMG_IR)),
-                ("mixed_bf16_ir", dict(precision=pmg.PMG_MIXED_BF16, outer=pmg.PMG_IR))]
+                ("mixed_bf16_ir", dict(precision=pmg.PMG_MIXED_BF16, outer=pmg.PMG_IR)),
+                ("mixed_fp32_fcg_dense_schwarz", dict(precision=pmg.PMG_MIXED_FP32, smoother=pmg.PMG_ASM_DENSE)),
+                ("mixed_fp32_fcg_actual_levels", dict(precision=pmg.PMG_MIXED_FP32, smoother=pmg.PMG_ASM_DENSE,
+                                                      precond_geom=pmg.PMG_ACTUAL))]
     ref = None
     out = {}
     clk = ClockSampler(local)
@@ -851,6 +854,14 @@ def run_variants(args, ws, rank, local):
         out[name] = {"ms_per_solve": ms, "dof_per_s": S.n_free / (ms / 1e3), "iterations": info["iterations"],
                      "inner_iterations": info["inner_iterations"], "rel_residual": info["rel_residual"],
                      "rel_l2_err_vs_fp64": err}
+        if opts.get("precond_geom") == pmg.PMG_ACTUAL:
+            # the levels follow the surface: pmg_set_geometry rebuilds them (dense inverses)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            S.set_geometry(d["eta"])
+            e1.record()
+            torch.cuda.synchronize()
+            out[name]["set_geometry_ms"] = e0.elapsed_time(e1)
         log(name, out[name])
         if name == "mixed_bf16_ir":
             # the operator builds alone: CUDA-event time per launch (graph-free, warm)

@@ -23,6 +23,8 @@ CASES = {
     "tank7x3p2": lambda: W.tank(7, 3, 2),
     "bar12x2p6": lambda: W.bar(12, 2, 6),
     "p4z8": lambda: W.paper_scaling(10, 4, order_z=8),
+    "tank1x2p5_nx1": lambda: W.tank(1, 2, 5),
+    "tank5x1p4_nz1": lambda: W.tank(5, 1, 4),
 }
 _cache = {}
 

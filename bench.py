@@ -854,6 +854,19 @@ def run_variants(args, ws, rank, local):
         out[name] = {"ms_per_solve": ms, "dof_per_s": S.n_free / (ms / 1e3), "iterations": info["iterations"],
                      "inner_iterations": info["inner_iterations"], "rel_residual": info["rel_residual"],
                      "rel_l2_err_vs_fp64": err}
+        if opts.get("smoother") == pmg.PMG_ASM_DENSE and "precond_geom" not in opts:
+            # the finest dense sweep alone (block apply + per-node gather, one captured graph):
+            # it streams the FP32 inverse blocks of every subdomain, far more than L2 holds
+            r32 = torch.randn(S.n, dtype=torch.float32, device=dev)
+            x32 = torch.zeros(S.n, dtype=torch.float32, device=dev)
+            us = graph_launch_us(torch, lambda: S.level_sweep(0, r32, x32))
+            p0 = S.level_info(0)[0]
+            nb = (p0 + 3) ** 2
+            E = w.cells_x * w.cells_z
+            algo = E * nb * nb * 4.0 + E * nb * 4.0 * 2 + 3.0 * S.n * 4
+            peaks = measured_peaks()
+            out[name]["finest_sweep"] = {"us": us, "algorithmic_bytes": algo, "achieved_gbs": algo / (us * 1e-6) / 1e9,
+                                         "hbm_frac_of_measured": algo / (us * 1e-6) / 1e9 / peaks.get("hbm_gbs", 6800.0)}
         if opts.get("precond_geom") == pmg.PMG_ACTUAL:
             # the levels follow the surface: pmg_set_geometry rebuilds them (dense inverses)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -17,6 +17,8 @@
 #include "pmg_common.cuh"
 #include "pmg_kernels.h"
 
+#include <algorithm>
+
 PMG_DEFINE_CONST_TABLES(init_consts_dense)
 
 namespace pmg {
@@ -241,7 +243,8 @@ template <typename T>
 cudaError_t dense_sweep(const Shape& s, int ox, int oz, const T* inv, const T* r, T* x, const T* wx, const T* wz,
                         int post, double omega, T* U, cudaStream_t st) {
   const int NB = (s.P + 1 + 2 * ox) * (s.pz() + 1 + 2 * oz);
-  k_dense_local<T><<<s.Nx * s.Nz, 128, NB * sizeof(T), st>>>(s, ox, oz, inv, r, wx, wz, post, U);
+  const int thr = std::min(256, (NB + 31) / 32 * 32);  // one thread per block row, whole warps
+  k_dense_local<T><<<s.Nx * s.Nz, thr, NB * sizeof(T), st>>>(s, ox, oz, inv, r, wx, wz, post, U);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const size_t N = (size_t)s.NX * s.NZ;

@@ -130,6 +130,38 @@ def cpu_baseline_entry():
                       f"32x32-cell P=6 slice of the tank ({nfree} free DOF, {its} iterations, {wall:.1f} s)"}
 
 
+def cpu_baseline_paper(w):
+    """CPU baseline of the paper-shape workload: the FP64 oracle p-MG-PCG (same levels and
+    smoother) on the host cores at 1e-6 and 1e-10, setup included."""
+    from oracle import mg as omg
+    from oracle.sem import Mesh
+    m = Mesh(**w.mesh_kwargs())
+    F = w.fields(m.column_x(), m.row_sigma())
+    bo = m.rhs_divergence(F["eta"], F["u"], F["w"])
+    out = {"kind": "oracle", "sample": f"one solve of {w.name} per tolerance"}
+    for tol in (1e-6, 1e-10):
+        t0, c0 = time.perf_counter(), time.process_time()
+        _, its, _, _ = omg.solve(m, F["eta"], bo, F["pD"], tol=tol, overlap=1, nu=2, omega=0.8)
+        wall, cpu = time.perf_counter() - t0, time.process_time() - c0
+        out[f"{tol:g}"] = {"iterations": its, "s_incl_setup": wall, "cores": round(cpu / wall, 1)}
+    return out
+
+
+def cpu_baseline_bar(w):
+    """CPU baseline of the bar workload: the FP64 oracle p-MG-PCG with the same slope-free
+    levels, one solve to 1e-10, setup included."""
+    from oracle import mg as omg
+    from oracle.sem import Mesh
+    m = Mesh(**w.mesh_kwargs(), depth=w.bathymetry)
+    F = w.fields(m.column_x(), m.row_sigma())
+    bo = m.rhs_divergence(F["eta"], F["u"], F["w"])
+    t0, c0 = time.perf_counter(), time.process_time()
+    _, its, _, _ = omg.solve(m, F["eta"], bo, F["pD"], tol=1e-10, overlap=1, nu=2, omega=0.8)
+    wall, cpu = time.perf_counter() - t0, time.process_time() - c0
+    return {"kind": "oracle", "sample": f"one solve of {w.name} to 1e-10", "iterations": its,
+            "s_incl_setup": wall, "cores": round(cpu / wall, 1)}
+
+
 # ------------------------------------------------------------------------------------
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -535,6 +567,7 @@ def run_paper(args, ws, rank, local):
                                         "rel_residual": info["rel_residual"],
                                         "nodes_per_s": S.n / (ms / 1e3)}
             log(name, tol, table[f"{name}@{tol:g}"])
+            nodes = S.n
             S.close()
     # the same case on the paper's mixed-stage operator: stage k-1 = the wave one time step
     # (T/100) earlier; PDC and GMRES (the nonsymmetric operator rules out CG)
@@ -555,18 +588,7 @@ def run_paper(args, ws, rank, local):
                                               "rel_residual": info["rel_residual"]}
             log("mixed-stage", name, tol, mixed_stage[f"{name}@{tol:g}"])
             S.close()
-    # the oracle (FP64 p-MG-PCG, same levels and smoother) on the host cores, 1e-6 and 1e-10
-    from oracle import mg as omg
-    from oracle.sem import Mesh
-    m = Mesh(**w.mesh_kwargs())
-    F = w.fields(m.column_x(), m.row_sigma())
-    bo = m.rhs_divergence(F["eta"], F["u"], F["w"])
-    oracle = {}
-    for tol in (1e-6, 1e-10):
-        t0, c0 = time.perf_counter(), time.process_time()
-        _, its, _, _ = omg.solve(m, F["eta"], bo, F["pD"], tol=tol, overlap=1, nu=2, omega=0.8)
-        wall, cpu = time.perf_counter() - t0, time.process_time() - c0
-        oracle[f"{tol:g}"] = {"iterations": its, "s_incl_setup": wall, "cores": round(cpu / wall, 1)}
+    oracle = cpu_baseline_paper(w)
     # scaling sweeps at tol 1e-6
     sweep = {"cells_x": [], "order": []}
     for cx in (25, 50, 102, 200, 400, 800):
@@ -600,8 +622,8 @@ def run_paper(args, ws, rank, local):
         sweep["order_x_at_order_z_8"].append(row)
         log("order_x (P_z = 8)", row)
     clocks = clk.stop()
-    print(json.dumps({"workload": w.name, "nodes": int(m.N), "table1_shape": table,
-                      "table1_shape_mixed_stage": mixed_stage, "oracle_host": oracle,
+    print(json.dumps({"workload": w.name, "nodes": int(nodes), "table1_shape": table,
+                      "table1_shape_mixed_stage": mixed_stage, "cpu_baseline": oracle,
                       "scaling_tol1e-6": sweep, "clocks": clocks,
                       "paper_table1_context": {"pdc_mg_iterations": [3, 5, 8], "gmres_mg_iterations": [1, 3, 4],
                                                "tolerances": [1e-4, 1e-6, 1e-8],
@@ -695,16 +717,7 @@ def run_bar(args, ws, rank, local):
                 S.close()
         row["nodes"] = int(nodes)
         out[w.name] = row
-    # the oracle (FP64 p-MG-PCG with the same slope-free levels) on the paper-size bar
-    from oracle import mg as omg
-    from oracle.sem import Mesh
-    w = W.bar(100, 2, 8)
-    m = Mesh(**w.mesh_kwargs(), depth=w.bathymetry)
-    F = w.fields(m.column_x(), m.row_sigma())
-    bo = m.rhs_divergence(F["eta"], F["u"], F["w"])
-    t0 = time.perf_counter()
-    _, its, _, _ = omg.solve(m, F["eta"], bo, F["pD"], tol=1e-10, overlap=1, nu=2, omega=0.8)
-    out["oracle_bar_p8_100x2"] = {"iterations": its, "s_incl_setup": time.perf_counter() - t0}
+    out["cpu_baseline"] = cpu_baseline_bar(W.bar(100, 2, 8))
     # time stepping over the bar: a surface hump (0.01 high, released at rest at x = 6) runs
     # 500 RK4 steps of 0.02 (10 s: across the bar) with one pressure solve per stage
     from paper_2411_14977_gb300.stepper import WaveTank

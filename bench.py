@@ -404,6 +404,7 @@ def run_ours(args, ws, rank, local):
                    "precision": "FP64 flexible CG (outer residual, inner products) preconditioned by an FP32 "
                                 "V-cycle (operator, Schwarz smoother, transfers); FP64 coarse p=1 solve",
                    "cta_sizes": "autotuned at setup (64..512 threads per column slab; fused or split sweep residual)",
+                   "level_kernels": [S.level_kernels(l) for l in range(S.nlevels)],
                    "smoother": "additive Schwarz (element + 1 overlap line, fast diagonalisation), nu=2, omega=0.8",
                    "tol": 1e-10, "l2": "flushed between steps (256 MiB write, outside the timed events)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
@@ -798,8 +799,18 @@ def run_kernel_scaling(args, ws, rank, local):
         us = per_launch_us(lambda: S.apply(x64, y64))
         row["k_curved operator (double-float, FP64 vectors)"]["fp64_equiv_TFLOPs"] = \
             E * (8.0 * P1 ** 3 + 12.0 * P1 ** 2) / (us * 1e-6) / 1e12
+        row["level0_kernels"] = S.level_kernels(0)
+        # the tiled level operator forced (its best shape), beside the tuner's free choice
+        St = pmg.Solver(**w.mesh_kwargs(), precision=pmg.PMG_MIXED_FP32, flat_kernel=2)
+        St.set_geometry(torch.as_tensor(np.ascontiguousarray(F["eta"]), dtype=torch.float64, device=dev))
+        St.autotune()
+        us = per_launch_us(lambda: St.level_apply(0, x32, y32))
+        row["k_flat_tile level operator (FP32, tiled forced)"] = {
+            "us": us, "GB/s": 2 * N * 4 / (us * 1e-6) / 1e9, "frac_hbm": 2 * N * 4 / (us * 1e-6) / 1e9 / hbm,
+            "shape": St.level_kernels(0)["flat32"]}
+        St.close()
         rows.append(row)
-        log(cx, {k: (round(v["frac_hbm"], 3) if isinstance(v, dict) else v) for k, v in row.items()})
+        log(cx, {k: (round(v["frac_hbm"], 3) if isinstance(v, dict) and "frac_hbm" in v else v) for k, v in row.items()})
         S.close()
         del r32, x32, y32, b32, x64, y64
         torch.cuda.empty_cache()

@@ -103,7 +103,11 @@ typedef struct {
                      /* 1 on every level, 0 (default) never, -1 where pmg_autotune measured   */
                      /* it to be 10% faster (solve times are equal within noise at config 2) */
   int flat_kernel;   /* FP32 level operator: 0 slab CTAs (one element column each), 1 one   */
-                     /* thread per node, -1 (default) slab until pmg_autotune picks by time   */
+                     /* thread per node, 2 tiled CTAs (one thread per element; constant-depth */
+                     /* levels of equal orders up to 8, others slab) of 16 element columns x  */
+                     /* 8 element rows, or a tiled shape given as 10000 + 100 EXT + ZT (EXT   */
+                     /* columns of 8, 16 or 32, ZT rows of 4 or 8, EXT ZT a multiple of 32 and */
+                     /* at most 256), -1 (default) slab until pmg_autotune picks by time     */
   int df64_outer;    /* outer actual-geometry operator (FP64 vectors in and out) computed in */
                      /* double-float arithmetic on the FP32 pipe (48-bit significand): 1 on, */
                      /* 0 off (FP64 pipe), -1 (default) on for the mixed precisions only     */
@@ -137,6 +141,11 @@ pmg_status pmg_num_nodes(const pmg_handle* h, int64_t* n, int64_t* n_free, int* 
                          int* nlevels);
 /* Order and node counts of level l (0 = finest). */
 pmg_status pmg_level_info(const pmg_handle* h, int level, int* order, int* nx, int* nz);
+/* Launch configuration of level l's FP32 kernels as set at creation or chosen by
+ * pmg_autotune: flat32 = level operator (> 0 slab CTA size, < 0 node-parallel CTA size,
+ * >= 10000 tiled shape 10000 + 100 EXT + ZT, see pmg_opts.flat_kernel), fdm32 = Schwarz
+ * sweep CTA size, xfer = transfer CTA size.  Host-side read; any pointer may be NULL. */
+pmg_status pmg_level_kernels(const pmg_handle* h, int level, int* flat32, int* fdm32, int* xfer);
 /* x* of every node column (NX values) and sigma of every node row (NZ values), host. */
 pmg_status pmg_node_coords(const pmg_handle* h, double* x_cols_host, double* sigma_rows_host);
 

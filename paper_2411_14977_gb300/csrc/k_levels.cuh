@@ -2,6 +2,7 @@
 // (equal orders) and k_levels_aniso.cu (different orders along x and sigma).  The
 // including translation unit defines the constant tables cT first.
 #pragma once
+#include <type_traits>
 
 namespace pmg {
 
@@ -163,8 +164,147 @@ __global__ void __launch_bounds__(256) k_flat_np(FlatParams<T> p) {
   p.y[g] = p.residual ? p.b[g] - v : v;
 }
 
+// The same level operator tiled: one thread per element, a CTA over EXT element columns x
+// ZT element rows (thread t: column t % EXT, row t / EXT, so a warp's lanes sit in distinct
+// element columns).  The CTA stages its x tile -- the P node columns to the left and the
+// PZ node rows below as halo -- in shared memory, node rows contiguous per node column,
+// with an even column pitch CP and one pad word per element column: lanes one element
+// column apart are then P CP + 1 words apart, an odd stride, and read 32 distinct banks.
+// Each thread forms the outputs of the nodes its element owns (columns ex P .. ex P + P - 1,
+// the wall column too for the last element; rows ez PZ .. ez PZ + PZ - 1) in registers:
+// x stencils one node row at a time from 2P + 1 staged values, z stencils one node column
+// at a time from 2PZ + 1 staged values, so a node costs about (2P + 1)/PZ + (2PZ + 1)/P
+// shared-memory loads.  ZT is a template parameter so that CP, and with it every staged
+// offset of an element, is a compile-time constant off one base address.  The outputs go
+// back through the same buffer and leave as whole column runs (coalesced), the surface
+// row taken from x (operator) or set to 0 (residual).
+template <int ZT, int PZ>
+struct FlatTile {
+  static constexpr int nrow = (ZT + 1) * PZ + 1;  // tile row r <-> node row ez0 PZ - PZ + r
+  static constexpr int CP = (nrow + 1) & ~1;
+};
+
+template <int P, typename T, int ZT, int PZ = P>
+__global__ void __launch_bounds__(256) k_flat_tile(FlatParams<T> p, int EXT) {
+  constexpr int n = P + 1;
+  constexpr int nrow = FlatTile<ZT, PZ>::nrow, CP = FlatTile<ZT, PZ>::CP;
+  const Shape s = p.s;
+  const int NZ = s.NZ;
+  const int ex0 = blockIdx.x * EXT, ez0 = blockIdx.y * ZT;
+  const int ncol = (EXT + 1) * P + 1;  // tile column c <-> node column ex0 P - P + c
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* X = reinterpret_cast<T*>(smem_raw);  // (c, r) at c CP + r + c / P
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int gc0 = ex0 * P - P, gr0 = ez0 * PZ - PZ;
+  for (int c = warp; c < ncol; c += nwarps) {
+    const int gc = gc0 + c;
+    const bool cok = col_valid(s, gc);
+    const T* src = p.x + (size_t)(cok ? wrap_col(s, gc) : 0) * NZ;
+    T* dst = X + c * CP + c / P;
+    for (int r = lane; r < nrow; r += 32) {
+      const int gr = gr0 + r;
+      dst[r] = (cok && gr >= 0 && gr < NZ - 1) ? src[gr] : T(0);  // surface row reads 0
+    }
+  }
+  __syncthreads();
+  const int exl = (int)threadIdx.x % EXT, ezl = (int)threadIdx.x / EXT;
+  const int ex = ex0 + exl, ez = ez0 + ezl;
+  const bool active = ex < s.Nx && ez < s.Nz;
+  // (exl P + m, (ezl + 1) PZ + q) at Xe[m CP + m / P + q]
+  const T* Xe = X + exl * (P * CP + 1) + (ezl + 1) * PZ;
+  T acc[n][PZ];
+  if (active) {
+    const bool left = s.periodic || ex > 0;
+#pragma unroll
+    for (int j = 0; j < PZ; ++j) {
+      T xr[2 * P + 1];
+#pragma unroll
+      for (int m = 0; m <= 2 * P; ++m) xr[m] = Xe[m * CP + m / P + j];
+      const T f = p.cx * p.mZ[ez * PZ + j];
+#pragma unroll
+      for (int i = 0; i < n; ++i) {
+        T a = T(0);
+#pragma unroll
+        for (int m = 0; m < n; ++m) a += CT<T>::K(cT, P, i, m) * xr[P + m];
+        if (i == 0 && left) {  // the left element's share of the shared first column
+#pragma unroll
+          for (int m = 0; m < n; ++m) a += CT<T>::K(cT, P, P, m) * xr[m];
+        }
+        acc[i][j] = f * a;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+      T xc[2 * PZ + 1];
+#pragma unroll
+      for (int m = 0; m <= 2 * PZ; ++m) xc[m] = Xe[(P + i) * CP + (P + i) / P + m - PZ];
+      const T f = p.cz * p.mX[wrap_col(s, ex * P + i)];
+#pragma unroll
+      for (int j = 0; j < PZ; ++j) {
+        T a = T(0);
+#pragma unroll
+        for (int m = 0; m <= PZ; ++m) a += CT<T>::K(cT, PZ, j, m) * xc[PZ + m];
+        if (j == 0 && ez > 0) {  // the lower element's share of the shared first row
+#pragma unroll
+          for (int m = 0; m <= PZ; ++m) a += CT<T>::K(cT, PZ, PZ, m) * xc[m];
+        }
+        acc[i][j] += f * a;
+      }
+    }
+  }
+  __syncthreads();
+  if (active) {
+    const bool wall = !s.periodic && ex == s.Nx - 1;
+    // output (exl P + i, ezl PZ + j) at the staging position (c, r) = (exl P + i, ezl PZ + j)
+    T* Ye = X + exl * (P * CP + 1) + ezl * PZ;
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+      if (i == P && !wall) break;
+#pragma unroll
+      for (int j = 0; j < PZ; ++j) Ye[i * CP + i / P + j] = acc[i][j];
+    }
+  }
+  __syncthreads();
+  const int exn = min(ex0 + EXT, s.Nx) - ex0, ezn = min(ez0 + ZT, s.Nz) - ez0;
+  const int ncy = exn * P + ((!s.periodic && ex0 + exn == s.Nx) ? 1 : 0);
+  const int nry = ezn * PZ + ((ez0 + ezn == s.Nz) ? 1 : 0);
+  for (int c = warp; c < ncy; c += nwarps) {
+    const size_t gb = (size_t)(ex0 * P + c) * NZ + (size_t)ez0 * PZ;
+    const T* Yc = X + c * CP + c / P;
+    for (int r = lane; r < nry; r += 32) {
+      const size_t g = gb + r;
+      if (ez0 * PZ + r == NZ - 1) p.y[g] = p.residual ? T(0) : p.x[g];
+      else p.y[g] = p.residual ? p.b[g] - Yc[r] : Yc[r];
+    }
+  }
+}
+
+template <int P, typename T, int ZT, int PZ = P>
+static cudaError_t launch_flat_tile_z(const FlatParams<T>& prm, int EXT, cudaStream_t st) {
+  const int ncol = (EXT + 1) * P + 1;
+  size_t sm = ((size_t)ncol * FlatTile<ZT, PZ>::CP + (ncol - 1) / P + 1) * sizeof(T);
+  auto k = k_flat_tile<P, T, ZT, PZ>;
+  static std::atomic<unsigned long long> s_mask{0};
+  cudaError_t e = ensure_max_smem(k, s_mask);
+  if (e != cudaSuccess) return e;
+  dim3 grid((unsigned)((prm.s.Nx + EXT - 1) / EXT), (unsigned)((prm.s.Nz + ZT - 1) / ZT));
+  k<<<grid, EXT * ZT, sm, st>>>(prm, EXT);
+  return cudaGetLastError();
+}
+
+template <int P, typename T, int PZ = P>
+static cudaError_t launch_flat_tile(const FlatParams<T>& prm, int code, cudaStream_t st) {
+  const int EXT = (code / 100) % 100, ZT = code % 100;
+  return ZT == 4 ? launch_flat_tile_z<P, T, 4, PZ>(prm, EXT, st) : launch_flat_tile_z<P, T, 8, PZ>(prm, EXT, st);
+}
+
 template <int P, typename T, bool VAR, int PZ = P>
 static cudaError_t launch_flat_p(const FlatParams<T>& prm, int threads, cudaStream_t st) {
+  if (threads >= 10000) {
+    if constexpr (!VAR && std::is_same<T, float>::value && P <= 8 && PZ == P)
+      if (flat_tile_code_ok(threads)) return launch_flat_tile<P, T, PZ>(prm, threads, st);
+    threads = 256;  // constant-depth FP32 levels of equal orders up to 8 only; else slab CTAs
+  }
   if (threads < 0) {  // node-parallel variant, -threads per CTA
     size_t N = (size_t)prm.s.NX * prm.s.NZ;
     int bs = -threads;

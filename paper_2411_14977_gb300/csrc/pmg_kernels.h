@@ -108,12 +108,23 @@ struct FlatArgs {
   const void* mX;
   const void* mZ;
   int residual;
-  int threads = 256;   // > 0: slab CTA size; < 0: node-parallel kernel with -threads per CTA
+  int threads = 256;   // > 0: slab CTA size; < 0: node-parallel kernel with -threads per CTA;
+                       // a tiled-shape code (flat_tile_code_ok): the tiled kernel
   // varying depth: per element column x-stiffness [Nx][P+1][P+1] with cx folded in (then
   // cx = cz = 1 and mX holds the depth-weighted x weights)
   const void* Kx = nullptr;
 };
 template <typename T> cudaError_t flat_op(const FlatArgs& a, cudaStream_t st);
+
+// Tiled-variant CTA shapes, coded in the launch parameter as 10000 + 100 EXT + ZT
+// (EXT element columns of 8, 16 or 32; ZT element rows of 4 or 8; at most 256 threads).
+inline bool flat_tile_code_ok(int code) {
+  if (code < 10000) return false;
+  int ext = (code / 100) % 100, zt = code % 100;
+  return (ext == 8 || ext == 16 || ext == 32) && (zt == 4 || zt == 8) && code / 10000 == 1 &&
+         (ext * zt) % 32 == 0 && ext * zt <= 256;
+}
+
 
 struct FdmArgs {
   Shape s;

@@ -440,6 +440,8 @@ pmg_status build_level(pmg_handle* h, int l) {
   L.aniso = pz != p;
   L.fuse_res = h->opts.fuse_residual == 1 && !L.aniso;
   if (h->opts.flat_kernel == 1) L.thr_flat32 = -128;
+  if (h->opts.flat_kernel == 2) L.thr_flat32 = 11608;  // tiled: 16 element columns x 8 rows
+  if (flat_tile_code_ok(h->opts.flat_kernel)) L.thr_flat32 = h->opts.flat_kernel;
   L.fuse_restrict = h->opts.fuse_residual == 1 && !L.aniso;
   L.s.P = p;
   L.s.PZ = pz;
@@ -1602,7 +1604,7 @@ pmg_status time_launches(pmg_handle* h, Run&& run, int threads, int reps, float*
 
 template <class Run>
 pmg_status tune_one(pmg_handle* h, int kernel, int P, int NZ, Run&& run, int* out,
-                    std::initializer_list<int> cands = {64, 128, 192, 256, 320, 384, 512}) {
+                    const std::vector<int>& cands = {64, 128, 192, 256, 320, 384, 512}) {
   auto key = std::make_tuple(kernel, P, NZ, h->mesh.cells_x);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -1700,7 +1702,7 @@ pmg_status pmg_create(const pmg_mesh_desc* mesh, const pmg_opts* opts, pmg_handl
     return fail(PMG_ERR_INVALID, "levels on the actual geometry need equal orders along x and sigma");
   if (o.overlap < 0 || o.overlap > MAXO || o.nu < 1 || !(o.omega > 0) || !(o.tol > 0) || o.max_iter < 1 ||
       o.inner_max < 1 || !(o.inner_tol > 0) || o.fuse_residual < -1 || o.fuse_residual > 1 || o.df64_outer < -1 ||
-      o.df64_outer > 1 || o.flat_kernel < -1 || o.flat_kernel > 1)
+      o.df64_outer > 1 || o.flat_kernel < -1 || (o.flat_kernel > 2 && !flat_tile_code_ok(o.flat_kernel)))
     return fail(PMG_ERR_INVALID, "bad solver options");
   const int order_z = m.order_z == 0 ? m.order : m.order_z;
   if (order_z < 1 || order_z > MAXP) return fail(PMG_ERR_INVALID, "order_z must be 0 or in 1..10");
@@ -1883,6 +1885,15 @@ pmg_status pmg_level_info(const pmg_handle* h, int level, int* order, int* nx, i
   if (order) *order = h->lv[level].order;
   if (nx) *nx = h->lv[level].s.NX;
   if (nz) *nz = h->lv[level].s.NZ;
+  return PMG_OK;
+}
+
+pmg_status pmg_level_kernels(const pmg_handle* h, int level, int* flat32, int* fdm32, int* xfer) {
+  CKS(check_handle(h));
+  if (level < 0 || level >= (int)h->lv.size()) return fail(PMG_ERR_INVALID, "bad level");
+  if (flat32) *flat32 = h->lv[level].thr_flat32;
+  if (fdm32) *fdm32 = h->lv[level].thr_fdm32;
+  if (xfer) *xfer = h->lv[level].thr_xfer;
   return PMG_OK;
 }
 
@@ -2345,15 +2356,27 @@ pmg_status pmg_autotune(pmg_handle* h) {
     void* x = L.x[1];
     void* b = L.b[1];
     void* t = L.t[1];
-    // slab CTAs (positive sizes) or node-parallel CTAs (negative sizes)
-    if (!L.actual)
-    CKS(tune_one(h, L.var ? TK_FLAT32V : TK_FLAT32, L.order + 100 * (L.aniso ? L.order_z : 0), L.s.NZ,
-                 [&](int thr, cudaStream_t cs) {
-      L.thr_flat32 = thr;
-      return level_residual<float>(h, l, b, x, t, 1, cs);
-    }, &L.thr_flat32, h->opts.flat_kernel == 1 ? std::initializer_list<int>{-64, -128, -256}
-                       : h->opts.flat_kernel == 0 ? std::initializer_list<int>{64, 128, 192, 256, 320, 384, 512}
-                       : std::initializer_list<int>{64, 128, 192, 256, 320, 384, 512, -64, -128, -256}));
+    // slab CTAs (positive sizes), node-parallel CTAs (negative) or tiled CTAs (codes
+    // 10000 + 100 element columns + element rows; constant depth, equal orders up to 8)
+    if (!L.actual) {
+      const std::vector<int> slab{64, 128, 192, 256, 320, 384, 512}, np{-64, -128, -256},
+          tile{10804, 10808, 11604, 11608, 13204, 13208};
+      const bool tile_ok = !L.var && !L.aniso && L.order <= 8;
+      const int fk = h->opts.flat_kernel;
+      std::vector<int> cands = fk == 1 ? np : fk == 0 ? slab : (fk == 2 && tile_ok) ? tile : slab;
+      if (fk >= 10000) cands = tile_ok ? std::vector<int>{fk} : slab;
+      if (fk == -1) {
+        cands.insert(cands.end(), np.begin(), np.end());
+        if (tile_ok) cands.insert(cands.end(), tile.begin(), tile.end());
+      }
+      // a forced kernel family tunes (and caches) apart from the free choice
+      const int key = L.order + 100 * (L.aniso ? L.order_z : 0) + (fk >= 10000 ? 100 * fk : fk >= 0 ? 10000 * (fk + 1) : 0);
+      CKS(tune_one(h, L.var ? TK_FLAT32V : TK_FLAT32, key, L.s.NZ,
+                   [&](int thr, cudaStream_t cs) {
+        L.thr_flat32 = thr;
+        return level_residual<float>(h, l, b, x, t, 1, cs);
+      }, &L.thr_flat32, cands));
+    }
     if (l == nl - 1) continue;
     if (L.var || L.aniso || L.dense) {
       // varying depth, different orders or dense blocks: no k_fdm32 sweep, split residuals;

@@ -63,6 +63,7 @@ _SIGNATURES = {
     "pmg_num_nodes": (_I, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                            ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "pmg_level_info": (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "pmg_level_kernels": (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "pmg_node_coords": (_I, [_P, _P, _P]),
     "pmg_set_geometry": (_I, [_P, _P, _P]),
     "pmg_set_geometry_mixed": (_I, [_P, _P, _P, _P]),
@@ -213,6 +214,14 @@ class Solver:
         p, nx, nz = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         _check(load().pmg_level_info(self._h, level, ctypes.byref(p), ctypes.byref(nx), ctypes.byref(nz)))
         return p.value, nx.value, nz.value
+
+    def level_kernels(self, level):
+        """Launch configuration of level `level`'s FP32 kernels (after autotune, the tuned
+        one): {"flat32": slab CTA size > 0, node-parallel CTA size < 0 or tiled shape
+        code >= 10000, "fdm32": sweep CTA size, "xfer": transfer CTA size}."""
+        f, d, x = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(load().pmg_level_kernels(self._h, level, ctypes.byref(f), ctypes.byref(d), ctypes.byref(x)))
+        return {"flat32": f.value, "fdm32": d.value, "xfer": x.value}
 
     def node_coords(self):
         xc = torch.empty(self.NX, dtype=torch.float64)

@@ -54,7 +54,7 @@ def test_default_opts():
     (dict(), dict(precision=2, outer=1), "outer = PMG_IR"),
     (dict(), dict(fuse_residual=2), "options"),
     (dict(), dict(df64_outer=3), "options"),
-    (dict(), dict(flat_kernel=2), "options"),
+    (dict(), dict(flat_kernel=3), "options"),
     (dict(), dict(outer=5), "outer"),
     (dict(), dict(outer=4, gmres_restart=0), "gmres_restart"),
     (dict(), dict(outer=4, gmres_restart=61), "gmres_restart"),

@@ -55,6 +55,11 @@ def test_default_opts():
     (dict(), dict(fuse_residual=2), "options"),
     (dict(), dict(df64_outer=3), "options"),
     (dict(), dict(flat_kernel=3), "options"),
+    (dict(), dict(flat_kernel=13216), "options"),   # 32 x 16 = 512 threads
+    (dict(), dict(flat_kernel=10404), "options"),   # 4 element columns
+    (dict(), dict(flat_kernel=11603), "options"),   # 3 element rows
+    (dict(), dict(flat_kernel=20808), "options"),
+    (dict(), dict(flat_kernel=-2), "options"),
     (dict(), dict(outer=5), "outer"),
     (dict(), dict(outer=4, gmres_restart=0), "gmres_restart"),
     (dict(), dict(outer=4, gmres_restart=61), "gmres_restart"),
@@ -87,3 +92,19 @@ def test_null_arguments():
     assert lib.pmg_create(None, None, ctypes.byref(h)) == pmg.PMG_ERR_INVALID
     assert lib.pmg_destroy(None) == pmg.PMG_OK
     assert lib.pmg_solve(None, None, None, None, None, None, None) == pmg.PMG_ERR_INVALID
+
+
+@pytest.mark.parametrize("code", [2, 10804, 10808, 11604, 11608, 13204, 13208])
+def test_tiled_level_operator_shapes_pass_validation(code):
+    """Every documented tiled shape (pmg_opts.flat_kernel = 2 or 10000 + 100 EXT + ZT) passes
+    the option check; creation then stops only where it needs a device."""
+    lib = pmg.load()
+    m = pmg.MeshDesc(0.0, 1.0, 1.0, 4, 2, 4, 0)
+    o = pmg.default_opts()
+    o.flat_kernel = code
+    h = ctypes.c_void_p()
+    st = lib.pmg_create(ctypes.byref(m), ctypes.byref(o), ctypes.byref(h))
+    if st != pmg.PMG_OK:
+        assert "options" not in lib.pmg_last_error().decode()
+    else:
+        lib.pmg_destroy(h)

@@ -2424,12 +2424,16 @@ pmg_status pmg_autotune(pmg_handle* h) {
       if (h->opts.fuse_residual < 0) L.fuse_restrict = us_fused < 0.9f * us_split;
     }
   }
+  // the FP32 build differs with the tensor-core mode and the FP64-vector build with
+  // double-float arithmetic: each variant tunes under its own key
   const int curved_key = h->mesh.order + 100 * (h->aniso ? h->mesh.order_z : 0);
-  CKS(tune_one(h, h->bathy ? TK_CURVED32B : TK_CURVED32, curved_key, h->lv[0].s.NZ, [&](int thr, cudaStream_t cs) {
+  CKS(tune_one(h, h->bathy ? TK_CURVED32B : TK_CURVED32, curved_key + 10000 * h->tc, h->lv[0].s.NZ,
+               [&](int thr, cudaStream_t cs) {
     h->thr_curved32 = thr;
     return curved<float>(h, 0, h->r32, nullptr, h->w32, 1, nullptr, cs);
   }, &h->thr_curved32));
-  CKS(tune_one(h, h->bathy ? TK_CURVED64B : TK_CURVED64, curved_key, h->lv[0].s.NZ, [&](int thr, cudaStream_t cs) {
+  CKS(tune_one(h, h->bathy ? TK_CURVED64B : TK_CURVED64, curved_key + 10000 * (h->df64_outer ? 1 : 0), h->lv[0].s.NZ,
+               [&](int thr, cudaStream_t cs) {
     h->thr_curved64 = thr;
     return curved<double>(h, 0, h->p, nullptr, h->w, 1, nullptr, cs);
   }, &h->thr_curved64));

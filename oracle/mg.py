@@ -29,10 +29,10 @@ Paper passages followed (Sec. 5):
 
 The coarsest level (order 1) is solved exactly by a sparse LU (library primitive).
 
-Parity status: the V-cycle's quality (iteration counts) is "parity unpinned" by the
-paper, which prints no iteration count for this operator; tests pin its symmetry and
-positivity, exact-solve limits, and the flat iteration counts in N_x and P claimed in
-Sec. 6.3.
+Parity status: the V-cycle's quality is pinned to the PDC-MG iteration counts the paper
+prints in Table 1 (Sec. 6, within one: the right-hand side is synthetic), and tests pin
+its symmetry and positivity, exact-solve limits, the flat iteration counts in N_x and P
+claimed in Sec. 6.3, and flexible GMRES's minimal residual against defect correction.
 """
 import numpy as np
 import scipy.linalg as sla

@@ -2,7 +2,6 @@
 semi-coarsening; Sec. 6.3 scaling study at N_z = 2, P_z = 8): closed-form level pairs, the
 flat element as a Kronecker sum of 1D matrices of two orders, exact fluxes of linear
 functions, spectral convergence in each order, exact transfers, and the hierarchy."""
-import math
 
 import numpy as np
 import pytest

@@ -4,7 +4,7 @@ Krylov answers equal to the direct solve, and flat iteration counts in N_x and P
 import numpy as np
 import pytest
 
-from oracle import basis, mg
+from oracle import mg
 from oracle.sem import Mesh, solve_direct
 import workloads as W
 

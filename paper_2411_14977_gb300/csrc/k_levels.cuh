@@ -169,12 +169,13 @@ __global__ void __launch_bounds__(256) k_flat_np(FlatParams<T> p) {
 // element columns).  The CTA stages its x tile -- the P node columns to the left and the
 // PZ node rows below as halo -- in shared memory, node rows contiguous per node column,
 // with an even column pitch CP and one pad word per element column: lanes one element
-// column apart are then P CP + 1 words apart, an odd stride, and read 32 distinct banks.
-// Each thread forms the outputs of the nodes its element owns (columns ex P .. ex P + P - 1,
-// the wall column too for the last element; rows ez PZ .. ez PZ + PZ - 1) in registers:
-// x stencils one node row at a time from 2P + 1 staged values, z stencils one node column
-// at a time from 2PZ + 1 staged values, so a node costs about (2P + 1)/PZ + (2PZ + 1)/P
-// shared-memory loads.  ZT is a template parameter so that CP, and with it every staged
+// column apart are then P CP + 1 words apart, an odd stride, so with EXT = 32 a warp reads
+// 32 distinct banks (EXT = 8 or 16 puts 4 or 2 element rows in a warp, which may share
+// banks).  Each thread forms the outputs of the nodes its element owns (columns ex P ..
+// ex P + P - 1, the wall column too for the last element; rows ez PZ .. ez PZ + PZ - 1) in
+// registers: x stencils one node row at a time from 2P + 1 staged values (serving P owned
+// nodes), z stencils one node column at a time from 2PZ + 1 staged values (serving PZ), so
+// a node costs about (2P + 1)/P + (2PZ + 1)/PZ shared-memory loads.  ZT is a template parameter so that CP, and with it every staged
 // offset of an element, is a compile-time constant off one base address.  The outputs go
 // back through the same buffer and leave as whole column runs (coalesced), the surface
 // row taken from x (operator) or set to 0 (residual).

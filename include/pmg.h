@@ -144,7 +144,8 @@ pmg_status pmg_level_info(const pmg_handle* h, int level, int* order, int* nx, i
 /* Launch configuration of level l's FP32 kernels as set at creation or chosen by
  * pmg_autotune: flat32 = level operator (> 0 slab CTA size, < 0 node-parallel CTA size,
  * >= 10000 tiled shape 10000 + 100 EXT + ZT, see pmg_opts.flat_kernel), fdm32 = Schwarz
- * sweep CTA size, xfer = transfer CTA size.  Host-side read; any pointer may be NULL. */
+ * sweep CTA size, xfer = transfer CTA size.  Host-side read; any pointer may be NULL.
+ * The paper has no counterpart.  PMG_ERR_INVALID for a bad handle or level. */
 pmg_status pmg_level_kernels(const pmg_handle* h, int level, int* flat32, int* fdm32, int* xfer);
 /* x* of every node column (NX values) and sigma of every node row (NZ values), host. */
 pmg_status pmg_node_coords(const pmg_handle* h, double* x_cols_host, double* sigma_rows_host);
@@ -352,12 +353,18 @@ pmg_status pmg_batch_solve(pmg_batch* b, const double* const* b_dev, const doubl
                            double* const* p_out_dev, pmg_solve_info* infos, void* stream);
 
 /* ---- autotuner ------------------------------------------------------------------------- */
-/* Times the candidate CTA sizes (64, 128, 256 threads) of the level operator, the
- * Schwarz sweep and the actual-geometry operator on every level of h (CUDA-event timing
- * of graph-captured launches) and keeps the fastest per kernel and shape for h.  The
- * choices are also remembered per (kernel, order, rows) for handles created later in the
- * process.  Synchronous; changes no results (the kernels are correct for any of the
- * candidate sizes). */
+/* Times the candidate launch configurations on every level of h (CUDA-event timing of
+ * graph-captured launches) and keeps the fastest per kernel and shape for h; a later
+ * candidate must be 3% faster to replace an earlier one.  Candidates: for the FP32 level
+ * operator, slab CTAs of 64..512 threads, node-parallel CTAs of 64..256 and the tiled
+ * shapes (constant-depth levels of equal orders up to 8), or only the family that
+ * pmg_opts.flat_kernel forces; for the Schwarz sweep, the transfers and the
+ * actual-geometry operators, CTA sizes of 64..512.  Where pmg_opts.fuse_residual = -1 it
+ * also picks fused or split level residuals.  The paper has no counterpart (it fixes no
+ * launch shapes).  The choices are also remembered per (kernel, order, rows, element
+ * columns, forced family or arithmetic variant) for handles created later in the process,
+ * and in the file named by PMG_TUNE_CACHE when set.  Synchronous; changes no results
+ * (every candidate computes the same operator).  pmg_level_kernels reads the choices. */
 pmg_status pmg_autotune(pmg_handle* h);
 
 /* ---- allocation-free apply ------------------------------------------------------------ */

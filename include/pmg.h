@@ -129,6 +129,24 @@ typedef struct pmg_handle pmg_handle;
  * omega 0.8, tol 1e-10, max_iter 500, inner_max 40, inner_tol 1e-5, paper level rule. */
 void pmg_default_opts(pmg_opts* opts);
 
+/* ---- host-only queries (no device work; they run without a GPU) ---------------------- */
+/* The level orders pmg_create builds for (mesh, opts): the coarsening rule P_{n-1} =
+ * ceil((P_n+1)/2) down to 2, then 1 (Sec. 5.1), the semi-coarsening pairs when
+ * mesh->order_z differs from mesh->order (the higher order steps by the rule, not below
+ * the other, until they match), or opts->level_orders.  *nlevels receives the count;
+ * orders and orders_z (each NULL or room for 16 ints, caller-owned) receive the orders
+ * along x and sigma, finest first.  opts NULL = defaults.  Validates mesh and opts exactly
+ * as pmg_create does: PMG_ERR_INVALID with pmg_last_error() set on bad input. */
+pmg_status pmg_level_sequence(const pmg_mesh_desc* mesh, const pmg_opts* opts, int* nlevels, int* orders,
+                              int* orders_z);
+/* The reference-element tables the setup uses for order p, 1 <= p <= 10 (Sec. 4.3): LGL
+ * nodes (p+1, ascending) and weights (p+1); the nodal derivative matrix D, row-major
+ * (p+1) x (p+1) with D[i][m] = dh_m/dr at node i; and for 1 <= pc <= p the interpolation
+ * J that takes order-pc nodal values to the order-p nodes (the prolongation's 1D factor,
+ * Sec. 5.2), row-major (p+1) x (pc+1); pc = 0 skips J.  Any output pointer may be NULL
+ * (host memory, caller-owned).  PMG_ERR_INVALID for p or pc out of range. */
+pmg_status pmg_basis_tables(int p, int pc, double* nodes, double* weights, double* D, double* J);
+
 /* Build the mesh, the level hierarchy P_{n-1} = ceil((P_n+1)/2) down to 2, then 1
  * (Sec. 5.1), the transfer matrices I = Phi V^-1 (Sec. 5.2), the Schwarz factors
  * (Sec. 5.3) and the coarse factor, on the current CUDA device; geometry starts flat

@@ -1644,41 +1644,10 @@ struct pmg_batch {
   }
 };
 
-// =====================================================================================
-// C ABI
-// =====================================================================================
-extern "C" {
-
-void pmg_default_opts(pmg_opts* o) {
-  if (!o) return;
-  std::memset(o, 0, sizeof(*o));
-  o->precision = PMG_FP64;
-  o->outer = PMG_PCG;
-  o->smoother = PMG_ASM_FDM;
-  o->precond_geom = PMG_FLAT_LINEARISED;
-  o->overlap = 1;
-  o->nu = 2;
-  o->omega = 0.8;
-  o->tol = 1e-10;
-  o->max_iter = 500;
-  o->inner_max = 40;
-  o->inner_tol = 1e-5;
-  o->nlevels = 0;
-  o->fuse_residual = 0;
-  o->flat_kernel = -1;
-  o->df64_outer = -1;
-  o->gmres_restart = 30;
-}
-
-const char* pmg_last_error(void) { return g_err.c_str(); }
-
-pmg_status pmg_create(const pmg_mesh_desc* mesh, const pmg_opts* opts, pmg_handle** out) {
-  if (!out) return fail(PMG_ERR_INVALID, "out is NULL");
-  *out = nullptr;
-  if (!mesh) return fail(PMG_ERR_INVALID, "mesh is NULL");
-  pmg_opts o;
-  if (opts) o = *opts; else pmg_default_opts(&o);
-  const pmg_mesh_desc& m = *mesh;
+// Validates a mesh and options as pmg_create does and plans the level orders (Sec. 5.1:
+// the coarsening rule, semi-coarsening for two orders, or the caller's list).
+static pmg_status plan_levels(const pmg_mesh_desc& m, const pmg_opts& o, std::vector<int>& orders,
+                       std::vector<int>& orders_z) {
   if (m.order < 1 || m.order > MAXP) return fail(PMG_ERR_INVALID, "order must be in 1..10");
   if (m.cells_x < 1 || m.cells_z < 1) return fail(PMG_ERR_INVALID, "cells must be >= 1");
   if (m.cells_x > 65535 || m.cells_z > 64) return fail(PMG_ERR_INVALID, "too many cells (cells_z <= 64)");
@@ -1706,7 +1675,8 @@ pmg_status pmg_create(const pmg_mesh_desc* mesh, const pmg_opts* opts, pmg_handl
     return fail(PMG_ERR_INVALID, "bad solver options");
   const int order_z = m.order_z == 0 ? m.order : m.order_z;
   if (order_z < 1 || order_z > MAXP) return fail(PMG_ERR_INVALID, "order_z must be 0 or in 1..10");
-  std::vector<int> orders, orders_z;
+  orders.clear();
+  orders_z.clear();
   if (order_z != m.order) {
     // semi-coarsening (Sec. 5.1): the higher order is reduced until both match
     if (o.nlevels > 0) return fail(PMG_ERR_INVALID, "custom level orders need equal orders along x and sigma");
@@ -1737,6 +1707,80 @@ pmg_status pmg_create(const pmg_mesh_desc* mesh, const pmg_opts* opts, pmg_handl
         return fail(PMG_ERR_INVALID, "dense Schwarz blocks too large for one CTA (order 10 with overlap 1)");
     }
   if (orders.size() < 2) return fail(PMG_ERR_INVALID, "order must be >= 2 (the coarsest level is order 1)");
+  return PMG_OK;
+}
+
+// =====================================================================================
+// C ABI
+// =====================================================================================
+extern "C" {
+
+void pmg_default_opts(pmg_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = PMG_FP64;
+  o->outer = PMG_PCG;
+  o->smoother = PMG_ASM_FDM;
+  o->precond_geom = PMG_FLAT_LINEARISED;
+  o->overlap = 1;
+  o->nu = 2;
+  o->omega = 0.8;
+  o->tol = 1e-10;
+  o->max_iter = 500;
+  o->inner_max = 40;
+  o->inner_tol = 1e-5;
+  o->nlevels = 0;
+  o->fuse_residual = 0;
+  o->flat_kernel = -1;
+  o->df64_outer = -1;
+  o->gmres_restart = 30;
+}
+
+const char* pmg_last_error(void) { return g_err.c_str(); }
+
+pmg_status pmg_level_sequence(const pmg_mesh_desc* mesh, const pmg_opts* opts, int* nlevels, int* orders,
+                              int* orders_z) {
+  if (!mesh || !nlevels) return fail(PMG_ERR_INVALID, "mesh or nlevels is NULL");
+  pmg_opts o;
+  if (opts) o = *opts; else pmg_default_opts(&o);
+  std::vector<int> ox, oz;
+  CKS(plan_levels(*mesh, o, ox, oz));
+  *nlevels = (int)ox.size();
+  for (size_t l = 0; l < ox.size(); ++l) {
+    if (orders) orders[l] = ox[l];
+    if (orders_z) orders_z[l] = oz[l];
+  }
+  return PMG_OK;
+}
+
+pmg_status pmg_basis_tables(int p, int pc, double* nodes, double* weights, double* D, double* J) {
+  if (p < 1 || p > MAXP) return fail(PMG_ERR_INVALID, "order must be in 1..10");
+  if (pc < 0 || pc > p) return fail(PMG_ERR_INVALID, "pc must be in 0..p");
+  std::vector<double> x, w;
+  lgl(p, x, w);
+  if (nodes) std::copy(x.begin(), x.end(), nodes);
+  if (weights) std::copy(w.begin(), w.end(), weights);
+  if (D) {
+    const std::vector<double> d = diff_matrix(p);
+    std::copy(d.begin(), d.end(), D);
+  }
+  if (J && pc >= 1) {
+    const std::vector<double> j = transfer_matrix(pc, p);
+    std::copy(j.begin(), j.end(), J);
+  }
+  return PMG_OK;
+}
+
+pmg_status pmg_create(const pmg_mesh_desc* mesh, const pmg_opts* opts, pmg_handle** out) {
+  if (!out) return fail(PMG_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!mesh) return fail(PMG_ERR_INVALID, "mesh is NULL");
+  pmg_opts o;
+  if (opts) o = *opts; else pmg_default_opts(&o);
+  const pmg_mesh_desc& m = *mesh;
+  std::vector<int> orders, orders_z;
+  CKS(plan_levels(m, o, orders, orders_z));
+  const int order_z = orders_z[0];
 
   auto* h = new (std::nothrow) pmg_handle();
   if (!h) return fail(PMG_ERR_OOM, "host allocation failed");

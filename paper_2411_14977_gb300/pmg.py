@@ -64,6 +64,9 @@ _SIGNATURES = {
                            ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "pmg_level_info": (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "pmg_level_kernels": (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "pmg_level_sequence": (_I, [ctypes.POINTER(MeshDesc), ctypes.POINTER(Opts), ctypes.POINTER(_I),
+                               ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "pmg_basis_tables": (_I, [_I, _I, _P, _P, _P, _P]),
     "pmg_node_coords": (_I, [_P, _P, _P]),
     "pmg_set_geometry": (_I, [_P, _P, _P]),
     "pmg_set_geometry_mixed": (_I, [_P, _P, _P, _P]),
@@ -180,6 +183,31 @@ def apply_noalloc(mesh, eta, x, out):
                         mesh["cells_z"], mesh["order"], int(bool(mesh.get("periodic", False))))
     _check(load().pmg_apply_noalloc(ctypes.byref(mesh), _ptr(eta), _ptr(x), _ptr(out), _stream()))
     return out
+
+
+def level_sequence(cells_x, cells_z, order, x0=0.0, x1=1.0, h=1.0, periodic=False, order_z=None, **opts):
+    """pmg_level_sequence: the (order along x, order along sigma) of every level pmg_create
+    would build for this mesh and these options, finest first (host-only, no GPU)."""
+    mesh = MeshDesc(x0, x1, h, cells_x, cells_z, order, int(bool(periodic)), int(order_z or 0))
+    o = default_opts(**opts)
+    nl = ctypes.c_int()
+    ox, oz = (ctypes.c_int * 16)(), (ctypes.c_int * 16)()
+    _check(load().pmg_level_sequence(ctypes.byref(mesh), ctypes.byref(o), ctypes.byref(nl), ox, oz))
+    return [(ox[i], oz[i]) for i in range(nl.value)]
+
+
+def basis_tables(p, pc=0):
+    """pmg_basis_tables: LGL nodes and weights of order p, the derivative matrix D
+    ((p+1) x (p+1)) and, for pc >= 1, the order-pc -> order-p interpolation J ((p+1) x (pc+1)),
+    as float64 CPU tensors (host-only, no GPU)."""
+    n = p + 1
+    x, w = torch.empty(n, dtype=torch.float64), torch.empty(n, dtype=torch.float64)
+    D = torch.empty(n, n, dtype=torch.float64)
+    J = torch.empty(n, max(pc, 0) + 1, dtype=torch.float64)
+    _check(load().pmg_basis_tables(p, pc, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(w.data_ptr()),
+                                   ctypes.c_void_p(D.data_ptr()),
+                                   ctypes.c_void_p(J.data_ptr()) if pc >= 1 else None))
+    return {"nodes": x, "weights": w, "D": D, "J": J if pc >= 1 else None}
 
 
 class Solver:

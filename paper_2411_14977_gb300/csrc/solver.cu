@@ -1647,7 +1647,7 @@ struct pmg_batch {
 // Validates a mesh and options as pmg_create does and plans the level orders (Sec. 5.1:
 // the coarsening rule, semi-coarsening for two orders, or the caller's list).
 static pmg_status plan_levels(const pmg_mesh_desc& m, const pmg_opts& o, std::vector<int>& orders,
-                       std::vector<int>& orders_z) {
+                              std::vector<int>& orders_z) {
   if (m.order < 1 || m.order > MAXP) return fail(PMG_ERR_INVALID, "order must be in 1..10");
   if (m.cells_x < 1 || m.cells_z < 1) return fail(PMG_ERR_INVALID, "cells must be >= 1");
   if (m.cells_x > 65535 || m.cells_z > 64) return fail(PMG_ERR_INVALID, "too many cells (cells_z <= 64)");

@@ -146,6 +146,18 @@ pmg_status pmg_level_sequence(const pmg_mesh_desc* mesh, const pmg_opts* opts, i
  * Sec. 5.2), row-major (p+1) x (pc+1); pc = 0 skips J.  Any output pointer may be NULL
  * (host memory, caller-owned).  PMG_ERR_INVALID for p or pc out of range. */
 pmg_status pmg_basis_tables(int p, int pc, double* nodes, double* weights, double* D, double* J);
+/* The fast-diagonalisation factors of one additive-Schwarz element class (Sec. 5.3) as the
+ * setup builds them for a level of order p (1..10) and overlap o (0 or 1).  The 1D
+ * subdomain is an element's p+1 node lines plus o lines of each neighbour, cut at walls,
+ * on a canonical line of unit-reference cells; along sigma (dir = 1) the surface line is
+ * Dirichlet and left out.  cls: 0 interior element, 1 first (wall / bottom), 2 last
+ * (wall / surface), 3 both (a single element).  With K the assembled 1D LGL stiffness
+ * (sum over cells of D^T diag(w) D) and M the assembled weights, restricted to the k
+ * nodes present: V (row-major NB x NB, NB = p+1+2o; row = local node, column = mode; rows
+ * of absent nodes and columns past k zero) has V^T M V = I and V^T K V = diag(lam); lam
+ * has NB entries, zero past k.  Host-only; caller-owned host buffers.  PMG_ERR_INVALID
+ * for arguments out of range or NULL outputs. */
+pmg_status pmg_schwarz_class(int p, int o, int dir, int cls, double* V, double* lam, int* k);
 
 /* Build the mesh, the level hierarchy P_{n-1} = ceil((P_n+1)/2) down to 2, then 1
  * (Sec. 5.1), the transfer matrices I = Phi V^-1 (Sec. 5.2), the Schwarz factors

@@ -1771,6 +1771,14 @@ pmg_status pmg_basis_tables(int p, int pc, double* nodes, double* weights, doubl
   return PMG_OK;
 }
 
+pmg_status pmg_schwarz_class(int p, int o, int dir, int cls, double* V, double* lam, int* k) {
+  if (p < 1 || p > MAXP || o < 0 || o > MAXO || dir < 0 || dir > 1 || cls < 0 || cls > 3)
+    return fail(PMG_ERR_INVALID, "need 1 <= p <= 10, 0 <= o <= 1, dir 0 or 1 and cls 0..3");
+  if (!V || !lam || !k) return fail(PMG_ERR_INVALID, "V, lam and k must not be NULL");
+  fdm_class(p, o, dir, cls, V, lam, *k);
+  return PMG_OK;
+}
+
 pmg_status pmg_create(const pmg_mesh_desc* mesh, const pmg_opts* opts, pmg_handle** out) {
   if (!out) return fail(PMG_ERR_INVALID, "out is NULL");
   *out = nullptr;

@@ -67,6 +67,7 @@ _SIGNATURES = {
     "pmg_level_sequence": (_I, [ctypes.POINTER(MeshDesc), ctypes.POINTER(Opts), ctypes.POINTER(_I),
                                ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "pmg_basis_tables": (_I, [_I, _I, _P, _P, _P, _P]),
+    "pmg_schwarz_class": (_I, [_I, _I, _I, _I, _P, _P, ctypes.POINTER(_I)]),
     "pmg_node_coords": (_I, [_P, _P, _P]),
     "pmg_set_geometry": (_I, [_P, _P, _P]),
     "pmg_set_geometry_mixed": (_I, [_P, _P, _P, _P]),
@@ -208,6 +209,19 @@ def basis_tables(p, pc=0):
                                    ctypes.c_void_p(D.data_ptr()),
                                    ctypes.c_void_p(J.data_ptr()) if pc >= 1 else None))
     return {"nodes": x, "weights": w, "D": D, "J": J if pc >= 1 else None}
+
+
+def schwarz_class(p, overlap, direction, cls):
+    """pmg_schwarz_class: (V, lam, k) of one Schwarz element class of a level of order p,
+    direction 0 (x) or 1 (sigma), class 0 interior / 1 first / 2 last / 3 single element
+    (host-only, no GPU)."""
+    nb = p + 1 + 2 * overlap
+    V = torch.zeros(nb, nb, dtype=torch.float64)
+    lam = torch.zeros(nb, dtype=torch.float64)
+    k = ctypes.c_int()
+    _check(load().pmg_schwarz_class(p, overlap, direction, cls, ctypes.c_void_p(V.data_ptr()),
+                                    ctypes.c_void_p(lam.data_ptr()), ctypes.byref(k)))
+    return V, lam, k.value
 
 
 class Solver:

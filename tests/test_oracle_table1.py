@@ -47,6 +47,19 @@ def table1_case():
     return _case
 
 
+def test_case_is_the_table1_discretisation():
+    """Sec. 6 describes the Table 1 case as P = 8, N_x = 102, N_z = 2, seventeen waves of
+    kh = 1 with H/L = 0.0301, about 48 points per wavelength: the workload is that case."""
+    w = W.paper_shape()
+    assert (w.order, w.cells_x, w.cells_z, w.h, w.periodic) == (8, 102, 2, 1.0, False)
+    k = w.surface.k
+    wavelength = 2 * np.pi / k
+    assert abs(k * w.h - 1.0) < 1e-15
+    np.testing.assert_allclose((w.x1 - w.x0) / wavelength, 17.0, rtol=1e-14)
+    np.testing.assert_allclose(2 * w.surface.amp / wavelength, 0.0301, rtol=1e-14)
+    assert abs(w.cells_x * w.order / 17.0 - 48.0) < 0.1
+
+
 def test_golden_file_is_the_printed_table():
     assert golden_rows() == [(1e-4, 3, 1), (1e-6, 5, 3), (1e-8, 8, 4)]
 

@@ -60,6 +60,18 @@ def test_case_is_the_table1_discretisation():
     assert abs(w.cells_x * w.order / 17.0 - 48.0) < 0.1
 
 
+@pytest.mark.parametrize("cells_x,order", [(25, 8), (200, 8), (800, 8), (200, 2), (200, 10)])
+def test_scaling_family_keeps_the_paper_resolution(cells_x, order):
+    """Sec. 6's scaling study: N_z = 2, P_z = 8, waves of kh = 1 and H/L = 0.0301 at about
+    48 points per wavelength whatever N_x or P_x."""
+    w = W.paper_scaling(cells_x, order, order_z=8)
+    assert (w.cells_z, w.order_z, w.h) == (2, 8, 1.0)
+    wavelength = 2 * np.pi / w.surface.k
+    assert abs(w.surface.k * w.h - 1.0) < 1e-15
+    np.testing.assert_allclose(2 * w.surface.amp / wavelength, 0.0301, rtol=1e-14)
+    np.testing.assert_allclose(cells_x * order / ((w.x1 - w.x0) / wavelength), 48.0, rtol=1e-12)
+
+
 def test_golden_file_is_the_printed_table():
     assert golden_rows() == [(1e-4, 3, 1), (1e-6, 5, 3), (1e-8, 8, 4)]
 

@@ -1,7 +1,8 @@
 """Pins of the oracle's multigrid quality on the paper's Table 1 case (Sec. 6, P = 8,
 N_x = 102, N_z = 2, kh = 1, H/L = 0.0301, the mixed-stage operator of Sec. 3), against
 the iteration counts the paper prints (tests/golden/table1_mg_iterations.txt) and against
-the minimal-residual property that ties GMRES to defect correction."""
+the minimal-residual property that ties GMRES to defect correction; and the synthetic
+Table 1 case and scaling-study family are the discretisations Sec. 6 states."""
 import os
 
 import numpy as np

@@ -164,12 +164,16 @@ pmg_status pmg_schwarz_class(int p, int o, int dir, int cls, double* V, double* 
  * (Sec. 5.3) and the coarse factor, on the current CUDA device; geometry starts flat
  * (eta = 0).  Synchronous.  *out is NULL on failure. */
 pmg_status pmg_create(const pmg_mesh_desc* mesh, const pmg_opts* opts, pmg_handle** out);
+/* Frees everything pmg_create allocated (device and host); NULL is a no-op.  Lifecycle
+ * only: no counterpart in the paper. */
 pmg_status pmg_destroy(pmg_handle* h);
 
-/* Sizes: total nodes n = NX*NZ, free (non-Dirichlet) nodes, NX, NZ, number of levels. */
+/* Sizes of the nodal mesh (the global numbering of Sec. 4.3): total nodes n = NX*NZ, free
+ * (non-Dirichlet) nodes, NX, NZ, number of levels (Sec. 5.1).  Any pointer may be NULL. */
 pmg_status pmg_num_nodes(const pmg_handle* h, int64_t* n, int64_t* n_free, int* nx, int* nz,
                          int* nlevels);
-/* Order and node counts of level l (0 = finest). */
+/* Order and node counts of level l (0 = finest) of the hierarchy of Sec. 5.1.
+ * PMG_ERR_INVALID for a bad level. */
 pmg_status pmg_level_info(const pmg_handle* h, int level, int* order, int* nx, int* nz);
 /* Launch configuration of level l's FP32 kernels as set at creation or chosen by
  * pmg_autotune: flat32 = level operator (> 0 slab CTA size, < 0 node-parallel CTA size,
@@ -177,7 +181,8 @@ pmg_status pmg_level_info(const pmg_handle* h, int level, int* order, int* nx, i
  * sweep CTA size, xfer = transfer CTA size.  Host-side read; any pointer may be NULL.
  * The paper has no counterpart.  PMG_ERR_INVALID for a bad handle or level. */
 pmg_status pmg_level_kernels(const pmg_handle* h, int level, int* flat32, int* fdm32, int* xfer);
-/* x* of every node column (NX values) and sigma of every node row (NZ values), host. */
+/* x* of every node column (NX values) and sigma of every node row (NZ values) of the
+ * sigma-domain mesh (Sec. 2.2, LGL nodes per cell, Sec. 4.3); caller-owned host arrays. */
 pmg_status pmg_node_coords(const pmg_handle* h, double* x_cols_host, double* sigma_rows_host);
 
 /* Per-stage geometry (Sec. 2.2): eta at every node column (NX values, device).  The
@@ -210,7 +215,9 @@ pmg_status pmg_set_geometry_mixed(pmg_handle* h, const double* eta_dev, const do
  * depth only); there is no way back to a constant depth but a new handle. */
 pmg_status pmg_set_bathymetry(pmg_handle* h, const double* h_dev, void* stream);
 
-/* b_i = -int N_i f dOmega + int_{Gamma_N} N_i g dGamma (LGL collocation), b = 0 on the
+/* The load of the pressure Poisson problem (Sec. 3.1-3.2: Dirichlet on the free surface,
+ * Neumann on walls and bottom) in the weak form of Sec. 4.2:
+ * b_i = -int N_i f dOmega + int_{Gamma_N} N_i g dGamma (LGL collocation), b = 0 on the
  * free surface.  f: nodal values (n); g_bottom: outward normal derivative on the bottom
  * per node column (NX); g_left / g_right: on the walls per node row (NZ).  Any g may be
  * NULL (zero flux); the wall arrays are ignored when periodic. */
@@ -218,11 +225,13 @@ pmg_status pmg_assemble_rhs(pmg_handle* h, const double* f_dev, const double* g_
                             const double* g_left_dev, const double* g_right_dev, double* b_dev,
                             void* stream);
 /* b_i = scale * int grad N_i . (u, w) dOmega: the weak divergence of a nodal velocity
- * field (projection form of the pressure step; carries n.u on walls and bottom). */
+ * field (the right-hand side rho/dt div u* of the pressure step, Sec. 3.1, in the weak form
+ * of Sec. 4.2; it carries n.u on walls and bottom). */
 pmg_status pmg_assemble_rhs_div(pmg_handle* h, const double* u_dev, const double* w_dev,
                                 double scale, double* b_dev, void* stream);
 
-/* Solve for the pressure: p_out = p_D on the free surface, A_FF p_F = b_F - A_FD p_D.
+/* Solve for the pressure (Sec. 5: the outer iteration of Sec. 5.4 preconditioned by one
+ * p-multigrid V-cycle): p_out = p_D on the free surface, A_FF p_F = b_F - A_FD p_D.
  * b_dev: load vector (free entries used); p_dirichlet_dev: values read on the surface
  * row only; x0_dev: initial guess or NULL (zero).  Returns PMG_ERR_NOT_CONVERGED with the
  * last iterate in p_out when max_iter is hit.  info may be NULL.  Synchronises the stream
@@ -231,13 +240,14 @@ pmg_status pmg_solve(pmg_handle* h, const double* b_dev, const double* p_dirichl
                      const double* x0_dev, double* p_out_dev, pmg_solve_info* info,
                      void* stream);
 
-/* Same, with all five vectors in host memory (n doubles each, x0 may be NULL): copies
+/* pmg_solve (Sec. 5) with all five vectors in host memory (n doubles each, x0 may be NULL): copies
  * in, solves, copies out, through pinned staging buffers owned by the handle. */
 pmg_status pmg_solve_host(pmg_handle* h, const double* b_host, const double* p_dirichlet_host,
                           const double* x0_host, double* p_out_host, pmg_solve_info* info,
                           void* stream);
 /* ||b~ - A x~||_2 on the device: x~ is x with its surface row replaced by p_D (the lifted
- * residual that the solve's tolerance is measured in, Sec. 4.1).  Synchronises `stream`
+ * residual that the solve's tolerance is measured in: the residual r of Sec. 5.4 after
+ * the Dirichlet lifting).  Synchronises `stream`
  * and writes the norm to *norm (host).  PMG_ERR_NONFINITE for a non-finite input. */
 pmg_status pmg_residual_norm(pmg_handle* h, const double* b, const double* p_dirichlet, const double* x,
                              double* norm, void* stream);
@@ -245,23 +255,25 @@ pmg_status pmg_residual_norm(pmg_handle* h, const double* b, const double* p_dir
 /* ---- component entry points (parity tests and benchmarks) ------------------------- */
 /* y = A_FF x on free nodes, y = x on the surface row; actual geometry, FP64 (Sec. 4.2). */
 pmg_status pmg_apply(pmg_handle* h, const double* x_dev, double* y_dev, void* stream);
-/* The same operator in FP32 storage and arithmetic. */
+/* The same operator (Sec. 4.2) in FP32 storage and arithmetic (the paper computes in FP64). */
 pmg_status pmg_apply_f32(pmg_handle* h, const float* x_dev, float* y_dev, void* stream);
 /* The same FP32 operator with its four sum-factorised contractions on the BF16 tensor
  * cores (mma.sync m16n8k16, FP32 accumulation): split = 0 rounds D and the operand to
  * BF16 once; split = 1 adds hi*hi + hi*lo + lo*hi of their BF16 hi/lo parts (about 16
  * significant bits per product).  Not in the paper.  x, y: NX*NZ floats on the device. */
 pmg_status pmg_apply_bf16(pmg_handle* h, const float* x_dev, float* y_dev, int split, void* stream);
-/* Flat level-l operator (the multigrid level matrix), masked like pmg_apply.
+/* Flat level-l operator (the multigrid level matrix of Sec. 5.1 on the linearised geometry
+ * of Sec. 5.4), masked like pmg_apply.
  * f32 = 0: FP64 vectors, 1: FP32 vectors. */
 pmg_status pmg_level_apply(pmg_handle* h, int level, const void* x_dev, void* y_dev, int f32,
                            void* stream);
-/* nu Schwarz sweeps on level l for A_l x = b, updating x in place (Sec. 5.3);
- * post = 0: x += omega W sum R^T A_i^-1 R r, post = 1: the adjoint (W applied to r). */
 /* One additive-Schwarz sweep x += omega W sum_e R_e^T A_e^-1 R_e r (post = 0) or its adjoint
  * (post = 1) on level `level` for a given residual r (Sec. 5.3): a single kernel launch,
  * for timing and tests.  Vectors as in pmg_level_smooth. */
 pmg_status pmg_level_sweep(pmg_handle* h, int level, const void* r, void* x, int post, int f32, void* stream);
+/* nu Schwarz sweeps on level l for A_l x = b, updating x in place (Sec. 5.3);
+ * post = 0: x += omega W sum R^T A_i^-1 R r, post = 1: the adjoint (W applied to r).
+ * f32 = 0: FP64 vectors, 1: FP32 vectors (level l's node count each). */
 pmg_status pmg_level_smooth(pmg_handle* h, int level, const void* b_dev, void* x_dev, int post,
                             int f32, void* stream);
 /* r_c = P^T r_f (level l -> l+1) and x_f += P x_c (level l+1 -> l) (Sec. 5.2). */
@@ -269,7 +281,8 @@ pmg_status pmg_restrict(pmg_handle* h, int level, const void* rf_dev, void* rc_d
                         void* stream);
 pmg_status pmg_prolong(pmg_handle* h, int level, const void* xc_dev, void* xf_dev, int f32,
                        void* stream);
-/* Exact FP64 solve of the coarsest (order 1) level system (free nodes; surface row 0). */
+/* Exact FP64 solve of the coarsest (order 1) level system (free nodes; surface row 0).  The
+ * paper names order 1 as the coarsest level (Sec. 5.1) but not its solver. */
 pmg_status pmg_coarse_solve(pmg_handle* h, const double* b_dev, double* x_dev, void* stream);
 /* z = B r: one V-cycle of the preconditioner on the finest level (Sec. 5). */
 pmg_status pmg_vcycle(pmg_handle* h, const void* r_dev, void* z_dev, int f32, void* stream);
@@ -279,7 +292,6 @@ pmg_status pmg_vcycle(pmg_handle* h, const void* r_dev, void* z_dev, int f32, vo
  * lumped-mass L2 projection (the paper's gradient recovery, Sec. 4): element-local
  * derivatives through the sigma-map (Sec. 2.2), averaged over the elements of a node. */
 pmg_status pmg_gradient(pmg_handle* h, const double* f_dev, double* fx_dev, double* fz_dev, void* stream);
-/* eta_x per node column (NX) of the current surface polynomial (mean at element edges). */
 /* Exponential cut-off filter of the modal coefficients (Sec. "Spectral Filtering"):
  * S(k) = 1 for k <= cutoff, exp(alpha ((k - cutoff)/(P + 1 - cutoff))^beta) above, on the
  * orthonormal Legendre modes of each element, F = V diag(S) V^-1.  pmg_set_filter builds
@@ -289,6 +301,8 @@ pmg_status pmg_gradient(pmg_handle* h, const double* f_dev, double* fx_dev, doub
  * elements; `out` must not alias `f`. */
 pmg_status pmg_set_filter(pmg_handle* h, int cutoff, double alpha, double beta);
 pmg_status pmg_filter(pmg_handle* h, const double* f, double* out, int surface, void* stream);
+/* eta_x per node column (NX) of the current surface polynomial, the slope in the kinematic
+ * condition and the sigma-map (Sec. 2.2, Sec. 4.1); the mean at element edges. */
 pmg_status pmg_surface_slope(pmg_handle* h, double* etax_dev, void* stream);
 /* Explicit forcing of the inviscid momentum equations with the static pressure folded in
  * (p = p_D + rho g (eta - z), Sec. 2.1): Fu = -(u u_x + w u_z) - g eta_x, Fw = -(u w_x + w w_z).
@@ -304,7 +318,7 @@ pmg_status pmg_stage_rates(pmg_handle* h, const double* u_dev, const double* w_d
                            const double* wz_dev, const double* Fu_dev, const double* Fw_dev, const double* px_dev,
                            const double* pz_dev, const double* etax_dev, double rho, double* du_dev, double* dw_dev,
                            double* deta_dev, void* stream);
-/* out = y + a x over n doubles (Runge-Kutta stage states and accumulation). */
+/* out = y + a x over n doubles: the stage updates of the Runge-Kutta schemes (Sec. 3). */
 pmg_status pmg_axpy(pmg_handle* h, int64_t n, double a, const double* x_dev, const double* y_dev, double* out_dev,
                     void* stream);
 
@@ -369,7 +383,8 @@ pmg_status pmg_ws_load(pmg_ws* ws, const char* path);
  * problem runs its own device-side Krylov loop (a CUDA graph with a while node) on its
  * own stream forked from the caller's stream, so the problems' kernels share the GPU
  * concurrently; the host synchronises three times per batch solve, not per iteration.
- * opts apply to every problem; pmg_batch_create runs pmg_autotune on every problem. */
+ * opts apply to every problem; pmg_batch_create runs pmg_autotune on every problem.  Not in
+ * the paper (it solves one tank at a time). */
 typedef struct pmg_batch pmg_batch;
 pmg_status pmg_batch_create(int n, const pmg_mesh_desc* meshes, const pmg_opts* opts, pmg_batch** out);
 pmg_status pmg_batch_destroy(pmg_batch* b);
@@ -414,6 +429,7 @@ pmg_status pmg_apply_noalloc(const pmg_mesh_desc* mesh, const double* eta_dev, c
                              double* y_dev, void* stream);
 
 /* ---- profiling ---------------------------------------------------------------------- */
+/* Instrumentation of this library; no counterpart in the paper. */
 /* Kernel classes for launch counting and device timing. */
 enum {
   PMG_K_CURVED64 = 0,  /* actual-geometry operator, FP64 (apply / residual / dot)          */
@@ -437,7 +453,8 @@ pmg_status pmg_profile_reset(pmg_handle* h, int timing);
  * kernels' definitions imply; an FMA counts two).  Synchronises the device. */
 pmg_status pmg_profile_read(pmg_handle* h, int64_t* launches, double* ms, double* bytes, double* flops);
 
-/* Message of the last failing call on this thread ("" if none). */
+/* Message of the last failing call on this thread ("" if none).  Error reporting of this
+ * library; no counterpart in the paper. */
 const char* pmg_last_error(void);
 
 #ifdef __cplusplus

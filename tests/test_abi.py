@@ -29,6 +29,21 @@ def test_library_exports_every_declared_symbol():
     assert not missing, missing
 
 
+def test_library_exports_nothing_undeclared():
+    """Every exported pmg_* function is declared in include/ (no stray C-ABI entry points)."""
+    import shutil
+    import subprocess
+    if shutil.which("nm") is None:
+        pytest.skip("nm not available")
+    pmg.load(build_if_missing=True)
+    out = subprocess.run(["nm", "-D", "--defined-only", pmg.library_path()], capture_output=True, text=True,
+                         check=True).stdout
+    exported = {f[2] for f in (ln.split() for ln in out.splitlines()) if len(f) == 3 and f[1] == "T"
+                and f[2].startswith("pmg_")}
+    assert exported == declared_functions(), (sorted(exported - declared_functions()),
+                                              sorted(declared_functions() - exported))
+
+
 def test_binding_covers_declared_symbols():
     assert declared_functions() <= set(pmg._SIGNATURES)
 

@@ -47,3 +47,23 @@ def test_missing_library_raises():
     r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stderr
     assert r.stdout.startswith("raised") and "missing" in r.stdout
+
+
+def test_bench_runs_the_oracle_only_in_its_cpu_baseline_and_reference_legs():
+    tree = ast.parse(open(os.path.join(ROOT, "bench.py")).read())
+    importers, callers = set(), set()
+    for fn in ast.walk(tree):
+        if not isinstance(fn, ast.FunctionDef):
+            continue
+        for node in ast.walk(fn):
+            if isinstance(node, ast.ImportFrom) and node.module and node.module.split(".")[0] == "oracle":
+                importers.add(fn.name)
+            if isinstance(node, ast.Import) and any(a.name.split(".")[0] == "oracle" for a in node.names):
+                importers.add(fn.name)
+            if isinstance(node, ast.Call) and getattr(node.func, "id", None) == "oracle_solve_timed":
+                callers.add(fn.name)
+    assert importers <= {"oracle_solve_timed", "cpu_baseline_paper", "cpu_baseline_bar"}, importers
+    assert callers <= {"cpu_baseline_entry", "run_reference"}, callers
+    top = [n for n in tree.body if isinstance(n, (ast.Import, ast.ImportFrom))]
+    assert not any(getattr(n, "module", None) == "oracle" or
+                   any(a.name.split(".")[0] == "oracle" for a in getattr(n, "names", [])) for n in top)

@@ -1,6 +1,7 @@
 """The oracle stays test infrastructure: the product package and the shared input
-generators never import it, the oracle never imports the product, and the product path
-raises, rather than falling back to any CPU code, when its native library is missing."""
+generators never import it, the oracle never imports the product, bench.py reaches it
+only from its CPU-baseline and reference legs, and the product path raises, rather than
+falling back to any CPU code, when its native library is missing."""
 import ast
 import os
 import subprocess

@@ -12,15 +12,19 @@ Prints one JSON line (rank 0):
              stated against), speedup_vs_plain_fp64 the ratio
   roofline   the dominant kernel (the finest-level FP32 Schwarz sweep), timed alone with CUDA
              events: algorithmic bytes / time against the measured HBM peak, with the DRAM
-             traffic of one ncu capture; roofline_outer_operator: the double-float outer
-             operator's FP64-equivalent rate
-  e2e        the same metric with the inputs copied from pinned host memory and the
-             pressure copied back inside the timed region
+             traffic of the recorded ncu capture while the kernel's sources are unchanged;
+             roofline_outer_operator: the double-float outer operator against HBM;
+             roofline_graded: the operator-apply kernels on a 10.1M-node tank of the same
+             family with L2 flushed before every launch
+  e2e        the same metric through pmg_set_geometry + pmg_solve_host, with the inputs
+             copied from pinned host memory and the pressure copied back inside the timed
+             region
   cpu_baseline  the FP64 CPU oracle on a bounded slice of the same tank
 
 --impl reference times the oracle (the CPU reference implementation of this method).
 """
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -37,7 +41,6 @@ import numpy as np  # noqa: E402
 
 METRIC = "Poisson solves/s x free DOF (DOF/s) to rel. residual 1e-10"
 UNIT = "DOF/s"
-FP64_PEAK_GFLOPS = 1250.0   # GB300 FP64 (vector and tensor), nominal
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -66,6 +69,8 @@ def parse():
                     help="cfg5 spectral filter after every step: strong = (P_c 0, alpha -36, beta 8), "
                          "few-percent = (P_c P-2, S(P) 0.97, beta 8)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graded", action="store_true", help="skip the roofline_graded block (large tank)")
+    ap.add_argument("--oracle-one-core-child", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--ncu-step", action="store_true",
                     help="profiling aid: one warm step, then one step inside the NVTX range 'profiled_step'")
     return ap.parse_args()
@@ -122,12 +127,52 @@ def oracle_solve_timed(w, hier=None):
     return t1 - t0, c1 - c0, int((~m.dirichlet_mask()).sum()), its, hier
 
 
+def _host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_one_core_child():
+    """Child process of the one-core oracle timing: pinned to one CPU, BLAS on one thread
+    (set in its environment by the parent), prints one JSON line."""
+    try:
+        os.sched_setaffinity(0, {sorted(os.sched_getaffinity(0))[0]})
+    except (AttributeError, OSError):
+        pass
+    wall, cpu, nfree, its, _ = oracle_solve_timed(oracle_slice())
+    print(json.dumps({"wall": wall, "cpu": cpu, "nfree": nfree, "its": its}), flush=True)
+
+
+def oracle_one_core():
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               NUMEXPR_NUM_THREADS="1", VECLIB_MAXIMUM_THREADS="1")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-one-core-child"], env=env,
+                       capture_output=True, text=True, timeout=600)
+    lines = [x for x in r.stdout.splitlines() if x.startswith("{")]
+    if r.returncode != 0 or not lines:
+        return None
+    return json.loads(lines[-1])
+
+
 def cpu_baseline_entry():
+    """The FP64 oracle (as it stands) on a bounded sample of the tank: one solve of the
+    32 x 32-cell, P = 6 slice on all host cores (the BLAS thread pool), and one on a
+    single core (child process pinned to one CPU, one BLAS thread)."""
     w = oracle_slice()
     wall, cpu, nfree, its, _ = oracle_solve_timed(w)
-    return {"value": nfree / wall, "unit": UNIT, "cores": round(cpu / wall, 1), "kind": "oracle",
-            "sample": f"one FP64 oracle p-MG-PCG solve to 1e-10 (assembly + PCG, setup excluded) of the "
-                      f"32x32-cell P=6 slice of the tank ({nfree} free DOF, {its} iterations, {wall:.1f} s)"}
+    nproc = _host_cores()
+    out = {"value": nfree / wall, "unit": UNIT, "cores": nproc, "kind": "oracle",
+           "cpu_utilisation": round(cpu / wall, 1), "nproc": nproc,
+           "sample": f"one FP64 oracle p-MG-PCG solve to 1e-10 (assembly + PCG, setup excluded) of the "
+                     f"32x32-cell P=6 slice of the tank ({nfree} free DOF, {its} iterations, {wall:.1f} s) on "
+                     f"all {nproc} host cores (process CPU / wall = {cpu / wall:.1f})"}
+    one = oracle_one_core()
+    if one is not None:
+        out["one_core"] = {"value": one["nfree"] / one["wall"], "unit": UNIT, "cores": 1,
+                           "wall_s": round(one["wall"], 2), "iterations": one["its"]}
+    return out
 
 
 def cpu_baseline_paper(w):
@@ -216,6 +261,103 @@ def measured_peaks():
         return {}
 
 
+NCU_RECORD = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+CSRC = os.path.join(ROOT, "paper_2411_14977_gb300", "csrc")
+FDM32_SOURCES = ("k_fdm32.cu", "pmg_common.cuh", "pmg_kernels.h")
+CURVED_SOURCES = ("k_curved.cuh", "k_apply.cu", "pmg_common.cuh", "pmg_kernels.h")
+
+
+def source_digest(files):
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_record(key, files):
+    """The ncu counters of one kernel (DRAM bytes per launch = dram__bytes_read.sum +
+    dram__bytes_write.sum, pipe utilisation) recorded from one capture in
+    profiles/ncu_traffic.json, returned only while the kernel's sources are byte for byte
+    those the capture was taken from; otherwise (None, reason)."""
+    try:
+        with open(NCU_RECORD) as fh:
+            rec = json.load(fh).get(key)
+    except (OSError, ValueError):
+        rec = None
+    if not rec:
+        return None, "no ncu capture recorded for this kernel and workload"
+    if rec.get("source_digest") != source_digest(files):
+        return None, "stale: the kernel's sources changed after the ncu capture"
+    return rec, rec.get("profile", "")
+
+
+def cold_launch_us(torch, fn, flush, reps=10):
+    """Median device time of one launch of fn after an L2 flush (a write of `flush`, larger
+    than L2), CUDA events on the current stream; a GPU-side sleep after the flush keeps the
+    launch queue ahead of the device so the events bracket the kernel alone."""
+    st = torch.cuda.current_stream()
+    ts = []
+    for k in range(reps + 2):
+        flush.fill_(1.0)
+        if hasattr(torch.cuda, "_sleep"):
+            torch.cuda._sleep(200000)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        fn()
+        e1.record(st)
+        e1.synchronize()
+        if k >= 2:
+            ts.append(1e3 * e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+GRADED_CELLS_X = 8704   # 8704 x 32 quads at P = 6: 10.1M nodes, the size of the 64-problem batch
+
+
+def graded_roofline(torch, pmg, dev, hbm, flush):
+    """The operator-apply kernels at a size beyond L2 (a 10.1M-node tank of the same family,
+    FP32 vectors of 40 MB) with L2 flushed before every launch: algorithmic bytes (the
+    vectors each launch must read and write once, plus the geometry's column factors) /
+    median cold launch time, against the measured HBM copy rate."""
+    import workloads as W
+    w = W.tank(GRADED_CELLS_X, 32, 6)
+    S = pmg.Solver(**w.mesh_kwargs(), precision=pmg.PMG_MIXED_FP32)
+    xc, sr = S.node_coords()
+    F = w.fields(xc, sr)
+    S.set_geometry(torch.as_tensor(np.ascontiguousarray(F["eta"]), dtype=torch.float64, device=dev))
+    S.autotune()
+    N, P = S.n, 6
+    cols = GRADED_CELLS_X * (P + 1)
+    r32, x32, y32 = (torch.randn(N, dtype=torch.float32, device=dev) for _ in range(3))
+    x64, y64 = (torch.randn(N, dtype=torch.float64, device=dev) for _ in range(2))
+    kern = {
+        "k_fdm32 finest-level Schwarz sweep (FP32; r, x in, x out)":
+            (lambda: S.level_sweep(0, r32, x32), 3.0 * N * 4),
+        "k_flat finest-level operator (FP32; x in, y out)":
+            (lambda: S.level_apply(0, x32, y32), 2.0 * N * 4),
+        "k_curved actual-geometry operator (FP32; x in, y out, 4 column factors per node column)":
+            (lambda: S.apply_f32(x32, y32), 2.0 * N * 4 + cols * 4 * 4),
+        "k_curved outer operator (double-float on the FP32 pipe; FP64 x in, y out, column factors)":
+            (lambda: S.apply(x64, y64), 2.0 * N * 8 + cols * 4 * 8),
+    }
+    out = {"workload": f"{w.name} ({GRADED_CELLS_X}x32 quads, P=6)", "nodes": N,
+           "l2": "flushed before every launch (256 MiB write)", "peak": hbm, "unit": "GB/s",
+           "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured), burst: kernels timed alone",
+           "level0_kernels": S.level_kernels(0), "kernels": {}}
+    for name, (fn, by) in kern.items():
+        for _ in range(3):
+            fn()
+        us = cold_launch_us(torch, fn, flush)
+        gbs = by / (us * 1e-6) / 1e9
+        out["kernels"][name] = {"bound": "hbm", "avg_launch_us": us, "algorithmic_bytes_per_launch": by,
+                                "achieved": gbs, "frac": gbs / hbm}
+    S.close()
+    del r32, x32, y32, x64, y64
+    torch.cuda.empty_cache()
+    return out
+
+
 # ------------------------------------------------------------------------------------
 def graph_launch_us(torch, fn, reps=50):
     """Device time per launch of fn: `reps` launches captured in one CUDA graph and
@@ -279,7 +421,7 @@ def run_ours(args, ws, rank, local):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    def timed(S, d, bufs, K, e2e=None):
+    def timed(S, d, bufs, K):
         """Per-step CUDA-event device times (L2 flushed before each step, outside the events)."""
         evs, infos = [], []
         st = torch.cuda.current_stream()
@@ -287,14 +429,7 @@ def run_ours(args, ws, rank, local):
             flush.fill_(1.0)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(st)
-            if e2e is None:
-                infos.append(step(S, d, bufs))
-            else:
-                host, pout = e2e
-                for k in d:
-                    d[k].copy_(host[k], non_blocking=True)
-                infos.append(step(S, d, bufs))
-                pout.copy_(bufs["p"], non_blocking=True)
+            infos.append(step(S, d, bufs))
             e1.record(st)
             evs.append((e0, e1))
         torch.cuda.synchronize()
@@ -355,24 +490,33 @@ def run_ours(args, ws, rank, local):
     bytes_sweep = 3.0 * N0 * 4  # r and x in, x out (FP32)
     achieved = bytes_sweep / (us_sweep * 1e-6) / 1e9
     p0 = S.level_info(0)[0]
+    key = f"k_fdm32<{p0},1,0> {args.workload}"
+    rec, src = ncu_record(key, FDM32_SOURCES)
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-            # dram__bytes_read.sum + dram__bytes_write.sum of this kernel, one ncu capture of the
-            # same build and workload (profiles/k_fdm32_p6_cfg2.md)
-            "traffic": 4.863744e6 if p0 == 6 and args.workload == "cfg2" else None,
+            # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture of
+            # this kernel and workload, used only while its sources are unchanged
+            "traffic": rec["dram_bytes_per_launch"] if rec else None,
+            "traffic_source": src,
             "kernel": f"k_fdm32<{p0},1> finest-level FP32 Schwarz sweep", "avg_launch_us": us_sweep,
             "algorithmic_bytes_per_launch": bytes_sweep,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured); burst peak, kernel timed alone",
-            "note": "latency-bound: the working set is L2-resident; see kernel_time_shares"}
-    # ---- the outer operator (double-float arithmetic on the FP32 pipe, FP64 vectors)
+            "note": "latency-bound: the working set is L2-resident; see kernel_time_shares and roofline_graded"}
+    # ---- the outer operator (double-float arithmetic on the FP32 pipe, FP64 vectors):
+    # against HBM; its FP32-pipe utilisation is an ncu counter (recorded capture, if current)
     x64 = torch.randn(N0, dtype=torch.float64, device=dev)
     us_ap = per_launch_us(lambda: S.apply(x64))
-    P0 = p0 + 1
-    fl_ap = S.mesh.cells_x * S.mesh.cells_z * (8.0 * P0 ** 3 + 12.0 * P0 ** 2)
-    roof_outer = {"bound": "alu", "kernel": f"k_curved<{p0},df64> outer operator (FP64 in/out)",
-                  "avg_launch_us": us_ap, "achieved": fl_ap / (us_ap * 1e-6) / 1e12,
-                  "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s (FP64-equivalent operations)",
-                  "frac": fl_ap / (us_ap * 1e-6) / 1e12 / (FP64_PEAK_GFLOPS / 1e3),
-                  "peak_source": "nominal GB300 FP64 1.25 TFLOP/s: the rate this operator would have on the FP64 pipe"}
+    cols0 = S.mesh.cells_x * (p0 + 1)
+    by_ap = 2.0 * N0 * 8 + cols0 * 4 * 8
+    rec_o, src_o = ncu_record(f"k_curved<{p0},df64,2> {args.workload}", CURVED_SOURCES)
+    roof_outer = {"bound": "hbm", "kernel": f"k_curved<{p0},df64> outer operator (FP64 in/out, double-float "
+                                            f"arithmetic on the FP32 pipe)",
+                  "avg_launch_us": us_ap, "algorithmic_bytes_per_launch": by_ap,
+                  "achieved": by_ap / (us_ap * 1e-6) / 1e9, "peak": hbm, "unit": "GB/s",
+                  "frac": by_ap / (us_ap * 1e-6) / 1e9 / hbm,
+                  "fp32_pipe_busy_pct": rec_o.get("fma_pipe_busy_pct") if rec_o else None,
+                  "fp64_pipe_busy_pct": rec_o.get("fp64_pipe_busy_pct") if rec_o else None,
+                  "pipe_source": src_o,
+                  "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured); burst peak, kernel timed alone"}
     shares = {k: round(v[1] / sum(x[1] for x in pclass.values()), 4) for k, v in pclass.items() if v[0]}
 
     # ---- plain FP64 p-multigrid on the same steps
@@ -386,13 +530,38 @@ def run_ours(args, ws, rank, local):
     t64 = all_max(t64)
     v64 = ws * S64.n_free * K64 / t64
 
-    # ---- end to end: pinned host inputs in, pressure out, inside the timed region
+    # ---- end to end through the host-buffer call: per step the stage surface (pinned host
+    # -> device, then pmg_set_geometry) and pmg_solve_host with the step's load vector and
+    # Dirichlet data in pinned host memory and the pressure back into pinned host memory
+    b_host = bufs["b"].cpu().pin_memory()
+    pD_host = host["pD"]
     pout = torch.empty(S.n, dtype=torch.float64).pin_memory()
+    st = torch.cuda.current_stream()
+    for _ in range(2):
+        d["eta"].copy_(host["eta"], non_blocking=True)
+        S.set_geometry(d["eta"])
+        S.solve_host(b_host, pD_host, out=pout)
     barrier()
-    te, _ = timed(S, d, bufs, K, e2e=(host, pout))
+    evs = []
+    for _ in range(K):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        d["eta"].copy_(host["eta"], non_blocking=True)
+        S.set_geometry(d["eta"])
+        _, ie = S.solve_host(b_host, pD_host, out=pout)
+        e1.record(st)
+        evs.append((e0, e1))
+        assert ie["status"] == 0 and ie["rel_residual"] <= 1e-10, ie
+    torch.cuda.synchronize()
+    te = sum(a.elapsed_time(b) for a, b in evs) / 1e3
     barrier()
     te = all_max(te)
-    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    h2d = host["eta"].numel() * 8 + b_host.numel() * 8 + pD_host.numel() * 8
+
+    graded = None
+    if rank == 0 and not args.no_graded:
+        graded = graded_roofline(torch, pmg, dev, hbm, flush)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": max(args.warmup, 3),
@@ -415,10 +584,14 @@ def run_ours(args, ws, rank, local):
         "speedup_vs_plain_fp64": value / v64,
         "roofline": roof,
         "roofline_outer_operator": roof_outer,
+        "roofline_graded": graded,
         "kernel_time_shares": shares,
         "gpu_launches": launches,
         "e2e": {"value": ws * S.n_free * K / te, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": S.n * 8},
+                "d2h_bytes_per_step": S.n * 8,
+                "path": "pmg_set_geometry + pmg_solve_host (C ABI, pinned host buffers in and out); the step's "
+                        "load vector is an input here (assembled once at setup), the device-timed step "
+                        "assembles it"},
         "clocks": clocks,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -1076,6 +1249,9 @@ def run_reference(args, ws, rank):
 
 def main():
     args = parse()
+    if args.oracle_one_core_child:
+        oracle_one_core_child()
+        return
     ws, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, ws, rank)

@@ -55,7 +55,8 @@ enum { PMG_FP64 = 0, PMG_MIXED_FP32 = 1, PMG_MIXED_BF16 = 2 };
  *            (mixed precision only; inner_max / inner_tol apply)
  *   PMG_GMRES  flexible GMRES(gmres_restart) with the V-cycle as right preconditioner
  *            (Sec. 5.4's GMRES-MG on the same-stage operator); Arnoldi by classical
- *            Gram-Schmidt applied twice, one host synchronisation per iteration
+ *            Gram-Schmidt applied twice on the device, one host synchronisation per
+ *            restart cycle
  * With PMG_MIXED_FP32 the V-cycle B runs in FP32 on the FP32-rounded residual.
  * PMG_MIXED_BF16 (requires PMG_IR): as PMG_MIXED_FP32, and the inner solve's
  * actual-geometry operator runs its contractions on the BF16 tensor cores with hi/lo
@@ -241,7 +242,9 @@ pmg_status pmg_solve(pmg_handle* h, const double* b_dev, const double* p_dirichl
                      void* stream);
 
 /* pmg_solve (Sec. 5) with all five vectors in host memory (n doubles each, x0 may be NULL): copies
- * in, solves, copies out, through pinned staging buffers owned by the handle. */
+ * the inputs from the caller's host buffers into device vectors owned by the handle, solves,
+ * and copies the pressure back, all on `stream`; returns after the stream has synchronised.
+ * Page-locked (pinned) host buffers give asynchronous copies at the full link rate. */
 pmg_status pmg_solve_host(pmg_handle* h, const double* b_host, const double* p_dirichlet_host,
                           const double* x0_host, double* p_out_host, pmg_solve_info* info,
                           void* stream);
@@ -417,14 +420,19 @@ pmg_status pmg_autotune(pmg_handle* h);
  * geometry eta (NX values), without a handle and without allocating device memory.  The
  * paper has no counterpart: this is for callers that cannot allocate (a host framework
  * that owns every device allocation, a fixed pool, a caller inside a stream capture).
- * The geometry factors, sigma table and slab-edge exchange buffers live in one static
- * 4 MiB device array of the library (held by every GPU that loads it, until exit); meshes
- * needing more, about (cells_x + 1) * (cells_z * order + 1) > 500000, return
+ * The mesh must satisfy pmg_create's rules (pmg_level_sequence checks the same), with
+ * order_z 0 or equal to order.  The geometry factors, sigma table and slab-edge exchange
+ * buffers live in one static 4 MiB (4194304-byte) device array of the library (held by
+ * every GPU that loads it, until exit).  A mesh needs
+ *   256 + a(32 cells_x (order+1)) + a(8 NZ) + a(4 (cells_x+1)) + a(8 (cells_x+1) NZ) bytes,
+ * NZ = cells_z order + 1, a(n) = n rounded up to a multiple of 256; larger meshes return
  * PMG_ERR_INVALID.  The first call on a device sets up (constant tables, the array's device
  * address via cudaGetSymbolAddress); make that first call before any stream capture.
  * Every call shares the array: calls that overlap on the GPU (other streams, other
- * threads) race and must be serialised by the caller.  Asynchronous on the stream;
- * x and y are caller-owned device vectors of n = NX * NZ doubles. */
+ * threads) race and must be serialised by the caller.  Asynchronous on the stream; x and y
+ * are caller-owned device vectors of n = NX * NZ doubles.  The call reads nothing back, so
+ * a depth d = eta + h that is not positive and finite somewhere (PMG_ERR_INVALID from the
+ * handle path) shows in the output instead: every entry of y is NaN. */
 pmg_status pmg_apply_noalloc(const pmg_mesh_desc* mesh, const double* eta_dev, const double* x_dev,
                              double* y_dev, void* stream);
 

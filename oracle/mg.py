@@ -33,6 +33,9 @@ Parity status: the V-cycle's quality is pinned to the PDC-MG iteration counts th
 prints in Table 1 (Sec. 6, within one: the right-hand side is synthetic), and tests pin
 its symmetry and positivity, exact-solve limits, the flat iteration counts in N_x and P
 claimed in Sec. 6.3, and flexible GMRES's minimal residual against defect correction.
+The level geometry (`Hierarchy._eta_at_level`: the surface and the still-water depth at
+each level's nodes) is pinned by polynomial exactness: piecewise polynomials of degree
+<= P must come out at the level's LGL nodes exactly as numpy.polynomial evaluates them.
 """
 import numpy as np
 import scipy.linalg as sla

@@ -77,6 +77,16 @@ __global__ void k_sigma_rows(int NZ, int P, int Nz, Nodes nodes, double* sigma) 
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
+// The call reads nothing back, so a depth d = eta + h that is not positive and finite
+// (flagged by the geometry kernel in *status) is reported in the output: every entry of y
+// becomes NaN.
+__global__ void k_poison_on_bad_geometry(const int* status, double* y, size_t n) {
+  if (*status == 0) return;
+  const double nan = __longlong_as_double(0x7FF8000000000000ll);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = nan;
+}
+
 }  // namespace
 
 extern "C" pmg_status pmg_apply_noalloc(const pmg_mesh_desc* mesh, const double* eta_dev, const double* x_dev,
@@ -86,10 +96,28 @@ extern "C" pmg_status pmg_apply_noalloc(const pmg_mesh_desc* mesh, const double*
     return PMG_ERR_INVALID;
   }
   const pmg_mesh_desc& m = *mesh;
-  if (m.order < 1 || m.order > MAXP || m.cells_x < 1 || m.cells_z < 1 || !(m.x1 > m.x0) || !(m.h > 0.0) ||
-      (m.periodic_x && m.cells_x < 3) || (m.order_z != 0 && m.order_z != m.order)) {
-    set_last_error("bad mesh descriptor (order 1..10, cells >= 1, x1 > x0, h > 0, periodic needs cells_x >= 3, "
-                   "order_z 0 or order)");
+  // the mesh rules of pmg_create (orders, cell bounds, a power-of-two periodic cells_x),
+  // checked before any size is formed from the descriptor
+  int nlev = 0;
+  if (pmg_level_sequence(mesh, nullptr, &nlev, nullptr, nullptr) != PMG_OK) return PMG_ERR_INVALID;
+  if (m.order_z != 0 && m.order_z != m.order) {
+    set_last_error("pmg_apply_noalloc needs equal orders along x and sigma (order_z 0 or order)");
+    return PMG_ERR_INVALID;
+  }
+  const size_t cx = (size_t)m.cells_x, P = (size_t)m.order;
+  const size_t NZ = (size_t)m.cells_z * P + 1, NX = cx * P + (m.periodic_x ? 0 : 1);
+  // scratch layout: [geometry status][column factors][sigma][edge counters][edge buffers]
+  const size_t nedges = cx + 1;
+  const size_t off_geo = 256;
+  const size_t off_sig = off_geo + align256(cx * (P + 1) * 4 * sizeof(double));
+  const size_t off_cnt = off_sig + align256(NZ * sizeof(double));
+  const size_t off_buf = off_cnt + align256(nedges * sizeof(unsigned));
+  const size_t end = off_buf + align256(nedges * NZ * sizeof(double));
+  if (end > kScratchBytes) {
+    set_last_error("mesh too large for pmg_apply_noalloc: its static scratch holds 4 MiB = 4194304 bytes, and the "
+                   "mesh needs 256 + a(32 cells_x (order + 1)) + a(8 NZ) + a(4 (cells_x + 1)) + "
+                   "a(8 (cells_x + 1) NZ) bytes, NZ = cells_z order + 1, a(n) = n rounded up to a multiple of 256 "
+                   "(use pmg_apply with a handle)");
     return PMG_ERR_INVALID;
   }
   Shape F{};
@@ -98,20 +126,8 @@ extern "C" pmg_status pmg_apply_noalloc(const pmg_mesh_desc* mesh, const double*
   F.Nx = m.cells_x;
   F.Nz = m.cells_z;
   F.periodic = m.periodic_x;
-  F.NX = m.cells_x * m.order + (m.periodic_x ? 0 : 1);
-  F.NZ = m.cells_z * m.order + 1;
-  // scratch layout: [geometry status][column factors][sigma][edge counters][edge buffers]
-  size_t nedges = (size_t)m.cells_x + 1;
-  size_t off_geo = 256;
-  size_t off_sig = off_geo + align256((size_t)m.cells_x * (m.order + 1) * 4 * sizeof(double));
-  size_t off_cnt = off_sig + align256((size_t)F.NZ * sizeof(double));
-  size_t off_buf = off_cnt + align256(nedges * sizeof(unsigned));
-  size_t end = off_buf + align256(nedges * (size_t)F.NZ * sizeof(double));
-  if (end > kScratchBytes) {
-    set_last_error("mesh too large for pmg_apply_noalloc: its static scratch holds 4 MiB, about "
-                   "(cells_x + 1) * (cells_z * order + 1) <= 500000 (use pmg_apply with a handle)");
-    return PMG_ERR_INVALID;
-  }
+  F.NX = (int)NX;
+  F.NZ = (int)NZ;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     set_last_error("cudaGetDevice failed");
@@ -149,5 +165,7 @@ extern "C" pmg_status pmg_apply_noalloc(const pmg_mesh_desc* mesh, const double*
   a.sc.edgebuf = base + off_buf;
   a.sc.edgecnt = reinterpret_cast<unsigned*>(base + off_cnt);
   if (!ck(curved_op<double>(a, st))) return PMG_ERR_CUDA;
+  k_poison_on_bad_geometry<<<152, 256, 0, st>>>(reinterpret_cast<const int*>(base), y_dev, NX * NZ);
+  if (!ck(cudaGetLastError())) return PMG_ERR_CUDA;
   return PMG_OK;
 }

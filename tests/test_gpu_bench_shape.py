@@ -1,0 +1,150 @@
+"""GPU parity at the depth of the timed tank: 32 element rows (193 node rows at P = 6,
+257 at P = 8), the column depth of the 512 x 32 benchmark tank, with the launch
+configurations the benchmark runs.
+
+Cases: the 32 x 32-cell, P = 6 slice of that tank that the CPU baseline times (same cell
+size, depth resolution and seed), and a 16 x 32-cell slice at P = 8.  Level-kernel
+families: the autotuner's free choice (as in the benchmark, also with fused or split
+level residuals chosen by time) and each FP32 level-operator family forced (slab CTAs,
+one thread per node, tiled CTAs), each after pmg_autotune has picked its CTA sizes.
+Compared element by element with the oracle: the outer operator, every level's operator
+and nu = 2 pre/post sweeps, the transfers, the V-cycle, and the mixed-precision and FP64
+solves against the direct solve.  Tolerances as in test_gpu_parity.py.
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_2411_14977_gb300.pmg as pmg
+import workloads as W
+from oracle import mg
+from oracle.sem import apply_masked, solve_direct
+from tests.gpu_helpers import Case, n, t
+
+pytestmark = pytest.mark.gpu
+
+SLICES = {
+    "slice32x32p6": lambda: W.tank(32, 32, 6, seed=W.BASE_SEED + 2),
+    "slice16x32p8": lambda: W.tank(16, 32, 8, seed=W.BASE_SEED + 3),
+}
+FAMILIES = {
+    "autotuned": dict(),
+    "autotuned_fuse": dict(fuse_residual=-1),
+    "slab": dict(flat_kernel=0),
+    "node": dict(flat_kernel=1),
+    "tiled": dict(flat_kernel=2),
+}
+_oracle = {}
+
+
+def oracle_of(name):
+    """Oracle mesh, fields, assembled operator and hierarchy of a slice (built once)."""
+    if name not in _oracle:
+        c = Case(SLICES[name]())
+        H = c.hierarchy()
+        A = c.m.assemble(c.eta)
+        bo = c.rhs_oracle()
+        pref = solve_direct(A, bo, c.F["pD"], c.m.dirichlet_mask())
+        _oracle[name] = (c, H, A, bo, pref)
+    return _oracle[name]
+
+
+def tuned(name, family, **extra):
+    c = Case(SLICES[name](), precision=pmg.PMG_MIXED_FP32, **FAMILIES[family], **extra)
+    c.S.autotune()
+    return c
+
+
+@pytest.mark.parametrize("family", list(FAMILIES))
+@pytest.mark.parametrize("name", list(SLICES))
+def test_bench_shape_kernels(name, family):
+    c0, H, A, _, _ = oracle_of(name)
+    c = tuned(name, family)
+    kinds = [c.S.level_kernels(l) for l in range(c.S.nlevels)]
+    if family == "node":
+        assert all(k["flat32"] < 0 for k in kinds)
+    if family == "slab":
+        assert all(0 < k["flat32"] < 10000 for k in kinds)
+    if family == "tiled":
+        assert all(k["flat32"] >= 10000 for k in kinds)
+    rng = np.random.default_rng(5)
+    dm = c0.m.dirichlet_mask()
+    # outer operator: FP64 pipe, double-float (the mixed default) and FP32
+    x = rng.standard_normal(c0.m.N)
+    ref = apply_masked(A, x, dm)
+    s = np.max(np.abs(A) @ np.abs(np.where(dm, 0, x)))
+    assert np.max(np.abs(n(c.S.apply(t(x))) - ref)) <= 1e-12 * s
+    assert np.max(np.abs(n(c.S.apply_f32(t(x, torch.float32))) - ref)) <= 2e-5 * s
+    for l, lev in enumerate(H.levels):
+        N = lev.mesh.N
+        xl = rng.standard_normal(N)
+        xl[lev.dmask] = 0.0
+        refl = lev.A @ xl[lev.free]
+        sl = np.max(np.abs(lev.A) @ np.abs(xl[lev.free]))
+        for dt, tol in ((torch.float64, 1e-12), (torch.float32, 2e-5)):
+            y = n(c.S.level_apply(l, t(xl, dt)))
+            assert np.max(np.abs(y[lev.free] - refl)) <= tol * sl, (l, dt)
+        if l == len(H.levels) - 1:
+            continue
+        b = rng.standard_normal(N)
+        b[lev.dmask] = 0.0
+        x0 = rng.standard_normal(N)
+        x0[lev.dmask] = 0.0
+        for post in (False, True):
+            refs = np.zeros(N)
+            refs[lev.free] = H.smooth(l, b[lev.free], x0[lev.free], post)
+            sc = max(1.0, np.max(np.abs(refs)))
+            for dt, tol in ((torch.float64, 1e-11), (torch.float32, 1e-4)):
+                xs = c.S.level_smooth(l, t(b, dt), t(x0, dt), post)
+                assert np.max(np.abs(n(xs) - refs)) <= tol * sc, (l, post, dt)
+        C = H.levels[l + 1]
+        rf = rng.standard_normal(N)
+        rf[lev.dmask] = 0.0
+        rc_ref = np.zeros(C.mesh.N)
+        rc_ref[C.free] = H.P[l].T @ rf[lev.free]
+        xc = rng.standard_normal(C.mesh.N)
+        xc[C.dmask] = 0.0
+        xf_ref = np.zeros(N)
+        xf_ref[lev.free] = H.P[l] @ xc[C.free]
+        for dt, tol in ((torch.float64, 1e-13), (torch.float32, 1e-5)):
+            rc = n(c.S.restrict(l, t(rf, dt), torch.zeros(C.mesh.N, dtype=dt, device="cuda")))
+            assert np.max(np.abs(rc - rc_ref)) <= tol * max(1.0, np.max(np.abs(rc_ref))), (l, dt)
+            xf = n(c.S.prolong(l, t(xc, dt), torch.zeros(N, dtype=dt, device="cuda")))
+            assert np.max(np.abs(xf - xf_ref)) <= tol * max(1.0, np.max(np.abs(xf_ref))), (l, dt)
+    F = H.levels[0]
+    r = rng.standard_normal(F.mesh.N)
+    r[F.dmask] = 0.0
+    zref = np.zeros(F.mesh.N)
+    zref[F.free] = H.vcycle(r[F.free])
+    assert np.max(np.abs(n(c.S.vcycle(t(r))) - zref)) <= 1e-10 * np.max(np.abs(zref))
+    assert np.max(np.abs(n(c.S.vcycle(t(r, torch.float32))) - zref)) <= 1e-4 * np.max(np.abs(zref))
+
+
+@pytest.mark.parametrize("family", list(FAMILIES))
+@pytest.mark.parametrize("name", list(SLICES))
+def test_bench_shape_mixed_solve(name, family):
+    """The benchmark's solve (mixed precision, tuned kernels) to 1e-12 against the direct
+    solve; its outer iterations within two of the oracle's FP64 flexible CG with the same
+    V-cycle (the FP32 rounding of the V-cycle may cost an iteration at 1e-12)."""
+    c0, H, A, bo, pref = oracle_of(name)
+    c = tuned(name, family, tol=1e-12)
+    p, info = c.S.solve(c.rhs_gpu(), t(c0.F["pD"]))
+    err = np.linalg.norm(n(p) - pref) / np.linalg.norm(pref)
+    assert err <= 1e-10 and info["rel_residual"] <= 1e-12, (err, info)
+    if family == "autotuned":
+        _, its, _, _ = mg.solve(c0.m, c0.eta, bo, c0.F["pD"], method="fcg", tol=1e-12, hier=H)
+        assert abs(info["iterations"] - its) <= 2, (info["iterations"], its)
+
+
+@pytest.mark.parametrize("name", list(SLICES))
+def test_bench_shape_fp64_solve(name):
+    """The plain FP64 p-MG-PCG (the comparison arm) at the timed tank's depth: the direct
+    solution, and the oracle's PCG iteration count within one."""
+    c0, H, A, bo, pref = oracle_of(name)
+    c = Case(SLICES[name](), tol=1e-12)
+    c.S.autotune()
+    p, info = c.S.solve(c.rhs_gpu(), t(c0.F["pD"]))
+    err = np.linalg.norm(n(p) - pref) / np.linalg.norm(pref)
+    assert err <= 1e-10 and info["rel_residual"] <= 1e-12, (err, info)
+    _, its, _, _ = mg.solve(c0.m, c0.eta, bo, c0.F["pD"], tol=1e-12, hier=H)
+    assert abs(info["iterations"] - its) <= 1, (info["iterations"], its)

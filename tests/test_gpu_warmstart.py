@@ -124,14 +124,16 @@ def wave_scales(amp, om, dt):
     return dict(s_eta=amp, s_deta=amp * om * dt, s_p=RHO * G * amp, s_dp=RHO * G * amp * om * dt)
 
 
-def test_warm_start_against_previous_pressure():
+def test_warm_start_no_regression_against_previous_pressure():
     """Train on recorded stage solves of a small periodic wave tank, then continue from the
-    same state with and without the network.  The network fits the pressure change far
-    better than the previous pressure does (L2 loss down by 100x); with the residual
-    fallback the solves never take more iterations than from the previous pressure, and
-    the state is the same to the solve tolerance.  Whether the guess also lowers the
-    iteration count is measured and printed, not assumed: the previous stage's pressure is
-    already a strong guess."""
+    same state with and without the network.  What this asserts: the network fits the
+    pressure change far better than the previous pressure does (L2 loss down by 100x),
+    and with the residual fallback the learned warm start causes NO REGRESSION -- the
+    solves never take more iterations than from the previous pressure, and the state is
+    the same to the solve tolerance.  It does not assert a gain: on these workloads the
+    fallback rejects the network's guesses (their residual is above the previous
+    pressure's), so the iteration counts are equal; the counts and the residual ratio are
+    printed."""
     from paper_2411_14977_gb300.stepper import WaveTank
     L, amp = 4.0, 0.04
     w = W.Workload("gain_32x2_p6", 32, 2, 6, 0.0, L, 1.0, True, W.BASE_SEED + 130, W.Surface(amp, 2 * np.pi / L),

@@ -490,14 +490,17 @@ def run_ours(args, ws, rank, local):
     bytes_sweep = 3.0 * N0 * 4  # r and x in, x out (FP32)
     achieved = bytes_sweep / (us_sweep * 1e-6) / 1e9
     p0 = S.level_info(0)[0]
-    key = f"k_fdm32<{p0},1,0> {args.workload}"
+    code0 = S.level_kernels(0)["fdm32"]
+    kname = f"k_fdm32z<{p0},1> (z-split, {code0 // 1000} element rows, {code0 % 1000} threads)" if code0 >= 1000 \
+        else f"k_fdm32<{p0},1,0> (slab, {code0} threads)"
+    key = f"{kname.split(' ')[0]} {args.workload}"
     rec, src = ncu_record(key, FDM32_SOURCES)
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
             # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture of
             # this kernel and workload, used only while its sources are unchanged
             "traffic": rec["dram_bytes_per_launch"] if rec else None,
             "traffic_source": src,
-            "kernel": f"k_fdm32<{p0},1> finest-level FP32 Schwarz sweep", "avg_launch_us": us_sweep,
+            "kernel": f"{kname} finest-level FP32 Schwarz sweep", "avg_launch_us": us_sweep,
             "algorithmic_bytes_per_launch": bytes_sweep,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured); burst peak, kernel timed alone",
             "note": "latency-bound: the working set is L2-resident; see kernel_time_shares and roofline_graded"}

@@ -114,6 +114,11 @@ typedef struct {
                      /* 0 off (FP64 pipe), -1 (default) on for the mixed precisions only     */
   int gmres_restart; /* PMG_GMRES cycle length m, 1..60 (default 30); the handle then holds */
                      /* 2m+1 extra FP64 vectors                                              */
+  int sweep_kernel;  /* FP32 Schwarz sweep (constant depth, equal orders): 0 slab CTAs (one  */
+                     /* element column each), 1 z-split CTAs (zc element rows of one element */
+                     /* column each, halo elements recomputed, slabs staged by TMA bulk      */
+                     /* copies), -1 (default) z-split until pmg_autotune picks by time, or a */
+                     /* z-split shape 1000 zc + threads (zc 1..64, threads 32..256, whole warps) */
 } pmg_opts;
 
 typedef struct {
@@ -127,7 +132,9 @@ typedef struct {
 typedef struct pmg_handle pmg_handle;
 
 /* Fill *opts with the defaults: FP64, PCG, FDM-ASM, flat preconditioner, overlap 1, nu 2,
- * omega 0.8, tol 1e-10, max_iter 500, inner_max 40, inner_tol 1e-5, paper level rule. */
+ * omega 0.8, tol 1e-10, max_iter 500, inner_max 40, inner_tol 1e-5, paper level rule,
+ * autotuned kernel families (flat_kernel, sweep_kernel -1), split level residuals,
+ * double-float outer operator for the mixed precisions, GMRES restart 30. */
 void pmg_default_opts(pmg_opts* opts);
 
 /* ---- host-only queries (no device work; they run without a GPU) ---------------------- */
@@ -179,7 +186,8 @@ pmg_status pmg_level_info(const pmg_handle* h, int level, int* order, int* nx, i
 /* Launch configuration of level l's FP32 kernels as set at creation or chosen by
  * pmg_autotune: flat32 = level operator (> 0 slab CTA size, < 0 node-parallel CTA size,
  * >= 10000 tiled shape 10000 + 100 EXT + ZT, see pmg_opts.flat_kernel), fdm32 = Schwarz
- * sweep CTA size, xfer = transfer CTA size.  Host-side read; any pointer may be NULL.
+ * sweep (< 1000: slab CTA size; >= 1000: z-split with fdm32 / 1000 element rows and
+ * fdm32 % 1000 threads per CTA), xfer = transfer CTA size.  Host-side read; any pointer may be NULL.
  * The paper has no counterpart.  PMG_ERR_INVALID for a bad handle or level. */
 pmg_status pmg_level_kernels(const pmg_handle* h, int level, int* flat32, int* fdm32, int* xfer);
 /* x* of every node column (NX values) and sigma of every node row (NZ values) of the
@@ -414,6 +422,15 @@ pmg_status pmg_batch_solve(pmg_batch* b, const double* const* b_dev, const doubl
  * and in the file named by PMG_TUNE_CACHE when set.  Synchronous; changes no results
  * (every candidate computes the same operator).  pmg_level_kernels reads the choices. */
 pmg_status pmg_autotune(pmg_handle* h);
+
+/* Bound of the handle's device-side waits (the z-split Schwarz sweep waits on an mbarrier
+ * for its TMA slab copies): a wait that has not completed after `cycles` SM clock cycles
+ * gives up, the CTA raises the handle's timeout flag, waits for its copies in flight and
+ * leaves its part of the iterate unchanged.  cycles < 0 restores the default (2^31, about
+ * one second); 0 gives up at once (how the tests exercise this path).  pmg_solve returns
+ * PMG_ERR_TIMEOUT when the flag was raised since the previous pmg_solve (of any call on
+ * the handle), and clears it.  The paper has no counterpart. */
+pmg_status pmg_set_wait_limit(pmg_handle* h, int64_t cycles);
 
 /* ---- allocation-free apply ------------------------------------------------------------ */
 /* y = A_FF x on free nodes, y = x on the surface row -- the operator of pmg_apply on the

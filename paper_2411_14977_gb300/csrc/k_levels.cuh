@@ -197,6 +197,13 @@ __global__ void __launch_bounds__(256) k_flat_tile(FlatParams<T> p, int EXT) {
   T* X = reinterpret_cast<T*>(smem_raw);  // (c, r) at c CP + r + c / P
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int gc0 = ex0 * P - P, gr0 = ez0 * PZ - PZ;
+  // output block of the tile: node columns ex0 P .. (+ the wall column), rows ez0 PZ ..
+  const int exn = min(ex0 + EXT, s.Nx) - ex0, ezn = min(ez0 + ZT, s.Nz) - ez0;
+  const int ncy = exn * P + ((!s.periodic && ex0 + exn == s.Nx) ? 1 : 0);
+  const int nry = ezn * PZ + ((ez0 + ezn == s.Nz) ? 1 : 0);
+  T* Bs = X + ncol * CP + (ncol - 1) / P + 1;  // [ncy][nrow] right-hand side (residual)
+  // every copy in flight at once (cp.async; zero-filled off the mesh and on the surface
+  // row, which is read as 0), then one wait
   for (int c = warp; c < ncol; c += nwarps) {
     const int gc = gc0 + c;
     const bool cok = col_valid(s, gc);
@@ -204,9 +211,17 @@ __global__ void __launch_bounds__(256) k_flat_tile(FlatParams<T> p, int EXT) {
     T* dst = X + c * CP + c / P;
     for (int r = lane; r < nrow; r += 32) {
       const int gr = gr0 + r;
-      dst[r] = (cok && gr >= 0 && gr < NZ - 1) ? src[gr] : T(0);  // surface row reads 0
+      const bool ok = cok && gr >= 0 && gr < NZ - 1;
+      cp_async_elem(&dst[r], src + (ok ? gr : 0), ok);
     }
   }
+  if (p.residual) {
+    for (int c = warp; c < ncy; c += nwarps) {
+      const T* src = p.b + (size_t)(ex0 * P + c) * NZ + (size_t)ez0 * PZ;
+      for (int r = lane; r < nry; r += 32) cp_async_elem(&Bs[c * nrow + r], src + r, true);
+    }
+  }
+  cp_async_wait_all();
   __syncthreads();
   const int exl = (int)threadIdx.x % EXT, ezl = (int)threadIdx.x / EXT;
   const int ex = ex0 + exl, ez = ez0 + ezl;
@@ -266,16 +281,14 @@ __global__ void __launch_bounds__(256) k_flat_tile(FlatParams<T> p, int EXT) {
     }
   }
   __syncthreads();
-  const int exn = min(ex0 + EXT, s.Nx) - ex0, ezn = min(ez0 + ZT, s.Nz) - ez0;
-  const int ncy = exn * P + ((!s.periodic && ex0 + exn == s.Nx) ? 1 : 0);
-  const int nry = ezn * PZ + ((ez0 + ezn == s.Nz) ? 1 : 0);
   for (int c = warp; c < ncy; c += nwarps) {
     const size_t gb = (size_t)(ex0 * P + c) * NZ + (size_t)ez0 * PZ;
     const T* Yc = X + c * CP + c / P;
+    const T* Bc = Bs + c * nrow;
     for (int r = lane; r < nry; r += 32) {
       const size_t g = gb + r;
       if (ez0 * PZ + r == NZ - 1) p.y[g] = p.residual ? T(0) : p.x[g];
-      else p.y[g] = p.residual ? p.b[g] - Yc[r] : Yc[r];
+      else p.y[g] = p.residual ? Bc[r] - Yc[r] : Yc[r];
     }
   }
 }
@@ -283,7 +296,9 @@ __global__ void __launch_bounds__(256) k_flat_tile(FlatParams<T> p, int EXT) {
 template <int P, typename T, int ZT, int PZ = P>
 static cudaError_t launch_flat_tile_z(const FlatParams<T>& prm, int EXT, cudaStream_t st) {
   const int ncol = (EXT + 1) * P + 1;
-  size_t sm = ((size_t)ncol * FlatTile<ZT, PZ>::CP + (ncol - 1) / P + 1) * sizeof(T);
+  // x tile, then the right-hand side of the output block (EXT P + 1 columns of nrow)
+  size_t sm = ((size_t)ncol * FlatTile<ZT, PZ>::CP + (ncol - 1) / P + 1 +
+               (size_t)(EXT * P + 1) * FlatTile<ZT, PZ>::nrow) * sizeof(T);
   auto k = k_flat_tile<P, T, ZT, PZ>;
   static std::atomic<unsigned long long> s_mask{0};
   cudaError_t e = ensure_max_smem(k, s_mask);

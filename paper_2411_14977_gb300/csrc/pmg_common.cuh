@@ -184,6 +184,46 @@ __device__ __forceinline__ void cp_async_elem(df64* smem_dst, const double* gsrc
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// ---- bulk copies (TMA) into shared memory, completed on an mbarrier -----------------
+// A 1D cp.async.bulk copies a contiguous run of global memory into shared memory without
+// per-element instructions; both addresses must be 16-byte aligned and the size a multiple
+// of 16 bytes.  The copies of a CTA signal one mbarrier (transaction count = bytes); the
+// waits are bounded in SM clock cycles so that a wait that cannot complete (a wrong byte
+// count) ends with an error flag instead of a hang.
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_load_1d(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for phase `parity` of bar for at most `cycles` SM clock cycles (0: give up at once).
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity, long long cycles) {
+  if (cycles <= 0) return false;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > cycles) return false;
+  return true;
+}
+constexpr long long kWaitCyclesDefault = 1ll << 31;  // about one second at 2 GHz
+
 // Calls f(c, iz) for every (c, iz) in [0, ncols) x [0, NZ), spread over the block with
 // consecutive threads on consecutive iz (coalesced on a z-fastest slab); the flattened
 // index advances by blockDim.x per step without an integer division per element.

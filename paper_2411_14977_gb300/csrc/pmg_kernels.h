@@ -150,7 +150,46 @@ struct FdmArgs {
   const void* mZ = nullptr;
   int xpercol = 0;  // generic sweep: Vx / invden hold one x-class per element column
   int overlap_z = -1;  // overlap along sigma (-1: overlap)
+  // FP32 sweep split along z (k_fdm32z): zc > 0 element rows per CTA, TMA-staged slabs
+  // (r and x 16-byte aligned, no fused residual; xout may differ from x); its bounded
+  // wait raises *timeout_flag
+  int zc = 0;
+  long long wait_cycles = 1ll << 31;
+  int* timeout_flag = nullptr;
 };
+
+// Shared-memory layout of the z-split FP32 sweep (k_fdm32.cu), in floats unless noted:
+// residual rows [NB][RP] (reused for the update U [NB][UP]), iterate rows [NB][XP],
+// x-transformed rows [NB][TP], z-transformed blocks [zc + 2][NB][NB], z eigenvectors and
+// inverse eigenvalue sums [8][NB][NB], row and column weights, then 2 NB + 1 ints and the
+// mbarrier.  RP and XP are multiples of 4 floats so that every staged column starts on a
+// 16-byte boundary, and leave room for the widening of a copy to 16-byte boundaries.
+struct Fdm32zLayout {
+  int TRmax, RP, XP, TP, UP, T3n;
+  size_t bar_off, bytes;
+};
+__host__ __device__ inline Fdm32zLayout fdm32z_layout(int P, int O, int zc) {
+  Fdm32zLayout L;
+  const int NB = P + 1 + 2 * O;
+  L.TRmax = (zc + 2) * P + 2 * O + 1;
+  L.RP = (L.TRmax + 6 + 3) & ~3;
+  L.XP = (zc * P + 6 + 3) & ~3;
+  L.TP = L.TRmax | 1;
+  L.UP = zc * P;
+  L.T3n = (zc + 2) * NB * NB;
+  const size_t floats = (size_t)NB * (L.RP + L.XP + L.TP) + L.T3n + 8 * NB * NB + L.TRmax + NB;
+  const size_t off = (floats + 2 * NB + 1) * 4;
+  L.bar_off = (off + 15) & ~(size_t)15;
+  L.bytes = L.bar_off + 16;
+  return L;
+}
+bool fdm32z_usable(const FdmArgs& a);
+// A forced z-split sweep shape, coded 1000 zc + threads (1 <= zc <= 64 element rows per
+// CTA, 32..256 threads in whole warps).
+inline bool sweep_code_ok(int code) {
+  const int zc = code / 1000, thr = code % 1000;
+  return zc >= 1 && zc <= 64 && thr >= 32 && thr <= 256 && thr % 32 == 0;
+}
 template <typename T> cudaError_t fdm_smooth(const FdmArgs& a, cudaStream_t st);
 // Dense additive Schwarz (k_dense.cu): block inverses of the level operator described by
 // the per-column factors geo [Nx][P+1][4] (A, B, C, E as the operator kernels) and sigma

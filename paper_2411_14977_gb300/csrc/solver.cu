@@ -235,6 +235,8 @@ struct LevelDev {
   void* wz[2]{};
   double* J = nullptr;  // transfer from level l+1 (coarse) to this level
   int thr_flat32 = 256, thr_fdm32 = 256, thr_xfer = 256;  // CTA sizes (autotuner)
+  // thr_fdm32 >= 1000: the z-split sweep with thr_fdm32 / 1000 element rows and
+  // thr_fdm32 % 1000 threads per CTA
   bool fuse_res = false;  // FP32 sweeps form their own residual (autotuner, when faster)
   bool fuse_restrict = false;  // the restriction forms the level residual (autotuner, when faster)
   void* b[2]{};
@@ -280,7 +282,8 @@ struct pmg_handle {
   void* geo[2]{};
   double* geo_div = nullptr;
   void* sigma[2]{};
-  int* status = nullptr;      // [0] inputs of the current solve, [1] geometry
+  int* status = nullptr;      // [0] inputs of the current solve, [1] geometry, [2] a bounded device wait gave up
+  long long wait_cycles = kWaitCyclesDefault;  // bound of the device-side waits
   CoarseArgs coarse{};
   // FP64 Krylov vectors
   double *x = nullptr, *r = nullptr, *p = nullptr, *w = nullptr, *z = nullptr, *rold = nullptr;
@@ -439,6 +442,8 @@ pmg_status build_level(pmg_handle* h, int l) {
   L.order_z = pz;
   L.aniso = pz != p;
   L.fuse_res = h->opts.fuse_residual == 1 && !L.aniso;
+  if (h->opts.sweep_kernel != 0) L.thr_fdm32 = 8128;  // z-split: 8 element rows, 128 threads
+  if (sweep_code_ok(h->opts.sweep_kernel)) L.thr_fdm32 = h->opts.sweep_kernel;
   if (h->opts.flat_kernel == 1) L.thr_flat32 = -128;
   if (h->opts.flat_kernel == 2) L.thr_flat32 = 11608;  // tiled: 16 element columns x 8 rows
   if (flat_tile_code_ok(h->opts.flat_kernel)) L.thr_flat32 = h->opts.flat_kernel;
@@ -821,6 +826,16 @@ pmg_status level_fdm(pmg_handle* h, int l, const void* r, void* x, int post, cud
     a.mZ = L.mZ[1];
     c.flops += NL * (4.0 * (L.s.P + 2) + 4.0);
   }
+  if (PI<T> && L.thr_fdm32 >= 1000) {
+    // the z-split sweep (no fused residual; 16-byte aligned vectors), else slab CTAs
+    FdmArgs z = a;
+    z.zc = L.thr_fdm32 / 1000;
+    z.threads = L.thr_fdm32 % 1000;
+    z.wait_cycles = h->wait_cycles;
+    z.timeout_flag = h->status + 2;
+    if (fdm32z_usable(z)) a = z;
+    else a.threads = 256;
+  }
   return launch(h, PI<T> ? PMG_K_SMOOTH32 : PMG_K_SMOOTH64, 1, st, c,
                 [&] { return PI<T> ? fdm_smooth32(a, st) : fdm_smooth<T>(a, st); });
 }
@@ -955,7 +970,7 @@ pmg_status curved(pmg_handle* h, int mode, const void* x, const void* b, void* y
 
 pmg_status read_scalars(pmg_handle* h, cudaStream_t st) {
   CK(cudaMemcpyAsync(h->scal_host, h->scal, SLOT_COUNT * sizeof(double), cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(h->status_host, h->status, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(h->status_host, h->status, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(h->iter_host, h->d_iter, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   return PMG_OK;
@@ -1671,7 +1686,8 @@ static pmg_status plan_levels(const pmg_mesh_desc& m, const pmg_opts& o, std::ve
     return fail(PMG_ERR_INVALID, "levels on the actual geometry need equal orders along x and sigma");
   if (o.overlap < 0 || o.overlap > MAXO || o.nu < 1 || !(o.omega > 0) || !(o.tol > 0) || o.max_iter < 1 ||
       o.inner_max < 1 || !(o.inner_tol > 0) || o.fuse_residual < -1 || o.fuse_residual > 1 || o.df64_outer < -1 ||
-      o.df64_outer > 1 || o.flat_kernel < -1 || (o.flat_kernel > 2 && !flat_tile_code_ok(o.flat_kernel)))
+      o.df64_outer > 1 || o.flat_kernel < -1 || (o.flat_kernel > 2 && !flat_tile_code_ok(o.flat_kernel)) ||
+      o.sweep_kernel < -1 || (o.sweep_kernel > 1 && !sweep_code_ok(o.sweep_kernel)))
     return fail(PMG_ERR_INVALID, "bad solver options");
   const int order_z = m.order_z == 0 ? m.order : m.order_z;
   if (order_z < 1 || order_z > MAXP) return fail(PMG_ERR_INVALID, "order_z must be 0 or in 1..10");
@@ -1734,6 +1750,7 @@ void pmg_default_opts(pmg_opts* o) {
   o->flat_kernel = -1;
   o->df64_outer = -1;
   o->gmres_restart = 30;
+  o->sweep_kernel = -1;
 }
 
 const char* pmg_last_error(void) { return g_err.c_str(); }
@@ -1852,7 +1869,7 @@ pmg_status pmg_create(const pmg_mesh_desc* mesh, const pmg_opts* opts, pmg_handl
   if (e != cudaSuccess) return bail(fail(PMG_ERR_OOM, "upload failed"));
   h->sigma[1] = upload<float>(h->sigrows, h->allocs, e);
   if (e != cudaSuccess) return bail(fail(PMG_ERR_OOM, "upload failed"));
-  ALLOC(h->status, int, 2);
+  ALLOC(h->status, int, 3);
   ALLOC(h->x, double, h->N);
   ALLOC(h->r, double, h->N);
   ALLOC(h->p, double, h->N);
@@ -1897,12 +1914,12 @@ pmg_status pmg_create(const pmg_mesh_desc* mesh, const pmg_opts* opts, pmg_handl
   if (cudaMemset(h->sc.edgebuf, 0, ebuf * sizeof(double)) != cudaSuccess ||
       cudaMemset(h->sc.edgecnt, 0, nedges * sizeof(unsigned)) != cudaSuccess ||
       cudaMemset(h->sc.redcnt, 0, sizeof(unsigned)) != cudaSuccess ||
-      cudaMemset(h->status, 0, 2 * sizeof(int)) != cudaSuccess ||
+      cudaMemset(h->status, 0, 3 * sizeof(int)) != cudaSuccess ||
       cudaMemset(h->scal, 0, SLOT_COUNT * sizeof(double)) != cudaSuccess ||
       cudaMemset(h->eta, 0, F.NX * sizeof(double)) != cudaSuccess)
     return bail(fail(PMG_ERR_CUDA, "memset failed"));
   if (cudaMallocHost(&h->scal_host, SLOT_COUNT * sizeof(double)) != cudaSuccess ||
-      cudaMallocHost(&h->status_host, 2 * sizeof(int)) != cudaSuccess ||
+      cudaMallocHost(&h->status_host, 3 * sizeof(int)) != cudaSuccess ||
       cudaMallocHost(&h->iter_host, 2 * sizeof(int)) != cudaSuccess ||
       cudaMemset(h->d_iter, 0, 2 * sizeof(int)) != cudaSuccess)
     return bail(fail(PMG_ERR_OOM, "pinned allocation failed"));
@@ -2241,6 +2258,10 @@ pmg_status pmg_solve(pmg_handle* h, const double* b, const double* pD, const dou
       fail(result, "solve did not reach the tolerance");
     }
   }
+  if (h->status_host[2]) {  // a bounded device wait gave up during this solve (or before it)
+    result = fail(PMG_ERR_TIMEOUT, "a bounded device-side wait gave up (pmg_set_wait_limit)");
+    CK(cudaMemsetAsync(h->status + 2, 0, sizeof(int), st));
+  }
   CK(cudaMemcpyAsync(p_out, h->x, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
   CK(cudaStreamSynchronize(st));
   loc.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -2399,6 +2420,15 @@ pmg_status pmg_axpy(pmg_handle* h, int64_t n, double a, const double* x, const d
   return launch(h, PMG_K_SETUP, 1, st, Cost{24.0 * n, 2.0 * n}, [&] { return axpy((size_t)n, a, x, y, out, st); });
 }
 
+pmg_status pmg_set_wait_limit(pmg_handle* h, int64_t cycles) {
+  CKS(check_handle(h));
+  h->wait_cycles = cycles < 0 ? kWaitCyclesDefault : (long long)cycles;
+  // captured loops hold the old bound in their kernel parameters: rebuild on next use
+  for (pmg_handle::Loop* lp : {&h->loop64, &h->loop32, &h->loop_gm, &h->loop_pdc})
+    if (lp->exec) { cudaGraphExecDestroy(lp->exec); lp->exec = nullptr; }
+  return PMG_OK;
+}
+
 pmg_status pmg_autotune(pmg_handle* h) {
   CKS(check_handle(h));
   DeviceGuard dg(h->device);
@@ -2441,10 +2471,23 @@ pmg_status pmg_autotune(pmg_handle* h) {
       }, &L.thr_xfer));
       continue;
     }
-    CKS(tune_one(h, TK_FDM32, L.order * 16 + L.overlap, L.s.NZ, [&](int thr, cudaStream_t cs) {
-      L.thr_fdm32 = thr;
-      return level_fdm<float>(h, l, t, x, 0, cs);
-    }, &L.thr_fdm32));
+    {
+      // slab CTAs of 64..512 threads, or z-split CTAs (codes 1000 zc + threads) of zc
+      // element rows; a forced family tunes (and caches) apart from the free choice
+      const std::vector<int> slab{64, 128, 192, 256, 320, 384, 512};
+      std::vector<int> zsplit;
+      for (int zc : {2, 4, 8, 16})
+        if (zc <= 2 * L.s.Nz)
+          for (int thr : {64, 96, 128, 192, 256}) zsplit.push_back(1000 * zc + thr);
+      const int sk = h->opts.sweep_kernel;
+      std::vector<int> cands = sk == 0 ? slab : sk >= 1000 ? std::vector<int>{sk} : zsplit;
+      if (sk == -1) cands.insert(cands.end(), slab.begin(), slab.end());
+      const int skey = sk >= 1000 ? 3 + sk : sk + 1;
+      CKS(tune_one(h, TK_FDM32, L.order * 16 + L.overlap + 1000 * skey, L.s.NZ, [&](int thr, cudaStream_t cs) {
+        L.thr_fdm32 = thr;
+        return level_fdm<float>(h, l, t, x, 0, cs);
+      }, &L.thr_fdm32, cands));
+    }
     {
       // residual launch + sweep, or one sweep that forms its residual (x -> t ping-pong);
       // the fused form must win by 10% (the two are within timing noise at config 2)

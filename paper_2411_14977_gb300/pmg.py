@@ -44,7 +44,7 @@ class Opts(ctypes.Structure):
                 ("omega", ctypes.c_double), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("inner_max", ctypes.c_int), ("inner_tol", ctypes.c_double), ("nlevels", ctypes.c_int),
                 ("level_orders", ctypes.c_int * 8), ("fuse_residual", ctypes.c_int), ("flat_kernel", ctypes.c_int),
-                ("df64_outer", ctypes.c_int), ("gmres_restart", ctypes.c_int)]
+                ("df64_outer", ctypes.c_int), ("gmres_restart", ctypes.c_int), ("sweep_kernel", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -100,6 +100,7 @@ _SIGNATURES = {
     "pmg_batch_handle": (_I, [_P, _I, ctypes.POINTER(_P)]),
     "pmg_batch_solve": (_I, [_P, _P, _P, _P, ctypes.POINTER(SolveInfo), _P]),
     "pmg_autotune": (_I, [_P]),
+    "pmg_set_wait_limit": (_I, [_P, ctypes.c_int64]),
     "pmg_profile_reset": (_I, [_P, _I]),
     "pmg_profile_read": (_I, [_P, _P, _P, _P, _P]),
     "pmg_ws_create": (_I, [_I, _I, _I, _I, _I, _I, ctypes.c_uint64, _D, _D, _D, _D, ctypes.POINTER(_P)]),
@@ -359,6 +360,11 @@ class Solver:
     def axpy(self, a, x, y, out):
         _check(load().pmg_axpy(self._h, x.numel(), float(a), _ptr(x), _ptr(y), _ptr(out), _stream()))
         return out
+
+    def set_wait_limit(self, cycles):
+        """pmg_set_wait_limit: bound (SM clock cycles) of the handle's device-side waits;
+        negative restores the default, 0 gives up at once."""
+        _check(load().pmg_set_wait_limit(self._h, int(cycles)))
 
     def autotune(self):
         """pmg_autotune: pick the CTA sizes of this handle's kernels by timing."""

@@ -33,6 +33,8 @@ FAMILIES = {
     "slab": dict(flat_kernel=0),
     "node": dict(flat_kernel=1),
     "tiled": dict(flat_kernel=2),
+    "slab_sweep": dict(sweep_kernel=0),
+    "zsplit_sweep": dict(sweep_kernel=1),
 }
 _oracle = {}
 
@@ -67,6 +69,10 @@ def test_bench_shape_kernels(name, family):
         assert all(0 < k["flat32"] < 10000 for k in kinds)
     if family == "tiled":
         assert all(k["flat32"] >= 10000 for k in kinds)
+    if family == "slab_sweep":
+        assert all(k["fdm32"] < 1000 for k in kinds[:-1])
+    if family == "zsplit_sweep":
+        assert all(k["fdm32"] >= 1000 for k in kinds[:-1])
     rng = np.random.default_rng(5)
     dm = c0.m.dirichlet_mask()
     # outer operator: FP64 pipe, double-float (the mixed default) and FP32
@@ -123,11 +129,23 @@ def test_bench_shape_kernels(name, family):
 @pytest.mark.parametrize("family", list(FAMILIES))
 @pytest.mark.parametrize("name", list(SLICES))
 def test_bench_shape_mixed_solve(name, family):
-    """The benchmark's solve (mixed precision, tuned kernels) to 1e-12 against the direct
-    solve; its outer iterations within two of the oracle's FP64 flexible CG with the same
-    V-cycle (the FP32 rounding of the V-cycle may cost an iteration at 1e-12)."""
+    """The benchmark's solve (mixed precision, tuned kernels) against the direct solve.
+
+    Its outer operator runs in double-float arithmetic (48-bit significands): on these
+    32-row tanks |A||x| is about 5e3 ||b||, so the true relative residual it can reach
+    stalls near 2e-11 (measured 1.8e-11, against 4.9e-13 for the FP64-pipe operator) while
+    the pressure already matches the direct solve to 1e-12.  So the double-float solve is
+    run to 5e-11 (below the timed 1e-10), and the same solve with the FP64-pipe outer
+    operator (df64_outer = 0: the mixed V-cycle unchanged) to 1e-12; both must be within
+    1e-10 of the direct solve in relative L2.  The outer iterations of the 1e-12 solve are
+    within two of the oracle's FP64 flexible CG with the same V-cycle (the FP32 rounding
+    of the V-cycle may cost an iteration)."""
     c0, H, A, bo, pref = oracle_of(name)
-    c = tuned(name, family, tol=1e-12)
+    c = tuned(name, family, tol=5e-11)
+    p, info = c.S.solve(c.rhs_gpu(), t(c0.F["pD"]))
+    err = np.linalg.norm(n(p) - pref) / np.linalg.norm(pref)
+    assert err <= 1e-10 and info["rel_residual"] <= 5e-11, (err, info)
+    c = tuned(name, family, tol=1e-12, df64_outer=0)
     p, info = c.S.solve(c.rhs_gpu(), t(c0.F["pD"]))
     err = np.linalg.norm(n(p) - pref) / np.linalg.norm(pref)
     assert err <= 1e-10 and info["rel_residual"] <= 1e-12, (err, info)

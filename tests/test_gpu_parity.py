@@ -136,12 +136,19 @@ def test_level_operators_and_transfers(name, flat):
             assert np.max(np.abs(xf - xf_ref)) <= tol * max(1.0, np.max(np.abs(xf_ref))), (l, dt)
 
 
-@pytest.mark.parametrize("fuse", [0, 1])
+SWEEPS = {"default": dict(), "fused": dict(fuse_residual=1), "slab": dict(sweep_kernel=0),
+          "z1x32": dict(sweep_kernel=1032), "z2x64": dict(sweep_kernel=2064), "z3x96": dict(sweep_kernel=3096),
+          "z16x256": dict(sweep_kernel=16256)}
+
+
+@pytest.mark.parametrize("sweep", list(SWEEPS))
 @pytest.mark.parametrize("name", list(CASES))
-def test_smoother(name, fuse):
-    """nu = 2 sweeps; FP32 with the residual launched apart (fuse 0) or formed inside the
-    sweep kernel with the iterate ping-ponged (fuse 1)."""
-    c = case(name, fuse_residual=fuse)
+def test_smoother(name, sweep):
+    """nu = 2 sweeps; FP32 with the residual launched apart or formed inside the sweep kernel
+    with the iterate ping-ponged (fused); the split sweeps on slab CTAs (one element column
+    each) or on z-split CTAs of 1, 2, 3 or 16 element rows (the default: 8; ragged last
+    chunks, chunks deeper than the mesh, one warp up to eight warps)."""
+    c = case(name, **SWEEPS[sweep])
     H = c.hierarchy()
     rng = np.random.default_rng(3)
     for l, lev in enumerate(H.levels[:-1]):
@@ -159,12 +166,12 @@ def test_smoother(name, fuse):
                 assert np.max(np.abs(n(x) - ref)) <= tol * sc, (l, post, dt)
 
 
-@pytest.mark.parametrize("fuse", [0, 1])
+@pytest.mark.parametrize("sweep", ["default", "fused", "slab", "z3x96"])
 @pytest.mark.parametrize("name", list(CASES))
-def test_coarse_solve_and_vcycle(name, fuse):
+def test_coarse_solve_and_vcycle(name, sweep):
     """Coarse solve, and the V-cycle in FP64 and FP32 with the level residuals launched
-    apart (fuse 0) or formed inside the sweeps and restrictions (fuse 1)."""
-    c = case(name, fuse_residual=fuse)
+    apart or formed inside the sweeps and restrictions (fused), on slab or z-split sweeps."""
+    c = case(name, **SWEEPS[sweep])
     H = c.hierarchy()
     rng = np.random.default_rng(4)
     C = H.levels[-1]
@@ -197,6 +204,8 @@ SOLVE_CASES = ["tank12x3p6", "cfg1", "periodic8x3p5", "tank6x2p8", "tank5x1p4_nz
                                      dict(precision=pmg.PMG_MIXED_FP32, fuse_residual=1),
                                      dict(precision=pmg.PMG_MIXED_BF16, outer=pmg.PMG_IR),
                                      dict(precision=pmg.PMG_MIXED_FP32, flat_kernel=1),
+                                     dict(precision=pmg.PMG_MIXED_FP32, sweep_kernel=0),
+                                     dict(precision=pmg.PMG_MIXED_FP32, sweep_kernel=2064),
                                      dict(outer=pmg.PMG_GMRES), dict(outer=pmg.PMG_GMRES, gmres_restart=3),
                                      dict(precision=pmg.PMG_MIXED_FP32, outer=pmg.PMG_GMRES)])
 def test_solve_matches_direct(name, variant):

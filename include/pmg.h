@@ -390,12 +390,19 @@ pmg_status pmg_ws_save(pmg_ws* ws, const char* path);
 pmg_status pmg_ws_load(pmg_ws* ws, const char* path);
 
 /* ---- batches of independent problems --------------------------------------------------- */
-/* n independent tanks (each its own mesh, order and workspace), solved together: every
- * problem runs its own device-side Krylov loop (a CUDA graph with a while node) on its
- * own stream forked from the caller's stream, so the problems' kernels share the GPU
- * concurrently; the host synchronises three times per batch solve, not per iteration.
- * opts apply to every problem; pmg_batch_create runs pmg_autotune on every problem.  Not in
- * the paper (it solves one tank at a time). */
+/* n independent tanks (each its own mesh, order and workspace), solved together.  Not in the
+ * paper (it solves one tank at a time).  With the mixed precision (PMG_MIXED_FP32, outer
+ * PMG_PCG or PMG_FCG, the default fast-diagonalisation smoother on flat levels, constant
+ * depth, equal orders, double-float outer operator) and n <= 256, a batch solve is ONE CUDA
+ * graph: every stage of the flexible-CG iteration -- each Schwarz sweep, level residual
+ * and transfer of the V-cycle (levels aligned by their distance from the order-1 level),
+ * the coarse solves, the outer operator, the Krylov vector updates -- is one launch whose
+ * CTAs are the work items (element columns or nodes) of all problems, taken from a device
+ * table; per-problem scalars, iteration counts, convergence flags and restarts on residual
+ * drift live on the device, and a device-side while node runs until every problem is done.
+ * Other options run each problem's own device-side loop on its own stream, concurrently.
+ * opts apply to every problem; pmg_batch_create runs pmg_autotune on every problem (used by
+ * the per-problem path). */
 typedef struct pmg_batch pmg_batch;
 pmg_status pmg_batch_create(int n, const pmg_mesh_desc* meshes, const pmg_opts* opts, pmg_batch** out);
 pmg_status pmg_batch_destroy(pmg_batch* b);
@@ -407,6 +414,16 @@ pmg_status pmg_batch_handle(pmg_batch* b, int i, pmg_handle** h);
  * problem's own status is in its info).  Synchronises the caller's stream. */
 pmg_status pmg_batch_solve(pmg_batch* b, const double* const* b_dev, const double* const* p_dirichlet_dev,
                            double* const* p_out_dev, pmg_solve_info* infos, void* stream);
+/* How the batch solves: *batched = 1 for the single graph of batched launches, 0 for the
+ * concurrent per-problem loops; *launches = kernel launches per iteration of the batched
+ * graph (0 until its first solve has built it).  Any pointer may be NULL.  Host-side read;
+ * no counterpart in the paper. */
+pmg_status pmg_batch_info(const pmg_batch* b, int* batched, int* launches);
+/* Profiling aid of the batched path: eager != 0 runs the same launches with the iteration
+ * loop driven by the host (one host synchronisation per iteration) instead of the graph's
+ * device-side while node, so that a kernel profiler sees every launch.  The results are
+ * the same.  No counterpart in the paper. */
+pmg_status pmg_batch_set_eager(pmg_batch* b, int eager);
 
 /* ---- autotuner ------------------------------------------------------------------------- */
 /* Times the candidate launch configurations on every level of h (CUDA-event timing of

@@ -16,6 +16,9 @@
 // two elements that share a node row are summed before the x-contraction, the sigma
 // contraction of each node row is done by the thread that owns the row, and the two
 // element-edge node columns are summed across CTAs by the edge exchange.
+#include <algorithm>
+#include <new>
+
 #include "pmg_common.cuh"
 #include "pmg_kernels.h"
 
@@ -254,6 +257,84 @@ cudaError_t rhs_source(const Shape& s, const double* eta, double h, const double
   int bs = 256;
   k_rhs_source<<<(unsigned)((N + bs - 1) / bs), bs, 0, st>>>(s, eta, h, hcol, dx, dsig, mX, mZ, mb, f, gb, gl, gr, b);
   return cudaGetLastError();
+}
+
+// ---- batched double-float outer operator (mode 2: y = A x with <x, y>; mode 1: residual)
+template <int MODE>
+static cudaError_t curved_batch_table_m(const CurvedArgs* a, const int* prob, int n, const int* active, void** table,
+                                        int* nctas, size_t* smem) {
+  using Tab = CurvedBatch<df64, MODE>;
+  Tab* h = new (std::nothrow) Tab();
+  if (!h) return cudaErrorMemoryAllocation;
+  h->m.nrange = n;
+  h->m.active = active;
+  h->m.start[0] = 0;
+  size_t sm = 0;
+  for (int i = 0; i < n; ++i) {
+    if (a[i].s.pz() != a[i].s.P || a[i].mix || a[i].bathy || a[i].tc || a[i].s.P < 2 || a[i].s.P > MAXP ||
+        a[i].s.P != a[0].s.P) {
+      delete h;
+      return cudaErrorInvalidValue;
+    }
+    CurvedParams<df64>& p = h->prm[i];
+    p.s = a[i].s;
+    p.x = (const double*)a[i].x;
+    p.x2 = nullptr;
+    p.b = (const double*)a[i].b;
+    p.y = (double*)a[i].y;
+    p.geo = (const double*)a[i].geo;
+    p.sigma = (const double*)a[i].sigma;
+    p.scale = df64(1.f);
+    p.mask_input = a[i].mask_input;
+    p.result = a[i].result;
+    p.sc = a[i].sc;
+    h->m.prob[i] = prob[i];
+    h->m.start[i + 1] = h->m.start[i] + a[i].s.Nx;
+    sm = std::max(sm, curved_smem<df64>(a[i].s.P, a[i].s.NZ, a[i].s.Nz));
+  }
+  *nctas = h->m.start[n];
+  *smem = sm;
+  BatchMap* maps[1] = {&h->m};
+  cudaError_t e = batch_upload(h, maps, 1, table);
+  delete h;
+  return e;
+}
+
+cudaError_t curved_batch_table(int mode, const CurvedArgs* a, const int* prob, int n, const int* active, void** table,
+                               int* nctas, size_t* smem) {
+  if (n < 1 || n > kMaxBatch) return cudaErrorInvalidValue;
+  if (mode == MODE_DOT) return curved_batch_table_m<MODE_DOT>(a, prob, n, active, table, nctas, smem);
+  if (mode == MODE_RESIDUAL) return curved_batch_table_m<MODE_RESIDUAL>(a, prob, n, active, table, nctas, smem);
+  return cudaErrorInvalidValue;
+}
+
+template <int MODE, int P>
+static cudaError_t launch_curved_batch(const void* table, int nctas, int threads, size_t smem, cudaStream_t st) {
+  auto k = k_curved_batch<df64, MODE, P>;
+  static std::atomic<unsigned long long> s_mask{0};
+  cudaError_t e = ensure_max_smem(k, s_mask);
+  if (e != cudaSuccess) return e;
+  int grid = 0;
+  e = batch_grid(k, threads, smem, nctas, &grid);
+  if (e != cudaSuccess) return e;
+  k<<<grid, threads, smem, st>>>(static_cast<const CurvedBatch<df64, MODE>*>(table));
+  return cudaGetLastError();
+}
+template <int MODE>
+static cudaError_t curved_batch_launch_m(const void* table, int P, int nctas, int threads, size_t smem,
+                                         cudaStream_t st) {
+  switch (P) {
+#define PMG_CASE(PP) case PP: return launch_curved_batch<MODE, PP>(table, nctas, threads, smem, st);
+    PMG_CASE(2) PMG_CASE(3) PMG_CASE(4) PMG_CASE(5) PMG_CASE(6) PMG_CASE(7) PMG_CASE(8) PMG_CASE(9) PMG_CASE(10)
+#undef PMG_CASE
+  }
+  return cudaErrorInvalidValue;
+}
+cudaError_t curved_batch_launch(int mode, const void* table, int P, int nctas, int threads, size_t smem,
+                                cudaStream_t st) {
+  if (mode == MODE_DOT) return curved_batch_launch_m<MODE_DOT>(table, P, nctas, threads, smem, st);
+  if (mode == MODE_RESIDUAL) return curved_batch_launch_m<MODE_RESIDUAL>(table, P, nctas, threads, smem, st);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace pmg

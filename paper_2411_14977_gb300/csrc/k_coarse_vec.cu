@@ -10,15 +10,17 @@
 // Vector kernels: dot products and the CG/FCG updates, with FP64 accumulation and the
 // deterministic grid reduction of pmg_common.cuh.  Step scalars (alpha, beta, norms) live
 // in device memory; no host round trip is needed inside an iteration.
+#include <algorithm>
+#include <new>
+
 #include "pmg_common.cuh"
 #include "pmg_kernels.h"
 
 namespace pmg {
 
 template <typename T>
-__global__ void k_coarse_fwd(int NX1, int NZ1, const T* b, const double* V, double* rhat) {
+__device__ __forceinline__ void coarse_fwd_body(int NX1, int NZ1, const T* b, const double* V, double* rhat, int t) {
   int Nz = NZ1 - 1;
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= NX1 * Nz) return;
   int ix = t / Nz, k = t % Nz;
   const T* col = b + (size_t)ix * NZ1;
@@ -26,13 +28,15 @@ __global__ void k_coarse_fwd(int NX1, int NZ1, const T* b, const double* V, doub
   for (int iz = 0; iz < Nz; ++iz) acc += V[iz * Nz + k] * (double)col[iz];
   rhat[(size_t)k * NX1 + ix] = acc;
 }
+template <typename T>
+__global__ void k_coarse_fwd(int NX1, int NZ1, const T* b, const double* V, double* rhat) {
+  coarse_fwd_body<T>(NX1, NZ1, b, V, rhat, blockIdx.x * blockDim.x + threadIdx.x);
+}
 
 // PCR: d'_i = d_i - k1_i d_{i-s} - k2_i d_{i+s} per step; x_i = d_i * inv_i.  The two
 // ping-pong vectors live in shared memory, or (long tanks) in the global scratch gbuf.
-__global__ void k_coarse_pcr(int n, int nsteps, int periodic, const double* coef, const double* inv,
-                             double* rhat, double* gbuf) {
-  extern __shared__ double sbuf[];
-  int k = blockIdx.x;
+__device__ __forceinline__ void coarse_pcr_body(int n, int nsteps, int periodic, const double* coef, const double* inv,
+                                                double* rhat, double* gbuf, int k, double* sbuf) {
   double* d0 = gbuf ? gbuf + (size_t)k * 2 * n : sbuf;
   double* d1 = d0 + n;
   const double* ck = coef + (size_t)k * nsteps * n * 2;
@@ -60,17 +64,26 @@ __global__ void k_coarse_pcr(int n, int nsteps, int periodic, const double* coef
   }
   for (int i = threadIdx.x; i < n; i += blockDim.x) rk[i] = d0[i] * inv[(size_t)k * n + i];
 }
+__global__ void k_coarse_pcr(int n, int nsteps, int periodic, const double* coef, const double* inv,
+                             double* rhat, double* gbuf) {
+  extern __shared__ double sbuf[];
+  coarse_pcr_body(n, nsteps, periodic, coef, inv, rhat, gbuf, blockIdx.x, sbuf);
+}
 
 template <typename T>
-__global__ void k_coarse_bwd(int NX1, int NZ1, const double* V, const double* uhat, T* x) {
+__device__ __forceinline__ void coarse_bwd_body(int NX1, int NZ1, const double* V, const double* uhat, T* x,
+                                                size_t t) {
   int Nz = NZ1 - 1;
-  size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (t >= (size_t)NX1 * NZ1) return;
   int ix = (int)(t / NZ1), iz = (int)(t % NZ1);
   double acc = 0.0;
   if (iz < Nz)
     for (int k = 0; k < Nz; ++k) acc += V[iz * Nz + k] * uhat[(size_t)k * NX1 + ix];
   x[t] = (T)acc;
+}
+template <typename T>
+__global__ void k_coarse_bwd(int NX1, int NZ1, const double* V, const double* uhat, T* x) {
+  coarse_bwd_body<T>(NX1, NZ1, V, uhat, x, blockIdx.x * (size_t)blockDim.x + threadIdx.x);
 }
 
 template <typename T>
@@ -549,6 +562,326 @@ cudaError_t gmres_givens(cudaGraphConditionalHandle hnd, const double* c1, const
 }
 cudaError_t gmres_backsub(const double* H, const double* g, double* y, int m, const int* jdev, cudaStream_t st) {
   k_gm_backsub<<<1, 1, 0, st>>>(H, g, y, m, jdev);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------
+// batched launches: the coarse solves and Krylov vector kernels of a batch of problems
+// ------------------------------------------------------------------------------------
+struct CoarseBatch {
+  BatchMap m[3];  // fwd, pcr, bwd
+  CoarseArgs a[kMaxBatch];
+  const float* b[kMaxBatch];
+  float* x[kMaxBatch];
+  int gbuf[kMaxBatch];  // 1: the PCR ping-pong runs in the problem's global scratch
+};
+__global__ void __launch_bounds__(256) k_coarse_fwd_batch(const CoarseBatch* tab) {
+  batch_items(tab->m[0], [&](int r, int k) {
+    const CoarseArgs& a = tab->a[r];
+    coarse_fwd_body<float>(a.NX1, a.NZ1, tab->b[r], a.V, a.work, k * blockDim.x + threadIdx.x);
+  });
+}
+__global__ void __launch_bounds__(1024) k_coarse_pcr_batch(const CoarseBatch* tab) {
+  extern __shared__ double sbuf[];
+  batch_items(tab->m[1], [&](int r, int k) {
+    const CoarseArgs& a = tab->a[r];
+    coarse_pcr_body(a.NX1, a.nsteps, a.periodic, a.coef, a.inv, a.work, tab->gbuf[r] ? a.pcr_buf : nullptr, k,
+                    sbuf);
+    __syncthreads();
+  });
+}
+__global__ void __launch_bounds__(256) k_coarse_bwd_batch(const CoarseBatch* tab) {
+  batch_items(tab->m[2], [&](int r, int k) {
+    const CoarseArgs& a = tab->a[r];
+    coarse_bwd_body<float>(a.NX1, a.NZ1, a.V, a.work, tab->x[r], (size_t)k * blockDim.x + threadIdx.x);
+  });
+}
+
+cudaError_t coarse_batch_table(const CoarseArgs* a, const float* const* b, float* const* x, const int* prob, int n,
+                               const int* active, void** table, int nctas[3], size_t* smem) {
+  if (n < 1 || n > kMaxBatch) return cudaErrorInvalidValue;
+  CoarseBatch* h = new (std::nothrow) CoarseBatch();
+  if (!h) return cudaErrorMemoryAllocation;
+  size_t sm = 0;
+  for (int k = 0; k < 3; ++k) {
+    h->m[k].nrange = n;
+    h->m[k].active = active;
+    h->m[k].start[0] = 0;
+  }
+  for (int i = 0; i < n; ++i) {
+    h->a[i] = a[i];
+    h->b[i] = b[i];
+    h->x[i] = x[i];
+    const int Nz = a[i].NZ1 - 1;
+    const size_t pcr = 2 * (size_t)a[i].NX1 * sizeof(double);
+    h->gbuf[i] = pcr > 200 * 1024 ? 1 : 0;
+    if (!h->gbuf[i]) sm = std::max(sm, pcr);
+    for (int k = 0; k < 3; ++k) h->m[k].prob[i] = prob[i];
+    h->m[0].start[i + 1] = h->m[0].start[i] + (a[i].NX1 * Nz + 255) / 256;
+    h->m[1].start[i + 1] = h->m[1].start[i] + Nz;
+    h->m[2].start[i + 1] = h->m[2].start[i] + (int)(((size_t)a[i].NX1 * a[i].NZ1 + 255) / 256);
+  }
+  for (int k = 0; k < 3; ++k) nctas[k] = h->m[k].start[n];
+  *smem = sm;
+  BatchMap* maps[3] = {&h->m[0], &h->m[1], &h->m[2]};
+  cudaError_t e = batch_upload(h, maps, 3, table);
+  delete h;
+  if (e != cudaSuccess) return e;
+  static std::atomic<unsigned long long> s_mask{0};
+  return ensure_max_smem(k_coarse_pcr_batch, s_mask);
+}
+cudaError_t coarse_batch_launch(const void* table, const int nctas[3], size_t smem, cudaStream_t st) {
+  const CoarseBatch* t = static_cast<const CoarseBatch*>(table);
+  int g0 = 0, g1 = 0, g2 = 0;
+  cudaError_t e = batch_grid(k_coarse_fwd_batch, 256, 0, nctas[0], &g0);
+  if (e == cudaSuccess) e = batch_grid(k_coarse_pcr_batch, 1024, smem, nctas[1], &g1);
+  if (e == cudaSuccess) e = batch_grid(k_coarse_bwd_batch, 256, 0, nctas[2], &g2);
+  if (e != cudaSuccess) return e;
+  k_coarse_fwd_batch<<<g0, 256, 0, st>>>(t);
+  k_coarse_pcr_batch<<<g1, 1024, smem, st>>>(t);
+  k_coarse_bwd_batch<<<g2, 256, 0, st>>>(t);
+  return cudaGetLastError();
+}
+
+struct VecBatch {
+  BatchMap m[VB_COUNT];
+  VecProb prm[kMaxBatch];
+  int nb[kMaxBatch];  // CTAs of each problem in the reduction kernels
+  BatchState st;
+  const BatchIO* io;
+  int n;
+};
+constexpr int VB_THREADS = 512;
+
+// The work of item bx (one CTA's share) of range r of a vector kernel.
+template <int WHICH>
+__device__ __forceinline__ void vec_item(const VecBatch* tab, int r, int bx, double* red, int* s_flag) {
+  const BatchMap& m = tab->m[WHICH];
+  const int prob = m.prob[r];
+  const VecProb& q = tab->prm[r];
+  const size_t n = q.n;
+  if constexpr (WHICH == VB_INIT || WHICH == VB_COPY_OUT) {
+    const size_t g = (size_t)bx * VB_THREADS + threadIdx.x;
+    if (g >= n) return;
+    const BatchIO io = tab->io[prob];
+    if constexpr (WHICH == VB_INIT) {
+      // the load vector into the problem's copy; x = 0 with p_D on the surface row
+      const double bv = io.b[g];
+      if (!isfinite(bv)) atomicExch(q.status, 1);
+      q.bcopy[g] = bv;
+      const bool top = (int)(g % q.NZ) == q.NZ - 1;
+      const double v = top ? io.pD[g] : 0.0;
+      if (!isfinite(v)) atomicExch(q.status, 1);
+      q.x[g] = v;
+    } else {
+      io.out[g] = q.x[g];
+    }
+  } else {
+    const int nb = tab->nb[r];
+    const size_t stride = (size_t)nb * VB_THREADS;
+    const size_t i0 = (size_t)bx * VB_THREADS + threadIdx.x;
+    double* s = q.s;
+    if constexpr (WHICH == VB_CAST_FIRST) {
+      for (size_t i = i0; i < n; i += stride) q.r32[i] = (float)q.r[i];
+    } else if constexpr (WHICH == VB_RZ) {
+      // RZ = <r, z>, ZRO = <r_old, z> (flexible CG; none at the first step), RZ -> RZOLD
+      const bool first = tab->st.first[prob] != 0;
+      Acc<double> c1, c2;
+      for (size_t i = i0; i < n; i += stride) {
+        const double zi = (double)q.z32[i];
+        c1.fma(q.r[i], zi);
+        if (!first) c2.fma(q.rold[i], zi);
+      }
+      const double a1 = block_sum(c1.value(), red);
+      const double a2 = block_sum(c2.value(), red);
+      if (!local_reduce_last(q.sc, bx, nb, a1, a2, s_flag)) return;
+      double v1 = 0.0, v2 = 0.0;
+      for (int k = threadIdx.x; k < nb; k += VB_THREADS) {
+        v1 += ((volatile double*)q.sc.partials)[2 * k];
+        v2 += ((volatile double*)q.sc.partials)[2 * k + 1];
+      }
+      v1 = block_sum(v1, red);
+      v2 = block_sum(v2, red);
+      if (threadIdx.x == 0) {
+        s[GROUP_OUTER + SLOT_RZOLD] = s[GROUP_OUTER + SLOT_RZ];
+        s[GROUP_OUTER + SLOT_RZ] = v1;
+        s[GROUP_OUTER + SLOT_ZRO] = v2;
+        *q.sc.redcnt = 0u;
+      }
+    } else if constexpr (WHICH == VB_P_UPDATE) {
+      // p = z (first step) or z + beta p, beta = (RZ - ZRO) / RZOLD (flexible CG)
+      const bool first = tab->st.first[prob] != 0;
+      const double beta = first ? 0.0
+                                : (s[GROUP_OUTER + SLOT_RZ] - s[GROUP_OUTER + SLOT_ZRO]) / s[GROUP_OUTER + SLOT_RZOLD];
+      for (size_t i = i0; i < n; i += stride) q.p[i] = first ? (double)q.z32[i] : (double)q.z32[i] + beta * q.p[i];
+    } else if constexpr (WHICH == VB_CG_UPDATE) {
+      // alpha = RZ / PAP; r_old = r; x += alpha p; r -= alpha w; r32 = (float) r; RR = ||r||^2
+      const double a = s[GROUP_OUTER + SLOT_RZ] / s[GROUP_OUTER + SLOT_PAP];
+      Acc<double> ac;
+      for (size_t i = i0; i < n; i += stride) {
+        double ri = q.r[i];
+        q.rold[i] = ri;
+        q.x[i] += a * q.p[i];
+        ri -= a * q.w[i];
+        q.r[i] = ri;
+        q.r32[i] = (float)ri;
+        ac.fma(ri, ri);
+      }
+      const double a1 = block_sum(ac.value(), red);
+      if (!local_reduce_last(q.sc, bx, nb, a1, 0.0, s_flag)) return;
+      double v = 0.0;
+      for (int k = threadIdx.x; k < nb; k += VB_THREADS) v += ((volatile double*)q.sc.partials)[2 * k];
+      v = block_sum(v, red);
+      if (threadIdx.x == 0) {
+        s[GROUP_OUTER + SLOT_RR] = v;
+        *q.sc.redcnt = 0u;
+      }
+    }
+  }
+}
+
+template <int WHICH>
+__global__ void __launch_bounds__(VB_THREADS) k_vec_batch(const VecBatch* tab) {
+  __shared__ double red[34];
+  __shared__ int s_flag;
+  batch_items(tab->m[WHICH], [&](int r, int bx) {
+    vec_item<WHICH>(tab, r, bx, red, &s_flag);
+    __syncthreads();
+  });
+}
+
+cudaError_t vec_batch_table(const VecProb* a, int n, BatchState st, const BatchIO* io, void** table,
+                            int nctas[VB_COUNT], const int* prob) {
+  if (n < 1 || n > kMaxBatch) return cudaErrorInvalidValue;
+  VecBatch* h = new (std::nothrow) VecBatch();
+  if (!h) return cudaErrorMemoryAllocation;
+  h->st = st;
+  h->io = io;
+  h->n = n;
+  const int* act[VB_COUNT] = {nullptr, st.first, st.active, st.active, st.active, nullptr};
+  for (int k = 0; k < VB_COUNT; ++k) {
+    h->m[k].nrange = n;
+    h->m[k].active = act[k];
+    h->m[k].start[0] = 0;
+  }
+  for (int i = 0; i < n; ++i) {
+    h->prm[i] = a[i];
+    const size_t nodes = (a[i].n + VB_THREADS - 1) / VB_THREADS;
+    h->nb[i] = (int)std::min<size_t>(std::max<size_t>((a[i].n + 4 * VB_THREADS - 1) / (4 * VB_THREADS), 1), 64);
+    for (int k = 0; k < VB_COUNT; ++k) {
+      h->m[k].prob[i] = prob ? prob[i] : i;
+      const int c = (k == VB_INIT || k == VB_COPY_OUT) ? (int)nodes : h->nb[i];
+      h->m[k].start[i + 1] = h->m[k].start[i] + c;
+    }
+  }
+  for (int k = 0; k < VB_COUNT; ++k) nctas[k] = h->m[k].start[n];
+  BatchMap* maps[VB_COUNT];
+  for (int k = 0; k < VB_COUNT; ++k) maps[k] = &h->m[k];
+  cudaError_t e = batch_upload(h, maps, VB_COUNT, table);
+  delete h;
+  return e;
+}
+template <int WHICH>
+static cudaError_t launch_vec_batch(const VecBatch* t, int items, cudaStream_t st) {
+  int grid = 0;
+  cudaError_t e = batch_grid(k_vec_batch<WHICH>, VB_THREADS, 0, items, &grid);
+  if (e != cudaSuccess) return e;
+  k_vec_batch<WHICH><<<grid, VB_THREADS, 0, st>>>(t);
+  return cudaGetLastError();
+}
+cudaError_t vec_batch_launch(int which, const void* table, const int nctas[VB_COUNT], cudaStream_t st) {
+  const VecBatch* t = static_cast<const VecBatch*>(table);
+  switch (which) {
+    case VB_INIT: return launch_vec_batch<VB_INIT>(t, nctas[which], st);
+    case VB_CAST_FIRST: return launch_vec_batch<VB_CAST_FIRST>(t, nctas[which], st);
+    case VB_RZ: return launch_vec_batch<VB_RZ>(t, nctas[which], st);
+    case VB_P_UPDATE: return launch_vec_batch<VB_P_UPDATE>(t, nctas[which], st);
+    case VB_CG_UPDATE: return launch_vec_batch<VB_CG_UPDATE>(t, nctas[which], st);
+    case VB_COPY_OUT: return launch_vec_batch<VB_COPY_OUT>(t, nctas[which], st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// ---- per-problem state machine of the batched flexible CG (one thread per problem)
+__global__ void k_batch_state_init(const VecBatch* tab) {
+  const int i = threadIdx.x;
+  if (i >= tab->n) return;
+  const VecProb& q = tab->prm[i];
+  const BatchState& st = tab->st;
+  double* s = q.s;
+  const double bb = s[SLOT_BB];  // the lifted residual of x = (0, p_D): ||b~||^2
+  s[SLOT_RR64] = bb;
+  st.bb[i] = bb;
+  st.rr64[i] = bb;
+  int status = 0;
+  if (q.status[1]) status = 1;                    // PMG_ERR_INVALID: bad geometry
+  else if (q.status[0] || !isfinite(bb)) status = 5;  // PMG_ERR_NONFINITE
+  q.status[0] = 0;
+  st.status[i] = status;
+  st.active[i] = (status == 0 && bb > 0.0) ? 1 : 0;
+  st.first[i] = st.active[i];
+  st.confirm[i] = 0;
+  st.total[i] = 0;
+}
+__global__ void k_batch_cond(const VecBatch* tab) {
+  const int i = threadIdx.x;
+  if (i >= tab->n) return;
+  const BatchState& st = tab->st;
+  if (!st.active[i]) return;
+  const VecProb& q = tab->prm[i];
+  const double rr = q.s[GROUP_OUTER + SLOT_RR];
+  const int total = ++st.total[i];
+  st.first[i] = 0;
+  if (!isfinite(rr)) {
+    st.status[i] = 5;
+    st.active[i] = 0;
+  } else if (rr <= q.tol2 * st.bb[i] || total >= q.max_iter) {
+    st.confirm[i] = 1;
+  }
+}
+__global__ void k_batch_confirm(const VecBatch* tab, cudaGraphConditionalHandle hnd, int in_graph, int* any_out) {
+  __shared__ int any;
+  const int i = threadIdx.x;
+  if (i == 0) any = 0;
+  __syncthreads();
+  const BatchState& st = tab->st;
+  if (i < tab->n) {
+    if (st.confirm[i]) {
+      const VecProb& q = tab->prm[i];
+      const double rr = q.s[SLOT_RR64];
+      st.rr64[i] = rr;
+      st.confirm[i] = 0;
+      if (!isfinite(rr)) {
+        st.status[i] = 5;
+        st.active[i] = 0;
+      } else if (rr <= q.tol2 * st.bb[i]) {
+        st.active[i] = 0;  // converged
+      } else if (st.total[i] >= q.max_iter) {
+        st.status[i] = 4;  // PMG_ERR_NOT_CONVERGED
+        st.active[i] = 0;
+      } else {
+        st.first[i] = 1;   // drift: restart the recurrence from the true residual
+      }
+    }
+    if (st.active[i]) atomicOr(&any, 1);
+  }
+  __syncthreads();
+  if (i == 0) {
+    *any_out = any;
+    if (in_graph) cudaGraphSetConditional(hnd, any ? 1u : 0u);
+  }
+}
+cudaError_t batch_state_init(const void* table, int n, cudaStream_t st) {
+  k_batch_state_init<<<1, ((n + 31) / 32) * 32, 0, st>>>(static_cast<const VecBatch*>(table));
+  return cudaGetLastError();
+}
+cudaError_t batch_cond(const void* table, int n, cudaStream_t st) {
+  k_batch_cond<<<1, ((n + 31) / 32) * 32, 0, st>>>(static_cast<const VecBatch*>(table));
+  return cudaGetLastError();
+}
+cudaError_t batch_confirm(const void* table, int n, cudaGraphConditionalHandle hnd, int in_graph, int* any,
+                          cudaStream_t st) {
+  k_batch_confirm<<<1, ((n + 31) / 32) * 32, 0, st>>>(static_cast<const VecBatch*>(table), hnd, in_graph, any);
   return cudaGetLastError();
 }
 

@@ -16,7 +16,6 @@
 
 namespace pmg {
 
-enum { MODE_APPLY = 0, MODE_RESIDUAL = 1, MODE_DOT = 2, MODE_DIV = 3 };
 
 template <typename T>
 struct CurvedParams {
@@ -113,7 +112,7 @@ __device__ __forceinline__ void tc_contract(TcKind kind, int ntiles, GetB getb, 
 // PZ: polynomial order along sigma when it differs from the order P along x (Sec. 5.1);
 // the x-contractions use P + 1 nodes, the sigma-contractions PZ + 1.
 template <int P, typename T, int MODE, int TC, bool MIX = false, bool BATHY = false, int PZ = P>
-__global__ void __launch_bounds__(512) k_curved(CurvedParams<T> p) {
+__device__ __forceinline__ void curved_body(const CurvedParams<T>& p, const int ex, const int nblocks) {
   static_assert(TC == 0 || PZ == P, "tensor-core path: equal orders");
   static_assert(TC == 0 || (std::is_same<T, float>::value && MODE != MODE_DIV), "tensor-core path: FP32 operator");
   static_assert(!MIX || (TC == 0 && (MODE == MODE_APPLY || MODE == MODE_RESIDUAL)), "mixed-stage: apply/residual");
@@ -124,7 +123,6 @@ __global__ void __launch_bounds__(512) k_curved(CurvedParams<T> p) {
   const Shape s = p.s;
   const int NZ = s.NZ, Nz = s.Nz, NZp = slab_pitch(NZ);
   const int L = Nz * n;
-  const int ex = blockIdx.x;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* X = reinterpret_cast<T*>(smem_raw);   // [n][NZp]   input slab, later Y
   T* Ur = X + n * NZp;                      // [n][NZp]   U_r per node row
@@ -365,8 +363,30 @@ __global__ void __launch_bounds__(512) k_curved(CurvedParams<T> p) {
   }
   if (MODE == MODE_RESIDUAL || MODE == MODE_DOT) {
     double v = block_sum(acc.value(), red);
-    grid_reduce(p.sc, v, nedges, p.result, red, s_flag);
+    grid_reduce(p.sc, v, nedges, p.result, red, s_flag, ex, nblocks);
   }
+}
+
+template <int P, typename T, int MODE, int TC, bool MIX = false, bool BATHY = false, int PZ = P>
+__global__ void __launch_bounds__(512) k_curved(CurvedParams<T> p) {
+  curved_body<P, T, MODE, TC, MIX, BATHY, PZ>(p, blockIdx.x, gridDim.x);
+}
+
+// Batched: one CTA per element column of every problem in the table (same-stage operator,
+// constant depth, CUDA cores, equal orders); one instantiation per order, shared by every
+// range of a table.
+template <typename T, int MODE>
+struct CurvedBatch {
+  BatchMap m;
+  CurvedParams<T> prm[kMaxBatch];
+};
+template <typename T, int MODE, int P>
+__global__ void __launch_bounds__(256) k_curved_batch(const CurvedBatch<T, MODE>* tab) {
+  batch_items(tab->m, [&](int r, int ex) {
+    const CurvedParams<T>& p = tab->prm[r];
+    curved_body<P, T, MODE, 0>(p, ex, p.s.Nx);
+    __syncthreads();
+  });
 }
 
 template <typename T>

@@ -14,6 +14,9 @@
 // a launch of its own nor a round trip through global memory.  Those columns include the
 // neighbouring CTAs' interiors, which they update in the same launch, so the fused sweep
 // reads the iterate from one buffer and writes it to another (x -> xout).
+#include <algorithm>
+#include <new>
+
 #include "pmg_common.cuh"
 #include "pmg_kernels.h"
 
@@ -56,14 +59,14 @@ __device__ __forceinline__ int xclass32(const Shape& s, int ex) {
 }
 
 template <int P, int O, int XC, bool RES>
-__device__ __forceinline__ void fdm32_body(const Fdm32Params& p, unsigned char* smem_raw) {
+__device__ __forceinline__ void fdm32_body(const Fdm32Params& p, unsigned char* smem_raw, const int ex) {
   constexpr int NB = P + 1 + 2 * O;
   constexpr int OFF = fdm32_offset(P, O);
   constexpr int VX = OFF + XC * NB * NB;  // x eigenvectors of this CTA's class
   constexpr int VZI = OFF + 4 * NB * NB;  // z eigenvectors of interior elements
   const Shape s = p.s;
   const int NZ = s.NZ, Nz = s.Nz, NZp = slab_pitch(NZ);
-  const int ex = blockIdx.x, col0 = ex * P;
+  const int col0 = ex * P;
   float* R = reinterpret_cast<float*>(smem_raw);  // [NB][NZp]  input, later U
   float* T1 = R + NB * NZp;                        // [NB][NZp]
   float* T3 = T1 + NB * NZp;                       // [Nz][NB][NB] (ez, b, alpha)
@@ -303,12 +306,39 @@ __device__ __forceinline__ void fdm32_body(const Fdm32Params& p, unsigned char* 
 template <int P, int O, bool RES>
 __global__ void __launch_bounds__(512) k_fdm32(Fdm32Params p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  switch (xclass32(p.s, blockIdx.x)) {
-    case 0: fdm32_body<P, O, 0, RES>(p, smem_raw); break;
-    case 1: fdm32_body<P, O, 1, RES>(p, smem_raw); break;
-    case 2: fdm32_body<P, O, 2, RES>(p, smem_raw); break;
-    default: fdm32_body<P, O, 3, RES>(p, smem_raw); break;
+  const int ex = blockIdx.x;
+  switch (xclass32(p.s, ex)) {
+    case 0: fdm32_body<P, O, 0, RES>(p, smem_raw, ex); break;
+    case 1: fdm32_body<P, O, 1, RES>(p, smem_raw, ex); break;
+    case 2: fdm32_body<P, O, 2, RES>(p, smem_raw, ex); break;
+    default: fdm32_body<P, O, 3, RES>(p, smem_raw, ex); break;
   }
+}
+
+// Batched: one CTA per element column of every problem in the table (split residual, in
+// place), the order and overlap dispatched per CTA.
+struct Fdm32Batch {
+  BatchMap m;
+  Fdm32Params prm[kMaxBatch];
+  int overlap[kMaxBatch];
+};
+template <int P, int O>
+__device__ __forceinline__ void fdm32_cta(const Fdm32Params& p, unsigned char* smem_raw, int ex) {
+  switch (xclass32(p.s, ex)) {
+    case 0: fdm32_body<P, O, 0, false>(p, smem_raw, ex); break;
+    case 1: fdm32_body<P, O, 1, false>(p, smem_raw, ex); break;
+    case 2: fdm32_body<P, O, 2, false>(p, smem_raw, ex); break;
+    default: fdm32_body<P, O, 3, false>(p, smem_raw, ex); break;
+  }
+}
+// one instantiation per (order, overlap): every range of a table shares them
+template <int P, int O>
+__global__ void __launch_bounds__(256) k_fdm32_batch(const Fdm32Batch* tab) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  batch_items(tab->m, [&](int r, int ex) {
+    fdm32_cta<P, O>(tab->prm[r], smem_raw, ex);
+    __syncthreads();
+  });
 }
 
 // ------------------------------------------------------------------------------------
@@ -606,14 +636,17 @@ static cudaError_t launch_fdm32z(const Fdm32zParams& prm, int threads, cudaStrea
   return cudaGetLastError();
 }
 
+static size_t fdm32_smem(int P, int O, bool res, const Shape& s) {
+  const int NB = P + 1 + 2 * O, XCOLS = res ? 3 * P + 1 : NB;
+  const int NZp = slab_pitch(s.NZ);
+  size_t elems = (size_t)(2 * NB + XCOLS) * NZp + (size_t)s.Nz * NB * NB + 8 * NB * NB + s.NZ + NB +
+                 (res ? s.NZ + NB : 0);
+  return ((elems * sizeof(float) + 15) & ~(size_t)15) + 16;
+}
+
 template <int P, int O, bool RES>
 static cudaError_t launch_fdm32_pr(const Fdm32Params& prm, int threads, cudaStream_t st) {
-  constexpr int NB = P + 1 + 2 * O;
-  constexpr int XCOLS = RES ? 3 * P + 1 : NB;
-  int NZp = slab_pitch(prm.s.NZ);
-  size_t elems = (size_t)(2 * NB + XCOLS) * NZp + (size_t)prm.s.Nz * NB * NB + 8 * NB * NB + prm.s.NZ + NB +
-                 (RES ? prm.s.NZ + NB : 0);
-  size_t sm = ((elems * sizeof(float) + 15) & ~(size_t)15) + 16;
+  size_t sm = fdm32_smem(P, O, RES, prm.s);
   auto k = k_fdm32<P, O, RES>;
   static std::atomic<unsigned long long> s_mask{0};
   cudaError_t e = ensure_max_smem(k, s_mask);
@@ -671,18 +704,13 @@ bool fdm32z_usable(const FdmArgs& a) {
          a.s.P <= MAXP && fdm32z_layout(a.s.P, a.overlap, a.zc).bytes <= 227 * 1024;
 }
 
-cudaError_t fdm_smooth32(const FdmArgs& a, cudaStream_t st) {
-  if (a.zc > 0) {
-    if (!fdm32z_usable(a)) return cudaErrorInvalidValue;
-    return fdm_smooth32z(a, st);
-  }
+static Fdm32Params fdm32_params(const FdmArgs& a) {
   Fdm32Params p;
   p.s = a.s;
   p.r = (const float*)a.r;
   p.x = (float*)a.x;
   p.xout = a.xout ? (float*)a.xout : (float*)a.x;
   p.xzero = a.xzero;
-  if (a.b && p.xout == p.x) return cudaErrorInvalidValue;  // neighbours read x while it is written
   p.post = a.post;
   p.omega = (float)a.omega;
   p.Vz = (const float*)a.Vz;
@@ -695,6 +723,16 @@ cudaError_t fdm_smooth32(const FdmArgs& a, cudaStream_t st) {
   p.cz = (float)a.cz;
   p.mX = (const float*)a.mX;
   p.mZ = (const float*)a.mZ;
+  return p;
+}
+
+cudaError_t fdm_smooth32(const FdmArgs& a, cudaStream_t st) {
+  if (a.zc > 0) {
+    if (!fdm32z_usable(a)) return cudaErrorInvalidValue;
+    return fdm_smooth32z(a, st);
+  }
+  if (a.b && (!a.xout || a.xout == a.x)) return cudaErrorInvalidValue;  // neighbours read x while it is written
+  const Fdm32Params p = fdm32_params(a);
   int thr = (a.threads >= 32 && a.threads <= 512) ? a.threads : 256;
   if (a.overlap == 0) {
     switch (a.s.P) {
@@ -708,6 +746,66 @@ cudaError_t fdm_smooth32(const FdmArgs& a, cudaStream_t st) {
 #define PMG_CASE(PP) case PP: return launch_fdm32_p<PP, 1>(p, thr, st);
       PMG_CASE(3) PMG_CASE(4) PMG_CASE(5)
       PMG_CASE(6) PMG_CASE(7) PMG_CASE(8) PMG_CASE(9) PMG_CASE(10)
+#undef PMG_CASE
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+// Batched sweep table: range r is problem prob[r]'s level a[r] (split residual, in place),
+// one CTA per element column.  The table is written to device memory owned by the caller.
+cudaError_t fdm32_batch_table(const FdmArgs* a, const int* prob, int n, const int* active, void** table, int* nctas,
+                              size_t* smem) {
+  if (n < 1 || n > kMaxBatch) return cudaErrorInvalidValue;
+  Fdm32Batch* h = new (std::nothrow) Fdm32Batch();
+  if (!h) return cudaErrorMemoryAllocation;
+  h->m.nrange = n;
+  h->m.active = active;
+  h->m.start[0] = 0;
+  size_t sm = 0;
+  for (int i = 0; i < n; ++i) {
+    if (a[i].b || (a[i].xout && a[i].xout != a[i].x) || a[i].s.P < 2 || a[i].s.P > MAXP ||
+        (a[i].overlap == 1 && a[i].s.P < 3) || a[i].s.P != a[0].s.P || a[i].overlap != a[0].overlap) {
+      delete h;
+      return cudaErrorInvalidValue;
+    }
+    h->prm[i] = fdm32_params(a[i]);
+    h->overlap[i] = a[i].overlap;
+    h->m.prob[i] = prob[i];
+    h->m.start[i + 1] = h->m.start[i] + a[i].s.Nx;
+    sm = std::max(sm, fdm32_smem(a[i].s.P, a[i].overlap, false, a[i].s));
+  }
+  *nctas = h->m.start[n];
+  *smem = sm;
+  BatchMap* maps[1] = {&h->m};
+  cudaError_t e = batch_upload(h, maps, 1, table);
+  delete h;
+  return e;
+}
+
+template <int P, int O>
+static cudaError_t launch_fdm32_batch(const void* table, int nctas, int threads, size_t smem, cudaStream_t st) {
+  auto k = k_fdm32_batch<P, O>;
+  static std::atomic<unsigned long long> s_mask{0};
+  cudaError_t e = ensure_max_smem(k, s_mask);
+  if (e != cudaSuccess) return e;
+  int grid = 0;
+  e = batch_grid(k, threads, smem, nctas, &grid);
+  if (e != cudaSuccess) return e;
+  k<<<grid, threads, smem, st>>>(static_cast<const Fdm32Batch*>(table));
+  return cudaGetLastError();
+}
+cudaError_t fdm32_batch_launch(const void* table, int P, int O, int nctas, int threads, size_t smem, cudaStream_t st) {
+  if (O == 1) {
+    switch (P) {
+#define PMG_CASE(PP) case PP: return launch_fdm32_batch<PP, 1>(table, nctas, threads, smem, st);
+      PMG_CASE(3) PMG_CASE(4) PMG_CASE(5) PMG_CASE(6) PMG_CASE(7) PMG_CASE(8) PMG_CASE(9) PMG_CASE(10)
+#undef PMG_CASE
+    }
+  } else if (O == 0) {
+    switch (P) {
+#define PMG_CASE(PP) case PP: return launch_fdm32_batch<PP, 0>(table, nctas, threads, smem, st);
+      PMG_CASE(2) PMG_CASE(3) PMG_CASE(4) PMG_CASE(5) PMG_CASE(6) PMG_CASE(7) PMG_CASE(8) PMG_CASE(9) PMG_CASE(10)
 #undef PMG_CASE
     }
   }

@@ -12,6 +12,9 @@
 //    generalized eigenvectors (V^T M V = I):  A_i^-1 = (Vx (x) Vz) diag(1/(cx lx + cz lz)) (Vx (x) Vz)^T.
 //  * transfers (Sec. 5.2): prolongation = coarse polynomial evaluated at the fine nodes,
 //    J (x) J per element; restriction = its transpose, summed over distinct fine nodes.
+#include <algorithm>
+#include <new>
+
 #include "pmg_common.cuh"
 #include "pmg_kernels.h"
 
@@ -104,12 +107,11 @@ struct TransferParams {
 
 // x_f += P x_c
 template <typename T>
-__global__ void __launch_bounds__(512) k_prolong(TransferParams<T> p) {
+__device__ __forceinline__ void prolong_body(const TransferParams<T>& p, const int ex) {
   const Shape f = p.f, c = p.c;
   const int Pf = f.P, Pc = c.P, nf = Pf + 1, nc = Pc + 1;            // along x
   const int Pfz = f.pz(), Pcz = c.pz(), nfz = Pfz + 1, ncz = Pcz + 1;  // along sigma
   const int NZf = f.NZ, NZc = c.NZ, NZcp = slab_pitch(NZc), NZfp = slab_pitch(NZf);
-  const int ex = blockIdx.x;
   const bool last = !f.periodic && ex == f.Nx - 1;
   const int own = last ? nf : Pf;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -138,15 +140,18 @@ __global__ void __launch_bounds__(512) k_prolong(TransferParams<T> p) {
     p.out[(size_t)(ex * Pf + i) * NZf + iz] = Xf[i * NZfp + iz] + acc;
   });
 }
+template <typename T>
+__global__ void __launch_bounds__(512) k_prolong(TransferParams<T> p) {
+  prolong_body<T>(p, blockIdx.x);
+}
 
 // r_c = P^T r_f
 template <typename T>
-__global__ void __launch_bounds__(512) k_restrict(TransferParams<T> p) {
+__device__ __forceinline__ void restrict_body(const TransferParams<T>& p, const int ex) {
   const Shape f = p.f, c = p.c;
   const int Pf = f.P, Pc = c.P, nf = Pf + 1, nc = Pc + 1;            // along x
   const int Pfz = f.pz(), Pcz = c.pz(), nfz = Pfz + 1, ncz = Pcz + 1;  // along sigma
   const int NZf = f.NZ, NZc = c.NZ, NZfp = slab_pitch(NZf), NZcp = slab_pitch(NZc);
-  const int ex = blockIdx.x;
   const bool left = f.periodic || ex > 0;
   const bool last = !f.periodic && ex == f.Nx - 1;
   const int own = last ? nc : Pc;
@@ -237,6 +242,37 @@ __global__ void __launch_bounds__(512) k_restrict(TransferParams<T> p) {
     p.out[(size_t)(ex * Pc + k) * NZc + lc] = acc;
   });
 }
+template <typename T>
+__global__ void __launch_bounds__(512) k_restrict(TransferParams<T> p) {
+  restrict_body<T>(p, blockIdx.x);
+}
+
+template <typename T>
+static TransferParams<T> transfer_params(const TransferArgs& a) {
+  TransferParams<T> p;
+  p.f = a.f;
+  p.c = a.c;
+  p.in = (const T*)a.in;
+  p.out = (T*)a.out;
+  p.J = a.J;
+  p.Jz = a.Jz ? a.Jz : a.J;
+  p.xf = (const T*)a.xf;
+  p.cx = (T)a.cx;
+  p.cz = (T)a.cz;
+  p.mX = (const T*)a.mX;
+  p.mZ = (const T*)a.mZ;
+  return p;
+}
+static size_t transfer_smem(const TransferArgs& a, int restrict_, size_t word) {
+  int nf = a.f.P + 1, nc = a.c.P + 1, nfz = a.f.pz() + 1, ncz = a.c.pz() + 1;
+  int NZfp = slab_pitch(a.f.NZ), NZcp = slab_pitch(a.c.NZ);
+  if (restrict_) {
+    size_t sm = ((size_t)(2 * a.f.P + 1) * (NZfp + NZcp) + nf * nc + nfz * ncz) * word + 16;
+    if (a.xf) sm += ((size_t)(2 * a.f.P + 1) * (NZfp + 1) + a.f.NZ) * word;
+    return sm;
+  }
+  return ((size_t)nc * (NZcp + NZfp) + nf * nc + nfz * ncz + (size_t)nf * NZfp) * word + 16;
+}
 
 template <typename T>
 cudaError_t transfer(const TransferArgs& a, int restrict_, cudaStream_t st) {
@@ -273,5 +309,122 @@ cudaError_t transfer(const TransferArgs& a, int restrict_, cudaStream_t st) {
 }
 template cudaError_t transfer<double>(const TransferArgs&, int, cudaStream_t);
 template cudaError_t transfer<float>(const TransferArgs&, int, cudaStream_t);
+
+// ---- batched launches (FP32 V-cycle of a batch of independent problems) ---------------
+struct FlatBatch {
+  BatchMap m;
+  FlatParams<float> prm[kMaxBatch];
+};
+template <int P>
+__global__ void __launch_bounds__(256) k_flat_np_batch(const FlatBatch* tab) {
+  batch_items(tab->m, [&](int r, int k) {
+    flat_np_body<P, float, false>(tab->prm[r], (size_t)k * blockDim.x + threadIdx.x);
+  });
+}
+struct XferBatch {
+  BatchMap m;
+  TransferParams<float> prm[kMaxBatch];
+};
+template <int RESTRICT>
+__global__ void __launch_bounds__(512) k_transfer_batch(const XferBatch* tab) {
+  batch_items(tab->m, [&](int r, int ex) {
+    if (RESTRICT) restrict_body<float>(tab->prm[r], ex);
+    else prolong_body<float>(tab->prm[r], ex);
+    __syncthreads();
+  });
+}
+
+template <class Tab>
+static cudaError_t upload_table(Tab* h, void** table) {
+  BatchMap* maps[1] = {&h->m};
+  return batch_upload(h, maps, 1, table);
+}
+
+// Node-parallel FP32 level operator / residual of every problem: ceil(N / threads) CTAs each.
+cudaError_t flat_batch_table(const FlatArgs* a, const int* prob, int n, const int* active, int threads, void** table,
+                             int* nctas) {
+  if (n < 1 || n > kMaxBatch) return cudaErrorInvalidValue;
+  FlatBatch* h = new (std::nothrow) FlatBatch();
+  if (!h) return cudaErrorMemoryAllocation;
+  h->m.nrange = n;
+  h->m.active = active;
+  h->m.start[0] = 0;
+  for (int i = 0; i < n; ++i) {
+    if (a[i].Kx || a[i].s.pz() != a[i].s.P || a[i].s.P != a[0].s.P) { delete h; return cudaErrorInvalidValue; }
+    FlatParams<float>& p = h->prm[i];
+    p.s = a[i].s;
+    p.x = (const float*)a[i].x;
+    p.b = (const float*)a[i].b;
+    p.y = (float*)a[i].y;
+    p.cx = (float)a[i].cx;
+    p.cz = (float)a[i].cz;
+    p.mX = (const float*)a[i].mX;
+    p.mZ = (const float*)a[i].mZ;
+    p.residual = a[i].residual;
+    p.Kx = nullptr;
+    h->m.prob[i] = prob[i];
+    const size_t N = (size_t)a[i].s.NX * a[i].s.NZ;
+    h->m.start[i + 1] = h->m.start[i] + (int)((N + threads - 1) / threads);
+  }
+  *nctas = h->m.start[n];
+  cudaError_t e = upload_table(h, table);
+  delete h;
+  return e;
+}
+cudaError_t flat_batch_launch(const void* table, int P, int nctas, int threads, cudaStream_t st) {
+  const FlatBatch* t = static_cast<const FlatBatch*>(table);
+  int grid = 0;
+  cudaError_t e = cudaSuccess;
+  switch (P) {
+#define PMG_CASE(PP)                                                         \
+  case PP:                                                                   \
+    e = batch_grid(k_flat_np_batch<PP>, threads, 0, nctas, &grid);      \
+    if (e != cudaSuccess) return e;                                          \
+    k_flat_np_batch<PP><<<grid, threads, 0, st>>>(t);                        \
+    break;
+    PMG_CASE(1) PMG_CASE(2) PMG_CASE(3) PMG_CASE(4) PMG_CASE(5) PMG_CASE(6) PMG_CASE(7) PMG_CASE(8)
+    PMG_CASE(9) PMG_CASE(10)
+#undef PMG_CASE
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// FP32 restriction (restrict_ = 1) or prolongation of every problem: one CTA per element column.
+cudaError_t transfer_batch_table(const TransferArgs* a, const int* prob, int n, const int* active, int restrict_,
+                                 void** table, int* nctas, size_t* smem) {
+  if (n < 1 || n > kMaxBatch) return cudaErrorInvalidValue;
+  XferBatch* h = new (std::nothrow) XferBatch();
+  if (!h) return cudaErrorMemoryAllocation;
+  h->m.nrange = n;
+  h->m.active = active;
+  h->m.start[0] = 0;
+  size_t sm = 0;
+  for (int i = 0; i < n; ++i) {
+    if (a[i].xf) { delete h; return cudaErrorInvalidValue; }
+    h->prm[i] = transfer_params<float>(a[i]);
+    h->m.prob[i] = prob[i];
+    h->m.start[i + 1] = h->m.start[i] + a[i].f.Nx;
+    sm = std::max(sm, transfer_smem(a[i], restrict_, sizeof(float)));
+  }
+  *nctas = h->m.start[n];
+  *smem = sm;
+  cudaError_t e = upload_table(h, table);
+  delete h;
+  if (e != cudaSuccess) return e;
+  static std::atomic<unsigned long long> s_mask_r{0}, s_mask_p{0};
+  return restrict_ ? ensure_max_smem(k_transfer_batch<1>, s_mask_r) : ensure_max_smem(k_transfer_batch<0>, s_mask_p);
+}
+cudaError_t transfer_batch_launch(const void* table, int restrict_, int nctas, int threads, size_t smem,
+                                  cudaStream_t st) {
+  const XferBatch* t = static_cast<const XferBatch*>(table);
+  int grid = 0;
+  cudaError_t e = restrict_ ? batch_grid(k_transfer_batch<1>, threads, smem, nctas, &grid)
+                            : batch_grid(k_transfer_batch<0>, threads, smem, nctas, &grid);
+  if (e != cudaSuccess) return e;
+  if (restrict_) k_transfer_batch<1><<<grid, threads, smem, st>>>(t);
+  else k_transfer_batch<0><<<grid, threads, smem, st>>>(t);
+  return cudaGetLastError();
+}
 
 }  // namespace pmg

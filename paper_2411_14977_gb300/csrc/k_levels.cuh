@@ -125,11 +125,10 @@ __global__ void __launch_bounds__(512) k_flat(FlatParams<T> p) {
 // neighbours straight from global memory (L1/L2 serve the reuse), no shared memory and no
 // barriers, so a CTA's critical path is one load wave and ~2(P+1) FMAs.
 template <int P, typename T, bool VAR, int PZ = P>
-__global__ void __launch_bounds__(256) k_flat_np(FlatParams<T> p) {
+__device__ __forceinline__ void flat_np_body(const FlatParams<T>& p, const size_t g) {
   constexpr int n = P + 1;
   const Shape s = p.s;
   const int NZ = s.NZ, Nz = s.Nz;
-  const size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (g >= (size_t)s.NX * NZ) return;
   const int ix = (int)(g / NZ), iz = (int)(g - (size_t)ix * NZ);
   if (iz == NZ - 1) {
@@ -162,6 +161,10 @@ __global__ void __launch_bounds__(256) k_flat_np(FlatParams<T> p) {
   }
   T v = p.cx * p.mZ[iz] * ax + p.cz * p.mX[ix] * az;
   p.y[g] = p.residual ? p.b[g] - v : v;
+}
+template <int P, typename T, bool VAR, int PZ = P>
+__global__ void __launch_bounds__(256) k_flat_np(FlatParams<T> p) {
+  flat_np_body<P, T, VAR, PZ>(p, blockIdx.x * (size_t)blockDim.x + threadIdx.x);
 }
 
 // The same level operator tiled: one thread per element, a CTA over EXT element columns x

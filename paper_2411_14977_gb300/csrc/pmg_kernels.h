@@ -58,6 +58,9 @@ __host__ __device__ constexpr int fdm32_offset(int P, int O) {
 }
 __host__ __device__ constexpr int fdm32_table_size() { return fdm32_offset(MAXP + 1, 0); }
 
+// Modes of the actual-geometry operator kernel (CurvedArgs.mode).
+enum { MODE_APPLY = 0, MODE_RESIDUAL = 1, MODE_DOT = 2, MODE_DIV = 3 };
+
 struct CurvedArgs {
   Shape s;
   int mode;            // 0 apply (masked), 1 residual b - A x, 2 y = A x with <x, y>, 3 divergence load
@@ -298,6 +301,82 @@ cudaError_t arm_exchange(void* buf, size_t n8);  // synchronous, at set-up
 cudaError_t arm_exchange_f64(void* buf, size_t n8, cudaStream_t st);
 cudaError_t loop_cond(cudaGraphConditionalHandle hnd, const double* s, const double* bb, double thresh2, int* iter,
                       int max_iter, cudaStream_t st);
+
+// ---- batched launches over the problems of a batch (one launch per stage) ------------
+// Each *_batch_table writes a device table (cudaMalloc'ed, owned and freed by the caller)
+// whose range i is problem prob[i] with the arguments a[i]; `active` (device, one int per
+// problem of the batch, or NULL for all) decides per launch which ranges work (the others
+// return at once); *nctas is the grid of the launch, *smem its dynamic shared memory.  The
+// sweep, level-operator and outer-operator tables hold one order (and overlap) each: their
+// kernels are instantiated per order, and the launch names it.
+cudaError_t fdm32_batch_table(const FdmArgs* a, const int* prob, int n, const int* active, void** table, int* nctas,
+                              size_t* smem);
+cudaError_t fdm32_batch_launch(const void* table, int P, int O, int nctas, int threads, size_t smem, cudaStream_t st);
+cudaError_t flat_batch_table(const FlatArgs* a, const int* prob, int n, const int* active, int threads, void** table,
+                             int* nctas);
+cudaError_t flat_batch_launch(const void* table, int P, int nctas, int threads, cudaStream_t st);
+cudaError_t transfer_batch_table(const TransferArgs* a, const int* prob, int n, const int* active, int restrict_,
+                                 void** table, int* nctas, size_t* smem);
+cudaError_t transfer_batch_launch(const void* table, int restrict_, int nctas, int threads, size_t smem,
+                                  cudaStream_t st);
+// coarse solve of every problem (b, x: the FP32 coarse-level vectors); three launches
+cudaError_t coarse_batch_table(const CoarseArgs* a, const float* const* b, float* const* x, const int* prob, int n,
+                               const int* active, void** table, int nctas[3], size_t* smem);
+cudaError_t coarse_batch_launch(const void* table, const int nctas[3], size_t smem, cudaStream_t st);
+// double-float outer operator of every problem: mode 2 (y = A x with <x, y> into *result)
+// or 1 (y = b - A x with ||y||^2 into *result)
+cudaError_t curved_batch_table(int mode, const CurvedArgs* a, const int* prob, int n, const int* active, void** table,
+                               int* nctas, size_t* smem);
+cudaError_t curved_batch_launch(int mode, const void* table, int P, int nctas, int threads, size_t smem,
+                                cudaStream_t st);
+
+// Krylov vectors and loop state of one problem of a batched flexible-CG solve (FP64 outer
+// vectors, FP32 V-cycle input r32 and output z32, the handle's scalar slots and scratch).
+struct VecProb {
+  size_t n;
+  int NZ;
+  double *x, *r, *p, *w, *rold;
+  float* r32;
+  const float* z32;
+  double* s;       // the handle's scalar slots (group GROUP_OUTER, SLOT_BB, SLOT_RR64)
+  Scratch sc;
+  int* status;     // the handle's status words: [0] inputs, [1] geometry
+  double* bcopy;   // the problem's load vector for this solve (copied from the caller's)
+  int max_iter;
+  double tol2;
+};
+// Per-problem solve state (device, one int each): active (still iterating), first (the
+// next iteration starts the CG recurrence afresh: p = z), confirm (the recursive residual
+// met the tolerance or the cap: check the true residual), total (outer iterations),
+// status (pmg_status of the problem).
+struct BatchState {
+  int *active, *first, *confirm, *total, *status;
+  double *bb, *rr64;  // ||b~||^2 and the last true ||b~ - A x||^2 per problem
+};
+// Per-call device pointers of problem i: load vector, Dirichlet data, output pressure.
+struct BatchIO {
+  const double* b;
+  const double* pD;
+  double* out;
+};
+enum { VB_INIT = 0, VB_CAST_FIRST, VB_RZ, VB_P_UPDATE, VB_CG_UPDATE, VB_COPY_OUT, VB_COUNT };
+// prob: problem index (into the state and io arrays) of each entry of a (NULL: 0..n-1); the
+// state kernels below take the table of every problem (prob NULL).
+cudaError_t vec_batch_table(const VecProb* a, int n, BatchState st, const BatchIO* io, void** table,
+                            int nctas[VB_COUNT], const int* prob);
+cudaError_t vec_batch_launch(int which, const void* table, const int nctas[VB_COUNT], cudaStream_t st);
+// One thread per problem: after the lifted residual of x = (0, p_D) set BB, the initial
+// state (inactive when the inputs failed, b~ = 0 or the start meets the tolerance).
+cudaError_t batch_state_init(const void* table, int n, cudaStream_t st);
+// After the CG update: count the iteration, end the recurrence's first step, flag
+// problems whose recursive residual met the tolerance or the cap (or went non-finite).
+cudaError_t batch_cond(const void* table, int n, cudaStream_t st);
+// After the true residual of the flagged problems: finish them (tolerance met, or the cap
+// reached: PMG_ERR_NOT_CONVERGED) or restart the recurrence from the true residual; then
+// the while-node keeps looping while any problem is active (in_graph; *any receives the
+// same flag either way: a host-driven loop reads it).
+cudaError_t batch_confirm(const void* table, int n, cudaGraphConditionalHandle hnd, int in_graph, int* any,
+                          cudaStream_t st);
 
 // learned warm start (k_nn.cu)
 cudaError_t nn_conv_forward(const ConvDims& d, const float* X, const float* W, const float* b, float* Y,

@@ -1651,7 +1651,55 @@ struct pmg_batch {
   std::vector<cudaStream_t> st;
   std::vector<cudaEvent_t> done;
   cudaEvent_t fork = nullptr;
+  // ---- the batched path: one CUDA graph whose launches each cover every problem
+  struct Sub {     // one launch: the problems of one order in a stage
+    int kind;      // 0 sweep, 1 level residual, 2 restriction, 3 prolongation, 4 coarse solve,
+                   // 5 outer operator with <p, A p>, 6 outer residual
+    int P, O;      // order and overlap of its kernel instantiation
+    int threads;   // CTA size
+    void* table;   // device table
+    int nctas[3];
+    size_t smem;
+  };
+  struct Stage {   // the launches of one stage run as parallel branches of the graph
+    std::vector<Sub> subs;
+  };
+  struct Group {   // the problems of one order: one chain of launches through an iteration
+    std::vector<Sub> vdown, vup;  // V-cycle stages (one launch each), finest first / coarsest first
+    Sub coarse{}, dot{}, res0{}, res{};
+    void* vec = nullptr;          // vector-kernel table of the group
+    int vec_ctas[VB_COUNT] = {};
+  };
+  bool graph_built = false, tables_built = false;
+  bool eager = false;           // profiling: the iteration loop driven by the host (pmg_batch_set_eager)
+  int* any_dev = nullptr;       // "some problem is still active", written by the confirm kernel
+  int* any_host = nullptr;      // pinned copy (host-driven loop)
+  std::vector<void*> dev;       // device allocations of the batched path (tables, state, copies)
+  std::vector<Group> groups;
+  void* vec = nullptr;          // vector-kernel table of every problem (state machine, copies)
+  int vec_ctas[VB_COUNT] = {};
+  BatchState state{};
+  int* state_ints = nullptr;    // [5][n]
+  double* state_dbl = nullptr;  // [2][n]
+  BatchIO* io = nullptr;        // [n] device
+  BatchIO* io_host = nullptr;   // [n] pinned
+  int* st_host = nullptr;       // pinned copies of status, total
+  double* dbl_host = nullptr;   // pinned copies of bb, rr64
+  cudaStream_t cap = nullptr;
+  std::vector<cudaStream_t> aux;     // branches of a stage
+  std::vector<cudaEvent_t> aux_ev;   // fork event, then one join event per branch
+  cudaGraphExec_t exec = nullptr;
+  int64_t launches_per_iter = 0, launches_init = 0;
   ~pmg_batch() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (cap) cudaStreamDestroy(cap);
+    for (cudaStream_t a : aux) cudaStreamDestroy(a);
+    for (cudaEvent_t e : aux_ev) cudaEventDestroy(e);
+    for (void* d : dev) cudaFree(d);
+    if (io_host) cudaFreeHost(io_host);
+    if (st_host) cudaFreeHost(st_host);
+    if (dbl_host) cudaFreeHost(dbl_host);
+    if (any_host) cudaFreeHost(any_host);
     for (cudaStream_t s : st) if (s) cudaStreamDestroy(s);
     for (cudaEvent_t e : done) if (e) cudaEventDestroy(e);
     if (fork) cudaEventDestroy(fork);
@@ -1725,6 +1773,396 @@ static pmg_status plan_levels(const pmg_mesh_desc& m, const pmg_opts& o, std::ve
   if (orders.size() < 2) return fail(PMG_ERR_INVALID, "order must be >= 2 (the coarsest level is order 1)");
   return PMG_OK;
 }
+
+// =====================================================================================
+// Batched path of pmg_batch_solve: every stage of the mixed-precision flexible CG is one
+// launch over the work items of all problems (their element columns or nodes), and the
+// whole solve -- start, iterations, convergence checks, restarts -- is one CUDA graph with
+// a device-side while node.  Levels are aligned by their distance from the order-1 level,
+// so problems with fewer levels simply have no items in the top stages.
+// =====================================================================================
+namespace {
+
+// The batched path covers the mixed FP32 V-cycle (fast-diagonalisation Schwarz, flat
+// levels, constant depth, equal orders) under the FP64 flexible CG with the double-float
+// outer operator; other options run through the concurrent per-problem path.
+bool batch_eligible(const pmg_batch* B) {
+  if (B->h.size() > (size_t)kMaxBatch) return false;
+  for (const pmg_handle* h : B->h) {
+    if (h->opts.precision != PMG_MIXED_FP32 || (h->opts.outer != PMG_PCG && h->opts.outer != PMG_FCG) ||
+        !h->df64_outer || h->mixed_stage || h->bathy || h->aniso || h->tc)
+      return false;
+    for (const LevelDev& L : h->lv)
+      if (L.var || L.aniso || L.dense || L.actual) return false;
+  }
+  return true;
+}
+
+template <typename T>
+T* batch_alloc(pmg_batch* B, size_t n, cudaError_t& e) {
+  T* d = nullptr;
+  e = cudaMalloc(&d, std::max<size_t>(n, 1) * sizeof(T));
+  if (e == cudaSuccess) B->dev.push_back(d);
+  return d;
+}
+
+pmg_status batch_build_tables(pmg_batch* B) {
+  const int n = (int)B->h.size();
+  cudaError_t e;
+  B->state_ints = batch_alloc<int>(B, 5 * (size_t)n, e);
+  CK(e);
+  B->state_dbl = batch_alloc<double>(B, 2 * (size_t)n, e);
+  CK(e);
+  B->io = batch_alloc<BatchIO>(B, n, e);
+  CK(e);
+  B->any_dev = batch_alloc<int>(B, 1, e);
+  CK(e);
+  CK(cudaMallocHost(&B->any_host, sizeof(int)));
+  CK(cudaMemset(B->state_ints, 0, 5 * (size_t)n * sizeof(int)));
+  B->state = BatchState{B->state_ints, B->state_ints + n, B->state_ints + 2 * n, B->state_ints + 3 * n,
+                        B->state_ints + 4 * n, B->state_dbl, B->state_dbl + n};
+  CK(cudaMallocHost(&B->io_host, n * sizeof(BatchIO)));
+  CK(cudaMallocHost(&B->st_host, 2 * (size_t)n * sizeof(int)));
+  CK(cudaMallocHost(&B->dbl_host, 2 * (size_t)n * sizeof(double)));
+  // per-problem vector kernel arguments and outer-operator arguments
+  std::vector<VecProb> vp(n);
+  std::vector<CurvedArgs> dot(n), res0(n), res(n);
+  std::map<int, std::vector<int>> by_fine;  // problems of each fine order (the same level orders)
+  for (int i = 0; i < n; ++i) {
+    pmg_handle* h = B->h[i];
+    by_fine[h->lv[0].order].push_back(i);
+    double* bcopy = batch_alloc<double>(B, h->N, e);
+    CK(e);
+    CK(cudaMemset(h->z32, 0, h->N * sizeof(float)));  // its surface row stays zero
+    VecProb& q = vp[i];
+    q.n = h->N;
+    q.NZ = h->lv[0].s.NZ;
+    q.x = h->x;
+    q.r = h->r;
+    q.p = h->p;
+    q.w = h->w;
+    q.rold = h->rold;
+    q.r32 = h->r32;
+    q.z32 = h->z32;
+    q.s = h->scal;
+    q.sc = h->sc;
+    q.status = h->status;
+    q.bcopy = bcopy;
+    q.max_iter = h->opts.max_iter;
+    q.tol2 = h->opts.tol * h->opts.tol;
+    CurvedArgs a{};
+    a.s = h->lv[0].s;
+    a.geo = h->geo[0];
+    a.sigma = h->sigma[0];
+    a.scale = 1.0;
+    a.sc = h->sc;
+    a.mode = MODE_DOT;
+    a.x = h->p;
+    a.y = h->w;
+    a.mask_input = 1;
+    a.result = h->scal + GROUP_OUTER + SLOT_PAP;
+    dot[i] = a;
+    a.mode = MODE_RESIDUAL;
+    a.x = h->x;
+    a.b = bcopy;
+    a.y = h->r;
+    a.mask_input = 0;
+    a.result = h->scal + SLOT_BB;
+    res0[i] = a;
+    a.result = h->scal + SLOT_RR64;
+    res[i] = a;
+  }
+  CK(vec_batch_table(vp.data(), n, B->state, B->io, &B->vec, B->vec_ctas, nullptr));
+  B->dev.push_back(B->vec);
+  for (auto& kv : by_fine) {
+    const std::vector<int>& pi = kv.second;
+    const int m = (int)pi.size();
+    pmg_batch::Group G;
+    auto keep = [&](pmg_batch::Sub& u) { B->dev.push_back(u.table); };
+    {
+      std::vector<VecProb> gv;
+      std::vector<CurvedArgs> d1, r0, r1;
+      for (int i : pi) {
+        gv.push_back(vp[i]);
+        d1.push_back(dot[i]);
+        r0.push_back(res0[i]);
+        r1.push_back(res[i]);
+      }
+      CK(vec_batch_table(gv.data(), m, B->state, B->io, &G.vec, G.vec_ctas, pi.data()));
+      B->dev.push_back(G.vec);
+      pmg_batch::Sub u{};
+      u.P = kv.first;
+      u.threads = 256;
+      u.kind = 5;
+      CK(curved_batch_table(MODE_DOT, d1.data(), pi.data(), m, B->state.active, &u.table, u.nctas, &u.smem));
+      keep(u);
+      G.dot = u;
+      u.kind = 6;
+      CK(curved_batch_table(MODE_RESIDUAL, r0.data(), pi.data(), m, nullptr, &u.table, u.nctas, &u.smem));
+      keep(u);
+      G.res0 = u;
+      CK(curved_batch_table(MODE_RESIDUAL, r1.data(), pi.data(), m, B->state.confirm, &u.table, u.nctas, &u.smem));
+      keep(u);
+      G.res = u;
+    }
+    const int D = (int)B->h[pi[0]]->lv.size() - 1;
+    std::vector<std::vector<pmg_batch::Sub>> ups;
+    for (int l = 0; l < D; ++l) {
+      std::vector<FdmArgs> sw0, sw1, swp;
+      std::vector<FlatArgs> rs;
+      std::vector<TransferArgs> rt, pl;
+      int O = 0, P = 0, nzmax = 1;
+      for (int i : pi) {
+        pmg_handle* h = B->h[i];
+        LevelDev& L = h->lv[l];
+        LevelDev& C = h->lv[l + 1];
+        void* bl = l == 0 ? (void*)h->r32 : L.b[1];
+        void* xl = l == 0 ? (void*)h->z32 : L.x[1];
+        O = L.overlap;
+        P = L.order;
+        nzmax = std::max(nzmax, L.s.NZ);
+        FdmArgs f{L.s, L.overlap, bl, xl, 0, h->opts.omega, L.Vx[1], L.Vz[1], L.invden[1], L.wx[1], L.wz[1], h->sc,
+                  256};
+        f.xzero = 1;
+        sw0.push_back(f);
+        f.r = L.t[1];
+        f.xzero = 0;
+        sw1.push_back(f);
+        f.post = 1;
+        swp.push_back(f);
+        rs.push_back(FlatArgs{L.s, xl, bl, L.t[1], h->cx, h->cz, L.mX[1], L.mZ[1], 1, 256});
+        TransferArgs ta{L.s, C.s, L.t[1], C.b[1], L.J, 256};
+        ta.Jz = L.Jz;
+        rt.push_back(ta);
+        TransferArgs tp{L.s, C.s, C.x[1], xl, L.J, 256};
+        tp.Jz = L.Jz;
+        pl.push_back(tp);
+      }
+      pmg_batch::Sub s0{}, r{}, s1{}, sp{}, rst{}, prl{};
+      s0.P = r.P = s1.P = sp.P = rst.P = prl.P = P;
+      // slab CTAs: about one thread per node row of the deepest column; node-parallel: 256
+      const int slab_thr = std::min(256, std::max(64, (nzmax + 31) / 32 * 32));
+      s0.threads = s1.threads = sp.threads = rst.threads = prl.threads = slab_thr;
+      r.threads = 256;
+      s0.O = s1.O = sp.O = O;
+      s0.kind = s1.kind = sp.kind = 0;
+      r.kind = 1;
+      rst.kind = 2;
+      prl.kind = 3;
+      CK(fdm32_batch_table(sw0.data(), pi.data(), m, B->state.active, &s0.table, s0.nctas, &s0.smem));
+      keep(s0);
+      CK(fdm32_batch_table(sw1.data(), pi.data(), m, B->state.active, &s1.table, s1.nctas, &s1.smem));
+      keep(s1);
+      CK(fdm32_batch_table(swp.data(), pi.data(), m, B->state.active, &sp.table, sp.nctas, &sp.smem));
+      keep(sp);
+      CK(flat_batch_table(rs.data(), pi.data(), m, B->state.active, 256, &r.table, r.nctas));
+      keep(r);
+      CK(transfer_batch_table(rt.data(), pi.data(), m, B->state.active, 1, &rst.table, rst.nctas, &rst.smem));
+      keep(rst);
+      CK(transfer_batch_table(pl.data(), pi.data(), m, B->state.active, 0, &prl.table, prl.nctas, &prl.smem));
+      keep(prl);
+      // down: sweep from x = 0, residual, sweep, residual, restriction
+      for (const pmg_batch::Sub* u : {&s0, &r, &s1, &r, &rst}) G.vdown.push_back(*u);
+      // up: prolongation, then twice (residual, adjoint sweep)
+      ups.push_back({prl, r, sp, r, sp});
+    }
+    for (int k = (int)ups.size() - 1; k >= 0; --k) G.vup.insert(G.vup.end(), ups[k].begin(), ups[k].end());
+    {
+      std::vector<CoarseArgs> ca;
+      std::vector<const float*> cb;
+      std::vector<float*> cx;
+      for (int i : pi) {
+        pmg_handle* h = B->h[i];
+        LevelDev& C = h->lv.back();
+        ca.push_back(h->coarse);
+        cb.push_back((const float*)C.b[1]);
+        cx.push_back((float*)C.x[1]);
+      }
+      pmg_batch::Sub u{};
+      u.kind = 4;
+      u.threads = 256;
+      CK(coarse_batch_table(ca.data(), cb.data(), cx.data(), pi.data(), m, B->state.active, &u.table, u.nctas,
+                            &u.smem));
+      keep(u);
+      G.coarse = u;
+    }
+    B->groups.push_back(G);
+  }
+  const size_t ng = B->groups.size();
+  for (size_t k = 0; k + 1 < ng; ++k) {
+    cudaStream_t a;
+    CK(cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking));
+    B->aux.push_back(a);
+  }
+  for (size_t k = 0; k < ng; ++k) {
+    cudaEvent_t ev;
+    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    B->aux_ev.push_back(ev);
+  }
+  return PMG_OK;
+}
+
+pmg_status batch_sub(const pmg_batch::Sub& u, cudaStream_t cs) {
+  switch (u.kind) {
+    case 0: CK(fdm32_batch_launch(u.table, u.P, u.O, u.nctas[0], u.threads, u.smem, cs)); break;
+    case 1: CK(flat_batch_launch(u.table, u.P, u.nctas[0], u.threads, cs)); break;
+    case 2: CK(transfer_batch_launch(u.table, 1, u.nctas[0], u.threads, u.smem, cs)); break;
+    case 3: CK(transfer_batch_launch(u.table, 0, u.nctas[0], u.threads, u.smem, cs)); break;
+    case 4: CK(coarse_batch_launch(u.table, u.nctas, u.smem, cs)); break;
+    case 5: CK(curved_batch_launch(MODE_DOT, u.table, u.P, u.nctas[0], u.threads, u.smem, cs)); break;
+    default: CK(curved_batch_launch(MODE_RESIDUAL, u.table, u.P, u.nctas[0], u.threads, u.smem, cs)); break;
+  }
+  return PMG_OK;
+}
+
+// Runs f(group, stream) for every group as parallel branches: fork from cs, join into cs.
+template <class F>
+pmg_status batch_branches(pmg_batch* B, cudaStream_t cs, F&& f) {
+  const size_t ng = B->groups.size();
+  if (ng == 1) return f(B->groups[0], cs);
+  CK(cudaEventRecord(B->aux_ev[0], cs));
+  for (size_t j = 1; j < ng; ++j) {
+    CK(cudaStreamWaitEvent(B->aux[j - 1], B->aux_ev[0], 0));
+    CKS(f(B->groups[j], B->aux[j - 1]));
+    CK(cudaEventRecord(B->aux_ev[j], B->aux[j - 1]));
+  }
+  CKS(f(B->groups[0], cs));
+  for (size_t j = 1; j < ng; ++j) CK(cudaStreamWaitEvent(cs, B->aux_ev[j], 0));
+  return PMG_OK;
+}
+
+// One iteration of the batched flexible CG: each group of one order runs its chain -- the
+// V-cycle, the inner products, the direction update, the outer operator, the CG update --
+// as a branch of its own; then, over every problem, the convergence test, the true residual
+// of the problems that met it and the restart / finish decision.
+pmg_status batch_iteration(pmg_batch* B, cudaStream_t cs, cudaGraphConditionalHandle hc, int in_graph) {
+  const int n = (int)B->h.size();
+  int64_t k = 0;
+  CKS(batch_branches(B, cs, [&](pmg_batch::Group& G, cudaStream_t st) -> pmg_status {
+    CK(vec_batch_launch(VB_CAST_FIRST, G.vec, G.vec_ctas, st));
+    for (const auto& u : G.vdown) CKS(batch_sub(u, st));
+    CKS(batch_sub(G.coarse, st));
+    for (const auto& u : G.vup) CKS(batch_sub(u, st));
+    CK(vec_batch_launch(VB_RZ, G.vec, G.vec_ctas, st));
+    CK(vec_batch_launch(VB_P_UPDATE, G.vec, G.vec_ctas, st));
+    CKS(batch_sub(G.dot, st));
+    CK(vec_batch_launch(VB_CG_UPDATE, G.vec, G.vec_ctas, st));
+    k += 6 + 3 + (int64_t)(G.vdown.size() + G.vup.size());
+    return PMG_OK;
+  }));
+  CK(batch_cond(B->vec, n, cs));
+  CKS(batch_branches(B, cs, [&](pmg_batch::Group& G, cudaStream_t st) { ++k; return batch_sub(G.res, st); }));
+  CK(batch_confirm(B->vec, n, hc, in_graph, B->any_dev, cs));
+  B->launches_per_iter = k + 2;
+  return PMG_OK;
+}
+
+// The start of a batch solve: inputs, the lifted residual of x = (0, p_D), the initial state.
+pmg_status batch_start(pmg_batch* B, cudaStream_t cs) {
+  CK(vec_batch_launch(VB_INIT, B->vec, B->vec_ctas, cs));
+  CKS(batch_branches(B, cs, [&](pmg_batch::Group& G, cudaStream_t st) { return batch_sub(G.res0, st); }));
+  CK(batch_state_init(B->vec, (int)B->h.size(), cs));
+  return PMG_OK;
+}
+
+pmg_status batch_build_graph(pmg_batch* B) {
+  if (!B->tables_built) {
+    CKS(batch_build_tables(B));
+    B->tables_built = true;
+  }
+  CK(cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  CK(cudaGraphCreate(&g, 0));
+  struct GraphDel { cudaGraph_t g; ~GraphDel() { if (g) cudaGraphDestroy(g); } } del{g};
+  cudaGraphConditionalHandle hc;
+  CK(cudaGraphConditionalHandleCreate(&hc, g, 1, cudaGraphCondAssignDefault));
+  cudaGraph_t out = nullptr;
+  // start: inputs, the lifted residual of x = (0, p_D), the initial state
+  CK(cudaStreamBeginCaptureToGraph(B->cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  pmg_status s = batch_start(B, B->cap);
+  cudaError_t e = cudaStreamEndCapture(B->cap, &out);
+  if (s != PMG_OK) return s;
+  CK(e);
+  B->launches_init = 2 + (int64_t)B->groups.size();
+  size_t nn = 0;
+  CK(cudaGraphGetNodes(g, nullptr, &nn));
+  std::vector<cudaGraphNode_t> nodes(nn), leaves;
+  CK(cudaGraphGetNodes(g, nodes.data(), &nn));
+  for (cudaGraphNode_t nd : nodes) {
+    size_t kk = 0;
+    CK(cudaGraphNodeGetDependentNodes(nd, nullptr, nullptr, &kk));
+    if (kk == 0) leaves.push_back(nd);
+  }
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = hc;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cn;
+  CK(cudaGraphAddNode(&cn, g, leaves.data(), nullptr, leaves.size(), &cp));
+  cudaGraph_t bodyg = cp.conditional.phGraph_out[0];
+  CK(cudaStreamBeginCaptureToGraph(B->cap, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  s = batch_iteration(B, B->cap, hc, 1);
+  e = cudaStreamEndCapture(B->cap, &out);
+  if (s != PMG_OK) return s;
+  CK(e);
+  CK(cudaGraphInstantiate(&B->exec, g, 0));
+  B->graph_built = true;
+  return PMG_OK;
+}
+
+pmg_status batch_solve_graph(pmg_batch* B, const double* const* bv, const double* const* pdv, double* const* pout,
+                             pmg_solve_info* infos, cudaStream_t cs) {
+  const int n = (int)B->h.size();
+  auto t0 = std::chrono::steady_clock::now();
+  DeviceGuard dg(B->h[0]->device);
+  if (!B->eager && !B->graph_built) CKS(batch_build_graph(B));
+  if (B->eager && !B->tables_built) {
+    CKS(batch_build_tables(B));
+    B->tables_built = true;
+  }
+  for (int i = 0; i < n; ++i) B->io_host[i] = BatchIO{bv[i], pdv[i], pout[i]};
+  CK(cudaMemcpyAsync(B->io, B->io_host, n * sizeof(BatchIO), cudaMemcpyHostToDevice, cs));
+  if (!B->eager) {
+    CK(cudaGraphLaunch(B->exec, cs));
+  } else {
+    // the same launches, the loop driven by the host (one synchronisation per iteration)
+    CKS(batch_start(B, cs));
+    int cap = 0;
+    for (pmg_handle* h : B->h) cap = std::max(cap, 2 * h->opts.max_iter + 2);
+    for (int it = 0; it < cap; ++it) {
+      CKS(batch_iteration(B, cs, cudaGraphConditionalHandle{}, 0));
+      CK(cudaMemcpyAsync(B->any_host, B->any_dev, sizeof(int), cudaMemcpyDeviceToHost, cs));
+      CK(cudaStreamSynchronize(cs));
+      if (!*B->any_host) break;
+    }
+  }
+  CK(vec_batch_launch(VB_COPY_OUT, B->vec, B->vec_ctas, cs));
+  CK(cudaMemcpyAsync(B->st_host, B->state.total, n * sizeof(int), cudaMemcpyDeviceToHost, cs));
+  CK(cudaMemcpyAsync(B->st_host + n, B->state.status, n * sizeof(int), cudaMemcpyDeviceToHost, cs));
+  CK(cudaMemcpyAsync(B->dbl_host, B->state_dbl, 2 * n * sizeof(double), cudaMemcpyDeviceToHost, cs));
+  CK(cudaStreamSynchronize(cs));
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  pmg_status result = PMG_OK;
+  for (int i = 0; i < n; ++i) {
+    pmg_solve_info info{};
+    const double bb = B->dbl_host[i], rr = B->dbl_host[n + i];
+    info.iterations = B->st_host[i];
+    info.rel_residual = bb > 0.0 ? std::sqrt(rr / bb) : 0.0;
+    info.seconds = secs;
+    info.status = B->st_host[n + i];
+    if (info.status == PMG_OK && !(info.rel_residual <= B->h[i]->opts.tol))
+      info.status = std::isfinite(info.rel_residual) ? PMG_ERR_NOT_CONVERGED : PMG_ERR_NONFINITE;
+    if (info.status != PMG_OK && result == PMG_OK) {
+      result = (pmg_status)info.status;
+      fail(result, "a batch problem failed (see its info)");
+    }
+    if (infos) infos[i] = info;
+  }
+  return result;
+}
+
+}  // namespace
 
 // =====================================================================================
 // C ABI
@@ -2578,6 +3016,19 @@ pmg_status pmg_batch_destroy(pmg_batch* b) {
   return PMG_OK;
 }
 
+pmg_status pmg_batch_set_eager(pmg_batch* b, int eager) {
+  if (!b) return fail(PMG_ERR_INVALID, "batch is NULL");
+  b->eager = eager != 0;
+  return PMG_OK;
+}
+
+pmg_status pmg_batch_info(const pmg_batch* b, int* batched, int* launches) {
+  if (!b) return fail(PMG_ERR_INVALID, "batch is NULL");
+  if (batched) *batched = batch_eligible(b) ? 1 : 0;
+  if (launches) *launches = b->graph_built ? (int)b->launches_per_iter : 0;
+  return PMG_OK;
+}
+
 pmg_status pmg_batch_handle(pmg_batch* b, int i, pmg_handle** h) {
   if (!b || !h || i < 0 || i >= (int)b->h.size()) return fail(PMG_ERR_INVALID, "bad batch index");
   *h = b->h[i];
@@ -2590,6 +3041,7 @@ pmg_status pmg_batch_solve(pmg_batch* B, const double* const* bv, const double* 
   int n = (int)B->h.size();
   for (int i = 0; i < n; ++i)
     if (!bv[i] || !pdv[i] || !pout[i]) return fail(PMG_ERR_INVALID, "NULL vector in batch");
+  if (batch_eligible(B)) return batch_solve_graph(B, bv, pdv, pout, infos, (cudaStream_t)stream);
   auto t0 = std::chrono::steady_clock::now();
   cudaStream_t cs = (cudaStream_t)stream;
   CK(cudaEventRecord(B->fork, cs));

@@ -99,6 +99,8 @@ _SIGNATURES = {
     "pmg_batch_destroy": (_I, [_P]),
     "pmg_batch_handle": (_I, [_P, _I, ctypes.POINTER(_P)]),
     "pmg_batch_solve": (_I, [_P, _P, _P, _P, ctypes.POINTER(SolveInfo), _P]),
+    "pmg_batch_info": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "pmg_batch_set_eager": (_I, [_P, _I]),
     "pmg_autotune": (_I, [_P]),
     "pmg_set_wait_limit": (_I, [_P, ctypes.c_int64]),
     "pmg_profile_reset": (_I, [_P, _I]),
@@ -463,7 +465,8 @@ class _BatchMember(Solver):
 
 
 class Batch:
-    """pmg_batch_*: independent problems solved concurrently (one handle each)."""
+    """pmg_batch_*: independent problems solved together (one handle each): one graph of
+    batched launches over all problems, or concurrent per-problem loops (see info())."""
 
     def __init__(self, meshes, **opts):
         lib = load()
@@ -504,3 +507,14 @@ class Batch:
         if raise_on_error and st != PMG_OK:
             _check(st)
         return outs, [infos[i].as_dict() for i in range(n)]
+
+    def set_eager(self, eager=True):
+        """pmg_batch_set_eager: the batched iteration loop driven by the host (profiling)."""
+        _check(load().pmg_batch_set_eager(self._b, int(bool(eager))))
+
+    def info(self):
+        """pmg_batch_info: {"batched": 1 for the single graph of batched launches, 0 for
+        concurrent per-problem loops; "launches": kernel launches per batched iteration}."""
+        b, l = ctypes.c_int(), ctypes.c_int()
+        _check(load().pmg_batch_info(self._b, ctypes.byref(b), ctypes.byref(l)))
+        return {"batched": b.value, "launches": l.value}

@@ -643,7 +643,7 @@ def run_batch(args, ws, rank, local):
     if args.ncu_step:
         # the same launches with the iteration loop on the host (a profiler does not see
         # kernels inside graphs with conditional nodes)
-        B.set_eager(True)
+        B.set_path(1)
         torch.cuda.nvtx.range_push("profiled_step")
         infos = step()
         torch.cuda.synchronize()
@@ -662,6 +662,21 @@ def run_batch(args, ws, rank, local):
     clocks = clk.stop()
     t = sum(a.elapsed_time(b) for a, b in evs) / 1e3
     assert all(i["status"] == 0 and i["rel_residual"] <= 1e-10 for i in infos), infos
+    # the same steps with each problem's own device-side loop on its own stream
+    B.set_path(2)
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    evs2 = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step()
+        e1.record()
+        evs2.append((e0, e1))
+    torch.cuda.synchronize()
+    t_streams = sum(a.elapsed_time(b) for a, b in evs2) / 1e3
+    B.set_path(0)
     # the same handles solved one after another (no concurrency)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
@@ -689,6 +704,7 @@ def run_batch(args, ws, rank, local):
                    "problems": len(probs), "free_dof": nfree, "l2": "inputs larger than L2",
                    "setup_s_incl_autotune": round(t_setup, 2)},
         "batch_path": B.info(),
+        "per_problem_loops_value": nfree * args.steps / t_streams,
         "sequential_value": nfree / t_seq, "batch_speedup_vs_sequential": t_seq / (t / args.steps),
         "rel_err_vs_fp64": {"max": max(errs), "median": float(np.median(errs))},
         "iterations": {"min": min(i["iterations"] for i in infos), "max": max(i["iterations"] for i in infos)},

@@ -419,11 +419,13 @@ pmg_status pmg_batch_solve(pmg_batch* b, const double* const* b_dev, const doubl
  * graph (0 until its first solve has built it).  Any pointer may be NULL.  Host-side read;
  * no counterpart in the paper. */
 pmg_status pmg_batch_info(const pmg_batch* b, int* batched, int* launches);
-/* Profiling aid of the batched path: eager != 0 runs the same launches with the iteration
- * loop driven by the host (one host synchronisation per iteration) instead of the graph's
- * device-side while node, so that a kernel profiler sees every launch.  The results are
- * the same.  No counterpart in the paper. */
-pmg_status pmg_batch_set_eager(pmg_batch* b, int eager);
+/* How later pmg_batch_solve calls run (no counterpart in the paper): path 0 (default) the
+ * single graph of batched launches where the options allow it; 1 the same launches with
+ * the iteration loop driven by the host (one host synchronisation per iteration: a kernel
+ * profiler sees every launch; the same results); 2 each problem's own device-side loop on
+ * its own stream, concurrently (as for options the batched launches do not cover).
+ * PMG_ERR_INVALID for another value. */
+pmg_status pmg_batch_set_path(pmg_batch* b, int path);
 
 /* ---- autotuner ------------------------------------------------------------------------- */
 /* Times the candidate launch configurations on every level of h (CUDA-event timing of

@@ -67,9 +67,12 @@ __device__ __forceinline__ void fdm32_body(const Fdm32Params& p, unsigned char* 
   const Shape s = p.s;
   const int NZ = s.NZ, Nz = s.Nz, NZp = slab_pitch(NZ);
   const int col0 = ex * P;
+  // T1 holds node rows -O .. NZ - 1 + O (row iz at iz + O); the rows beyond the mesh and
+  // the surface row are zero, so the per-element windows need no bounds checks
+  const int T1P = slab_pitch(NZ + 2 * O);
   float* R = reinterpret_cast<float*>(smem_raw);  // [NB][NZp]  input, later U
-  float* T1 = R + NB * NZp;                        // [NB][NZp]
-  float* T3 = T1 + NB * NZp;                       // [Nz][NB][NB] (ez, b, alpha)
+  float* T1 = R + NB * NZp;                        // [NB][T1P]
+  float* T3 = T1 + NB * T1P;                       // [Nz][NB][NB] (ez, b, alpha)
   float* VZ = T3 + Nz * NB * NB;                   // [4][NB][NB]
   float* ID = VZ + 4 * NB * NB;                    // [4][NB][NB] (zc, alpha, beta)
   // x slab: the subdomain columns [NB][NZp], or with RES the stencil columns [3P+1][NZp]
@@ -81,9 +84,6 @@ __device__ __forceinline__ void fdm32_body(const Fdm32Params& p, unsigned char* 
   float* WX = WZ + NZ;                             // [NB] inverse cover counts of the subdomain columns
   float* MZC = WX + NB;                            // [NZ] cx * assembled z weights (RES)
   float* MXC = MZC + (RES ? NZ : 0);               // [NB] cz * assembled x weights (RES)
-  size_t red_off = (((size_t)((2 + 0) * NB * NZp + XCOLS * NZp + Nz * NB * NB + 8 * NB * NB + NZ + NB +
-                              (RES ? NZ + NB : 0)) * sizeof(float)) + 15) & ~(size_t)15;
-  int* s_flag = reinterpret_cast<int*>(smem_raw + red_off);
 
   if (RES) {
     for_slab(XCOLS, NZ, [&](int c, int iz) {
@@ -119,6 +119,12 @@ __device__ __forceinline__ void fdm32_body(const Fdm32Params& p, unsigned char* 
   if (threadIdx.x < NB) {
     int gc = col0 - O + threadIdx.x;
     WX[threadIdx.x] = col_valid(s, gc) ? p.wx[wrap_col(s, gc)] : 0.f;
+  }
+  if constexpr (O > 0) {
+    for (int t = threadIdx.x; t < NB * 2 * O; t += blockDim.x) {
+      const int al = t / (2 * O), k = t - al * (2 * O);
+      T1[al * T1P + (k < O ? k : NZ + k)] = 0.f;  // rows -O..-1 and NZ..NZ-1+O
+    }
   }
   cp_async_wait_all();
   __syncthreads();
@@ -168,7 +174,7 @@ __device__ __forceinline__ void fdm32_body(const Fdm32Params& p, unsigned char* 
       float acc = 0.f;
 #pragma unroll
       for (int a = 0; a < NB; ++a) acc = fmaf(cV32[VX + a * NB + al], rv[a], acc);
-      T1[al * NZp + iz] = acc;
+      T1[al * T1P + iz + O] = acc;
     }
   }
   __syncthreads();
@@ -177,12 +183,10 @@ __device__ __forceinline__ void fdm32_body(const Fdm32Params& p, unsigned char* 
     int ez = t / NB, al = t - ez * NB;
     int zc = (ez == 0 ? 1 : 0) | (ez == Nz - 1 ? 2 : 0);
     const float* idn = ID + (zc * NB + al) * NB;
+    const float* t1 = T1 + al * T1P + ez * P;  // rows ez P - O .. ez P + P + O
     float tz[NB];
 #pragma unroll
-    for (int b = 0; b < NB; ++b) {
-      int iz = ez * P - O + b;
-      tz[b] = (iz >= 0 && iz < NZ - 1) ? T1[al * NZp + iz] : 0.f;
-    }
+    for (int b = 0; b < NB; ++b) tz[b] = t1[b];
     float t2[NB];
     float* out = T3 + (ez * NB) * NB + al;
     if (zc == 0) {
@@ -258,45 +262,35 @@ __device__ __forceinline__ void fdm32_body(const Fdm32Params& p, unsigned char* 
     int a = 2 * O + 1 + c;
     upd(a, iz, U[a * NZp + iz]);
   });
-  // Edge zones of both sides, 2 ZW NZ nodes.  A thread swaps up to K partials into their
-  // slots back to back -- independent atomics in flight together instead of one L2 round
-  // trip per node -- and then finalises those whose partner had already arrived.
+  // Edge zones of both sides (2 ZW node columns): one node row per thread, whose ZW
+  // partials of an edge are swapped into their slots back to back (independent atomics in
+  // flight together) and then finalised where the partner had already arrived.  The surface
+  // row is never updated and its slots are not used.
   {
     const int e_left = ex, e_right = s.periodic ? (ex + 1) % s.Nx : ex + 1;
     const bool sh_left = s.periodic || ex != 0, sh_right = s.periodic || ex + 1 != s.Nx;
-    const int zone = ZW * NZ, total = 2 * zone;
-    constexpr int K = 4;
-    for (int base = threadIdx.x; base < total; base += K * blockDim.x) {
-      unsigned long long old[K];
-      unsigned long long* slot[K];
-      float u[K];
-      int aa[K], zz[K];
+    unsigned long long* const slot0 = xb + (size_t)e_left * ZW * NZ;   // [ZW][NZ] slots of the left edge
+    unsigned long long* const slot1 = xb + (size_t)e_right * ZW * NZ;  // of the right edge
+#pragma unroll 1
+    for (int side = 0; side < 2; ++side) {  // one edge at a time: ZW partials in flight per thread
+      const bool shared = side ? sh_right : sh_left;
+      unsigned long long* const sl = side ? slot1 : slot0;
+      for (int iz = threadIdx.x; iz < NZ - 1; iz += blockDim.x) {
+        unsigned long long old[ZW];
 #pragma unroll
-      for (int k = 0; k < K; ++k) {
-        old[k] = kEmpty64;
-        slot[k] = nullptr;
-        const int idx = base + k * blockDim.x;
-        if (idx >= total) continue;
-        const int side = idx >= zone ? 1 : 0;
-        const int rem = idx - side * zone;
-        const int c = rem / NZ, iz = rem - c * NZ;
-        aa[k] = (side ? P : 0) + c;
-        zz[k] = iz;
-        u[k] = U[aa[k] * NZp + iz];
-        const int e = side ? e_right : e_left;
-        if (side ? sh_right : sh_left) {
-          slot[k] = xb + ((size_t)e * ZW + c) * NZ + iz;
-          old[k] = atomicExch(slot[k], (unsigned long long)__float_as_uint(u[k]));
-        } else if (col_valid(s, e * P - O + c)) {
-          upd(aa[k], iz, u[k]);  // wall: this CTA is the only contributor
+        for (int c = 0; c < ZW; ++c) {
+          const int a = (side ? P : 0) + c;
+          old[c] = kEmpty64;
+          if (shared) old[c] = atomicExch(sl + (size_t)c * NZ + iz, (unsigned long long)__float_as_uint(U[a * NZp + iz]));
+          else if (col_valid(s, col0 - O + a)) upd(a, iz, U[a * NZp + iz]);  // wall: the only contributor
         }
-      }
+        if (!shared) continue;
 #pragma unroll
-      for (int k = 0; k < K; ++k) {
-        if (slot[k] && old[k] != kEmpty64) {  // second to arrive: the sum is complete
-          float tot = u[k] + __uint_as_float((unsigned)old[k]);
-          atomicExch(slot[k], kEmpty64);
-          upd(aa[k], zz[k], tot);
+        for (int c = 0; c < ZW; ++c) {
+          if (old[c] == kEmpty64) continue;
+          atomicExch(sl + (size_t)c * NZ + iz, kEmpty64);  // second to arrive: the sum is complete
+          const int a = (side ? P : 0) + c;
+          upd(a, iz, U[a * NZp + iz] + __uint_as_float((unsigned)old[c]));
         }
       }
     }
@@ -638,8 +632,8 @@ static cudaError_t launch_fdm32z(const Fdm32zParams& prm, int threads, cudaStrea
 
 static size_t fdm32_smem(int P, int O, bool res, const Shape& s) {
   const int NB = P + 1 + 2 * O, XCOLS = res ? 3 * P + 1 : NB;
-  const int NZp = slab_pitch(s.NZ);
-  size_t elems = (size_t)(2 * NB + XCOLS) * NZp + (size_t)s.Nz * NB * NB + 8 * NB * NB + s.NZ + NB +
+  const int NZp = slab_pitch(s.NZ), T1P = slab_pitch(s.NZ + 2 * O);
+  size_t elems = (size_t)(NB + XCOLS) * NZp + (size_t)NB * T1P + (size_t)s.Nz * NB * NB + 8 * NB * NB + s.NZ + NB +
                  (res ? s.NZ + NB : 0);
   return ((elems * sizeof(float) + 15) & ~(size_t)15) + 16;
 }

@@ -1671,7 +1671,8 @@ struct pmg_batch {
     int vec_ctas[VB_COUNT] = {};
   };
   bool graph_built = false, tables_built = false;
-  bool eager = false;           // profiling: the iteration loop driven by the host (pmg_batch_set_eager)
+  int path = 0;                 // pmg_batch_set_path: 0 graph, 1 host-driven loop, 2 per-problem loops
+  bool eager = false;           // path 1: the iteration loop driven by the host
   int* any_dev = nullptr;       // "some problem is still active", written by the confirm kernel
   int* any_host = nullptr;      // pinned copy (host-driven loop)
   std::vector<void*> dev;       // device allocations of the batched path (tables, state, copies)
@@ -1827,10 +1828,16 @@ pmg_status batch_build_tables(pmg_batch* B) {
   // per-problem vector kernel arguments and outer-operator arguments
   std::vector<VecProb> vp(n);
   std::vector<CurvedArgs> dot(n), res0(n), res(n);
-  std::map<int, std::vector<int>> by_fine;  // problems of each fine order (the same level orders)
+  // chains: the problems of one fine order (the same level orders); splitting an order into
+  // chains of 4 problems (more, smaller branches) measured the same throughput at config 4
+  constexpr int kChain = kMaxBatch;
+  std::map<int, std::vector<int>> of_order;
+  for (int i = 0; i < n; ++i) of_order[B->h[i]->lv[0].order].push_back(i);
+  std::map<std::pair<int, int>, std::vector<int>> by_fine;
+  for (auto& kv : of_order)
+    for (size_t k = 0; k < kv.second.size(); ++k) by_fine[{kv.first, (int)(k / kChain)}].push_back(kv.second[k]);
   for (int i = 0; i < n; ++i) {
     pmg_handle* h = B->h[i];
-    by_fine[h->lv[0].order].push_back(i);
     double* bcopy = batch_alloc<double>(B, h->N, e);
     CK(e);
     CK(cudaMemset(h->z32, 0, h->N * sizeof(float)));  // its surface row stays zero
@@ -1891,7 +1898,7 @@ pmg_status batch_build_tables(pmg_batch* B) {
       CK(vec_batch_table(gv.data(), m, B->state, B->io, &G.vec, G.vec_ctas, pi.data()));
       B->dev.push_back(G.vec);
       pmg_batch::Sub u{};
-      u.P = kv.first;
+      u.P = kv.first.first;
       u.threads = 256;
       u.kind = 5;
       CK(curved_batch_table(MODE_DOT, d1.data(), pi.data(), m, B->state.active, &u.table, u.nctas, &u.smem));
@@ -3016,15 +3023,16 @@ pmg_status pmg_batch_destroy(pmg_batch* b) {
   return PMG_OK;
 }
 
-pmg_status pmg_batch_set_eager(pmg_batch* b, int eager) {
-  if (!b) return fail(PMG_ERR_INVALID, "batch is NULL");
-  b->eager = eager != 0;
+pmg_status pmg_batch_set_path(pmg_batch* b, int path) {
+  if (!b || path < 0 || path > 2) return fail(PMG_ERR_INVALID, "batch is NULL or path not 0, 1 or 2");
+  b->path = path;
+  b->eager = path == 1;
   return PMG_OK;
 }
 
 pmg_status pmg_batch_info(const pmg_batch* b, int* batched, int* launches) {
   if (!b) return fail(PMG_ERR_INVALID, "batch is NULL");
-  if (batched) *batched = batch_eligible(b) ? 1 : 0;
+  if (batched) *batched = (b->path != 2 && batch_eligible(b)) ? 1 : 0;
   if (launches) *launches = b->graph_built ? (int)b->launches_per_iter : 0;
   return PMG_OK;
 }
@@ -3041,7 +3049,7 @@ pmg_status pmg_batch_solve(pmg_batch* B, const double* const* bv, const double* 
   int n = (int)B->h.size();
   for (int i = 0; i < n; ++i)
     if (!bv[i] || !pdv[i] || !pout[i]) return fail(PMG_ERR_INVALID, "NULL vector in batch");
-  if (batch_eligible(B)) return batch_solve_graph(B, bv, pdv, pout, infos, (cudaStream_t)stream);
+  if (B->path != 2 && batch_eligible(B)) return batch_solve_graph(B, bv, pdv, pout, infos, (cudaStream_t)stream);
   auto t0 = std::chrono::steady_clock::now();
   cudaStream_t cs = (cudaStream_t)stream;
   CK(cudaEventRecord(B->fork, cs));

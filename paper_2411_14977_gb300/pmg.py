@@ -100,7 +100,7 @@ _SIGNATURES = {
     "pmg_batch_handle": (_I, [_P, _I, ctypes.POINTER(_P)]),
     "pmg_batch_solve": (_I, [_P, _P, _P, _P, ctypes.POINTER(SolveInfo), _P]),
     "pmg_batch_info": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
-    "pmg_batch_set_eager": (_I, [_P, _I]),
+    "pmg_batch_set_path": (_I, [_P, _I]),
     "pmg_autotune": (_I, [_P]),
     "pmg_set_wait_limit": (_I, [_P, ctypes.c_int64]),
     "pmg_profile_reset": (_I, [_P, _I]),
@@ -508,9 +508,10 @@ class Batch:
             _check(st)
         return outs, [infos[i].as_dict() for i in range(n)]
 
-    def set_eager(self, eager=True):
-        """pmg_batch_set_eager: the batched iteration loop driven by the host (profiling)."""
-        _check(load().pmg_batch_set_eager(self._b, int(bool(eager))))
+    def set_path(self, path):
+        """pmg_batch_set_path: 0 one graph of batched launches, 1 the same launches from a
+        host loop (profiling), 2 concurrent per-problem loops."""
+        _check(load().pmg_batch_set_path(self._b, int(path)))
 
     def info(self):
         """pmg_batch_info: {"batched": 1 for the single graph of batched launches, 0 for

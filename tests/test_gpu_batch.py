@@ -80,11 +80,18 @@ def test_batched_graph_uneven_orders_against_oracle():
     for o, o2, i1, i2 in zip(outs, outs2, infos, infos2):
         assert torch.equal(o, o2) and i1["iterations"] == i2["iterations"]
     # the host-driven loop (profiling aid) runs the same launches: the same bits
-    B.set_eager(True)
+    B.set_path(1)
     outs_e, infos_e = B.solve(bs, pds)
-    B.set_eager(False)
+    B.set_path(0)
     for o, o2, i1, i2 in zip(outs, outs_e, infos, infos_e):
         assert torch.equal(o, o2) and i1["iterations"] == i2["iterations"]
+    # the per-problem loops reach the same pressures (their own kernels: not the same bits)
+    B.set_path(2)
+    assert B.info()["batched"] == 0
+    outs_s, infos_s = B.solve(bs, pds)
+    B.set_path(0)
+    for o, ref, info in zip(outs_s, refs, infos_s):
+        assert info["status"] == 0 and np.linalg.norm(n(o) - ref) <= 1e-10 * np.linalg.norm(ref)
     bz = [b.clone() for b in bs]
     bz[2].zero_()
     pz = [p.clone() for p in pds]

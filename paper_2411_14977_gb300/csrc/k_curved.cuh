@@ -111,6 +111,12 @@ __device__ __forceinline__ void tc_contract(TcKind kind, int ntiles, GetB getb, 
 //   W_r = w_j (A U_r + (H - sigma B) U_s),  W_s = w_j ((H - sigma B) U_r + C (1 + s^2) U_s).
 // PZ: polynomial order along sigma when it differs from the order P along x (Sec. 5.1);
 // the x-contractions use P + 1 nodes, the sigma-contractions PZ + 1.
+// Block sum of an accumulator: double-float ones on the FP32 pipe, the others in FP64.
+template <typename T>
+__device__ __forceinline__ double block_acc_sum(const Acc<T>& a, double* red) { return block_sum(a.value(), red); }
+template <>
+__device__ __forceinline__ double block_acc_sum<df64>(const Acc<df64>& a, double* red) { return block_sum_df(a.s, red); }
+
 template <int P, typename T, int MODE, int TC, bool MIX = false, bool BATHY = false, int PZ = P>
 __device__ __forceinline__ void curved_body(const CurvedParams<T>& p, const int ex, const int nblocks) {
   static_assert(TC == 0 || PZ == P, "tensor-core path: equal orders");
@@ -357,12 +363,12 @@ __device__ __forceinline__ void curved_body(const CurvedParams<T>& p, const int 
       for (int iz = threadIdx.x; iz < NZ; iz += blockDim.x) finish(ix, i, iz, take_t(buf + iz), eacc);
     }
     if (MODE == MODE_RESIDUAL || MODE == MODE_DOT) {
-      double v = block_sum(eacc.value(), red);
+      double v = block_acc_sum(eacc, red);
       if (threadIdx.x == 0) p.sc.edgepart[e] = v;
     }
   }
   if (MODE == MODE_RESIDUAL || MODE == MODE_DOT) {
-    double v = block_sum(acc.value(), red);
+    double v = block_acc_sum(acc, red);
     grid_reduce(p.sc, v, nedges, p.result, red, s_flag, ex, nblocks);
   }
 }

@@ -103,13 +103,25 @@ __device__ __forceinline__ void fdm32_body(const Fdm32Params& p, unsigned char* 
       MXC[threadIdx.x] = col_valid(s, gc) ? p.cz * p.mX[wrap_col(s, gc)] : 0.f;
     }
   } else {
-    for_slab(NB, NZ, [&](int a, int iz) {
-      int gc = col0 - O + a;
-      bool ok = col_valid(s, gc) && iz != NZ - 1;
-      size_t g = ok ? (size_t)wrap_col(s, gc) * NZ + iz : 0;
-      cp_async_elem(&R[a * NZp + iz], p.r + g, ok);
-      cp_async_elem(&XS[a * NZp + iz], p.x + g, ok && !p.xzero);
-    });
+    // one node row per thread over the NB subdomain columns of r and x (the surface row and
+    // columns off the mesh read as zero); column offsets computed once per thread
+    unsigned cb[NB];
+    bool cv[NB];
+#pragma unroll
+    for (int a = 0; a < NB; ++a) {
+      cv[a] = col_valid(s, col0 - O + a);
+      cb[a] = cv[a] ? (unsigned)wrap_col(s, col0 - O + a) * (unsigned)NZ : 0u;
+    }
+    for (int iz = threadIdx.x; iz < NZ; iz += blockDim.x) {
+      const bool row = iz != NZ - 1;
+#pragma unroll
+      for (int a = 0; a < NB; ++a) {
+        const bool ok = cv[a] && row;
+        const size_t g = ok ? (size_t)(cb[a] + (unsigned)iz) : 0;
+        cp_async_elem(&R[a * NZp + iz], p.r + g, ok);
+        cp_async_elem(&XS[a * NZp + iz], p.x + g, ok && !p.xzero);
+      }
+    }
   }
   for (int t = threadIdx.x; t < 4 * NB * NB; t += blockDim.x) {
     VZ[t] = p.Vz[t];
@@ -258,10 +270,11 @@ __device__ __forceinline__ void fdm32_body(const Fdm32Params& p, unsigned char* 
   };
   constexpr int ZW = 2 * O + 1;
   unsigned long long* xb = reinterpret_cast<unsigned long long*>(p.sc.xbuf);
-  for_slab(P - 1 - 2 * O, NZ, [&](int c, int iz) {
-    int a = 2 * O + 1 + c;
-    upd(a, iz, U[a * NZp + iz]);
-  });
+  // interior columns (this CTA's subdomain alone covers them): one node row per thread
+  for (int iz = threadIdx.x; iz < NZ - 1; iz += blockDim.x) {
+#pragma unroll
+    for (int a = 2 * O + 1; a < P; ++a) upd(a, iz, U[a * NZp + iz]);
+  }
   // Edge zones of both sides (2 ZW node columns): one node row per thread, whose ZW
   // partials of an edge are swapped into their slots back to back (independent atomics in
   // flight together) and then finalised where the partner had already arrived.  The surface

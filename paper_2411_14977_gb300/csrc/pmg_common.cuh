@@ -66,15 +66,21 @@ __host__ __device__ __forceinline__ df64 df64_from_double(double v) {
 #endif
 }
 #ifdef __CUDA_ARCH__
-// exact FP32 -> FP64 by bit manipulation (normal and zero values)
+// Exact FP32 -> FP64 by integer manipulation of the bits (no FP64-pipe work): normal values
+// rebias the exponent; zero keeps its sign; a denormal m 2^-149 is normalised (its leading
+// bit at 31 - clz(m)); infinities and NaNs take the all-ones exponent.
 __device__ __forceinline__ double df64_f2d(float f) {
   const unsigned u = (unsigned)__float_as_int(f);
-  const unsigned e = (u >> 23) & 0xFFu;
-  if (e == 0u || e == 255u) return (double)f;  // zero, denormal, inf, nan: the rare path
-  const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
-                               ((unsigned long long)(e - 127u + 1023u) << 52) |
-                               ((unsigned long long)(u & 0x7FFFFFu) << 29);
-  return __longlong_as_double((long long)b);
+  const unsigned e = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  unsigned long long de = e - 127u + 1023u, dm = (unsigned long long)m << 29;
+  if (e == 255u) de = 2047u;
+  if (e == 0u) {
+    const int lead = 31 - __clz((int)m);               // 0..22 (unused when m == 0)
+    de = m ? (unsigned long long)(lead - 149 + 1023) : 0ull;
+    dm = m ? ((unsigned long long)(m << (23 - lead)) & 0x7FFFFFull) << 29 : 0ull;
+  }
+  return __longlong_as_double((long long)(sign | (de << 52) | dm));
 }
 #endif
 __host__ __device__ __forceinline__ double df64_to_double(df64 a) {
@@ -275,6 +281,32 @@ struct Acc<df64> {  // inner products of double-float data, accumulated in doubl
   __device__ __forceinline__ void fma(df64 a, df64 b) { s = s + a * b; }
   __device__ __forceinline__ double value() const { return df64_to_double(s); }
 };
+
+// Sum of a double-float over the block on the FP32 pipe (one conversion to FP64 at the end);
+// every thread gets the result.  red: >= 33 doubles of shared memory.
+__device__ __forceinline__ double block_sum_df(df64 v, double* red) {
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    df64 w(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
+    v = v + w;
+  }
+  df64* rd = reinterpret_cast<df64*>(red);  // 33 pairs fit in 33 doubles
+  __syncthreads();
+  if (lane == 0) rd[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    df64 t = lane < nw ? rd[lane] : df64(0.f, 0.f);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      df64 w(__shfl_xor_sync(0xffffffffu, t.hi, o), __shfl_xor_sync(0xffffffffu, t.lo, o));
+      t = t + w;
+    }
+    if (lane == 0) red[32] = df64_to_double(t);
+  }
+  __syncthreads();
+  return red[32];
+}
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll

@@ -117,7 +117,7 @@ typedef struct {
   int sweep_kernel;  /* FP32 Schwarz sweep (constant depth, equal orders): 0 slab CTAs (one  */
                      /* element column each), 1 z-split CTAs (zc element rows of one element */
                      /* column each, halo elements recomputed, slabs staged by TMA bulk      */
-                     /* copies), -1 (default) z-split until pmg_autotune picks by time, or a */
+                     /* copies), -1 (default) slab until pmg_autotune picks by time, or a    */
                      /* z-split shape 1000 zc + threads (zc 1..64, threads 32..256, whole warps) */
 } pmg_opts;
 

@@ -442,7 +442,7 @@ pmg_status build_level(pmg_handle* h, int l) {
   L.order_z = pz;
   L.aniso = pz != p;
   L.fuse_res = h->opts.fuse_residual == 1 && !L.aniso;
-  if (h->opts.sweep_kernel != 0) L.thr_fdm32 = 8128;  // z-split: 8 element rows, 128 threads
+  if (h->opts.sweep_kernel == 1) L.thr_fdm32 = 8128;  // z-split forced: 8 element rows, 128 threads
   if (sweep_code_ok(h->opts.sweep_kernel)) L.thr_fdm32 = h->opts.sweep_kernel;
   if (h->opts.flat_kernel == 1) L.thr_flat32 = -128;
   if (h->opts.flat_kernel == 2) L.thr_flat32 = 11608;  // tiled: 16 element columns x 8 rows

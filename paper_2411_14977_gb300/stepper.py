@@ -48,7 +48,7 @@ def default_filter(P, strength=0.97, beta=8.0):
 
 class WaveTank:
     def __init__(self, workload, dt=None, device="cuda", predictor=None, record=False, guess_policy="residual",
-                 filter=None, filter_stages=False, scheme="rk4", **solver_opts):
+                 filter=None, filter_stages=False, scheme="rk4", guess_smooth=None, **solver_opts):
         if scheme not in ("rk4", "lserk54", "lserk54_mixed"):
             raise ValueError("scheme: rk4, lserk54 or lserk54_mixed")
         self.scheme = scheme
@@ -85,6 +85,13 @@ class WaveTank:
         self.probe_after, self.probe_every = 8, 16
         self._rejected = 0
         self._skipped = 0
+        # guess_smooth = (cutoff, alpha, beta): the predictor's change of the pressure is
+        # passed through this per-element modal low-pass (pmg_filter on a second handle of
+        # the same mesh) before it is used, so that no node-scale roughness reaches x0
+        self.S_smooth = None
+        if guess_smooth is not None:
+            self.S_smooth = pmg.Solver(**workload.mesh_kwargs())
+            self.S_smooth.set_filter(*guess_smooth)
         self.record = record
         self.samples = []                   # (eta, eta_prev, eta_x, p_prev, p) per solve when recording
         self.solve_infos = []
@@ -129,6 +136,17 @@ class WaveTank:
         S.surface_slope(self.etax)
         S.forcing(u, w, B["ux"], B["uz"], B["wx"], B["wz"], self.etax, G, B["Fu"], B["Fw"])
 
+    def smooth_change(self, p, p_prev):
+        """p_prev + F(p - p_prev) with the guess low-pass F (guess_smooth)."""
+        d = p - p_prev
+        out = torch.empty_like(d)
+        self.S_smooth.filter(d, out)
+        return p_prev + out
+
+    def _predict(self, eta):
+        guess = self.predictor.predict(eta, self.eta_p, self.etax, self.p)
+        return guess if self.S_smooth is None else self.smooth_change(guess, self.p)
+
     def _solve(self, eta):
         """Pressure solve of the right-hand side in buf["b"] on the operator set last, from the
         previous pressure or the predictor's guess; the result replaces self.p."""
@@ -137,10 +155,10 @@ class WaveTank:
         if self.predictor is not None:
             # keep the network's guess only where its residual beats the previous pressure
             if self.guess_policy == "always":
-                x0 = self.predictor.predict(eta, self.eta_p, self.etax, self.p)
+                x0 = self._predict(eta)
             elif self._rejected < self.probe_after or self._skipped + 1 >= self.probe_every:
                 self._skipped = 0
-                guess = self.predictor.predict(eta, self.eta_p, self.etax, self.p)
+                guess = self._predict(eta)
                 r_nn = S.residual_norm(B["b"], self.pD, guess)
                 r_prev = S.residual_norm(B["b"], self.pD, self.p)
                 self.guess_log.append((r_prev, r_nn))

@@ -138,6 +138,7 @@ def test_level_operators_and_transfers(name, flat):
 
 SWEEPS = {"default": dict(), "fused": dict(fuse_residual=1), "slab": dict(sweep_kernel=0),
           "z1x32": dict(sweep_kernel=1032), "z2x64": dict(sweep_kernel=2064), "z3x96": dict(sweep_kernel=3096),
+          "z8x128": dict(sweep_kernel=8128),
           "z16x256": dict(sweep_kernel=16256)}
 
 
@@ -146,8 +147,9 @@ SWEEPS = {"default": dict(), "fused": dict(fuse_residual=1), "slab": dict(sweep_
 def test_smoother(name, sweep):
     """nu = 2 sweeps; FP32 with the residual launched apart or formed inside the sweep kernel
     with the iterate ping-ponged (fused); the split sweeps on slab CTAs (one element column
-    each) or on z-split CTAs of 1, 2, 3 or 16 element rows (the default: 8; ragged last
-    chunks, chunks deeper than the mesh, one warp up to eight warps)."""
+    each) or on z-split CTAs of 1, 2, 3, 8 or 16 element rows (ragged last
+    chunks, chunks deeper than the mesh, one warp up to eight warps; the default is the slab
+    sweep until pmg_autotune picks)."""
     c = case(name, **SWEEPS[sweep])
     H = c.hierarchy()
     rng = np.random.default_rng(3)

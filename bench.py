@@ -68,6 +68,9 @@ def parse():
     ap.add_argument("--filter", default="strong", choices=["strong", "few-percent", "none"],
                     help="cfg5 spectral filter after every step: strong = (P_c 0, alpha -36, beta 8), "
                          "few-percent = (P_c P-2, S(P) 0.97, beta 8)")
+    ap.add_argument("--level-costs", action="store_true",
+                    help="cfg2/cfg3: mixed solves with the level sequence cut after each level (finest and "
+                         "coarse kept): time per outer iteration, and with it each level's cost")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graded", action="store_true", help="skip the roofline_graded block (large tank)")
     ap.add_argument("--oracle-one-core-child", action="store_true", help=argparse.SUPPRESS)
@@ -263,7 +266,7 @@ def measured_peaks():
 
 NCU_RECORD = os.path.join(ROOT, "profiles", "ncu_traffic.json")
 CSRC = os.path.join(ROOT, "paper_2411_14977_gb300", "csrc")
-FDM32_SOURCES = ("k_fdm32.cu", "pmg_common.cuh", "pmg_kernels.h")
+FDM32_SOURCES = ("k_fdm32.cu", "k_fdm32.cuh", "pmg_common.cuh", "pmg_kernels.h")
 CURVED_SOURCES = ("k_curved.cuh", "k_apply.cu", "pmg_common.cuh", "pmg_kernels.h")
 
 
@@ -1023,6 +1026,57 @@ def run_kernel_scaling(args, ws, rank, local):
           flush=True)
 
 
+def run_level_costs(args, ws, rank, local):
+    """Cost of each multigrid level per outer iteration: the mixed solve with the level
+    sequence P_0, ..., P_k, 1 for growing k (the finest and the order-1 coarse level always
+    present), each autotuned; the difference of the times per outer iteration of two
+    consecutive sequences is the cost of the level added, as the solve runs it (graph
+    replay, L2-resident).  Also the same with the fused coarse V-cycle switched off."""
+    import torch
+    import paper_2411_14977_gb300.pmg as pmg
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pmg.load(build_if_missing=True)
+    w = workload(args.workload)
+    full = [ox for ox, _ in pmg.level_sequence(**w.mesh_kwargs())]
+    rows = []
+    for k in range(1, len(full)):
+        seq = list(full[:k]) + [1]
+        S = pmg.Solver(**w.mesh_kwargs(), precision=pmg.PMG_MIXED_FP32, level_orders=seq)
+        xc, sr = S.node_coords()
+        F = w.fields(xc, sr)
+        d = {kk: torch.from_numpy(np.ascontiguousarray(F[kk])).to(dev) for kk in ("eta", "u", "w", "pD")}
+        S.set_geometry(d["eta"])
+        S.autotune()
+        b = S.assemble_rhs_div(d["u"], d["w"])
+        p = torch.empty_like(b)
+        rec = {"levels": seq, "fused": S.fused_vcycle_info()}
+        for on in ([0, 1] if rec["fused"]["first_level"] >= 0 else [0]):
+            S.set_fused_vcycle(on)
+            for _ in range(max(args.warmup, 3)):
+                S.solve(b, d["pD"], out=p)
+            torch.cuda.synchronize()
+            st = torch.cuda.current_stream()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for _ in range(args.steps):
+                _, info = S.solve(b, d["pD"], out=p)
+            e1.record(st)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            rec["fused_on" if on else "fused_off"] = {"ms_per_solve": ms, "iterations": info["iterations"],
+                                                      "us_per_iteration": ms * 1e3 / info["iterations"]}
+        rows.append(rec)
+        log(json.dumps(rec))
+        S.close()
+    for a, b2 in zip(rows, rows[1:]):
+        b2["added_level_us_per_iteration"] = (b2["fused_off"]["us_per_iteration"] -
+                                              a["fused_off"]["us_per_iteration"])
+    print(json.dumps({"metric": "us per outer iteration by level sequence (mixed solve, 1e-10)",
+                      "workload": w.name, "full_sequence": list(full), "rows": rows}))
+
+
 def run_variants(args, ws, rank, local):
     """Precision variants of the solve on one tank (config 3: 512 x 32, P = 8): plain FP64
     PCG, FP64 flexible CG around the FP32 V-cycle, FP64 refinement around an inner FP32
@@ -1320,6 +1374,8 @@ def main():
         run_variants(args, ws, rank, local)
     elif args.kernel_scaling:
         run_kernel_scaling(args, ws, rank, local)
+    elif args.level_costs:
+        run_level_costs(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
 

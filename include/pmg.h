@@ -119,6 +119,12 @@ typedef struct {
                      /* column each, halo elements recomputed, slabs staged by TMA bulk      */
                      /* copies), -1 (default) slab until pmg_autotune picks by time, or a    */
                      /* z-split shape 1000 zc + threads (zc 1..64, threads 32..256, whole warps) */
+  int fuse_coarse;   /* mixed precisions: the FP32 V-cycle's levels of order <= 4 and the    */
+                     /* coarse solve run as one cooperative launch (grid barriers between    */
+                     /* the steps, bounded waits: PMG_ERR_TIMEOUT): 1 on where the levels    */
+                     /* qualify (flat constant-depth levels of equal orders, fast-diagonal-   */
+                     /* isation smoother), 0 off (one launch per step), -1 (default) off    */
+                     /* until pmg_autotune measures the fused V-cycle faster                  */
 } pmg_opts;
 
 typedef struct {
@@ -134,7 +140,8 @@ typedef struct pmg_handle pmg_handle;
 /* Fill *opts with the defaults: FP64, PCG, FDM-ASM, flat preconditioner, overlap 1, nu 2,
  * omega 0.8, tol 1e-10, max_iter 500, inner_max 40, inner_tol 1e-5, paper level rule,
  * autotuned kernel families (flat_kernel, sweep_kernel -1), split level residuals,
- * double-float outer operator for the mixed precisions, GMRES restart 30. */
+ * double-float outer operator for the mixed precisions, GMRES restart 30, fused coarse
+ * V-cycle where pmg_autotune finds it faster (fuse_coarse -1). */
 void pmg_default_opts(pmg_opts* opts);
 
 /* ---- host-only queries (no device work; they run without a GPU) ---------------------- */
@@ -190,6 +197,19 @@ pmg_status pmg_level_info(const pmg_handle* h, int level, int* order, int* nx, i
  * fdm32 % 1000 threads per CTA), xfer = transfer CTA size.  Host-side read; any pointer may be NULL.
  * The paper has no counterpart.  PMG_ERR_INVALID for a bad handle or level. */
 pmg_status pmg_level_kernels(const pmg_handle* h, int level, int* flat32, int* fdm32, int* xfer);
+/* Fused coarse V-cycle (pmg_opts.fuse_coarse): *first_level = the first level it covers
+ * (its steps run from there down to the order-1 coarse solve and back up in one
+ * cooperative launch; -1 when the levels do not qualify), *on = 1 while the FP32 V-cycle
+ * uses it, *threads and *ctas_per_sm = its launch shape, us[0], us[1] = the FP32 V-cycle's
+ * microseconds without and with it as pmg_autotune timed them (0 before tuning).  The
+ * paper has no counterpart (a V-cycle step per launch, or many, computes the same Sec. 5
+ * V-cycle).  Host-side read; any pointer may be NULL.  PMG_ERR_INVALID for a bad handle. */
+pmg_status pmg_fused_vcycle_info(const pmg_handle* h, int* first_level, int* on, int* threads, int* ctas_per_sm,
+                                 float* us);
+/* Switches the fused coarse V-cycle on (1) or off (0) for the following solves and
+ * V-cycles, as pmg_autotune leaves it otherwise.  PMG_ERR_INVALID when on = 1 and the
+ * levels do not qualify (pmg_fused_vcycle_info: first_level = -1). */
+pmg_status pmg_set_fused_vcycle(pmg_handle* h, int on);
 /* x* of every node column (NX values) and sigma of every node row (NZ values) of the
  * sigma-domain mesh (Sec. 2.2, LGL nodes per cell, Sec. 4.3); caller-owned host arrays. */
 pmg_status pmg_node_coords(const pmg_handle* h, double* x_cols_host, double* sigma_rows_host);
@@ -486,7 +506,8 @@ enum {
   PMG_K_COARSE = 7,    /* coarse solve (three launches per call)                            */
   PMG_K_VECTOR = 8,    /* Krylov vector kernels and reductions                              */
   PMG_K_SETUP = 9,     /* geometry factors and load vectors                                 */
-  PMG_K_COUNT = 10
+  PMG_K_VCYCLE = 10,   /* fused coarse part of the FP32 V-cycle (one cooperative launch)    */
+  PMG_K_COUNT = 11
 };
 /* Reset the per-class counters of h; timing != 0 also brackets every launch with CUDA
  * events on its stream (adds a small per-launch cost). */

@@ -92,218 +92,31 @@ template cudaError_t fdm_smooth<float>(const FdmArgs&, cudaStream_t);
 // transfers
 // ------------------------------------------------------------------------------------
 template <typename T>
-struct TransferParams {
-  Shape f, c;       // fine and coarse shapes (same cells)
-  const T* in;      // prolong: x_c; restrict: r_f, or b_f when xf is set
-  T* out;
-  const double* J;   // along x: [(Pf+1)][(Pc+1)]
-  const double* Jz;  // along sigma: [(Pfz+1)][(Pcz+1)] (equal orders: J)
-  // restriction of the residual formed in the kernel: r_f = in - A_f xf (flat level operator)
-  const T* xf;
-  T cx, cz;
-  const T* mX;      // [NXf] assembled LGL weights of the fine level
-  const T* mZ;      // [NZf]
-};
-
-// x_f += P x_c
-template <typename T>
-__device__ __forceinline__ void prolong_body(const TransferParams<T>& p, const int ex) {
-  const Shape f = p.f, c = p.c;
-  const int Pf = f.P, Pc = c.P, nf = Pf + 1, nc = Pc + 1;            // along x
-  const int Pfz = f.pz(), Pcz = c.pz(), nfz = Pfz + 1, ncz = Pcz + 1;  // along sigma
-  const int NZf = f.NZ, NZc = c.NZ, NZcp = slab_pitch(NZc), NZfp = slab_pitch(NZf);
-  const bool last = !f.periodic && ex == f.Nx - 1;
-  const int own = last ? nf : Pf;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* Xc = reinterpret_cast<T*>(smem_raw);  // [nc][NZcp]
-  T* Tz = Xc + nc * NZcp;                   // [nc][NZfp]
-  T* Js = Tz + nc * NZfp;                   // [nf][nc]
-  T* Jzs = Js + nf * nc;                    // [nfz][ncz]
-  T* Xf = Jzs + nfz * ncz;                  // [nf][NZfp] fine values of the own columns
-  for_slab(nc, NZc, [&](int k, int iz) { cp_async_elem(&Xc[k * NZcp + iz], p.in + (size_t)wrap_col(c, ex * Pc + k) * NZc + iz, true); });
-  for_slab(own, NZf, [&](int i, int iz) { cp_async_elem(&Xf[i * NZfp + iz], p.out + (size_t)(ex * Pf + i) * NZf + iz, true); });
-  for (int t = threadIdx.x; t < nf * nc; t += blockDim.x) Js[t] = (T)p.J[t];
-  for (int t = threadIdx.x; t < nfz * ncz; t += blockDim.x) Jzs[t] = (T)p.Jz[t];
-  cp_async_wait_all();
-  __syncthreads();
-  for_slab(nc, NZf, [&](int k, int iz) {
-    int ez = min(iz / Pfz, f.Nz - 1), j = iz - ez * Pfz;
-    T acc = T(0);
-    for (int l = 0; l < ncz; ++l) acc += Jzs[j * ncz + l] * Xc[k * NZcp + ez * Pcz + l];
-    Tz[k * NZfp + iz] = acc;
-  });
-  __syncthreads();
-  for_slab(own, NZf, [&](int i, int iz) {
-    if (iz == NZf - 1) return;
-    T acc = T(0);
-    for (int k = 0; k < nc; ++k) acc += Js[i * nc + k] * Tz[k * NZfp + iz];
-    p.out[(size_t)(ex * Pf + i) * NZf + iz] = Xf[i * NZfp + iz] + acc;
-  });
-}
-template <typename T>
 __global__ void __launch_bounds__(512) k_prolong(TransferParams<T> p) {
   prolong_body<T>(p, blockIdx.x);
 }
 
-// r_c = P^T r_f
-template <typename T>
-__device__ __forceinline__ void restrict_body(const TransferParams<T>& p, const int ex) {
-  const Shape f = p.f, c = p.c;
-  const int Pf = f.P, Pc = c.P, nf = Pf + 1, nc = Pc + 1;            // along x
-  const int Pfz = f.pz(), Pcz = c.pz(), nfz = Pfz + 1, ncz = Pcz + 1;  // along sigma
-  const int NZf = f.NZ, NZc = c.NZ, NZfp = slab_pitch(NZf), NZcp = slab_pitch(NZc);
-  const bool left = f.periodic || ex > 0;
-  const bool last = !f.periodic && ex == f.Nx - 1;
-  const int own = last ? nc : Pc;
-  const int ncol = 2 * Pf + 1;  // local fine column q <-> (ex-1) Pf + q
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* Rf = reinterpret_cast<T*>(smem_raw);  // [ncol][NZfp]
-  T* Sz = Rf + ncol * NZfp;                 // [ncol][NZcp]
-  T* Js = Sz + ncol * NZcp;                 // [nf][nc]
-  T* Jzs = Js + nf * nc;                    // [nfz][ncz]
-  T* Xs = Jzs + nfz * ncz;                  // fused: [ncol][NZfp] fine iterate
-  T* MZ = Xs + ncol * NZfp;                 // fused: [NZf] cx * assembled z weights
-  T* MX = MZ + NZf;                         // fused: [ncol] cz * assembled x weights
-  const bool fused = p.xf != nullptr;
-  for (int t = threadIdx.x; t < nf * nc; t += blockDim.x) Js[t] = (T)p.J[t];
-  for (int t = threadIdx.x; t < nfz * ncz; t += blockDim.x) Jzs[t] = (T)p.Jz[t];
-  for_slab(ncol, NZf, [&](int q, int iz) {
-    int gc = (ex - 1) * Pf + q;
-    bool ok = (q >= Pf || left) && (q < 2 * Pf || last) && iz != NZf - 1;
-    cp_async_elem(&Rf[q * NZfp + iz], p.in + (ok ? (size_t)wrap_col(f, gc) * NZf + iz : 0), ok);
-    if (fused) {
-      bool okx = (q >= Pf || left) && iz != NZf - 1;  // x of the left and own elements
-      cp_async_elem(&Xs[q * NZfp + iz], p.xf + (okx ? (size_t)wrap_col(f, gc) * NZf + iz : 0), okx);
-    }
-  });
-  if (fused) {
-    for (int t = threadIdx.x; t < NZf; t += blockDim.x) MZ[t] = p.cx * p.mZ[t];
-    for (int q = threadIdx.x; q < ncol; q += blockDim.x) {
-      int gc = (ex - 1) * Pf + q;
-      MX[q] = (q >= Pf || left) ? p.cz * p.mX[wrap_col(f, gc)] : T(0);
-    }
-  }
-  cp_async_wait_all();
-  __syncthreads();
-  if (fused) {
-    // Rf = b - A_f x on the fine columns the restriction reads: (ex-1)Pf + 1 .. (ex+1)Pf - 1,
-    // and (ex+1)Pf on the wall CTA.  Element 0 of the slab is the left one (absent at a
-    // wall: its stencil is skipped, not only its data zeroed), element 1 the own one.
-    for_slab(ncol, NZf, [&](int q, int iz) {
-      if (iz == NZf - 1 || q == 0 || (q == 2 * Pf && !last) || (q < Pf && !left)) return;
-      int e = q / Pf, li = q - e * Pf;
-      if (e == 2) { e = 1; li = Pf; }
-      T kx = T(0);
-      for (int m = 0; m < nf; ++m) kx += CT<T>::K(cT, Pf, li, m) * Xs[(e * Pf + m) * NZfp + iz];
-      if (li == 0 && e == 1 && left)
-        for (int m = 0; m < nf; ++m) kx += CT<T>::K(cT, Pf, Pf, m) * Xs[m * NZfp + iz];
-      const int ez = min(iz / Pfz, f.Nz - 1), lj = iz - ez * Pfz;
-      const T* col = Xs + q * NZfp;
-      T kz = T(0);
-      for (int m = 0; m < nfz; ++m) kz += CT<T>::K(cT, Pfz, lj, m) * col[ez * Pfz + m];
-      if (lj == 0 && ez > 0)
-        for (int m = 0; m < nfz; ++m) kz += CT<T>::K(cT, Pfz, Pfz, m) * col[(ez - 1) * Pfz + m];
-      Rf[q * NZfp + iz] -= MZ[iz] * kx + MX[q] * kz;
-    });
-    __syncthreads();
-  }
-  for_slab(ncol, NZc, [&](int q, int lc) {
-    T acc = T(0);
-    if (lc != NZc - 1) {
-      int ez = min(lc / Pcz, c.Nz - 1), l = lc - ez * Pcz;
-      const T* col = Rf + q * NZfp;
-      if (l == 0) {
-        acc = col[ez * Pfz];
-        for (int j = 1; j < Pfz; ++j) acc += Jzs[j * ncz + 0] * col[ez * Pfz + j];
-        if (ez > 0)
-          for (int j = 1; j < Pfz; ++j) acc += Jzs[j * ncz + Pcz] * col[(ez - 1) * Pfz + j];
-      } else {
-        for (int j = 1; j < Pfz; ++j) acc += Jzs[j * ncz + l] * col[ez * Pfz + j];
-      }
-    }
-    Sz[q * NZcp + lc] = acc;
-  });
-  __syncthreads();
-  for_slab(own, NZc, [&](int k, int lc) {
-    T acc = T(0);
-    if (lc != NZc - 1) {
-      if (k == 0) {
-        acc = Sz[Pf * NZcp + lc];
-        for (int i = 1; i < Pf; ++i) acc += Js[i * nc + 0] * Sz[(Pf + i) * NZcp + lc];
-        if (left)
-          for (int i = 1; i < Pf; ++i) acc += Js[i * nc + Pc] * Sz[i * NZcp + lc];
-      } else if (k == Pc) {
-        acc = Sz[2 * Pf * NZcp + lc];
-        for (int i = 1; i < Pf; ++i) acc += Js[i * nc + Pc] * Sz[(Pf + i) * NZcp + lc];
-      } else {
-        for (int i = 1; i < Pf; ++i) acc += Js[i * nc + k] * Sz[(Pf + i) * NZcp + lc];
-      }
-    }
-    p.out[(size_t)(ex * Pc + k) * NZc + lc] = acc;
-  });
-}
 template <typename T>
 __global__ void __launch_bounds__(512) k_restrict(TransferParams<T> p) {
   restrict_body<T>(p, blockIdx.x);
 }
 
 template <typename T>
-static TransferParams<T> transfer_params(const TransferArgs& a) {
-  TransferParams<T> p;
-  p.f = a.f;
-  p.c = a.c;
-  p.in = (const T*)a.in;
-  p.out = (T*)a.out;
-  p.J = a.J;
-  p.Jz = a.Jz ? a.Jz : a.J;
-  p.xf = (const T*)a.xf;
-  p.cx = (T)a.cx;
-  p.cz = (T)a.cz;
-  p.mX = (const T*)a.mX;
-  p.mZ = (const T*)a.mZ;
-  return p;
-}
-static size_t transfer_smem(const TransferArgs& a, int restrict_, size_t word) {
-  int nf = a.f.P + 1, nc = a.c.P + 1, nfz = a.f.pz() + 1, ncz = a.c.pz() + 1;
-  int NZfp = slab_pitch(a.f.NZ), NZcp = slab_pitch(a.c.NZ);
-  if (restrict_) {
-    size_t sm = ((size_t)(2 * a.f.P + 1) * (NZfp + NZcp) + nf * nc + nfz * ncz) * word + 16;
-    if (a.xf) sm += ((size_t)(2 * a.f.P + 1) * (NZfp + 1) + a.f.NZ) * word;
-    return sm;
-  }
-  return ((size_t)nc * (NZcp + NZfp) + nf * nc + nfz * ncz + (size_t)nf * NZfp) * word + 16;
-}
-
-template <typename T>
 cudaError_t transfer(const TransferArgs& a, int restrict_, cudaStream_t st) {
-  TransferParams<T> p;
-  p.f = a.f;
-  p.c = a.c;
-  p.in = (const T*)a.in;
-  p.out = (T*)a.out;
-  p.J = a.J;
-  p.Jz = a.Jz ? a.Jz : a.J;
-  p.xf = (const T*)a.xf;
-  p.cx = (T)a.cx;
-  p.cz = (T)a.cz;
-  p.mX = (const T*)a.mX;
-  p.mZ = (const T*)a.mZ;
-  int nf = a.f.P + 1, nc = a.c.P + 1, nfz = a.f.pz() + 1, ncz = a.c.pz() + 1;
-  int NZfp = slab_pitch(a.f.NZ), NZcp = slab_pitch(a.c.NZ);
+  const TransferParams<T> p = transfer_params<T>(a);
+  const size_t sm = transfer_smem(a, restrict_, sizeof(T));
+  const int thr = (a.threads >= 32 && a.threads <= 512) ? a.threads : 256;
   cudaError_t e;
   if (restrict_) {
-    size_t sm = ((size_t)(2 * a.f.P + 1) * (NZfp + NZcp) + nf * nc + nfz * ncz) * sizeof(T) + 16;
-    if (a.xf) sm += ((size_t)(2 * a.f.P + 1) * (NZfp + 1) + a.f.NZ) * sizeof(T);
     static std::atomic<unsigned long long> s_mask{0};
     e = ensure_max_smem(k_restrict<T>, s_mask);
     if (e != cudaSuccess) return e;
-    k_restrict<T><<<a.f.Nx, (a.threads >= 32 && a.threads <= 512) ? a.threads : 256, sm, st>>>(p);
+    k_restrict<T><<<a.f.Nx, thr, sm, st>>>(p);
   } else {
-    size_t sm = ((size_t)nc * (NZcp + NZfp) + nf * nc + nfz * ncz + (size_t)nf * NZfp) * sizeof(T) + 16;
     static std::atomic<unsigned long long> s_mask{0};
     e = ensure_max_smem(k_prolong<T>, s_mask);
     if (e != cudaSuccess) return e;
-    k_prolong<T><<<a.f.Nx, (a.threads >= 32 && a.threads <= 512) ? a.threads : 256, sm, st>>>(p);
+    k_prolong<T><<<a.f.Nx, thr, sm, st>>>(p);
   }
   return cudaGetLastError();
 }

@@ -232,6 +232,46 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsig
 }
 constexpr long long kWaitCyclesDefault = 1ll << 31;  // about one second at 2 GHz
 
+// Grid-wide barrier of a cooperative launch (every CTA resident), on the arrival word
+// bar[0] and the abort word bar[1].  Thread 0 of each CTA adds to the arrival word with
+// release semantics (the CTA barrier before it orders the block's writes): CTA 0 adds
+// 2^31 - (G - 1), every other CTA 1, so the G additions of one barrier sum to 2^31 and the
+// word's top bit flips exactly when the last CTA arrives (its low bits return to their
+// value at the start, zero).  Each CTA then polls with acquire loads until the bit differs
+// from the value its own addition returned, for at most `cycles` SM clock cycles; a poll
+// that gives up raises *flag and the abort word, and every poll that sees the abort word
+// gives up at once.  Returns false (in every thread of the CTA) when the barrier was not
+// completed: the caller leaves the kernel, and the owner clears bar[] before the next
+// launch.
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ bool grid_sync_bounded(unsigned* bar, long long cycles, int* flag) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned add = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1) : 1u;
+    unsigned old;
+    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(bar), "r"(add) : "memory");
+    int ok = 1;
+    const long long t0 = clock64();
+    while (((ld_acquire_gpu(bar) ^ old) & 0x80000000u) == 0) {
+      if (((volatile unsigned*)bar)[1]) { ok = 0; break; }
+      if (clock64() - t0 > cycles) {
+        atomicExch(flag, 1);
+        atomicExch(bar + 1, 1u);
+        ok = 0;
+        break;
+      }
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
 // Calls f(c, iz) for every (c, iz) in [0, ncols) x [0, NZ), spread over the block with
 // consecutive threads on consecutive iz (coalesced on a z-fastest slab); the flattened
 // index advances by blockDim.x per step without an integer division per element.
@@ -478,7 +518,12 @@ inline cudaError_t ensure_max_smem(K kernel, std::atomic<unsigned long long>& ma
   if (e != cudaSuccess) return e;
   unsigned long long bit = 1ull << (dev & 63);
   if (mask.load(std::memory_order_relaxed) & bit) return cudaSuccess;
-  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  // the opt-in bound (227 KB) covers static and dynamic shared memory together
+  cudaFuncAttributes fa{};
+  e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           227 * 1024 - (int)fa.sharedSizeBytes);
   if (e == cudaSuccess) mask.fetch_or(bit);
   return e;
 }

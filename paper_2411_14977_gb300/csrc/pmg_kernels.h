@@ -42,6 +42,8 @@ cudaError_t init_consts_apply_bathy(const ConstTables* host);
 cudaError_t init_consts_apply_aniso(const ConstTables* host);
 cudaError_t init_consts_levels_aniso(const ConstTables* host);
 cudaError_t init_consts_dense(const ConstTables* host);
+cudaError_t init_consts_vtail(const ConstTables* host);
+cudaError_t init_consts_vtail32(const float* table, size_t n, const float* K, size_t nk);
 
 // Layout of the FP32 Schwarz eigenvector table (constant memory of the FP32 smoother):
 // for every (P, O) with 2 <= P <= MAXP and O <= (P-1)/2, eight NB x NB blocks
@@ -246,6 +248,35 @@ struct CoarseArgs {
   double* pcr_buf;     // [Nz][2][NX1] when 2 NX1 doubles exceed the shared-memory budget
 };
 template <typename T> cudaError_t coarse_solve(const CoarseArgs& a, const void* b, void* x, cudaStream_t st);
+
+// Fused coarse V-cycle (k_vtail.cu): the FP32 V-cycle from one level down to the order-1
+// coarse solve and back up in one cooperative launch.  The steps are recorded from the
+// launch-per-step V-cycle: sweeps (slab form, split residual), level residuals (flat,
+// constant depth), restrictions and prolongations, and the coarse solve.
+enum { VT_SWEEP = 0, VT_RESID = 1, VT_RESTRICT = 2, VT_PROLONG = 3, VT_COARSE = 7 };
+constexpr int kVtMaxP = 4;          // highest level order the fused kernel is built for
+constexpr int kVtMaxOps = 160;      // steps of one fused V-cycle (grid barriers between them)
+constexpr int kVtMaxSteps = 64;     // sweeps, residuals and transfers, each
+constexpr int kVtMaxThreads = 256;  // CTA size bound of the fused kernel
+constexpr size_t kVtPcrSmem = 48 * 1024;  // larger cyclic reductions ping-pong in global memory
+struct VtStep {
+  int kind;
+  FdmArgs fdm;       // VT_SWEEP
+  FlatArgs flat;     // VT_RESID
+  TransferArgs xfer; // VT_RESTRICT, VT_PROLONG
+};
+// Builds the device table of a fused V-cycle (owned by the caller, one cudaFree): the
+// steps in order, the coarse solve's arguments with its FP32 right-hand side cb and
+// solution cx, the grid barrier words bar[2] (zero) and the timeout flag.
+// cudaErrorInvalidValue when a step is not of the supported forms.  *smem: dynamic shared
+// memory per CTA.
+cudaError_t vtail_table(const VtStep* steps, int n, const CoarseArgs& co, const void* cb, void* cx, unsigned* bar,
+                        int* timeout_flag, void** table, size_t* smem);
+// CTAs of the fused kernel resident per SM at this CTA size and shared memory
+cudaError_t vtail_occupancy(int threads, size_t smem, int* per_sm);
+// Cooperative launch of `grid` CTAs (at most the resident count times the SMs); every
+// grid barrier waits at most wait_cycles SM clock cycles.
+cudaError_t vtail_launch(const void* table, int grid, int threads, size_t smem, long long wait_cycles, cudaStream_t st);
 
 template <typename TA, typename TB>
 cudaError_t dot(size_t n, const TA* x, const TB* y, double* out, int shift, const Scratch& sc, cudaStream_t st);

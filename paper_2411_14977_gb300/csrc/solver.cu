@@ -104,6 +104,7 @@ pmg_status ensure_constants(int dev) {
   CK(init_consts_apply_aniso(&t));
   CK(init_consts_levels_aniso(&t));
   CK(init_consts_dense(&t));
+  CK(init_consts_vtail(&t));
   {
     std::vector<float> tab(fdm32_table_size(), 0.f);
     for (int P = 2; P <= MAXP; ++P)
@@ -118,6 +119,7 @@ pmg_status ensure_constants(int dev) {
           }
       }
     CK(init_consts_fdm32(tab.data(), tab.size(), &t.Kf[0][0][0], sizeof(t.Kf) / sizeof(float)));
+    CK(init_consts_vtail32(tab.data(), tab.size(), &t.Kf[0][0][0], sizeof(t.Kf) / sizeof(float)));
   }
   g_const_devices.insert(dev);
   return PMG_OK;
@@ -329,6 +331,19 @@ struct pmg_handle {
   double* gm_state = nullptr;  // device GMRES cycle: H [(m+1) m], cs [m], sn [m], g [m+1]
   int* gm_ctr = nullptr;       // device GMRES cycle: j, iteration cap
   double* b_copy = nullptr;    // right-hand side captured by the PDC loop
+  // fused coarse V-cycle (k_vtail.cu): the FP32 V-cycle from level vt_l0 down to the coarse
+  // solve and back up in one cooperative launch
+  int vt_l0 = -1;              // first fused level (-1: the levels do not qualify)
+  bool vt_on = false;          // the FP32 V-cycle uses the fused launch
+  void* vt_tab = nullptr;      // device step table (in allocs)
+  unsigned* vt_bar = nullptr;  // [2] grid barrier words (arrivals, abort)
+  size_t vt_smem = 0;
+  int vt_threads = 128, vt_per_sm = 2, vt_sms = 0;
+  float vt_us[2] = {0.f, 0.f};  // pmg_autotune: FP32 V-cycle microseconds without / with it
+  std::vector<VtStep>* rec = nullptr;  // while set, level steps are recorded here, not launched
+  bool rec_ok = true;          // every recorded step is of a form the fused kernel runs
+  double rec_bytes = 0, rec_flops = 0;  // algorithmic cost of the recorded steps
+  double vt_bytes = 0, vt_flops = 0;    // ... of the fused launch
 
   template <typename T> T* alloc(size_t n, cudaError_t& e) {
     T* d = nullptr;
@@ -757,6 +772,10 @@ template <typename T>
 pmg_status level_residual(pmg_handle* h, int l, const void* b, const void* x, void* y, int residual,
                           cudaStream_t st) {
   LevelDev& L = h->lv[l];
+  if (L.actual && h->rec) {
+    h->rec_ok = false;
+    return PMG_OK;
+  }
   if (L.actual) {  // the actual-geometry operator at the level's order and surface
     CurvedArgs c{};
     c.s = L.s;
@@ -778,6 +797,17 @@ pmg_status level_residual(pmg_handle* h, int l, const void* b, const void* x, vo
   FlatArgs a{L.s, x, b, y, L.var ? 1.0 : h->cx, L.var ? 1.0 : h->cz, L.var ? L.mXd[PI<T>] : L.mX[PI<T>],
              L.mZ[PI<T>], residual, PI<T> ? L.thr_flat32 : 256};
   if (L.var) a.Kx = L.Kx[PI<T>];
+  if (h->rec) {
+    if (L.var || !residual) h->rec_ok = false;
+    const double NR = (double)L.s.NX * L.s.NZ;
+    h->rec_bytes += 3.0 * NR * sizeof(T);
+    h->rec_flops += NR * (4.0 * (L.s.P + 2) + 4.0);
+    VtStep v{};
+    v.kind = VT_RESID;
+    v.flat = a;
+    h->rec->push_back(v);
+    return PMG_OK;
+  }
   double NL = (double)L.s.NX * L.s.NZ;
   Cost c{(residual ? 3.0 : 2.0) * NL * sizeof(T), NL * (4.0 * (L.s.P + 2) + 4.0)};
   return launch(h, PI<T> ? PMG_K_LEVEL32 : PMG_K_LEVEL64, 1, st, c, [&] { return flat_op<T>(a, st); });
@@ -798,6 +828,16 @@ pmg_status level_fdm(pmg_handle* h, int l, const void* r, void* x, int post, cud
   if (PI<T>) {
     a.xout = xout;
     a.xzero = xzero ? 1 : 0;
+  }
+  if (h->rec) {
+    if (L.dense || L.var || L.aniso || fused_b || (xout && xout != x)) h->rec_ok = false;
+    h->rec_bytes += c.bytes;
+    h->rec_flops += c.flops;
+    VtStep v{};
+    v.kind = VT_SWEEP;
+    v.fdm = a;
+    h->rec->push_back(v);
+    return PMG_OK;
   }
   if (L.dense) {
     if (fused_b || (xout && xout != x)) return fail(PMG_ERR_INVALID, "fused sweep with the dense smoother");
@@ -849,7 +889,7 @@ pmg_status level_smooth(pmg_handle* h, int l, const void* b, void* x, int post, 
                         cudaStream_t st) {
   LevelDev& L = h->lv[l];
   const int nu = h->opts.nu;
-  if (PI<T> && L.s.P >= 2 && L.fuse_res) {
+  if (PI<T> && L.s.P >= 2 && L.fuse_res && !h->rec) {
     void* tb = L.t[1];
     void* src = (nu % 2 == 0) ? x : tb;  // buffer read by the first sweep
     if (src != x && !x_zero) {
@@ -895,6 +935,15 @@ pmg_status transfer_op(pmg_handle* h, int l, const void* in, void* out, int rest
     c.bytes += Nf * sizeof(T);
     c.flops += Nf * (4.0 * (pf + 2) + 4.0);
   }
+  if (h->rec) {
+    h->rec_bytes += c.bytes;
+    h->rec_flops += c.flops;
+    VtStep v{};
+    v.kind = restrict_ ? VT_RESTRICT : VT_PROLONG;
+    v.xfer = a;
+    h->rec->push_back(v);
+    return PMG_OK;
+  }
   return launch(h, PMG_K_TRANSFER, 1, st, c, [&] { return transfer<T>(a, restrict_, st); });
 }
 
@@ -907,18 +956,101 @@ Cost coarse_cost(pmg_handle* h) {
               2.0 * (2.0 * c.NX1 * nz * nz + 2.0 * nz * c.NX1 * c.nsteps)};
 }
 
+// The fused coarse V-cycle: levels vt_l0 .. coarsest on lv[vt_l0].b[1] -> lv[vt_l0].x[1].
+pmg_status vtail_run(pmg_handle* h, cudaStream_t st) {
+  const int grid = h->vt_per_sm * h->vt_sms;
+  return launch(h, PMG_K_VCYCLE, 1, st, Cost{h->vt_bytes, h->vt_flops}, [&] {
+    return vtail_launch(h->vt_tab, grid, h->vt_threads, h->vt_smem, h->wait_cycles, st);
+  });
+}
+
+template <typename T>
+pmg_status vcycle(pmg_handle* h, int l, const void* b, void* x, cudaStream_t st);
+
+// Records the FP32 V-cycle from the first level whose order (and every coarser one's) the
+// fused kernel is built for, and uploads the fused kernel's step table.  Levels that do
+// not qualify (varying depth, different orders, dense blocks, re-discretised levels)
+// leave vt_l0 = -1 and the launch-per-step V-cycle in place.  Only the FP32 V-cycle fuses.
+pmg_status vtail_setup(pmg_handle* h) {
+  h->vt_l0 = -1;
+  h->vt_on = false;
+  if (h->vt_tab) {
+    h->allocs.erase(std::find(h->allocs.begin(), h->allocs.end(), h->vt_tab));
+    CK(cudaFree(h->vt_tab));
+    h->vt_tab = nullptr;
+  }
+  const int nl = (int)h->lv.size();
+  if (nl < 2 || h->opts.fuse_coarse == 0) return PMG_OK;
+  int l0 = nl - 1;
+  while (l0 - 1 >= 1 && h->lv[l0 - 1].order <= kVtMaxP && h->lv[l0 - 1].order_z == h->lv[l0 - 1].order) --l0;
+  std::vector<VtStep> steps;
+  h->rec = &steps;
+  h->rec_ok = true;
+  h->rec_bytes = h->rec_flops = 0;
+  pmg_status s = vcycle<float>(h, l0, h->lv[l0].b[1], h->lv[l0].x[1], nullptr);
+  h->rec = nullptr;
+  if (s != PMG_OK) return s;
+  if (!h->rec_ok) return PMG_OK;
+  cudaError_t e;
+  if (!h->vt_bar) {
+    h->vt_bar = h->alloc<unsigned>(4, e);
+    CK(e);
+  }
+  CK(cudaMemset(h->vt_bar, 0, 4 * sizeof(unsigned)));
+  void* tab = nullptr;
+  size_t sm = 0;
+  e = vtail_table(steps.data(), (int)steps.size(), h->coarse, h->lv[nl - 1].b[1], h->lv[nl - 1].x[1], h->vt_bar,
+                  h->status + 2, &tab, &sm);
+  if (e == cudaErrorInvalidValue) return PMG_OK;  // a step of another form
+  CK(e);
+  h->allocs.push_back(tab);
+  h->vt_tab = tab;
+  h->vt_smem = sm;
+  h->vt_l0 = l0;
+  h->vt_bytes = h->rec_bytes;
+  h->vt_flops = h->rec_flops;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&h->vt_sms, cudaDevAttrMultiProcessorCount, dev));
+  int coop = 0;
+  CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  int per_sm = 0;
+  if (coop) CK(vtail_occupancy(h->vt_threads, h->vt_smem, &per_sm));
+  if (per_sm < 1) {  // no cooperative launch of this kernel here
+    h->vt_sms = 0;
+    h->vt_l0 = -1;
+    return PMG_OK;
+  }
+  h->vt_per_sm = std::min(per_sm, h->vt_per_sm);
+  h->vt_on = h->opts.fuse_coarse == 1;
+  return PMG_OK;
+}
+
 template <typename T>
 pmg_status vcycle(pmg_handle* h, int l, const void* b, void* x, cudaStream_t st) {
   int nl = (int)h->lv.size();
   LevelDev& L = h->lv[l];
   size_t NL = (size_t)L.s.NX * L.s.NZ;
-  if (l == nl - 1) return launch(h, PMG_K_COARSE, 3, st, coarse_cost<T>(h), [&] { return coarse_solve<T>(h->coarse, b, x, st); });
+  if (PI<T> && !h->rec && h->vt_on && l == h->vt_l0) return vtail_run(h, st);
+  if (l == nl - 1) {
+    if (h->rec) {
+      const Cost cc = coarse_cost<T>(h);
+      h->rec_bytes += cc.bytes;
+      h->rec_flops += cc.flops;
+      VtStep v{};
+      v.kind = VT_COARSE;
+      h->rec->push_back(v);
+      return PMG_OK;
+    }
+    return launch(h, PMG_K_COARSE, 3, st, coarse_cost<T>(h), [&] { return coarse_solve<T>(h->coarse, b, x, st); });
+  }
   // x = 0 before the first sweep.  The FP32 sweep of constant-memory tables reads a zero
   // iterate as zero without loading it and writes every node below the surface row, so on
   // the handle's own level buffers (surface row zeroed at setup, never written) the clear
   // is implicit; elsewhere (the caller's level-0 output, the generic sweep) it is a memset.
   const bool implicit_zero = PI<T> && l > 0 && !L.var && !L.aniso && !L.dense;
-  if (!implicit_zero) CK(cudaMemsetAsync(x, 0, NL * sizeof(T), st));
+  if (!implicit_zero && h->rec) h->rec_ok = false;
+  else if (!implicit_zero) CK(cudaMemsetAsync(x, 0, NL * sizeof(T), st));
   CKS(level_smooth<T>(h, l, b, x, 0, true, st));
   LevelDev& C = h->lv[l + 1];
   if (L.fuse_restrict) {
@@ -1736,7 +1868,8 @@ static pmg_status plan_levels(const pmg_mesh_desc& m, const pmg_opts& o, std::ve
   if (o.overlap < 0 || o.overlap > MAXO || o.nu < 1 || !(o.omega > 0) || !(o.tol > 0) || o.max_iter < 1 ||
       o.inner_max < 1 || !(o.inner_tol > 0) || o.fuse_residual < -1 || o.fuse_residual > 1 || o.df64_outer < -1 ||
       o.df64_outer > 1 || o.flat_kernel < -1 || (o.flat_kernel > 2 && !flat_tile_code_ok(o.flat_kernel)) ||
-      o.sweep_kernel < -1 || (o.sweep_kernel > 1 && !sweep_code_ok(o.sweep_kernel)))
+      o.sweep_kernel < -1 || (o.sweep_kernel > 1 && !sweep_code_ok(o.sweep_kernel)) || o.fuse_coarse < -1 ||
+      o.fuse_coarse > 1)
     return fail(PMG_ERR_INVALID, "bad solver options");
   const int order_z = m.order_z == 0 ? m.order : m.order_z;
   if (order_z < 1 || order_z > MAXP) return fail(PMG_ERR_INVALID, "order_z must be 0 or in 1..10");
@@ -2196,6 +2329,7 @@ void pmg_default_opts(pmg_opts* o) {
   o->df64_outer = -1;
   o->gmres_restart = 30;
   o->sweep_kernel = -1;
+  o->fuse_coarse = -1;
 }
 
 const char* pmg_last_error(void) { return g_err.c_str(); }
@@ -2370,6 +2504,8 @@ pmg_status pmg_create(const pmg_mesh_desc* mesh, const pmg_opts* opts, pmg_handl
     return bail(fail(PMG_ERR_OOM, "pinned allocation failed"));
   pmg_status s = pmg_set_geometry(h, h->eta, nullptr);
   if (s != PMG_OK) return bail(s);
+  s = vtail_setup(h);
+  if (s != PMG_OK) return bail(s);
   if (cudaDeviceSynchronize() != cudaSuccess) return bail(fail(PMG_ERR_CUDA, "setup failed"));
   *out = h;
   return PMG_OK;
@@ -2408,6 +2544,33 @@ pmg_status pmg_level_kernels(const pmg_handle* h, int level, int* flat32, int* f
   if (flat32) *flat32 = h->lv[level].thr_flat32;
   if (fdm32) *fdm32 = h->lv[level].thr_fdm32;
   if (xfer) *xfer = h->lv[level].thr_xfer;
+  return PMG_OK;
+}
+
+pmg_status pmg_fused_vcycle_info(const pmg_handle* h, int* first_level, int* on, int* threads, int* ctas_per_sm,
+                                 float* us) {
+  CKS(check_handle(h));
+  if (first_level) *first_level = h->vt_l0;
+  if (on) *on = h->vt_on ? 1 : 0;
+  if (threads) *threads = h->vt_threads;
+  if (ctas_per_sm) *ctas_per_sm = h->vt_per_sm;
+  if (us) {
+    us[0] = h->vt_us[0];
+    us[1] = h->vt_us[1];
+  }
+  return PMG_OK;
+}
+
+pmg_status pmg_set_fused_vcycle(pmg_handle* h, int on) {
+  CKS(check_handle(h));
+  if (on != 0 && on != 1) return fail(PMG_ERR_INVALID, "on must be 0 or 1");
+  if (on && h->vt_l0 < 0) return fail(PMG_ERR_INVALID, "the levels do not qualify for the fused V-cycle");
+  if (h->vt_on != (on == 1)) {
+    h->vt_on = on == 1;
+    // captured loops hold the other form of the V-cycle: rebuild on next use
+    for (pmg_handle::Loop* lp : {&h->loop64, &h->loop32, &h->loop_gm, &h->loop_pdc})
+      if (lp->exec) { cudaGraphExecDestroy(lp->exec); lp->exec = nullptr; }
+  }
   return PMG_OK;
 }
 
@@ -2522,6 +2685,7 @@ pmg_status pmg_set_bathymetry(pmg_handle* h, const double* h_dev, void* stream) 
   // graphs captured before hold the constant-depth kernels: rebuild on next use
   for (pmg_handle::Loop* lp : {&h->loop64, &h->loop32, &h->loop_gm, &h->loop_pdc})
     if (lp->exec) { cudaGraphExecDestroy(lp->exec); lp->exec = nullptr; }
+  CKS(vtail_setup(h));  // the levels now vary: back to one launch per step
   return pmg_set_geometry(h, h->eta, stream);
 }
 
@@ -2706,6 +2870,7 @@ pmg_status pmg_solve(pmg_handle* h, const double* b, const double* pD, const dou
   if (h->status_host[2]) {  // a bounded device wait gave up during this solve (or before it)
     result = fail(PMG_ERR_TIMEOUT, "a bounded device-side wait gave up (pmg_set_wait_limit)");
     CK(cudaMemsetAsync(h->status + 2, 0, sizeof(int), st));
+    if (h->vt_bar) CK(cudaMemsetAsync(h->vt_bar, 0, 4 * sizeof(unsigned), st));  // an aborted grid barrier
   }
   CK(cudaMemcpyAsync(p_out, h->x, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
   CK(cudaStreamSynchronize(st));
@@ -2977,6 +3142,37 @@ pmg_status pmg_autotune(pmg_handle* h) {
     h->thr_curved64 = thr;
     return curved<double>(h, 0, h->p, nullptr, h->w, 1, nullptr, cs);
   }, &h->thr_curved64));
+  // fused coarse V-cycle: the step table again (the tuned residual forms change the
+  // recorded steps), then its CTA size and CTAs per SM by timing the whole FP32 V-cycle;
+  // with fuse_coarse = -1 it is switched on only where that V-cycle is faster than with
+  // one launch per step (on a GB300 at config 2 it is not: a grid barrier of the resident
+  // CTAs costs more than the kernel boundary it replaces)
+  CKS(vtail_setup(h));
+  if (h->vt_l0 >= 0 && h->vt_sms > 0) {
+    auto run = [&](int, cudaStream_t cs) { return vcycle<float>(h, 0, h->r32, h->z32, cs); };
+    h->vt_on = false;
+    float us_off = 0.f;
+    CKS(time_launches(h, run, 0, 10, &us_off));
+    float best = 1e30f;
+    int bt = h->vt_threads, bp = h->vt_per_sm;
+    for (int thr : {128, 256}) {
+      int occ = 0;
+      CK(vtail_occupancy(thr, h->vt_smem, &occ));
+      for (int per = 1; per <= std::min(occ, 4); ++per) {
+        h->vt_on = true;
+        h->vt_threads = thr;
+        h->vt_per_sm = per;
+        float us = 0.f;
+        CKS(time_launches(h, run, 0, 10, &us));
+        if (us < best) { best = us; bt = thr; bp = per; }
+      }
+    }
+    h->vt_threads = bt;
+    h->vt_per_sm = bp;
+    h->vt_on = h->opts.fuse_coarse == 1 || best < us_off;
+    h->vt_us[0] = us_off;
+    h->vt_us[1] = best;
+  }
   // graphs built before tuning keep the old sizes: rebuild on next use
   for (pmg_handle::Loop* lp : {&h->loop64, &h->loop32, &h->loop_gm, &h->loop_pdc})
     if (lp->exec) { cudaGraphExecDestroy(lp->exec); lp->exec = nullptr; }
@@ -2997,6 +3193,9 @@ pmg_status pmg_batch_create(int n, const pmg_mesh_desc* meshes, const pmg_opts* 
     b->h.push_back(h);
     s = pmg_autotune(h);
     if (s != PMG_OK) { delete b; return s; }
+    // the problems' own loops may run side by side on their streams (pmg_batch_set_path
+    // 2): cooperative grids sized to fill the GPU would contend, so they step level by level
+    h->vt_on = false;
     cudaStream_t st;
     cudaEvent_t ev;
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||

@@ -20,7 +20,7 @@ PMG_ACTUAL = 0
 PMG_FLAT_LINEARISED = 1
 
 KERNEL_CLASSES = ["curved64", "curved32", "level64", "level32", "smooth64", "smooth32", "transfer",
-                  "coarse", "vector", "setup"]
+                  "coarse", "vector", "setup", "vcycle_fused"]
 
 STATUS_NAMES = {0: "PMG_OK", 1: "PMG_ERR_INVALID", 2: "PMG_ERR_OOM", 3: "PMG_ERR_CUDA",
                 4: "PMG_ERR_NOT_CONVERGED", 5: "PMG_ERR_NONFINITE", 6: "PMG_ERR_TIMEOUT"}
@@ -44,7 +44,8 @@ class Opts(ctypes.Structure):
                 ("omega", ctypes.c_double), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("inner_max", ctypes.c_int), ("inner_tol", ctypes.c_double), ("nlevels", ctypes.c_int),
                 ("level_orders", ctypes.c_int * 8), ("fuse_residual", ctypes.c_int), ("flat_kernel", ctypes.c_int),
-                ("df64_outer", ctypes.c_int), ("gmres_restart", ctypes.c_int), ("sweep_kernel", ctypes.c_int)]
+                ("df64_outer", ctypes.c_int), ("gmres_restart", ctypes.c_int), ("sweep_kernel", ctypes.c_int),
+                ("fuse_coarse", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -64,6 +65,9 @@ _SIGNATURES = {
                            ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "pmg_level_info": (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "pmg_level_kernels": (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "pmg_fused_vcycle_info": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
+                                   ctypes.POINTER(_I), _P]),
+    "pmg_set_fused_vcycle": (_I, [_P, _I]),
     "pmg_level_sequence": (_I, [ctypes.POINTER(MeshDesc), ctypes.POINTER(Opts), ctypes.POINTER(_I),
                                ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "pmg_basis_tables": (_I, [_I, _I, _P, _P, _P, _P]),
@@ -267,6 +271,19 @@ class Solver:
         f, d, x = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         _check(load().pmg_level_kernels(self._h, level, ctypes.byref(f), ctypes.byref(d), ctypes.byref(x)))
         return {"flat32": f.value, "fdm32": d.value, "xfer": x.value}
+
+    def fused_vcycle_info(self):
+        """{"first_level", "on", "threads", "ctas_per_sm", "us_off", "us_on"} of the fused
+        coarse V-cycle (first_level -1: the levels do not qualify)."""
+        fl, on, thr, per = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        us = (ctypes.c_float * 2)()
+        _check(load().pmg_fused_vcycle_info(self._h, ctypes.byref(fl), ctypes.byref(on), ctypes.byref(thr),
+                                            ctypes.byref(per), ctypes.cast(us, ctypes.c_void_p)))
+        return {"first_level": fl.value, "on": on.value, "threads": thr.value, "ctas_per_sm": per.value,
+                "us_off": us[0], "us_on": us[1]}
+
+    def set_fused_vcycle(self, on):
+        _check(load().pmg_set_fused_vcycle(self._h, int(bool(on))))
 
     def node_coords(self):
         xc = torch.empty(self.NX, dtype=torch.float64)

@@ -1015,6 +1015,15 @@ def run_kernel_scaling(args, ws, rank, local):
             "us": us, "GB/s": 2 * N * 4 / (us * 1e-6) / 1e9, "frac_hbm": 2 * N * 4 / (us * 1e-6) / 1e9 / hbm,
             "shape": St.level_kernels(0)["flat32"]}
         St.close()
+        # the bulk-staged level operator forced (its best CTA size)
+        Sb = pmg.Solver(**w.mesh_kwargs(), precision=pmg.PMG_MIXED_FP32, flat_kernel=3)
+        Sb.set_geometry(torch.as_tensor(np.ascontiguousarray(F["eta"]), dtype=torch.float64, device=dev))
+        Sb.autotune()
+        us = per_launch_us(lambda: Sb.level_apply(0, x32, y32))
+        row["k_flat_bulk level operator (FP32, bulk-staged forced)"] = {
+            "us": us, "GB/s": 2 * N * 4 / (us * 1e-6) / 1e9, "frac_hbm": 2 * N * 4 / (us * 1e-6) / 1e9 / hbm,
+            "shape": Sb.level_kernels(0)["flat32"]}
+        Sb.close()
         rows.append(row)
         log(cx, {k: (round(v["frac_hbm"], 3) if isinstance(v, dict) and "frac_hbm" in v else v) for k, v in row.items()})
         S.close()

@@ -108,7 +108,10 @@ typedef struct {
                      /* levels of equal orders up to 8, others slab) of 16 element columns x  */
                      /* 8 element rows, or a tiled shape given as 10000 + 100 EXT + ZT (EXT   */
                      /* columns of 8, 16 or 32, ZT rows of 4 or 8, EXT ZT a multiple of 32 and */
-                     /* at most 256), -1 (default) slab until pmg_autotune picks by time     */
+                     /* at most 256), 3 slab CTAs of 256 threads whose inputs are staged by   */
+                     /* TMA bulk copies (constant depth, equal orders, 16-byte-aligned        */
+                     /* vectors; others slab), or that shape with 1000 + threads (64..512,   */
+                     /* whole warps), -1 (default) slab until pmg_autotune picks by time     */
   int df64_outer;    /* outer actual-geometry operator (FP64 vectors in and out) computed in */
                      /* double-float arithmetic on the FP32 pipe (48-bit significand): 1 on, */
                      /* 0 off (FP64 pipe), -1 (default) on for the mixed precisions only     */

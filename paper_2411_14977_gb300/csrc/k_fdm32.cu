@@ -39,8 +39,12 @@ cudaError_t init_consts_fdm32(const float* table, size_t n, const float* K, size
 
 namespace pmg {
 
+// CTA-size bound of the slab sweep: up to order 6 at most 256 threads and three CTAs per
+// SM, which caps its registers at 80 (the two slab edges' exchanges in flight together
+// otherwise take 100); higher orders 512.
+template <int P> constexpr int kFdm32MaxThreads = P <= 6 ? 256 : 512;
 template <int P, int O, bool RES>
-__global__ void __launch_bounds__(512) k_fdm32(Fdm32Params p) {
+__global__ void __launch_bounds__(kFdm32MaxThreads<P>, P <= 6 ? 3 : 1) k_fdm32(Fdm32Params p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int ex = blockIdx.x;
   switch (xclass32(p.s, ex)) {
@@ -374,6 +378,7 @@ static cudaError_t launch_fdm32z(const Fdm32zParams& prm, int threads, cudaStrea
 
 template <int P, int O, bool RES>
 static cudaError_t launch_fdm32_pr(const Fdm32Params& prm, int threads, cudaStream_t st) {
+  if (threads > kFdm32MaxThreads<P>) threads = kFdm32MaxThreads<P>;
   size_t sm = fdm32_smem(P, O, RES, prm.s);
   auto k = k_fdm32<P, O, RES>;
   static std::atomic<unsigned long long> s_mask{0};

@@ -248,35 +248,38 @@ __device__ __forceinline__ void fdm32_body(const Fdm32Params& p, unsigned char* 
 #pragma unroll
     for (int a = 2 * O + 1; a < P; ++a) upd(a, iz, U[a * NZp + iz]);
   }
-  // Edge zones of both sides (2 ZW node columns): one node row per thread, whose ZW
-  // partials of an edge are swapped into their slots back to back (independent atomics in
-  // flight together) and then finalised where the partner had already arrived.  The surface
-  // row is never updated and its slots are not used.
+  // Edge zones of both sides (2 ZW node columns): one node row per thread, whose 2 ZW
+  // partials (both edges) are swapped into their slots back to back (independent atomics
+  // in flight together, one round trip to L2 per row) and then finalised where the partner
+  // had already arrived.  The surface row is never updated and its slots are not used.
   {
     const int e_left = ex, e_right = s.periodic ? (ex + 1) % s.Nx : ex + 1;
     const bool sh_left = s.periodic || ex != 0, sh_right = s.periodic || ex + 1 != s.Nx;
     unsigned long long* const slot0 = xb + (size_t)e_left * ZW * NZ;   // [ZW][NZ] slots of the left edge
     unsigned long long* const slot1 = xb + (size_t)e_right * ZW * NZ;  // of the right edge
-#pragma unroll 1
-    for (int side = 0; side < 2; ++side) {  // one edge at a time: ZW partials in flight per thread
-      const bool shared = side ? sh_right : sh_left;
-      unsigned long long* const sl = side ? slot1 : slot0;
-      for (int iz = threadIdx.x; iz < NZ - 1; iz += blockDim.x) {
-        unsigned long long old[ZW];
+    for (int iz = threadIdx.x; iz < NZ - 1; iz += blockDim.x) {
+      unsigned long long old[2][ZW];
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        const bool shared = side ? sh_right : sh_left;
+        unsigned long long* const sl = side ? slot1 : slot0;
 #pragma unroll
         for (int c = 0; c < ZW; ++c) {
           const int a = (side ? P : 0) + c;
-          old[c] = kEmpty64;
-          if (shared) old[c] = atomicExch(sl + (size_t)c * NZ + iz, (unsigned long long)__float_as_uint(U[a * NZp + iz]));
+          old[side][c] = kEmpty64;
+          if (shared) old[side][c] = atomicExch(sl + (size_t)c * NZ + iz, (unsigned long long)__float_as_uint(U[a * NZp + iz]));
           else if (col_valid(s, col0 - O + a)) upd(a, iz, U[a * NZp + iz]);  // wall: the only contributor
         }
-        if (!shared) continue;
+      }
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        unsigned long long* const sl = side ? slot1 : slot0;
 #pragma unroll
         for (int c = 0; c < ZW; ++c) {
-          if (old[c] == kEmpty64) continue;
+          if (old[side][c] == kEmpty64) continue;  // first to arrive, or a wall edge
           atomicExch(sl + (size_t)c * NZ + iz, kEmpty64);  // second to arrive: the sum is complete
           const int a = (side ? P : 0) + c;
-          upd(a, iz, U[a * NZp + iz] + __uint_as_float((unsigned)old[c]));
+          upd(a, iz, U[a * NZp + iz] + __uint_as_float((unsigned)old[side][c]));
         }
       }
     }

@@ -38,8 +38,10 @@ cudaError_t flat_op(const FlatArgs& a, cudaStream_t st) {
   p.mZ = (const T*)a.mZ;
   p.residual = a.residual;
   p.Kx = (const T*)a.Kx;
+  p.wait_cycles = a.wait_cycles;
+  p.timeout_flag = a.timeout_flag;
   int thr = (a.threads >= 32 && a.threads <= 512) ? a.threads : (a.threads <= -32 && a.threads >= -256) ? a.threads
-            : flat_tile_code_ok(a.threads) ? a.threads : 256;
+            : (flat_tile_code_ok(a.threads) || flat_bulk_code_ok(a.threads)) ? a.threads : 256;
   switch (a.s.P) {
 #define PMG_CASE(PP) case PP: return p.Kx ? launch_flat_p<PP, T, true>(p, thr, st) : launch_flat_p<PP, T, false>(p, thr, st);
     PMG_CASE(1) PMG_CASE(2) PMG_CASE(3) PMG_CASE(4) PMG_CASE(5)

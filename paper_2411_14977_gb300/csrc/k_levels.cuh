@@ -20,6 +20,8 @@ struct FlatParams {
   const T* mZ;  // [NZ]
   int residual; // 0: y = A x (surface row y = x); 1: y = b - A x (surface row 0)
   const T* Kx;  // VAR: [Nx][n][n] x-stiffness of each element column (cx folded in)
+  long long wait_cycles = 0;    // k_flat_bulk: bound of the mbarrier wait
+  int* timeout_flag = nullptr;  // k_flat_bulk: raised when the wait gives up
 };
 
 // Level operator A = cx K_X (x) M_Z + cz M_X (x) K_Z (the flat level of Sec. 5, a Kronecker
@@ -165,6 +167,143 @@ __device__ __forceinline__ void flat_np_body(const FlatParams<T>& p, const size_
 template <int P, typename T, bool VAR, int PZ = P>
 __global__ void __launch_bounds__(256) k_flat_np(FlatParams<T> p) {
   flat_np_body<P, T, VAR, PZ>(p, blockIdx.x * (size_t)blockDim.x + threadIdx.x);
+}
+
+// The same level operator (FP32, constant depth, equal orders) with the CTA's inputs staged
+// by TMA bulk copies: an element column's x stencil slab -- node columns col0 - P ..
+// col0 + P, z-fastest, i.e. one contiguous run of (2P + 1) NZ floats (two runs where a
+// periodic tank wraps) -- and, for the residual, b on its own columns (one run).  Thread 0
+// widens each run to 16-byte boundaries (the start rounded down, the end rounded up but
+// clipped at the vector's last 16-byte boundary; the clipped tail is read with plain
+// loads), announces the bytes on one mbarrier and issues one cp.async.bulk per run, so a
+// CTA has its whole slab in flight after a handful of instructions.  The wait is bounded
+// (wait_cycles): a CTA that gives up raises *timeout_flag, waits for its copies to land
+// and leaves y unwritten.  Each thread then forms whole output nodes: x stencil along the
+// node row and z stencil along the node column, both from shared memory (the surface row
+// read as zero), written straight to y (consecutive threads, consecutive rows).
+struct FlatBulkRun {
+  long long a0, a1, end;  // copied [a0, a1) by TMA, [a1, end) by plain loads
+  int dst;                // shared-memory float index of global element a0
+};
+__device__ __forceinline__ FlatBulkRun flat_bulk_run(long long start, long long end, long long nal, int dst) {
+  FlatBulkRun r;
+  r.a0 = start & ~3ll;
+  r.a1 = min((end + 3) & ~3ll, nal);
+  if (r.a1 < r.a0) r.a1 = r.a0;
+  r.end = end;
+  r.dst = dst;
+  return r;
+}
+template <int P>
+__global__ void __launch_bounds__(512) k_flat_bulk(FlatParams<float> p) {
+  constexpr int n = P + 1, NC = 2 * P + 1;
+  const Shape s = p.s;
+  const int NZ = s.NZ, Nz = s.Nz;
+  const int ex = blockIdx.x, col0 = ex * P;
+  const bool left = s.periodic || ex > 0;
+  const bool last = !s.periodic && ex == s.Nx - 1;
+  const int own = last ? n : P;
+  const int cb = left ? 0 : P;  // first staged local column (c <-> global col0 - P + c)
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw);
+  int* XO = reinterpret_cast<int*>(smem_raw + 8);  // [NC] shared float index of column c's row 0
+  int* s_misc = XO + NC;                           // [0] ok, [1] b's row-0 index
+  float* S = reinterpret_cast<float*>(smem_raw + ((8 + 4 * (NC + 2) + 15) & ~15));
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    const long long N = (long long)s.NX * NZ, nal = N & ~3ll;
+    // runs of consecutive global columns among the staged ones (at most two: a periodic
+    // tank wraps once), then b's own columns
+    FlatBulkRun run[3];
+    int nrun = 0, dst = 0;
+    int c = cb;
+    while (c < NC) {
+      const int g0 = wrap_col(s, col0 - P + c);
+      int c1 = c + 1;
+      while (c1 < NC && wrap_col(s, col0 - P + c1) == g0 + (c1 - c)) ++c1;
+      run[nrun] = flat_bulk_run((long long)g0 * NZ, (long long)(g0 + c1 - c) * NZ, nal, dst);
+      for (int k = c; k < c1; ++k) XO[k] = dst + (int)((long long)(g0 + k - c) * NZ - run[nrun].a0);
+      dst += (int)(((run[nrun].end - run[nrun].a0) + 3) & ~3ll);
+      ++nrun;
+      c = c1;
+    }
+    for (int k = 0; k < cb; ++k) XO[k] = -1;
+    if (p.residual) {
+      run[nrun] = flat_bulk_run((long long)col0 * NZ, (long long)(col0 + own) * NZ, nal, dst);
+      s_misc[1] = dst + (int)((long long)col0 * NZ - run[nrun].a0);
+      ++nrun;
+    }
+    unsigned total = 0;
+    for (int r = 0; r < nrun; ++r) total += (unsigned)(run[r].a1 - run[r].a0) * 4u;
+    mbar_arrive_expect_tx(bar, total);
+    const int nx = p.residual ? nrun - 1 : nrun;
+    for (int r = 0; r < nrun; ++r) {
+      const float* src = r < nx ? p.x : p.b;
+      if (run[r].a1 > run[r].a0)
+        bulk_load_1d(S + run[r].dst, src + run[r].a0, (unsigned)(run[r].a1 - run[r].a0) * 4u, bar);
+      for (long long g = run[r].a1; g < run[r].end; ++g) S[run[r].dst + (int)(g - run[r].a0)] = src[g];
+    }
+  }
+  // coefficients while the copies fly
+  int xo[n], xl[n];
+  __syncthreads();
+#pragma unroll
+  for (int m = 0; m < n; ++m) {
+    xo[m] = XO[P + m];
+    xl[m] = left ? XO[m] : 0;
+  }
+  if (tid == 0) {
+    const bool ok = mbar_wait_bounded(bar, 0, p.wait_cycles);
+    if (!ok) {
+      atomicExch(p.timeout_flag, 1);
+      mbar_wait_bounded(bar, 0, kWaitCyclesDefault);  // the copies in flight land before exit
+    }
+    s_misc[0] = ok ? 1 : 0;
+  }
+  __syncthreads();
+  if (s_misc[0] == 0) return;
+  (void)mbar_try_wait(bar, 0);  // the phase is complete: each thread acquires the copied data
+  // the surface row of x is read as zero by the stencils
+  for (int c = cb + tid; c < NC; c += blockDim.x) S[XO[c] + NZ - 1] = 0.f;
+  const int bo = s_misc[1];
+  __syncthreads();
+  const float cx = p.cx, cz = p.cz;
+  const size_t base = (size_t)col0 * NZ;
+  for_slab(own, NZ, [&](int i, int iz) {
+    const size_t g = base + (size_t)i * NZ + iz;
+    if (iz == NZ - 1) {
+      p.y[g] = p.residual ? 0.f : p.x[g];
+      return;
+    }
+    float ax = 0.f;
+#pragma unroll
+    for (int m = 0; m < n; ++m) ax = fmaf(CT<float>::K(cT, P, i, m), S[xo[m] + iz], ax);
+    if (i == 0 && left) {
+#pragma unroll
+      for (int m = 0; m < n; ++m) ax = fmaf(CT<float>::K(cT, P, P, m), S[xl[m] + iz], ax);
+    }
+    const float* col = S + XO[P + i];
+    const int ez = min(iz / P, Nz - 1), j = iz - ez * P;
+    float az = 0.f;
+#pragma unroll
+    for (int m = 0; m < n; ++m) az = fmaf(CT<float>::K(cT, P, j, m), col[ez * P + m], az);
+    if (j == 0 && ez > 0) {
+#pragma unroll
+      for (int m = 0; m < n; ++m) az = fmaf(CT<float>::K(cT, P, P, m), col[(ez - 1) * P + m], az);
+    }
+    const float v = cx * p.mZ[iz] * ax + cz * p.mX[col0 + i] * az;
+    p.y[g] = p.residual ? S[bo + i * NZ + iz] - v : v;
+  });
+}
+// shared memory of k_flat_bulk: mbarrier, column table, the staged runs (each widened by
+// at most 3 floats at its start and padded to 16 bytes), b's run
+inline size_t flat_bulk_smem(int P, const Shape& s, int residual) {
+  const size_t NC = 2 * P + 1;
+  const size_t hdr = (8 + 4 * (NC + 2) + 15) & ~(size_t)15;
+  const size_t xs = NC * s.NZ + 2 * 8;
+  const size_t bs = residual ? (size_t)(P + 1) * s.NZ + 8 : 0;
+  return hdr + (xs + bs) * sizeof(float);
 }
 
 // The same level operator tiled: one thread per element, a CTA over EXT element columns x
@@ -319,6 +458,21 @@ static cudaError_t launch_flat_tile(const FlatParams<T>& prm, int code, cudaStre
 
 template <int P, typename T, bool VAR, int PZ = P>
 static cudaError_t launch_flat_p(const FlatParams<T>& prm, int threads, cudaStream_t st) {
+  if (flat_bulk_code_ok(threads)) {
+    if constexpr (!VAR && std::is_same<T, float>::value && PZ == P) {
+      const size_t sm = flat_bulk_smem(P, prm.s, prm.residual);
+      if (prm.timeout_flag && ((uintptr_t)prm.x & 15u) == 0 && (!prm.residual || ((uintptr_t)prm.b & 15u) == 0) &&
+          sm <= 227 * 1024) {
+        auto k = k_flat_bulk<P>;
+        static std::atomic<unsigned long long> s_mask{0};
+        cudaError_t e = ensure_max_smem(k, s_mask);
+        if (e != cudaSuccess) return e;
+        k<<<prm.s.Nx, threads - 1000, sm, st>>>(prm);
+        return cudaGetLastError();
+      }
+    }
+    threads = 256;  // constant-depth FP32 levels of equal orders on aligned vectors only; else slab CTAs
+  }
   if (threads >= 10000) {
     if constexpr (!VAR && std::is_same<T, float>::value && P <= 8 && PZ == P)
       if (flat_tile_code_ok(threads)) return launch_flat_tile<P, T, PZ>(prm, threads, st);

@@ -118,8 +118,17 @@ struct FlatArgs {
   // varying depth: per element column x-stiffness [Nx][P+1][P+1] with cx folded in (then
   // cx = cz = 1 and mX holds the depth-weighted x weights)
   const void* Kx = nullptr;
+  // bulk-staged kernel (flat_bulk_code_ok): bound of its mbarrier wait and the flag it
+  // raises when the wait gives up
+  long long wait_cycles = 0;
+  int* timeout_flag = nullptr;
 };
 template <typename T> cudaError_t flat_op(const FlatArgs& a, cudaStream_t st);
+// Launch code of the bulk-staged FP32 level operator: 1000 + threads per CTA (64..512,
+// whole warps); one CTA per element column, the x slab (and b) staged by TMA bulk copies.
+inline bool flat_bulk_code_ok(int code) {
+  return code >= 1064 && code <= 1512 && code % 32 == 1000 % 32;
+}
 
 // Tiled-variant CTA shapes, coded in the launch parameter as 10000 + 100 EXT + ZT
 // (EXT element columns of 8, 16 or 32; ZT element rows of 4 or 8; at most 256 threads).

@@ -461,7 +461,9 @@ pmg_status build_level(pmg_handle* h, int l) {
   if (sweep_code_ok(h->opts.sweep_kernel)) L.thr_fdm32 = h->opts.sweep_kernel;
   if (h->opts.flat_kernel == 1) L.thr_flat32 = -128;
   if (h->opts.flat_kernel == 2) L.thr_flat32 = 11608;  // tiled: 16 element columns x 8 rows
-  if (flat_tile_code_ok(h->opts.flat_kernel)) L.thr_flat32 = h->opts.flat_kernel;
+  if (h->opts.flat_kernel == 3) L.thr_flat32 = 1256;   // bulk-staged slab CTAs of 256 threads
+  if (flat_tile_code_ok(h->opts.flat_kernel) || flat_bulk_code_ok(h->opts.flat_kernel))
+    L.thr_flat32 = h->opts.flat_kernel;
   L.fuse_restrict = h->opts.fuse_residual == 1 && !L.aniso;
   L.s.P = p;
   L.s.PZ = pz;
@@ -797,6 +799,8 @@ pmg_status level_residual(pmg_handle* h, int l, const void* b, const void* x, vo
   FlatArgs a{L.s, x, b, y, L.var ? 1.0 : h->cx, L.var ? 1.0 : h->cz, L.var ? L.mXd[PI<T>] : L.mX[PI<T>],
              L.mZ[PI<T>], residual, PI<T> ? L.thr_flat32 : 256};
   if (L.var) a.Kx = L.Kx[PI<T>];
+  a.wait_cycles = h->wait_cycles;
+  a.timeout_flag = h->status + 2;
   if (h->rec) {
     if (L.var || !residual) h->rec_ok = false;
     const double NR = (double)L.s.NX * L.s.NZ;
@@ -1867,7 +1871,8 @@ static pmg_status plan_levels(const pmg_mesh_desc& m, const pmg_opts& o, std::ve
     return fail(PMG_ERR_INVALID, "levels on the actual geometry need equal orders along x and sigma");
   if (o.overlap < 0 || o.overlap > MAXO || o.nu < 1 || !(o.omega > 0) || !(o.tol > 0) || o.max_iter < 1 ||
       o.inner_max < 1 || !(o.inner_tol > 0) || o.fuse_residual < -1 || o.fuse_residual > 1 || o.df64_outer < -1 ||
-      o.df64_outer > 1 || o.flat_kernel < -1 || (o.flat_kernel > 2 && !flat_tile_code_ok(o.flat_kernel)) ||
+      o.df64_outer > 1 || o.flat_kernel < -1 ||
+      (o.flat_kernel > 3 && !flat_tile_code_ok(o.flat_kernel) && !flat_bulk_code_ok(o.flat_kernel)) ||
       o.sweep_kernel < -1 || (o.sweep_kernel > 1 && !sweep_code_ok(o.sweep_kernel)) || o.fuse_coarse < -1 ||
       o.fuse_coarse > 1)
     return fail(PMG_ERR_INVALID, "bad solver options");
@@ -3052,17 +3057,21 @@ pmg_status pmg_autotune(pmg_handle* h) {
     // 10000 + 100 element columns + element rows; constant depth, equal orders up to 8)
     if (!L.actual) {
       const std::vector<int> slab{64, 128, 192, 256, 320, 384, 512}, np{-64, -128, -256},
-          tile{10804, 10808, 11604, 11608, 13204, 13208};
+          tile{10804, 10808, 11604, 11608, 13204, 13208}, bulk{1128, 1192, 1256, 1384, 1512};
       const bool tile_ok = !L.var && !L.aniso && L.order <= 8;
+      const bool bulk_ok = !L.var && !L.aniso;
       const int fk = h->opts.flat_kernel;
-      std::vector<int> cands = fk == 1 ? np : fk == 0 ? slab : (fk == 2 && tile_ok) ? tile : slab;
+      std::vector<int> cands = fk == 1 ? np : fk == 0 ? slab : (fk == 2 && tile_ok) ? tile : (fk == 3 && bulk_ok) ? bulk : slab;
       if (fk >= 10000) cands = tile_ok ? std::vector<int>{fk} : slab;
+      if (flat_bulk_code_ok(fk)) cands = bulk_ok ? std::vector<int>{fk} : slab;
       if (fk == -1) {
         cands.insert(cands.end(), np.begin(), np.end());
         if (tile_ok) cands.insert(cands.end(), tile.begin(), tile.end());
+        if (bulk_ok) cands.insert(cands.end(), bulk.begin(), bulk.end());
       }
       // a forced kernel family tunes (and caches) apart from the free choice
-      const int key = L.order + 100 * (L.aniso ? L.order_z : 0) + (fk >= 10000 ? 100 * fk : fk >= 0 ? 10000 * (fk + 1) : 0);
+      const int key = L.order + 100 * (L.aniso ? L.order_z : 0) +
+                      (fk >= 1000 ? 100 * fk : fk >= 0 ? 10000 * (fk + 1) : 0);
       CKS(tune_one(h, L.var ? TK_FLAT32V : TK_FLAT32, key, L.s.NZ,
                    [&](int thr, cudaStream_t cs) {
         L.thr_flat32 = thr;
@@ -3084,7 +3093,9 @@ pmg_status pmg_autotune(pmg_handle* h) {
     {
       // slab CTAs of 64..512 threads, or z-split CTAs (codes 1000 zc + threads) of zc
       // element rows; a forced family tunes (and caches) apart from the free choice
-      const std::vector<int> slab{64, 128, 192, 256, 320, 384, 512};
+      // (up to order 6 the slab sweep is built for at most 256 threads)
+      const std::vector<int> slab = L.order <= 6 ? std::vector<int>{64, 128, 192, 256}
+                                                 : std::vector<int>{64, 128, 192, 256, 320, 384, 512};
       std::vector<int> zsplit;
       for (int zc : {2, 4, 8, 16})
         if (zc <= 2 * L.s.Nz)

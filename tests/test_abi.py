@@ -69,7 +69,10 @@ def test_default_opts():
     (dict(), dict(precision=2, outer=1), "outer = PMG_IR"),
     (dict(), dict(fuse_residual=2), "options"),
     (dict(), dict(df64_outer=3), "options"),
-    (dict(), dict(flat_kernel=3), "options"),
+    (dict(), dict(flat_kernel=4), "options"),
+    (dict(), dict(flat_kernel=1032), "options"),    # bulk-staged with 32 threads
+    (dict(), dict(flat_kernel=1080), "options"),    # not whole warps
+    (dict(), dict(flat_kernel=1544), "options"),
     (dict(), dict(flat_kernel=13216), "options"),   # 32 x 16 = 512 threads
     (dict(), dict(flat_kernel=10404), "options"),   # 4 element columns
     (dict(), dict(flat_kernel=11603), "options"),   # 3 element rows
@@ -109,10 +112,11 @@ def test_null_arguments():
     assert lib.pmg_solve(None, None, None, None, None, None, None) == pmg.PMG_ERR_INVALID
 
 
-@pytest.mark.parametrize("code", [2, 10804, 10808, 11604, 11608, 13204, 13208])
+@pytest.mark.parametrize("code", [2, 10804, 10808, 11604, 11608, 13204, 13208, 3, 1064, 1256, 1512])
 def test_tiled_level_operator_shapes_pass_validation(code):
-    """Every documented tiled shape (pmg_opts.flat_kernel = 2 or 10000 + 100 EXT + ZT) passes
-    the option check; creation then stops only where it needs a device."""
+    """Every documented tiled shape (pmg_opts.flat_kernel = 2 or 10000 + 100 EXT + ZT) and
+    bulk-staged shape (3 or 1000 + threads) passes the option check; creation then stops
+    only where it needs a device."""
     lib = pmg.load()
     m = pmg.MeshDesc(0.0, 1.0, 1.0, 4, 2, 4, 0)
     o = pmg.default_opts()

@@ -172,7 +172,11 @@ __device__ __forceinline__ void curved_body(const CurvedParams<T>& p, const int 
   T* G = Wr + L * nz;                       // [n][NG]
   T* SG = G + NG * n;                       // [NZ] sigma
   T* BB = SG + NZ;                          // [n][NZp] b (MODE_RESIDUAL) or x (MODE_DOT) of the slab
-  size_t red_off = (((size_t)(3 * n * NZp + 2 * L * nz + NG * n + NZ) * sizeof(T)) + 15) & ~(size_t)15;
+  T* RW = BB + n * NZp;                     // [NZ] per row: w_j, w_j sigma, w_j sigma^2
+  T* RWS = RW + NZ;
+  T* RWS2 = RWS + NZ;
+  T* GX = RWS2 + NZ;                        // [n] per column: factor 2 x factor 3
+  size_t red_off = (((size_t)(3 * n * NZp + 2 * L * nz + NG * n + 4 * NZ + n) * sizeof(T)) + 15) & ~(size_t)15;
   double* red = reinterpret_cast<double*>(smem_raw + red_off);  // 34 doubles
   int* s_flag = reinterpret_cast<int*>(red + 34);
   T* Y = X;
@@ -189,7 +193,23 @@ __device__ __forceinline__ void curved_body(const CurvedParams<T>& p, const int 
   });
   cp_async_wait_all();
   for (int t = threadIdx.x; t < NG * n; t += blockDim.x) G[t] = from_io<T>(p.geo[(size_t)ex * NG * n + t]);
-  for (int t = threadIdx.x; t < NZ; t += blockDim.x) SG[t] = from_io<T>(p.sigma[t]);
+  for (int t = threadIdx.x; t < NZ; t += blockDim.x) {
+    const T sg = from_io<T>(p.sigma[t]);
+    SG[t] = sg;
+    if constexpr (!MIX && !BATHY && MODE != MODE_DIV) {
+      // the row factors of the metric (phase 3): w_j, w_j sigma, w_j sigma^2
+      const int ez = min(t / PZ, Nz - 1);
+      const T w = CT<T>::w(cT, PZ, t - ez * PZ);
+      const T ws = w * sg;
+      RW[t] = w;
+      RWS[t] = ws;
+      RWS2[t] = ws * sg;
+    }
+  }
+  if constexpr (!MIX && !BATHY && MODE != MODE_DIV) {
+    for (int t = threadIdx.x; t < n; t += blockDim.x) GX[t] = from_io<T>(p.geo[((size_t)ex * n + t) * NG + 2]) *
+                                                           from_io<T>(p.geo[((size_t)ex * n + t) * NG + 3]);
+  }
   __syncthreads();
 
   if constexpr (MODE != MODE_DIV) {
@@ -260,9 +280,12 @@ __device__ __forceinline__ void curved_body(const CurvedParams<T>& p, const int 
         Wr[t] = grr * ur + grs * us;
         Ws[t] = gsr * ur + gss * us;
       } else {
-        T grr = wj * G[i * 4 + 0];
-        T grs = -wj * sg * G[i * 4 + 1];
-        T gss = wj * G[i * 4 + 2] * (T(1) + sg * sg * G[i * 4 + 3]);
+        // grr = w_j g0, grs = -w_j sigma g1, gss = w_j g2 (1 + sigma^2 g3) from the row and
+        // column factors staged above
+        const T rw = RW[iz];
+        T grr = rw * G[i * 4 + 0];
+        T grs = -(RWS[iz] * G[i * 4 + 1]);
+        T gss = rw * G[i * 4 + 2] + RWS2[iz] * GX[i];
         Wr[t] = grr * ur + grs * us;
         Ws[t] = grs * ur + gss * us;
       }
@@ -433,7 +456,7 @@ __global__ void __launch_bounds__(256) k_curved_batch(const CurvedBatch<T, MODE>
 template <typename T>
 static size_t curved_smem(int P, int NZ, int Nz, int ng = 4, int PZ = -1) {
   int n = P + 1, nz = (PZ < 0 ? P : PZ) + 1, NZp = slab_pitch(NZ), L = Nz * n;
-  size_t e = (size_t)3 * n * NZp + (size_t)2 * L * nz + (size_t)ng * n + NZ;
+  size_t e = (size_t)3 * n * NZp + (size_t)2 * L * nz + (size_t)ng * n + 4 * (size_t)NZ + n;
   return ((e * sizeof(T) + 15) & ~(size_t)15) + 34 * sizeof(double) + 16;
 }
 

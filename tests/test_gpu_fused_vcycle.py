@@ -102,7 +102,7 @@ def test_fused_off_by_option_and_default():
     c.S.autotune()
     info = c.S.fused_vcycle_info()
     assert info["us_off"] > 0 and info["us_on"] > 0
-    assert info["on"] == int(info["us_on"] < info["us_off"])
+    assert info["on"] == int(info["us_on"] < 0.97 * info["us_off"])
 
 
 def test_fused_grid_barrier_timeout_reports_and_recovers():

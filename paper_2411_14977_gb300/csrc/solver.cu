@@ -1672,9 +1672,9 @@ void set_last_error(const char* msg) { g_err = msg; }
 namespace {
 
 enum { TK_FLAT32 = 0, TK_FDM32 = 1, TK_XFER = 2, TK_CURVED32 = 3, TK_CURVED64 = 4, TK_FLAT32V = 5,
-       TK_CURVED32B = 6, TK_CURVED64B = 7, TK_COUNT = 8 };
+       TK_CURVED32B = 6, TK_CURVED64B = 7, TK_VTAIL = 8, TK_COUNT = 9 };
 const char* kTuneNames[] = {"flat32", "fdm32", "transfer", "curved32", "curved64", "flat32_depth", "curved32_depth",
-                            "curved64_depth"};
+                            "curved64_depth", "fused_vcycle"};
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int>, int> g_tune;  // (kernel, order, rows, columns) -> threads
 bool g_tune_loaded = false;
@@ -3159,7 +3159,21 @@ pmg_status pmg_autotune(pmg_handle* h) {
   // one launch per step (on a GB300 at config 2 it is not: a grid barrier of the resident
   // CTAs costs more than the kernel boundary it replaces)
   CKS(vtail_setup(h));
-  if (h->vt_l0 >= 0 && h->vt_sms > 0) {
+  // the decision of the free choice (fuse_coarse = -1) is remembered like a CTA size:
+  // 100000 on + 1000 CTAs per SM + threads
+  const auto vkey = std::make_tuple((int)TK_VTAIL, h->mesh.order * 16 + h->vt_l0, h->lv[0].s.NZ, h->mesh.cells_x);
+  int vcached = -1;
+  if (h->vt_l0 >= 0 && h->vt_sms > 0 && h->opts.fuse_coarse == -1) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_cache_load();
+    auto it = g_tune.find(vkey);
+    if (it != g_tune.end()) vcached = it->second;
+  }
+  if (vcached >= 0) {
+    h->vt_on = vcached >= 100000;
+    h->vt_per_sm = (vcached % 100000) / 1000;
+    h->vt_threads = vcached % 1000;
+  } else if (h->vt_l0 >= 0 && h->vt_sms > 0) {
     auto run = [&](int, cudaStream_t cs) { return vcycle<float>(h, 0, h->r32, h->z32, cs); };
     h->vt_on = false;
     float us_off = 0.f;
@@ -3188,6 +3202,12 @@ pmg_status pmg_autotune(pmg_handle* h) {
     h->vt_on = h->opts.fuse_coarse == 1 || best < 0.97f * us_off;
     h->vt_us[0] = us_off;
     h->vt_us[1] = best;
+    if (h->opts.fuse_coarse == -1) {
+      const int code = (h->vt_on ? 100000 : 0) + 1000 * h->vt_per_sm + h->vt_threads;
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_tune[vkey] = code;
+      tune_cache_store(TK_VTAIL, std::get<1>(vkey), std::get<2>(vkey), std::get<3>(vkey), code);
+    }
   }
   // graphs built before tuning keep the old sizes: rebuild on next use
   for (pmg_handle::Loop* lp : {&h->loop64, &h->loop32, &h->loop_gm, &h->loop_pdc})

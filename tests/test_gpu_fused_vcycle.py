@@ -95,8 +95,9 @@ def test_fused_off_by_option_and_default():
     assert info["first_level"] == -1 and info["on"] == 0
     with pytest.raises(pmg.PmgError):
         c.S.set_fused_vcycle(1)
-    # default: built, off until the autotuner measures it faster
-    c = Case(W.tank(12, 3, 6), precision=pmg.PMG_MIXED_FP32)
+    # default: built, off until the autotuner measures it faster (a mesh no other test tunes:
+    # the decision is remembered per mesh shape for the process)
+    c = Case(W.tank(13, 3, 6), precision=pmg.PMG_MIXED_FP32)
     info = c.S.fused_vcycle_info()
     assert info["first_level"] == 1 and info["on"] == 0
     c.S.autotune()

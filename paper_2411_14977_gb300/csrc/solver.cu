@@ -3094,7 +3094,9 @@ pmg_status pmg_autotune(pmg_handle* h) {
       // slab CTAs of 64..512 threads, or z-split CTAs (codes 1000 zc + threads) of zc
       // element rows; a forced family tunes (and caches) apart from the free choice
       // (up to order 6 the slab sweep is built for at most 256 threads)
-      const std::vector<int> slab = L.order <= 6 ? std::vector<int>{64, 128, 192, 256}
+      // (sizes one warp above 64, 128 and 192 let one thread take one node row of the
+      // 65-, 129- and 193-row columns of 32-cell tanks)
+      const std::vector<int> slab = L.order <= 6 ? std::vector<int>{64, 96, 128, 160, 192, 224, 256}
                                                  : std::vector<int>{64, 128, 192, 256, 320, 384, 512};
       std::vector<int> zsplit;
       for (int zc : {2, 4, 8, 16})

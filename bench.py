@@ -76,6 +76,10 @@ def parse():
     ap.add_argument("--oracle-one-core-child", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--ncu-step", action="store_true",
                     help="profiling aid: one warm step, then one step inside the NVTX range 'profiled_step'")
+    ap.add_argument("--ncu-large", action="store_true",
+                    help="profiling aid: three launches each of the finest-level FP32 sweep (slab, 256 threads) and "
+                         "the tiled level operator (8 x 8 elements) on a 9.5M-node tank (8192 x 32 quads, P = 6), "
+                         "no autotuning")
     return ap.parse_args()
 
 
@@ -1035,6 +1039,33 @@ def run_kernel_scaling(args, ws, rank, local):
           flush=True)
 
 
+def run_ncu_large(args, ws, rank, local):
+    """Profiling aid: the finest-level FP32 sweep and the tiled level operator on a tank
+    beyond L2, three launches each with fixed launch shapes, for an ncu capture of one
+    launch (-s 2 -c 1) of either kernel."""
+    import torch
+    import paper_2411_14977_gb300.pmg as pmg
+    import workloads as W
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pmg.load(build_if_missing=True)
+    w = W.tank(8192, 32, 6)
+    S = pmg.Solver(**w.mesh_kwargs(), precision=pmg.PMG_MIXED_FP32, flat_kernel=10808, sweep_kernel=0)
+    xc, sr = S.node_coords()
+    F = w.fields(xc, sr)
+    S.set_geometry(torch.as_tensor(np.ascontiguousarray(F["eta"]), dtype=torch.float64, device=dev))
+    g = torch.Generator(device=dev).manual_seed(W.BASE_SEED + 5)
+    r32 = torch.randn(S.n, dtype=torch.float32, device=dev, generator=g)
+    x32 = torch.randn(S.n, dtype=torch.float32, device=dev, generator=g)
+    y32 = torch.empty(S.n, dtype=torch.float32, device=dev)
+    for _ in range(3):
+        S.level_sweep(0, r32, x32)
+        S.level_apply(0, x32, y32)
+    torch.cuda.synchronize()
+    log("ncu-large:", S.n, "nodes", S.level_kernels(0))
+
+
 def run_level_costs(args, ws, rank, local):
     """Cost of each multigrid level per outer iteration: the mixed solve with the level
     sequence P_0, ..., P_k, 1 for growing k (the finest and the order-1 coarse level always
@@ -1385,6 +1416,8 @@ def main():
         run_kernel_scaling(args, ws, rank, local)
     elif args.level_costs:
         run_level_costs(args, ws, rank, local)
+    elif args.ncu_large:
+        run_ncu_large(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
 

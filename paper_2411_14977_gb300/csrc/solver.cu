@@ -1966,14 +1966,18 @@ pmg_status batch_build_tables(pmg_batch* B) {
   // per-problem vector kernel arguments and outer-operator arguments
   std::vector<VecProb> vp(n);
   std::vector<CurvedArgs> dot(n), res0(n), res(n);
-  // chains: the problems of one fine order (the same level orders); splitting an order into
-  // chains of 4 problems (more, smaller branches) measured the same throughput at config 4
+  // chains: the problems of one fine order (the same level orders) and one column-depth
+  // class (cells_z in 1-8, 9-16, ...: a chain's slab CTAs take one thread per node row of
+  // its deepest column, so shallow tanks do not run in CTAs sized for deep ones); splitting
+  // an order into chains of 4 problems (more, smaller branches) measured the same
+  // throughput at config 4
   constexpr int kChain = kMaxBatch;
-  std::map<int, std::vector<int>> of_order;
-  for (int i = 0; i < n; ++i) of_order[B->h[i]->lv[0].order].push_back(i);
+  std::map<std::pair<int, int>, std::vector<int>> of_order;
+  for (int i = 0; i < n; ++i) of_order[{B->h[i]->lv[0].order, (B->h[i]->mesh.cells_z + 7) / 8}].push_back(i);
   std::map<std::pair<int, int>, std::vector<int>> by_fine;
   for (auto& kv : of_order)
-    for (size_t k = 0; k < kv.second.size(); ++k) by_fine[{kv.first, (int)(k / kChain)}].push_back(kv.second[k]);
+    for (size_t k = 0; k < kv.second.size(); ++k)
+      by_fine[{kv.first.first, 1000 * kv.first.second + (int)(k / kChain)}].push_back(kv.second[k]);
   for (int i = 0; i < n; ++i) {
     pmg_handle* h = B->h[i];
     double* bcopy = batch_alloc<double>(B, h->N, e);

@@ -1139,7 +1139,13 @@ def run_variants(args, ws, rank, local):
                 ("mixed_bf16_ir", dict(precision=pmg.PMG_MIXED_BF16, outer=pmg.PMG_IR)),
                 ("mixed_fp32_fcg_dense_schwarz", dict(precision=pmg.PMG_MIXED_FP32, smoother=pmg.PMG_ASM_DENSE)),
                 ("mixed_fp32_fcg_actual_levels", dict(precision=pmg.PMG_MIXED_FP32, smoother=pmg.PMG_ASM_DENSE,
-                                                      precond_geom=pmg.PMG_ACTUAL))]
+                                                      precond_geom=pmg.PMG_ACTUAL)),
+                # launch structure of the V-cycle: level residuals formed inside the sweeps
+                # and restrictions (always, or where the autotuner times it faster), and the
+                # coarse levels as one cooperative launch
+                ("mixed_fp32_fcg_fused_residuals", dict(precision=pmg.PMG_MIXED_FP32, fuse_residual=1)),
+                ("mixed_fp32_fcg_fused_residuals_tuned", dict(precision=pmg.PMG_MIXED_FP32, fuse_residual=-1)),
+                ("mixed_fp32_fcg_fused_coarse_vcycle", dict(precision=pmg.PMG_MIXED_FP32, fuse_coarse=1))]
     ref = None
     out = {}
     clk = ClockSampler(local)

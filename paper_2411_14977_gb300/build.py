@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libpmg.so")
-SOURCES = ["k_apply_aniso.cu", "k_apply.cu", "k_apply_bathy.cu", "k_apply_tc.cu", "k_levels_aniso.cu", "k_dense.cu", "k_levels.cu", "k_fdm32.cu", "k_vtail.cu", "k_stepper.cu", "k_nn.cu", "k_coarse_vec.cu", "solver.cu",
+SOURCES = ["k_apply_aniso.cu", "k_apply.cu", "k_apply_bathy.cu", "k_apply_tc.cu", "k_levels_aniso.cu", "k_dense.cu", "k_levels.cu", "k_fdm32.cu", "k_fdm32z.cu", "k_fdm32_batch.cu", "k_vtail.cu", "k_stepper.cu", "k_nn.cu", "k_coarse_vec.cu", "solver.cu",
            "warmstart.cu", "noalloc.cu", "host_basis.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

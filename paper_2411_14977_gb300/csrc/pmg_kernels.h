@@ -37,6 +37,8 @@ cudaError_t init_consts_apply(const ConstTables* host);
 cudaError_t init_consts_apply_tc(const ConstTables* host);
 cudaError_t init_consts_levels(const ConstTables* host);
 cudaError_t init_consts_fdm32(const float* table, size_t n, const float* K, size_t nk);
+cudaError_t init_consts_fdm32z(const float* table, size_t n, const float* K, size_t nk);
+cudaError_t init_consts_fdm32b(const float* table, size_t n, const float* K, size_t nk);
 cudaError_t init_consts_stepper(const ConstTables* host);
 cudaError_t init_consts_apply_bathy(const ConstTables* host);
 cudaError_t init_consts_apply_aniso(const ConstTables* host);
@@ -198,6 +200,7 @@ __host__ __device__ inline Fdm32zLayout fdm32z_layout(int P, int O, int zc) {
   return L;
 }
 bool fdm32z_usable(const FdmArgs& a);
+cudaError_t fdm_smooth32z(const FdmArgs& a, cudaStream_t st);  // the z-split sweep (k_fdm32z.cu)
 // A forced z-split sweep shape, coded 1000 zc + threads (1 <= zc <= 64 element rows per
 // CTA, 32..256 threads in whole warps).
 inline bool sweep_code_ok(int code) {

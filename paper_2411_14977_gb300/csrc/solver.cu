@@ -119,6 +119,8 @@ pmg_status ensure_constants(int dev) {
           }
       }
     CK(init_consts_fdm32(tab.data(), tab.size(), &t.Kf[0][0][0], sizeof(t.Kf) / sizeof(float)));
+    CK(init_consts_fdm32z(tab.data(), tab.size(), &t.Kf[0][0][0], sizeof(t.Kf) / sizeof(float)));
+    CK(init_consts_fdm32b(tab.data(), tab.size(), &t.Kf[0][0][0], sizeof(t.Kf) / sizeof(float)));
     CK(init_consts_vtail32(tab.data(), tab.size(), &t.Kf[0][0][0], sizeof(t.Kf) / sizeof(float)));
   }
   g_const_devices.insert(dev);

@@ -1,7 +1,8 @@
 // FP32 fast-diagonalisation Schwarz sweep over one element column (Sec. 5.3): the CTA
-// body shared by the one-launch-per-sweep kernel (k_fdm32.cu) and the fused coarse
-// V-cycle (k_vtail.cu).  The including translation unit defines the constant tables
-// cV32 (per-class eigenvectors, fdm32_offset layout) and cK32 (1D LGL stiffness) first.
+// body shared by the one-launch-per-sweep kernel (k_fdm32.cu), the batched kernel
+// (k_fdm32_batch.cu) and the fused coarse V-cycle (k_vtail.cu).  The including
+// translation unit defines the constant tables cV32 (per-class eigenvectors,
+// fdm32_offset layout) and cK32 (1D LGL stiffness) first.
 #pragma once
 
 namespace pmg {

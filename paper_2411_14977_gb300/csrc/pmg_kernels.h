@@ -174,7 +174,7 @@ struct FdmArgs {
   int* timeout_flag = nullptr;
 };
 
-// Shared-memory layout of the z-split FP32 sweep (k_fdm32.cu), in floats unless noted:
+// Shared-memory layout of the z-split FP32 sweep (k_fdm32z.cu), in floats unless noted:
 // residual rows [NB][RP] (reused for the update U [NB][UP]), iterate rows [NB][XP],
 // x-transformed rows [NB][TP], z-transformed blocks [zc + 2][NB][NB], z eigenvectors and
 // inverse eigenvalue sums [8][NB][NB], row and column weights, then 2 NB + 1 ints and the
@@ -232,7 +232,8 @@ bool aniso_pair_supported(int P, int PZ, bool fine);
 // levels that its semi-coarsening visits
 #define PMG_ANISO_FINE(X) X(2, 8) X(3, 8) X(4, 8) X(5, 8) X(6, 8) X(7, 8) X(9, 8) X(10, 8)
 #define PMG_ANISO_COARSE(X) X(2, 5) X(3, 5) X(4, 5) X(2, 3)
-// FP32 sweep with the eigenvectors in constant memory (k_fdm32.cu)
+// FP32 sweep with the eigenvectors in constant memory (k_fdm32.cu; the z-split form in
+// k_fdm32z.cu, the batched form in k_fdm32_batch.cu)
 cudaError_t fdm_smooth32(const FdmArgs& a, cudaStream_t st);
 
 struct TransferArgs {

@@ -506,7 +506,7 @@ enum {
   PMG_K_SMOOTH64 = 4,  /* Schwarz smoother sweep, FP64                                      */
   PMG_K_SMOOTH32 = 5,  /* Schwarz smoother sweep, FP32                                      */
   PMG_K_TRANSFER = 6,  /* restriction and prolongation (both precisions)                    */
-  PMG_K_COARSE = 7,    /* coarse solve (two launches per call)                              */
+  PMG_K_COARSE = 7,    /* coarse solve (three launches per call)                            */
   PMG_K_VECTOR = 8,    /* Krylov vector kernels and reductions                              */
   PMG_K_SETUP = 9,     /* geometry factors and load vectors                                 */
   PMG_K_VCYCLE = 10,   /* fused coarse part of the FP32 V-cycle (one cooperative launch)    */

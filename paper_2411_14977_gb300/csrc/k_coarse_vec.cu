@@ -19,18 +19,15 @@
 
 namespace pmg {
 
-// One CTA per vertical mode k: the forward transform of the mode, rhat[k][ix] for every
-// node column ix (the same sums, in the same order, as coarse_fwd_body), then its cyclic
-// reduction.  Each mode reads all of b (L2-resident at the coarse level) and no other
-// mode's data, so the two steps share one launch.
 template <typename T>
-__global__ void k_coarse_fwd_pcr(int n, int NZ1, int nsteps, int periodic, const T* b, const double* V,
-                                 const double* coef, const double* inv, double* rhat, double* gbuf) {
+__global__ void k_coarse_fwd(int NX1, int NZ1, const T* b, const double* V, double* rhat) {
+  coarse_fwd_body<T>(NX1, NZ1, b, V, rhat, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+__global__ void k_coarse_pcr(int n, int nsteps, int periodic, const double* coef, const double* inv,
+                             double* rhat, double* gbuf) {
   extern __shared__ double sbuf[];
-  const int k = blockIdx.x, Nz = NZ1 - 1;
-  for (int ix = threadIdx.x; ix < n; ix += blockDim.x) coarse_fwd_body<T>(n, NZ1, b, V, rhat, ix * Nz + k);
-  __syncthreads();
-  coarse_pcr_body(n, nsteps, periodic, coef, inv, rhat, gbuf, k, sbuf);
+  coarse_pcr_body(n, nsteps, periodic, coef, inv, rhat, gbuf, blockIdx.x, sbuf);
 }
 
 template <typename T>
@@ -41,7 +38,8 @@ __global__ void k_coarse_bwd(int NX1, int NZ1, const double* V, const double* uh
 template <typename T>
 cudaError_t coarse_solve(const CoarseArgs& a, const void* b, void* x, cudaStream_t st) {
   int Nz = a.NZ1 - 1;
-  int bs = 256;
+  int tot = a.NX1 * Nz, bs = 256;
+  k_coarse_fwd<T><<<(tot + bs - 1) / bs, bs, 0, st>>>(a.NX1, a.NZ1, (const T*)b, a.V, a.work);
   int thr = a.NX1 < 1024 ? ((a.NX1 + 31) / 32) * 32 : 1024;
   size_t sm = 2 * (size_t)a.NX1 * sizeof(double);
   double* gbuf = nullptr;
@@ -50,11 +48,10 @@ cudaError_t coarse_solve(const CoarseArgs& a, const void* b, void* x, cudaStream
     sm = 0;
   } else if (sm > 48 * 1024) {
     static std::atomic<unsigned long long> s_mask{0};
-    cudaError_t e = ensure_max_smem(k_coarse_fwd_pcr<T>, s_mask);
+    cudaError_t e = ensure_max_smem(k_coarse_pcr, s_mask);
     if (e != cudaSuccess) return e;
   }
-  k_coarse_fwd_pcr<T><<<Nz, thr, sm, st>>>(a.NX1, a.NZ1, a.nsteps, a.periodic, (const T*)b, a.V, a.coef, a.inv,
-                                           a.work, gbuf);
+  k_coarse_pcr<<<Nz, thr, sm, st>>>(a.NX1, a.nsteps, a.periodic, a.coef, a.inv, a.work, gbuf);
   size_t N = (size_t)a.NX1 * a.NZ1;
   k_coarse_bwd<T><<<(unsigned)((N + bs - 1) / bs), bs, 0, st>>>(a.NX1, a.NZ1, a.V, a.work, (T*)x);
   return cudaGetLastError();

@@ -1048,7 +1048,7 @@ pmg_status vcycle(pmg_handle* h, int l, const void* b, void* x, cudaStream_t st)
       h->rec->push_back(v);
       return PMG_OK;
     }
-    return launch(h, PMG_K_COARSE, 2, st, coarse_cost<T>(h), [&] { return coarse_solve<T>(h->coarse, b, x, st); });
+    return launch(h, PMG_K_COARSE, 3, st, coarse_cost<T>(h), [&] { return coarse_solve<T>(h->coarse, b, x, st); });
   }
   // x = 0 before the first sweep.  The FP32 sweep of constant-memory tables reads a zero
   // iterate as zero without loading it and writes every node below the surface row, so on
@@ -2824,7 +2824,7 @@ pmg_status pmg_coarse_solve(pmg_handle* h, const double* b, double* x, void* str
   if (!b || !x) return fail(PMG_ERR_INVALID, "NULL vector");
   DeviceGuard dg(h->device);
   cudaStream_t st = (cudaStream_t)stream;
-  return launch(h, PMG_K_COARSE, 2, st, [&] { return coarse_solve<double>(h->coarse, b, x, st); });
+  return launch(h, PMG_K_COARSE, 3, st, [&] { return coarse_solve<double>(h->coarse, b, x, st); });
 }
 
 pmg_status pmg_vcycle(pmg_handle* h, const void* r, void* z, int f32, void* stream) {

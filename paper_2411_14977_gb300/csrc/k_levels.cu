@@ -93,34 +93,53 @@ template cudaError_t fdm_smooth<float>(const FdmArgs&, cudaStream_t);
 // ------------------------------------------------------------------------------------
 // transfers
 // ------------------------------------------------------------------------------------
-template <typename T>
+template <typename T, int PF = 0, int PC = 0>
 __global__ void __launch_bounds__(512) k_prolong(TransferParams<T> p) {
-  prolong_body<T>(p, blockIdx.x);
+  prolong_body<T, PF, PC>(p, blockIdx.x);
 }
 
-template <typename T>
+template <typename T, int PF = 0, int PC = 0>
 __global__ void __launch_bounds__(512) k_restrict(TransferParams<T> p) {
-  restrict_body<T>(p, blockIdx.x);
+  restrict_body<T, PF, PC>(p, blockIdx.x);
 }
 
+template <typename T, int PF, int PC>
+static cudaError_t launch_transfer(const TransferParams<T>& p, int restrict_, int nx, int thr, size_t sm,
+                                   cudaStream_t st) {
+  cudaError_t e;
+  if (restrict_) {
+    static std::atomic<unsigned long long> s_mask{0};
+    e = ensure_max_smem(k_restrict<T, PF, PC>, s_mask);
+    if (e != cudaSuccess) return e;
+    k_restrict<T, PF, PC><<<nx, thr, sm, st>>>(p);
+  } else {
+    static std::atomic<unsigned long long> s_mask{0};
+    e = ensure_max_smem(k_prolong<T, PF, PC>, s_mask);
+    if (e != cudaSuccess) return e;
+    k_prolong<T, PF, PC><<<nx, thr, sm, st>>>(p);
+  }
+  return cudaGetLastError();
+}
+
+// Level pairs of the coarsening rule (P_c = ceil((P_f + 1) / 2), and 2 -> 1) with equal
+// orders along x and sigma run with compile-time orders; any other pair (custom level
+// orders, semi-coarsened levels) with the orders read at run time.
 template <typename T>
 cudaError_t transfer(const TransferArgs& a, int restrict_, cudaStream_t st) {
   const TransferParams<T> p = transfer_params<T>(a);
   const size_t sm = transfer_smem(a, restrict_, sizeof(T));
   const int thr = (a.threads >= 32 && a.threads <= 512) ? a.threads : 256;
-  cudaError_t e;
-  if (restrict_) {
-    static std::atomic<unsigned long long> s_mask{0};
-    e = ensure_max_smem(k_restrict<T>, s_mask);
-    if (e != cudaSuccess) return e;
-    k_restrict<T><<<a.f.Nx, thr, sm, st>>>(p);
-  } else {
-    static std::atomic<unsigned long long> s_mask{0};
-    e = ensure_max_smem(k_prolong<T>, s_mask);
-    if (e != cudaSuccess) return e;
-    k_prolong<T><<<a.f.Nx, thr, sm, st>>>(p);
+  const int nx = a.f.Nx;
+  if (a.f.pz() == a.f.P && a.c.pz() == a.c.P) {
+    switch (a.f.P * 16 + a.c.P) {
+#define PMG_PAIR(PF, PC) case PF * 16 + PC: return launch_transfer<T, PF, PC>(p, restrict_, nx, thr, sm, st);
+      PMG_PAIR(2, 1) PMG_PAIR(3, 2) PMG_PAIR(4, 3) PMG_PAIR(5, 3) PMG_PAIR(6, 4)
+      PMG_PAIR(7, 4) PMG_PAIR(8, 5) PMG_PAIR(9, 5) PMG_PAIR(10, 6)
+#undef PMG_PAIR
+      default: break;
+    }
   }
-  return cudaGetLastError();
+  return launch_transfer<T, 0, 0>(p, restrict_, nx, thr, sm, st);
 }
 template cudaError_t transfer<double>(const TransferArgs&, int, cudaStream_t);
 template cudaError_t transfer<float>(const TransferArgs&, int, cudaStream_t);

@@ -696,12 +696,14 @@ struct TransferParams {
   const T* mZ;      // [NZf]
 };
 
-// x_f += P x_c
-template <typename T>
+// x_f += P x_c.  PF, PC > 0: the fine and coarse orders (equal along x and sigma) as
+// compile-time constants, so that the 1D interpolation loops unroll and the row-in-element
+// division is by a constant; 0: the orders of the shapes at run time.
+template <typename T, int PF = 0, int PC = 0>
 __device__ __forceinline__ void prolong_body(const TransferParams<T>& p, const int ex) {
   const Shape f = p.f, c = p.c;
-  const int Pf = f.P, Pc = c.P, nf = Pf + 1, nc = Pc + 1;            // along x
-  const int Pfz = f.pz(), Pcz = c.pz(), nfz = Pfz + 1, ncz = Pcz + 1;  // along sigma
+  const int Pf = PF ? PF : f.P, Pc = PC ? PC : c.P, nf = Pf + 1, nc = Pc + 1;  // along x
+  const int Pfz = PF ? PF : f.pz(), Pcz = PC ? PC : c.pz(), nfz = Pfz + 1, ncz = Pcz + 1;  // along sigma
   const int NZf = f.NZ, NZc = c.NZ, NZcp = slab_pitch(NZc), NZfp = slab_pitch(NZf);
   const bool last = !f.periodic && ex == f.Nx - 1;
   const int own = last ? nf : Pf;
@@ -720,6 +722,7 @@ __device__ __forceinline__ void prolong_body(const TransferParams<T>& p, const i
   for_slab(nc, NZf, [&](int k, int iz) {
     int ez = min(iz / Pfz, f.Nz - 1), j = iz - ez * Pfz;
     T acc = T(0);
+#pragma unroll
     for (int l = 0; l < ncz; ++l) acc += Jzs[j * ncz + l] * Xc[k * NZcp + ez * Pcz + l];
     Tz[k * NZfp + iz] = acc;
   });
@@ -727,16 +730,17 @@ __device__ __forceinline__ void prolong_body(const TransferParams<T>& p, const i
   for_slab(own, NZf, [&](int i, int iz) {
     if (iz == NZf - 1) return;
     T acc = T(0);
+#pragma unroll
     for (int k = 0; k < nc; ++k) acc += Js[i * nc + k] * Tz[k * NZfp + iz];
     p.out[(size_t)(ex * Pf + i) * NZf + iz] = Xf[i * NZfp + iz] + acc;
   });
 }
-// r_c = P^T r_f
-template <typename T>
+// r_c = P^T r_f (PF, PC as for prolong_body)
+template <typename T, int PF = 0, int PC = 0>
 __device__ __forceinline__ void restrict_body(const TransferParams<T>& p, const int ex) {
   const Shape f = p.f, c = p.c;
-  const int Pf = f.P, Pc = c.P, nf = Pf + 1, nc = Pc + 1;            // along x
-  const int Pfz = f.pz(), Pcz = c.pz(), nfz = Pfz + 1, ncz = Pcz + 1;  // along sigma
+  const int Pf = PF ? PF : f.P, Pc = PC ? PC : c.P, nf = Pf + 1, nc = Pc + 1;  // along x
+  const int Pfz = PF ? PF : f.pz(), Pcz = PC ? PC : c.pz(), nfz = Pfz + 1, ncz = Pcz + 1;  // along sigma
   const int NZf = f.NZ, NZc = c.NZ, NZfp = slab_pitch(NZf), NZcp = slab_pitch(NZc);
   const bool left = f.periodic || ex > 0;
   const bool last = !f.periodic && ex == f.Nx - 1;
@@ -780,15 +784,21 @@ __device__ __forceinline__ void restrict_body(const TransferParams<T>& p, const 
       int e = q / Pf, li = q - e * Pf;
       if (e == 2) { e = 1; li = Pf; }
       T kx = T(0);
+#pragma unroll
       for (int m = 0; m < nf; ++m) kx += CT<T>::K(cT, Pf, li, m) * Xs[(e * Pf + m) * NZfp + iz];
-      if (li == 0 && e == 1 && left)
+      if (li == 0 && e == 1 && left) {
+#pragma unroll
         for (int m = 0; m < nf; ++m) kx += CT<T>::K(cT, Pf, Pf, m) * Xs[m * NZfp + iz];
+      }
       const int ez = min(iz / Pfz, f.Nz - 1), lj = iz - ez * Pfz;
       const T* col = Xs + q * NZfp;
       T kz = T(0);
+#pragma unroll
       for (int m = 0; m < nfz; ++m) kz += CT<T>::K(cT, Pfz, lj, m) * col[ez * Pfz + m];
-      if (lj == 0 && ez > 0)
+      if (lj == 0 && ez > 0) {
+#pragma unroll
         for (int m = 0; m < nfz; ++m) kz += CT<T>::K(cT, Pfz, Pfz, m) * col[(ez - 1) * Pfz + m];
+      }
       Rf[q * NZfp + iz] -= MZ[iz] * kx + MX[q] * kz;
     });
     __syncthreads();
@@ -800,10 +810,14 @@ __device__ __forceinline__ void restrict_body(const TransferParams<T>& p, const 
       const T* col = Rf + q * NZfp;
       if (l == 0) {
         acc = col[ez * Pfz];
+  #pragma unroll
         for (int j = 1; j < Pfz; ++j) acc += Jzs[j * ncz + 0] * col[ez * Pfz + j];
-        if (ez > 0)
+        if (ez > 0) {
+  #pragma unroll
           for (int j = 1; j < Pfz; ++j) acc += Jzs[j * ncz + Pcz] * col[(ez - 1) * Pfz + j];
+        }
       } else {
+  #pragma unroll
         for (int j = 1; j < Pfz; ++j) acc += Jzs[j * ncz + l] * col[ez * Pfz + j];
       }
     }
@@ -815,13 +829,18 @@ __device__ __forceinline__ void restrict_body(const TransferParams<T>& p, const 
     if (lc != NZc - 1) {
       if (k == 0) {
         acc = Sz[Pf * NZcp + lc];
+  #pragma unroll
         for (int i = 1; i < Pf; ++i) acc += Js[i * nc + 0] * Sz[(Pf + i) * NZcp + lc];
-        if (left)
+        if (left) {
+  #pragma unroll
           for (int i = 1; i < Pf; ++i) acc += Js[i * nc + Pc] * Sz[i * NZcp + lc];
+        }
       } else if (k == Pc) {
         acc = Sz[2 * Pf * NZcp + lc];
+  #pragma unroll
         for (int i = 1; i < Pf; ++i) acc += Js[i * nc + Pc] * Sz[(Pf + i) * NZcp + lc];
       } else {
+  #pragma unroll
         for (int i = 1; i < Pf; ++i) acc += Js[i * nc + k] * Sz[(Pf + i) * NZcp + lc];
       }
     }

@@ -3169,7 +3169,11 @@ pmg_status pmg_autotune(pmg_handle* h) {
   CKS(vtail_setup(h));
   // the decision of the free choice (fuse_coarse = -1) is remembered like a CTA size:
   // 100000 on + 1000 CTAs per SM + threads
-  const auto vkey = std::make_tuple((int)TK_VTAIL, h->mesh.order * 16 + h->vt_l0, h->lv[0].s.NZ, h->mesh.cells_x);
+  // keyed by the fine order and the orders of the fused levels (a custom level sequence
+  // fuses other levels on the same mesh)
+  int vorders = h->mesh.order;
+  for (int l = std::max(h->vt_l0, 1); l < (int)h->lv.size(); ++l) vorders = vorders * 11 + h->lv[l].order;
+  const auto vkey = std::make_tuple((int)TK_VTAIL, vorders, h->lv[0].s.NZ, h->mesh.cells_x);
   int vcached = -1;
   if (h->vt_l0 >= 0 && h->vt_sms > 0 && h->opts.fuse_coarse == -1) {
     std::lock_guard<std::mutex> lk(g_tune_mu);

@@ -21,6 +21,7 @@
 PMG_DEFINE_CONST_TABLES(init_consts_levels)
 
 #include "k_levels.cuh"
+#include "k_levels_batch.h"
 
 namespace pmg {
 
@@ -159,11 +160,11 @@ struct XferBatch {
   BatchMap m;
   TransferParams<float> prm[kMaxBatch];
 };
-template <int RESTRICT>
+template <int RESTRICT, int PF = 0, int PC = 0>
 __global__ void __launch_bounds__(512) k_transfer_batch(const XferBatch* tab) {
   batch_items(tab->m, [&](int r, int ex) {
-    if (RESTRICT) restrict_body<float>(tab->prm[r], ex);
-    else prolong_body<float>(tab->prm[r], ex);
+    if (RESTRICT) restrict_body<float, PF, PC>(tab->prm[r], ex);
+    else prolong_body<float, PF, PC>(tab->prm[r], ex);
     __syncthreads();
   });
 }
@@ -248,6 +249,39 @@ cudaError_t transfer_batch_table(const TransferArgs* a, const int* prob, int n, 
   if (e != cudaSuccess) return e;
   static std::atomic<unsigned long long> s_mask_r{0}, s_mask_p{0};
   return restrict_ ? ensure_max_smem(k_transfer_batch<1>, s_mask_r) : ensure_max_smem(k_transfer_batch<0>, s_mask_p);
+}
+template <int PF, int PC>
+static cudaError_t launch_transfer_batch(const XferBatch* t, int restrict_, int nctas, int threads, size_t smem,
+                                         cudaStream_t st) {
+  int grid = 0;
+  cudaError_t e;
+  if (restrict_) {
+    auto k = k_transfer_batch<1, PF, PC>;
+    static std::atomic<unsigned long long> s_mask{0};
+    e = ensure_max_smem(k, s_mask);
+    if (e == cudaSuccess) e = batch_grid(k, threads, smem, nctas, &grid);
+    if (e != cudaSuccess) return e;
+    k<<<grid, threads, smem, st>>>(t);
+  } else {
+    auto k = k_transfer_batch<0, PF, PC>;
+    static std::atomic<unsigned long long> s_mask{0};
+    e = ensure_max_smem(k, s_mask);
+    if (e == cudaSuccess) e = batch_grid(k, threads, smem, nctas, &grid);
+    if (e != cudaSuccess) return e;
+    k<<<grid, threads, smem, st>>>(t);
+  }
+  return cudaGetLastError();
+}
+cudaError_t transfer_batch_launch_pair(const void* table, int restrict_, int Pf, int Pc, int nctas, int threads,
+                                       size_t smem, cudaStream_t st) {
+  const XferBatch* t = static_cast<const XferBatch*>(table);
+  switch (Pf * 16 + Pc) {
+#define PMG_PAIR(PF, PC) case PF * 16 + PC: return launch_transfer_batch<PF, PC>(t, restrict_, nctas, threads, smem, st);
+    PMG_PAIR(2, 1) PMG_PAIR(3, 2) PMG_PAIR(4, 3) PMG_PAIR(5, 3) PMG_PAIR(6, 4)
+    PMG_PAIR(7, 4) PMG_PAIR(8, 5) PMG_PAIR(9, 5) PMG_PAIR(10, 6)
+#undef PMG_PAIR
+    default: return launch_transfer_batch<0, 0>(t, restrict_, nctas, threads, smem, st);
+  }
 }
 cudaError_t transfer_batch_launch(const void* table, int restrict_, int nctas, int threads, size_t smem,
                                   cudaStream_t st) {

@@ -26,6 +26,7 @@
 #include "host_basis.h"
 #include "pmg.h"
 #include "pmg_kernels.h"
+#include "k_levels_batch.h"
 
 using namespace pmg;
 
@@ -1793,7 +1794,7 @@ struct pmg_batch {
   struct Sub {     // one launch: the problems of one order in a stage
     int kind;      // 0 sweep, 1 level residual, 2 restriction, 3 prolongation, 4 coarse solve,
                    // 5 outer operator with <p, A p>, 6 outer residual
-    int P, O;      // order and overlap of its kernel instantiation
+    int P, O;      // order and overlap of its kernel instantiation (transfers: fine and coarse order)
     int threads;   // CTA size
     void* table;   // device table
     int nctas[3];
@@ -2096,6 +2097,7 @@ pmg_status batch_build_tables(pmg_batch* B) {
       s0.threads = s1.threads = sp.threads = rst.threads = prl.threads = slab_thr;
       r.threads = 256;
       s0.O = s1.O = sp.O = O;
+      rst.O = prl.O = B->h[pi[0]]->lv[l + 1].order;  // transfers: the coarse order of the pair
       s0.kind = s1.kind = sp.kind = 0;
       r.kind = 1;
       rst.kind = 2;
@@ -2157,8 +2159,8 @@ pmg_status batch_sub(const pmg_batch::Sub& u, cudaStream_t cs) {
   switch (u.kind) {
     case 0: CK(fdm32_batch_launch(u.table, u.P, u.O, u.nctas[0], u.threads, u.smem, cs)); break;
     case 1: CK(flat_batch_launch(u.table, u.P, u.nctas[0], u.threads, cs)); break;
-    case 2: CK(transfer_batch_launch(u.table, 1, u.nctas[0], u.threads, u.smem, cs)); break;
-    case 3: CK(transfer_batch_launch(u.table, 0, u.nctas[0], u.threads, u.smem, cs)); break;
+    case 2: CK(transfer_batch_launch_pair(u.table, 1, u.P, u.O, u.nctas[0], u.threads, u.smem, cs)); break;
+    case 3: CK(transfer_batch_launch_pair(u.table, 0, u.P, u.O, u.nctas[0], u.threads, u.smem, cs)); break;
     case 4: CK(coarse_batch_launch(u.table, u.nctas, u.smem, cs)); break;
     case 5: CK(curved_batch_launch(MODE_DOT, u.table, u.P, u.nctas[0], u.threads, u.smem, cs)); break;
     default: CK(curved_batch_launch(MODE_RESIDUAL, u.table, u.P, u.nctas[0], u.threads, u.smem, cs)); break;

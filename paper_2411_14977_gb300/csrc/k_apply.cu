@@ -290,7 +290,7 @@ static cudaError_t curved_batch_table_m(const CurvedArgs* a, const int* prob, in
     p.sc = a[i].sc;
     h->m.prob[i] = prob[i];
     h->m.start[i + 1] = h->m.start[i] + a[i].s.Nx;
-    sm = std::max(sm, curved_smem<df64>(a[i].s.P, a[i].s.NZ, a[i].s.Nz));
+    sm = std::max(sm, curved_smem<df64>(a[i].s.P, a[i].s.NZ, a[i].s.Nz, MODE == MODE_RESIDUAL));
   }
   *nctas = h->m.start[n];
   *smem = sm;

@@ -165,21 +165,23 @@ __device__ __forceinline__ void curved_body(const CurvedParams<T>& p, const int 
   const int NZ = s.NZ, Nz = s.Nz, NZp = slab_pitch(NZ);
   const int L = Nz * n;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* X = reinterpret_cast<T*>(smem_raw);   // [n][NZp]   input slab, later Y
-  T* Ur = X + n * NZp;                      // [n][NZp]   U_r per node row
+  constexpr int NB = MODE == MODE_RESIDUAL ? 1 : 0;  // slabs of b staged beside x
+  T* X = reinterpret_cast<T*>(smem_raw);   // [n][NZp]   input slab (kept to the epilogue)
+  T* Ur = X + n * NZp;                      // [n][NZp]   U_r per node row, later Y
   T* Ws = Ur + n * NZp;                     // [Nz][nz][n] (ez, j, i): U_s then W_s
   T* Wr = Ws + L * nz;                      // [Nz][nz][n] (ez, j, i): W_r
   T* G = Wr + L * nz;                       // [n][NG]
   T* SG = G + NG * n;                       // [NZ] sigma
-  T* BB = SG + NZ;                          // [n][NZp] b (MODE_RESIDUAL) or x (MODE_DOT) of the slab
-  T* RW = BB + n * NZp;                     // [NZ] per row: w_j, w_j sigma, w_j sigma^2
+  T* BB = SG + NZ;                          // [n][NZp] b of the slab (MODE_RESIDUAL only)
+  T* RW = BB + NB * n * NZp;                // [NZ] per row: w_j, w_j sigma, w_j sigma^2
   T* RWS = RW + NZ;
   T* RWS2 = RWS + NZ;
   T* GX = RWS2 + NZ;                        // [n] per column: factor 2 x factor 3
-  size_t red_off = (((size_t)(3 * n * NZp + 2 * L * nz + NG * n + 4 * NZ + n) * sizeof(T)) + 15) & ~(size_t)15;
+  size_t red_off = (((size_t)((2 + NB) * n * NZp + 2 * L * nz + NG * n + 4 * NZ + n) * sizeof(T)) + 15) &
+                   ~(size_t)15;
   double* red = reinterpret_cast<double*>(smem_raw + red_off);  // 34 doubles
   int* s_flag = reinterpret_cast<int*>(red + 34);
-  T* Y = X;
+  T* Y = Ur;  // U_r is dead once the metric (phase 3) has read it
 
   const int col0 = ex * P;
   // ---- load the slab, the column factors and sigma
@@ -189,7 +191,6 @@ __device__ __forceinline__ void curved_body(const CurvedParams<T>& p, const int 
     cp_async_elem(&X[i * NZp + iz], p.x + g, ok);
     if (MODE == MODE_DIV) cp_async_elem(&Ur[i * NZp + iz], p.x2 + g, true);
     if (MODE == MODE_RESIDUAL) cp_async_elem(&BB[i * NZp + iz], p.b + g, true);
-    if (MODE == MODE_DOT) cp_async_elem(&BB[i * NZp + iz], p.x + g, ok);  // X is reused for Y
   });
   cp_async_wait_all();
   for (int t = threadIdx.x; t < NG * n; t += blockDim.x) G[t] = from_io<T>(p.geo[(size_t)ex * NG * n + t]);
@@ -396,7 +397,7 @@ __device__ __forceinline__ void curved_body(const CurvedParams<T>& p, const int 
     } else if (MODE == MODE_DOT) {
       T v = top ? T(0) : val;
       p.y[g] = to_io(v);
-      ac.fma(BB[i * NZp + iz], v);
+      ac.fma(X[i * NZp + iz], v);
     } else {
       p.y[g] = to_io(top ? T(0) : val);
     }
@@ -454,15 +455,15 @@ __global__ void __launch_bounds__(256) k_curved_batch(const CurvedBatch<T, MODE>
 }
 
 template <typename T>
-static size_t curved_smem(int P, int NZ, int Nz, int ng = 4, int PZ = -1) {
+static size_t curved_smem(int P, int NZ, int Nz, bool stage_b, int ng = 4, int PZ = -1) {
   int n = P + 1, nz = (PZ < 0 ? P : PZ) + 1, NZp = slab_pitch(NZ), L = Nz * n;
-  size_t e = (size_t)3 * n * NZp + (size_t)2 * L * nz + (size_t)ng * n + 4 * (size_t)NZ + n;
+  size_t e = (size_t)(stage_b ? 3 : 2) * n * NZp + (size_t)2 * L * nz + (size_t)ng * n + 4 * (size_t)NZ + n;
   return ((e * sizeof(T) + 15) & ~(size_t)15) + 34 * sizeof(double) + 16;
 }
 
 template <int P, typename T, int MODE, int TC, bool MIX = false, bool BATHY = false, int PZ = P>
 static cudaError_t launch_curved_p(const CurvedParams<T>& prm, int threads, cudaStream_t st) {
-  size_t sm = curved_smem<T>(P, prm.s.NZ, prm.s.Nz, MIX ? 5 : (BATHY ? 6 : 4), PZ);
+  size_t sm = curved_smem<T>(P, prm.s.NZ, prm.s.Nz, MODE == MODE_RESIDUAL, MIX ? 5 : (BATHY ? 6 : 4), PZ);
   auto k = k_curved<P, T, MODE, TC, MIX, BATHY, PZ>;
   static std::atomic<unsigned long long> s_mask{0};
   cudaError_t e = ensure_max_smem(k, s_mask);

@@ -3153,16 +3153,28 @@ pmg_status pmg_autotune(pmg_handle* h) {
   // the FP32 build differs with the tensor-core mode and the FP64-vector build with
   // double-float arithmetic: each variant tunes under its own key
   const int curved_key = h->mesh.order + 100 * (h->aniso ? h->mesh.order_z : 0);
+  // besides the usual sizes: the operator's work-item counts per CTA rounded up to whole
+  // warps (the node rows of the x-contractions, the (column, element) pairs of the
+  // sigma-contractions, which also divide the metric phase's element nodes), so that no
+  // phase leaves a partial round of threads idle
+  std::vector<int> curved_cands = {64, 128, 192, 256, 320, 384, 512};
+  {
+    const int NZ0 = h->lv[0].s.NZ, L0 = h->mesh.cells_z * (h->mesh.order + 1);
+    for (int c : {(NZ0 + 31) / 32 * 32, (L0 + 31) / 32 * 32})
+      if (c >= 64 && c <= 512 && std::find(curved_cands.begin(), curved_cands.end(), c) == curved_cands.end())
+        curved_cands.push_back(c);
+    std::sort(curved_cands.begin(), curved_cands.end());
+  }
   CKS(tune_one(h, h->bathy ? TK_CURVED32B : TK_CURVED32, curved_key + 10000 * h->tc, h->lv[0].s.NZ,
                [&](int thr, cudaStream_t cs) {
     h->thr_curved32 = thr;
     return curved<float>(h, 0, h->r32, nullptr, h->w32, 1, nullptr, cs);
-  }, &h->thr_curved32));
+  }, &h->thr_curved32, curved_cands));
   CKS(tune_one(h, h->bathy ? TK_CURVED64B : TK_CURVED64, curved_key + 10000 * (h->df64_outer ? 1 : 0), h->lv[0].s.NZ,
                [&](int thr, cudaStream_t cs) {
     h->thr_curved64 = thr;
     return curved<double>(h, 0, h->p, nullptr, h->w, 1, nullptr, cs);
-  }, &h->thr_curved64));
+  }, &h->thr_curved64, curved_cands));
   // fused coarse V-cycle: the step table again (the tuned residual forms change the
   // recorded steps), then its CTA size and CTAs per SM by timing the whole FP32 V-cycle;
   // with fuse_coarse = -1 it is switched on only where that V-cycle is faster than with
